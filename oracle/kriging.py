@@ -1,0 +1,288 @@
+"""Plain FP64 kriging interpolator on the HEALPix sphere: the CPU oracle.
+
+Test infrastructure: only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` use it.  It shares no code with the CUDA path.
+
+For every target pixel p (RING index) the oracle performs the steps of the
+method in the paper's order:
+
+1. Displaced direction (Sec. 3.1, lensed-direction equation): with |d| the
+   length of the deflection (d_theta, d_phi) in the local basis (e_theta,
+   e_phi) at the pixel centre n,
+       n' = cos|d| n + sin|d| (d_theta e_theta + d_phi e_phi) / |d|.
+2. Stencil: the K pixel centres nearest to n' in chord distance
+   t = |n' - n_q|^2, ties broken by the lower RING index.  The search scans a
+   ring window and proves the result exact by comparing the K-th distance with
+   a lower bound for every pixel outside the window; points where the proof
+   fails are searched again in a larger window.
+3. Covariances (Eqs. fundamental_variance, v_spins): S_ij = xi(t_ij)/xi(0)
+   between stencil pixels, c_i = xi(t(n', n_i))/xi(0) to the target.  Spin 2
+   uses the Hermitian <P_i P_j^*> = xi+(t_ij) exp(2i(a_ij - a_ji)) with a_ij the
+   angle at n_i, measured from e_theta towards e_phi, of the geodesic towards
+   n_j.
+4. Cholesky (Sec. 2.4) of S + n I with the nugget n = epsilon = 1.49e-8 when
+   that factorisation has only positive pivots, and otherwise the paper's rule
+   n = -lambda_min + epsilon (lambda_min the lowest eigenvalue of S).
+5. Conditional mean and variance (Eqs. best_temperature_field, gaussvar,
+   major_eq, gaussvar_pol): with L L^H = S + n I, z_c = L^{-1} conj(c),
+   z_y = L^{-1} y,
+       value = z_c^H z_y,   variance = xi(0) (1 - |z_c|^2).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import healpix as hp
+from . import xi as xi_mod
+
+EPS_NUGGET = 1.49e-8  # square root of the double-precision machine epsilon (Sec. 2.4)
+
+
+# ------------------------------------------------------------- geometry
+def local_basis(v: np.ndarray):
+    """(e_theta, e_phi) at unit vectors v (..., 3); undefined exactly at the poles."""
+    x, y, z = v[..., 0], v[..., 1], v[..., 2]
+    s = np.sqrt(x * x + y * y)
+    cphi = np.where(s > 0, x / np.where(s > 0, s, 1.0), 1.0)
+    sphi = np.where(s > 0, y / np.where(s > 0, s, 1.0), 0.0)
+    e_th = np.stack([z * cphi, z * sphi, -s], axis=-1)
+    e_ph = np.stack([-sphi, cphi, np.zeros_like(s)], axis=-1)
+    return e_th, e_ph
+
+
+def displace(nside: int, pix: np.ndarray, defl: np.ndarray) -> np.ndarray:
+    """Displaced unit vectors n' for target pixels ``pix`` with deflections ``defl`` (n, 2)."""
+    z, s, phi = hp.pix2ang(nside, pix)
+    cphi, sphi = np.cos(phi), np.sin(phi)
+    n = np.stack([s * cphi, s * sphi, z], axis=-1)
+    e_th = np.stack([z * cphi, z * sphi, -s], axis=-1)
+    e_ph = np.stack([-sphi, cphi, np.zeros_like(s)], axis=-1)
+    dth = defl[:, 0]
+    dph = defl[:, 1]
+    dl = np.sqrt(dth * dth + dph * dph)
+    sinc = np.sinc(dl / np.pi)  # sin|d| / |d|, equal to 1 at |d| = 0
+    return (np.cos(dl)[:, None] * n
+            + (sinc * dth)[:, None] * e_th
+            + (sinc * dph)[:, None] * e_ph)
+
+
+def _chord2(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    d = a - b
+    return np.sum(d * d, axis=-1)
+
+
+def knn(nside: int, targets: np.ndarray, K: int, R: int | None = None, W: int | None = None):
+    """Exact K nearest RING pixels to each unit vector in ``targets`` (P, 3).
+
+    Returns (indices (P, K) int64, squared chords (P, K)) sorted by (chord^2, index).
+    """
+    targets = np.asarray(targets, dtype=np.float64)
+    P = targets.shape[0]
+    N = int(nside)
+    rho = math.sqrt(K / 3.0)  # radius of a cap holding K pixels, in units of 1/Nside
+    if R is None:
+        R = int(math.ceil(2.0 * rho / 0.6)) + 1
+    if W is None:
+        W = int(math.ceil(2.0 * rho / 1.1)) + 1
+    idx_out = np.empty((P, K), dtype=np.int64)
+    key_out = np.empty((P, K))
+    todo = np.arange(P)
+    while todo.size:
+        ok, idx, key = _knn_window(N, targets[todo], K, R, W)
+        idx_out[todo[ok]] = idx[ok]
+        key_out[todo[ok]] = key[ok]
+        todo = todo[~ok]
+        R, W = 2 * R, 2 * W
+        if R > 4 * N and W > 4 * N:
+            # the window covers the whole sphere: brute force
+            allpix = np.arange(hp.npix(N))
+            vv = hp.pix2vec(N, allpix)
+            for p in todo:
+                kk = _chord2(targets[p][None, :], vv)
+                order = np.lexsort((allpix, kk))[:K]
+                idx_out[p] = allpix[order]
+                key_out[p] = kk[order]
+            break
+    return idx_out, key_out
+
+
+def _knn_window(N: int, tv: np.ndarray, K: int, R: int, W: int):
+    P = tv.shape[0]
+    z = np.clip(tv[:, 2], -1.0, 1.0)
+    ic = hp.ring_above(N, z)  # ring just north of (or at) the target latitude
+    ic = np.clip(ic, 1, 4 * N - 1)
+    offs = np.arange(-R, R + 2)  # rings ic-R .. ic+R+1
+    rings = ic[:, None] + offs[None, :]
+    rvalid = (rings >= 1) & (rings <= 4 * N - 1)
+    rr = np.clip(rings, 1, 4 * N - 1)
+    first, n_in, zr, sr, f, nq = hp.ring_info(N, rr)
+    phi_t = np.arctan2(tv[:, 1], tv[:, 0]) % (2.0 * np.pi)
+    jc = np.floor(phi_t[:, None] * (2.0 * nq) / np.pi - f + 0.5).astype(np.int64) % n_in
+    m = np.arange(-W, W + 1)
+    nw = 2 * W + 1
+    small = n_in <= nw  # whole ring fits in the window
+    j = np.where(small[..., None], np.arange(nw)[None, None, :],
+                 (jc[..., None] + m[None, None, :]) % n_in[..., None])
+    cvalid = rvalid[..., None] & np.where(small[..., None], np.arange(nw)[None, None, :] < n_in[..., None], True)
+    pix = first[..., None] + j
+    pix = np.where(cvalid, pix, 0)
+    vv = hp.pix2vec(N, pix.reshape(-1)).reshape(P, -1, 3)
+    key = _chord2(tv[:, None, :], vv)
+    cv = cvalid.reshape(P, -1)
+    key = np.where(cv, key, np.inf)
+    pflat = pix.reshape(P, -1)
+    order = np.lexsort((pflat, key), axis=-1)[:, :K]
+    kidx = np.take_along_axis(pflat, order, axis=1)
+    kkey = np.take_along_axis(key, order, axis=1)
+    # lower bound for every pixel outside the window
+    st = np.sqrt(np.maximum(tv[:, 0] ** 2 + tv[:, 1] ** 2, 0.0))
+    lb = np.full(P, np.inf)
+    for side in (0, -1):
+        r_out = rings[:, 0] - 1 if side == 0 else rings[:, -1] + 1
+        inside = (r_out >= 1) & (r_out <= 4 * N - 1)
+        _, _, zo, so, _, _ = hp.ring_info(N, np.clip(r_out, 1, 4 * N - 1))
+        b = (z - zo) ** 2 + (st - so) ** 2
+        lb = np.where(inside, np.minimum(lb, b), lb)
+    # excluded pixels of each window ring: the nearest ones are W+1 steps from jc
+    for dm in (-(W + 1), W + 1):
+        jo = (jc + dm) % n_in
+        po = first + jo
+        vo = hp.pix2vec(N, np.where(rvalid & ~small, po, 0).reshape(-1)).reshape(P, -1, 3)
+        ko = _chord2(tv[:, None, :], vo)
+        ko = np.where(rvalid & ~small, ko, np.inf)
+        lb = np.minimum(lb, ko.min(axis=1))
+    ok = np.isfinite(kkey[:, -1]) & (kkey[:, -1] < lb)
+    return ok, kidx, kkey
+
+
+# ------------------------------------------------------------ linear algebra
+def cholesky_batched(A: np.ndarray):
+    """Cholesky L L^H = A for a batch (P, K, K) of Hermitian matrices.
+
+    Returns (L, ok) where ok[p] is False if a pivot was not positive.
+    """
+    P, K, _ = A.shape
+    L = np.zeros_like(A)
+    ok = np.ones(P, dtype=bool)
+    for j in range(K):
+        d = A[:, j, j].real - np.sum(np.abs(L[:, j, :j]) ** 2, axis=1)
+        ok &= d > 0
+        ljj = np.sqrt(np.where(d > 0, d, 1.0))
+        L[:, j, j] = ljj
+        if j + 1 < K:
+            s = A[:, j + 1:, j] - np.einsum("pik,pk->pi", L[:, j + 1:, :j], np.conj(L[:, j, :j]))
+            L[:, j + 1:, j] = s / ljj[:, None]
+    return L, ok
+
+
+def forward_solve(L: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Solve L z = b for lower-triangular L (P, K, K) and right-hand sides b (P, K)."""
+    P, K, _ = L.shape
+    z = np.zeros(b.shape, dtype=np.result_type(L, b))
+    for j in range(K):
+        z[:, j] = (b[:, j] - np.einsum("pk,pk->p", L[:, j, :j], z[:, :j])) / L[:, j, j]
+    return z
+
+
+def factor_with_nugget(S: np.ndarray, eps: float = EPS_NUGGET):
+    """Cholesky of S + n I with the nugget rule of Sec. 2.4; returns (L, n per point)."""
+    P, K, _ = S.shape
+    eye = np.eye(K)
+    nug = np.full(P, eps)
+    L, ok = cholesky_batched(S + eps * eye)
+    bad = np.nonzero(~ok)[0]
+    if bad.size:
+        lam = np.linalg.eigvalsh(S[bad])[:, 0]
+        nb = np.where(lam < 0, -lam, 0.0) + eps
+        for _ in range(60):
+            Lb, okb = cholesky_batched(S[bad] + nb[:, None, None] * eye)
+            if okb.all():
+                break
+            nb = np.where(okb, nb, nb + eps)  # rounding can leave the shifted matrix indefinite
+        L[bad] = Lb
+        nug[bad] = nb
+    return L, nug
+
+
+# -------------------------------------------------------------- estimator
+@dataclass
+class Result:
+    value: np.ndarray      # (P,) float (spin 0) or complex Q + iU (spin 2)
+    variance: np.ndarray   # (P,)
+    stencil: np.ndarray    # (P, K) RING indices
+    keys: np.ndarray       # (P, K) squared chords to n'
+    nugget: np.ndarray     # (P,)
+    target: np.ndarray     # (P, 3) displaced unit vectors
+
+
+def phase2(va: np.ndarray, vb: np.ndarray) -> np.ndarray:
+    """exp(2i a_ab) where a_ab is the angle at va, from e_theta towards e_phi, of the
+    tangent direction towards vb (the projection of vb - va on the tangent plane)."""
+    e_th, e_ph = local_basis(va)
+    d = vb - va
+    A = np.sum(d * e_th, axis=-1)
+    B = np.sum(d * e_ph, axis=-1)
+    w = A + 1j * B
+    with np.errstate(invalid="ignore", divide="ignore"):  # a point paired with itself has no direction
+        return w * w / (A * A + B * B)
+
+
+def pair_phase(va: np.ndarray, vb: np.ndarray) -> np.ndarray:
+    """Phase of <P(va) P(vb)^*> relative to xi+: exp(2i (a_ab - a_ba))."""
+    return phase2(va, vb) * np.conj(phase2(vb, va))
+
+
+def interpolate(nside: int, K: int, spin: int, maps: np.ndarray, targets: np.ndarray,
+                f_plus, xi_zero: float, eps: float = EPS_NUGGET, batch: int = 4096) -> Result:
+    """Kriging at unit vectors ``targets`` (P, 3) from a RING map.
+
+    ``maps``: (Npix,) real for spin 0; (Npix, 2) (Q, U) for spin 2.
+    ``f_plus``: callable t -> xi(t)/xi(0) (spin 0) or xi+(t)/xi+(0) (spin 2),
+    either an ``xi.HermiteTable`` (tabulated mode) or a direct evaluation.
+    """
+    P = targets.shape[0]
+    vals = np.empty(P, dtype=np.float64 if spin == 0 else np.complex128)
+    var = np.empty(P)
+    sten = np.empty((P, K), dtype=np.int64)
+    keys = np.empty((P, K))
+    nugs = np.empty(P)
+    eye = np.eye(K)
+    for b0 in range(0, P, batch):
+        tv = targets[b0:b0 + batch]
+        idx, key = knn(nside, tv, K)
+        X = hp.pix2vec(nside, idx)  # (B, K, 3)
+        T = _chord2(X[:, :, None, :], X[:, None, :, :])
+        S = f_plus(T.reshape(-1)).reshape(T.shape)
+        c = f_plus(_chord2(tv[:, None, :], X))
+        if spin == 0:
+            y = maps[idx]
+            L, nug = factor_with_nugget(S, eps)
+            zc = forward_solve(L, c)
+            zy = forward_solve(L, y)
+            vals[b0:b0 + batch] = np.sum(zc * zy, axis=1)
+            var[b0:b0 + batch] = xi_zero * (1.0 - np.sum(zc * zc, axis=1))
+        else:
+            Ph = pair_phase(X[:, :, None, :], X[:, None, :, :])
+            C = S * Ph
+            C[:, np.arange(K), np.arange(K)] = 1.0
+            c0 = c * pair_phase(np.broadcast_to(tv[:, None, :], X.shape), X)
+            y = maps[idx, 0] + 1j * maps[idx, 1]
+            L, nug = factor_with_nugget(C, eps)
+            zc = forward_solve(L, np.conj(c0))
+            zy = forward_solve(L, y)
+            vals[b0:b0 + batch] = np.sum(np.conj(zc) * zy, axis=1)
+            var[b0:b0 + batch] = xi_zero * (1.0 - np.sum(np.abs(zc) ** 2, axis=1))
+        sten[b0:b0 + batch] = idx
+        keys[b0:b0 + batch] = key
+        nugs[b0:b0 + batch] = nug
+    return Result(vals, var, sten, keys, nugs, targets)
+
+
+def lens(nside: int, K: int, spin: int, maps: np.ndarray, defl: np.ndarray, pix: np.ndarray,
+         f_plus, xi_zero: float, eps: float = EPS_NUGGET) -> Result:
+    """Lensed values at target pixels ``pix`` (Born remap T(n + d(n)), Sec. 3.1)."""
+    tv = displace(nside, np.asarray(pix, dtype=np.int64), np.asarray(defl, dtype=np.float64))
+    return interpolate(nside, K, spin, maps, tv, f_plus, xi_zero, eps)

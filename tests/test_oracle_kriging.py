@@ -1,0 +1,239 @@
+"""Pins of the oracle's kriging estimator (Secs. 2.1, 2.2, 2.4, 3.1) against closed
+forms, library special cases, brute force and the paper's exact benchmark."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import healpix as hp
+from oracle import kriging as kr
+from oracle import sht
+from oracle import xi
+from tests.wigner_ref import wigner_d
+import workloads as wl
+
+RNG = np.random.default_rng(77)
+
+
+# ------------------------------------------------------------ displacement
+def test_displacement_geodesic():
+    nside = 32
+    pix = RNG.integers(0, hp.npix(nside), 300)
+    defl = RNG.normal(size=(300, 2)) * 3e-3
+    defl[:5] = 0.0
+    n = hp.pix2vec(nside, pix)
+    n2 = kr.displace(nside, pix, defl)
+    assert np.array_equal(n2[:5], n[:5])  # zero deflection leaves the centre in place
+    np.testing.assert_allclose(np.linalg.norm(n2, axis=1), 1.0, atol=2e-16)
+    # geodesic length equals |d|
+    ang = 2 * np.arcsin(np.linalg.norm(n2 - n, axis=1) / 2)
+    np.testing.assert_allclose(ang, np.hypot(defl[:, 0], defl[:, 1]), rtol=1e-12, atol=1e-18)
+    # initial direction is (d_theta, d_phi) in the local basis
+    e_th, e_ph = kr.local_basis(n)
+    a = np.sum((n2 - n) * e_th, axis=1)
+    b = np.sum((n2 - n) * e_ph, axis=1)
+    dl = np.hypot(defl[5:, 0], defl[5:, 1])
+    np.testing.assert_allclose(a[5:] / np.hypot(a[5:], b[5:]), defl[5:, 0] / dl, atol=1e-6)
+    np.testing.assert_allclose(b[5:] / np.hypot(a[5:], b[5:]), defl[5:, 1] / dl, atol=1e-6)
+
+
+# ---------------------------------------------------------- linear algebra
+def test_cholesky_and_solve_against_numpy():
+    P, K = 5, 12
+    X = RNG.normal(size=(P, K, K)) + 1j * RNG.normal(size=(P, K, K))
+    A = X @ np.conj(np.swapaxes(X, 1, 2)) + K * np.eye(K)
+    L, ok = kr.cholesky_batched(A)
+    assert ok.all()
+    np.testing.assert_allclose(L, np.linalg.cholesky(A), atol=1e-12)
+    b = RNG.normal(size=(P, K)) + 1j * RNG.normal(size=(P, K))
+    z = kr.forward_solve(L, b)
+    np.testing.assert_allclose(np.einsum("pij,pj->pi", L, z), b, atol=1e-12)
+
+
+def test_nugget_rule_for_indefinite_matrix():
+    K = 6
+    Q, _ = np.linalg.qr(RNG.normal(size=(K, K)))
+    lam = np.array([-3e-6, 1e-9, 0.1, 0.5, 1.0, 2.0])
+    S = (Q * lam) @ Q.T
+    L, nug = kr.factor_with_nugget(S[None])
+    # n = -lambda_min + epsilon (Sec. 2.4), up to the extra epsilon steps rounding may need
+    assert 3e-6 + kr.EPS_NUGGET - 1e-12 <= nug[0] <= 3e-6 + 3 * kr.EPS_NUGGET
+    np.testing.assert_allclose(L[0] @ L[0].T, S + nug[0] * np.eye(K), atol=1e-14)
+    # a positive-definite matrix takes n = epsilon
+    _, nug = kr.factor_with_nugget(((Q * np.abs(lam)) @ Q.T + 1e-3 * np.eye(K))[None])
+    assert nug[0] == kr.EPS_NUGGET
+
+
+# ------------------------------------------------------------------ spin 0
+@pytest.fixture(scope="module")
+def c1_table():
+    cl = wl.cl_tt(128, 100.0)
+    tmax = 4 * (2.0 * math.sqrt(16 / 3.0) / 64) ** 2
+    tab, x0 = xi.spin0_table(cl, tmax, 512)
+    return cl, tab, x0
+
+
+def test_pixel_centre_returns_pixel_value(c1_table):
+    # At a pixel centre c = S e_q, so with A = S + n I:
+    #   value - y_q = -n (A^-1 y)_q   and   variance = xi(0) n (1 - n (A^-1)_qq)   (closed forms)
+    cl, tab, x0 = c1_table
+    nside, K = 64, 16
+    y = wl.white_map(hp.npix(nside), 1, 11)
+    pix = RNG.integers(0, hp.npix(nside), 200)
+    res = kr.lens(nside, K, 0, y, np.zeros((200, 2)), pix, tab, x0)
+    assert np.all(res.stencil[:, 0] == pix)
+    assert np.all(res.variance <= kr.EPS_NUGGET * x0 * (1 + 1e-9))
+    assert np.all(res.variance >= 0)
+    for p in range(0, 200, 10):
+        X = hp.pix2vec(nside, res.stencil[p])
+        A = tab(np.sum((X[:, None] - X[None]) ** 2, axis=-1)) + kr.EPS_NUGGET * np.eye(K)
+        Ainv = np.linalg.inv(A)
+        gap = -kr.EPS_NUGGET * (Ainv @ y[res.stencil[p]])[0]
+        assert abs((res.value[p] - y[pix[p]]) - gap) < 1e-6 * abs(gap) + 1e-12
+        var = x0 * kr.EPS_NUGGET * (1 - kr.EPS_NUGGET * Ainv[0, 0])
+        assert abs(res.variance[p] - var) < 1e-6 * var
+
+
+def test_weights_match_dense_solve(c1_table):
+    cl, tab, x0 = c1_table
+    nside, K = 64, 16
+    y = wl.white_map(hp.npix(nside), 1, 12)
+    pix = RNG.integers(0, hp.npix(nside), 50)
+    defl = wl.random_deflection(50, 13) * 5
+    res = kr.lens(nside, K, 0, y, defl, pix, tab, x0)
+    for p in range(50):
+        X = hp.pix2vec(nside, res.stencil[p])
+        S = tab(np.sum((X[:, None] - X[None]) ** 2, axis=-1)) + kr.EPS_NUGGET * np.eye(K)
+        c = tab(np.sum((X - res.target[p]) ** 2, axis=-1))
+        w = np.linalg.solve(S, c)
+        assert abs(w @ y[res.stencil[p]] - res.value[p]) < 1e-9 * np.abs(y).max() * np.abs(w).sum()
+        assert abs(x0 * (1 - c @ w) - res.variance[p]) < 1e-10 * x0
+
+
+def test_monopole_limit_weights_sum_to_one():
+    # simple kriging does not reproduce constants, but a large monopole C_0 drives the
+    # weights towards the ordinary-kriging limit sum w = 1 as O(1/C_0)
+    nside, K = 64, 16
+    base = wl.cl_tt(128, 100.0)
+    tmax = 4 * (2.0 * math.sqrt(16 / 3.0) / 64) ** 2
+    pix = RNG.integers(0, hp.npix(nside), 20)
+    defl = wl.random_deflection(20, 14) * 5
+    gaps = []
+    for M in (1e2, 1e4):
+        cl = base.copy()
+        cl[0] = M * np.sum((2 * np.arange(129) + 1) * base) / (4 * math.pi) * 4 * math.pi
+        tab, x0 = xi.spin0_table(cl, tmax, 512)
+        ones = np.ones(hp.npix(nside))
+        res = kr.lens(nside, K, 0, ones, defl, pix, tab, x0)
+        gaps.append(np.max(np.abs(1 - res.value)))
+    assert gaps[1] < gaps[0] / 30
+
+
+# --------------------------------------------------- spin 2 phase convention
+def _sY2(ell, m, v):
+    th = np.arctan2(np.hypot(v[:, 0], v[:, 1]), v[:, 2])
+    ph = np.arctan2(v[:, 1], v[:, 0])
+    # Appendix A: sY_lm = (-1)^s sqrt((2l+1)/4pi) e^{i m phi} d^l_{m,-s}(theta), s = 2
+    return math.sqrt((2 * ell + 1) / (4 * math.pi)) * np.exp(1j * m * ph) * wigner_d(ell, m, -2, th)
+
+
+@pytest.mark.parametrize("ell", [2, 3, 5, 8])
+def test_spin2_pair_phase_by_addition_theorem(ell):
+    a = RNG.normal(size=(40, 3))
+    a /= np.linalg.norm(a, axis=1)[:, None]
+    b = a + RNG.normal(size=(40, 3)) * 0.3
+    b /= np.linalg.norm(b, axis=1)[:, None]
+    corr = sum(_sY2(ell, m, a) * np.conj(_sY2(ell, m, b)) for m in range(-ell, ell + 1))
+    beta = 2 * np.arcsin(np.linalg.norm(a - b, axis=1) / 2)
+    model = (2 * ell + 1) / (4 * math.pi) * wigner_d(ell, 2, 2, beta) * kr.pair_phase(a, b)
+    np.testing.assert_allclose(corr, model, atol=1e-13)
+
+
+def test_spin2_synthesis_matches_harmonics():
+    lmax = 6
+    v = RNG.normal(size=(15, 3))
+    v /= np.linalg.norm(v, axis=1)[:, None]
+    for ell in range(2, lmax + 1):
+        for m in range(0, ell + 1):
+            E = np.zeros((lmax + 1, lmax + 1), complex)
+            E[ell, m] = 0.7 - 0.2j
+            got = sht.synth_points(lmax, E, v, spin=2)
+            a = -E[ell, m]  # a_{2,lm} = -(E + iB)
+            ref = a * _sY2(ell, m, v)
+            if m > 0:
+                ref = ref + (-(-1) ** m * np.conj(E[ell, m])) * _sY2(ell, -m, v)
+            np.testing.assert_allclose(got, ref, atol=1e-14)
+
+
+def test_spin2_frame_covariance():
+    # rotating the local frame of every pixel (P_q -> e^{2i psi_q} P_q, covariances
+    # rotated alike) leaves the estimate unchanged
+    K = 10
+    Q, _ = np.linalg.qr(RNG.normal(size=(K, K)) + 1j * RNG.normal(size=(K, K)))
+    C = (Q * np.linspace(1e-6, 3, K)) @ np.conj(Q.T)
+    c = RNG.normal(size=K) + 1j * RNG.normal(size=K)
+    y = RNG.normal(size=K) + 1j * RNG.normal(size=K)
+    psi = np.exp(2j * RNG.uniform(0, np.pi, K))
+
+    def est(C, c, y):
+        L, _ = kr.factor_with_nugget(C[None])
+        zc = kr.forward_solve(L, np.conj(c)[None])[0]
+        zy = kr.forward_solve(L, y[None])[0]
+        return np.sum(np.conj(zc) * zy)
+
+    v0 = est(C, c, y)
+    v1 = est(psi[:, None] * C * np.conj(psi)[None, :], c * np.conj(psi), psi * y)
+    assert abs(v0 - v1) < 1e-10 * abs(v0)
+
+
+# -------------------------------------------- exact benchmark on C1 (spin 0)
+@pytest.fixture(scope="module")
+def c1_lensed():
+    W = wl.C1
+    cl, _ = W.cl()
+    alm = wl.draw_alm(cl, W.seed_map)
+    phi_alm = wl.draw_alm(wl.cl_phiphi(W.lmax), W.seed_phi)
+    tmap = sht.synth_map(W.nside, W.lmax, alm)
+    defl = sht.synth_map(W.nside, W.lmax, phi_alm, gradient=True)
+    pix = np.arange(W.npix)
+    tmax = 4 * (2.0 * math.sqrt(W.K / 3.0) / W.nside) ** 2 * 1.5
+    tab, x0 = xi.spin0_table(cl, tmax, 1024)
+    res = kr.lens(W.nside, W.K, 0, tmap, defl, pix, tab, x0)
+    truth = sht.synth_points(W.lmax, alm, res.target)
+    return tmap, defl, res, truth, x0
+
+
+def test_c1_deflection_rms(c1_lensed):
+    _, defl, _, _, _ = c1_lensed
+    rms = math.sqrt(np.mean(np.sum(defl ** 2, axis=1)))
+    assert 0.7 * wl.DEFLECTION_RMS < rms < 1.3 * wl.DEFLECTION_RMS
+
+
+def test_c1_error_statistics_match_predicted_variance(c1_lensed):
+    # Sec. 3.2 / Fig. cmb_exp_error: measured error / predicted sigma ~ N(0, 1)
+    tmap, _, res, truth, _ = c1_lensed
+    r = (res.value - truth) / np.sqrt(res.variance)
+    assert abs(np.mean(r)) < 0.05
+    assert 0.9 < np.std(r) < 1.1
+    rel = np.sqrt(np.mean((res.value - truth) ** 2) / np.mean(truth ** 2))
+    assert rel < 0.2
+
+
+def test_spin2_error_statistics_match_predicted_variance():
+    # spin-2 exact benchmark on an Nside 64 sky: Q/U kriged with the Hermitian
+    # xi+ covariance and parallel-transport phases; |error| / sigma ~ unit complex Gaussian
+    nside, lmax, K = 64, 128, 16
+    cl = wl.cl_ee(lmax, 100.0)
+    alm = wl.draw_alm(cl, 21)
+    P = sht.synth_map(nside, lmax, alm, spin=2)
+    qu = np.stack([P.real, P.imag], axis=1)
+    pix = wl.sample_pixels(hp.npix(nside), 4000, 22)
+    defl = wl.random_deflection(pix.size, 23)
+    tmax = 4 * (2.0 * math.sqrt(K / 3.0) / nside) ** 2 * 1.5
+    tp, tm, x0 = xi.spin2_tables(cl, None, tmax, 1024)
+    res = kr.lens(nside, K, 2, qu, defl, pix, tp, x0)
+    truth = sht.synth_points(lmax, alm, res.target, spin=2)
+    r = np.abs(res.value - truth) ** 2 / res.variance
+    assert 0.85 < np.mean(r) < 1.15  # E|P - P_hat|^2 = sigma^2 for a circular Gaussian
+    rel = np.sqrt(np.mean(np.abs(res.value - truth) ** 2) / np.mean(np.abs(truth) ** 2))
+    assert rel < 0.2
