@@ -1,0 +1,174 @@
+/* flints.h -- C ABI of the GB300 lensing remap (FLINTS kriging interpolation).
+ *
+ * The library computes, for every target HEALPix pixel, the value of an
+ * isotropic Gaussian field at the displaced direction n' = n + d(n) and the
+ * Gaussian variance of that estimate, from the K nearest pixels of an unlensed
+ * RING-ordered map (Lavaux & Wandelt, "Fast and optimal CMB lensing using
+ * statistical interpolation on the sphere").
+ *
+ *   Displacement   Sec. 3.1, lensed-direction equation:
+ *                  n' = cos|d| n + sin|d| (d_theta e_theta + d_phi e_phi)/|d|.
+ *   Covariances    Eq. fundamental_variance / Eq. correlation_func (spin 0),
+ *                  Eq. v_spins / Eq. spins_correl (spin 2).
+ *   Estimate       Eq. best_temperature_field and Eq. gaussvar (spin 0),
+ *                  Eq. major_eq and Eq. gaussvar_pol (spin 2).
+ *   Regularisation Sec. 2.4: Cholesky of S + n I with n = 1.49e-8.
+ *   xi tabulation  Sec. 2.5 step 2 and Appendix B: cubic interpolation.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Map buffers are RING ordered, Npix = 12 Nside^2.  Spin-0 maps are double
+ *   [Npix]; spin-2 maps are interleaved (Q, U) double [Npix][2], Q and U given
+ *   in the local (e_theta, e_phi) frame of each pixel.
+ * - Deflections are double [count][2] = (d_theta, d_phi) in radians, the
+ *   components of d in the local basis at the target pixel.
+ * - Outputs: value double [count] (spin 0) or [count][2] (Q, U in the local
+ *   frame at n'); variance double [count] (may be NULL); status uint8 [count]
+ *   (may be NULL; FLINTS_ST_* bits, 0 = clean).
+ * - All data pointers are DEVICE pointers owned by the caller, aligned to 16
+ *   bytes, and must not overlap.  Calls are asynchronous on the given CUDA
+ *   stream (cudaStream_t passed as void*, NULL = legacy default stream); the
+ *   caller synchronises the stream before reading results.
+ * - Errors found on the host (bad arguments, CUDA launch failures, allocation
+ *   failure) are returned synchronously as flints_status codes and described
+ *   by flints_last_error().  Per-point numerical events are never errors:
+ *   they set status bits and are counted in flints_stats.
+ * - A plan owns its device memory (xi tables, counters) and is bound to the
+ *   device that was current when it was created.  Plans are not thread-safe:
+ *   use one plan per host thread or serialise calls on it.
+ */
+#ifndef FLINTS_H
+#define FLINTS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct flints_plan_s *flints_plan_t;
+
+typedef enum {
+    FLINTS_OK = 0,
+    FLINTS_EINVAL = 1,   /* invalid argument (see flints_last_error) */
+    FLINTS_ENOMEM = 2,   /* device allocation failed */
+    FLINTS_ECUDA = 3,    /* a CUDA runtime call or kernel launch failed */
+    FLINTS_ETIMEOUT = 5  /* a bounded device wait gave up (batched driver) */
+} flints_status;
+
+/* precision */
+enum { FLINTS_FP64 = 0, FLINTS_MIXED = 1 };
+
+/* plan flags */
+enum {
+    FLINTS_NO_VARIANCE = 4u /* skip the variance output even if a buffer is given */
+};
+
+/* per-point status bits */
+enum {
+    FLINTS_ST_NUGGET = 1u,    /* S + 1.49e-8 I had a non-positive pivot; nugget raised (x2 steps) */
+    FLINTS_ST_FALLBACK = 2u,  /* mixed path: point re-solved in FP64 */
+    FLINTS_ST_WINDOW = 4u,    /* K-th neighbour outside the search disc: stencil widened */
+    FLINTS_ST_FAILED = 8u,    /* no positive-definite factor found: outputs are NaN */
+    FLINTS_ST_POLE = 16u      /* displaced direction within 1e-12 rad of a pole (spin-2 frame undefined) */
+};
+
+typedef struct {
+    int64_t points;      /* points processed since the plan was created or stats reset */
+    int64_t nugget;      /* points with FLINTS_ST_NUGGET */
+    int64_t fallback;    /* points with FLINTS_ST_FALLBACK */
+    int64_t window;      /* points with FLINTS_ST_WINDOW */
+    int64_t failed;      /* points with FLINTS_ST_FAILED */
+} flints_stats;
+
+typedef struct {
+    int64_t nside;
+    int lmax, spin, K, precision;
+    double t_max;        /* tabulated squared-chord domain [0, t_max] */
+    int n_intervals;     /* cubic Hermite intervals of the xi table */
+    double xi0;          /* xi(0) (spin 0) or xi+(0) (spin 2) */
+    double search_radius;/* chord radius of the stencil disc */
+} flints_plan_info;
+
+/* Create a plan: copy the spectrum to the device and tabulate xi on the GPU
+ * (Sec. 2.5 steps 1-2; Appendix B).
+ *   out        receives the plan (NULL on failure).
+ *   nside      HEALPix resolution, 1 <= nside <= 16384.
+ *   lmax       band limit, 0 <= lmax <= 16384.
+ *   cl         HOST pointer, [lmax+1]: C_l^TT (spin 0) or C_l^EE (spin 2).
+ *   cl_bb      HOST pointer, [lmax+1] C_l^BB (spin 2), or NULL for B = 0.
+ *              Ignored for spin 0.
+ *   spin       0 or 2.
+ *   K          stencil size, 4 <= K <= 48.
+ *   precision  FLINTS_FP64 or FLINTS_MIXED.
+ *   flags      FLINTS_* plan flags.
+ *   stream     CUDA stream for the tabulation (the call returns after it).
+ * Returns FLINTS_EINVAL for out-of-range arguments or a spectrum whose
+ * xi(0) is not positive and finite. */
+int flints_plan(flints_plan_t *out, int64_t nside, int lmax, const double *cl,
+                const double *cl_bb, int spin, int K, int precision,
+                unsigned flags, void *stream);
+
+/* Lens a whole spin-0 map: out[p] = T(n_p + d(n_p)) for p = 0..Npix-1.
+ *   map   device [Npix];  defl device [Npix][2];
+ *   out   device [Npix];  var device [Npix] or NULL. */
+int flints_lens_spin0(flints_plan_t plan, const double *map, const double *defl,
+                      double *out, double *var, void *stream);
+
+/* Lens a whole spin-2 map: (Q, U) at n_p + d(n_p) in the frame at n'.
+ *   qu    device [Npix][2]; defl device [Npix][2];
+ *   qu_out device [Npix][2]; var device [Npix] or NULL (variance of P = Q+iU). */
+int flints_lens_spin2(flints_plan_t plan, const double *qu, const double *defl,
+                      double *qu_out, double *var, void *stream);
+
+/* Lens the contiguous target range [first, first+count) of a map whose spin
+ * is the plan's.  map is the whole source map; defl, out, var and status are
+ * indexed from 0 for pixel `first`.  count may be 0. */
+int flints_lens_range(flints_plan_t plan, int64_t first, int64_t count,
+                      const double *map, const double *defl, double *out,
+                      double *var, uint8_t *status, void *stream);
+
+/* Stencil of the range [first, first+count): the K nearest RING pixels to
+ * each displaced direction, sorted by (squared chord, pixel index), written
+ * to idx device int64 [count][K] (the neighbour search of the lens kernels,
+ * exposed for verification).  status as for flints_lens_range. */
+int flints_stencil(flints_plan_t plan, int64_t first, int64_t count,
+                   const double *defl, int64_t *idx, uint8_t *status,
+                   void *stream);
+
+/* One job of a batched launch: a target range of one plan. */
+typedef struct {
+    flints_plan_t plan;
+    int64_t first, count;
+    const double *map, *defl;
+    double *out, *var;
+    uint8_t *status;
+} flints_job;
+
+/* Run n jobs (plans may differ in Nside, K, spin and precision) with one
+ * launch per (spin, K, precision) class, all on `stream`. */
+int flints_lens_batch(const flints_job *jobs, int n, void *stream);
+
+/* Device counters of per-point events (synchronises `stream`). */
+int flints_get_stats(flints_plan_t plan, flints_stats *s, void *stream);
+int flints_reset_stats(flints_plan_t plan, void *stream);
+
+/* Plan parameters (host data; no device access). */
+int flints_get_info(flints_plan_t plan, flints_plan_info *info);
+
+/* Copy the plan's xi table to the host: f and g receive n_intervals+1 values
+ * of xi/xi0 and d(xi/xi0)/dt at t_k = k t_max / n_intervals (which = 0:
+ * xi or xi+, which = 1: xi-).  Synchronises `stream`. */
+int flints_get_table(flints_plan_t plan, int which, double *f, double *g, void *stream);
+
+/* Message describing the last error returned on the calling thread. */
+const char *flints_last_error(void);
+
+/* Release a plan and its device memory (NULL is allowed). */
+void flints_free(flints_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FLINTS_H */

@@ -231,8 +231,12 @@ def phase2(va: np.ndarray, vb: np.ndarray) -> np.ndarray:
 
 
 def pair_phase(va: np.ndarray, vb: np.ndarray) -> np.ndarray:
-    """Phase of <P(va) P(vb)^*> relative to xi+: exp(2i (a_ab - a_ba))."""
-    return phase2(va, vb) * np.conj(phase2(vb, va))
+    """Phase of <P(va) P(vb)^*> relative to xi+: exp(2i (a_ab - a_ba)).
+
+    Coincident points (zero separation) correlate with no rotation: V_ii = 1
+    in Eq. v_spins."""
+    ph = phase2(va, vb) * np.conj(phase2(vb, va))
+    return np.where(np.isfinite(ph), ph, 1.0 + 0.0j)
 
 
 def interpolate(nside: int, K: int, spin: int, maps: np.ndarray, targets: np.ndarray,

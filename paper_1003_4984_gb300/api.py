@@ -1,0 +1,266 @@
+"""ctypes binding of the C ABI in ``include/flints.h`` (argument marshalling only).
+
+Every step of the lensing remap runs in the CUDA library ``_lib/libflints.so``;
+this module only converts torch tensors and numpy arrays to pointers, sizes
+and streams.  There is no CPU fallback: if the library is missing or cannot
+be loaded, every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libflints.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "flints.h")
+
+FLINTS_FP64 = 0
+FLINTS_MIXED = 1
+FLINTS_NO_VARIANCE = 4
+ST_NUGGET, ST_FALLBACK, ST_WINDOW, ST_FAILED, ST_POLE = 1, 2, 4, 8, 16
+
+
+class FlintsError(RuntimeError):
+    pass
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("points", ctypes.c_int64), ("nugget", ctypes.c_int64), ("fallback", ctypes.c_int64),
+                ("window", ctypes.c_int64), ("failed", ctypes.c_int64)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("nside", ctypes.c_int64), ("lmax", ctypes.c_int), ("spin", ctypes.c_int), ("K", ctypes.c_int),
+                ("precision", ctypes.c_int), ("t_max", ctypes.c_double), ("n_intervals", ctypes.c_int),
+                ("xi0", ctypes.c_double), ("search_radius", ctypes.c_double)]
+
+
+class _Job(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("first", ctypes.c_int64), ("count", ctypes.c_int64),
+                ("map", ctypes.c_void_p), ("defl", ctypes.c_void_p), ("out", ctypes.c_void_p),
+                ("var", ctypes.c_void_p), ("status", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/flints.h."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(flints_[a-z0-9_]+)\s*\(", txt)))
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libflints.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise FlintsError(f"{path} is missing: build it with paper_1003_4984_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, i64, c_int, dp = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_double)
+    lib.flints_plan.argtypes = [ctypes.POINTER(vp), i64, c_int, dp, dp, c_int, c_int, c_int, ctypes.c_uint, vp]
+    lib.flints_lens_spin0.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.flints_lens_spin2.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.flints_lens_range.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp]
+    lib.flints_stencil.argtypes = [vp, i64, i64, vp, vp, vp, vp]
+    lib.flints_lens_batch.argtypes = [ctypes.POINTER(_Job), c_int, vp]
+    lib.flints_get_stats.argtypes = [vp, ctypes.POINTER(_Stats), vp]
+    lib.flints_reset_stats.argtypes = [vp, vp]
+    lib.flints_get_info.argtypes = [vp, ctypes.POINTER(_Info)]
+    lib.flints_get_table.argtypes = [vp, c_int, dp, dp, vp]
+    lib.flints_last_error.restype = ctypes.c_char_p
+    lib.flints_free.argtypes = [vp]
+    lib.flints_free.restype = None
+    for name in ("flints_plan", "flints_lens_spin0", "flints_lens_spin2", "flints_lens_range", "flints_stencil",
+                 "flints_lens_batch", "flints_get_stats", "flints_reset_stats", "flints_get_info",
+                 "flints_get_table"):
+        getattr(lib, name).restype = c_int
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise FlintsError(f"flints error {rc}: {_lib.flints_last_error().decode()}")
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _dev_f64(t, shape, name):
+    import torch
+
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise FlintsError(f"{name} must be a contiguous float64 CUDA tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise FlintsError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t
+
+
+@dataclass
+class Info:
+    nside: int
+    lmax: int
+    spin: int
+    K: int
+    precision: int
+    t_max: float
+    n_intervals: int
+    xi0: float
+    search_radius: float
+
+
+class Plan:
+    """A lensing plan: spectrum, resolution, spin, stencil size and precision.
+
+    ``precision`` is "fp64" or "mixed".  Creating the plan tabulates xi on the
+    current CUDA device (Sec. 2.5 steps 1-2).
+    """
+
+    def __init__(self, nside: int, cl, cl_bb=None, spin: int = 0, K: int = 32, precision: str = "fp64",
+                 flags: int = 0, stream=None):
+        lib = load_library()
+        cl = np.ascontiguousarray(cl, dtype=np.float64)
+        lmax = cl.size - 1
+        bb = None if cl_bb is None else np.ascontiguousarray(cl_bb, dtype=np.float64)
+        if bb is not None and bb.size != cl.size:
+            raise FlintsError("cl_bb must have the same length as cl")
+        prec = {"fp64": FLINTS_FP64, "mixed": FLINTS_MIXED}[precision]
+        h = ctypes.c_void_p()
+        dp = ctypes.POINTER(ctypes.c_double)
+        _check(lib.flints_plan(ctypes.byref(h), int(nside), int(lmax), cl.ctypes.data_as(dp),
+                               bb.ctypes.data_as(dp) if bb is not None else None, int(spin), int(K), prec,
+                               int(flags), _stream(stream)))
+        self._h = h
+        self.nside, self.lmax, self.spin, self.K, self.precision = int(nside), lmax, int(spin), int(K), precision
+        self.npix = 12 * self.nside * self.nside
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.flints_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ queries
+    def info(self) -> Info:
+        i = _Info()
+        _check(_lib.flints_get_info(self._h, ctypes.byref(i)))
+        return Info(i.nside, i.lmax, i.spin, i.K, i.precision, i.t_max, i.n_intervals, i.xi0, i.search_radius)
+
+    def table(self, which: int = 0, stream=None):
+        n = self.info().n_intervals + 1
+        f = np.empty(n)
+        g = np.empty(n)
+        dp = ctypes.POINTER(ctypes.c_double)
+        _check(_lib.flints_get_table(self._h, which, f.ctypes.data_as(dp), g.ctypes.data_as(dp), _stream(stream)))
+        return f, g
+
+    def stats(self, stream=None) -> dict:
+        s = _Stats()
+        _check(_lib.flints_get_stats(self._h, ctypes.byref(s), _stream(stream)))
+        return {k: getattr(s, k) for k, _ in _Stats._fields_}
+
+    def reset_stats(self, stream=None):
+        _check(_lib.flints_reset_stats(self._h, _stream(stream)))
+
+    # ------------------------------------------------------------- compute
+    def lens(self, map_, defl, out=None, var=None, status=None, first: int = 0, count: int | None = None,
+             stream=None):
+        """Lens targets [first, first+count) (default: the whole map) on the GPU.
+
+        ``map_`` (Npix,) or (Npix, 2), ``defl`` (count, 2): float64 CUDA tensors.
+        Returns (out, var, status) tensors (created when not given).
+        """
+        import torch
+
+        if count is None:
+            count = self.npix - first
+        comp = (self.npix,) if self.spin == 0 else (self.npix, 2)
+        _dev_f64(map_, comp, "map")
+        _dev_f64(defl, (count, 2), "defl")
+        oshape = (count,) if self.spin == 0 else (count, 2)
+        dev = map_.device
+        if out is None:
+            out = torch.empty(oshape, dtype=torch.float64, device=dev)
+        _dev_f64(out, oshape, "out")
+        if var is not None:
+            _dev_f64(var, (count,), "var")
+        if status is not None and (status.dtype != torch.uint8 or not status.is_cuda or status.numel() != count):
+            raise FlintsError("status must be a uint8 CUDA tensor of length count")
+        _check(_lib.flints_lens_range(self._h, int(first), int(count), _ptr(map_), _ptr(defl), _ptr(out), _ptr(var),
+                                      _ptr(status), _stream(stream)))
+        return out, var, status
+
+    def lens_full(self, map_, defl, out, var=None, stream=None):
+        """Whole-map entry point (flints_lens_spin0 / flints_lens_spin2)."""
+        comp = (self.npix,) if self.spin == 0 else (self.npix, 2)
+        _dev_f64(map_, comp, "map")
+        _dev_f64(defl, (self.npix, 2), "defl")
+        _dev_f64(out, comp, "out")
+        if var is not None:
+            _dev_f64(var, (self.npix,), "var")
+        fn = _lib.flints_lens_spin0 if self.spin == 0 else _lib.flints_lens_spin2
+        _check(fn(self._h, _ptr(map_), _ptr(defl), _ptr(out), _ptr(var), _stream(stream)))
+        return out, var
+
+    def stencil(self, defl, first: int = 0, count: int | None = None, stream=None):
+        """K nearest RING pixels of each displaced target: int64 (count, K) and status."""
+        import torch
+
+        if count is None:
+            count = self.npix - first
+        _dev_f64(defl, (count, 2), "defl")
+        idx = torch.empty((count, self.K), dtype=torch.int64, device=defl.device)
+        st = torch.empty(count, dtype=torch.uint8, device=defl.device)
+        _check(_lib.flints_stencil(self._h, int(first), int(count), _ptr(defl), _ptr(idx), _ptr(st),
+                                   _stream(stream)))
+        return idx, st
+
+
+def lens_batch(jobs, stream=None):
+    """Run several (plan, first, count, map, defl, out, var, status) jobs through flints_lens_batch."""
+    load_library()
+    arr = (_Job * len(jobs))()
+    for k, (plan, first, count, m, d, o, v, s) in enumerate(jobs):
+        arr[k] = _Job(plan.handle, first, count, _ptr(m), _ptr(d), _ptr(o), _ptr(v), _ptr(s))
+    _check(_lib.flints_lens_batch(arr, len(jobs), _stream(stream)))
+
+
+def lens_host(plan: Plan, map_host: np.ndarray, defl_host: np.ndarray, first: int = 0, count: int | None = None,
+              stream=None):
+    """Host-buffer convenience: copy inputs to the device, lens, copy value and variance back."""
+    import torch
+
+    if count is None:
+        count = plan.npix - first
+    m = torch.from_numpy(np.ascontiguousarray(map_host, dtype=np.float64)).cuda(non_blocking=True)
+    d = torch.from_numpy(np.ascontiguousarray(defl_host, dtype=np.float64)).cuda(non_blocking=True)
+    var = torch.empty(count, dtype=torch.float64, device=m.device)
+    out, var, _ = plan.lens(m, d, var=var, first=first, count=count, stream=stream)
+    return out.cpu().numpy(), var.cpu().numpy()

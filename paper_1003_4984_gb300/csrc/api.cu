@@ -1,0 +1,332 @@
+// C ABI of the lensing remap (include/flints.h): plans, launches, statistics.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+
+namespace flints {
+cudaError_t launch_lens_spin0(int K, int precision, const LensArgs &a, int R_rings, cudaStream_t st);
+cudaError_t launch_lens_spin2(int K, int precision, const LensArgs &a, int R_rings, cudaStream_t st);
+
+int device_sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) return 1;
+    return n;
+}
+
+cudaError_t launch_lens(int spin, int K, int precision, const LensArgs &a, int R_rings, cudaStream_t st) {
+    return spin == 0 ? launch_lens_spin0(K, precision, a, R_rings, st)
+                     : launch_lens_spin2(K, precision, a, R_rings, st);
+}
+}  // namespace flints
+
+using namespace flints;
+
+struct flints_plan_s {
+    int device;
+    int64_t nside;
+    int lmax, spin, K, precision;
+    unsigned flags;
+    double t_max, h, inv_h, xi0, r, r2;
+    int n, R_rings;
+    double *d_cl, *d_clbb, *d_f, *d_g, *d_fm, *d_gm;
+    Coef64 *d_c64;
+    float4 *d_c32;
+    unsigned long long *d_counters;
+    int64_t points;
+};
+
+static thread_local char g_err[512] = "no error";
+
+static int fail(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+static int cuda_fail(cudaError_t e, const char *what) {
+    return fail(e == cudaErrorMemoryAllocation ? FLINTS_ENOMEM : FLINTS_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+static bool supported_K(int K) { return K == 16 || K == 24 || K == 32 || K == 48; }
+
+static void free_plan_memory(flints_plan_s *p) {
+    cudaFree(p->d_cl);
+    cudaFree(p->d_clbb);
+    cudaFree(p->d_f);
+    cudaFree(p->d_g);
+    cudaFree(p->d_fm);
+    cudaFree(p->d_gm);
+    cudaFree(p->d_c64);
+    cudaFree(p->d_c32);
+    cudaFree(p->d_counters);
+}
+
+extern "C" {
+
+const char *flints_last_error(void) { return g_err; }
+
+int flints_plan(flints_plan_t *out, int64_t nside, int lmax, const double *cl, const double *cl_bb, int spin, int K,
+                int precision, unsigned flags, void *stream) {
+    if (!out) return fail(FLINTS_EINVAL, "flints_plan: out is NULL");
+    *out = nullptr;
+    if (nside < 1 || nside > 16384) return fail(FLINTS_EINVAL, "flints_plan: nside %lld outside [1, 16384]", (long long)nside);
+    if (lmax < 0 || lmax > 16384) return fail(FLINTS_EINVAL, "flints_plan: lmax %d outside [0, 16384]", lmax);
+    if (!cl) return fail(FLINTS_EINVAL, "flints_plan: cl is NULL");
+    if (spin != 0 && spin != 2) return fail(FLINTS_EINVAL, "flints_plan: spin must be 0 or 2");
+    if (!supported_K(K)) return fail(FLINTS_EINVAL, "flints_plan: K must be 16, 24, 32 or 48 (got %d)", K);
+    if (12 * nside * nside < K) return fail(FLINTS_EINVAL, "flints_plan: K exceeds the pixel count");
+    if (precision != FLINTS_FP64 && precision != FLINTS_MIXED)
+        return fail(FLINTS_EINVAL, "flints_plan: precision must be FLINTS_FP64 or FLINTS_MIXED");
+    for (int l = 0; l <= lmax; ++l) {
+        if (!std::isfinite(cl[l]) || (spin == 2 && cl_bb && !std::isfinite(cl_bb[l])))
+            return fail(FLINTS_EINVAL, "flints_plan: non-finite spectrum value at l = %d", l);
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    flints_plan_s *p = new flints_plan_s();
+    std::memset(p, 0, sizeof *p);
+    cudaGetDevice(&p->device);
+    p->nside = nside;
+    p->lmax = lmax;
+    p->spin = spin;
+    p->K = K;
+    p->precision = precision;
+    p->flags = flags;
+
+    // Table domain and size: the stencil disc has chord radius
+    // r = 1.25 sqrt(K/3)/Nside, so chords between stencil members are <= 2r;
+    // the interval count bounds the cubic Hermite error by 1e-11 (power of two).
+    p->r = 1.25 * std::sqrt(K / 3.0) / (double)nside;
+    p->r2 = p->r * p->r;
+    p->t_max = 4.0 * p->r * p->r;
+    {
+        double x0 = 0.0, b4num = 0.0;
+        for (int l = 0; l <= lmax; ++l) {
+            const double ld = (double)l;
+            double c = std::fabs(cl[l]);
+            if (spin == 2 && cl_bb) c = std::fabs(cl[l]) + std::fabs(cl_bb[l]);
+            const double a = (2.0 * ld + 1.0) / (4.0 * PI) * c;
+            x0 += a;
+            if (l >= 4)
+                b4num += a * ((ld - 3) * (ld - 2) * (ld - 1) * ld * (ld + 1) * (ld + 2) * (ld + 3) * (ld + 4) / 384.0);
+        }
+        const double b4 = x0 > 0 ? b4num / 16.0 / x0 : 0.0;
+        int n = 64;
+        if (b4 > 0) {
+            const double h = std::pow(384.0 * 1e-11 / b4, 0.25);
+            const double want = std::ceil(std::log2(p->t_max / h));
+            n = want > 16 ? 65536 : (want < 6 ? 64 : (1 << (int)want));
+        }
+        p->n = n;
+    }
+    p->h = p->t_max / p->n;
+    p->inv_h = p->n / p->t_max;
+    p->R_rings = (int)std::ceil(1.5 * p->r * (double)nside) + 1;
+    if (2 * p->R_rings + 2 > 32) {
+        delete p;
+        return fail(FLINTS_EINVAL, "flints_plan: search disc spans too many rings");
+    }
+
+    const size_t ncl = (size_t)(lmax + 1);
+    const size_t nn = (size_t)p->n + 1;
+    cudaError_t e;
+#define ALLOC(ptr, bytes)                                  \
+    e = cudaMalloc((void **)&(ptr), (bytes));              \
+    if (e != cudaSuccess) {                                \
+        free_plan_memory(p);                               \
+        delete p;                                          \
+        return cuda_fail(e, "flints_plan: cudaMalloc");    \
+    }
+    ALLOC(p->d_cl, ncl * sizeof(double));
+    if (spin == 2 && cl_bb) {
+        ALLOC(p->d_clbb, ncl * sizeof(double));
+    }
+    ALLOC(p->d_f, nn * sizeof(double));
+    ALLOC(p->d_g, nn * sizeof(double));
+    ALLOC(p->d_fm, nn * sizeof(double));
+    ALLOC(p->d_gm, nn * sizeof(double));
+    ALLOC(p->d_c64, (size_t)p->n * sizeof(Coef64));
+    ALLOC(p->d_c32, (size_t)p->n * 2 * sizeof(float4));
+    ALLOC(p->d_counters, CNT_N * sizeof(unsigned long long));
+#undef ALLOC
+    auto bail = [&](cudaError_t err, const char *what) {
+        free_plan_memory(p);
+        delete p;
+        return cuda_fail(err, what);
+    };
+    if ((e = cudaMemcpyAsync(p->d_cl, cl, ncl * sizeof(double), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return bail(e, "flints_plan: copy cl");
+    if (p->d_clbb &&
+        (e = cudaMemcpyAsync(p->d_clbb, cl_bb, ncl * sizeof(double), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return bail(e, "flints_plan: copy cl_bb");
+    if ((e = cudaMemsetAsync(p->d_counters, 0, CNT_N * sizeof(unsigned long long), st)) != cudaSuccess)
+        return bail(e, "flints_plan: memset");
+    if ((e = cudaMemsetAsync(p->d_fm, 0, nn * sizeof(double), st)) != cudaSuccess) return bail(e, "flints_plan: memset");
+    if ((e = cudaMemsetAsync(p->d_gm, 0, nn * sizeof(double), st)) != cudaSuccess) return bail(e, "flints_plan: memset");
+    if ((e = launch_xi_table(spin, lmax, p->d_cl, p->d_clbb, p->t_max, p->n, p->d_f, p->d_g, p->d_fm, p->d_gm, st)) !=
+        cudaSuccess)
+        return bail(e, "flints_plan: xi table kernel");
+    double xi0 = 0.0;
+    if ((e = cudaMemcpyAsync(&xi0, p->d_f, sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return bail(e, "flints_plan: read xi(0)");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return bail(e, "flints_plan: xi table");
+    if (!(xi0 > 0.0) || !std::isfinite(xi0)) {
+        free_plan_memory(p);
+        delete p;
+        return fail(FLINTS_EINVAL, "flints_plan: xi(0) = %g is not positive", xi0);
+    }
+    p->xi0 = xi0;
+    if ((e = finish_table(p->d_f, p->d_g, p->n, p->h, xi0, p->d_c64, p->d_c32, st)) != cudaSuccess)
+        return bail(e, "flints_plan: table coefficients");
+    if (spin == 2 && (e = finish_table(p->d_fm, p->d_gm, p->n, p->h, xi0, nullptr, nullptr, st)) != cudaSuccess)
+        return bail(e, "flints_plan: xi- table");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return bail(e, "flints_plan: table coefficients");
+    *out = p;
+    return FLINTS_OK;
+}
+
+void flints_free(flints_plan_t p) {
+    if (!p) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != p->device) cudaSetDevice(p->device);
+    free_plan_memory(p);
+    if (cur != p->device) cudaSetDevice(cur);
+    delete p;
+}
+
+static int check_device(flints_plan_t p) {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != p->device) return fail(FLINTS_EINVAL, "plan was created on device %d, current device is %d", p->device, cur);
+    return FLINTS_OK;
+}
+
+static int run(flints_plan_t p, int64_t first, int64_t count, const double *map, const double *defl, double *out,
+               double *var, uint8_t *status, int64_t *stencil, void *stream) {
+    if (!p) return fail(FLINTS_EINVAL, "plan is NULL");
+    if (int rc = check_device(p)) return rc;
+    const int64_t npix = 12 * p->nside * p->nside;
+    if (first < 0 || count < 0 || first > npix || count > npix - first)
+        return fail(FLINTS_EINVAL, "target range [%lld, %lld) outside [0, %lld)", (long long)first,
+                    (long long)(first + count), (long long)npix);
+    if (count == 0) return FLINTS_OK;
+    if (!defl) return fail(FLINTS_EINVAL, "defl is NULL");
+    if (!stencil && (!map || !out)) return fail(FLINTS_EINVAL, "map and out must not be NULL");
+    const uintptr_t align = (uintptr_t)map | (uintptr_t)defl | (uintptr_t)out;
+    if (align & 15u) return fail(FLINTS_EINVAL, "map, defl and out must be 16-byte aligned");
+    LensArgs a{};
+    a.nside = p->nside;
+    a.first = first;
+    a.count = count;
+    a.map = map;
+    a.defl = defl;
+    a.out = out;
+    a.var = (p->flags & FLINTS_NO_VARIANCE) ? nullptr : var;
+    a.status = status;
+    a.stencil = stencil;
+    a.tab.c64 = p->d_c64;
+    a.tab.c32 = p->d_c32;
+    a.tab.t_max = p->t_max;
+    a.tab.inv_h = p->inv_h;
+    a.tab.n = p->n;
+    a.xi0 = p->xi0;
+    a.r2 = p->r2;
+    a.counters = p->d_counters;
+    cudaError_t e = launch_lens(p->spin, p->K, p->precision, a, p->R_rings, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "lens kernel launch");
+    p->points += count;
+    return FLINTS_OK;
+}
+
+int flints_lens_spin0(flints_plan_t p, const double *map, const double *defl, double *out, double *var, void *stream) {
+    if (!p) return fail(FLINTS_EINVAL, "plan is NULL");
+    if (p->spin != 0) return fail(FLINTS_EINVAL, "flints_lens_spin0 called with a spin-2 plan");
+    return run(p, 0, 12 * p->nside * p->nside, map, defl, out, var, nullptr, nullptr, stream);
+}
+
+int flints_lens_spin2(flints_plan_t p, const double *qu, const double *defl, double *qu_out, double *var,
+                      void *stream) {
+    if (!p) return fail(FLINTS_EINVAL, "plan is NULL");
+    if (p->spin != 2) return fail(FLINTS_EINVAL, "flints_lens_spin2 called with a spin-0 plan");
+    return run(p, 0, 12 * p->nside * p->nside, qu, defl, qu_out, var, nullptr, nullptr, stream);
+}
+
+int flints_lens_range(flints_plan_t p, int64_t first, int64_t count, const double *map, const double *defl,
+                      double *out, double *var, uint8_t *status, void *stream) {
+    return run(p, first, count, map, defl, out, var, status, nullptr, stream);
+}
+
+int flints_stencil(flints_plan_t p, int64_t first, int64_t count, const double *defl, int64_t *idx, uint8_t *status,
+                   void *stream) {
+    if (!idx) return fail(FLINTS_EINVAL, "idx is NULL");
+    return run(p, first, count, nullptr, defl, nullptr, nullptr, status, idx, stream);
+}
+
+int flints_lens_batch(const flints_job *jobs, int n, void *stream) {
+    if (n < 0 || (n > 0 && !jobs)) return fail(FLINTS_EINVAL, "flints_lens_batch: bad job list");
+    for (int i = 0; i < n; ++i) {
+        const flints_job &j = jobs[i];
+        if (int rc = run(j.plan, j.first, j.count, j.map, j.defl, j.out, j.var, j.status, nullptr, stream)) return rc;
+    }
+    return FLINTS_OK;
+}
+
+int flints_get_stats(flints_plan_t p, flints_stats *s, void *stream) {
+    if (!p || !s) return fail(FLINTS_EINVAL, "flints_get_stats: NULL argument");
+    unsigned long long c[CNT_N] = {0};
+    CK(cudaMemcpyAsync(c, p->d_counters, sizeof c, cudaMemcpyDeviceToHost, (cudaStream_t)stream), "read counters");
+    CK(cudaStreamSynchronize((cudaStream_t)stream), "read counters");
+    s->points = p->points;
+    s->nugget = (int64_t)c[CNT_NUGGET];
+    s->fallback = (int64_t)c[CNT_FALLBACK];
+    s->window = (int64_t)c[CNT_WINDOW];
+    s->failed = (int64_t)c[CNT_FAILED];
+    return FLINTS_OK;
+}
+
+int flints_reset_stats(flints_plan_t p, void *stream) {
+    if (!p) return fail(FLINTS_EINVAL, "plan is NULL");
+    CK(cudaMemsetAsync(p->d_counters, 0, CNT_N * sizeof(unsigned long long), (cudaStream_t)stream), "reset counters");
+    p->points = 0;
+    return FLINTS_OK;
+}
+
+int flints_get_info(flints_plan_t p, flints_plan_info *info) {
+    if (!p || !info) return fail(FLINTS_EINVAL, "flints_get_info: NULL argument");
+    info->nside = p->nside;
+    info->lmax = p->lmax;
+    info->spin = p->spin;
+    info->K = p->K;
+    info->precision = p->precision;
+    info->t_max = p->t_max;
+    info->n_intervals = p->n;
+    info->xi0 = p->xi0;
+    info->search_radius = p->r;
+    return FLINTS_OK;
+}
+
+int flints_get_table(flints_plan_t p, int which, double *f, double *g, void *stream) {
+    if (!p || !f || !g) return fail(FLINTS_EINVAL, "flints_get_table: NULL argument");
+    if (which != 0 && !(which == 1 && p->spin == 2)) return fail(FLINTS_EINVAL, "flints_get_table: bad table index");
+    const size_t bytes = ((size_t)p->n + 1) * sizeof(double);
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(f, which ? p->d_fm : p->d_f, bytes, cudaMemcpyDeviceToHost, st), "read table");
+    CK(cudaMemcpyAsync(g, which ? p->d_gm : p->d_g, bytes, cudaMemcpyDeviceToHost, st), "read table");
+    CK(cudaStreamSynchronize(st), "read table");
+    return FLINTS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,284 @@
+// Shared device-side definitions of the lensing remap library (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "flints.h"
+
+namespace flints {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr double PI = 3.141592653589793238462643383279502884;
+constexpr double NUGGET_EPS = 1.49e-8;  // sqrt of the double-precision epsilon (Sec. 2.4)
+constexpr int MAX_NUGGET_STEPS = 8;      // nugget doubled at most this many times
+
+// ---------------------------------------------------------------------------
+// Double-float numbers: value = hi + lo with |lo| <= ulp(hi)/2 after
+// normalisation, about 48 significant bits on the FP32 pipe.  The error-free
+// transforms are Knuth's TwoSum and the FMA form of Dekker's TwoProduct; the
+// __f*_rn intrinsics keep the compiler from contracting or reassociating them.
+// ---------------------------------------------------------------------------
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df df_from(double x) {
+    float h = __double2float_rn(x);
+    float l = __double2float_rn(x - (double)h);
+    return {h, l};
+}
+__device__ __forceinline__ double df_to(df a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ df quick_two_sum(float a, float b) {  // needs |a| >= |b|
+    float s = __fadd_rn(a, b);
+    float e = __fsub_rn(b, __fsub_rn(s, a));
+    return {s, e};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+    df s = two_sum(a.hi, b.hi);
+    df t = two_sum(a.lo, b.lo);
+    float e = __fadd_rn(s.lo, t.hi);
+    s = quick_two_sum(s.hi, e);
+    e = __fadd_rn(s.lo, t.lo);
+    return quick_two_sum(s.hi, e);
+}
+__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ df df_mul(df a, df b) {
+    float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return quick_two_sum(p, e);
+}
+__device__ __forceinline__ df df_mulf(df a, float b) {
+    float p = __fmul_rn(a.hi, b);
+    float e = __fmaf_rn(a.hi, b, -p);
+    e = __fmaf_rn(a.lo, b, e);
+    return quick_two_sum(p, e);
+}
+__device__ __forceinline__ df df_sqrt(df a) {
+    if (!(a.hi > 0.0f)) return {0.0f, 0.0f};
+    float s = __fsqrt_rn(a.hi);
+    float p = __fmul_rn(s, s);
+    float pe = __fmaf_rn(s, s, -p);
+    float r = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), pe), a.lo);
+    float c = __fdiv_rn(r, __fmul_rn(2.0f, s));
+    return quick_two_sum(s, c);
+}
+__device__ __forceinline__ df df_rcp(df a) {
+    float y = __frcp_rn(a.hi);
+    // e = 1 - a*y in double-float, then y + y*e
+    df ay = df_mulf(a, y);
+    df e = df_sub({1.0f, 0.0f}, ay);
+    float corr = __fmul_rn(y, e.hi);
+    return quick_two_sum(y, corr);
+}
+
+// Dot-product accumulator: acc -= x*y with the product's rounding error kept;
+// the low word is left unnormalised until the end (its error is relative to
+// the operands, which are O(1) in the kernels).
+struct dfacc {
+    float hi, lo;
+};
+__device__ __forceinline__ void dfacc_sub_prod(dfacc &a, df x, df y) {
+    float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    df s = two_sum(a.hi, -p);
+    a.hi = s.hi;
+    a.lo = __fsub_rn(a.lo, __fsub_rn(e, s.lo));
+}
+__device__ __forceinline__ void dfacc_add_prod(dfacc &a, df x, df y) {
+    float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    df s = two_sum(a.hi, p);
+    a.hi = s.hi;
+    a.lo = __fadd_rn(a.lo, __fadd_rn(e, s.lo));
+}
+__device__ __forceinline__ df dfacc_val(dfacc a) { return two_sum(a.hi, a.lo); }
+
+// ---------------------------------------------------------------------------
+// Precision policy: the same kernel source is instantiated for FP64 and for
+// double-float.
+// ---------------------------------------------------------------------------
+template <class R>
+struct Ops;
+
+template <>
+struct Ops<double> {
+    using T = double;
+    struct Acc {
+        double v;
+    };
+    static __device__ __forceinline__ T from(double x) { return x; }
+    static __device__ __forceinline__ double to(T x) { return x; }
+    static __device__ __forceinline__ T zero() { return 0.0; }
+    static __device__ __forceinline__ T add(T a, T b) { return a + b; }
+    static __device__ __forceinline__ T sub(T a, T b) { return a - b; }
+    static __device__ __forceinline__ T mul(T a, T b) { return a * b; }
+    static __device__ __forceinline__ T neg(T a) { return -a; }
+    static __device__ __forceinline__ T sqrt_(T a) { return sqrt(a); }
+    static __device__ __forceinline__ T rcp(T a) { return 1.0 / a; }
+    static __device__ __forceinline__ bool positive(T a) { return a > 0.0; }
+    static __device__ __forceinline__ Acc acc(T x) { return {x}; }
+    static __device__ __forceinline__ void sub_prod(Acc &a, T x, T y) { a.v = fma(-x, y, a.v); }
+    static __device__ __forceinline__ void add_prod(Acc &a, T x, T y) { a.v = fma(x, y, a.v); }
+    static __device__ __forceinline__ T val(Acc a) { return a.v; }
+    static __device__ __forceinline__ T shfl(T v, int src) { return __shfl_sync(FULL, v, src); }
+};
+
+template <>
+struct Ops<df> {
+    using T = df;
+    using Acc = dfacc;
+    static __device__ __forceinline__ T from(double x) { return df_from(x); }
+    static __device__ __forceinline__ double to(T x) { return df_to(x); }
+    static __device__ __forceinline__ T zero() { return {0.0f, 0.0f}; }
+    static __device__ __forceinline__ T add(T a, T b) { return df_add(a, b); }
+    static __device__ __forceinline__ T sub(T a, T b) { return df_sub(a, b); }
+    static __device__ __forceinline__ T mul(T a, T b) { return df_mul(a, b); }
+    static __device__ __forceinline__ T neg(T a) { return df_neg(a); }
+    static __device__ __forceinline__ T sqrt_(T a) { return df_sqrt(a); }
+    static __device__ __forceinline__ T rcp(T a) { return df_rcp(a); }
+    static __device__ __forceinline__ bool positive(T a) { return a.hi > 0.0f; }
+    static __device__ __forceinline__ Acc acc(T x) { return {x.hi, x.lo}; }
+    static __device__ __forceinline__ void sub_prod(Acc &a, T x, T y) { dfacc_sub_prod(a, x, y); }
+    static __device__ __forceinline__ void add_prod(Acc &a, T x, T y) { dfacc_add_prod(a, x, y); }
+    static __device__ __forceinline__ T val(Acc a) { return dfacc_val(a); }
+    static __device__ __forceinline__ T shfl(T v, int src) {
+        return {__shfl_sync(FULL, v.hi, src), __shfl_sync(FULL, v.lo, src)};
+    }
+};
+
+// ---------------------------------------------------------------------------
+// HEALPix RING geometry (integer-exact numerators, one rounding each).
+// ---------------------------------------------------------------------------
+struct Ring {
+    double z, s;
+    int64_t first;
+    int n_in, nq;
+    double f;  // phase offset: phi_j = (j + f) pi / (2 nq)
+};
+
+__device__ __forceinline__ Ring ring_of(int64_t N, int64_t i) {
+    Ring r;
+    const double Nd = (double)N;
+    if (i < N) {
+        const double id = (double)i, t3 = 3.0 * Nd * Nd;
+        r.z = (t3 - id * id) / t3;
+        r.s = id * sqrt(6.0 * Nd * Nd - id * id) / t3;
+        r.first = 2 * i * (i - 1);
+        r.nq = (int)i;
+        r.f = 0.5;
+    } else if (i <= 3 * N) {
+        const double id = (double)i;
+        r.z = (4.0 * Nd - 2.0 * id) / (3.0 * Nd);
+        r.s = sqrt((2.0 * id - Nd) * (7.0 * Nd - 2.0 * id)) / (3.0 * Nd);
+        r.first = 2 * N * (N - 1) + 4 * N * (i - N);
+        r.nq = (int)N;
+        r.f = ((i + N) & 1) ? 0.0 : 0.5;
+    } else {
+        const int64_t ip = 4 * N - i;
+        const double id = (double)ip, t3 = 3.0 * Nd * Nd;
+        r.z = -((t3 - id * id) / t3);
+        r.s = id * sqrt(6.0 * Nd * Nd - id * id) / t3;
+        r.first = 12 * N * N - 2 * ip * (ip + 1);
+        r.nq = (int)ip;
+        r.f = 0.5;
+    }
+    r.n_in = 4 * r.nq;
+    return r;
+}
+
+__device__ __forceinline__ int64_t cap_ring_of(int64_t p) {  // largest i with 2i(i-1) <= p
+    int64_t i = (int64_t)(0.5 * (1.0 + sqrt(1.0 + 2.0 * (double)p)));
+    while (i > 1 && 2 * i * (i - 1) > p) --i;
+    while (2 * (i + 1) * i <= p) ++i;
+    return i;
+}
+
+__device__ __forceinline__ void pix_ring(int64_t N, int64_t p, int64_t &ring, int64_t &j) {
+    const int64_t ncap = 2 * N * (N - 1), npix = 12 * N * N;
+    if (p < ncap) {
+        ring = cap_ring_of(p);
+        j = p - 2 * ring * (ring - 1);
+    } else if (p < npix - ncap) {
+        const int64_t q = p - ncap;
+        ring = q / (4 * N) + N;
+        j = q - (ring - N) * 4 * N;
+    } else {
+        const int64_t i = cap_ring_of(npix - 1 - p);
+        ring = 4 * N - i;
+        j = p - (npix - 2 * i * (i + 1));
+    }
+}
+
+// last ring whose z is >= z (0 if none)
+__device__ __forceinline__ int64_t ring_above(int64_t N, double z) {
+    const double za = fabs(z);
+    int64_t i;
+    if (za <= 2.0 / 3.0) {
+        i = (int64_t)floor((double)N * (2.0 - 1.5 * z));
+    } else {
+        const int64_t in = (int64_t)floor((double)N * sqrt(fmax(3.0 * (1.0 - za), 0.0)));
+        i = (z > 0) ? in : 4 * N - 1 - in;
+    }
+    i = i < 0 ? 0 : (i > 4 * N - 1 ? 4 * N - 1 : i);
+    for (int it = 0; it < 3; ++it) {
+        if (i >= 1 && ring_of(N, i).z < z) --i;
+        if (i + 1 <= 4 * N - 1 && ring_of(N, i + 1).z >= z) ++i;
+    }
+    return i;
+}
+
+// ---------------------------------------------------------------------------
+// Launch description.
+// ---------------------------------------------------------------------------
+// Per-interval cubic coefficients in FP64: p(s) = f + s (m + s (c2 + s c3)).
+struct alignas(32) Coef64 {
+    double f, m, c2, c3;
+};
+
+struct TableDev {
+    const Coef64 *c64;  // per interval: f_k, h g_k, c2, c3 (Horner in s)
+    const float4 *c32;   // per interval, double-float: (f.hi, f.lo, m.hi, m.lo), (c2.hi, c2.lo, c3.hi, c3.lo)
+    double t_max, inv_h;
+    int n;
+};
+
+struct LensArgs {
+    int64_t nside;
+    int64_t first, count;
+    const double *map;
+    const double *defl;
+    double *out, *var;
+    uint8_t *status;
+    int64_t *stencil;  // non-NULL: write the stencil and skip the solve
+    TableDev tab;
+    double xi0;
+    double r2;  // squared search radius (chord^2)
+    unsigned long long *counters;  // points, nugget, fallback, window, failed
+};
+
+enum { CNT_POINTS = 0, CNT_NUGGET = 1, CNT_FALLBACK = 2, CNT_WINDOW = 3, CNT_FAILED = 4, CNT_N = 5 };
+
+// Host-side launchers (lens_spin0.cu, lens_spin2.cu, xi_table.cu).
+cudaError_t launch_lens(int spin, int K, int precision, const LensArgs &a, int R_rings, cudaStream_t st);
+cudaError_t launch_xi_table(int spin, int lmax, const double *cl_dev, const double *clbb_dev, double t_max,
+                            int n, double *f_out, double *g_out, double *fm_out, double *gm_out,
+                            cudaStream_t st);
+cudaError_t finish_table(double *f, double *g, int n, double h, double xi0, Coef64 *c64, float4 *c32,
+                         cudaStream_t st);
+int device_sm_count();
+
+}  // namespace flints

@@ -1,0 +1,726 @@
+// Fused lensing-remap kernel: one warp per target point (Secs. 2.1-2.5, 3.1).
+//
+// Per tile of 32 consecutive RING targets a warp first displaces all 32
+// directions (one per lane, FP64), then, point by point:
+//   1. stencil search: the rings whose circle comes within the search radius r
+//      of n' (one ring per lane), the pixel range of each ring that can lie
+//      inside the disc, candidates enumerated in increasing RING index;
+//   2. exact K-nearest selection: squared chords in FP64, a warp bitonic sort
+//      on (chord^2, RING index); the K-th chord must lie inside the disc;
+//   3. covariance assembly S_ij = xi(t_ij)/xi(0) (+ nugget on the diagonal)
+//      and c_i = xi(t_i)/xi(0), spin 2 with the parallel-transport phase
+//      exp(2i(a_ij - a_ji)); lower triangle spread over the lanes;
+//   4. left-looking Cholesky, lane l owning rows l and l+32; the nugget is
+//      doubled while a pivot is not positive (Sec. 2.4);
+//   5. forward solves z_c = L^-1 conj(c), z_y = L^-1 y; value = z_c^H z_y,
+//      variance = xi(0) (1 - |z_c|^2) (Eqs. best_temperature_field, gaussvar,
+//      major_eq, gaussvar_pol).
+// Precision R = double (FP64 path) or df (double-float on the FP32 pipe, the
+// mixed path: FP64 geometry and selection, double-float assembly, factor and
+// solves, FP64 fallback for points whose double-float factor fails).
+#pragma once
+#include <type_traits>
+
+#include "common.cuh"
+
+namespace flints {
+
+template <class T>
+struct Cx {
+    T re, im;
+};
+
+template <int K>
+struct Shape {
+    static constexpr int NSLOT = K > 32 ? 256 : 128;  // candidate slots
+    static constexpr int SPL = NSLOT / 32;            // slots per lane
+    static constexpr int RPL = (K + 31) / 32;         // matrix rows per lane
+    static constexpr int LD = K + 1;                  // padded row stride
+    static constexpr int NTRI = K * (K + 1) / 2;
+};
+
+struct PointA {
+    double x, y, z, s, cph, sph;
+    int64_t ic;
+    int flags;
+    int pad;
+};
+
+struct RingRec {
+    double z, s, f;
+    int64_t first;
+    int n_in, nq, j0, cnt, end, pad;
+};
+
+template <int K, int SPIN, class R>
+struct WarpSmem {
+    using Elem = typename std::conditional<SPIN == 0, typename Ops<R>::T, Cx<typename Ops<R>::T>>::type;
+    static constexpr int NSLOT = Shape<K>::NSLOT;
+    PointA pts[32];
+    double ox[K], oy[K], oz[K];  // neighbour offsets X_i - n'
+    double nz[K], ns[K], nc[K], nsn[K];  // neighbour z, sin(theta), cos(phi), sin(phi)
+    union U {
+        struct Cand {
+            RingRec rings[32];
+            double cx[NSLOT], cy[NSLOT], cz[NSLOT], cc[NSLOT], cs[NSLOT];
+            uint32_t cpix[NSLOT];
+        } cand;
+        Elem mat[K * Shape<K>::LD];
+    } u;
+};
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ bool key_less(unsigned long long ka, unsigned ia, unsigned long long kb, unsigned ib) {
+    return ka < kb || (ka == kb && ia < ib);
+}
+
+// Ascending bitonic sort of 32*SPL (key, id) pairs; element e = s*32 + lane.
+template <int SPL>
+__device__ __forceinline__ void bitonic_sort(unsigned long long (&key)[SPL], unsigned (&id)[SPL], int lane) {
+    constexpr int N = 32 * SPL;
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+            for (int s = 0; s < SPL; ++s) {
+                const int e = s * 32 + lane;
+                const bool up = (e & k) == 0;
+                if (j >= 32) {
+                    const int ps = s ^ (j >> 5);
+                    if (ps > s) {
+                        const bool sw = up ? key_less(key[ps], id[ps], key[s], id[s])
+                                           : key_less(key[s], id[s], key[ps], id[ps]);
+                        if (sw) {
+                            const unsigned long long tk = key[s];
+                            key[s] = key[ps];
+                            key[ps] = tk;
+                            const unsigned ti = id[s];
+                            id[s] = id[ps];
+                            id[ps] = ti;
+                        }
+                    }
+                } else {
+                    const unsigned long long pk = __shfl_xor_sync(FULL, key[s], j);
+                    const unsigned pi = __shfl_xor_sync(FULL, id[s], j);
+                    const bool lower = (lane & j) == 0;
+                    const bool keep_min = (lower == up);
+                    const bool partner_less = key_less(pk, pi, key[s], id[s]);
+                    if (keep_min ? partner_less : (!partner_less && (pk != key[s] || pi != id[s]))) {
+                        key[s] = pk;
+                        id[s] = pi;
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <class R>
+__device__ __forceinline__ typename Ops<R>::T table_eval(const TableDev &tab, typename Ops<R>::T t);
+
+template <>
+__device__ __forceinline__ double table_eval<double>(const TableDev &tab, double t) {
+    const double x = t * tab.inv_h;
+    int k = (int)x;
+    k = k > tab.n - 1 ? tab.n - 1 : (k < 0 ? 0 : k);
+    const double s = x - (double)k;
+    const double2 c01 = __ldg(reinterpret_cast<const double2 *>(tab.c64 + k));
+    const double2 c23 = __ldg(reinterpret_cast<const double2 *>(tab.c64 + k) + 1);
+    return fma(s, fma(s, fma(s, c23.y, c23.x), c01.y), c01.x);
+}
+
+template <>
+__device__ __forceinline__ df table_eval<df>(const TableDev &tab, df t) {
+    const df x = df_mul(t, df_from(tab.inv_h));
+    float kf = floorf(x.hi);
+    df s = two_sum(__fsub_rn(x.hi, kf), x.lo);
+    if (s.hi < 0.0f) {
+        kf -= 1.0f;
+        s = df_add(s, {1.0f, 0.0f});
+    }
+    int k = (int)kf;
+    if (k > tab.n - 1) {
+        s = df_add(s, {(float)(k - (tab.n - 1)), 0.0f});
+        k = tab.n - 1;
+    } else if (k < 0) {
+        s = df_add(s, {(float)k, 0.0f});
+        k = 0;
+    }
+    const float4 c0 = __ldg(&tab.c32[2 * k]);
+    const float4 c1 = __ldg(&tab.c32[2 * k + 1]);
+    df p = {c1.z, c1.w};
+    p = df_add(df_mul(p, s), df{c1.x, c1.y});
+    p = df_add(df_mul(p, s), df{c0.z, c0.w});
+    p = df_add(df_mul(p, s), df{c0.x, c0.y});
+    return p;
+}
+
+// exp(2i(a_ij - a_ji)) for the pair (i -> j) with d = X_j - X_i, from the
+// projections of d on the local bases at both ends.
+template <class R>
+__device__ __forceinline__ Cx<typename Ops<R>::T> pair_phase(typename Ops<R>::T dx, typename Ops<R>::T dy,
+                                                             typename Ops<R>::T dz, double zi, double si,
+                                                             double ci, double sni, double zj, double sj,
+                                                             double cj, double snj) {
+    using O = Ops<R>;
+    using T = typename O::T;
+    // at i: A1 = d.e_theta(i) = z_i (dx c_i + dy s_i) - s_i dz ; B1 = d.e_phi(i) = dy c_i - dx s_i
+    const T h1 = O::add(O::mul(dx, O::from(ci)), O::mul(dy, O::from(sni)));
+    const T A1 = O::sub(O::mul(O::from(zi), h1), O::mul(O::from(si), dz));
+    const T B1 = O::sub(O::mul(dy, O::from(ci)), O::mul(dx, O::from(sni)));
+    const T h2 = O::add(O::mul(dx, O::from(cj)), O::mul(dy, O::from(snj)));
+    const T A2 = O::sub(O::mul(O::from(zj), h2), O::mul(O::from(sj), dz));
+    const T B2 = O::sub(O::mul(dy, O::from(cj)), O::mul(dx, O::from(snj)));
+    const T A1s = O::mul(A1, A1), B1s = O::mul(B1, B1), A2s = O::mul(A2, A2), B2s = O::mul(B2, B2);
+    const T re1 = O::sub(A1s, B1s), im1 = O::mul(O::add(A1, A1), B1);
+    const T re2 = O::sub(A2s, B2s), im2 = O::neg(O::mul(O::add(A2, A2), B2));
+    const T nre = O::sub(O::mul(re1, re2), O::mul(im1, im2));
+    const T nim = O::add(O::mul(re1, im2), O::mul(im1, re2));
+    const T den = O::mul(O::add(A1s, B1s), O::add(A2s, B2s));
+    if (!O::positive(den)) return {O::from(1.0), O::zero()};  // coincident points: no rotation
+    const T inv = O::rcp(den);
+    return {O::mul(nre, inv), O::mul(nim, inv)};
+}
+
+// --------------------------------------------------- assemble, factor, solve
+// Returns false when a pivot of S + nugget I is not positive.
+template <int K, int SPIN, class R, class SM>
+__device__ bool solve_point(SM &sm, const PointA &P, int lane, double nugget, const TableDev &tab,
+                            const double (&keyd)[Shape<K>::RPL], const double (&yre)[Shape<K>::RPL],
+                            const double (&yim)[Shape<K>::RPL], double &val_re, double &val_im,
+                            double &var_rel) {
+    using O = Ops<R>;
+    using T = typename O::T;
+    constexpr int RPL = Shape<K>::RPL, LD = Shape<K>::LD, NTRI = Shape<K>::NTRI;
+    using Elem = typename SM::Elem;
+    Elem *mat = sm.u.mat;
+
+    // ---- assembly of the lower triangle
+    {
+        int i = 0, j = lane;  // q = lane -> (i, j) with q = i(i+1)/2 + j
+        while (j > i) {
+            j -= i + 1;
+            ++i;
+        }
+        for (int q = lane; q < NTRI; q += 32) {
+            Elem e;
+            if (i == j) {
+                if constexpr (SPIN == 0) {
+                    e = O::from(1.0 + nugget);
+                } else {
+                    e.re = O::from(1.0 + nugget);
+                    e.im = O::zero();
+                }
+            } else {
+                const T dx = O::sub(O::from(sm.ox[j]), O::from(sm.ox[i]));
+                const T dy = O::sub(O::from(sm.oy[j]), O::from(sm.oy[i]));
+                const T dz = O::sub(O::from(sm.oz[j]), O::from(sm.oz[i]));
+                const T t = O::add(O::add(O::mul(dx, dx), O::mul(dy, dy)), O::mul(dz, dz));
+                const T fv = table_eval<R>(tab, t);
+                if constexpr (SPIN == 0) {
+                    e = fv;
+                } else {
+                    const Cx<T> ph = pair_phase<R>(dx, dy, dz, sm.nz[i], sm.ns[i], sm.nc[i], sm.nsn[i], sm.nz[j],
+                                                   sm.ns[j], sm.nc[j], sm.nsn[j]);
+                    e.re = O::mul(fv, ph.re);
+                    e.im = O::mul(fv, ph.im);
+                }
+            }
+            mat[i * LD + j] = e;
+            // advance q by 32
+            j += 32;
+            while (j > i) {
+                j -= i + 1;
+                ++i;
+            }
+        }
+    }
+    // ---- right-hand sides: conj(c_i) and y_i for the owned rows
+    Elem bc[RPL], by[RPL];
+#pragma unroll
+    for (int r = 0; r < RPL; ++r) {
+        const int i = lane + 32 * r;
+        if (i < K) {
+            const T fv = table_eval<R>(tab, O::from(keyd[r]));
+            if constexpr (SPIN == 0) {
+                bc[r] = fv;
+                by[r] = O::from(yre[r]);
+            } else {
+                // target -> neighbour: d = X_i - n' (offset), phase at n' and at X_i
+                const Cx<T> ph = pair_phase<R>(O::from(sm.ox[i]), O::from(sm.oy[i]), O::from(sm.oz[i]), P.z, P.s,
+                                               P.cph, P.sph, sm.nz[i], sm.ns[i], sm.nc[i], sm.nsn[i]);
+                bc[r].re = O::mul(fv, ph.re);
+                bc[r].im = O::neg(O::mul(fv, ph.im));  // conj(c0_i)
+                by[r].re = O::from(yre[r]);
+                by[r].im = O::from(yim[r]);
+            }
+        }
+    }
+    __syncwarp();
+
+    // ---- left-looking Cholesky
+    T inv[RPL];
+#pragma unroll
+    for (int r = 0; r < RPL; ++r) inv[r] = O::zero();
+    bool ok = true;
+    for (int j = 0; j < K; ++j) {
+        Elem srow[RPL];
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+            const int i = lane + 32 * r;
+            if (i < K && i >= j) {
+                const Elem *Li = mat + i * LD;
+                const Elem *Lj = mat + j * LD;
+                if constexpr (SPIN == 0) {
+                    typename O::Acc acc = O::acc(Li[j]);
+                    for (int k = 0; k < j; ++k) O::sub_prod(acc, Li[k], Lj[k]);
+                    srow[r] = O::val(acc);
+                } else {
+                    typename O::Acc ar = O::acc(Li[j].re), ai = O::acc(Li[j].im);
+                    for (int k = 0; k < j; ++k) {
+                        const Elem a = Li[k], b = Lj[k];
+                        O::sub_prod(ar, a.re, b.re);
+                        O::sub_prod(ar, a.im, b.im);
+                        O::sub_prod(ai, a.im, b.re);
+                        O::add_prod(ai, a.re, b.im);
+                    }
+                    srow[r].re = O::val(ar);
+                    srow[r].im = O::val(ai);
+                }
+            }
+        }
+        // pivot from the owner of row j
+        const int owner = j & 31, rj = j >> 5;
+        T dmine;
+        if constexpr (SPIN == 0) {
+            dmine = (RPL > 1 && rj == 1) ? srow[RPL - 1] : srow[0];
+        } else {
+            dmine = (RPL > 1 && rj == 1) ? srow[RPL - 1].re : srow[0].re;
+        }
+        const T d = O::shfl(dmine, owner);
+        if (!O::positive(d)) {
+            ok = false;
+            break;
+        }
+        const T ljj = O::sqrt_(d);
+        const T il = O::rcp(ljj);
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+            const int i = lane + 32 * r;
+            if (i < K && i > j) {
+                Elem v;
+                if constexpr (SPIN == 0) {
+                    v = O::mul(srow[r], il);
+                } else {
+                    v.re = O::mul(srow[r].re, il);
+                    v.im = O::mul(srow[r].im, il);
+                }
+                mat[i * LD + j] = v;
+            } else if (i == j) {
+                Elem v;
+                if constexpr (SPIN == 0) {
+                    v = ljj;
+                } else {
+                    v.re = ljj;
+                    v.im = O::zero();
+                }
+                mat[i * LD + j] = v;
+                inv[r] = il;
+            }
+        }
+        __syncwarp();
+    }
+    if (!ok) return false;
+
+    // ---- forward solves, column oriented
+    for (int j = 0; j < K; ++j) {
+        const int owner = j & 31, rj = j >> 5;
+        Elem zc, zy;
+        if (lane == owner) {
+            const int r = (RPL > 1 && rj == 1) ? RPL - 1 : 0;
+            if constexpr (SPIN == 0) {
+                bc[r] = O::mul(bc[r], inv[r]);
+                by[r] = O::mul(by[r], inv[r]);
+            } else {
+                bc[r].re = O::mul(bc[r].re, inv[r]);
+                bc[r].im = O::mul(bc[r].im, inv[r]);
+                by[r].re = O::mul(by[r].re, inv[r]);
+                by[r].im = O::mul(by[r].im, inv[r]);
+            }
+        }
+        {
+            const int r = (RPL > 1 && rj == 1) ? RPL - 1 : 0;
+            if constexpr (SPIN == 0) {
+                zc = O::shfl(bc[r], owner);
+                zy = O::shfl(by[r], owner);
+            } else {
+                zc.re = O::shfl(bc[r].re, owner);
+                zc.im = O::shfl(bc[r].im, owner);
+                zy.re = O::shfl(by[r].re, owner);
+                zy.im = O::shfl(by[r].im, owner);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+            const int i = lane + 32 * r;
+            if (i < K && i > j) {
+                const Elem l = mat[i * LD + j];
+                if constexpr (SPIN == 0) {
+                    typename O::Acc a1 = O::acc(bc[r]), a2 = O::acc(by[r]);
+                    O::sub_prod(a1, l, zc);
+                    O::sub_prod(a2, l, zy);
+                    bc[r] = O::val(a1);
+                    by[r] = O::val(a2);
+                } else {
+                    typename O::Acc cr = O::acc(bc[r].re), ci = O::acc(bc[r].im);
+                    typename O::Acc yr = O::acc(by[r].re), yi = O::acc(by[r].im);
+                    O::sub_prod(cr, l.re, zc.re);
+                    O::add_prod(cr, l.im, zc.im);
+                    O::sub_prod(ci, l.re, zc.im);
+                    O::sub_prod(ci, l.im, zc.re);
+                    O::sub_prod(yr, l.re, zy.re);
+                    O::add_prod(yr, l.im, zy.im);
+                    O::sub_prod(yi, l.re, zy.im);
+                    O::sub_prod(yi, l.im, zy.re);
+                    bc[r].re = O::val(cr);
+                    bc[r].im = O::val(ci);
+                    by[r].re = O::val(yr);
+                    by[r].im = O::val(yi);
+                }
+            }
+        }
+    }
+    // ---- value = z_c^H z_y, variance = 1 - |z_c|^2 (FP64 sums)
+    double vr = 0.0, vi = 0.0, nc = 0.0;
+#pragma unroll
+    for (int r = 0; r < RPL; ++r) {
+        const int i = lane + 32 * r;
+        if (i < K) {
+            if constexpr (SPIN == 0) {
+                const double c = O::to(bc[r]), y = O::to(by[r]);
+                vr = fma(c, y, vr);
+                nc = fma(c, c, nc);
+            } else {
+                const double cr = O::to(bc[r].re), ci = O::to(bc[r].im);
+                const double yr = O::to(by[r].re), yi = O::to(by[r].im);
+                vr = fma(cr, yr, fma(ci, yi, vr));
+                vi = fma(cr, yi, fma(-ci, yr, vi));
+                nc = fma(cr, cr, fma(ci, ci, nc));
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        vr += __shfl_xor_sync(FULL, vr, o);
+        vi += __shfl_xor_sync(FULL, vi, o);
+        nc += __shfl_xor_sync(FULL, nc, o);
+    }
+    val_re = vr;
+    val_im = vi;
+    var_rel = 1.0 - nc;
+    return true;
+}
+
+// ------------------------------------------------------------------ kernel
+template <int K, int SPIN, int MIXED, int WPB>
+__global__ void __launch_bounds__(WPB * 32) lens_kernel(LensArgs a, int R_rings) {
+    using SMd = WarpSmem<K, SPIN, double>;
+    using SMf = WarpSmem<K, SPIN, df>;
+    constexpr int SPL = Shape<K>::SPL, RPL = Shape<K>::RPL, NSLOT = Shape<K>::NSLOT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr size_t WS = sizeof(SMd) > sizeof(SMf) ? sizeof(SMd) : sizeof(SMf);
+    unsigned char *wbase = smem_raw + (size_t)warp * ((WS + 15) / 16 * 16);
+    SMd &sm = *reinterpret_cast<SMd *>(wbase);
+
+    const int64_t N = a.nside;
+    const int64_t ntiles = (a.count + 31) / 32;
+    unsigned long long cnt_nug = 0, cnt_fb = 0, cnt_win = 0, cnt_fail = 0;
+
+    for (int64_t tile = (int64_t)blockIdx.x * WPB + warp; tile < ntiles; tile += (int64_t)gridDim.x * WPB) {
+        // ------------------------------------------------ phase A: displace
+        {
+            const int64_t p = tile * 32 + lane;
+            PointA P{};
+            if (p < a.count) {
+                const int64_t pix = a.first + p;
+                int64_t ring, jj;
+                pix_ring(N, pix, ring, jj);
+                const Ring rg = ring_of(N, ring);
+                double sp, cp;
+                sincospi(((double)jj + rg.f) / (2.0 * (double)rg.nq), &sp, &cp);
+                const double nx = rg.s * cp, ny = rg.s * sp, nz = rg.z;
+                const double2 dd = __ldg(reinterpret_cast<const double2 *>(a.defl) + p);
+                const double dl = sqrt(dd.x * dd.x + dd.y * dd.y);
+                double x = nx, y = ny, z = nz;
+                if (dl > 0.0) {
+                    double sd, cd;
+                    sincos(dl, &sd, &cd);
+                    const double k = sd / dl;
+                    // e_theta = (z cos phi, z sin phi, -s), e_phi = (-sin phi, cos phi, 0)
+                    const double tx = dd.x * nz * cp - dd.y * sp;
+                    const double ty = dd.x * nz * sp + dd.y * cp;
+                    const double tz = -dd.x * rg.s;
+                    x = cd * nx + k * tx;
+                    y = cd * ny + k * ty;
+                    z = cd * nz + k * tz;
+                }
+                const double s = sqrt(x * x + y * y);
+                P.x = x;
+                P.y = y;
+                P.z = z;
+                P.s = s;
+                if (s > 1e-12) {
+                    P.cph = x / s;
+                    P.sph = y / s;
+                } else {
+                    P.cph = 1.0;
+                    P.sph = 0.0;
+                    P.flags |= FLINTS_ST_POLE;
+                }
+                P.ic = ring_above(N, z);
+            }
+            sm.pts[lane] = P;
+        }
+        __syncwarp();
+
+        // ------------------------------------------------ phase B: per point
+        for (int q = 0; q < 32; ++q) {
+            const int64_t p = tile * 32 + q;
+            if (p >= a.count) break;
+            const PointA P = sm.pts[q];
+            int flags = P.flags;
+            // rings of the search disc, one per lane
+            int cnt = 0;
+            {
+                RingRec rec{};
+                const int64_t i = P.ic - R_rings + lane;
+                if (lane < 2 * R_rings + 2 && i >= 1 && i <= 4 * N - 1) {
+                    const Ring rg = ring_of(N, i);
+                    const double dz = P.z - rg.z, ds = P.s - rg.s;
+                    const double lb = dz * dz + ds * ds;
+                    if (lb <= a.r2) {
+                        const double den = 4.0 * P.s * rg.s;
+                        const double qv = den > 0.0 ? (a.r2 - lb) / den : 2.0;
+                        int j0 = 0, c = rg.n_in;
+                        if (qv < 1.0) {
+                            const double half = 2.0 * asin(sqrt(qv));
+                            const double phi = atan2(P.sph, P.cph);
+                            const double step = (double)rg.n_in / (2.0 * PI);  // pixels per radian
+                            const double lo = (phi - half) * step - rg.f;
+                            const double hi = (phi + half) * step - rg.f;
+                            const int64_t jl = (int64_t)floor(lo), jh = (int64_t)ceil(hi);
+                            const int64_t cc = jh - jl + 1;
+                            if (cc < rg.n_in) {
+                                c = (int)cc;
+                                int64_t m = jl % rg.n_in;
+                                if (m < 0) m += rg.n_in;
+                                j0 = (int)m;
+                            }
+                        }
+                        rec.z = rg.z;
+                        rec.s = rg.s;
+                        rec.f = rg.f;
+                        rec.first = rg.first;
+                        rec.n_in = rg.n_in;
+                        rec.nq = rg.nq;
+                        rec.j0 = j0;
+                        rec.cnt = c;
+                        cnt = c;
+                    }
+                }
+                // inclusive scan of counts
+                int incl = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(FULL, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                rec.end = incl;
+                sm.u.cand.rings[lane] = rec;
+                cnt = __shfl_sync(FULL, incl, 31);  // total candidates
+            }
+            const int C = cnt;
+            __syncwarp();
+            bool fail = false;
+            if (C > NSLOT || C < K) {
+                fail = true;
+                flags |= FLINTS_ST_WINDOW | FLINTS_ST_FAILED;
+            }
+            unsigned long long key[SPL];
+            unsigned id[SPL];
+            if (!fail) {
+#pragma unroll
+                for (int s = 0; s < SPL; ++s) {
+                    const int c = s * 32 + lane;
+                    key[s] = 0x7ff0000000000000ull;  // +inf
+                    id[s] = 0xffffffffu;
+                    if (c < C) {
+                        // ring holding candidate c: first r with end > c
+                        int lo = 0, hi = 31;
+                        while (lo < hi) {
+                            const int mid = (lo + hi) >> 1;
+                            if (sm.u.cand.rings[mid].end > c) hi = mid;
+                            else lo = mid + 1;
+                        }
+                        const RingRec &rr = sm.u.cand.rings[lo];
+                        const int k = c - (rr.end - rr.cnt);
+                        const int w = rr.j0 + rr.cnt - rr.n_in;  // wrapped count
+                        const int jj = (w > 0) ? (k < w ? k : rr.j0 + (k - w)) : rr.j0 + k;
+                        double sp, cp;
+                        sincospi(((double)jj + rr.f) / (2.0 * (double)rr.nq), &sp, &cp);
+                        const double cx = rr.s * cp, cy = rr.s * sp, cz = rr.z;
+                        const double ex = P.x - cx, ey = P.y - cy, ez = P.z - cz;
+                        const double kk = ex * ex + ey * ey + ez * ez;
+                        sm.u.cand.cx[c] = cx;
+                        sm.u.cand.cy[c] = cy;
+                        sm.u.cand.cz[c] = cz;
+                        sm.u.cand.cc[c] = cp;
+                        sm.u.cand.cs[c] = sp;
+                        sm.u.cand.cpix[c] = (uint32_t)(rr.first + jj);
+                        key[s] = (unsigned long long)__double_as_longlong(kk);
+                        id[s] = (unsigned)c;
+                    }
+                }
+                bitonic_sort<SPL>(key, id, lane);
+                // K-th neighbour inside the disc?
+                const unsigned long long kK = __shfl_sync(FULL, key[(K - 1) >> 5], (K - 1) & 31);
+                if (__longlong_as_double((long long)kK) > a.r2) {
+                    fail = true;
+                    flags |= FLINTS_ST_WINDOW | FLINTS_ST_FAILED;
+                }
+            }
+            __syncwarp();
+            double keyd[RPL], yre[RPL], yim[RPL];
+            uint32_t pixr[RPL];
+            if (!fail) {
+#pragma unroll
+                for (int r = 0; r < RPL; ++r) {
+                    const int i = lane + 32 * r;
+                    keyd[r] = 0.0;
+                    yre[r] = 0.0;
+                    yim[r] = 0.0;
+                    pixr[r] = 0;
+                    if (i < K) {
+                        const unsigned c = id[r];
+                        keyd[r] = __longlong_as_double((long long)key[r]);
+                        const double cx = sm.u.cand.cx[c], cy = sm.u.cand.cy[c], cz = sm.u.cand.cz[c];
+                        sm.ox[i] = cx - P.x;
+                        sm.oy[i] = cy - P.y;
+                        sm.oz[i] = cz - P.z;
+                        sm.nz[i] = cz;
+                        sm.ns[i] = sqrt(cx * cx + cy * cy);
+                        sm.nc[i] = sm.u.cand.cc[c];
+                        sm.nsn[i] = sm.u.cand.cs[c];
+                        pixr[r] = sm.u.cand.cpix[c];
+                    }
+                }
+            }
+            __syncwarp();
+            if (a.stencil) {
+                if (!fail) {
+#pragma unroll
+                    for (int r = 0; r < RPL; ++r) {
+                        const int i = lane + 32 * r;
+                        if (i < K) a.stencil[p * K + i] = (int64_t)pixr[r];
+                    }
+                } else {
+                    for (int i = lane; i < K; i += 32) a.stencil[p * K + i] = -1;
+                }
+                if (lane == 0) {
+                    if (a.status) a.status[p] = (uint8_t)flags;
+                    if (flags & FLINTS_ST_WINDOW) ++cnt_win;
+                    if (flags & FLINTS_ST_FAILED) ++cnt_fail;
+                }
+                continue;
+            }
+            double vre = __longlong_as_double(0x7ff8000000000000ll), vim = vre, vrel = vre;
+            if (!fail) {
+#pragma unroll
+                for (int r = 0; r < RPL; ++r) {
+                    const int i = lane + 32 * r;
+                    if (i < K) {
+                        if (SPIN == 0) {
+                            yre[r] = __ldg(a.map + pixr[r]);
+                        } else {
+                            const double2 v = __ldg(reinterpret_cast<const double2 *>(a.map) + pixr[r]);
+                            yre[r] = v.x;
+                            yim[r] = v.y;
+                        }
+                    }
+                }
+                bool solved = false;
+                if (MIXED) {
+                    SMf &smf = *reinterpret_cast<SMf *>(wbase);
+                    solved = solve_point<K, SPIN, df>(smf, P, lane, NUGGET_EPS, a.tab, keyd, yre, yim, vre, vim,
+                                                      vrel);
+                    if (!solved) flags |= FLINTS_ST_FALLBACK;
+                    __syncwarp();
+                }
+                double nug = NUGGET_EPS;
+                for (int step = 0; !solved && step <= MAX_NUGGET_STEPS; ++step) {
+                    if (step > 0) {
+                        nug *= 2.0;
+                        flags |= FLINTS_ST_NUGGET;
+                    }
+                    solved = solve_point<K, SPIN, double>(sm, P, lane, nug, a.tab, keyd, yre, yim, vre, vim, vrel);
+                    __syncwarp();
+                }
+                if (!solved) {
+                    flags |= FLINTS_ST_FAILED;
+                    vre = vim = vrel = __longlong_as_double(0x7ff8000000000000ll);
+                }
+            }
+            if (lane == 0) {
+                if (SPIN == 0) {
+                    a.out[p] = vre;
+                } else {
+                    reinterpret_cast<double2 *>(a.out)[p] = make_double2(vre, vim);
+                }
+                if (a.var) a.var[p] = a.xi0 * vrel;
+                if (a.status) a.status[p] = (uint8_t)flags;
+                if (flags & FLINTS_ST_NUGGET) ++cnt_nug;
+                if (flags & FLINTS_ST_FALLBACK) ++cnt_fb;
+                if (flags & FLINTS_ST_WINDOW) ++cnt_win;
+                if (flags & FLINTS_ST_FAILED) ++cnt_fail;
+            }
+            __syncwarp();
+        }
+    }
+    if (lane == 0 && a.counters) {
+        if (cnt_nug) atomicAdd(a.counters + CNT_NUGGET, cnt_nug);
+        if (cnt_fb) atomicAdd(a.counters + CNT_FALLBACK, cnt_fb);
+        if (cnt_win) atomicAdd(a.counters + CNT_WINDOW, cnt_win);
+        if (cnt_fail) atomicAdd(a.counters + CNT_FAILED, cnt_fail);
+    }
+}
+
+template <int K, int SPIN, int MIXED>
+constexpr size_t warp_smem_bytes() {
+    using SMd = WarpSmem<K, SPIN, double>;
+    using SMf = WarpSmem<K, SPIN, df>;
+    constexpr size_t WS = sizeof(SMd) > sizeof(SMf) ? sizeof(SMd) : sizeof(SMf);
+    return (WS + 15) / 16 * 16;
+}
+
+template <int K, int SPIN, int MIXED, int WPB>
+cudaError_t launch_one(const LensArgs &a, int R_rings, int num_sms, cudaStream_t st) {
+    const size_t smem = (size_t)WPB * warp_smem_bytes<K, SPIN, MIXED>();
+    auto kern = lens_kernel<K, SPIN, MIXED, WPB>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WPB * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const int64_t ntiles = (a.count + 31) / 32;
+    int64_t blocks = (int64_t)num_sms * per_sm;
+    const int64_t need = (ntiles + WPB - 1) / WPB;
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    kern<<<(unsigned)blocks, WPB * 32, smem, st>>>(a, R_rings);
+    return cudaGetLastError();
+}
+
+}  // namespace flints

@@ -1,0 +1,23 @@
+// Instantiations of the fused lens kernel for spin-2 fields.
+#include "lens.cuh"
+
+namespace flints {
+
+cudaError_t launch_lens_spin2(int K, int precision, const LensArgs &a, int R_rings, cudaStream_t st) {
+    const int sms = device_sm_count();
+    const bool mixed = precision == FLINTS_MIXED;
+    switch (K) {
+        case 16:
+            return mixed ? launch_one<16, 2, 1, 4>(a, R_rings, sms, st) : launch_one<16, 2, 0, 4>(a, R_rings, sms, st);
+        case 24:
+            return mixed ? launch_one<24, 2, 1, 4>(a, R_rings, sms, st) : launch_one<24, 2, 0, 4>(a, R_rings, sms, st);
+        case 32:
+            return mixed ? launch_one<32, 2, 1, 4>(a, R_rings, sms, st) : launch_one<32, 2, 0, 4>(a, R_rings, sms, st);
+        case 48:
+            return mixed ? launch_one<48, 2, 1, 4>(a, R_rings, sms, st) : launch_one<48, 2, 0, 4>(a, R_rings, sms, st);
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace flints

@@ -1,0 +1,192 @@
+"""GPU parity on whole small skies: xi tables, stencils (bit-exact indices) and
+lensed values/variances of the CUDA path against the FP64 oracle.
+
+Tolerances (parity metric = max |gpu - oracle| / sigma_map for values and
+max |gpu - oracle| / xi(0) for variances): FP64 path 1e-9, mixed path 1e-6.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import healpix as hp
+from oracle import kriging as kr
+from oracle import sht
+from oracle import xi
+from tests.gpu_common import oracle_table, parity_metric, realistic_inputs, require_gpu, to_host
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-9, "mixed": 1e-6}
+
+
+@pytest.fixture(scope="module")
+def fl():
+    return require_gpu()
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+
+    return t
+
+
+# ---------------------------------------------------------------- xi tables
+@pytest.mark.parametrize("spin,nside,lmax,ld,K", [(0, 64, 128, 100.0, 16), (0, 2048, 4096, 2500.0, 32),
+                                                    (2, 4096, 4096, 2500.0, 32), (2, 256, 512, 312.0, 48)])
+def test_xi_table_matches_oracle(fl, spin, nside, lmax, ld, K):
+    cl = wl.cl_tt(lmax, ld) if spin == 0 else wl.cl_ee(lmax, ld)
+    bb = None if spin == 0 else 0.1 * cl
+    plan = fl.Plan(nside, cl, bb, spin=spin, K=K)
+    info = plan.info()
+    weight = np.abs(cl) if spin == 0 else np.abs(cl) + np.abs(bb)
+    t_max, n = xi.grid_rule(weight, K, nside)
+    assert info.t_max == t_max and info.n_intervals == n
+    nodes = np.arange(n + 1) * (t_max / n)
+    f, g = plan.table(0)
+    if spin == 0:
+        ref, dref = xi.xi0_direct(cl, nodes, deriv=True)
+    else:
+        xp, xm, dxp, dxm = xi.xi2_direct(cl, bb, nodes, deriv=True)
+        ref, dref = xp, dxp
+        fm, gm = plan.table(1)
+        np.testing.assert_allclose(fm, xm / xp[0], atol=1e-13)
+        np.testing.assert_allclose(gm * t_max, dxm / xp[0] * t_max, atol=1e-11)
+    assert abs(info.xi0 - ref[0]) <= 1e-13 * ref[0]
+    np.testing.assert_allclose(f, ref / ref[0], atol=1e-13)
+    # slopes compared in units of the table domain
+    np.testing.assert_allclose(g * t_max, dref / ref[0] * t_max, atol=1e-11)
+
+
+# ------------------------------------------------------------------ stencil
+def _near_tie(nside, targets, K):
+    idx, key = kr.knn(nside, targets, K + 1)
+    gap = (key[:, K] - key[:, K - 1]) / np.maximum(key[:, K], 1e-300)
+    return idx[:, :K], gap < 1e-11
+
+
+@pytest.mark.parametrize("nside,K", [(64, 16), (64, 48), (16, 24), (128, 32)])
+def test_stencil_bit_exact(fl, torch, nside, K):
+    npix = hp.npix(nside)
+    cl = wl.cl_tt(2 * nside, 1.2 * nside)
+    plan = fl.Plan(nside, cl, spin=0, K=K)
+    defl = wl.random_deflection(npix, 31 + K) * 2.0 * (64 / nside)
+    idx, st = plan.stencil(torch.from_numpy(defl).cuda())
+    idx, st = to_host(idx), to_host(st)
+    assert np.all(st == 0)
+    tv = kr.displace(nside, np.arange(npix), defl)
+    ref, tie = _near_tie(nside, tv, K)
+    same = np.all(idx == ref, axis=1)
+    assert np.all(same | tie), f"{np.sum(~same & ~tie)} stencils differ"
+    # where the K-th and (K+1)-th neighbours tie, the GPU set must still be a valid K-nearest set
+    for p in np.nonzero(~same)[0]:
+        keys = np.sum((hp.pix2vec(nside, idx[p]) - tv[p]) ** 2, axis=1)
+        refk = np.sum((hp.pix2vec(nside, ref[p]) - tv[p]) ** 2, axis=1)
+        assert abs(keys.max() - refk.max()) <= 1e-12 * refk.max()
+
+
+def test_stencil_at_pixel_centres_is_the_pixel(fl, torch):
+    nside, K = 32, 16
+    plan = fl.Plan(nside, wl.cl_tt(64, 40.0), spin=0, K=K)
+    npix = hp.npix(nside)
+    idx, st = plan.stencil(torch.zeros((npix, 2), dtype=torch.float64, device="cuda"))
+    idx = to_host(idx)
+    assert np.array_equal(idx[:, 0], np.arange(npix))
+
+
+# ------------------------------------------------------------- lensed maps
+@pytest.fixture(scope="module")
+def c1_inputs():
+    W = wl.C1
+    cl, _ = W.cl()
+    alm, m, defl = realistic_inputs(W.nside, W.lmax, 0, cl, W.seed_map, W.seed_phi)
+    tab, x0, _, _ = oracle_table(cl, None, 0, W.K, W.nside)
+    ref = kr.lens(W.nside, W.K, 0, m, defl, np.arange(W.npix), tab, x0)
+    return W, cl, alm, m, defl, ref
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_c1_full_sky_parity(fl, torch, c1_inputs, precision):
+    W, cl, alm, m, defl, ref = c1_inputs
+    plan = fl.Plan(W.nside, cl, spin=0, K=W.K, precision=precision)
+    md, dd = torch.from_numpy(m).cuda(), torch.from_numpy(defl).cuda()
+    out = torch.empty(W.npix, dtype=torch.float64, device="cuda")
+    var = torch.empty_like(out)
+    plan.lens_full(md, dd, out, var)
+    torch.cuda.synchronize()
+    v, s2 = to_host(out), to_host(var)
+    sigma = float(np.std(m))
+    assert parity_metric(v, ref.value, sigma) <= TOL[precision]
+    assert parity_metric(s2, ref.variance, ref.variance.max() * 0 + plan.info().xi0) <= TOL[precision]
+    st = plan.stats()
+    assert st["failed"] == 0 and st["window"] == 0
+    if precision == "fp64":
+        assert st["fallback"] == 0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_c1_ragged_ranges(fl, torch, c1_inputs, precision):
+    W, cl, alm, m, defl, ref = c1_inputs
+    plan = fl.Plan(W.nside, cl, spin=0, K=W.K, precision=precision)
+    md = torch.from_numpy(m).cuda()
+    for first, count in [(0, 1), (777, 45), (W.npix - 33, 33), (12345, 0), (100, 1000)]:
+        dd = torch.from_numpy(np.ascontiguousarray(defl[first:first + count])).cuda()
+        status = torch.empty(count, dtype=torch.uint8, device="cuda")
+        var = torch.empty(count, dtype=torch.float64, device="cuda")
+        out, var, status = plan.lens(md, dd, var=var, status=status, first=first, count=count)
+        torch.cuda.synchronize()
+        if count == 0:
+            continue
+        sigma = float(np.std(m))
+        assert parity_metric(to_host(out), ref.value[first:first + count], sigma) <= TOL[precision]
+        assert np.all(to_host(status) & fl.ST_FAILED == 0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("K", [16, 24, 32, 48])
+def test_spin2_sky_parity(fl, torch, precision, K):
+    nside, lmax = 32, 64
+    cl = wl.cl_ee(lmax, 50.0)
+    bb = 0.2 * cl
+    alm = wl.draw_alm(cl, 41)
+    blm = wl.draw_alm(bb, 42)
+    P = sht.synth_map(nside, lmax, alm, spin=2, blm=blm)
+    m = np.ascontiguousarray(np.stack([P.real, P.imag], axis=1))
+    defl = wl.random_deflection(hp.npix(nside), 43) * 8
+    tab, x0, _, _ = oracle_table(cl, bb, 2, K, nside)
+    ref = kr.lens(nside, K, 2, m, defl, np.arange(hp.npix(nside)), tab, x0)
+    plan = fl.Plan(nside, cl, bb, spin=2, K=K, precision=precision)
+    out = torch.empty((hp.npix(nside), 2), dtype=torch.float64, device="cuda")
+    var = torch.empty(hp.npix(nside), dtype=torch.float64, device="cuda")
+    plan.lens_full(torch.from_numpy(m).cuda(), torch.from_numpy(defl).cuda(), out, var)
+    torch.cuda.synchronize()
+    v = to_host(out)
+    sigma = float(np.sqrt(np.mean(P.real ** 2 + P.imag ** 2)))
+    assert parity_metric(v[:, 0] + 1j * v[:, 1], ref.value, sigma) <= TOL[precision]
+    assert parity_metric(to_host(var), ref.variance, x0) <= TOL[precision]
+
+
+@pytest.mark.parametrize("K", [16, 24, 48])
+def test_spin0_all_stencil_sizes(fl, torch, K):
+    nside, lmax = 32, 64
+    cl = wl.cl_tt(lmax, 50.0)
+    alm = wl.draw_alm(cl, 51)
+    m = sht.synth_map(nside, lmax, alm)
+    defl = wl.random_deflection(hp.npix(nside), 52) * 8
+    tab, x0, _, _ = oracle_table(cl, None, 0, K, nside)
+    ref = kr.lens(nside, K, 0, m, defl, np.arange(hp.npix(nside)), tab, x0)
+    for precision in ("fp64", "mixed"):
+        plan = fl.Plan(nside, cl, spin=0, K=K, precision=precision)
+        out = torch.empty(hp.npix(nside), dtype=torch.float64, device="cuda")
+        plan.lens_full(torch.from_numpy(m).cuda(), torch.from_numpy(defl).cuda(), out)
+        torch.cuda.synchronize()
+        assert parity_metric(to_host(out), ref.value, float(np.std(m))) <= TOL[precision]
+
+
+def test_wrong_spin_entry_point_is_an_error(fl, torch):
+    plan = fl.Plan(16, wl.cl_tt(32, 20.0), spin=0, K=16)
+    z = torch.zeros((hp.npix(16), 2), dtype=torch.float64, device="cuda")
+    with pytest.raises(fl.FlintsError):
+        fl.api._check(fl.api._lib.flints_lens_spin2(plan._h, z.data_ptr(), z.data_ptr(), z.data_ptr(), None, None))
