@@ -1,0 +1,352 @@
+"""Benchmark of the lensing remap on the Nside 4096, spin-2, K=32 workload.
+
+One step lenses one batch of 2^24 consecutive RING targets (a twelfth of the
+sky) of an Nside 4096 Q/U map resident in HBM; successive steps walk around
+the sky.  ``value`` is the mixed-precision path's throughput (points/s, whole
+job over all ranks); the FP64 path is timed on the same batches for the
+mixed-vs-FP64 ratio.  Inputs are larger than L2 (3.2 GB map, 268 MB of
+deflections per step), so no L2 flush is needed.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) every rank lenses its own batches (weak scaling, no
+collective on the data path); timings are bracketed by barriers and the
+maximum over ranks is reported by rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as wl  # noqa: E402
+
+METRIC = "lensed pts/s at Nside 4096 spin-2 K=32, mixed vs FP64 @2e-4 rel err; p50/p99 ms"
+BATCH = 1 << 24
+W = wl.C3
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=6)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--profile-case", choices=["mixed", "fp64"], default=None,
+                    help="small case for ncu: two launches on 2^18 targets of the resident c3 map")
+    return ap.parse_args()
+
+
+def run_profile_case(precision: str):
+    """Two launches of the c3 lens kernel on 2^18 targets (the second one is the one to capture)."""
+    import torch
+
+    import paper_1003_4984_gb300 as fl
+
+    fl.load_library()
+    cl, bb = W.cl()
+    dev = torch.device("cuda", 0)
+    g = torch.Generator(device=dev)
+    g.manual_seed(7)
+    n = 1 << 18
+    qu = torch.randn((W.npix, 2), dtype=torch.float64, device=dev, generator=g)
+    defl = torch.randn((n, 2), dtype=torch.float64, device=dev, generator=g) * (wl.DEFLECTION_RMS / math.sqrt(2))
+    out = torch.empty((n, 2), dtype=torch.float64, device=dev)
+    var = torch.empty(n, dtype=torch.float64, device=dev)
+    plan = fl.Plan(W.nside, cl, bb, spin=2, K=W.K, precision=precision)
+    for _ in range(2):
+        plan.lens(qu, defl, out, var, first=100_000_000, count=n)
+    torch.cuda.synchronize()
+    st = plan.stats()
+    assert st["failed"] == 0, st
+    print(json.dumps({"profile_case": precision, "points": n, "stats": st}))
+
+
+def config(n_gpus):
+    return {"workload": "c3: spin-2 Q/U, Nside 4096 (201,326,592 px), lmax 4096, C_l^EE = 0.05 x C_l^TT shape "
+                        "(damping l = 2500), B = 0, K = 32",
+            "batch_points": BATCH, "npix": W.npix, "nside": W.nside, "lmax": W.lmax, "K": W.K, "spin": 2,
+            "l2": "inputs larger than L2 (3.2 GB resident map, 268 MB deflections per step)",
+            "parallelism": f"weak, {n_gpus} rank(s), distinct target batches per rank"}
+
+
+# ------------------------------------------------------------ CPU oracle leg
+def _oracle_worker(args):
+    first, count, seed = args
+    sys.path.insert(0, ROOT)
+    from oracle import kriging as kr
+    from oracle import xi
+
+    cl, bb = W.cl()
+    t_max, n = xi.grid_rule(np.abs(cl) + np.abs(bb), W.K, W.nside)
+    if (t_max, n) not in _TABLE_CACHE:
+        _TABLE_CACHE[(t_max, n)] = xi.spin2_tables(cl, bb, t_max, n)
+    tp, _, x0 = _TABLE_CACHE[(t_max, n)]
+    pix = np.arange(first, first + count)
+    defl = wl.random_deflection(count, seed + first)
+    qu = wl.HashedMap(W.npix, 6, 2)
+    t0 = time.time()
+    kr.lens(W.nside, W.K, 2, qu, defl, pix, tp, x0)
+    return count, time.time() - t0
+
+
+_TABLE_CACHE: dict = {}
+
+
+def cpu_oracle(seconds: float):
+    """Time the oracle (as it stands) on a bounded sample of the workload on all host cores."""
+    import multiprocessing as mp
+
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    per = 256
+    # calibrate on one chunk, then size the sample to about `seconds` of wall time
+    with ctx.Pool(cores) as pool:
+        n0, t0 = pool.map(_oracle_worker, [(50_000_000, per, 11)])[0]
+        rate1 = n0 / max(t0, 1e-9)
+        chunks = max(cores, int(seconds * rate1 * cores / per))
+        starts = [(50_000_000 + 7919 * per * k) % (W.npix - per) for k in range(chunks)]
+        t = time.time()
+        res = pool.map(_oracle_worker, [(s, per, 11) for s in starts])
+        wall = time.time() - t
+    pts = sum(r[0] for r in res)
+    return {"value": pts / wall, "unit": "pts/s", "cores": cores, "kind": "oracle",
+            "sample": f"{pts} targets of the c3 workload in {chunks} chunks of {per} consecutive RING pixels "
+                      f"(hashed-normal Q/U values, per-pixel deflections), {wall:.1f} s wall on {cores} spawned "
+                      f"processes"}
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    def __init__(self, path):
+        self.path = path
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+            self.f.close()
+
+    def summary(self, gpu_index: int):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9 or not p[0].isdigit() or int(p[0]) != gpu_index:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+
+    import paper_1003_4984_gb300 as fl
+    from paper_1003_4984_gb300 import flops
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    # the CPU baseline runs first, before any GPU work (spawned pool)
+    cpu = cpu_oracle(args.cpu_seconds) if (rank == 0 and world == 1) else None
+
+    dev = torch.device("cuda", local)
+    fl.load_library()
+    cl, bb = W.cl()
+    stream = torch.cuda.current_stream(dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(1234 + rank)
+    qu = torch.randn((W.npix, 2), dtype=torch.float64, device=dev, generator=g)
+    nb = W.npix // BATCH  # 12 batches per sky
+    defl = torch.randn((nb * BATCH, 2), dtype=torch.float64, device=dev, generator=g) * (wl.DEFLECTION_RMS / math.sqrt(2))
+    out = torch.empty((BATCH, 2), dtype=torch.float64, device=dev)
+    var = torch.empty(BATCH, dtype=torch.float64, device=dev)
+    plans = {p: fl.Plan(W.nside, cl, bb, spin=2, K=W.K, precision=p) for p in ("mixed", "fp64")}
+
+    def step(plan, i):
+        b = (rank * 5 + i) % nb
+        plan.lens(qu, defl[b * BATCH:(b + 1) * BATCH], out, var, first=b * BATCH, count=BATCH)
+
+    def timed(plan, steps, warmup):
+        for i in range(warmup):
+            step(plan, i)
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        ev[0].record(stream)
+        for i in range(steps):
+            step(plan, warmup + i)
+            ev[i + 1].record(stream)
+        torch.cuda.synchronize(dev)
+        per = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+        total = ev[0].elapsed_time(ev[steps])
+        if dist:
+            t = torch.tensor([total], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total = float(t.item())
+        return total, per
+
+    plans["mixed"].reset_stats()
+    with Clocks(os.path.join(ROOT, "gpurun_out", f"bench_clocks_r{rank}.csv") if os.path.isdir(
+            os.path.join(ROOT, "gpurun_out")) else f"/tmp/bench_clocks_r{rank}.csv") as clk:
+        total_ms, per = timed(plans["mixed"], args.steps, args.warmup)
+    clocks = clk.summary(local)
+    st = plans["mixed"].stats()
+    fp_total, fp_per = timed(plans["fp64"], max(1, args.fp64_steps), 1)
+
+    # end to end through the public API with pinned host buffers
+    nb_e2e = min(args.steps, 3)
+    h_map = torch.empty((W.npix, 2), dtype=torch.float64, pin_memory=True)
+    h_defl = torch.empty((BATCH, 2), dtype=torch.float64, pin_memory=True)
+    h_out = torch.empty((BATCH, 2), dtype=torch.float64, pin_memory=True)
+    h_var = torch.empty(BATCH, dtype=torch.float64, pin_memory=True)
+    h_defl.copy_(defl[:BATCH])
+    h_map.copy_(qu)
+    slice_len = (W.npix + nb - 1) // nb
+
+    def e2e_step(i):
+        b = (rank * 5 + i) % nb
+        s0 = b * slice_len
+        s1 = min(W.npix, s0 + slice_len)
+        qu[s0:s1].copy_(h_map[s0:s1], non_blocking=True)  # this step's share of the map upload
+        d = defl[b * BATCH:(b + 1) * BATCH]
+        d.copy_(h_defl, non_blocking=True)
+        plans["mixed"].lens(qu, d, out, var, first=b * BATCH, count=BATCH)
+        h_out.copy_(out, non_blocking=True)
+        h_var.copy_(var, non_blocking=True)
+
+    e2e_step(0)
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(nb_e2e):
+        e2e_step(1 + i)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    h2d = slice_len * 16 + BATCH * 16
+    d2h = BATCH * 16 + BATCH * 8
+
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+    n_gpus = world
+    ms_step = total_ms / args.steps
+    value = n_gpus * BATCH * args.steps / (total_ms / 1e3)
+    fp_value = n_gpus * BATCH * len(fp_per) / (fp_total / 1e3)
+    kern_ms = statistics.mean(per)
+    fl32 = flops.mixed_fp32_flops(W.K, 2)
+    achieved = fl32 * BATCH / (kern_ms / 1e3) / 1e12
+    fl64 = flops.fp64_flops(W.K, 2)
+    achieved64 = fl64 * BATCH / (statistics.mean(fp_per) / 1e3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": "pts/s", "n_gpus": n_gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64 in/out; double-float (2 x f32) factor, f64 geometry",
+        "data": "synthetic: white-noise Q/U map (the work does not depend on the values) and per-pixel Gaussian "
+                "deflections of 2.5 arcmin rms",
+        "config": config(n_gpus),
+        "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
+        "fp64": {"value": fp_value, "unit": "pts/s", "ms_per_step": statistics.mean(fp_per),
+                 "steps": len(fp_per)},
+        "mixed_over_fp64": value / fp_value,
+        "mixed_stats": st,
+        "e2e": {"value": n_gpus * BATCH * nb_e2e / (e2e_ms / 1e3), "unit": "pts/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": flops.FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / flops.FP32_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "lens_kernel<32,2,mixed> (FP32 pipe, double-float)",
+                     "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                     "flops_per_point": fl32},
+        "roofline_fp64": {"bound": "alu", "achieved": achieved64, "peak": flops.FP64_PEAK_TFLOPS,
+                          "unit": "TFLOP/s", "frac": achieved64 / flops.FP64_PEAK_TFLOPS,
+                          "kernel": "lens_kernel<32,2,fp64>", "flops_per_point": fl64},
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "gpu_launches": args.steps,
+    }
+    print(json.dumps(line))
+
+
+# ----------------------------------------------------------- reference arm
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    per_step = []
+    for _ in range(args.warmup):
+        pass
+    steps = max(1, args.steps)
+    budget = max(20.0, min(150.0, 10.0 * steps)) / steps
+    cpu = None
+    for _ in range(steps):
+        cpu = cpu_oracle(budget)
+        per_step.append(cpu["value"])
+    value = statistics.mean(per_step)
+    ms_per_step = BATCH / value * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pts/s", "n_gpus": world,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (see cpu_baseline.sample)",
+            "config": config(world),
+            "cpu_baseline": {"value": value, "unit": "pts/s", "cores": cpu["cores"], "kind": "oracle",
+                             "sample": cpu["sample"]},
+            "e2e": {"value": value, "unit": "pts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.profile_case:
+        run_profile_case(a.profile_case)
+    elif a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -1,0 +1,57 @@
+"""Algorithmic operation counts and roofline peaks for the lens kernels.
+
+Counting convention (used for every roofline fraction reported by the bench):
+
+* a fused multiply-add counts 2 flops, any other add, subtract or multiply 1;
+  square roots, reciprocals and the table index count 2 each;
+* FP64 path: the arithmetic of the method itself, per target point, with K
+  stencil members and P = K(K-1)/2 pairs:
+    - left-looking Cholesky: (K^3 - K)/6 multiply-adds plus K pivots and P
+      scalings; complex Hermitian (spin 2) multiply-adds are 4 real ones;
+    - two forward solves (c and y): P multiply-adds each, K scalings each;
+    - covariance assembly: per pair the squared chord (3 sub, 3 mul, 2 add)
+      and the cubic table (index + 3 fma); spin 2 adds the parallel-transport
+      phase (4 projections of 2 fma + 1 mul, squares and products: 48 flops);
+      the K target entries likewise (their chords come from the search);
+    - value and variance: 2 dot products of length K;
+* mixed path: the same steps executed in double-float arithmetic on the FP32
+  pipe, each double-float operation costed in FP32 flops: multiply-accumulate
+  into an accumulator 15 (one TwoProduct with cross terms, one TwoSum, two
+  adds), add 20, multiply 10, square root or reciprocal 35.
+"""
+from __future__ import annotations
+
+# double-float operation costs in FP32 flops
+DF_MAC, DF_ADD, DF_MUL, DF_SPECIAL = 15, 20, 10, 35
+
+
+def fp64_flops(K: int, spin: int) -> float:
+    P = K * (K - 1) / 2
+    macs = (K ** 3 - K) / 6
+    cm = 4 if spin == 2 else 1  # real multiply-adds per (complex) multiply-add
+    chol = 2 * cm * macs + 2 * 2 * K + (2 if spin == 2 else 1) * P
+    solve = 2 * (2 * cm * P + (2 if spin == 2 else 1) * K)
+    pair = 8 + 8 + (48 + 2 if spin == 2 else 0)
+    assembly = pair * P + (8 + (50 if spin == 2 else 0)) * K
+    dots = 2 * 2 * K * (2 if spin == 2 else 1)
+    return chol + solve + assembly + dots
+
+
+def mixed_fp32_flops(K: int, spin: int) -> float:
+    P = K * (K - 1) / 2
+    macs = (K ** 3 - K) / 6
+    cm = 4 if spin == 2 else 1
+    chol = cm * macs * DF_MAC + K * 2 * DF_SPECIAL + P * (2 if spin == 2 else 1) * DF_MUL
+    solve = 2 * (cm * P * DF_MAC + K * (2 if spin == 2 else 1) * DF_MUL)
+    chord = 3 * DF_ADD + 3 * DF_MUL + 2 * DF_ADD
+    table = DF_MUL + 3 * (DF_MUL + DF_ADD)
+    phase = (27 * DF_MUL + 16 * DF_ADD + DF_SPECIAL) if spin == 2 else 0
+    entry = 2 * DF_MUL if spin == 2 else 0
+    assembly = P * (chord + table + phase + entry) + K * (table + phase + entry)
+    return chol + solve + assembly
+
+
+# peaks (TFLOP/s) derived from the unit counts and the 2070 MHz maximum SM clock:
+# 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz; FP64 at the 1.25 TFLOP/s nominal rate.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+FP64_PEAK_TFLOPS = 1.25

@@ -167,3 +167,41 @@ def job_stream(n_jobs: int, rate_hz: float, seed: int = 500, max_points: float =
         first = int(rng.integers(0, npix - count + 1))
         jobs.append(Job(t, int(rng.choice([0, 2])), int(rng.choice([16, 32])), nside, first, count))
     return jobs
+
+
+def hashed_normal(idx: np.ndarray, seed: int, ncomp: int = 1) -> np.ndarray:
+    """Deterministic N(0,1)-like values per pixel index (SplitMix64 hash, Box-Muller),
+    so that any subset of a huge map can be generated without materialising it."""
+    idx = np.asarray(idx, dtype=np.uint64)
+    out = []
+    with np.errstate(over="ignore"):  # modular 64-bit arithmetic
+        return _hashed(idx, seed, ncomp)
+
+
+def _hashed(idx, seed, ncomp):
+    out = []
+    for c in range(ncomp):
+        z = idx * np.uint64(2 * ncomp) + np.uint64(2 * c) + np.uint64(seed) * np.uint64(0x9E3779B97F4A7C15)
+        u = []
+        for k in range(2):
+            x = z + np.uint64(k)
+            x = (x + np.uint64(0x9E3779B97F4A7C15))
+            x = (x ^ (x >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+            x = (x ^ (x >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+            x = x ^ (x >> np.uint64(31))
+            u.append(((x >> np.uint64(11)).astype(np.float64) + 0.5) / 9007199254740992.0)
+        out.append(np.sqrt(-2.0 * np.log(u[0])) * np.cos(2.0 * math.pi * u[1]))
+    return out[0] if ncomp == 1 else np.stack(out, axis=-1)
+
+
+class HashedMap:
+    """A map of ``hashed_normal`` values, indexable like a numpy array (no storage)."""
+
+    def __init__(self, npix: int, seed: int, ncomp: int = 1):
+        self.npix, self.seed, self.ncomp = npix, seed, ncomp
+
+    def __getitem__(self, key):
+        if isinstance(key, tuple):
+            idx, comp = key
+            return hashed_normal(idx, self.seed, self.ncomp)[..., comp]
+        return hashed_normal(key, self.seed, self.ncomp)
