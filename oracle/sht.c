@@ -145,14 +145,20 @@ void oracle_theta_coeffs(int lmax, int mode,
                          double *out_re, double *out_im)
 {
     int L1 = lmax + 1;
-    double *A = malloc(sizeof(double) * L1), *B = malloc(sizeof(double) * L1), *C = malloc(sizeof(double) * L1);
-    double *wr = malloc(sizeof(double) * L1), *wi = malloc(sizeof(double) * L1);
     memset(out_re, 0, sizeof(double) * npts * 2 * L1);
     memset(out_im, 0, sizeof(double) * npts * 2 * L1);
     int mp = (mode == 2) ? -2 : 0;
     int nsides = (mode == 2) ? 2 : 1;
-    for (int side = 0; side < nsides; ++side) {
-        for (int m0 = 0; m0 <= lmax; ++m0) {
+    /* few directions: parallel over m; many: parallel over directions */
+    int over_m = npts < 256;
+    long nm = (long)nsides * L1;
+#pragma omp parallel if (over_m)
+    {
+        double *A = malloc(sizeof(double) * L1), *B = malloc(sizeof(double) * L1), *C = malloc(sizeof(double) * L1);
+        double *wr = malloc(sizeof(double) * L1), *wi = malloc(sizeof(double) * L1);
+#pragma omp for schedule(dynamic, 4)
+        for (long it = 0; it < nm; ++it) {
+            int side = (int)(it / L1), m0 = (int)(it % L1);
             int m = side ? -m0 : m0;
             if (side && m0 == 0) continue;
             coefs(lmax, m, mp, A, B, C);
@@ -176,7 +182,7 @@ void oracle_theta_coeffs(int lmax, int mode,
                 wr[l] = ar * nl;
                 wi[l] = ai * nl;
             }
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if (!over_m)
             for (long p = 0; p < npts; ++p) {
                 double r, i_, dr = 0, di = 0;
                 column(lmax, m, mp, theta[p], A, B, C, wr, wi, &r, &i_,
@@ -191,6 +197,6 @@ void oracle_theta_coeffs(int lmax, int mode,
                 }
             }
         }
+        free(A); free(B); free(C); free(wr); free(wi);
     }
-    free(A); free(B); free(C); free(wr); free(wi);
 }

@@ -241,6 +241,8 @@ static int run(flints_plan_t p, int64_t first, int64_t count, const double *map,
     a.tab.c32 = p->d_c32;
     a.tab.t_max = p->t_max;
     a.tab.inv_h = p->inv_h;
+    a.tab.inv_h_hi = (float)p->inv_h;
+    a.tab.inv_h_lo = (float)(p->inv_h - (double)a.tab.inv_h_hi);
     a.tab.n = p->n;
     a.xi0 = p->xi0;
     a.r2 = p->r2;

@@ -135,6 +135,7 @@ struct Ops<double> {
     static __device__ __forceinline__ void add_prod(Acc &a, T x, T y) { a.v = fma(x, y, a.v); }
     static __device__ __forceinline__ T val(Acc a) { return a.v; }
     static __device__ __forceinline__ T shfl(T v, int src) { return __shfl_sync(FULL, v, src); }
+    static __device__ __forceinline__ T shfl_xor(T v, int m) { return __shfl_xor_sync(FULL, v, m); }
 };
 
 template <>
@@ -157,6 +158,9 @@ struct Ops<df> {
     static __device__ __forceinline__ T val(Acc a) { return dfacc_val(a); }
     static __device__ __forceinline__ T shfl(T v, int src) {
         return {__shfl_sync(FULL, v.hi, src), __shfl_sync(FULL, v.lo, src)};
+    }
+    static __device__ __forceinline__ T shfl_xor(T v, int m) {
+        return {__shfl_xor_sync(FULL, v.hi, m), __shfl_xor_sync(FULL, v.lo, m)};
     }
 };
 
@@ -253,6 +257,7 @@ struct TableDev {
     const Coef64 *c64;  // per interval: f_k, h g_k, c2, c3 (Horner in s)
     const float4 *c32;   // per interval, double-float: (f.hi, f.lo, m.hi, m.lo), (c2.hi, c2.lo, c3.hi, c3.lo)
     double t_max, inv_h;
+    float inv_h_hi, inv_h_lo;  // inv_h as a double-float pair
     int n;
 };
 

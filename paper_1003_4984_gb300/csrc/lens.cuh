@@ -56,18 +56,27 @@ template <int K, int SPIN, class R>
 struct WarpSmem {
     using Elem = typename std::conditional<SPIN == 0, typename Ops<R>::T, Cx<typename Ops<R>::T>>::type;
     static constexpr int NSLOT = Shape<K>::NSLOT;
+    // packed lower triangle of S + n I (row i starts at i(i+1)/2), then the two
+    // bordered right-hand-side rows (c and y), K entries each
+    static constexpr int MAT = K * (K + 1) / 2 + 2 * K;
     PointA pts[32];
-    double ox[K], oy[K], oz[K];  // neighbour offsets X_i - n'
+    double ox[K], oy[K], oz[K];          // neighbour offsets X_i - n' (FP64)
     double nz[K], ns[K], nc[K], nsn[K];  // neighbour z, sin(theta), cos(phi), sin(phi)
+    df gx[K], gy[K], gz[K], gnz[K], gns[K], gnc[K], gnsn[K];  // the same in double-float
     union U {
         struct Cand {
             RingRec rings[32];
             double cx[NSLOT], cy[NSLOT], cz[NSLOT], cc[NSLOT], cs[NSLOT];
             uint32_t cpix[NSLOT];
         } cand;
-        Elem mat[K * Shape<K>::LD];
+        Elem mat[MAT];
     } u;
 };
+
+template <int K>
+__device__ __forceinline__ int tri(int i, int k) {
+    return i < K ? i * (i + 1) / 2 + k : K * (K + 1) / 2 + (i - K) * K + k;
+}
 
 // ------------------------------------------------------------------ helpers
 __device__ __forceinline__ bool key_less(unsigned long long ka, unsigned ia, unsigned long long kb, unsigned ib) {
@@ -132,7 +141,7 @@ __device__ __forceinline__ double table_eval<double>(const TableDev &tab, double
 
 template <>
 __device__ __forceinline__ df table_eval<df>(const TableDev &tab, df t) {
-    const df x = df_mul(t, df_from(tab.inv_h));
+    const df x = df_mul(t, df{tab.inv_h_hi, tab.inv_h_lo});
     float kf = floorf(x.hi);
     df s = two_sum(__fsub_rn(x.hi, kf), x.lo);
     if (s.hi < 0.0f) {
@@ -157,21 +166,25 @@ __device__ __forceinline__ df table_eval<df>(const TableDev &tab, df t) {
 }
 
 // exp(2i(a_ij - a_ji)) for the pair (i -> j) with d = X_j - X_i, from the
-// projections of d on the local bases at both ends.
+// projections of d on the local bases at both ends: with e_theta = (z cos phi,
+// z sin phi, -s) and e_phi = (-sin phi, cos phi, 0),
+//   A = d.e_theta = z (dx cos phi + dy sin phi) - s dz,  B = d.e_phi = dy cos phi - dx sin phi,
+// exp(2i a) = (A + iB)^2 / (A^2 + B^2) at each end, the far end conjugated.
 template <class R>
 __device__ __forceinline__ Cx<typename Ops<R>::T> pair_phase(typename Ops<R>::T dx, typename Ops<R>::T dy,
-                                                             typename Ops<R>::T dz, double zi, double si,
-                                                             double ci, double sni, double zj, double sj,
-                                                             double cj, double snj) {
+                                                             typename Ops<R>::T dz, typename Ops<R>::T zi,
+                                                             typename Ops<R>::T si, typename Ops<R>::T ci,
+                                                             typename Ops<R>::T sni, typename Ops<R>::T zj,
+                                                             typename Ops<R>::T sj, typename Ops<R>::T cj,
+                                                             typename Ops<R>::T snj) {
     using O = Ops<R>;
     using T = typename O::T;
-    // at i: A1 = d.e_theta(i) = z_i (dx c_i + dy s_i) - s_i dz ; B1 = d.e_phi(i) = dy c_i - dx s_i
-    const T h1 = O::add(O::mul(dx, O::from(ci)), O::mul(dy, O::from(sni)));
-    const T A1 = O::sub(O::mul(O::from(zi), h1), O::mul(O::from(si), dz));
-    const T B1 = O::sub(O::mul(dy, O::from(ci)), O::mul(dx, O::from(sni)));
-    const T h2 = O::add(O::mul(dx, O::from(cj)), O::mul(dy, O::from(snj)));
-    const T A2 = O::sub(O::mul(O::from(zj), h2), O::mul(O::from(sj), dz));
-    const T B2 = O::sub(O::mul(dy, O::from(cj)), O::mul(dx, O::from(snj)));
+    const T h1 = O::add(O::mul(dx, ci), O::mul(dy, sni));
+    const T A1 = O::sub(O::mul(zi, h1), O::mul(si, dz));
+    const T B1 = O::sub(O::mul(dy, ci), O::mul(dx, sni));
+    const T h2 = O::add(O::mul(dx, cj), O::mul(dy, snj));
+    const T A2 = O::sub(O::mul(zj, h2), O::mul(sj, dz));
+    const T B2 = O::sub(O::mul(dy, cj), O::mul(dx, snj));
     const T A1s = O::mul(A1, A1), B1s = O::mul(B1, B1), A2s = O::mul(A2, A2), B2s = O::mul(B2, B2);
     const T re1 = O::sub(A1s, B1s), im1 = O::mul(O::add(A1, A1), B1);
     const T re2 = O::sub(A2s, B2s), im2 = O::neg(O::mul(O::add(A2, A2), B2));
@@ -184,7 +197,44 @@ __device__ __forceinline__ Cx<typename Ops<R>::T> pair_phase(typename Ops<R>::T 
 }
 
 // --------------------------------------------------- assemble, factor, solve
+// Neighbour geometry in precision R (FP64 arrays, or their double-float copies).
+template <class R, class SM>
+struct Geom;
+template <class SM>
+struct Geom<double, SM> {
+    static __device__ __forceinline__ double x(const SM &s, int i) { return s.ox[i]; }
+    static __device__ __forceinline__ double y(const SM &s, int i) { return s.oy[i]; }
+    static __device__ __forceinline__ double z(const SM &s, int i) { return s.oz[i]; }
+    static __device__ __forceinline__ double nz(const SM &s, int i) { return s.nz[i]; }
+    static __device__ __forceinline__ double ns(const SM &s, int i) { return s.ns[i]; }
+    static __device__ __forceinline__ double nc(const SM &s, int i) { return s.nc[i]; }
+    static __device__ __forceinline__ double nsn(const SM &s, int i) { return s.nsn[i]; }
+};
+template <class SM>
+struct Geom<df, SM> {
+    static __device__ __forceinline__ df x(const SM &s, int i) { return s.gx[i]; }
+    static __device__ __forceinline__ df y(const SM &s, int i) { return s.gy[i]; }
+    static __device__ __forceinline__ df z(const SM &s, int i) { return s.gz[i]; }
+    static __device__ __forceinline__ df nz(const SM &s, int i) { return s.gnz[i]; }
+    static __device__ __forceinline__ df ns(const SM &s, int i) { return s.gns[i]; }
+    static __device__ __forceinline__ df nc(const SM &s, int i) { return s.gnc[i]; }
+    static __device__ __forceinline__ df nsn(const SM &s, int i) { return s.gnsn[i]; }
+};
+
+template <class R>
+__device__ __forceinline__ Cx<typename Ops<R>::T> cx_conj(Cx<typename Ops<R>::T> a) {
+    return {a.re, Ops<R>::neg(a.im)};
+}
+
 // Returns false when a pivot of S + nugget I is not positive.
+//
+// Factorisation: left-looking Cholesky of the matrix bordered by the two
+// right-hand-side rows (row K holds c (spin 2: c0 = <P(n') P_i^*>), row K+1
+// holds conj(y)); the factor's bordered rows are then conj(L^-1 conj(c)) and
+// conj(L^-1 y), so the forward solves need no separate pass.  At column j the
+// K+2-j active rows are spread over 32/s lane groups of s lanes, s the largest
+// power of two with (K+2-j) s <= 32, and each group splits the dot product
+// over k < j and reduces it with shuffles.
 template <int K, int SPIN, class R, class SM>
 __device__ bool solve_point(SM &sm, const PointA &P, int lane, double nugget, const TableDev &tab,
                             const double (&keyd)[Shape<K>::RPL], const double (&yre)[Shape<K>::RPL],
@@ -192,7 +242,9 @@ __device__ bool solve_point(SM &sm, const PointA &P, int lane, double nugget, co
                             double &var_rel) {
     using O = Ops<R>;
     using T = typename O::T;
-    constexpr int RPL = Shape<K>::RPL, LD = Shape<K>::LD, NTRI = Shape<K>::NTRI;
+    using G = Geom<R, SM>;
+    constexpr int RPL = Shape<K>::RPL, NTRI = Shape<K>::NTRI;
+    constexpr int NROW = K + 2;
     using Elem = typename SM::Elem;
     Elem *mat = sm.u.mat;
 
@@ -213,22 +265,22 @@ __device__ bool solve_point(SM &sm, const PointA &P, int lane, double nugget, co
                     e.im = O::zero();
                 }
             } else {
-                const T dx = O::sub(O::from(sm.ox[j]), O::from(sm.ox[i]));
-                const T dy = O::sub(O::from(sm.oy[j]), O::from(sm.oy[i]));
-                const T dz = O::sub(O::from(sm.oz[j]), O::from(sm.oz[i]));
+                const T dx = O::sub(G::x(sm, j), G::x(sm, i));
+                const T dy = O::sub(G::y(sm, j), G::y(sm, i));
+                const T dz = O::sub(G::z(sm, j), G::z(sm, i));
                 const T t = O::add(O::add(O::mul(dx, dx), O::mul(dy, dy)), O::mul(dz, dz));
                 const T fv = table_eval<R>(tab, t);
                 if constexpr (SPIN == 0) {
                     e = fv;
                 } else {
-                    const Cx<T> ph = pair_phase<R>(dx, dy, dz, sm.nz[i], sm.ns[i], sm.nc[i], sm.nsn[i], sm.nz[j],
-                                                   sm.ns[j], sm.nc[j], sm.nsn[j]);
+                    const Cx<T> ph = pair_phase<R>(dx, dy, dz, G::nz(sm, i), G::ns(sm, i), G::nc(sm, i),
+                                                   G::nsn(sm, i), G::nz(sm, j), G::ns(sm, j), G::nc(sm, j),
+                                                   G::nsn(sm, j));
                     e.re = O::mul(fv, ph.re);
                     e.im = O::mul(fv, ph.im);
                 }
             }
-            mat[i * LD + j] = e;
-            // advance q by 32
+            mat[q] = e;
             j += 32;
             while (j > i) {
                 j -= i + 1;
@@ -236,176 +288,126 @@ __device__ bool solve_point(SM &sm, const PointA &P, int lane, double nugget, co
             }
         }
     }
-    // ---- right-hand sides: conj(c_i) and y_i for the owned rows
-    Elem bc[RPL], by[RPL];
+    // ---- bordered rows: row K = c (spin 2: c0), row K+1 = conj(y)
 #pragma unroll
     for (int r = 0; r < RPL; ++r) {
         const int i = lane + 32 * r;
         if (i < K) {
             const T fv = table_eval<R>(tab, O::from(keyd[r]));
             if constexpr (SPIN == 0) {
-                bc[r] = fv;
-                by[r] = O::from(yre[r]);
+                mat[tri<K>(K, i)] = fv;
+                mat[tri<K>(K + 1, i)] = O::from(yre[r]);
             } else {
-                // target -> neighbour: d = X_i - n' (offset), phase at n' and at X_i
-                const Cx<T> ph = pair_phase<R>(O::from(sm.ox[i]), O::from(sm.oy[i]), O::from(sm.oz[i]), P.z, P.s,
-                                               P.cph, P.sph, sm.nz[i], sm.ns[i], sm.nc[i], sm.nsn[i]);
-                bc[r].re = O::mul(fv, ph.re);
-                bc[r].im = O::neg(O::mul(fv, ph.im));  // conj(c0_i)
-                by[r].re = O::from(yre[r]);
-                by[r].im = O::from(yim[r]);
+                // target -> neighbour: d = X_i - n', phase at n' and at X_i
+                const Cx<T> ph = pair_phase<R>(G::x(sm, i), G::y(sm, i), G::z(sm, i), O::from(P.z), O::from(P.s),
+                                               O::from(P.cph), O::from(P.sph), G::nz(sm, i), G::ns(sm, i),
+                                               G::nc(sm, i), G::nsn(sm, i));
+                Elem c0, yc;
+                c0.re = O::mul(fv, ph.re);
+                c0.im = O::mul(fv, ph.im);
+                yc.re = O::from(yre[r]);
+                yc.im = O::from(-yim[r]);
+                mat[tri<K>(K, i)] = c0;
+                mat[tri<K>(K + 1, i)] = yc;
             }
         }
     }
     __syncwarp();
 
-    // ---- left-looking Cholesky
-    T inv[RPL];
-#pragma unroll
-    for (int r = 0; r < RPL; ++r) inv[r] = O::zero();
-    bool ok = true;
+    // ---- split left-looking Cholesky over the bordered rows
     for (int j = 0; j < K; ++j) {
-        Elem srow[RPL];
+        const int nrows = NROW - j;
+        int s = 1;
+        while ((s << 1) * nrows <= 32) s <<= 1;
+        const int g = 32 / s;
+        const int part = lane & (s - 1), grp = lane / s;
+        const Elem *Lj = mat + tri<K>(j, 0);
+        Elem srow[2];
 #pragma unroll
-        for (int r = 0; r < RPL; ++r) {
-            const int i = lane + 32 * r;
-            if (i < K && i >= j) {
-                const Elem *Li = mat + i * LD;
-                const Elem *Lj = mat + j * LD;
-                if constexpr (SPIN == 0) {
-                    typename O::Acc acc = O::acc(Li[j]);
-                    for (int k = 0; k < j; ++k) O::sub_prod(acc, Li[k], Lj[k]);
-                    srow[r] = O::val(acc);
-                } else {
-                    typename O::Acc ar = O::acc(Li[j].re), ai = O::acc(Li[j].im);
-                    for (int k = 0; k < j; ++k) {
-                        const Elem a = Li[k], b = Lj[k];
+        for (int t = 0; t < 2; ++t) {
+            const int r = j + grp + t * g;
+            const bool act = r < NROW;
+            const int rr = act ? r : j;
+            const Elem *Lr = mat + tri<K>(rr, 0);
+            if constexpr (SPIN == 0) {
+                typename O::Acc acc = O::acc((part == 0 && act) ? Lr[j] : O::zero());
+                if (act)
+                    for (int k = part; k < j; k += s) O::sub_prod(acc, Lr[k], Lj[k]);
+                T v = O::val(acc);
+                for (int o = 1; o < s; o <<= 1) v = O::add(v, O::shfl_xor(v, o));
+                srow[t] = v;
+            } else {
+                const Elem a0 = Lr[j];
+                typename O::Acc ar = O::acc((part == 0 && act) ? a0.re : O::zero());
+                typename O::Acc ai = O::acc((part == 0 && act) ? a0.im : O::zero());
+                if (act)
+                    for (int k = part; k < j; k += s) {
+                        const Elem a = Lr[k], b = Lj[k];
                         O::sub_prod(ar, a.re, b.re);
                         O::sub_prod(ar, a.im, b.im);
                         O::sub_prod(ai, a.im, b.re);
                         O::add_prod(ai, a.re, b.im);
                     }
-                    srow[r].re = O::val(ar);
-                    srow[r].im = O::val(ai);
+                T vr = O::val(ar), vi = O::val(ai);
+                for (int o = 1; o < s; o <<= 1) {
+                    vr = O::add(vr, O::shfl_xor(vr, o));
+                    vi = O::add(vi, O::shfl_xor(vi, o));
                 }
+                srow[t].re = vr;
+                srow[t].im = vi;
             }
         }
-        // pivot from the owner of row j
-        const int owner = j & 31, rj = j >> 5;
-        T dmine;
+        // pivot: row j is held by lane 0 (group 0, part 0, t = 0)
+        T d;
         if constexpr (SPIN == 0) {
-            dmine = (RPL > 1 && rj == 1) ? srow[RPL - 1] : srow[0];
+            d = O::shfl(srow[0], 0);
         } else {
-            dmine = (RPL > 1 && rj == 1) ? srow[RPL - 1].re : srow[0].re;
+            d = O::shfl(srow[0].re, 0);
         }
-        const T d = O::shfl(dmine, owner);
-        if (!O::positive(d)) {
-            ok = false;
-            break;
-        }
+        if (!O::positive(d)) return false;
         const T ljj = O::sqrt_(d);
         const T il = O::rcp(ljj);
+        __syncwarp();
+        if (part == 0) {
 #pragma unroll
-        for (int r = 0; r < RPL; ++r) {
-            const int i = lane + 32 * r;
-            if (i < K && i > j) {
-                Elem v;
-                if constexpr (SPIN == 0) {
-                    v = O::mul(srow[r], il);
-                } else {
-                    v.re = O::mul(srow[r].re, il);
-                    v.im = O::mul(srow[r].im, il);
+            for (int t = 0; t < 2; ++t) {
+                const int r = j + grp + t * g;
+                if (r < NROW) {
+                    Elem v;
+                    if constexpr (SPIN == 0) {
+                        v = (r == j) ? ljj : O::mul(srow[t], il);
+                    } else {
+                        if (r == j) {
+                            v.re = ljj;
+                            v.im = O::zero();
+                        } else {
+                            v.re = O::mul(srow[t].re, il);
+                            v.im = O::mul(srow[t].im, il);
+                        }
+                    }
+                    mat[tri<K>(r, j)] = v;
                 }
-                mat[i * LD + j] = v;
-            } else if (i == j) {
-                Elem v;
-                if constexpr (SPIN == 0) {
-                    v = ljj;
-                } else {
-                    v.re = ljj;
-                    v.im = O::zero();
-                }
-                mat[i * LD + j] = v;
-                inv[r] = il;
             }
         }
         __syncwarp();
     }
-    if (!ok) return false;
-
-    // ---- forward solves, column oriented
-    for (int j = 0; j < K; ++j) {
-        const int owner = j & 31, rj = j >> 5;
-        Elem zc, zy;
-        if (lane == owner) {
-            const int r = (RPL > 1 && rj == 1) ? RPL - 1 : 0;
-            if constexpr (SPIN == 0) {
-                bc[r] = O::mul(bc[r], inv[r]);
-                by[r] = O::mul(by[r], inv[r]);
-            } else {
-                bc[r].re = O::mul(bc[r].re, inv[r]);
-                bc[r].im = O::mul(bc[r].im, inv[r]);
-                by[r].re = O::mul(by[r].re, inv[r]);
-                by[r].im = O::mul(by[r].im, inv[r]);
-            }
-        }
-        {
-            const int r = (RPL > 1 && rj == 1) ? RPL - 1 : 0;
-            if constexpr (SPIN == 0) {
-                zc = O::shfl(bc[r], owner);
-                zy = O::shfl(by[r], owner);
-            } else {
-                zc.re = O::shfl(bc[r].re, owner);
-                zc.im = O::shfl(bc[r].im, owner);
-                zy.re = O::shfl(by[r].re, owner);
-                zy.im = O::shfl(by[r].im, owner);
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < RPL; ++r) {
-            const int i = lane + 32 * r;
-            if (i < K && i > j) {
-                const Elem l = mat[i * LD + j];
-                if constexpr (SPIN == 0) {
-                    typename O::Acc a1 = O::acc(bc[r]), a2 = O::acc(by[r]);
-                    O::sub_prod(a1, l, zc);
-                    O::sub_prod(a2, l, zy);
-                    bc[r] = O::val(a1);
-                    by[r] = O::val(a2);
-                } else {
-                    typename O::Acc cr = O::acc(bc[r].re), ci = O::acc(bc[r].im);
-                    typename O::Acc yr = O::acc(by[r].re), yi = O::acc(by[r].im);
-                    O::sub_prod(cr, l.re, zc.re);
-                    O::add_prod(cr, l.im, zc.im);
-                    O::sub_prod(ci, l.re, zc.im);
-                    O::sub_prod(ci, l.im, zc.re);
-                    O::sub_prod(yr, l.re, zy.re);
-                    O::add_prod(yr, l.im, zy.im);
-                    O::sub_prod(yi, l.re, zy.im);
-                    O::sub_prod(yi, l.im, zy.re);
-                    bc[r].re = O::val(cr);
-                    bc[r].im = O::val(ci);
-                    by[r].re = O::val(yr);
-                    by[r].im = O::val(yi);
-                }
-            }
-        }
-    }
-    // ---- value = z_c^H z_y, variance = 1 - |z_c|^2 (FP64 sums)
+    // ---- value = z_c^H z_y = sum_k row_K[k] conj(row_K+1[k]);  variance = 1 - |z_c|^2
     double vr = 0.0, vi = 0.0, nc = 0.0;
 #pragma unroll
     for (int r = 0; r < RPL; ++r) {
-        const int i = lane + 32 * r;
-        if (i < K) {
+        const int k = lane + 32 * r;
+        if (k < K) {
+            const Elem c = mat[tri<K>(K, k)], y = mat[tri<K>(K + 1, k)];
             if constexpr (SPIN == 0) {
-                const double c = O::to(bc[r]), y = O::to(by[r]);
-                vr = fma(c, y, vr);
-                nc = fma(c, c, nc);
+                const double cd = O::to(c), yd = O::to(y);
+                vr = fma(cd, yd, vr);
+                nc = fma(cd, cd, nc);
             } else {
-                const double cr = O::to(bc[r].re), ci = O::to(bc[r].im);
-                const double yr = O::to(by[r].re), yi = O::to(by[r].im);
+                const double cr = O::to(c.re), ci = O::to(c.im);
+                const double yr = O::to(y.re), yi = O::to(y.im);
+                // (cr + i ci)(yr - i yi)
                 vr = fma(cr, yr, fma(ci, yi, vr));
-                vi = fma(cr, yi, fma(-ci, yr, vi));
+                vi = fma(ci, yr, fma(-cr, yi, vi));
                 nc = fma(cr, cr, fma(ci, ci, nc));
             }
         }
@@ -614,6 +616,15 @@ __global__ void __launch_bounds__(WPB * 32) lens_kernel(LensArgs a, int R_rings)
                         sm.nc[i] = sm.u.cand.cc[c];
                         sm.nsn[i] = sm.u.cand.cs[c];
                         pixr[r] = sm.u.cand.cpix[c];
+                        if (MIXED) {
+                            sm.gx[i] = df_from(sm.ox[i]);
+                            sm.gy[i] = df_from(sm.oy[i]);
+                            sm.gz[i] = df_from(sm.oz[i]);
+                            sm.gnz[i] = df_from(cz);
+                            sm.gns[i] = df_from(sm.ns[i]);
+                            sm.gnc[i] = df_from(sm.nc[i]);
+                            sm.gnsn[i] = df_from(sm.nsn[i]);
+                        }
                     }
                 }
             }
