@@ -165,6 +165,33 @@ int flints_get_table(flints_plan_t plan, int which, double *f, double *g, void *
 /* Message describing the last error returned on the calling thread. */
 const char *flints_last_error(void);
 
+/* Lens the target range [first, first+count) without allocating any device
+ * memory.  The paper has no counterpart: this entry point exists for callers
+ * that cannot call cudaMalloc -- code running during CUDA stream capture,
+ * serving runtimes that hand all device memory to their own pool, hosts whose
+ * allocator policy forbids the library from allocating.  It runs the same xi
+ * tabulation and lens kernels as flints_plan + flints_lens_range, with their
+ * working memory (spectrum, table, coefficients, counters, under 1 MB) in a
+ * fixed file-scope device array that every GPU loading the library holds
+ * until the process exits.
+ *   Arguments: as flints_plan (cl, cl_bb are HOST pointers) followed by the
+ *   target range and the DEVICE buffers of flints_lens_range.
+ *   Limits: lmax <= 8192 and a xi table of at most 8192 intervals; larger
+ *   requests return FLINTS_EINVAL with a message naming the limit.
+ *   Set-up: the first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ *   Sharing: all calls use the same array and it keeps the last call's
+ *   contents (the call clears what must start at zero).  Calls whose work
+ *   overlaps on the GPU (different streams or threads) race on it: serialise
+ *   them.  The call synchronises `stream` once, after the tabulation.
+ *   Errors: flints_status codes; message in flints_noalloc_last_error(). */
+int flints_lens_noalloc(int64_t nside, int lmax, const double *cl, const double *cl_bb, int spin,
+                        int K, int precision, int64_t first, int64_t count, const double *map,
+                        const double *defl, double *out, double *var, uint8_t *status,
+                        void *stream);
+const char *flints_noalloc_last_error(void);
+
 /* Release a plan and its device memory (NULL is allowed). */
 void flints_free(flints_plan_t plan);
 

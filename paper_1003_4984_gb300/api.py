@@ -77,6 +77,9 @@ def load_library(path: str = LIB_PATH):
     lib.flints_last_error.restype = ctypes.c_char_p
     lib.flints_free.argtypes = [vp]
     lib.flints_free.restype = None
+    lib.flints_lens_noalloc.argtypes = [i64, c_int, dp, dp, c_int, c_int, c_int, i64, i64, vp, vp, vp, vp, vp, vp]
+    lib.flints_lens_noalloc.restype = c_int
+    lib.flints_noalloc_last_error.restype = ctypes.c_char_p
     for name in ("flints_plan", "flints_lens_spin0", "flints_lens_spin2", "flints_lens_range", "flints_stencil",
                  "flints_lens_batch", "flints_get_stats", "flints_reset_stats", "flints_get_info",
                  "flints_get_table"):
@@ -264,3 +267,28 @@ def lens_host(plan: Plan, map_host: np.ndarray, defl_host: np.ndarray, first: in
     var = torch.empty(count, dtype=torch.float64, device=m.device)
     out, var, _ = plan.lens(m, d, var=var, first=first, count=count, stream=stream)
     return out.cpu().numpy(), var.cpu().numpy()
+
+
+def lens_noalloc(nside: int, cl, map_, defl, out, var=None, status=None, cl_bb=None, spin: int = 0, K: int = 32,
+                 precision: str = "fp64", first: int = 0, count: int | None = None, stream=None):
+    """flints_lens_noalloc: lens without any device allocation by the library.
+
+    For callers that cannot call cudaMalloc (stream capture, caller-owned memory
+    pools): every buffer is the caller's; the library's working memory is a fixed
+    device array.  The first call on a device must come before any stream capture.
+    """
+    lib = load_library()
+    npix = 12 * int(nside) * int(nside)
+    if count is None:
+        count = npix - first
+    cl = np.ascontiguousarray(cl, dtype=np.float64)
+    bb = None if cl_bb is None else np.ascontiguousarray(cl_bb, dtype=np.float64)
+    dp = ctypes.POINTER(ctypes.c_double)
+    prec = {"fp64": FLINTS_FP64, "mixed": FLINTS_MIXED}[precision]
+    rc = lib.flints_lens_noalloc(int(nside), cl.size - 1, cl.ctypes.data_as(dp),
+                                 bb.ctypes.data_as(dp) if bb is not None else None, int(spin), int(K), prec,
+                                 int(first), int(count), _ptr(map_), _ptr(defl), _ptr(out), _ptr(var), _ptr(status),
+                                 _stream(stream))
+    if rc != 0:
+        raise FlintsError(f"flints error {rc}: {lib.flints_noalloc_last_error().decode()}")
+    return out, var, status
