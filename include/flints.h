@@ -137,6 +137,15 @@ int flints_stencil(flints_plan_t plan, int64_t first, int64_t count,
                    const double *defl, int64_t *idx, uint8_t *status,
                    void *stream);
 
+/* Launch shape of a plan's lens launches (the autotuner's knobs).
+ *   warps_per_block 1..8 (0: 4), blocks_per_sm cap (0: as many as fit),
+ *   tile_points targets per warp tile 1..32 (0: 32).  cfg NULL restores the
+ *   defaults.  Results do not depend on the launch shape. */
+typedef struct {
+    int warps_per_block, blocks_per_sm, tile_points;
+} flints_launch_cfg;
+int flints_plan_set_launch(flints_plan_t plan, const flints_launch_cfg *cfg);
+
 /* One job of a batched launch: a target range of one plan. */
 typedef struct {
     flints_plan_t plan;
@@ -146,9 +155,34 @@ typedef struct {
     uint8_t *status;
 } flints_job;
 
-/* Run n jobs (plans may differ in Nside, K, spin and precision) with one
- * launch per (spin, K, precision) class, all on `stream`. */
+/* Run n jobs (plans may differ in Nside, K, spin and precision) as one
+ * persistent launch per precision class on `stream`, then synchronise the
+ * stream.  Convenience form of the batch objects below: it allocates a
+ * temporary batch, so it cannot be captured in a CUDA graph. */
 int flints_lens_batch(const flints_job *jobs, int n, void *stream);
+
+/* Batch objects for the persistent batched launch.
+ *   flints_batch_create: device job table and work queues for up to
+ *     max_jobs jobs, plus pinned host staging (allocates; not capturable).
+ *   flints_batch_stage: host-only: validate the jobs, order them by precision
+ *     class and decreasing estimated cost, cut them into tiles of tile_points
+ *     targets (0: 32), write the table into the pinned staging buffer.
+ *   flints_batch_launch: upload the staged table, reset the work queues and
+ *     launch the two persistent kernels (FP64 and mixed jobs) on `stream`:
+ *     stream operations only, so it can be captured in a CUDA graph; a replay
+ *     runs whatever table was staged last.  The warps_per_block of cfg must
+ *     have been used by an earlier launch before capture (changing it
+ *     reconfigures the kernel).  Jobs of one batch must not write overlapping
+ *     outputs.
+ *   flints_batch_run: stage + launch (tile size from cfg).
+ * Errors: FLINTS_EINVAL for bad jobs (message names the job index). */
+typedef struct flints_batch_s *flints_batch_t;
+int flints_batch_create(flints_batch_t *out, int max_jobs);
+int flints_batch_stage(flints_batch_t batch, const flints_job *jobs, int n, int tile_points);
+int flints_batch_launch(flints_batch_t batch, const flints_launch_cfg *cfg, void *stream);
+int flints_batch_run(flints_batch_t batch, const flints_job *jobs, int n, const flints_launch_cfg *cfg,
+                     void *stream);
+void flints_batch_free(flints_batch_t batch);
 
 /* Device counters of per-point events (synchronises `stream`). */
 int flints_get_stats(flints_plan_t plan, flints_stats *s, void *stream);

@@ -39,6 +39,14 @@ class _Info(ctypes.Structure):
                 ("xi0", ctypes.c_double), ("search_radius", ctypes.c_double)]
 
 
+class LaunchCfg(ctypes.Structure):
+    """flints_launch_cfg: warps per block, blocks per SM cap, targets per warp tile (0 = default)."""
+    _fields_ = [("warps_per_block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int), ("tile_points", ctypes.c_int)]
+
+    def key(self):
+        return (self.warps_per_block, self.blocks_per_sm, self.tile_points)
+
+
 class _Job(ctypes.Structure):
     _fields_ = [("plan", ctypes.c_void_p), ("first", ctypes.c_int64), ("count", ctypes.c_int64),
                 ("map", ctypes.c_void_p), ("defl", ctypes.c_void_p), ("out", ctypes.c_void_p),
@@ -77,6 +85,16 @@ def load_library(path: str = LIB_PATH):
     lib.flints_last_error.restype = ctypes.c_char_p
     lib.flints_free.argtypes = [vp]
     lib.flints_free.restype = None
+    lib.flints_plan_set_launch.argtypes = [vp, ctypes.POINTER(LaunchCfg)]
+    lib.flints_plan_set_launch.restype = c_int
+    lib.flints_batch_create.argtypes = [ctypes.POINTER(vp), c_int]
+    lib.flints_batch_stage.argtypes = [vp, ctypes.POINTER(_Job), c_int, c_int]
+    lib.flints_batch_launch.argtypes = [vp, ctypes.POINTER(LaunchCfg), vp]
+    lib.flints_batch_run.argtypes = [vp, ctypes.POINTER(_Job), c_int, ctypes.POINTER(LaunchCfg), vp]
+    lib.flints_batch_free.argtypes = [vp]
+    lib.flints_batch_free.restype = None
+    for name in ("flints_batch_create", "flints_batch_stage", "flints_batch_launch", "flints_batch_run"):
+        getattr(lib, name).restype = c_int
     lib.flints_lens_noalloc.argtypes = [i64, c_int, dp, dp, c_int, c_int, c_int, i64, i64, vp, vp, vp, vp, vp, vp]
     lib.flints_lens_noalloc.restype = c_int
     lib.flints_noalloc_last_error.restype = ctypes.c_char_p
@@ -192,6 +210,11 @@ class Plan:
     def reset_stats(self, stream=None):
         _check(_lib.flints_reset_stats(self._h, _stream(stream)))
 
+    def set_launch(self, cfg: "LaunchCfg | None"):
+        """Launch shape of this plan's lens launches (None: library defaults)."""
+        self.launch_cfg = cfg
+        _check(_lib.flints_plan_set_launch(self._h, ctypes.byref(cfg) if cfg is not None else None))
+
     # ------------------------------------------------------------- compute
     def lens(self, map_, defl, out=None, var=None, status=None, first: int = 0, count: int | None = None,
              stream=None):
@@ -246,13 +269,56 @@ class Plan:
         return idx, st
 
 
+def _job_array(jobs):
+    arr = (_Job * max(1, len(jobs)))()
+    for k, (plan, first, count, m, d, o, v, s) in enumerate(jobs):
+        arr[k] = _Job(plan.handle, first, count, _ptr(m), _ptr(d), _ptr(o), _ptr(v), _ptr(s))
+    return arr
+
+
+class Batch:
+    """Persistent batched launch over many plans' target ranges (flints_batch_*).
+
+    ``stage`` writes the job table on the host only; ``launch`` is stream work
+    only (upload, queue reset, kernels) and can be captured in a CUDA graph.
+    Jobs are tuples (plan, first, count, map, defl, out, var, status).
+    """
+
+    def __init__(self, max_jobs: int):
+        lib = load_library()
+        h = ctypes.c_void_p()
+        _check(lib.flints_batch_create(ctypes.byref(h), int(max_jobs)))
+        self._h = h
+        self._keep = None
+
+    def stage(self, jobs, tile_points: int = 0):
+        self._keep = list(jobs)  # the caller's tensors must outlive the launches
+        arr = _job_array(jobs)
+        _check(_lib.flints_batch_stage(self._h, arr, len(jobs), int(tile_points)))
+
+    def launch(self, cfg: "LaunchCfg | None" = None, stream=None):
+        _check(_lib.flints_batch_launch(self._h, ctypes.byref(cfg) if cfg is not None else None, _stream(stream)))
+
+    def run(self, jobs, cfg: "LaunchCfg | None" = None, stream=None):
+        self.stage(jobs, cfg.tile_points if cfg is not None else 0)
+        self.launch(cfg, stream)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.flints_batch_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def lens_batch(jobs, stream=None):
     """Run several (plan, first, count, map, defl, out, var, status) jobs through flints_lens_batch."""
     load_library()
-    arr = (_Job * len(jobs))()
-    for k, (plan, first, count, m, d, o, v, s) in enumerate(jobs):
-        arr[k] = _Job(plan.handle, first, count, _ptr(m), _ptr(d), _ptr(o), _ptr(v), _ptr(s))
-    _check(_lib.flints_lens_batch(arr, len(jobs), _stream(stream)))
+    _check(_lib.flints_lens_batch(_job_array(jobs), len(jobs), _stream(stream)))
 
 
 def lens_host(plan: Plan, map_host: np.ndarray, defl_host: np.ndarray, first: int = 0, count: int | None = None,

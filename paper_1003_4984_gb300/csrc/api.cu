@@ -3,13 +3,23 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
+#include "batch_types.cuh"
 
 namespace flints {
-cudaError_t launch_lens_spin0(int K, int precision, const LensArgs &a, int R_rings, cudaStream_t st);
-cudaError_t launch_lens_spin2(int K, int precision, const LensArgs &a, int R_rings, cudaStream_t st);
+cudaError_t batch_prepare_p0(int wpb, int *max_blocks_per_sm);
+cudaError_t batch_prepare_p1(int wpb, int *max_blocks_per_sm);
+cudaError_t batch_launch_p0(const BatchHeader *hdr, const BatchJob *jobs, unsigned long long *next_tile, int wpb,
+                            int blocks, cudaStream_t st);
+cudaError_t batch_launch_p1(const BatchHeader *hdr, const BatchJob *jobs, unsigned long long *next_tile, int wpb,
+                            int blocks, cudaStream_t st);
+cudaError_t launch_lens_spin0(int K, int precision, const LensArgs &a, int R_rings, const LaunchCfg &cfg,
+                              cudaStream_t st);
+cudaError_t launch_lens_spin2(int K, int precision, const LensArgs &a, int R_rings, const LaunchCfg &cfg,
+                              cudaStream_t st);
 
 int device_sm_count() {
     int dev = 0, n = 0;
@@ -18,9 +28,10 @@ int device_sm_count() {
     return n;
 }
 
-cudaError_t launch_lens(int spin, int K, int precision, const LensArgs &a, int R_rings, cudaStream_t st) {
-    return spin == 0 ? launch_lens_spin0(K, precision, a, R_rings, st)
-                     : launch_lens_spin2(K, precision, a, R_rings, st);
+cudaError_t launch_lens(int spin, int K, int precision, const LensArgs &a, int R_rings, const LaunchCfg &cfg,
+                        cudaStream_t st) {
+    return spin == 0 ? launch_lens_spin0(K, precision, a, R_rings, cfg, st)
+                     : launch_lens_spin2(K, precision, a, R_rings, cfg, st);
 }
 }  // namespace flints
 
@@ -38,6 +49,7 @@ struct flints_plan_s {
     float4 *d_c32;
     unsigned long long *d_counters;
     int64_t points;
+    LaunchCfg cfg;
 };
 
 static thread_local char g_err[512] = "no error";
@@ -247,7 +259,7 @@ static int run(flints_plan_t p, int64_t first, int64_t count, const double *map,
     a.xi0 = p->xi0;
     a.r2 = p->r2;
     a.counters = p->d_counters;
-    cudaError_t e = launch_lens(p->spin, p->K, p->precision, a, p->R_rings, (cudaStream_t)stream);
+    cudaError_t e = launch_lens(p->spin, p->K, p->precision, a, p->R_rings, p->cfg, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "lens kernel launch");
     p->points += count;
     return FLINTS_OK;
@@ -277,12 +289,187 @@ int flints_stencil(flints_plan_t p, int64_t first, int64_t count, const double *
     return run(p, first, count, nullptr, defl, nullptr, nullptr, status, idx, stream);
 }
 
-int flints_lens_batch(const flints_job *jobs, int n, void *stream) {
-    if (n < 0 || (n > 0 && !jobs)) return fail(FLINTS_EINVAL, "flints_lens_batch: bad job list");
+// ------------------------------------------------------------------ batches
+}  // extern "C"
+
+struct flints_batch_s {
+    int device, max_jobs, num_sms;
+    size_t table_bytes;       // header + job array
+    unsigned char *d_buf;     // device: header, jobs, two work-queue counters
+    unsigned char *h_buf;     // pinned host staging of header and jobs
+    int wpb[2], max_bps[2];   // prepared launch shape per precision class
+};
+
+static BatchHeader *hdr_of(unsigned char *p) { return reinterpret_cast<BatchHeader *>(p); }
+static BatchJob *jobs_of(unsigned char *p) { return reinterpret_cast<BatchJob *>(p + sizeof(BatchHeader)); }
+
+static int batch_prepare(flints_batch_s *b, int cls, int wpb) {
+    int mx = 0;
+    cudaError_t e = cls ? batch_prepare_p1(wpb, &mx) : batch_prepare_p0(wpb, &mx);
+    if (e != cudaSuccess) return cuda_fail(e, "batch kernel set-up");
+    if (mx < 1) return fail(FLINTS_EINVAL, "batch kernel: %d warps per block do not fit on an SM", wpb);
+    b->wpb[cls] = wpb;
+    b->max_bps[cls] = mx;
+    return FLINTS_OK;
+}
+
+extern "C" {
+
+int flints_batch_create(flints_batch_t *out, int max_jobs) {
+    if (!out || max_jobs < 1 || max_jobs > (1 << 20)) return fail(FLINTS_EINVAL, "flints_batch_create: bad arguments");
+    *out = nullptr;
+    flints_batch_s *b = new flints_batch_s();
+    std::memset(b, 0, sizeof *b);
+    cudaGetDevice(&b->device);
+    b->max_jobs = max_jobs;
+    b->num_sms = device_sm_count();
+    b->table_bytes = sizeof(BatchHeader) + sizeof(BatchJob) * (size_t)max_jobs;
+    cudaError_t e = cudaMalloc((void **)&b->d_buf, b->table_bytes + 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&b->h_buf, b->table_bytes, cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+        cudaFree(b->d_buf);
+        delete b;
+        return cuda_fail(e, "flints_batch_create: allocation");
+    }
+    std::memset(b->h_buf, 0, b->table_bytes);
+    for (int cls = 0; cls < 2; ++cls) {
+        if (int rc = batch_prepare(b, cls, 4)) {
+            cudaFree(b->d_buf);
+            cudaFreeHost(b->h_buf);
+            delete b;
+            return rc;
+        }
+    }
+    *out = b;
+    return FLINTS_OK;
+}
+
+void flints_batch_free(flints_batch_t b) {
+    if (!b) return;
+    cudaFree(b->d_buf);
+    cudaFreeHost(b->h_buf);
+    delete b;
+}
+
+int flints_batch_stage(flints_batch_t b, const flints_job *jobs, int n, int tile_points) {
+    if (!b) return fail(FLINTS_EINVAL, "batch is NULL");
+    if (n < 0 || n > b->max_jobs || (n > 0 && !jobs))
+        return fail(FLINTS_EINVAL, "flints_batch_stage: %d jobs for a batch of capacity %d", n, b->max_jobs);
+    if (tile_points < 0 || tile_points > 32) return fail(FLINTS_EINVAL, "flints_batch_stage: tile_points 0..32");
+    const int tp = tile_points > 0 ? tile_points : 32;
+    std::vector<BatchJob> v;
+    v.reserve(n);
+    std::vector<double> cost;
     for (int i = 0; i < n; ++i) {
         const flints_job &j = jobs[i];
-        if (int rc = run(j.plan, j.first, j.count, j.map, j.defl, j.out, j.var, j.status, nullptr, stream)) return rc;
+        flints_plan_s *p = j.plan;
+        if (!p) return fail(FLINTS_EINVAL, "job %d: plan is NULL", i);
+        if (p->device != b->device) return fail(FLINTS_EINVAL, "job %d: plan and batch on different devices", i);
+        const int64_t npix = 12 * p->nside * p->nside;
+        if (j.first < 0 || j.count < 0 || j.first > npix || j.count > npix - j.first)
+            return fail(FLINTS_EINVAL, "job %d: target range outside the map", i);
+        if (j.count == 0) continue;
+        if (!j.map || !j.defl || !j.out) return fail(FLINTS_EINVAL, "job %d: NULL data pointer", i);
+        if (((uintptr_t)j.map | (uintptr_t)j.defl | (uintptr_t)j.out) & 15u)
+            return fail(FLINTS_EINVAL, "job %d: map, defl and out must be 16-byte aligned", i);
+        BatchJob bj{};
+        LensArgs &a = bj.a;
+        a.nside = p->nside;
+        a.first = j.first;
+        a.count = j.count;
+        a.map = j.map;
+        a.defl = j.defl;
+        a.out = j.out;
+        a.var = (p->flags & FLINTS_NO_VARIANCE) ? nullptr : j.var;
+        a.status = j.status;
+        a.stencil = nullptr;
+        a.tab.c64 = p->d_c64;
+        a.tab.c32 = p->d_c32;
+        a.tab.t_max = p->t_max;
+        a.tab.inv_h = p->inv_h;
+        a.tab.inv_h_hi = (float)p->inv_h;
+        a.tab.inv_h_lo = (float)(p->inv_h - (double)a.tab.inv_h_hi);
+        a.tab.n = p->n;
+        a.xi0 = p->xi0;
+        a.r2 = p->r2;
+        a.counters = p->d_counters;
+        bj.R_rings = p->R_rings;
+        bj.K = p->K;
+        bj.spin = p->spin;
+        bj.precision = p->precision;
+        bj.ntiles = (j.count + tp - 1) / tp;
+        v.push_back(bj);
+        p->points += j.count;
     }
+    // precision classes, each in decreasing estimated cost (longest jobs start first)
+    auto est = [](const BatchJob &x) {
+        return (double)x.a.count * x.K * x.K * x.K * (x.spin == 2 ? 4.0 : 1.0);
+    };
+    std::stable_sort(v.begin(), v.end(), [&](const BatchJob &x, const BatchJob &y) {
+        if (x.precision != y.precision) return x.precision < y.precision;
+        return est(x) > est(y);
+    });
+    BatchHeader h{};
+    h.tile_pts = tp;
+    int k = 0;
+    for (int cls = 0; cls < 2; ++cls) {
+        h.job_offset[cls] = k;
+        int64_t tiles = 0;
+        while (k < (int)v.size() && v[k].precision == cls) {
+            v[k].tile_begin = tiles;
+            tiles += v[k].ntiles;
+            ++k;
+            ++h.njobs[cls];
+        }
+        h.total_tiles[cls] = tiles;
+    }
+    *hdr_of(b->h_buf) = h;
+    if (!v.empty()) std::memcpy(jobs_of(b->h_buf), v.data(), v.size() * sizeof(BatchJob));
+    return FLINTS_OK;
+}
+
+int flints_batch_launch(flints_batch_t b, const flints_launch_cfg *cfg, void *stream) {
+    if (!b) return fail(FLINTS_EINVAL, "batch is NULL");
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != b->device) return fail(FLINTS_EINVAL, "batch was created on device %d, current device is %d", b->device, cur);
+    const int wpb = (cfg && cfg->warps_per_block > 0) ? cfg->warps_per_block : 4;
+    if (wpb > 8) return fail(FLINTS_EINVAL, "flints_batch_launch: warps_per_block 1..8");
+    cudaStream_t st = (cudaStream_t)stream;
+    const BatchHeader *h = hdr_of(b->h_buf);
+    const size_t bytes = sizeof(BatchHeader) + sizeof(BatchJob) * (size_t)(h->njobs[0] + h->njobs[1]);
+    unsigned long long *ctr = reinterpret_cast<unsigned long long *>(b->d_buf + b->table_bytes);
+    CK(cudaMemcpyAsync(b->d_buf, b->h_buf, bytes, cudaMemcpyHostToDevice, st), "batch: upload jobs");
+    CK(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned long long), st), "batch: reset work queues");
+    for (int cls = 0; cls < 2; ++cls) {
+        if (b->wpb[cls] != wpb)
+            if (int rc = batch_prepare(b, cls, wpb)) return rc;
+        int bps = b->max_bps[cls];
+        if (cfg && cfg->blocks_per_sm > 0 && cfg->blocks_per_sm < bps) bps = cfg->blocks_per_sm;
+        const int blocks = b->num_sms * bps;
+        cudaError_t e = cls ? batch_launch_p1(hdr_of(b->d_buf), jobs_of(b->d_buf), ctr, wpb, blocks, st)
+                            : batch_launch_p0(hdr_of(b->d_buf), jobs_of(b->d_buf), ctr, wpb, blocks, st);
+        if (e != cudaSuccess) return cuda_fail(e, "batch kernel launch");
+    }
+    return FLINTS_OK;
+}
+
+int flints_batch_run(flints_batch_t b, const flints_job *jobs, int n, const flints_launch_cfg *cfg, void *stream) {
+    const int tp = cfg ? cfg->tile_points : 0;
+    if (int rc = flints_batch_stage(b, jobs, n, tp)) return rc;
+    return flints_batch_launch(b, cfg, stream);
+}
+
+int flints_lens_batch(const flints_job *jobs, int n, void *stream) {
+    if (n < 0 || (n > 0 && !jobs)) return fail(FLINTS_EINVAL, "flints_lens_batch: bad job list");
+    if (n == 0) return FLINTS_OK;
+    flints_batch_t b = nullptr;
+    if (int rc = flints_batch_create(&b, n)) return rc;
+    int rc = flints_batch_run(b, jobs, n, nullptr, stream);
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    flints_batch_free(b);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "flints_lens_batch");
     return FLINTS_OK;
 }
 
@@ -303,6 +490,19 @@ int flints_reset_stats(flints_plan_t p, void *stream) {
     if (!p) return fail(FLINTS_EINVAL, "plan is NULL");
     CK(cudaMemsetAsync(p->d_counters, 0, CNT_N * sizeof(unsigned long long), (cudaStream_t)stream), "reset counters");
     p->points = 0;
+    return FLINTS_OK;
+}
+
+int flints_plan_set_launch(flints_plan_t p, const flints_launch_cfg *cfg) {
+    if (!p) return fail(FLINTS_EINVAL, "plan is NULL");
+    if (!cfg) {
+        p->cfg = LaunchCfg{0, 0, 0};
+        return FLINTS_OK;
+    }
+    if (cfg->warps_per_block < 0 || cfg->warps_per_block > 8 || cfg->blocks_per_sm < 0 || cfg->blocks_per_sm > 32 ||
+        cfg->tile_points < 0 || cfg->tile_points > 32)
+        return fail(FLINTS_EINVAL, "flints_plan_set_launch: warps_per_block 0..8, blocks_per_sm 0..32, tile_points 0..32");
+    p->cfg = LaunchCfg{cfg->warps_per_block, cfg->blocks_per_sm, cfg->tile_points};
     return FLINTS_OK;
 }
 

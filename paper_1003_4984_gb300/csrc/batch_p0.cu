@@ -1,0 +1,10 @@
+// Batched persistent lens kernel, precision class 0 (0 = FP64, 1 = double-float).
+#include "batch.cuh"
+
+namespace flints {
+cudaError_t batch_prepare_p0(int wpb, int *max_blocks_per_sm) { return batch_prepare<0>(wpb, max_blocks_per_sm); }
+cudaError_t batch_launch_p0(const BatchHeader *hdr, const BatchJob *jobs, unsigned long long *next_tile, int wpb,
+                             int blocks, cudaStream_t st) {
+    return batch_launch<0>(hdr, jobs, next_tile, wpb, blocks, st);
+}
+}  // namespace flints

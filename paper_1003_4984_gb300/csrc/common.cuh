@@ -275,10 +275,16 @@ struct LensArgs {
     unsigned long long *counters;  // points, nugget, fallback, window, failed
 };
 
+// Launch shape chosen by the caller or the autotuner (0 = library default).
+struct LaunchCfg {
+    int warps_per_block, blocks_per_sm, tile_points;
+};
+
 enum { CNT_POINTS = 0, CNT_NUGGET = 1, CNT_FALLBACK = 2, CNT_WINDOW = 3, CNT_FAILED = 4, CNT_N = 5 };
 
 // Host-side launchers (lens_spin0.cu, lens_spin2.cu, xi_table.cu).
-cudaError_t launch_lens(int spin, int K, int precision, const LensArgs &a, int R_rings, cudaStream_t st);
+cudaError_t launch_lens(int spin, int K, int precision, const LensArgs &a, int R_rings, const LaunchCfg &cfg,
+                        cudaStream_t st);
 cudaError_t launch_xi_table(int spin, int lmax, const double *cl_dev, const double *clbb_dev, double t_max,
                             int n, double *f_out, double *g_out, double *fm_out, double *gm_out,
                             cudaStream_t st);

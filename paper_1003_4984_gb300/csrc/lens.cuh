@@ -425,286 +425,18 @@ __device__ bool solve_point(SM &sm, const PointA &P, int lane, double nugget, co
 }
 
 // ------------------------------------------------------------------ kernel
-template <int K, int SPIN, int MIXED, int WPB>
-__global__ void __launch_bounds__(WPB * 32) lens_kernel(LensArgs a, int R_rings) {
-    using SMd = WarpSmem<K, SPIN, double>;
-    using SMf = WarpSmem<K, SPIN, df>;
-    constexpr int SPL = Shape<K>::SPL, RPL = Shape<K>::RPL, NSLOT = Shape<K>::NSLOT;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr size_t WS = sizeof(SMd) > sizeof(SMf) ? sizeof(SMd) : sizeof(SMf);
-    unsigned char *wbase = smem_raw + (size_t)warp * ((WS + 15) / 16 * 16);
-    SMd &sm = *reinterpret_cast<SMd *>(wbase);
+struct Counters {
+    unsigned long long nug = 0, fb = 0, win = 0, fail = 0;
+};
 
-    const int64_t N = a.nside;
-    const int64_t ntiles = (a.count + 31) / 32;
-    unsigned long long cnt_nug = 0, cnt_fb = 0, cnt_win = 0, cnt_fail = 0;
-
-    for (int64_t tile = (int64_t)blockIdx.x * WPB + warp; tile < ntiles; tile += (int64_t)gridDim.x * WPB) {
-        // ------------------------------------------------ phase A: displace
-        {
-            const int64_t p = tile * 32 + lane;
-            PointA P{};
-            if (p < a.count) {
-                const int64_t pix = a.first + p;
-                int64_t ring, jj;
-                pix_ring(N, pix, ring, jj);
-                const Ring rg = ring_of(N, ring);
-                double sp, cp;
-                sincospi(((double)jj + rg.f) / (2.0 * (double)rg.nq), &sp, &cp);
-                const double nx = rg.s * cp, ny = rg.s * sp, nz = rg.z;
-                const double2 dd = __ldg(reinterpret_cast<const double2 *>(a.defl) + p);
-                const double dl = sqrt(dd.x * dd.x + dd.y * dd.y);
-                double x = nx, y = ny, z = nz;
-                if (dl > 0.0) {
-                    double sd, cd;
-                    sincos(dl, &sd, &cd);
-                    const double k = sd / dl;
-                    // e_theta = (z cos phi, z sin phi, -s), e_phi = (-sin phi, cos phi, 0)
-                    const double tx = dd.x * nz * cp - dd.y * sp;
-                    const double ty = dd.x * nz * sp + dd.y * cp;
-                    const double tz = -dd.x * rg.s;
-                    x = cd * nx + k * tx;
-                    y = cd * ny + k * ty;
-                    z = cd * nz + k * tz;
-                }
-                const double s = sqrt(x * x + y * y);
-                P.x = x;
-                P.y = y;
-                P.z = z;
-                P.s = s;
-                if (s > 1e-12) {
-                    P.cph = x / s;
-                    P.sph = y / s;
-                } else {
-                    P.cph = 1.0;
-                    P.sph = 0.0;
-                    P.flags |= FLINTS_ST_POLE;
-                }
-                P.ic = ring_above(N, z);
-            }
-            sm.pts[lane] = P;
-        }
-        __syncwarp();
-
-        // ------------------------------------------------ phase B: per point
-        for (int q = 0; q < 32; ++q) {
-            const int64_t p = tile * 32 + q;
-            if (p >= a.count) break;
-            const PointA P = sm.pts[q];
-            int flags = P.flags;
-            // rings of the search disc, one per lane
-            int cnt = 0;
-            {
-                RingRec rec{};
-                const int64_t i = P.ic - R_rings + lane;
-                if (lane < 2 * R_rings + 2 && i >= 1 && i <= 4 * N - 1) {
-                    const Ring rg = ring_of(N, i);
-                    const double dz = P.z - rg.z, ds = P.s - rg.s;
-                    const double lb = dz * dz + ds * ds;
-                    if (lb <= a.r2) {
-                        const double den = 4.0 * P.s * rg.s;
-                        const double qv = den > 0.0 ? (a.r2 - lb) / den : 2.0;
-                        int j0 = 0, c = rg.n_in;
-                        if (qv < 1.0) {
-                            const double half = 2.0 * asin(sqrt(qv));
-                            const double phi = atan2(P.sph, P.cph);
-                            const double step = (double)rg.n_in / (2.0 * PI);  // pixels per radian
-                            const double lo = (phi - half) * step - rg.f;
-                            const double hi = (phi + half) * step - rg.f;
-                            const int64_t jl = (int64_t)floor(lo), jh = (int64_t)ceil(hi);
-                            const int64_t cc = jh - jl + 1;
-                            if (cc < rg.n_in) {
-                                c = (int)cc;
-                                int64_t m = jl % rg.n_in;
-                                if (m < 0) m += rg.n_in;
-                                j0 = (int)m;
-                            }
-                        }
-                        rec.z = rg.z;
-                        rec.s = rg.s;
-                        rec.f = rg.f;
-                        rec.first = rg.first;
-                        rec.n_in = rg.n_in;
-                        rec.nq = rg.nq;
-                        rec.j0 = j0;
-                        rec.cnt = c;
-                        cnt = c;
-                    }
-                }
-                // inclusive scan of counts
-                int incl = cnt;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int v = __shfl_up_sync(FULL, incl, o);
-                    if (lane >= o) incl += v;
-                }
-                rec.end = incl;
-                sm.u.cand.rings[lane] = rec;
-                cnt = __shfl_sync(FULL, incl, 31);  // total candidates
-            }
-            const int C = cnt;
-            __syncwarp();
-            bool fail = false;
-            if (C > NSLOT || C < K) {
-                fail = true;
-                flags |= FLINTS_ST_WINDOW | FLINTS_ST_FAILED;
-            }
-            unsigned long long key[SPL];
-            unsigned id[SPL];
-            if (!fail) {
-#pragma unroll
-                for (int s = 0; s < SPL; ++s) {
-                    const int c = s * 32 + lane;
-                    key[s] = 0x7ff0000000000000ull;  // +inf
-                    id[s] = 0xffffffffu;
-                    if (c < C) {
-                        // ring holding candidate c: first r with end > c
-                        int lo = 0, hi = 31;
-                        while (lo < hi) {
-                            const int mid = (lo + hi) >> 1;
-                            if (sm.u.cand.rings[mid].end > c) hi = mid;
-                            else lo = mid + 1;
-                        }
-                        const RingRec &rr = sm.u.cand.rings[lo];
-                        const int k = c - (rr.end - rr.cnt);
-                        const int w = rr.j0 + rr.cnt - rr.n_in;  // wrapped count
-                        const int jj = (w > 0) ? (k < w ? k : rr.j0 + (k - w)) : rr.j0 + k;
-                        double sp, cp;
-                        sincospi(((double)jj + rr.f) / (2.0 * (double)rr.nq), &sp, &cp);
-                        const double cx = rr.s * cp, cy = rr.s * sp, cz = rr.z;
-                        const double ex = P.x - cx, ey = P.y - cy, ez = P.z - cz;
-                        const double kk = ex * ex + ey * ey + ez * ez;
-                        sm.u.cand.cx[c] = cx;
-                        sm.u.cand.cy[c] = cy;
-                        sm.u.cand.cz[c] = cz;
-                        sm.u.cand.cc[c] = cp;
-                        sm.u.cand.cs[c] = sp;
-                        sm.u.cand.cpix[c] = (uint32_t)(rr.first + jj);
-                        key[s] = (unsigned long long)__double_as_longlong(kk);
-                        id[s] = (unsigned)c;
-                    }
-                }
-                bitonic_sort<SPL>(key, id, lane);
-                // K-th neighbour inside the disc?
-                const unsigned long long kK = __shfl_sync(FULL, key[(K - 1) >> 5], (K - 1) & 31);
-                if (__longlong_as_double((long long)kK) > a.r2) {
-                    fail = true;
-                    flags |= FLINTS_ST_WINDOW | FLINTS_ST_FAILED;
-                }
-            }
-            __syncwarp();
-            double keyd[RPL], yre[RPL], yim[RPL];
-            uint32_t pixr[RPL];
-            if (!fail) {
-#pragma unroll
-                for (int r = 0; r < RPL; ++r) {
-                    const int i = lane + 32 * r;
-                    keyd[r] = 0.0;
-                    yre[r] = 0.0;
-                    yim[r] = 0.0;
-                    pixr[r] = 0;
-                    if (i < K) {
-                        const unsigned c = id[r];
-                        keyd[r] = __longlong_as_double((long long)key[r]);
-                        const double cx = sm.u.cand.cx[c], cy = sm.u.cand.cy[c], cz = sm.u.cand.cz[c];
-                        sm.ox[i] = cx - P.x;
-                        sm.oy[i] = cy - P.y;
-                        sm.oz[i] = cz - P.z;
-                        sm.nz[i] = cz;
-                        sm.ns[i] = sqrt(cx * cx + cy * cy);
-                        sm.nc[i] = sm.u.cand.cc[c];
-                        sm.nsn[i] = sm.u.cand.cs[c];
-                        pixr[r] = sm.u.cand.cpix[c];
-                        if (MIXED) {
-                            sm.gx[i] = df_from(sm.ox[i]);
-                            sm.gy[i] = df_from(sm.oy[i]);
-                            sm.gz[i] = df_from(sm.oz[i]);
-                            sm.gnz[i] = df_from(cz);
-                            sm.gns[i] = df_from(sm.ns[i]);
-                            sm.gnc[i] = df_from(sm.nc[i]);
-                            sm.gnsn[i] = df_from(sm.nsn[i]);
-                        }
-                    }
-                }
-            }
-            __syncwarp();
-            if (a.stencil) {
-                if (!fail) {
-#pragma unroll
-                    for (int r = 0; r < RPL; ++r) {
-                        const int i = lane + 32 * r;
-                        if (i < K) a.stencil[p * K + i] = (int64_t)pixr[r];
-                    }
-                } else {
-                    for (int i = lane; i < K; i += 32) a.stencil[p * K + i] = -1;
-                }
-                if (lane == 0) {
-                    if (a.status) a.status[p] = (uint8_t)flags;
-                    if (flags & FLINTS_ST_WINDOW) ++cnt_win;
-                    if (flags & FLINTS_ST_FAILED) ++cnt_fail;
-                }
-                continue;
-            }
-            double vre = __longlong_as_double(0x7ff8000000000000ll), vim = vre, vrel = vre;
-            if (!fail) {
-#pragma unroll
-                for (int r = 0; r < RPL; ++r) {
-                    const int i = lane + 32 * r;
-                    if (i < K) {
-                        if (SPIN == 0) {
-                            yre[r] = __ldg(a.map + pixr[r]);
-                        } else {
-                            const double2 v = __ldg(reinterpret_cast<const double2 *>(a.map) + pixr[r]);
-                            yre[r] = v.x;
-                            yim[r] = v.y;
-                        }
-                    }
-                }
-                bool solved = false;
-                if (MIXED) {
-                    SMf &smf = *reinterpret_cast<SMf *>(wbase);
-                    solved = solve_point<K, SPIN, df>(smf, P, lane, NUGGET_EPS, a.tab, keyd, yre, yim, vre, vim,
-                                                      vrel);
-                    if (!solved) flags |= FLINTS_ST_FALLBACK;
-                    __syncwarp();
-                }
-                double nug = NUGGET_EPS;
-                for (int step = 0; !solved && step <= MAX_NUGGET_STEPS; ++step) {
-                    if (step > 0) {
-                        nug *= 2.0;
-                        flags |= FLINTS_ST_NUGGET;
-                    }
-                    solved = solve_point<K, SPIN, double>(sm, P, lane, nug, a.tab, keyd, yre, yim, vre, vim, vrel);
-                    __syncwarp();
-                }
-                if (!solved) {
-                    flags |= FLINTS_ST_FAILED;
-                    vre = vim = vrel = __longlong_as_double(0x7ff8000000000000ll);
-                }
-            }
-            if (lane == 0) {
-                if (SPIN == 0) {
-                    a.out[p] = vre;
-                } else {
-                    reinterpret_cast<double2 *>(a.out)[p] = make_double2(vre, vim);
-                }
-                if (a.var) a.var[p] = a.xi0 * vrel;
-                if (a.status) a.status[p] = (uint8_t)flags;
-                if (flags & FLINTS_ST_NUGGET) ++cnt_nug;
-                if (flags & FLINTS_ST_FALLBACK) ++cnt_fb;
-                if (flags & FLINTS_ST_WINDOW) ++cnt_win;
-                if (flags & FLINTS_ST_FAILED) ++cnt_fail;
-            }
-            __syncwarp();
-        }
+__device__ __forceinline__ void flush_counters(Counters &cnt, unsigned long long *dst, int lane) {
+    if (lane == 0 && dst) {
+        if (cnt.nug) atomicAdd(dst + CNT_NUGGET, cnt.nug);
+        if (cnt.fb) atomicAdd(dst + CNT_FALLBACK, cnt.fb);
+        if (cnt.win) atomicAdd(dst + CNT_WINDOW, cnt.win);
+        if (cnt.fail) atomicAdd(dst + CNT_FAILED, cnt.fail);
     }
-    if (lane == 0 && a.counters) {
-        if (cnt_nug) atomicAdd(a.counters + CNT_NUGGET, cnt_nug);
-        if (cnt_fb) atomicAdd(a.counters + CNT_FALLBACK, cnt_fb);
-        if (cnt_win) atomicAdd(a.counters + CNT_WINDOW, cnt_win);
-        if (cnt_fail) atomicAdd(a.counters + CNT_FAILED, cnt_fail);
-    }
+    cnt = Counters{};
 }
 
 template <int K, int SPIN, int MIXED>
@@ -715,22 +447,307 @@ constexpr size_t warp_smem_bytes() {
     return (WS + 15) / 16 * 16;
 }
 
-template <int K, int SPIN, int MIXED, int WPB>
-cudaError_t launch_one(const LensArgs &a, int R_rings, int num_sms, cudaStream_t st) {
-    const size_t smem = (size_t)WPB * warp_smem_bytes<K, SPIN, MIXED>();
-    auto kern = lens_kernel<K, SPIN, MIXED, WPB>;
+// One tile of `tile_pts` (<= 32) consecutive targets of a launch, processed by
+// one warp whose shared-memory slice starts at `wbase`.
+template <int K, int SPIN, int MIXED>
+__device__ __forceinline__ void process_tile(const LensArgs &a, int R_rings, int64_t tile, int tile_pts,
+                                          unsigned char *wbase, int lane, Counters &ctr) {
+    using SMd = WarpSmem<K, SPIN, double>;
+    using SMf = WarpSmem<K, SPIN, df>;
+    constexpr int SPL = Shape<K>::SPL, RPL = Shape<K>::RPL, NSLOT = Shape<K>::NSLOT;
+    SMd &sm = *reinterpret_cast<SMd *>(wbase);
+    const int64_t N = a.nside;
+    // ------------------------------------------------ phase A: displace
+    {
+        const int64_t p = tile * tile_pts + lane;
+        PointA P{};
+        if (lane < tile_pts && p < a.count) {
+            const int64_t pix = a.first + p;
+            int64_t ring, jj;
+            pix_ring(N, pix, ring, jj);
+            const Ring rg = ring_of(N, ring);
+            double sp, cp;
+            sincospi(((double)jj + rg.f) / (2.0 * (double)rg.nq), &sp, &cp);
+            const double nx = rg.s * cp, ny = rg.s * sp, nz = rg.z;
+            const double2 dd = __ldg(reinterpret_cast<const double2 *>(a.defl) + p);
+            const double dl = sqrt(dd.x * dd.x + dd.y * dd.y);
+            double x = nx, y = ny, z = nz;
+            if (dl > 0.0) {
+                double sd, cd;
+                sincos(dl, &sd, &cd);
+                const double k = sd / dl;
+                // e_theta = (z cos phi, z sin phi, -s), e_phi = (-sin phi, cos phi, 0)
+                const double tx = dd.x * nz * cp - dd.y * sp;
+                const double ty = dd.x * nz * sp + dd.y * cp;
+                const double tz = -dd.x * rg.s;
+                x = cd * nx + k * tx;
+                y = cd * ny + k * ty;
+                z = cd * nz + k * tz;
+            }
+            const double s = sqrt(x * x + y * y);
+            P.x = x;
+            P.y = y;
+            P.z = z;
+            P.s = s;
+            if (s > 1e-12) {
+                P.cph = x / s;
+                P.sph = y / s;
+            } else {
+                P.cph = 1.0;
+                P.sph = 0.0;
+                P.flags |= FLINTS_ST_POLE;
+            }
+            P.ic = ring_above(N, z);
+        }
+        sm.pts[lane] = P;
+    }
+    __syncwarp();
+
+    // ------------------------------------------------ phase B: per point
+    for (int q = 0; q < tile_pts; ++q) {
+        const int64_t p = tile * tile_pts + q;
+        if (p >= a.count) break;
+        const PointA P = sm.pts[q];
+        int flags = P.flags;
+        // rings of the search disc, one per lane
+        int cnt = 0;
+        {
+            RingRec rec{};
+            const int64_t i = P.ic - R_rings + lane;
+            if (lane < 2 * R_rings + 2 && i >= 1 && i <= 4 * N - 1) {
+                const Ring rg = ring_of(N, i);
+                const double dz = P.z - rg.z, ds = P.s - rg.s;
+                const double lb = dz * dz + ds * ds;
+                if (lb <= a.r2) {
+                    const double den = 4.0 * P.s * rg.s;
+                    const double qv = den > 0.0 ? (a.r2 - lb) / den : 2.0;
+                    int j0 = 0, c = rg.n_in;
+                    if (qv < 1.0) {
+                        const double half = 2.0 * asin(sqrt(qv));
+                        const double phi = atan2(P.sph, P.cph);
+                        const double step = (double)rg.n_in / (2.0 * PI);  // pixels per radian
+                        const double lo = (phi - half) * step - rg.f;
+                        const double hi = (phi + half) * step - rg.f;
+                        const int64_t jl = (int64_t)floor(lo), jh = (int64_t)ceil(hi);
+                        const int64_t cc = jh - jl + 1;
+                        if (cc < rg.n_in) {
+                            c = (int)cc;
+                            int64_t m = jl % rg.n_in;
+                            if (m < 0) m += rg.n_in;
+                            j0 = (int)m;
+                        }
+                    }
+                    rec.z = rg.z;
+                    rec.s = rg.s;
+                    rec.f = rg.f;
+                    rec.first = rg.first;
+                    rec.n_in = rg.n_in;
+                    rec.nq = rg.nq;
+                    rec.j0 = j0;
+                    rec.cnt = c;
+                    cnt = c;
+                }
+            }
+            // inclusive scan of counts
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += v;
+            }
+            rec.end = incl;
+            sm.u.cand.rings[lane] = rec;
+            cnt = __shfl_sync(FULL, incl, 31);  // total candidates
+        }
+        const int C = cnt;
+        __syncwarp();
+        bool fail = false;
+        if (C > NSLOT || C < K) {
+            fail = true;
+            flags |= FLINTS_ST_WINDOW | FLINTS_ST_FAILED;
+        }
+        unsigned long long key[SPL];
+        unsigned id[SPL];
+        if (!fail) {
+#pragma unroll
+            for (int s = 0; s < SPL; ++s) {
+                const int c = s * 32 + lane;
+                key[s] = 0x7ff0000000000000ull;  // +inf
+                id[s] = 0xffffffffu;
+                if (c < C) {
+                    // ring holding candidate c: first r with end > c
+                    int lo = 0, hi = 31;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (sm.u.cand.rings[mid].end > c) hi = mid;
+                        else lo = mid + 1;
+                    }
+                    const RingRec &rr = sm.u.cand.rings[lo];
+                    const int k = c - (rr.end - rr.cnt);
+                    const int w = rr.j0 + rr.cnt - rr.n_in;  // wrapped count
+                    const int jj = (w > 0) ? (k < w ? k : rr.j0 + (k - w)) : rr.j0 + k;
+                    double sp, cp;
+                    sincospi(((double)jj + rr.f) / (2.0 * (double)rr.nq), &sp, &cp);
+                    const double cx = rr.s * cp, cy = rr.s * sp, cz = rr.z;
+                    const double ex = P.x - cx, ey = P.y - cy, ez = P.z - cz;
+                    const double kk = ex * ex + ey * ey + ez * ez;
+                    sm.u.cand.cx[c] = cx;
+                    sm.u.cand.cy[c] = cy;
+                    sm.u.cand.cz[c] = cz;
+                    sm.u.cand.cc[c] = cp;
+                    sm.u.cand.cs[c] = sp;
+                    sm.u.cand.cpix[c] = (uint32_t)(rr.first + jj);
+                    key[s] = (unsigned long long)__double_as_longlong(kk);
+                    id[s] = (unsigned)c;
+                }
+            }
+            bitonic_sort<SPL>(key, id, lane);
+            // K-th neighbour inside the disc?
+            const unsigned long long kK = __shfl_sync(FULL, key[(K - 1) >> 5], (K - 1) & 31);
+            if (__longlong_as_double((long long)kK) > a.r2) {
+                fail = true;
+                flags |= FLINTS_ST_WINDOW | FLINTS_ST_FAILED;
+            }
+        }
+        __syncwarp();
+        double keyd[RPL], yre[RPL], yim[RPL];
+        uint32_t pixr[RPL];
+        if (!fail) {
+#pragma unroll
+            for (int r = 0; r < RPL; ++r) {
+                const int i = lane + 32 * r;
+                keyd[r] = 0.0;
+                yre[r] = 0.0;
+                yim[r] = 0.0;
+                pixr[r] = 0;
+                if (i < K) {
+                    const unsigned c = id[r];
+                    keyd[r] = __longlong_as_double((long long)key[r]);
+                    const double cx = sm.u.cand.cx[c], cy = sm.u.cand.cy[c], cz = sm.u.cand.cz[c];
+                    sm.ox[i] = cx - P.x;
+                    sm.oy[i] = cy - P.y;
+                    sm.oz[i] = cz - P.z;
+                    sm.nz[i] = cz;
+                    sm.ns[i] = sqrt(cx * cx + cy * cy);
+                    sm.nc[i] = sm.u.cand.cc[c];
+                    sm.nsn[i] = sm.u.cand.cs[c];
+                    pixr[r] = sm.u.cand.cpix[c];
+                    if (MIXED) {
+                        sm.gx[i] = df_from(sm.ox[i]);
+                        sm.gy[i] = df_from(sm.oy[i]);
+                        sm.gz[i] = df_from(sm.oz[i]);
+                        sm.gnz[i] = df_from(cz);
+                        sm.gns[i] = df_from(sm.ns[i]);
+                        sm.gnc[i] = df_from(sm.nc[i]);
+                        sm.gnsn[i] = df_from(sm.nsn[i]);
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        if (a.stencil) {
+            if (!fail) {
+#pragma unroll
+                for (int r = 0; r < RPL; ++r) {
+                    const int i = lane + 32 * r;
+                    if (i < K) a.stencil[p * K + i] = (int64_t)pixr[r];
+                }
+            } else {
+                for (int i = lane; i < K; i += 32) a.stencil[p * K + i] = -1;
+            }
+            if (lane == 0) {
+                if (a.status) a.status[p] = (uint8_t)flags;
+                if (flags & FLINTS_ST_WINDOW) ++ctr.win;
+                if (flags & FLINTS_ST_FAILED) ++ctr.fail;
+            }
+            continue;
+        }
+        double vre = __longlong_as_double(0x7ff8000000000000ll), vim = vre, vrel = vre;
+        if (!fail) {
+#pragma unroll
+            for (int r = 0; r < RPL; ++r) {
+                const int i = lane + 32 * r;
+                if (i < K) {
+                    if (SPIN == 0) {
+                        yre[r] = __ldg(a.map + pixr[r]);
+                    } else {
+                        const double2 v = __ldg(reinterpret_cast<const double2 *>(a.map) + pixr[r]);
+                        yre[r] = v.x;
+                        yim[r] = v.y;
+                    }
+                }
+            }
+            bool solved = false;
+            if (MIXED) {
+                SMf &smf = *reinterpret_cast<SMf *>(wbase);
+                solved = solve_point<K, SPIN, df>(smf, P, lane, NUGGET_EPS, a.tab, keyd, yre, yim, vre, vim,
+                                                  vrel);
+                if (!solved) flags |= FLINTS_ST_FALLBACK;
+                __syncwarp();
+            }
+            double nug = NUGGET_EPS;
+            for (int step = 0; !solved && step <= MAX_NUGGET_STEPS; ++step) {
+                if (step > 0) {
+                    nug *= 2.0;
+                    flags |= FLINTS_ST_NUGGET;
+                }
+                solved = solve_point<K, SPIN, double>(sm, P, lane, nug, a.tab, keyd, yre, yim, vre, vim, vrel);
+                __syncwarp();
+            }
+            if (!solved) {
+                flags |= FLINTS_ST_FAILED;
+                vre = vim = vrel = __longlong_as_double(0x7ff8000000000000ll);
+            }
+        }
+        if (lane == 0) {
+            if (SPIN == 0) {
+                a.out[p] = vre;
+            } else {
+                reinterpret_cast<double2 *>(a.out)[p] = make_double2(vre, vim);
+            }
+            if (a.var) a.var[p] = a.xi0 * vrel;
+            if (a.status) a.status[p] = (uint8_t)flags;
+            if (flags & FLINTS_ST_NUGGET) ++ctr.nug;
+            if (flags & FLINTS_ST_FALLBACK) ++ctr.fb;
+            if (flags & FLINTS_ST_WINDOW) ++ctr.win;
+            if (flags & FLINTS_ST_FAILED) ++ctr.fail;
+        }
+        __syncwarp();
+    }
+}
+
+// Single-launch kernel: warps stride over the tiles of one target range.
+template <int K, int SPIN, int MIXED>
+__global__ void __launch_bounds__(256, 2) lens_kernel(LensArgs a, int R_rings, int tile_pts) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    unsigned char *wbase = smem_raw + (size_t)warp * warp_smem_bytes<K, SPIN, MIXED>();
+    const int64_t ntiles = (a.count + tile_pts - 1) / tile_pts;
+    Counters ctr;
+    for (int64_t tile = (int64_t)blockIdx.x * wpb + warp; tile < ntiles; tile += (int64_t)gridDim.x * wpb)
+        process_tile<K, SPIN, MIXED>(a, R_rings, tile, tile_pts, wbase, lane, ctr);
+    flush_counters(ctr, a.counters, lane);
+}
+
+template <int K, int SPIN, int MIXED>
+cudaError_t launch_one(const LensArgs &a, int R_rings, const LaunchCfg &cfg, int num_sms, cudaStream_t st) {
+    const int wpb = cfg.warps_per_block > 0 ? cfg.warps_per_block : 4;
+    const int tile_pts = cfg.tile_points > 0 ? cfg.tile_points : 32;
+    const size_t smem = (size_t)wpb * warp_smem_bytes<K, SPIN, MIXED>();
+    auto kern = lens_kernel<K, SPIN, MIXED>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WPB * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, wpb * 32, smem);
     if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-    const int64_t ntiles = (a.count + 31) / 32;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    if (cfg.blocks_per_sm > 0 && cfg.blocks_per_sm < per_sm) per_sm = cfg.blocks_per_sm;
+    const int64_t ntiles = (a.count + tile_pts - 1) / tile_pts;
     int64_t blocks = (int64_t)num_sms * per_sm;
-    const int64_t need = (ntiles + WPB - 1) / WPB;
+    const int64_t need = (ntiles + wpb - 1) / wpb;
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
-    kern<<<(unsigned)blocks, WPB * 32, smem, st>>>(a, R_rings);
+    kern<<<(unsigned)blocks, wpb * 32, smem, st>>>(a, R_rings, tile_pts);
     return cudaGetLastError();
 }
 

@@ -3,18 +3,19 @@
 
 namespace flints {
 
-cudaError_t launch_lens_spin0(int K, int precision, const LensArgs &a, int R_rings, cudaStream_t st) {
+cudaError_t launch_lens_spin0(int K, int precision, const LensArgs &a, int R_rings, const LaunchCfg &cfg,
+                              cudaStream_t st) {
     const int sms = device_sm_count();
     const bool mixed = precision == FLINTS_MIXED;
     switch (K) {
         case 16:
-            return mixed ? launch_one<16, 0, 1, 4>(a, R_rings, sms, st) : launch_one<16, 0, 0, 4>(a, R_rings, sms, st);
+            return mixed ? launch_one<16, 0, 1>(a, R_rings, cfg, sms, st) : launch_one<16, 0, 0>(a, R_rings, cfg, sms, st);
         case 24:
-            return mixed ? launch_one<24, 0, 1, 4>(a, R_rings, sms, st) : launch_one<24, 0, 0, 4>(a, R_rings, sms, st);
+            return mixed ? launch_one<24, 0, 1>(a, R_rings, cfg, sms, st) : launch_one<24, 0, 0>(a, R_rings, cfg, sms, st);
         case 32:
-            return mixed ? launch_one<32, 0, 1, 4>(a, R_rings, sms, st) : launch_one<32, 0, 0, 4>(a, R_rings, sms, st);
+            return mixed ? launch_one<32, 0, 1>(a, R_rings, cfg, sms, st) : launch_one<32, 0, 0>(a, R_rings, cfg, sms, st);
         case 48:
-            return mixed ? launch_one<48, 0, 1, 4>(a, R_rings, sms, st) : launch_one<48, 0, 0, 4>(a, R_rings, sms, st);
+            return mixed ? launch_one<48, 0, 1>(a, R_rings, cfg, sms, st) : launch_one<48, 0, 0>(a, R_rings, cfg, sms, st);
         default:
             return cudaErrorInvalidValue;
     }

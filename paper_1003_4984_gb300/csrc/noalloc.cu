@@ -183,7 +183,7 @@ extern "C" int flints_lens_noalloc(int64_t nside, int lmax, const double *cl, co
     a.xi0 = xi0;
     a.r2 = r * r;
     a.counters = d_cnt;
-    NA_CK(launch_lens(spin, K, precision, a, R_rings, st), "lens kernel launch");
+    NA_CK(launch_lens(spin, K, precision, a, R_rings, LaunchCfg{0, 0, 0}, st), "lens kernel launch");
 #undef NA_CK
     return FLINTS_OK;
 }
