@@ -1,0 +1,220 @@
+"""Continuous-batching lensing server on one GPU.
+
+Requests (a contiguous RING target range of a resident map, with its spin,
+stencil size K and deflections) are admitted while their device buffers fit
+in an HBM budget, then advanced chunk by chunk: every scheduling round builds
+a batch of chunks taken round-robin from all admitted requests (new arrivals
+join the next round while earlier requests are still running) and runs it as
+one persistent batched launch.  Two batch objects on two streams keep one
+batch executing while the next is staged, so work from different requests
+overlaps on the device.  Maps and plans (xi tables) stay resident between
+requests.  Completion is detected on the host with CUDA events; there is no
+device-side waiting.
+
+Results do not depend on how requests are mixed: each target is computed by
+the same per-point code from the same inputs whatever batch carries it.
+"""
+from __future__ import annotations
+
+import collections
+import time
+from dataclasses import dataclass, field
+
+from .api import Batch, LaunchCfg, Plan
+
+
+@dataclass
+class Request:
+    rid: int
+    map_key: tuple            # (nside, spin) of a registered map
+    K: int
+    first: int
+    count: int
+    defl: object              # device tensor (count, 2), or a callable producing it at admission
+    arrival: float = 0.0      # seconds from the start of the run
+    precision: str = "mixed"
+    # filled in by the server
+    out: object = None
+    var: object = None
+    done_points: int = 0
+    next_point: int = 0
+    admitted_at: float | None = None
+    finished_at: float | None = None
+    nbytes: int = 0
+
+    @property
+    def latency(self) -> float | None:
+        return None if self.finished_at is None else self.finished_at - self.arrival
+
+
+@dataclass
+class _InFlight:
+    event: object
+    chunks: list = field(default_factory=list)  # (request, n_points)
+
+
+class LensServer:
+    def __init__(self, hbm_budget: float = 150e9, batch_points: int = 1 << 22, chunk_points: int = 1 << 21,
+                 max_jobs: int = 64, cfg: LaunchCfg | None = None, device: int = 0):
+        import torch
+
+        self.torch = torch
+        self.dev = torch.device("cuda", device)
+        self.budget = float(hbm_budget)
+        self.batch_points = int(batch_points)
+        self.chunk_points = int(chunk_points)
+        self.max_jobs = int(max_jobs)
+        self.cfg = cfg
+        self.maps: dict = {}
+        self.spectra: dict = {}
+        self.plans: dict = {}
+        self.in_use = 0
+        self.pending: collections.deque = collections.deque()
+        self.active: list = []
+        self.finished: list = []
+        self.streams = [torch.cuda.Stream(self.dev), torch.cuda.Stream(self.dev)]
+        self.batches = [Batch(max_jobs), Batch(max_jobs)]
+        self.inflight: list = [None, None]
+        self.turn = 0
+        self.launches = 0
+
+    # ------------------------------------------------------------ residency
+    def register_map(self, nside: int, spin: int, tensor, cl, cl_bb=None):
+        """Keep an unlensed map and its spectrum resident on the device."""
+        self.maps[(nside, spin)] = tensor
+        self.spectra[(nside, spin)] = (cl, cl_bb)
+
+    def plan_for(self, req: Request) -> Plan:
+        key = (*req.map_key, req.K, req.precision)
+        if key not in self.plans:
+            cl, bb = self.spectra[req.map_key]
+            nside, spin = req.map_key
+            self.plans[key] = Plan(nside, cl, bb, spin=spin, K=req.K, precision=req.precision)
+            if self.cfg is not None:
+                self.plans[key].set_launch(self.cfg)
+        return self.plans[key]
+
+    @staticmethod
+    def request_bytes(req: Request) -> int:
+        spin = req.map_key[1]
+        return req.count * (16 + (8 if spin == 0 else 16) + 8)
+
+    # ------------------------------------------------------------ admission
+    def submit(self, req: Request):
+        self.pending.append(req)
+
+    def _admit(self, now: float):
+        torch = self.torch
+        while self.pending:
+            req = self.pending[0]
+            nb = self.request_bytes(req)
+            if self.in_use + nb > self.budget and self.active:
+                break  # wait for memory to free up (an oversized request runs alone)
+            self.pending.popleft()
+            spin = req.map_key[1]
+            if callable(req.defl):
+                req.defl = req.defl()
+            req.out = torch.empty((req.count,) if spin == 0 else (req.count, 2), dtype=torch.float64,
+                                  device=self.dev)
+            req.var = torch.empty(req.count, dtype=torch.float64, device=self.dev)
+            req.nbytes = nb
+            req.admitted_at = now
+            self.in_use += nb
+            self.plan_for(req)
+            self.active.append(req)
+
+    # ------------------------------------------------------------ scheduling
+    def _build_jobs(self):
+        jobs, chunks, budget = [], [], self.batch_points
+        progressed = True
+        while budget > 0 and len(jobs) < self.max_jobs and progressed:
+            progressed = False
+            for req in self.active:
+                if budget <= 0 or len(jobs) >= self.max_jobs:
+                    break
+                left = req.count - req.next_point
+                if left <= 0:
+                    continue
+                n = min(left, self.chunk_points, budget)
+                a = req.next_point
+                jobs.append((self.plan_for(req), req.first + a, n, self.maps[req.map_key], req.defl[a:a + n],
+                             req.out[a:a + n], req.var[a:a + n], None))
+                chunks.append((req, n))
+                req.next_point += n
+                budget -= n
+                progressed = True
+        return jobs, chunks
+
+    def _launch(self, slot: int):
+        jobs, chunks = self._build_jobs()
+        if not jobs:
+            return False
+        b, s = self.batches[slot], self.streams[slot]
+        b.stage(jobs, self.cfg.tile_points if self.cfg else 0)
+        b.launch(self.cfg, stream=s)
+        ev = self.torch.cuda.Event()
+        ev.record(s)
+        self.inflight[slot] = _InFlight(ev, chunks)
+        self.launches += 1
+        return True
+
+    def _retire(self, slot: int, now_fn):
+        f = self.inflight[slot]
+        if f is None or not f.event.query():
+            return False
+        now = now_fn()
+        for req, n in f.chunks:
+            req.done_points += n
+            if req.done_points == req.count:
+                req.finished_at = now
+                self.active.remove(req)
+                self.in_use -= req.nbytes
+                self.finished.append(req)
+        self.inflight[slot] = None
+        return True
+
+    # ------------------------------------------------------------ main loop
+    def run(self, requests, time_scale: float = 1.0, idle_sleep: float = 2e-4):
+        """Serve ``requests`` (sorted by arrival time, seconds) in real time.
+
+        Returns the finished requests; latency = completion - arrival."""
+        t0 = time.perf_counter()
+
+        def now():
+            return (time.perf_counter() - t0) / time_scale
+
+        todo = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        while todo or self.pending or self.active or any(self.inflight):
+            t = now()
+            while todo and todo[0].arrival <= t:
+                self.submit(todo.popleft())
+            self._admit(t)
+            busy = False
+            for slot in (0, 1):
+                busy |= self._retire(slot, now)
+            for _ in range(2):
+                slot = self.turn
+                if self.inflight[slot] is None:
+                    if self._launch(slot):
+                        busy = True
+                    self.turn ^= 1
+            if not busy:
+                time.sleep(idle_sleep)
+        return self.finished
+
+    def close(self):
+        for b in self.batches:
+            b.close()
+        for p in self.plans.values():
+            p.close()
+
+
+def latency_stats(finished) -> dict:
+    import numpy as np
+
+    lat = np.array([r.latency for r in finished]) * 1e3
+    pts = sum(r.count for r in finished)
+    span = max(r.finished_at for r in finished) - min(r.arrival for r in finished)
+    return {"requests": len(finished), "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()), "max_ms": float(lat.max()),
+            "points": int(pts), "points_per_s": pts / span, "span_s": span}
