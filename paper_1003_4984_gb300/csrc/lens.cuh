@@ -40,7 +40,7 @@ struct Shape {
 };
 
 struct PointA {
-    double x, y, z, s, cph, sph;
+    double x, y, z, s, cph, sph, phi;
     int64_t ic;
     int flags;
     int pad;
@@ -49,7 +49,10 @@ struct PointA {
 struct RingRec {
     double z, s, f;
     int64_t first;
-    int n_in, nq, j0, cnt, end, pad;
+    int n_in, nq, j0, cnt, end, jref;
+    // FP32 pre-selection key of pixel j of this ring:
+    //   a32 + b32 sin^2(pi (j - jref + frac) / n_in)
+    float a32, b32, frac, inv_n;
 };
 
 template <int K, int SPIN, class R>
@@ -125,6 +128,36 @@ __device__ __forceinline__ void bitonic_sort(unsigned long long (&key)[SPL], uns
     }
 }
 
+// Ascending bitonic sort of 32*SPL packed 64-bit keys; element e = s*32 + lane.
+template <int SPL>
+__device__ __forceinline__ void bitonic_sort_packed(unsigned long long (&key)[SPL], int lane) {
+    constexpr int N = 32 * SPL;
+#pragma unroll
+    for (int k = 2; k <= N; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+            for (int s = 0; s < SPL; ++s) {
+                const int e = s * 32 + lane;
+                const bool up = (e & k) == 0;
+                if (j >= 32) {
+                    const int ps = s ^ (j >> 5);
+                    if (ps > s) {
+                        const unsigned long long lo = key[s] < key[ps] ? key[s] : key[ps];
+                        const unsigned long long hi = key[s] < key[ps] ? key[ps] : key[s];
+                        key[s] = up ? lo : hi;
+                        key[ps] = up ? hi : lo;
+                    }
+                } else {
+                    const unsigned long long pk = __shfl_xor_sync(FULL, key[s], j);
+                    const bool keep_min = (((lane & j) == 0) == up);
+                    key[s] = keep_min ? (pk < key[s] ? pk : key[s]) : (pk > key[s] ? pk : key[s]);
+                }
+            }
+        }
+    }
+}
+
 template <class R>
 __device__ __forceinline__ typename Ops<R>::T table_eval(const TableDev &tab, typename Ops<R>::T t);
 
@@ -185,12 +218,14 @@ __device__ __forceinline__ Cx<typename Ops<R>::T> pair_phase(typename Ops<R>::T 
     const T h2 = O::add(O::mul(dx, cj), O::mul(dy, snj));
     const T A2 = O::sub(O::mul(zj, h2), O::mul(sj, dz));
     const T B2 = O::sub(O::mul(dy, cj), O::mul(dx, snj));
-    const T A1s = O::mul(A1, A1), B1s = O::mul(B1, B1), A2s = O::mul(A2, A2), B2s = O::mul(B2, B2);
-    const T re1 = O::sub(A1s, B1s), im1 = O::mul(O::add(A1, A1), B1);
-    const T re2 = O::sub(A2s, B2s), im2 = O::neg(O::mul(O::add(A2, A2), B2));
-    const T nre = O::sub(O::mul(re1, re2), O::mul(im1, im2));
-    const T nim = O::add(O::mul(re1, im2), O::mul(im1, re2));
-    const T den = O::mul(O::add(A1s, B1s), O::add(A2s, B2s));
+    // exp(2i a_ij) conj(exp(2i a_ji)) = q^2 / |q|^2 with q = (A1 + i B1)(A2 - i B2)
+    const T qr = O::add(O::mul(A1, A2), O::mul(B1, B2));
+    const T qi = O::sub(O::mul(B1, A2), O::mul(A1, B2));
+    const T qr2 = O::mul(qr, qr), qi2 = O::mul(qi, qi);
+    const T nre = O::sub(qr2, qi2);
+    const T qri = O::mul(qr, qi);
+    const T nim = O::add(qri, qri);
+    const T den = O::add(qr2, qi2);
     if (!O::positive(den)) return {O::from(1.0), O::zero()};  // coincident points: no rotation
     const T inv = O::rcp(den);
     return {O::mul(nre, inv), O::mul(nim, inv)};
@@ -331,24 +366,32 @@ __device__ bool solve_point(SM &sm, const PointA &P, int lane, double nugget, co
             const Elem *Lr = mat + tri<K>(rr, 0);
             if constexpr (SPIN == 0) {
                 typename O::Acc acc = O::acc((part == 0 && act) ? Lr[j] : O::zero());
-                if (act)
-                    for (int k = part; k < j; k += s) O::sub_prod(acc, Lr[k], Lj[k]);
-                T v = O::val(acc);
+                typename O::Acc acc2 = O::acc(O::zero());
+                if (act) {
+                    int k = part;
+                    for (; k + s < j; k += 2 * s) {  // two independent chains
+                        O::sub_prod(acc, Lr[k], Lj[k]);
+                        O::sub_prod(acc2, Lr[k + s], Lj[k + s]);
+                    }
+                    if (k < j) O::sub_prod(acc, Lr[k], Lj[k]);
+                }
+                T v = O::add(O::val(acc), O::val(acc2));
                 for (int o = 1; o < s; o <<= 1) v = O::add(v, O::shfl_xor(v, o));
                 srow[t] = v;
             } else {
                 const Elem a0 = Lr[j];
                 typename O::Acc ar = O::acc((part == 0 && act) ? a0.re : O::zero());
                 typename O::Acc ai = O::acc((part == 0 && act) ? a0.im : O::zero());
+                typename O::Acc br = O::acc(O::zero()), bi = O::acc(O::zero());
                 if (act)
-                    for (int k = part; k < j; k += s) {
+                    for (int k = part; k < j; k += s) {  // real and imaginary parts in two chains each
                         const Elem a = Lr[k], b = Lj[k];
                         O::sub_prod(ar, a.re, b.re);
-                        O::sub_prod(ar, a.im, b.im);
+                        O::sub_prod(br, a.im, b.im);
                         O::sub_prod(ai, a.im, b.re);
-                        O::add_prod(ai, a.re, b.im);
+                        O::add_prod(bi, a.re, b.im);
                     }
-                T vr = O::val(ar), vi = O::val(ai);
+                T vr = O::add(O::val(ar), O::val(br)), vi = O::add(O::val(ai), O::val(bi));
                 for (int o = 1; o < s; o <<= 1) {
                     vr = O::add(vr, O::shfl_xor(vr, o));
                     vi = O::add(vi, O::shfl_xor(vi, o));
@@ -497,6 +540,7 @@ __device__ __forceinline__ void process_tile(const LensArgs &a, int R_rings, int
                 P.sph = 0.0;
                 P.flags |= FLINTS_ST_POLE;
             }
+            P.phi = atan2(y, x);
             P.ic = ring_above(N, z);
         }
         sm.pts[lane] = P;
@@ -522,12 +566,11 @@ __device__ __forceinline__ void process_tile(const LensArgs &a, int R_rings, int
                     const double den = 4.0 * P.s * rg.s;
                     const double qv = den > 0.0 ? (a.r2 - lb) / den : 2.0;
                     int j0 = 0, c = rg.n_in;
+                    const double step = (double)rg.n_in / (2.0 * PI);  // pixels per radian
                     if (qv < 1.0) {
                         const double half = 2.0 * asin(sqrt(qv));
-                        const double phi = atan2(P.sph, P.cph);
-                        const double step = (double)rg.n_in / (2.0 * PI);  // pixels per radian
-                        const double lo = (phi - half) * step - rg.f;
-                        const double hi = (phi + half) * step - rg.f;
+                        const double lo = (P.phi - half) * step - rg.f;
+                        const double hi = (P.phi + half) * step - rg.f;
                         const int64_t jl = (int64_t)floor(lo), jh = (int64_t)ceil(hi);
                         const int64_t cc = jh - jl + 1;
                         if (cc < rg.n_in) {
@@ -537,6 +580,17 @@ __device__ __forceinline__ void process_tile(const LensArgs &a, int R_rings, int
                             j0 = (int)m;
                         }
                     }
+                    // FP32 key terms: chord^2 = dz^2 + ds^2 + 4 s' s sin^2(dphi/2) with
+                    // dphi/2 = pi (j + f - u') / n_in, u' = phi' n_in / (2 pi)
+                    const double u = P.phi * step;
+                    double jr = floor(u - rg.f + 0.5);
+                    rec.frac = (float)((jr + rg.f) - u);
+                    int64_t jri = (int64_t)jr % rg.n_in;
+                    if (jri < 0) jri += rg.n_in;
+                    rec.jref = (int)jri;
+                    rec.a32 = (float)lb;
+                    rec.b32 = (float)den;
+                    rec.inv_n = 1.0f / (float)rg.n_in;
                     rec.z = rg.z;
                     rec.s = rg.s;
                     rec.f = rg.f;
@@ -566,17 +620,19 @@ __device__ __forceinline__ void process_tile(const LensArgs &a, int R_rings, int
             fail = true;
             flags |= FLINTS_ST_WINDOW | FLINTS_ST_FAILED;
         }
-        unsigned long long key[SPL];
-        unsigned id[SPL];
+        // selected neighbours: FP64 key bits and candidate id per owned row
+        unsigned long long key[RPL];
+        unsigned id[RPL];
         if (!fail) {
+            // 1. FP32 keys of all candidates, packed with the candidate id (ids follow
+            //    the RING index, so equal keys order by pixel), one sort
+            unsigned long long pk[SPL];
 #pragma unroll
             for (int s = 0; s < SPL; ++s) {
                 const int c = s * 32 + lane;
-                key[s] = 0x7ff0000000000000ull;  // +inf
-                id[s] = 0xffffffffu;
+                pk[s] = ~0ull;
                 if (c < C) {
-                    // ring holding candidate c: first r with end > c
-                    int lo = 0, hi = 31;
+                    int lo = 0, hi = 31;  // ring holding candidate c: first r with end > c
                     while (lo < hi) {
                         const int mid = (lo + hi) >> 1;
                         if (sm.u.cand.rings[mid].end > c) hi = mid;
@@ -586,22 +642,72 @@ __device__ __forceinline__ void process_tile(const LensArgs &a, int R_rings, int
                     const int k = c - (rr.end - rr.cnt);
                     const int w = rr.j0 + rr.cnt - rr.n_in;  // wrapped count
                     const int jj = (w > 0) ? (k < w ? k : rr.j0 + (k - w)) : rr.j0 + k;
-                    double sp, cp;
-                    sincospi(((double)jj + rr.f) / (2.0 * (double)rr.nq), &sp, &cp);
-                    const double cx = rr.s * cp, cy = rr.s * sp, cz = rr.z;
-                    const double ex = P.x - cx, ey = P.y - cy, ez = P.z - cz;
-                    const double kk = ex * ex + ey * ey + ez * ez;
-                    sm.u.cand.cx[c] = cx;
-                    sm.u.cand.cy[c] = cy;
-                    sm.u.cand.cz[c] = cz;
-                    sm.u.cand.cc[c] = cp;
-                    sm.u.cand.cs[c] = sp;
-                    sm.u.cand.cpix[c] = (uint32_t)(rr.first + jj);
-                    key[s] = (unsigned long long)__double_as_longlong(kk);
-                    id[s] = (unsigned)c;
+                    int dj = jj - rr.jref;
+                    if (dj > rr.n_in / 2) dj -= rr.n_in;
+                    if (dj < -(rr.n_in / 2)) dj += rr.n_in;
+                    const float sn = sinpif(((float)dj + rr.frac) * rr.inv_n);
+                    const float k32 = fmaf(rr.b32, sn * sn, rr.a32);
+                    sm.u.cand.cpix[c] = ((uint32_t)lo << 24) | (uint32_t)jj;
+                    pk[s] = ((unsigned long long)__float_as_uint(fmaxf(k32, 0.0f)) << 32) | (unsigned)c;
                 }
             }
-            bitonic_sort<SPL>(key, id, lane);
+            bitonic_sort_packed<SPL>(pk, lane);
+            // 2. exact set unless the K-th and (K+1)-th FP32 keys are within 2^-16
+            const unsigned long long ka = __shfl_sync(FULL, pk[(K - 1) >> 5], (K - 1) & 31);
+            const unsigned long long kb = __shfl_sync(FULL, pk[K >> 5], K & 31);
+            const float fa = __uint_as_float((unsigned)(ka >> 32)), fb = __uint_as_float((unsigned)(kb >> 32));
+            const bool exact = (C == K) || (fb - fa > fb * 1.52587890625e-05f);
+            __syncwarp();
+            // 3. FP64 positions and keys: of the K selected (fast) or of all candidates
+            auto place = [&](int c) -> unsigned long long {
+                const uint32_t pkd = sm.u.cand.cpix[c];
+                const RingRec &rr = sm.u.cand.rings[pkd >> 24];
+                const int jj = (int)(pkd & 0xffffffu);
+                double sp, cp;
+                sincospi(((double)jj + rr.f) / (2.0 * (double)rr.nq), &sp, &cp);
+                const double cx = rr.s * cp, cy = rr.s * sp, cz = rr.z;
+                const double ex = P.x - cx, ey = P.y - cy, ez = P.z - cz;
+                sm.u.cand.cx[c] = cx;
+                sm.u.cand.cy[c] = cy;
+                sm.u.cand.cz[c] = cz;
+                sm.u.cand.cc[c] = cp;
+                sm.u.cand.cs[c] = sp;
+                return (unsigned long long)__double_as_longlong(ex * ex + ey * ey + ez * ez);
+            };
+            if (exact) {
+#pragma unroll
+                for (int r = 0; r < RPL; ++r) {
+                    key[r] = 0x7ff0000000000000ull;
+                    id[r] = 0xffffffffu;
+                    if (lane + 32 * r < K) {
+                        const unsigned c = (unsigned)(pk[r] & 0xffffffffu);
+                        key[r] = place((int)c);
+                        id[r] = c;
+                    }
+                }
+                __syncwarp();
+                bitonic_sort<RPL>(key, id, lane);
+            } else {
+                unsigned long long k2[SPL];
+                unsigned i2[SPL];
+#pragma unroll
+                for (int s = 0; s < SPL; ++s) {
+                    const int c = s * 32 + lane;
+                    k2[s] = 0x7ff0000000000000ull;
+                    i2[s] = 0xffffffffu;
+                    if (c < C) {
+                        k2[s] = place(c);
+                        i2[s] = (unsigned)c;
+                    }
+                }
+                __syncwarp();
+                bitonic_sort<SPL>(k2, i2, lane);
+#pragma unroll
+                for (int r = 0; r < RPL; ++r) {
+                    key[r] = k2[r];
+                    id[r] = i2[r];
+                }
+            }
             // K-th neighbour inside the disc?
             const unsigned long long kK = __shfl_sync(FULL, key[(K - 1) >> 5], (K - 1) & 31);
             if (__longlong_as_double((long long)kK) > a.r2) {
@@ -631,7 +737,10 @@ __device__ __forceinline__ void process_tile(const LensArgs &a, int R_rings, int
                     sm.ns[i] = sqrt(cx * cx + cy * cy);
                     sm.nc[i] = sm.u.cand.cc[c];
                     sm.nsn[i] = sm.u.cand.cs[c];
-                    pixr[r] = sm.u.cand.cpix[c];
+                    {
+                        const uint32_t pkd = sm.u.cand.cpix[c];
+                        pixr[r] = (uint32_t)(sm.u.cand.rings[pkd >> 24].first + (pkd & 0xffffffu));
+                    }
                     if (MIXED) {
                         sm.gx[i] = df_from(sm.ox[i]);
                         sm.gy[i] = df_from(sm.oy[i]);
