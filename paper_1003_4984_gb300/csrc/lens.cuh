@@ -66,6 +66,11 @@ struct WarpSmem {
     double ox[K], oy[K], oz[K];          // neighbour offsets X_i - n' (FP64)
     double nz[K], ns[K], nc[K], nsn[K];  // neighbour z, sin(theta), cos(phi), sin(phi)
     df gx[K], gy[K], gz[K], gnz[K], gns[K], gnc[K], gnsn[K];  // the same in double-float
+    // spin 2: per-neighbour target phase Phi0_i = phase(n' -> X_i), tangent-plane
+    // coordinates (u, v) of X_i - n' at n', and squared chords to n'
+    typename Ops<R>::T p0r[K], p0i[K], pu[K], pv[K];
+    double kt[K];
+    float ktf[K];
     union U {
         struct Cand {
             RingRec rings[32];
@@ -198,6 +203,13 @@ __device__ __forceinline__ df table_eval<df>(const TableDev &tab, df t) {
     return p;
 }
 
+template <class R>
+__device__ __forceinline__ Cx<typename Ops<R>::T> pair_phase_uv(
+    typename Ops<R>::T dx, typename Ops<R>::T dy, typename Ops<R>::T dz, typename Ops<R>::T zi,
+    typename Ops<R>::T si, typename Ops<R>::T ci, typename Ops<R>::T sni, typename Ops<R>::T zj,
+    typename Ops<R>::T sj, typename Ops<R>::T cj, typename Ops<R>::T snj, typename Ops<R>::T &u_out,
+    typename Ops<R>::T &v_out);
+
 // exp(2i(a_ij - a_ji)) for the pair (i -> j) with d = X_j - X_i, from the
 // projections of d on the local bases at both ends: with e_theta = (z cos phi,
 // z sin phi, -s) and e_phi = (-sin phi, cos phi, 0),
@@ -210,11 +222,24 @@ __device__ __forceinline__ Cx<typename Ops<R>::T> pair_phase(typename Ops<R>::T 
                                                              typename Ops<R>::T sni, typename Ops<R>::T zj,
                                                              typename Ops<R>::T sj, typename Ops<R>::T cj,
                                                              typename Ops<R>::T snj) {
+    typename Ops<R>::T u_dummy, v_dummy;
+    return pair_phase_uv<R>(dx, dy, dz, zi, si, ci, sni, zj, sj, cj, snj, u_dummy, v_dummy);
+}
+
+// As pair_phase, also returning the projections (A1, B1) of d on e_theta, e_phi at i.
+template <class R>
+__device__ __forceinline__ Cx<typename Ops<R>::T> pair_phase_uv(
+    typename Ops<R>::T dx, typename Ops<R>::T dy, typename Ops<R>::T dz, typename Ops<R>::T zi,
+    typename Ops<R>::T si, typename Ops<R>::T ci, typename Ops<R>::T sni, typename Ops<R>::T zj,
+    typename Ops<R>::T sj, typename Ops<R>::T cj, typename Ops<R>::T snj, typename Ops<R>::T &u_out,
+    typename Ops<R>::T &v_out) {
     using O = Ops<R>;
     using T = typename O::T;
     const T h1 = O::add(O::mul(dx, ci), O::mul(dy, sni));
     const T A1 = O::sub(O::mul(zi, h1), O::mul(si, dz));
     const T B1 = O::sub(O::mul(dy, ci), O::mul(dx, sni));
+    u_out = A1;
+    v_out = B1;
     const T h2 = O::add(O::mul(dx, cj), O::mul(dy, snj));
     const T A2 = O::sub(O::mul(zj, h2), O::mul(sj, dz));
     const T B2 = O::sub(O::mul(dy, cj), O::mul(dx, snj));
@@ -261,7 +286,55 @@ __device__ __forceinline__ Cx<typename Ops<R>::T> cx_conj(Cx<typename Ops<R>::T>
     return {a.re, Ops<R>::neg(a.im)};
 }
 
+// Pair phase through the target (spin 2): with Phi0_i = phase(n' -> X_i),
+//   phase(X_i -> X_j) = conj(Phi0_i) Phi0_j exp(-2iE_ij),
+// E_ij the spherical excess of the triangle (n', X_i, X_j), tan(E/2) = x =
+// (u_i v_j - v_i u_j) / (4 - (t_i + t_j + t_ij)/2) (Van Oosterom-Strackee, with
+// (u, v) the tangent-plane coordinates at n' and t the squared chords), and
+// exp(-2iE) = (1 - ix)^4 / (1 + x^2)^2, i.e. 1 + delta with
+//   delta = (-8x^2 - 4ix(1 - x^2)) / (1 + x^2)^2.
+// E is of order |X_i - n'||X_j - n'|, so delta is a small correction: FP64 on
+// the FP64 path, FP32 on the mixed path.
+struct Holo {
+    double dr, di;
+};
+__device__ __forceinline__ Holo holonomy64(double ui, double vi, double uj, double vj, double ti, double tj,
+                                           double tij) {
+    const double x = (ui * vj - vi * uj) / (4.0 - 0.5 * (ti + tj + tij));
+    const double x2 = x * x;
+    const double w = 1.0 / (1.0 + x2);
+    const double q = w * w;
+    return {-8.0 * x2 * q, -4.0 * x * (1.0 - x2) * q};
+}
+struct Holo32 {
+    float dr, di;
+};
+__device__ __forceinline__ Holo32 holonomy32(float ui, float vi, float uj, float vj, float ti, float tj, float tij) {
+    const float x = (ui * vj - vi * uj) / (4.0f - 0.5f * (ti + tj + tij));
+    const float x2 = x * x;
+    const float w = 1.0f / (1.0f + x2);
+    const float q = w * w;
+    return {-8.0f * x2 * q, -4.0f * x * (1.0f - x2) * q};
+}
+__device__ __forceinline__ df df_addf(df a, float c) {
+    const df s = two_sum(a.hi, c);
+    return quick_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+
+// conj(a) b (1 + delta), delta from holonomy64 / holonomy32
+__device__ __forceinline__ Cx<double> transported_phase(Cx<double> a, Cx<double> b, const Holo &h) {
+    const double br = fma(a.re, b.re, a.im * b.im), bi = fma(a.re, b.im, -a.im * b.re);
+    return {fma(br, h.dr, fma(-bi, h.di, br)), fma(br, h.di, fma(bi, h.dr, bi))};
+}
+__device__ __forceinline__ Cx<df> transported_phase(Cx<df> a, Cx<df> b, const Holo32 &h) {
+    const df br = df_add(df_mul(a.re, b.re), df_mul(a.im, b.im));
+    const df bi = df_sub(df_mul(a.re, b.im), df_mul(a.im, b.re));
+    const float cr = br.hi * h.dr - bi.hi * h.di, ci = br.hi * h.di + bi.hi * h.dr;
+    return {df_addf(br, cr), df_addf(bi, ci)};
+}
+
 // Returns false when a pivot of S + nugget I is not positive.
+
 //
 // Factorisation: left-looking Cholesky of the matrix bordered by the two
 // right-hand-side rows (row K holds c (spin 2: c0 = <P(n') P_i^*>), row K+1
@@ -282,6 +355,25 @@ __device__ bool solve_point(SM &sm, const PointA &P, int lane, double nugget, co
     constexpr int NROW = K + 2;
     using Elem = typename SM::Elem;
     Elem *mat = sm.u.mat;
+
+    // ---- spin 2: per-neighbour target phases and tangent coordinates
+    if constexpr (SPIN == 2) {
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+            const int i = lane + 32 * r;
+            if (i < K) {
+                T u, v;
+                const Cx<T> ph = pair_phase_uv<R>(G::x(sm, i), G::y(sm, i), G::z(sm, i), O::from(P.z), O::from(P.s),
+                                                  O::from(P.cph), O::from(P.sph), G::nz(sm, i), G::ns(sm, i),
+                                                  G::nc(sm, i), G::nsn(sm, i), u, v);
+                sm.p0r[i] = ph.re;
+                sm.p0i[i] = ph.im;
+                sm.pu[i] = u;
+                sm.pv[i] = v;
+            }
+        }
+        __syncwarp();
+    }
 
     // ---- assembly of the lower triangle
     {
@@ -308,9 +400,16 @@ __device__ bool solve_point(SM &sm, const PointA &P, int lane, double nugget, co
                 if constexpr (SPIN == 0) {
                     e = fv;
                 } else {
-                    const Cx<T> ph = pair_phase<R>(dx, dy, dz, G::nz(sm, i), G::ns(sm, i), G::nc(sm, i),
-                                                   G::nsn(sm, i), G::nz(sm, j), G::ns(sm, j), G::nc(sm, j),
-                                                   G::nsn(sm, j));
+                    Cx<T> ph;
+                    if constexpr (std::is_same<R, double>::value) {
+                        const Holo hol = holonomy64(sm.pu[i], sm.pv[i], sm.pu[j], sm.pv[j], sm.kt[i], sm.kt[j], t);
+                        ph = transported_phase(Cx<double>{sm.p0r[i], sm.p0i[i]}, Cx<double>{sm.p0r[j], sm.p0i[j]},
+                                               hol);
+                    } else {
+                        const Holo32 hol = holonomy32(sm.pu[i].hi, sm.pv[i].hi, sm.pu[j].hi, sm.pv[j].hi, sm.ktf[i],
+                                                      sm.ktf[j], t.hi);
+                        ph = transported_phase(Cx<df>{sm.p0r[i], sm.p0i[i]}, Cx<df>{sm.p0r[j], sm.p0i[j]}, hol);
+                    }
                     e.re = O::mul(fv, ph.re);
                     e.im = O::mul(fv, ph.im);
                 }
@@ -333,10 +432,8 @@ __device__ bool solve_point(SM &sm, const PointA &P, int lane, double nugget, co
                 mat[tri<K>(K, i)] = fv;
                 mat[tri<K>(K + 1, i)] = O::from(yre[r]);
             } else {
-                // target -> neighbour: d = X_i - n', phase at n' and at X_i
-                const Cx<T> ph = pair_phase<R>(G::x(sm, i), G::y(sm, i), G::z(sm, i), O::from(P.z), O::from(P.s),
-                                               O::from(P.cph), O::from(P.sph), G::nz(sm, i), G::ns(sm, i),
-                                               G::nc(sm, i), G::nsn(sm, i));
+                // target -> neighbour phase from the prologue
+                const Cx<T> ph{sm.p0r[i], sm.p0i[i]};
                 Elem c0, yc;
                 c0.re = O::mul(fv, ph.re);
                 c0.im = O::mul(fv, ph.im);
@@ -729,6 +826,8 @@ __device__ __forceinline__ void process_tile(const LensArgs &a, int R_rings, int
                 if (i < K) {
                     const unsigned c = id[r];
                     keyd[r] = __longlong_as_double((long long)key[r]);
+                    sm.kt[i] = keyd[r];
+                    sm.ktf[i] = (float)keyd[r];
                     const double cx = sm.u.cand.cx[c], cy = sm.u.cand.cy[c], cz = sm.u.cand.cz[c];
                     sm.ox[i] = cx - P.x;
                     sm.oy[i] = cy - P.y;

@@ -237,3 +237,22 @@ def test_spin2_error_statistics_match_predicted_variance():
     assert 0.85 < np.mean(r) < 1.15  # E|P - P_hat|^2 = sigma^2 for a circular Gaussian
     rel = np.sqrt(np.mean(np.abs(res.value - truth) ** 2) / np.mean(np.abs(truth) ** 2))
     assert rel < 0.2
+
+
+def test_spin2_pair_phase_factorises_through_the_target():
+    # The pair phase equals conj(phase(n', a)) phase(n', b) exp(-2iE), E the spherical excess
+    # of the triangle (n', a, b): tan(E/2) = n'.(a x b) / (1 + n'.a + a.b + b.n')
+    # (Van Oosterom-Strackee).  The CUDA path assembles spin-2 covariances this way.
+    n = RNG.normal(size=(500, 3))
+    n /= np.linalg.norm(n, axis=1)[:, None]
+    for scale in (1e-3, 3e-2, 0.3):
+        a = n + RNG.normal(size=(500, 3)) * scale
+        a /= np.linalg.norm(a, axis=1)[:, None]
+        b = n + RNG.normal(size=(500, 3)) * scale
+        b /= np.linalg.norm(b, axis=1)[:, None]
+        triple = np.einsum("pi,pi->p", n, np.cross(a, b))
+        den = 1 + np.sum(n * a, 1) + np.sum(a * b, 1) + np.sum(b * n, 1)
+        x = triple / den
+        g = (1 - 1j * x) ** 4 / (1 + x * x) ** 2  # exp(-2iE) with E = 2 atan(x)
+        got = np.conj(kr.pair_phase(n, a)) * kr.pair_phase(n, b) * g
+        np.testing.assert_allclose(got, kr.pair_phase(a, b), atol=1e-12)
