@@ -138,7 +138,8 @@ int flints_stencil(flints_plan_t plan, int64_t first, int64_t count,
                    void *stream);
 
 /* Launch shape of a plan's lens launches (the autotuner's knobs).
- *   warps_per_block 1..8 (0: 4), blocks_per_sm cap (0: as many as fit),
+ *   warps_per_block 1..8 (0: 4; lowered to what fits in shared memory),
+ *   blocks_per_sm cap (0: as many as fit),
  *   tile_points targets per warp tile 1..32 (0: 32).  cfg NULL restores the
  *   defaults.  Results do not depend on the launch shape. */
 typedef struct {

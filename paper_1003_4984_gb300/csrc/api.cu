@@ -11,6 +11,7 @@
 
 namespace flints {
 cudaError_t batch_prepare_p0(int wpb, int *max_blocks_per_sm);
+int batch_max_wpb();
 cudaError_t batch_prepare_p1(int wpb, int *max_blocks_per_sm);
 cudaError_t batch_launch_p0(const BatchHeader *hdr, const BatchJob *jobs, unsigned long long *next_tile, int wpb,
                             int blocks, cudaStream_t st);
@@ -26,6 +27,14 @@ int device_sm_count() {
     if (cudaGetDevice(&dev) != cudaSuccess) return 1;
     if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) return 1;
     return n;
+}
+
+size_t device_smem_optin() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 48 * 1024;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || n < 1)
+        return 48 * 1024;
+    return (size_t)n;
 }
 
 cudaError_t launch_lens(int spin, int K, int precision, const LensArgs &a, int R_rings, const LaunchCfg &cfg,
@@ -298,6 +307,7 @@ struct flints_batch_s {
     unsigned char *d_buf;     // device: header, jobs, two work-queue counters
     unsigned char *h_buf;     // pinned host staging of header and jobs
     int wpb[2], max_bps[2];   // prepared launch shape per precision class
+    int max_wpb;              // warps per block that fit in the opt-in shared memory
 };
 
 static BatchHeader *hdr_of(unsigned char *p) { return reinterpret_cast<BatchHeader *>(p); }
@@ -332,6 +342,7 @@ int flints_batch_create(flints_batch_t *out, int max_jobs) {
         return cuda_fail(e, "flints_batch_create: allocation");
     }
     std::memset(b->h_buf, 0, b->table_bytes);
+    b->max_wpb = batch_max_wpb();
     for (int cls = 0; cls < 2; ++cls) {
         if (int rc = batch_prepare(b, cls, 4)) {
             cudaFree(b->d_buf);
@@ -433,8 +444,9 @@ int flints_batch_launch(flints_batch_t b, const flints_launch_cfg *cfg, void *st
     int cur = -1;
     cudaGetDevice(&cur);
     if (cur != b->device) return fail(FLINTS_EINVAL, "batch was created on device %d, current device is %d", b->device, cur);
-    const int wpb = (cfg && cfg->warps_per_block > 0) ? cfg->warps_per_block : 4;
+    int wpb = (cfg && cfg->warps_per_block > 0) ? cfg->warps_per_block : 4;
     if (wpb > 8) return fail(FLINTS_EINVAL, "flints_batch_launch: warps_per_block 1..8");
+    if (wpb > b->max_wpb) wpb = b->max_wpb;  // a hint: keep the block within shared memory
     cudaStream_t st = (cudaStream_t)stream;
     const BatchHeader *h = hdr_of(b->h_buf);
     const size_t bytes = sizeof(BatchHeader) + sizeof(BatchJob) * (size_t)(h->njobs[0] + h->njobs[1]);

@@ -291,5 +291,6 @@ cudaError_t launch_xi_table(int spin, int lmax, const double *cl_dev, const doub
 cudaError_t finish_table(double *f, double *g, int n, double h, double xi0, Coef64 *c64, float4 *c32,
                          cudaStream_t st);
 int device_sm_count();
+size_t device_smem_optin();
 
 }  // namespace flints

@@ -939,8 +939,11 @@ __global__ void __launch_bounds__(256, 2) lens_kernel(LensArgs a, int R_rings, i
 
 template <int K, int SPIN, int MIXED>
 cudaError_t launch_one(const LensArgs &a, int R_rings, const LaunchCfg &cfg, int num_sms, cudaStream_t st) {
-    const int wpb = cfg.warps_per_block > 0 ? cfg.warps_per_block : 4;
+    int wpb = cfg.warps_per_block > 0 ? cfg.warps_per_block : 4;
     const int tile_pts = cfg.tile_points > 0 ? cfg.tile_points : 32;
+    // the launch shape is a hint: keep the block within the opt-in shared memory
+    const int fit = (int)(device_smem_optin() / warp_smem_bytes<K, SPIN, MIXED>());
+    if (wpb > fit) wpb = fit > 0 ? fit : 1;
     const size_t smem = (size_t)wpb * warp_smem_bytes<K, SPIN, MIXED>();
     auto kern = lens_kernel<K, SPIN, MIXED>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
