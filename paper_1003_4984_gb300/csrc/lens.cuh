@@ -293,19 +293,9 @@ __device__ __forceinline__ Cx<typename Ops<R>::T> cx_conj(Cx<typename Ops<R>::T>
 // (u, v) the tangent-plane coordinates at n' and t the squared chords), and
 // exp(-2iE) = (1 - ix)^4 / (1 + x^2)^2, i.e. 1 + delta with
 //   delta = (-8x^2 - 4ix(1 - x^2)) / (1 + x^2)^2.
-// E is of order |X_i - n'||X_j - n'|, so delta is a small correction: FP64 on
-// the FP64 path, FP32 on the mixed path.
-struct Holo {
-    double dr, di;
-};
-__device__ __forceinline__ Holo holonomy64(double ui, double vi, double uj, double vj, double ti, double tj,
-                                           double tij) {
-    const double x = (ui * vj - vi * uj) / (4.0 - 0.5 * (ti + tj + tij));
-    const double x2 = x * x;
-    const double w = 1.0 / (1.0 + x2);
-    const double q = w * w;
-    return {-8.0 * x2 * q, -4.0 * x * (1.0 - x2) * q};
-}
+// E is of order |X_i - n'||X_j - n'|, so delta is a small correction computed
+// in FP32 (the double-float path; the FP64 path uses the direct vector form,
+// cheaper in FP64 than the divisions below).
 struct Holo32 {
     float dr, di;
 };
@@ -321,11 +311,7 @@ __device__ __forceinline__ df df_addf(df a, float c) {
     return quick_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
 }
 
-// conj(a) b (1 + delta), delta from holonomy64 / holonomy32
-__device__ __forceinline__ Cx<double> transported_phase(Cx<double> a, Cx<double> b, const Holo &h) {
-    const double br = fma(a.re, b.re, a.im * b.im), bi = fma(a.re, b.im, -a.im * b.re);
-    return {fma(br, h.dr, fma(-bi, h.di, br)), fma(br, h.di, fma(bi, h.dr, bi))};
-}
+// conj(a) b (1 + delta), delta from holonomy32
 __device__ __forceinline__ Cx<df> transported_phase(Cx<df> a, Cx<df> b, const Holo32 &h) {
     const df br = df_add(df_mul(a.re, b.re), df_mul(a.im, b.im));
     const df bi = df_sub(df_mul(a.re, b.im), df_mul(a.im, b.re));
@@ -402,9 +388,9 @@ __device__ bool solve_point(SM &sm, const PointA &P, int lane, double nugget, co
                 } else {
                     Cx<T> ph;
                     if constexpr (std::is_same<R, double>::value) {
-                        const Holo hol = holonomy64(sm.pu[i], sm.pv[i], sm.pu[j], sm.pv[j], sm.kt[i], sm.kt[j], t);
-                        ph = transported_phase(Cx<double>{sm.p0r[i], sm.p0i[i]}, Cx<double>{sm.p0r[j], sm.p0i[j]},
-                                               hol);
+                        // FP64: the direct vector form is cheaper than the transported form's divisions
+                        ph = pair_phase<R>(dx, dy, dz, G::nz(sm, i), G::ns(sm, i), G::nc(sm, i), G::nsn(sm, i),
+                                           G::nz(sm, j), G::ns(sm, j), G::nc(sm, j), G::nsn(sm, j));
                     } else {
                         const Holo32 hol = holonomy32(sm.pu[i].hi, sm.pv[i].hi, sm.pu[j].hi, sm.pv[j].hi, sm.ktf[i],
                                                       sm.ktf[j], t.hi);
