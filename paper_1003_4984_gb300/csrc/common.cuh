@@ -48,6 +48,13 @@ __device__ __forceinline__ df df_add(df a, df b) {
     e = __fadd_rn(s.lo, t.lo);
     return quick_two_sum(s.hi, e);
 }
+// Sum with an error of about 2^-44 relative to the larger operand (not to the
+// result): used where the operands are O(1) partial sums or all terms are
+// positive, so that no cancellation can magnify it.
+__device__ __forceinline__ df df_add_fast(df a, df b) {
+    const df s = two_sum(a.hi, b.hi);
+    return quick_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
 __device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
 __device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
 __device__ __forceinline__ df df_mul(df a, df b) {
@@ -124,6 +131,7 @@ struct Ops<double> {
     static __device__ __forceinline__ double to(T x) { return x; }
     static __device__ __forceinline__ T zero() { return 0.0; }
     static __device__ __forceinline__ T add(T a, T b) { return a + b; }
+    static __device__ __forceinline__ T add_fast(T a, T b) { return a + b; }
     static __device__ __forceinline__ T sub(T a, T b) { return a - b; }
     static __device__ __forceinline__ T mul(T a, T b) { return a * b; }
     static __device__ __forceinline__ T neg(T a) { return -a; }
@@ -146,6 +154,7 @@ struct Ops<df> {
     static __device__ __forceinline__ double to(T x) { return df_to(x); }
     static __device__ __forceinline__ T zero() { return {0.0f, 0.0f}; }
     static __device__ __forceinline__ T add(T a, T b) { return df_add(a, b); }
+    static __device__ __forceinline__ T add_fast(T a, T b) { return df_add_fast(a, b); }
     static __device__ __forceinline__ T sub(T a, T b) { return df_sub(a, b); }
     static __device__ __forceinline__ T mul(T a, T b) { return df_mul(a, b); }
     static __device__ __forceinline__ T neg(T a) { return df_neg(a); }
@@ -174,34 +183,40 @@ struct Ring {
     double f;  // phase offset: phi_j = (j + f) pi / (2 nq)
 };
 
-__device__ __forceinline__ Ring ring_of(int64_t N, int64_t i) {
+// inv3N = 1/(3 Nside), inv3N2 = 1/(3 Nside^2): multiplications replace the
+// divisions of the ring formulas (positions then differ from the correctly
+// rounded ones by at most a couple of ulps).
+__device__ __forceinline__ Ring ring_of(int64_t N, int64_t i, double inv3N, double inv3N2) {
     Ring r;
     const double Nd = (double)N;
     if (i < N) {
-        const double id = (double)i, t3 = 3.0 * Nd * Nd;
-        r.z = (t3 - id * id) / t3;
-        r.s = id * sqrt(6.0 * Nd * Nd - id * id) / t3;
+        const double id = (double)i;
+        r.z = 1.0 - id * id * inv3N2;
+        r.s = id * sqrt(6.0 * Nd * Nd - id * id) * inv3N2;
         r.first = 2 * i * (i - 1);
         r.nq = (int)i;
         r.f = 0.5;
     } else if (i <= 3 * N) {
         const double id = (double)i;
-        r.z = (4.0 * Nd - 2.0 * id) / (3.0 * Nd);
-        r.s = sqrt((2.0 * id - Nd) * (7.0 * Nd - 2.0 * id)) / (3.0 * Nd);
+        r.z = (4.0 * Nd - 2.0 * id) * inv3N;
+        r.s = sqrt((2.0 * id - Nd) * (7.0 * Nd - 2.0 * id)) * inv3N;
         r.first = 2 * N * (N - 1) + 4 * N * (i - N);
         r.nq = (int)N;
         r.f = ((i + N) & 1) ? 0.0 : 0.5;
     } else {
         const int64_t ip = 4 * N - i;
-        const double id = (double)ip, t3 = 3.0 * Nd * Nd;
-        r.z = -((t3 - id * id) / t3);
-        r.s = id * sqrt(6.0 * Nd * Nd - id * id) / t3;
+        const double id = (double)ip;
+        r.z = -(1.0 - id * id * inv3N2);
+        r.s = id * sqrt(6.0 * Nd * Nd - id * id) * inv3N2;
         r.first = 12 * N * N - 2 * ip * (ip + 1);
         r.nq = (int)ip;
         r.f = 0.5;
     }
     r.n_in = 4 * r.nq;
     return r;
+}
+__device__ __forceinline__ Ring ring_of(int64_t N, int64_t i) {
+    return ring_of(N, i, 1.0 / (3.0 * (double)N), 1.0 / (3.0 * (double)N * (double)N));
 }
 
 __device__ __forceinline__ int64_t cap_ring_of(int64_t p) {  // largest i with 2i(i-1) <= p

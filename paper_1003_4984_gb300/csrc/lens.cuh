@@ -43,7 +43,7 @@ struct PointA {
     double x, y, z, s, cph, sph, phi;
     int64_t ic;
     int flags;
-    int pad;
+    float zf, sf, phif;  // FP32 copies for the candidate-range arithmetic
 };
 
 struct RingRec {
@@ -381,7 +381,7 @@ __device__ bool solve_point(SM &sm, const PointA &P, int lane, double nugget, co
                 const T dx = O::sub(G::x(sm, j), G::x(sm, i));
                 const T dy = O::sub(G::y(sm, j), G::y(sm, i));
                 const T dz = O::sub(G::z(sm, j), G::z(sm, i));
-                const T t = O::add(O::add(O::mul(dx, dx), O::mul(dy, dy)), O::mul(dz, dz));
+                const T t = O::add_fast(O::add_fast(O::mul(dx, dx), O::mul(dy, dy)), O::mul(dz, dz));
                 const T fv = table_eval<R>(tab, t);
                 if constexpr (SPIN == 0) {
                     e = fv;
@@ -458,8 +458,8 @@ __device__ bool solve_point(SM &sm, const PointA &P, int lane, double nugget, co
                     }
                     if (k < j) O::sub_prod(acc, Lr[k], Lj[k]);
                 }
-                T v = O::add(O::val(acc), O::val(acc2));
-                for (int o = 1; o < s; o <<= 1) v = O::add(v, O::shfl_xor(v, o));
+                T v = O::add_fast(O::val(acc), O::val(acc2));
+                for (int o = 1; o < s; o <<= 1) v = O::add_fast(v, O::shfl_xor(v, o));
                 srow[t] = v;
             } else {
                 const Elem a0 = Lr[j];
@@ -474,10 +474,10 @@ __device__ bool solve_point(SM &sm, const PointA &P, int lane, double nugget, co
                         O::sub_prod(ai, a.im, b.re);
                         O::add_prod(bi, a.re, b.im);
                     }
-                T vr = O::add(O::val(ar), O::val(br)), vi = O::add(O::val(ai), O::val(bi));
+                T vr = O::add_fast(O::val(ar), O::val(br)), vi = O::add_fast(O::val(ai), O::val(bi));
                 for (int o = 1; o < s; o <<= 1) {
-                    vr = O::add(vr, O::shfl_xor(vr, o));
-                    vi = O::add(vi, O::shfl_xor(vi, o));
+                    vr = O::add_fast(vr, O::shfl_xor(vr, o));
+                    vi = O::add_fast(vi, O::shfl_xor(vi, o));
                 }
                 srow[t].re = vr;
                 srow[t].im = vi;
@@ -583,6 +583,7 @@ __device__ __forceinline__ void process_tile(const LensArgs &a, int R_rings, int
     constexpr int SPL = Shape<K>::SPL, RPL = Shape<K>::RPL, NSLOT = Shape<K>::NSLOT;
     SMd &sm = *reinterpret_cast<SMd *>(wbase);
     const int64_t N = a.nside;
+    const double inv3N = 1.0 / (3.0 * (double)N), inv3N2 = inv3N / (double)N;
     // ------------------------------------------------ phase A: displace
     {
         const int64_t p = tile * tile_pts + lane;
@@ -591,7 +592,7 @@ __device__ __forceinline__ void process_tile(const LensArgs &a, int R_rings, int
             const int64_t pix = a.first + p;
             int64_t ring, jj;
             pix_ring(N, pix, ring, jj);
-            const Ring rg = ring_of(N, ring);
+            const Ring rg = ring_of(N, ring, inv3N, inv3N2);
             double sp, cp;
             sincospi(((double)jj + rg.f) / (2.0 * (double)rg.nq), &sp, &cp);
             const double nx = rg.s * cp, ny = rg.s * sp, nz = rg.z;
@@ -624,6 +625,9 @@ __device__ __forceinline__ void process_tile(const LensArgs &a, int R_rings, int
                 P.flags |= FLINTS_ST_POLE;
             }
             P.phi = atan2(y, x);
+            P.zf = (float)z;
+            P.sf = (float)s;
+            P.phif = (float)P.phi;
             P.ic = ring_above(N, z);
         }
         sm.pts[lane] = P;
@@ -642,37 +646,45 @@ __device__ __forceinline__ void process_tile(const LensArgs &a, int R_rings, int
             RingRec rec{};
             const int64_t i = P.ic - R_rings + lane;
             if (lane < 2 * R_rings + 2 && i >= 1 && i <= 4 * N - 1) {
-                const Ring rg = ring_of(N, i);
-                const double dz = P.z - rg.z, ds = P.s - rg.s;
-                const double lb = dz * dz + ds * ds;
-                if (lb <= a.r2) {
-                    const double den = 4.0 * P.s * rg.s;
-                    const double qv = den > 0.0 ? (a.r2 - lb) / den : 2.0;
+                // exact ring latitude in FP64 (needed for the selected neighbours' positions);
+                // the candidate range and the FP32 key terms in FP32, with
+                // ds = s' - s_r = -dz (z' + z_r)/(s' + s_r), accurate to FP32 from FP64 dz
+                const Ring rg = ring_of(N, i, inv3N, inv3N2);
+                const double dz = P.z - rg.z;
+                const float dzf = (float)dz;
+                const float zrf = (float)rg.z, srf = (float)rg.s;
+                const float dsf = -dzf * ((P.zf + zrf) / (P.sf + srf));
+                const float lbf = fmaf(dzf, dzf, dsf * dsf);
+                const float r2f = (float)a.r2;
+                if (lbf <= r2f * 1.00001f) {
+                    const float den = 4.0f * P.sf * srf;
+                    const float qv = den > 0.0f ? (r2f * 1.00001f - lbf) / den : 2.0f;
                     int j0 = 0, c = rg.n_in;
-                    const double step = (double)rg.n_in / (2.0 * PI);  // pixels per radian
-                    if (qv < 1.0) {
-                        const double half = 2.0 * asin(sqrt(qv));
-                        const double lo = (P.phi - half) * step - rg.f;
-                        const double hi = (P.phi + half) * step - rg.f;
-                        const int64_t jl = (int64_t)floor(lo), jh = (int64_t)ceil(hi);
-                        const int64_t cc = jh - jl + 1;
+                    const float stepf = (float)rg.n_in * 0.15915494309189535f;  // pixels per radian
+                    if (qv < 1.0f) {
+                        const float half = 2.0f * asinf(sqrtf(fmaxf(qv, 0.0f)));
+                        const float lo = (P.phif - half) * stepf - (float)rg.f;
+                        const float hi = (P.phif + half) * stepf - (float)rg.f;
+                        // FP32 rounding moves lo and hi by < 0.02 pixel for Nside <= 16384
+                        const int jl = (int)floorf(lo - 0.03125f), jh = (int)ceilf(hi + 0.03125f);
+                        const int cc = jh - jl + 1;
                         if (cc < rg.n_in) {
-                            c = (int)cc;
-                            int64_t m = jl % rg.n_in;
+                            c = cc;
+                            int m = jl % rg.n_in;
                             if (m < 0) m += rg.n_in;
-                            j0 = (int)m;
+                            j0 = m;
                         }
                     }
                     // FP32 key terms: chord^2 = dz^2 + ds^2 + 4 s' s sin^2(dphi/2) with
-                    // dphi/2 = pi (j + f - u') / n_in, u' = phi' n_in / (2 pi)
-                    const double u = P.phi * step;
-                    double jr = floor(u - rg.f + 0.5);
+                    // dphi/2 = pi (j + f - u') / n_in, u' = phi' n_in / (2 pi) in FP64
+                    const double u = P.phi * ((double)rg.n_in * (0.5 / PI));
+                    const double jr = floor(u - rg.f + 0.5);
                     rec.frac = (float)((jr + rg.f) - u);
                     int64_t jri = (int64_t)jr % rg.n_in;
                     if (jri < 0) jri += rg.n_in;
                     rec.jref = (int)jri;
-                    rec.a32 = (float)lb;
-                    rec.b32 = (float)den;
+                    rec.a32 = lbf;
+                    rec.b32 = den;
                     rec.inv_n = 1.0f / (float)rg.n_in;
                     rec.z = rg.z;
                     rec.s = rg.s;
