@@ -348,7 +348,7 @@ def run_c4(args):
         plans.append(plan)
     points = sum(j[2] for j in jobs)
     batch = fl.Batch(len(jobs))
-    cfg = autotune.tune_batch(batch, jobs, cands=[fl.LaunchCfg(w, 0, t) for w in (2, 4, 8) for t in (16, 32)])
+    cfg = autotune.tune_batch(batch, jobs, cands=[fl.LaunchCfg(w, 0, t) for w in (2, 4, 8) for t in (8, 16)])
     batch.stage(jobs, cfg.tile_points)
     stream = torch.cuda.Stream(dev)
     batch.launch(cfg, stream=stream)

@@ -62,7 +62,11 @@ enum { FLINTS_FP64 = 0, FLINTS_MIXED = 1 };
 
 /* plan flags */
 enum {
-    FLINTS_NO_VARIANCE = 4u /* skip the variance output even if a buffer is given */
+    FLINTS_NO_VARIANCE = 4u, /* skip the variance output even if a buffer is given */
+    /* testing aid (mixed plans): every double-float solve is discarded and the
+     * point is re-solved by the FP64 fallback, so that path can be checked on
+     * well-conditioned inputs; results carry FLINTS_ST_FALLBACK */
+    FLINTS_FORCE_FALLBACK = 256u
 };
 
 /* per-point status bits */
@@ -140,7 +144,7 @@ int flints_stencil(flints_plan_t plan, int64_t first, int64_t count,
 /* Launch shape of a plan's lens launches (the autotuner's knobs).
  *   warps_per_block 1..8 (0: 4; lowered to what fits in shared memory),
  *   blocks_per_sm cap (0: as many as fit),
- *   tile_points targets per warp tile 1..32 (0: 32).  cfg NULL restores the
+ *   tile_points targets per warp tile 1..16 (0: 16).  cfg NULL restores the
  *   defaults.  Results do not depend on the launch shape. */
 typedef struct {
     int warps_per_block, blocks_per_sm, tile_points;
@@ -167,7 +171,7 @@ int flints_lens_batch(const flints_job *jobs, int n, void *stream);
  *     max_jobs jobs, plus pinned host staging (allocates; not capturable).
  *   flints_batch_stage: host-only: validate the jobs, order them by precision
  *     class and decreasing estimated cost, cut them into tiles of tile_points
- *     targets (0: 32), write the table into the pinned staging buffer.
+ *     targets (1..16; 0: 16), write the table into the pinned staging buffer.
  *   flints_batch_launch: upload the staged table, reset the work queues and
  *     launch the two persistent kernels (FP64 and mixed jobs) on `stream`:
  *     stream operations only, so it can be captured in a CUDA graph; a replay

@@ -22,7 +22,7 @@ _lock = threading.Lock()
 
 def candidates(max_warps: int = 8):
     out = []
-    for w, b, t in itertools.product((2, 4, 8), (0, 1, 2), (16, 32)):
+    for w, b, t in itertools.product((2, 4, 8), (0, 1, 2), (8, 16)):
         if w <= max_warps:
             out.append(LaunchCfg(w, b, t))
     return out

@@ -111,6 +111,8 @@ int flints_plan(flints_plan_t *out, int64_t nside, int lmax, const double *cl, c
     if (12 * nside * nside < K) return fail(FLINTS_EINVAL, "flints_plan: K exceeds the pixel count");
     if (precision != FLINTS_FP64 && precision != FLINTS_MIXED)
         return fail(FLINTS_EINVAL, "flints_plan: precision must be FLINTS_FP64 or FLINTS_MIXED");
+    if (flags & ~(unsigned)(FLINTS_NO_VARIANCE | FLINTS_FORCE_FALLBACK))
+        return fail(FLINTS_EINVAL, "flints_plan: unknown flag bits 0x%x", flags);
     for (int l = 0; l <= lmax; ++l) {
         if (!std::isfinite(cl[l]) || (spin == 2 && cl_bb && !std::isfinite(cl_bb[l])))
             return fail(FLINTS_EINVAL, "flints_plan: non-finite spectrum value at l = %d", l);
@@ -256,6 +258,7 @@ static int run(flints_plan_t p, int64_t first, int64_t count, const double *map,
     a.defl = defl;
     a.out = out;
     a.var = (p->flags & FLINTS_NO_VARIANCE) ? nullptr : var;
+    a.force_fallback = (p->flags & FLINTS_FORCE_FALLBACK) ? 1 : 0;
     a.status = status;
     a.stencil = stencil;
     a.tab.c64 = p->d_c64;
@@ -366,8 +369,9 @@ int flints_batch_stage(flints_batch_t b, const flints_job *jobs, int n, int tile
     if (!b) return fail(FLINTS_EINVAL, "batch is NULL");
     if (n < 0 || n > b->max_jobs || (n > 0 && !jobs))
         return fail(FLINTS_EINVAL, "flints_batch_stage: %d jobs for a batch of capacity %d", n, b->max_jobs);
-    if (tile_points < 0 || tile_points > 32) return fail(FLINTS_EINVAL, "flints_batch_stage: tile_points 0..32");
-    const int tp = tile_points > 0 ? tile_points : 32;
+    if (tile_points < 0 || tile_points > MAX_TILE_POINTS)
+        return fail(FLINTS_EINVAL, "flints_batch_stage: tile_points 0..%d", MAX_TILE_POINTS);
+    const int tp = tile_points > 0 ? tile_points : MAX_TILE_POINTS;
     std::vector<BatchJob> v;
     v.reserve(n);
     std::vector<double> cost;
@@ -392,6 +396,7 @@ int flints_batch_stage(flints_batch_t b, const flints_job *jobs, int n, int tile
         a.defl = j.defl;
         a.out = j.out;
         a.var = (p->flags & FLINTS_NO_VARIANCE) ? nullptr : j.var;
+        a.force_fallback = (p->flags & FLINTS_FORCE_FALLBACK) ? 1 : 0;
         a.status = j.status;
         a.stencil = nullptr;
         a.tab.c64 = p->d_c64;
@@ -512,8 +517,9 @@ int flints_plan_set_launch(flints_plan_t p, const flints_launch_cfg *cfg) {
         return FLINTS_OK;
     }
     if (cfg->warps_per_block < 0 || cfg->warps_per_block > 8 || cfg->blocks_per_sm < 0 || cfg->blocks_per_sm > 32 ||
-        cfg->tile_points < 0 || cfg->tile_points > 32)
-        return fail(FLINTS_EINVAL, "flints_plan_set_launch: warps_per_block 0..8, blocks_per_sm 0..32, tile_points 0..32");
+        cfg->tile_points < 0 || cfg->tile_points > MAX_TILE_POINTS)
+        return fail(FLINTS_EINVAL, "flints_plan_set_launch: warps_per_block 0..8, blocks_per_sm 0..32, tile_points 0..%d",
+                    MAX_TILE_POINTS);
     p->cfg = LaunchCfg{cfg->warps_per_block, cfg->blocks_per_sm, cfg->tile_points};
     return FLINTS_OK;
 }

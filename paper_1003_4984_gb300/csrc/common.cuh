@@ -288,9 +288,13 @@ struct LensArgs {
     double xi0;
     double r2;  // squared search radius (chord^2)
     unsigned long long *counters;  // points, nugget, fallback, window, failed
+    int force_fallback;            // discard double-float solves (testing aid)
 };
 
 // Launch shape chosen by the caller or the autotuner (0 = library default).
+// Targets per warp tile (the displacement phase runs one target per lane).
+constexpr int MAX_TILE_POINTS = 16;
+
 struct LaunchCfg {
     int warps_per_block, blocks_per_sm, tile_points;
 };

@@ -19,6 +19,7 @@
 // mixed path: FP64 geometry and selection, double-float assembly, factor and
 // solves, FP64 fallback for points whose double-float factor fails).
 #pragma once
+#include <cstddef>
 #include <type_traits>
 
 #include "common.cuh"
@@ -62,10 +63,12 @@ struct WarpSmem {
     // packed lower triangle of S + n I (row i starts at i(i+1)/2), then the two
     // bordered right-hand-side rows (c and y), K entries each
     static constexpr int MAT = K * (K + 1) / 2 + 2 * K;
-    PointA pts[32];
-    double ox[K], oy[K], oz[K];          // neighbour offsets X_i - n' (FP64)
-    double nz[K], ns[K], nc[K], nsn[K];  // neighbour z, sin(theta), cos(phi), sin(phi)
-    df gx[K], gy[K], gz[K], gnz[K], gns[K], gnc[K], gnsn[K];  // the same in double-float
+    using T = typename Ops<R>::T;
+    PointA pts[MAX_TILE_POINTS];
+    // neighbour offsets X_i - n', and neighbour z, sin(theta), cos(phi), sin(phi),
+    // in the solve's precision (FP64 or double-float; both 8 bytes, so the two
+    // views of a warp's slice share every offset)
+    T gx[K], gy[K], gz[K], gnz[K], gns[K], gnc[K], gnsn[K];
     // spin 2: per-neighbour target phase Phi0_i = phase(n' -> X_i), tangent-plane
     // coordinates (u, v) of X_i - n' at n', and squared chords to n'
     typename Ops<R>::T p0r[K], p0i[K], pu[K], pv[K];
@@ -262,13 +265,13 @@ template <class R, class SM>
 struct Geom;
 template <class SM>
 struct Geom<double, SM> {
-    static __device__ __forceinline__ double x(const SM &s, int i) { return s.ox[i]; }
-    static __device__ __forceinline__ double y(const SM &s, int i) { return s.oy[i]; }
-    static __device__ __forceinline__ double z(const SM &s, int i) { return s.oz[i]; }
-    static __device__ __forceinline__ double nz(const SM &s, int i) { return s.nz[i]; }
-    static __device__ __forceinline__ double ns(const SM &s, int i) { return s.ns[i]; }
-    static __device__ __forceinline__ double nc(const SM &s, int i) { return s.nc[i]; }
-    static __device__ __forceinline__ double nsn(const SM &s, int i) { return s.nsn[i]; }
+    static __device__ __forceinline__ double x(const SM &s, int i) { return s.gx[i]; }
+    static __device__ __forceinline__ double y(const SM &s, int i) { return s.gy[i]; }
+    static __device__ __forceinline__ double z(const SM &s, int i) { return s.gz[i]; }
+    static __device__ __forceinline__ double nz(const SM &s, int i) { return s.gnz[i]; }
+    static __device__ __forceinline__ double ns(const SM &s, int i) { return s.gns[i]; }
+    static __device__ __forceinline__ double nc(const SM &s, int i) { return s.gnc[i]; }
+    static __device__ __forceinline__ double nsn(const SM &s, int i) { return s.gnsn[i]; }
 };
 template <class SM>
 struct Geom<df, SM> {
@@ -569,11 +572,14 @@ template <int K, int SPIN, int MIXED>
 constexpr size_t warp_smem_bytes() {
     using SMd = WarpSmem<K, SPIN, double>;
     using SMf = WarpSmem<K, SPIN, df>;
+    static_assert(offsetof(SMd, gx) == offsetof(SMf, gx) && offsetof(SMd, kt) == offsetof(SMf, kt) &&
+                      offsetof(SMd, u) == offsetof(SMf, u),
+                  "the FP64 and double-float views of a warp slice must share their layout");
     constexpr size_t WS = sizeof(SMd) > sizeof(SMf) ? sizeof(SMd) : sizeof(SMf);
     return (WS + 15) / 16 * 16;
 }
 
-// One tile of `tile_pts` (<= 32) consecutive targets of a launch, processed by
+// One tile of `tile_pts` (<= MAX_TILE_POINTS) consecutive targets of a launch, processed by
 // one warp whose shared-memory slice starts at `wbase`.
 template <int K, int SPIN, int MIXED>
 __device__ __forceinline__ void process_tile(const LensArgs &a, int R_rings, int64_t tile, int tile_pts,
@@ -630,7 +636,7 @@ __device__ __forceinline__ void process_tile(const LensArgs &a, int R_rings, int
             P.phif = (float)P.phi;
             P.ic = ring_above(N, z);
         }
-        sm.pts[lane] = P;
+        if (lane < MAX_TILE_POINTS) sm.pts[lane] = P;
     }
     __syncwarp();
 
@@ -827,25 +833,29 @@ __device__ __forceinline__ void process_tile(const LensArgs &a, int R_rings, int
                     sm.kt[i] = keyd[r];
                     sm.ktf[i] = (float)keyd[r];
                     const double cx = sm.u.cand.cx[c], cy = sm.u.cand.cy[c], cz = sm.u.cand.cz[c];
-                    sm.ox[i] = cx - P.x;
-                    sm.oy[i] = cy - P.y;
-                    sm.oz[i] = cz - P.z;
-                    sm.nz[i] = cz;
-                    sm.ns[i] = sqrt(cx * cx + cy * cy);
-                    sm.nc[i] = sm.u.cand.cc[c];
-                    sm.nsn[i] = sm.u.cand.cs[c];
+                    const double ox = cx - P.x, oy = cy - P.y, oz = cz - P.z;
+                    const double ns = sqrt(cx * cx + cy * cy), nc = sm.u.cand.cc[c], nsn = sm.u.cand.cs[c];
                     {
                         const uint32_t pkd = sm.u.cand.cpix[c];
                         pixr[r] = (uint32_t)(sm.u.cand.rings[pkd >> 24].first + (pkd & 0xffffffu));
                     }
                     if (MIXED) {
-                        sm.gx[i] = df_from(sm.ox[i]);
-                        sm.gy[i] = df_from(sm.oy[i]);
-                        sm.gz[i] = df_from(sm.oz[i]);
-                        sm.gnz[i] = df_from(cz);
-                        sm.gns[i] = df_from(sm.ns[i]);
-                        sm.gnc[i] = df_from(sm.nc[i]);
-                        sm.gnsn[i] = df_from(sm.nsn[i]);
+                        SMf &smf = *reinterpret_cast<SMf *>(wbase);
+                        smf.gx[i] = df_from(ox);
+                        smf.gy[i] = df_from(oy);
+                        smf.gz[i] = df_from(oz);
+                        smf.gnz[i] = df_from(cz);
+                        smf.gns[i] = df_from(ns);
+                        smf.gnc[i] = df_from(nc);
+                        smf.gnsn[i] = df_from(nsn);
+                    } else {
+                        sm.gx[i] = ox;
+                        sm.gy[i] = oy;
+                        sm.gz[i] = oz;
+                        sm.gnz[i] = cz;
+                        sm.gns[i] = ns;
+                        sm.gnc[i] = nc;
+                        sm.gnsn[i] = nsn;
                     }
                 }
             }
@@ -888,8 +898,25 @@ __device__ __forceinline__ void process_tile(const LensArgs &a, int R_rings, int
                 SMf &smf = *reinterpret_cast<SMf *>(wbase);
                 solved = solve_point<K, SPIN, df>(smf, P, lane, NUGGET_EPS, a.tab, keyd, yre, yim, vre, vim,
                                                   vrel);
-                if (!solved) flags |= FLINTS_ST_FALLBACK;
                 __syncwarp();
+                if (a.force_fallback) solved = false;
+                if (!solved) {
+                    // FP64 fallback: widen the double-float geometry in place (offsets keep
+                    // ~2^-48 of their own size, the O(1) terms ~2^-48 absolute)
+                    flags |= FLINTS_ST_FALLBACK;
+                    for (int i = lane; i < K; i += 32) {
+                        const double g[7] = {df_to(smf.gx[i]), df_to(smf.gy[i]), df_to(smf.gz[i]), df_to(smf.gnz[i]),
+                                             df_to(smf.gns[i]), df_to(smf.gnc[i]), df_to(smf.gnsn[i])};
+                        sm.gx[i] = g[0];
+                        sm.gy[i] = g[1];
+                        sm.gz[i] = g[2];
+                        sm.gnz[i] = g[3];
+                        sm.gns[i] = g[4];
+                        sm.gnc[i] = g[5];
+                        sm.gnsn[i] = g[6];
+                    }
+                    __syncwarp();
+                }
             }
             double nug = NUGGET_EPS;
             for (int step = 0; !solved && step <= MAX_NUGGET_STEPS; ++step) {
@@ -938,7 +965,7 @@ __global__ void __launch_bounds__(256, 2) lens_kernel(LensArgs a, int R_rings, i
 template <int K, int SPIN, int MIXED>
 cudaError_t launch_one(const LensArgs &a, int R_rings, const LaunchCfg &cfg, int num_sms, cudaStream_t st) {
     int wpb = cfg.warps_per_block > 0 ? cfg.warps_per_block : 4;
-    const int tile_pts = cfg.tile_points > 0 ? cfg.tile_points : 32;
+    const int tile_pts = cfg.tile_points > 0 && cfg.tile_points < MAX_TILE_POINTS ? cfg.tile_points : MAX_TILE_POINTS;
     // the launch shape is a hint: keep the block within the opt-in shared memory
     const int fit = (int)(device_smem_optin() / warp_smem_bytes<K, SPIN, MIXED>());
     if (wpb > fit) wpb = fit > 0 ? fit : 1;

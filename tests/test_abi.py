@@ -38,6 +38,11 @@ def test_binding_loads_and_reports_errors_without_gpu(lib_path):
     rc = lib.flints_plan(ctypes.byref(h), 0, 10, None, None, 0, 32, 0, 0, None)
     assert rc == 1 and not h.value
     assert b"nside" in lib.flints_last_error() or b"cl" in lib.flints_last_error()
+    cl = (ctypes.c_double * 33)(*([0.0, 0.0] + [1.0] * 31))
+    rc = lib.flints_plan(ctypes.byref(h), 16, 32, cl, None, 0, 16, 0, 1 << 12, None)
+    assert rc == 1 and not h.value and b"flag" in lib.flints_last_error()
+    rc = lib.flints_plan(ctypes.byref(h), 16, 32, cl, None, 0, 20, 0, 0, None)
+    assert rc == 1 and b"K must be" in lib.flints_last_error()
 
 
 def test_product_path_refuses_without_library(tmp_path):

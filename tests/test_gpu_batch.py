@@ -78,7 +78,7 @@ def test_batch_matches_single_launches(fl):
     _check(jobs, refs)
     after = [p.stats()["points"] for p in plans]
     assert [a - x for a, x in zip(after, before)] == [j[2] for j in jobs]
-    for cfg in (fl.LaunchCfg(2, 1, 16), fl.LaunchCfg(8, 0, 32), fl.LaunchCfg(4, 2, 7)):
+    for cfg in (fl.LaunchCfg(2, 1, 16), fl.LaunchCfg(8, 0, 12), fl.LaunchCfg(4, 2, 7)):
         for j in jobs:
             j[5].fill_(float("nan"))
         b.run(jobs, cfg)
@@ -98,7 +98,7 @@ def test_batch_graph_capture_and_restage(fl):
     ranges = [(0, 4096)] * len(SPECS)
     plans, jobs, refs = _jobs(fl, torch, ranges)
     b = fl.Batch(16)
-    cfg = fl.LaunchCfg(4, 0, 32)
+    cfg = fl.LaunchCfg(4, 0, 16)
     b.run(jobs, cfg)  # first launch with this shape happens before capture
     torch.cuda.synchronize()
     s = torch.cuda.Stream()
@@ -140,7 +140,7 @@ def test_autotuner_picks_and_caches(fl, tmp_path):
     n = 8192
     ref = plan.lens(m, d[:n].contiguous(), *_outputs(torch, plan, n), first=0, count=n)
     cache = str(tmp_path / "tune.json")
-    cands = [fl.LaunchCfg(2, 0, 32), fl.LaunchCfg(4, 0, 32), fl.LaunchCfg(8, 0, 16)]
+    cands = [fl.LaunchCfg(2, 0, 16), fl.LaunchCfg(4, 0, 16), fl.LaunchCfg(8, 0, 8)]
     cfg = autotune.tune_plan(plan, m, d[:n].contiguous(), 0, n, cache=cache, cands=cands)
     assert cfg.key() in [c.key() for c in cands]
     assert os.path.exists(cache)

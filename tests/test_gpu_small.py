@@ -185,6 +185,42 @@ def test_spin0_all_stencil_sizes(fl, torch, K):
         assert parity_metric(to_host(out), ref.value, float(np.std(m))) <= TOL[precision]
 
 
+@pytest.mark.parametrize("spin", [0, 2])
+def test_mixed_fp64_fallback_path(fl, torch, c1_inputs, spin):
+    """The FP64 fallback of the mixed path (taken when the double-float factor
+    meets a non-positive pivot) rebuilds its geometry from the double-float
+    copies; forcing it on every point checks that path against the oracle."""
+    if spin == 0:
+        W, cl, alm, m, defl, ref = c1_inputs
+        nside, K, bb, sigma, x0 = W.nside, W.K, None, float(np.std(m)), None
+    else:
+        nside, K, lmax = 32, 32, 64
+        cl = wl.cl_ee(lmax, 50.0)
+        bb = 0.2 * cl
+        P = sht.synth_map(nside, lmax, wl.draw_alm(cl, 61), spin=2, blm=wl.draw_alm(bb, 62))
+        m = np.ascontiguousarray(np.stack([P.real, P.imag], axis=1))
+        defl = wl.random_deflection(hp.npix(nside), 63) * 8
+        tab, x0, _, _ = oracle_table(cl, bb, 2, K, nside)
+        ref = kr.lens(nside, K, 2, m, defl, np.arange(hp.npix(nside)), tab, x0)
+        sigma = float(np.sqrt(np.mean(P.real ** 2 + P.imag ** 2)))
+    npix = hp.npix(nside)
+    plan = fl.Plan(nside, cl, bb, spin=spin, K=K, precision="mixed", flags=fl.FLINTS_FORCE_FALLBACK)
+    out = torch.empty((npix,) if spin == 0 else (npix, 2), dtype=torch.float64, device="cuda")
+    var = torch.empty(npix, dtype=torch.float64, device="cuda")
+    status = torch.empty(npix, dtype=torch.uint8, device="cuda")
+    plan.lens(torch.from_numpy(m).cuda(), torch.from_numpy(defl).cuda(), out, var, status)
+    torch.cuda.synchronize()
+    v = to_host(out)
+    if spin == 2:
+        v = v[:, 0] + 1j * v[:, 1]
+    # FP64 arithmetic on geometry carried to ~2^-48: well inside the mixed tolerance
+    assert parity_metric(v, ref.value, sigma) <= 1e-8
+    assert parity_metric(to_host(var), ref.variance, plan.info().xi0) <= 1e-8
+    st = to_host(status)
+    assert np.all(st & fl.ST_FALLBACK) and not np.any(st & fl.ST_FAILED)
+    assert plan.stats()["fallback"] == npix
+
+
 def test_wrong_spin_entry_point_is_an_error(fl, torch):
     plan = fl.Plan(16, wl.cl_tt(32, 20.0), spin=0, K=16)
     z = torch.zeros((hp.npix(16), 2), dtype=torch.float64, device="cuda")
