@@ -43,8 +43,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", choices=["c3", "c4", "c5"], default="c3",
-                    help="c3: Nside 4096 spin 2 (default); c4: 64-map batched persistent launch")
+    ap.add_argument("--workload", choices=["c3", "c4", "c5", "ss"], default="c3",
+                    help="c3: Nside 4096 spin 2 (default); c4: 64-map batched persistent launch; c5: serving; "
+                         "ss: supersampling Nside 2048 -> 4096")
     ap.add_argument("--duration", type=float, default=45.0, help="c5: seconds of Poisson arrivals")
     ap.add_argument("--profile-case", choices=["mixed", "fp64"], default=None,
                     help="small case for ncu: two launches on 2^18 targets of the resident c3 map")
@@ -487,12 +488,76 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+# ------------------------------------------------------- supersampling arm
+def run_ss(args):
+    """Supersampling (Sec. 2.6, Table 1 row Nside 2048 -> 4096, lmax 4096): an Nside
+    2048 map predicted at the pixel centres of the Nside 4096 grid, K = 32, spin 0,
+    2^24 targets per step.  Also reports the predicted precision sqrt(<sigma^2>)/sigma_map,
+    Table 1's precision column (its stencils have 9 and 36 neighbours)."""
+    import torch
+
+    import paper_1003_4984_gb300 as fl
+    from paper_1003_4984_gb300 import flops
+
+    fl.load_library()
+    Wc = wl.C2
+    nout = 2 * Wc.nside
+    npix_out = 12 * nout * nout
+    cl, _ = Wc.cl()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(4242)
+    m = torch.randn(Wc.npix, dtype=torch.float64, device=dev, generator=g)
+    out = torch.empty(BATCH, dtype=torch.float64, device=dev)
+    var = torch.empty(BATCH, dtype=torch.float64, device=dev)
+    nb = npix_out // BATCH
+    res = {}
+    for precision, steps in (("mixed", args.steps), ("fp64", max(1, args.fp64_steps))):
+        plan = fl.Plan(Wc.nside, cl, spin=0, K=Wc.K, precision=precision)
+        for i in range(args.warmup):
+            plan.supersample(m, nout, out, var, first=(i % nb) * BATCH, count=BATCH)
+        torch.cuda.synchronize(dev)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        ev[0].record(stream)
+        for i in range(steps):
+            plan.supersample(m, nout, out, var, first=((args.warmup + i) % nb) * BATCH, count=BATCH)
+            ev[i + 1].record(stream)
+        torch.cuda.synchronize(dev)
+        per = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+        res[precision] = (BATCH * steps / (ev[0].elapsed_time(ev[steps]) / 1e3), per, plan.info().xi0, plan.stats())
+        plan.close()
+    value, per, xi0, st = res["mixed"]
+    precision_pred = math.sqrt(float(var.mean()) / xi0)  # last batch, FP64 plan
+    fl32 = flops.mixed_fp32_flops(Wc.K, 0)
+    achieved = fl32 * BATCH / (statistics.mean(per) / 1e3) / 1e12
+    print(json.dumps({
+        "metric": "supersampled pts/s, Nside 2048 -> 4096, lmax 4096, K=32, spin 0", "value": value,
+        "unit": "pts/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": statistics.mean(per), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 in/out; double-float factor", "data": "synthetic white-noise Nside 2048 map",
+        "config": {"workload": "supersampling: Nside 2048 (lmax 4096, damping l = 2500) -> Nside 4096 pixel "
+                               "centres, K = 32", "batch_points": BATCH,
+                   "l2": "inputs larger than L2 (403 MB map, 2^24 targets per step)"},
+        "fp64": {"value": res["fp64"][0], "ms_per_step": statistics.mean(res["fp64"][1])},
+        "mixed_over_fp64": value / res["fp64"][0],
+        "predicted_precision": precision_pred,
+        "paper_table1": "Nside 2048 -> 4096, l 4096: 3e-3 (9 neighbours), 3e-4 (36 neighbours); serial "
+                        "Xeon E5410 3.3 / 19 min per map",
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": flops.FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / flops.FP32_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "lens_kernel<32,0,mixed>", "flops_per_point": fl32},
+        "mixed_stats": st, "gpu_launches": args.steps}))
+
+
 if __name__ == "__main__":
     a = parse()
     if a.workload == "c4" and a.impl == "ours" and not a.profile_case:
         run_c4(a)
     elif a.workload == "c5" and a.impl == "ours" and not a.profile_case:
         run_c5(a)
+    elif a.workload == "ss" and a.impl == "ours" and not a.profile_case:
+        run_ss(a)
     elif a.profile_case:
         run_profile_case(a.profile_case)
     elif a.impl == "reference":

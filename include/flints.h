@@ -133,6 +133,18 @@ int flints_lens_range(flints_plan_t plan, int64_t first, int64_t count,
                       const double *map, const double *defl, double *out,
                       double *var, uint8_t *status, void *stream);
 
+/* Supersampling (Sec. 2.6 and Table 1 of the paper: a map at Nside predicted
+ * at the pixel centres of a finer grid): interpolate the plan's map at the
+ * centres of RING pixels [first, first+count) of an Nside = nside_out grid
+ * (1..65536; any value, usually 2 x the plan's Nside), with no deflection.
+ * map is the whole source map at the plan's Nside (device, [Npix] or
+ * [Npix][2]); out, var and status are indexed from 0 for pixel `first`
+ * (spin 2: Q, U in the frame at the target).  Errors and status as for
+ * flints_lens_range. */
+int flints_supersample(flints_plan_t plan, int64_t nside_out, int64_t first, int64_t count,
+                       const double *map, double *out, double *var, uint8_t *status,
+                       void *stream);
+
 /* Stencil of the range [first, first+count): the K nearest RING pixels to
  * each displaced direction, sorted by (squared chord, pixel index), written
  * to idx device int64 [count][K] (the neighbour search of the lens kernels,

@@ -239,6 +239,31 @@ def pair_phase(va: np.ndarray, vb: np.ndarray) -> np.ndarray:
     return np.where(np.isfinite(ph), ph, 1.0 + 0.0j)
 
 
+def estimate(nside: int, spin: int, maps: np.ndarray, targets: np.ndarray, idx: np.ndarray,
+             f_plus, xi_zero: float, eps: float = EPS_NUGGET):
+    """Steps 3-5 on a given stencil ``idx`` (B, K): (values, variances, nuggets)."""
+    K = idx.shape[1]
+    X = hp.pix2vec(nside, idx)  # (B, K, 3)
+    T = _chord2(X[:, :, None, :], X[:, None, :, :])
+    S = f_plus(T.reshape(-1)).reshape(T.shape)
+    c = f_plus(_chord2(targets[:, None, :], X))
+    if spin == 0:
+        y = maps[idx]
+        L, nug = factor_with_nugget(S, eps)
+        zc = forward_solve(L, c)
+        zy = forward_solve(L, y)
+        return np.sum(zc * zy, axis=1), xi_zero * (1.0 - np.sum(zc * zc, axis=1)), nug
+    Ph = pair_phase(X[:, :, None, :], X[:, None, :, :])
+    C = S * Ph
+    C[:, np.arange(K), np.arange(K)] = 1.0
+    c0 = c * pair_phase(np.broadcast_to(targets[:, None, :], X.shape), X)
+    y = maps[idx, 0] + 1j * maps[idx, 1]
+    L, nug = factor_with_nugget(C, eps)
+    zc = forward_solve(L, np.conj(c0))
+    zy = forward_solve(L, y)
+    return np.sum(np.conj(zc) * zy, axis=1), xi_zero * (1.0 - np.sum(np.abs(zc) ** 2, axis=1)), nug
+
+
 def interpolate(nside: int, K: int, spin: int, maps: np.ndarray, targets: np.ndarray,
                 f_plus, xi_zero: float, eps: float = EPS_NUGGET, batch: int = 4096) -> Result:
     """Kriging at unit vectors ``targets`` (P, 3) from a RING map.
@@ -253,32 +278,12 @@ def interpolate(nside: int, K: int, spin: int, maps: np.ndarray, targets: np.nda
     sten = np.empty((P, K), dtype=np.int64)
     keys = np.empty((P, K))
     nugs = np.empty(P)
-    eye = np.eye(K)
     for b0 in range(0, P, batch):
         tv = targets[b0:b0 + batch]
         idx, key = knn(nside, tv, K)
-        X = hp.pix2vec(nside, idx)  # (B, K, 3)
-        T = _chord2(X[:, :, None, :], X[:, None, :, :])
-        S = f_plus(T.reshape(-1)).reshape(T.shape)
-        c = f_plus(_chord2(tv[:, None, :], X))
-        if spin == 0:
-            y = maps[idx]
-            L, nug = factor_with_nugget(S, eps)
-            zc = forward_solve(L, c)
-            zy = forward_solve(L, y)
-            vals[b0:b0 + batch] = np.sum(zc * zy, axis=1)
-            var[b0:b0 + batch] = xi_zero * (1.0 - np.sum(zc * zc, axis=1))
-        else:
-            Ph = pair_phase(X[:, :, None, :], X[:, None, :, :])
-            C = S * Ph
-            C[:, np.arange(K), np.arange(K)] = 1.0
-            c0 = c * pair_phase(np.broadcast_to(tv[:, None, :], X.shape), X)
-            y = maps[idx, 0] + 1j * maps[idx, 1]
-            L, nug = factor_with_nugget(C, eps)
-            zc = forward_solve(L, np.conj(c0))
-            zy = forward_solve(L, y)
-            vals[b0:b0 + batch] = np.sum(np.conj(zc) * zy, axis=1)
-            var[b0:b0 + batch] = xi_zero * (1.0 - np.sum(np.abs(zc) ** 2, axis=1))
+        v, s2, nug = estimate(nside, spin, maps, tv, idx, f_plus, xi_zero, eps)
+        vals[b0:b0 + batch] = v
+        var[b0:b0 + batch] = s2
         sten[b0:b0 + batch] = idx
         keys[b0:b0 + batch] = key
         nugs[b0:b0 + batch] = nug
@@ -289,4 +294,12 @@ def lens(nside: int, K: int, spin: int, maps: np.ndarray, defl: np.ndarray, pix:
          f_plus, xi_zero: float, eps: float = EPS_NUGGET) -> Result:
     """Lensed values at target pixels ``pix`` (Born remap T(n + d(n)), Sec. 3.1)."""
     tv = displace(nside, np.asarray(pix, dtype=np.int64), np.asarray(defl, dtype=np.float64))
+    return interpolate(nside, K, spin, maps, tv, f_plus, xi_zero, eps)
+
+
+def supersample(nside: int, nside_out: int, K: int, spin: int, maps: np.ndarray, pix_out: np.ndarray,
+                f_plus, xi_zero: float, eps: float = EPS_NUGGET) -> Result:
+    """Values at the centres of pixels ``pix_out`` of a finer Nside_out grid (Sec. 2.6):
+    the same estimator with undisplaced targets."""
+    tv = hp.pix2vec(nside_out, np.asarray(pix_out, dtype=np.int64))
     return interpolate(nside, K, spin, maps, tv, f_plus, xi_zero, eps)

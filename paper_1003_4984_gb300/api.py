@@ -78,6 +78,7 @@ def load_library(path: str = LIB_PATH):
     lib.flints_lens_spin2.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.flints_lens_range.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp]
     lib.flints_stencil.argtypes = [vp, i64, i64, vp, vp, vp, vp]
+    lib.flints_supersample.argtypes = [vp, i64, i64, i64, vp, vp, vp, vp, vp]
     lib.flints_lens_batch.argtypes = [ctypes.POINTER(_Job), c_int, vp]
     lib.flints_get_stats.argtypes = [vp, ctypes.POINTER(_Stats), vp]
     lib.flints_reset_stats.argtypes = [vp, vp]
@@ -242,6 +243,29 @@ class Plan:
             raise FlintsError("status must be a uint8 CUDA tensor of length count")
         _check(_lib.flints_lens_range(self._h, int(first), int(count), _ptr(map_), _ptr(defl), _ptr(out), _ptr(var),
                                       _ptr(status), _stream(stream)))
+        return out, var, status
+
+    def supersample(self, map_, nside_out: int, out=None, var=None, status=None, first: int = 0,
+                    count: int | None = None, stream=None):
+        """Interpolate the map at the centres of RING pixels [first, first+count) of an
+        Nside = ``nside_out`` grid (no deflection; flints_supersample)."""
+        import torch
+
+        npix_out = 12 * int(nside_out) ** 2
+        if count is None:
+            count = npix_out - first
+        comp = (self.npix,) if self.spin == 0 else (self.npix, 2)
+        _dev_f64(map_, comp, "map")
+        oshape = (count,) if self.spin == 0 else (count, 2)
+        if out is None:
+            out = torch.empty(oshape, dtype=torch.float64, device=map_.device)
+        _dev_f64(out, oshape, "out")
+        if var is not None:
+            _dev_f64(var, (count,), "var")
+        if status is not None and (status.dtype != torch.uint8 or not status.is_cuda or status.numel() != count):
+            raise FlintsError("status must be a uint8 CUDA tensor of length count")
+        _check(_lib.flints_supersample(self._h, int(nside_out), int(first), int(count), _ptr(map_), _ptr(out),
+                                       _ptr(var), _ptr(status), _stream(stream)))
         return out, var, status
 
     def lens_full(self, map_, defl, out, var=None, stream=None):

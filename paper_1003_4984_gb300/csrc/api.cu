@@ -237,16 +237,19 @@ static int check_device(flints_plan_t p) {
     return FLINTS_OK;
 }
 
-static int run(flints_plan_t p, int64_t first, int64_t count, const double *map, const double *defl, double *out,
-               double *var, uint8_t *status, int64_t *stencil, void *stream) {
+// nside_tgt = 0: lensing targets (pixels of the plan's grid displaced by defl);
+// nside_tgt > 0: the pixel centres of an Nside = nside_tgt grid (supersampling).
+static int run(flints_plan_t p, int64_t nside_tgt, int64_t first, int64_t count, const double *map,
+               const double *defl, double *out, double *var, uint8_t *status, int64_t *stencil, void *stream) {
     if (!p) return fail(FLINTS_EINVAL, "plan is NULL");
     if (int rc = check_device(p)) return rc;
-    const int64_t npix = 12 * p->nside * p->nside;
+    const int64_t nt = nside_tgt > 0 ? nside_tgt : p->nside;
+    const int64_t npix = 12 * nt * nt;
     if (first < 0 || count < 0 || first > npix || count > npix - first)
         return fail(FLINTS_EINVAL, "target range [%lld, %lld) outside [0, %lld)", (long long)first,
                     (long long)(first + count), (long long)npix);
     if (count == 0) return FLINTS_OK;
-    if (!defl) return fail(FLINTS_EINVAL, "defl is NULL");
+    if (!defl && nside_tgt == 0) return fail(FLINTS_EINVAL, "defl is NULL");
     if (!stencil && (!map || !out)) return fail(FLINTS_EINVAL, "map and out must not be NULL");
     const uintptr_t align = (uintptr_t)map | (uintptr_t)defl | (uintptr_t)out;
     if (align & 15u) return fail(FLINTS_EINVAL, "map, defl and out must be 16-byte aligned");
@@ -259,6 +262,7 @@ static int run(flints_plan_t p, int64_t first, int64_t count, const double *map,
     a.out = out;
     a.var = (p->flags & FLINTS_NO_VARIANCE) ? nullptr : var;
     a.force_fallback = (p->flags & FLINTS_FORCE_FALLBACK) ? 1 : 0;
+    a.nside_tgt = nside_tgt;
     a.status = status;
     a.stencil = stencil;
     a.tab.c64 = p->d_c64;
@@ -280,25 +284,33 @@ static int run(flints_plan_t p, int64_t first, int64_t count, const double *map,
 int flints_lens_spin0(flints_plan_t p, const double *map, const double *defl, double *out, double *var, void *stream) {
     if (!p) return fail(FLINTS_EINVAL, "plan is NULL");
     if (p->spin != 0) return fail(FLINTS_EINVAL, "flints_lens_spin0 called with a spin-2 plan");
-    return run(p, 0, 12 * p->nside * p->nside, map, defl, out, var, nullptr, nullptr, stream);
+    return run(p, 0, 0, 12 * p->nside * p->nside, map, defl, out, var, nullptr, nullptr, stream);
 }
 
 int flints_lens_spin2(flints_plan_t p, const double *qu, const double *defl, double *qu_out, double *var,
                       void *stream) {
     if (!p) return fail(FLINTS_EINVAL, "plan is NULL");
     if (p->spin != 2) return fail(FLINTS_EINVAL, "flints_lens_spin2 called with a spin-0 plan");
-    return run(p, 0, 12 * p->nside * p->nside, qu, defl, qu_out, var, nullptr, nullptr, stream);
+    return run(p, 0, 0, 12 * p->nside * p->nside, qu, defl, qu_out, var, nullptr, nullptr, stream);
 }
 
 int flints_lens_range(flints_plan_t p, int64_t first, int64_t count, const double *map, const double *defl,
                       double *out, double *var, uint8_t *status, void *stream) {
-    return run(p, first, count, map, defl, out, var, status, nullptr, stream);
+    return run(p, 0, first, count, map, defl, out, var, status, nullptr, stream);
+}
+
+int flints_supersample(flints_plan_t p, int64_t nside_out, int64_t first, int64_t count, const double *map,
+                       double *out, double *var, uint8_t *status, void *stream) {
+    if (!p) return fail(FLINTS_EINVAL, "plan is NULL");
+    if (nside_out < 1 || nside_out > 65536)
+        return fail(FLINTS_EINVAL, "flints_supersample: nside_out %lld outside [1, 65536]", (long long)nside_out);
+    return run(p, nside_out, first, count, map, nullptr, out, var, status, nullptr, stream);
 }
 
 int flints_stencil(flints_plan_t p, int64_t first, int64_t count, const double *defl, int64_t *idx, uint8_t *status,
                    void *stream) {
     if (!idx) return fail(FLINTS_EINVAL, "idx is NULL");
-    return run(p, first, count, nullptr, defl, nullptr, nullptr, status, idx, stream);
+    return run(p, 0, first, count, nullptr, defl, nullptr, nullptr, status, idx, stream);
 }
 
 // ------------------------------------------------------------------ batches

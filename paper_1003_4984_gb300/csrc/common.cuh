@@ -289,6 +289,7 @@ struct LensArgs {
     double r2;  // squared search radius (chord^2)
     unsigned long long *counters;  // points, nugget, fallback, window, failed
     int force_fallback;            // discard double-float solves (testing aid)
+    int64_t nside_tgt;             // > 0: targets are the pixel centres of this grid (no deflection)
 };
 
 // Launch shape chosen by the caller or the autotuner (0 = library default).

@@ -597,12 +597,14 @@ __device__ __forceinline__ void process_tile(const LensArgs &a, int R_rings, int
         if (lane < tile_pts && p < a.count) {
             const int64_t pix = a.first + p;
             int64_t ring, jj;
-            pix_ring(N, pix, ring, jj);
-            const Ring rg = ring_of(N, ring, inv3N, inv3N2);
+            // supersampling: the target is a pixel centre of the finer grid, undisplaced
+            const bool grid = a.nside_tgt > 0;
+            pix_ring(grid ? a.nside_tgt : N, pix, ring, jj);
+            const Ring rg = grid ? ring_of(a.nside_tgt, ring) : ring_of(N, ring, inv3N, inv3N2);
             double sp, cp;
             sincospi(((double)jj + rg.f) / (2.0 * (double)rg.nq), &sp, &cp);
             const double nx = rg.s * cp, ny = rg.s * sp, nz = rg.z;
-            const double2 dd = __ldg(reinterpret_cast<const double2 *>(a.defl) + p);
+            const double2 dd = grid ? make_double2(0.0, 0.0) : __ldg(reinterpret_cast<const double2 *>(a.defl) + p);
             const double dl = sqrt(dd.x * dd.x + dd.y * dd.y);
             double x = nx, y = ny, z = nz;
             if (dl > 0.0) {
@@ -789,24 +791,57 @@ __device__ __forceinline__ void process_tile(const LensArgs &a, int R_rings, int
                 __syncwarp();
                 bitonic_sort<RPL>(key, id, lane);
             } else {
-                unsigned long long k2[SPL];
-                unsigned i2[SPL];
+                // Near-tie at the K-th place.  A candidate whose FP32 key exceeds the
+                // K-th one by more than the margin is farther than the true K-th
+                // neighbour (FP32 keys are within 2^-17 relative), so FP64 keys are
+                // needed only for the FP32-ranked candidates below that threshold.
+                const unsigned thr = __float_as_uint(fa * (1.0f + 1.52587890625e-05f));
+                int hi = 0;
 #pragma unroll
-                for (int s = 0; s < SPL; ++s) {
-                    const int c = s * 32 + lane;
-                    k2[s] = 0x7ff0000000000000ull;
-                    i2[s] = 0xffffffffu;
-                    if (c < C) {
-                        k2[s] = place(c);
-                        i2[s] = (unsigned)c;
+                for (int s = 0; s < SPL; ++s) hi += __popc(__ballot_sync(FULL, (unsigned)(pk[s] >> 32) <= thr));
+                constexpr int S2 = RPL + 1 <= 2 ? 2 : 4;  // power of two >= RPL + 1, <= SPL
+                static_assert(S2 <= SPL, "near-tie slots exceed the candidate slots");
+                if (hi <= 32 * S2) {
+                    unsigned long long k2[S2];
+                    unsigned i2[S2];
+#pragma unroll
+                    for (int s = 0; s < S2; ++s) {
+                        k2[s] = 0x7ff0000000000000ull;
+                        i2[s] = 0xffffffffu;
+                        if (s * 32 + lane < hi) {
+                            const unsigned c = (unsigned)(pk[s] & 0xffffffffu);
+                            k2[s] = place((int)c);
+                            i2[s] = c;
+                        }
                     }
-                }
-                __syncwarp();
-                bitonic_sort<SPL>(k2, i2, lane);
+                    __syncwarp();
+                    bitonic_sort<S2>(k2, i2, lane);
 #pragma unroll
-                for (int r = 0; r < RPL; ++r) {
-                    key[r] = k2[r];
-                    id[r] = i2[r];
+                    for (int r = 0; r < RPL; ++r) {
+                        key[r] = k2[r];
+                        id[r] = i2[r];
+                    }
+                } else {
+                    // a wide tie (many equidistant candidates): FP64 keys of all
+                    unsigned long long k2[SPL];
+                    unsigned i2[SPL];
+#pragma unroll
+                    for (int s = 0; s < SPL; ++s) {
+                        const int c = s * 32 + lane;
+                        k2[s] = 0x7ff0000000000000ull;
+                        i2[s] = 0xffffffffu;
+                        if (c < C) {
+                            k2[s] = place(c);
+                            i2[s] = (unsigned)c;
+                        }
+                    }
+                    __syncwarp();
+                    bitonic_sort<SPL>(k2, i2, lane);
+#pragma unroll
+                    for (int r = 0; r < RPL; ++r) {
+                        key[r] = k2[r];
+                        id[r] = i2[r];
+                    }
                 }
             }
             // K-th neighbour inside the disc?

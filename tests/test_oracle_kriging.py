@@ -256,3 +256,27 @@ def test_spin2_pair_phase_factorises_through_the_target():
         g = (1 - 1j * x) ** 4 / (1 + x * x) ** 2  # exp(-2iE) with E = 2 atan(x)
         got = np.conj(kr.pair_phase(n, a)) * kr.pair_phase(n, b) * g
         np.testing.assert_allclose(got, kr.pair_phase(a, b), atol=1e-12)
+
+
+# ------------------------------------------------- supersampling (Sec. 2.6)
+def test_supersampling_error_statistics():
+    # An Nside 32 map band-limited at lmax 64 predicted at every Nside 64 pixel
+    # centre (Table 1's experiment, scaled down): the targets are the finer grid's
+    # centres and measured error / predicted sigma ~ N(0, 1) against the harmonic sum.
+    nside, lmax, K = 32, 64, 16
+    cl = wl.cl_tt(lmax, 50.0)
+    alm = wl.draw_alm(cl, 71)
+    m = sht.synth_map(nside, lmax, alm)
+    pix = np.arange(hp.npix(2 * nside))
+    tmax = 4 * (2.0 * math.sqrt(K / 3.0) / nside) ** 2 * 1.5
+    tab, x0 = xi.spin0_table(cl, tmax, 1024)
+    res = kr.supersample(nside, 2 * nside, K, 0, m, pix, tab, x0)
+    np.testing.assert_array_equal(res.target, hp.pix2vec(2 * nside, pix))
+    truth = sht.synth_points(lmax, alm, res.target)
+    r = (res.value - truth) / np.sqrt(res.variance)
+    assert abs(np.mean(r)) < 0.05
+    assert 0.9 < np.std(r) < 1.1
+    # predicted precision (Table 1's column: sqrt(mean sigma^2) / sigma_map) matches the measured one
+    pred = math.sqrt(np.mean(res.variance)) / np.std(m)
+    meas = math.sqrt(np.mean((res.value - truth) ** 2)) / np.std(m)
+    assert 0.85 < meas / pred < 1.15
