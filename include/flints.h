@@ -62,6 +62,12 @@ enum { FLINTS_FP64 = 0, FLINTS_MIXED = 1 };
 
 /* plan flags */
 enum {
+    /* spin 2: return P in the frame at the target pixel n instead of the frame at
+     * the displaced direction n': P(n') times exp(2i(a_nn' - a_n'n)), a_uv the
+     * angle at u (from e_theta towards e_phi) of the geodesic towards v, i.e. the
+     * polarisation parallel-transported back along the deflection (Sec. 3.1
+     * remaps P = Q + iU; the rotation is this library's reading) */
+    FLINTS_ROTATE_TO_TARGET = 2u,
     FLINTS_NO_VARIANCE = 4u, /* skip the variance output even if a buffer is given */
     /* testing aid (mixed plans): every double-float solve is discarded and the
      * point is re-solved by the FP64 fallback, so that path can be checked on

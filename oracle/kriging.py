@@ -291,10 +291,18 @@ def interpolate(nside: int, K: int, spin: int, maps: np.ndarray, targets: np.nda
 
 
 def lens(nside: int, K: int, spin: int, maps: np.ndarray, defl: np.ndarray, pix: np.ndarray,
-         f_plus, xi_zero: float, eps: float = EPS_NUGGET) -> Result:
-    """Lensed values at target pixels ``pix`` (Born remap T(n + d(n)), Sec. 3.1)."""
-    tv = displace(nside, np.asarray(pix, dtype=np.int64), np.asarray(defl, dtype=np.float64))
-    return interpolate(nside, K, spin, maps, tv, f_plus, xi_zero, eps)
+         f_plus, xi_zero: float, eps: float = EPS_NUGGET, rotate: bool = False) -> Result:
+    """Lensed values at target pixels ``pix`` (Born remap T(n + d(n)), Sec. 3.1).
+
+    ``rotate`` (spin 2): return P in the frame at the target pixel n rather than at
+    the displaced direction n', i.e. P(n') parallel-transported back along the
+    geodesic from n' to n, which multiplies it by pair_phase(n, n')."""
+    pix = np.asarray(pix, dtype=np.int64)
+    tv = displace(nside, pix, np.asarray(defl, dtype=np.float64))
+    res = interpolate(nside, K, spin, maps, tv, f_plus, xi_zero, eps)
+    if rotate and spin == 2:
+        res.value = res.value * pair_phase(hp.pix2vec(nside, pix), tv)
+    return res
 
 
 def supersample(nside: int, nside_out: int, K: int, spin: int, maps: np.ndarray, pix_out: np.ndarray,

@@ -20,6 +20,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "flints.h")
 
 FLINTS_FP64 = 0
 FLINTS_MIXED = 1
+FLINTS_ROTATE_TO_TARGET = 2  # spin 2: P in the frame at n, not n'
 FLINTS_NO_VARIANCE = 4
 FLINTS_FORCE_FALLBACK = 256  # testing aid: mixed plans re-solve every point in FP64
 ST_NUGGET, ST_FALLBACK, ST_WINDOW, ST_FAILED, ST_POLE = 1, 2, 4, 8, 16

@@ -111,8 +111,10 @@ int flints_plan(flints_plan_t *out, int64_t nside, int lmax, const double *cl, c
     if (12 * nside * nside < K) return fail(FLINTS_EINVAL, "flints_plan: K exceeds the pixel count");
     if (precision != FLINTS_FP64 && precision != FLINTS_MIXED)
         return fail(FLINTS_EINVAL, "flints_plan: precision must be FLINTS_FP64 or FLINTS_MIXED");
-    if (flags & ~(unsigned)(FLINTS_NO_VARIANCE | FLINTS_FORCE_FALLBACK))
+    if (flags & ~(unsigned)(FLINTS_ROTATE_TO_TARGET | FLINTS_NO_VARIANCE | FLINTS_FORCE_FALLBACK))
         return fail(FLINTS_EINVAL, "flints_plan: unknown flag bits 0x%x", flags);
+    if ((flags & FLINTS_ROTATE_TO_TARGET) && spin != 2)
+        return fail(FLINTS_EINVAL, "flints_plan: FLINTS_ROTATE_TO_TARGET applies to spin-2 plans");
     for (int l = 0; l <= lmax; ++l) {
         if (!std::isfinite(cl[l]) || (spin == 2 && cl_bb && !std::isfinite(cl_bb[l])))
             return fail(FLINTS_EINVAL, "flints_plan: non-finite spectrum value at l = %d", l);
@@ -262,6 +264,7 @@ static int run(flints_plan_t p, int64_t nside_tgt, int64_t first, int64_t count,
     a.out = out;
     a.var = (p->flags & FLINTS_NO_VARIANCE) ? nullptr : var;
     a.force_fallback = (p->flags & FLINTS_FORCE_FALLBACK) ? 1 : 0;
+    a.rotate = (p->flags & FLINTS_ROTATE_TO_TARGET) ? 1 : 0;
     a.nside_tgt = nside_tgt;
     a.status = status;
     a.stencil = stencil;
@@ -409,6 +412,7 @@ int flints_batch_stage(flints_batch_t b, const flints_job *jobs, int n, int tile
         a.out = j.out;
         a.var = (p->flags & FLINTS_NO_VARIANCE) ? nullptr : j.var;
         a.force_fallback = (p->flags & FLINTS_FORCE_FALLBACK) ? 1 : 0;
+        a.rotate = (p->flags & FLINTS_ROTATE_TO_TARGET) ? 1 : 0;
         a.status = j.status;
         a.stencil = nullptr;
         a.tab.c64 = p->d_c64;

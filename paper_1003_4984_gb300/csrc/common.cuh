@@ -290,6 +290,7 @@ struct LensArgs {
     unsigned long long *counters;  // points, nugget, fallback, window, failed
     int force_fallback;            // discard double-float solves (testing aid)
     int64_t nside_tgt;             // > 0: targets are the pixel centres of this grid (no deflection)
+    int rotate;                    // spin 2: return P in the frame at n instead of n'
 };
 
 // Launch shape chosen by the caller or the autotuner (0 = library default).

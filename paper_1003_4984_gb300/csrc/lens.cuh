@@ -42,6 +42,7 @@ struct Shape {
 
 struct PointA {
     double x, y, z, s, cph, sph, phi;
+    double rot_re, rot_im;  // spin 2: parallel-transport phase from the frame at n' to the frame at n
     int64_t ic;
     int flags;
     float zf, sf, phif;  // FP32 copies for the candidate-range arithmetic
@@ -633,6 +634,25 @@ __device__ __forceinline__ void process_tile(const LensArgs &a, int R_rings, int
                 P.flags |= FLINTS_ST_POLE;
             }
             P.phi = atan2(y, x);
+            P.rot_re = 1.0;
+            P.rot_im = 0.0;
+            if (SPIN == 2 && a.rotate && dl > 0.0) {
+                // P(n) = P(n') exp(2i(a_nn' - a_n'n)) with a_uv the angle at u, from e_theta
+                // towards e_phi, of the geodesic towards v: the polarisation parallel-
+                // transported back along the deflection.  At n the direction is
+                // (d_theta, d_phi) itself; at n' it is (n . e_theta(n'), n . e_phi(n')).
+                const double w1r = dd.x, w1i = dd.y;
+                const double cq = P.cph, sq = P.sph;
+                const double w2r = nx * z * cq + ny * z * sq - nz * s, w2i = ny * cq - nx * sq;
+                const double a1r = w1r * w1r - w1i * w1i, a1i = 2.0 * w1r * w1i;
+                const double a2r = w2r * w2r - w2i * w2i, a2i = 2.0 * w2r * w2i;
+                const double n1 = w1r * w1r + w1i * w1i, n2 = w2r * w2r + w2i * w2i;
+                if (n1 > 0.0 && n2 > 0.0) {
+                    const double inv = 1.0 / (n1 * n2);
+                    P.rot_re = (a1r * a2r + a1i * a2i) * inv;  // a1 conj(a2)
+                    P.rot_im = (a1i * a2r - a1r * a2i) * inv;
+                }
+            }
             P.zf = (float)z;
             P.sf = (float)s;
             P.phif = (float)P.phi;
@@ -971,7 +991,8 @@ __device__ __forceinline__ void process_tile(const LensArgs &a, int R_rings, int
             if (SPIN == 0) {
                 a.out[p] = vre;
             } else {
-                reinterpret_cast<double2 *>(a.out)[p] = make_double2(vre, vim);
+                reinterpret_cast<double2 *>(a.out)[p] =
+                    make_double2(vre * P.rot_re - vim * P.rot_im, vre * P.rot_im + vim * P.rot_re);
             }
             if (a.var) a.var[p] = a.xi0 * vrel;
             if (a.status) a.status[p] = (uint8_t)flags;

@@ -169,6 +169,31 @@ def test_spin2_sky_parity(fl, torch, precision, K):
     assert parity_metric(to_host(var), ref.variance, x0) <= TOL[precision]
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_spin2_rotation_to_target_frame(fl, torch, precision):
+    # FLINTS_ROTATE_TO_TARGET: P returned in the frame at n (parallel transport back
+    # along the deflection), against the oracle's rotated output
+    nside, lmax, K = 32, 64, 32
+    cl = wl.cl_ee(lmax, 50.0)
+    P = sht.synth_map(nside, lmax, wl.draw_alm(cl, 44), spin=2)
+    m = np.ascontiguousarray(np.stack([P.real, P.imag], axis=1))
+    npix = hp.npix(nside)
+    defl = wl.random_deflection(npix, 45) * 20
+    tab, x0, _, _ = oracle_table(cl, None, 2, K, nside)
+    ref = kr.lens(nside, K, 2, m, defl, np.arange(npix), tab, x0, rotate=True)
+    plain = kr.lens(nside, K, 2, m, defl, np.arange(npix), tab, x0)
+    sigma = float(np.sqrt(np.mean(P.real ** 2 + P.imag ** 2)))
+    assert parity_metric(ref.value, plain.value, sigma) > 1e-4  # the rotation is not negligible here
+    plan = fl.Plan(nside, cl, spin=2, K=K, precision=precision, flags=fl.FLINTS_ROTATE_TO_TARGET)
+    out = torch.empty((npix, 2), dtype=torch.float64, device="cuda")
+    plan.lens_full(torch.from_numpy(m).cuda(), torch.from_numpy(defl).cuda(), out)
+    torch.cuda.synchronize()
+    v = to_host(out)
+    assert parity_metric(v[:, 0] + 1j * v[:, 1], ref.value, sigma) <= TOL[precision]
+    with pytest.raises(fl.FlintsError):
+        fl.Plan(nside, wl.cl_tt(lmax, 50.0), spin=0, K=K, flags=fl.FLINTS_ROTATE_TO_TARGET)
+
+
 @pytest.mark.parametrize("K", [16, 24, 48])
 def test_spin0_all_stencil_sizes(fl, torch, K):
     nside, lmax = 32, 64

@@ -280,3 +280,43 @@ def test_supersampling_error_statistics():
     pred = math.sqrt(np.mean(res.variance)) / np.std(m)
     meas = math.sqrt(np.mean((res.value - truth) ** 2)) / np.std(m)
     assert 0.85 < meas / pred < 1.15
+
+
+# ------------------------------------- rotation to the target frame (Sec. 3.1)
+def _rodrigues(v, axis, ang):
+    k = axis / np.linalg.norm(axis, axis=-1, keepdims=True)
+    c, s = np.cos(ang)[..., None], np.sin(ang)[..., None]
+    return v * c + np.cross(k, v) * s + k * np.sum(k * v, axis=-1, keepdims=True) * (1 - c)
+
+
+def test_transport_phase_matches_rotation_along_the_geodesic():
+    # Parallel transport along a great circle is the rotation about that circle's
+    # axis taking n' to n.  A polarisation of orientation psi at n' (from e_theta
+    # towards e_phi, P = |P| exp(2i psi)) arrives at n with orientation chi; the
+    # oracle's rotation must give exp(2i chi) = exp(2i psi) pair_phase(n, n').
+    n = RNG.normal(size=(400, 3))
+    n /= np.linalg.norm(n, axis=1)[:, None]
+    for scale in (1e-4, 3e-3, 0.2):
+        defl = RNG.normal(size=(400, 2)) * scale
+        e_th, e_ph = kr.local_basis(n)
+        dl = np.linalg.norm(defl, axis=1)
+        npr = np.cos(dl)[:, None] * n + (np.sinc(dl / np.pi)[:, None]) * (defl[:, :1] * e_th + defl[:, 1:] * e_ph)
+        psi = RNG.uniform(0, np.pi, 400)
+        et2, ep2 = kr.local_basis(npr)
+        u = np.cos(psi)[:, None] * et2 + np.sin(psi)[:, None] * ep2
+        ang = np.arccos(np.clip(np.sum(n * npr, axis=1), -1, 1))
+        ut = _rodrigues(u, np.cross(npr, n), ang)
+        chi = np.arctan2(np.sum(ut * e_ph, axis=1), np.sum(ut * e_th, axis=1))
+        got = np.exp(2j * psi) * kr.pair_phase(n, npr)
+        np.testing.assert_allclose(got, np.exp(2j * chi), atol=1e-10)
+
+
+def test_transport_along_a_meridian_keeps_the_frame():
+    # a deflection along e_theta moves along the meridian: e_theta is transported
+    # onto e_theta, so the rotation is the identity
+    nside = 16
+    pix = np.arange(hp.npix(nside))
+    defl = np.zeros((pix.size, 2))
+    defl[:, 0] = RNG.normal(size=pix.size) * 1e-2
+    tv = kr.displace(nside, pix, defl)
+    np.testing.assert_allclose(kr.pair_phase(hp.pix2vec(nside, pix), tv), 1.0, atol=1e-12)
