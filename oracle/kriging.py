@@ -239,14 +239,61 @@ def pair_phase(va: np.ndarray, vb: np.ndarray) -> np.ndarray:
     return np.where(np.isfinite(ph), ph, 1.0 + 0.0j)
 
 
+def pseudo_phase(va: np.ndarray, vb: np.ndarray) -> np.ndarray:
+    """Phase of the pseudo-covariance <P(va) P(vb)> relative to xi-: exp(2i (a_ab + a_ba)).
+
+    Coincident points have xi-(0) = 0; their phase is set to 0."""
+    ph = phase2(va, vb) * phase2(vb, va)
+    return np.where(np.isfinite(ph), ph, 0.0 + 0.0j)
+
+
+def real_form(G: np.ndarray, C: np.ndarray) -> np.ndarray:
+    """Twice the covariance of the real vector (Q_1..Q_K, U_1..U_K) against
+    (Q_1..Q_M, U_1..U_M), from the Hermitian covariance G = <P P^H> and the
+    pseudo-covariance C = <P P^T> of P = Q + iU (blocks (..., K, M) -> (..., 2K, 2M)):
+        2<Q Q> = Re(G + C),  2<Q U> = Im(C - G),  2<U Q> = Im(G + C),  2<U U> = Re(G - C)."""
+    top = np.concatenate([(G + C).real, (C - G).imag], axis=-1)
+    bot = np.concatenate([(G + C).imag, (G - C).real], axis=-1)
+    return np.concatenate([top, bot], axis=-2)
+
+
+def _estimate_augmented(X, targets, y, S, c, f_minus, T, t0, xi_zero, eps):
+    """Widely linear (augmented) spin-2 estimate: the Gaussian conditional mean of
+    (Q, U) at the target given (Q_i, U_i), using both xi+ (through <P P^*>) and xi-
+    (through <P P>), as a 2K x 2K real system."""
+    K = X.shape[1]
+    G = S * pair_phase(X[:, :, None, :], X[:, None, :, :])
+    G[:, np.arange(K), np.arange(K)] = 1.0
+    C = f_minus(T.reshape(-1)).reshape(T.shape) * pseudo_phase(X[:, :, None, :], X[:, None, :, :])
+    C[:, np.arange(K), np.arange(K)] = 0.0
+    tb = np.broadcast_to(targets[:, None, :], X.shape)
+    g0 = c * pair_phase(X, tb)            # <P_i P_0^*> / xi+(0)
+    c0 = f_minus(t0) * pseudo_phase(X, tb)  # <P_i P_0> / xi+(0)
+    A = real_form(G, C)
+    B = real_form(g0[:, :, None], c0[:, :, None])  # (batch, 2K, 2): columns for Q_0 and U_0
+    L, nug = factor_with_nugget(A, eps)
+    ZQ = forward_solve(L, B[:, :, 0])
+    ZU = forward_solve(L, B[:, :, 1])
+    zx = forward_solve(L, np.concatenate([y.real, y.imag], axis=1))
+    val = np.sum(ZQ * zx, axis=1) + 1j * np.sum(ZU * zx, axis=1)
+    var = xi_zero * (1.0 - 0.5 * (np.sum(ZQ * ZQ, axis=1) + np.sum(ZU * ZU, axis=1)))
+    return val, var, nug
+
+
 def estimate(nside: int, spin: int, maps: np.ndarray, targets: np.ndarray, idx: np.ndarray,
-             f_plus, xi_zero: float, eps: float = EPS_NUGGET):
-    """Steps 3-5 on a given stencil ``idx`` (B, K): (values, variances, nuggets)."""
+             f_plus, xi_zero: float, eps: float = EPS_NUGGET, f_minus=None):
+    """Steps 3-5 on a given stencil ``idx`` (B, K): (values, variances, nuggets).
+
+    ``f_minus`` (spin 2): xi-/xi+(0); when given, the augmented estimator is used."""
     K = idx.shape[1]
     X = hp.pix2vec(nside, idx)  # (B, K, 3)
     T = _chord2(X[:, :, None, :], X[:, None, :, :])
     S = f_plus(T.reshape(-1)).reshape(T.shape)
-    c = f_plus(_chord2(targets[:, None, :], X))
+    t0 = _chord2(targets[:, None, :], X)
+    c = f_plus(t0)
+    if spin == 2 and f_minus is not None:
+        y = maps[idx, 0] + 1j * maps[idx, 1]
+        return _estimate_augmented(X, targets, y, S, c, f_minus, T, t0, xi_zero, eps)
     if spin == 0:
         y = maps[idx]
         L, nug = factor_with_nugget(S, eps)
@@ -265,12 +312,13 @@ def estimate(nside: int, spin: int, maps: np.ndarray, targets: np.ndarray, idx: 
 
 
 def interpolate(nside: int, K: int, spin: int, maps: np.ndarray, targets: np.ndarray,
-                f_plus, xi_zero: float, eps: float = EPS_NUGGET, batch: int = 4096) -> Result:
+                f_plus, xi_zero: float, eps: float = EPS_NUGGET, batch: int = 4096, f_minus=None) -> Result:
     """Kriging at unit vectors ``targets`` (P, 3) from a RING map.
 
     ``maps``: (Npix,) real for spin 0; (Npix, 2) (Q, U) for spin 2.
     ``f_plus``: callable t -> xi(t)/xi(0) (spin 0) or xi+(t)/xi+(0) (spin 2),
     either an ``xi.HermiteTable`` (tabulated mode) or a direct evaluation.
+    ``f_minus`` (spin 2, optional): xi-(t)/xi+(0); selects the augmented estimator.
     """
     P = targets.shape[0]
     vals = np.empty(P, dtype=np.float64 if spin == 0 else np.complex128)
@@ -281,7 +329,7 @@ def interpolate(nside: int, K: int, spin: int, maps: np.ndarray, targets: np.nda
     for b0 in range(0, P, batch):
         tv = targets[b0:b0 + batch]
         idx, key = knn(nside, tv, K)
-        v, s2, nug = estimate(nside, spin, maps, tv, idx, f_plus, xi_zero, eps)
+        v, s2, nug = estimate(nside, spin, maps, tv, idx, f_plus, xi_zero, eps, f_minus)
         vals[b0:b0 + batch] = v
         var[b0:b0 + batch] = s2
         sten[b0:b0 + batch] = idx
@@ -291,7 +339,7 @@ def interpolate(nside: int, K: int, spin: int, maps: np.ndarray, targets: np.nda
 
 
 def lens(nside: int, K: int, spin: int, maps: np.ndarray, defl: np.ndarray, pix: np.ndarray,
-         f_plus, xi_zero: float, eps: float = EPS_NUGGET, rotate: bool = False) -> Result:
+         f_plus, xi_zero: float, eps: float = EPS_NUGGET, rotate: bool = False, f_minus=None) -> Result:
     """Lensed values at target pixels ``pix`` (Born remap T(n + d(n)), Sec. 3.1).
 
     ``rotate`` (spin 2): return P in the frame at the target pixel n rather than at
@@ -299,7 +347,7 @@ def lens(nside: int, K: int, spin: int, maps: np.ndarray, defl: np.ndarray, pix:
     geodesic from n' to n, which multiplies it by pair_phase(n, n')."""
     pix = np.asarray(pix, dtype=np.int64)
     tv = displace(nside, pix, np.asarray(defl, dtype=np.float64))
-    res = interpolate(nside, K, spin, maps, tv, f_plus, xi_zero, eps)
+    res = interpolate(nside, K, spin, maps, tv, f_plus, xi_zero, eps, f_minus=f_minus)
     if rotate and spin == 2:
         res.value = res.value * pair_phase(hp.pix2vec(nside, pix), tv)
     return res

@@ -320,3 +320,111 @@ def test_transport_along_a_meridian_keeps_the_frame():
     defl[:, 0] = RNG.normal(size=pix.size) * 1e-2
     tv = kr.displace(nside, pix, defl)
     np.testing.assert_allclose(kr.pair_phase(hp.pix2vec(nside, pix), tv), 1.0, atol=1e-12)
+
+
+# ----------------------------------------- augmented (widely linear) spin 2
+def _sY(s, ell, m, v):
+    th = np.arctan2(np.hypot(v[:, 0], v[:, 1]), v[:, 2])
+    ph = np.arctan2(v[:, 1], v[:, 0])
+    # Appendix A: sY_lm = (-1)^s sqrt((2l+1)/4pi) e^{i m phi} d^l_{m,-s}(theta)
+    return (-1) ** s * math.sqrt((2 * ell + 1) / (4 * math.pi)) * np.exp(1j * m * ph) * wigner_d(ell, m, -s, th)
+
+
+@pytest.mark.parametrize("ell", [2, 3, 5, 8])
+def test_spin2_pseudo_phase_by_addition_theorem(ell):
+    # <P_a P_b> = sum_l (C^EE - C^BB) sum_m 2Y_lm(a) (-2Y_lm(b))^* (P = -sum (E + iB) 2Y with
+    # real E, B fields); for one l this must equal (2l+1)/4pi d^l_{2,-2}(beta) pseudo_phase(a, b)
+    a = RNG.normal(size=(40, 3))
+    a /= np.linalg.norm(a, axis=1)[:, None]
+    b = a + RNG.normal(size=(40, 3)) * 0.3
+    b /= np.linalg.norm(b, axis=1)[:, None]
+    corr = sum(_sY(2, ell, m, a) * np.conj(_sY(-2, ell, m, b)) for m in range(-ell, ell + 1))
+    beta = 2 * np.arcsin(np.linalg.norm(a - b, axis=1) / 2)
+    model = (2 * ell + 1) / (4 * math.pi) * wigner_d(ell, 2, -2, beta) * kr.pseudo_phase(a, b)
+    np.testing.assert_allclose(corr, model, atol=1e-13)
+
+
+def _aug_inputs(n_pts, K, spread, seed):
+    rng = np.random.default_rng(seed)
+    t = rng.normal(size=(n_pts, 3))
+    t /= np.linalg.norm(t, axis=1)[:, None]
+    X = t[:, None, :] + rng.normal(size=(n_pts, K, 3)) * spread
+    X /= np.linalg.norm(X, axis=2)[:, :, None]
+    y = rng.normal(size=(n_pts, K)) + 1j * rng.normal(size=(n_pts, K))
+    return t, X, y
+
+
+def test_augmented_real_form_matches_complex_augmented_solve():
+    # library special case: the widely linear estimator written in the complex augmented
+    # form z = (P, P^*), R = [[G, C], [C^*, G^*]], w = R^-1 E[z P_0^*], solved by numpy,
+    # against the oracle's 2K x 2K real form (nugget n on the diagonal of G in both)
+    lmax, K = 40, 6
+    cl = wl.cl_ee(lmax, 30.0)
+    bb = 0.3 * cl
+    nodes_t = 0.2
+    fp, fm, x0 = xi.spin2_tables(cl, bb, nodes_t, 2048)
+    t, X, y = _aug_inputs(30, K, 0.05, 5)
+    T = np.sum((X[:, :, None, :] - X[:, None, :, :]) ** 2, axis=-1)
+    t0 = np.sum((t[:, None, :] - X) ** 2, axis=-1)
+    S = fp(T.reshape(-1)).reshape(T.shape)
+    val, var, nug = kr._estimate_augmented(X, t, y, S, fp(t0), fm, T, t0, x0, kr.EPS_NUGGET)
+    for p in range(t.shape[0]):
+        G = np.empty((K, K), complex)
+        C = np.empty((K, K), complex)
+        for i in range(K):
+            for j in range(K):
+                if i == j:
+                    G[i, j], C[i, j] = 1.0 + nug[p], 0.0
+                else:
+                    G[i, j] = fp(np.array([T[p, i, j]]))[0] * kr.pair_phase(X[p, i], X[p, j])
+                    C[i, j] = fm(np.array([T[p, i, j]]))[0] * kr.pseudo_phase(X[p, i], X[p, j])
+        g0 = fp(t0[p]) * kr.pair_phase(X[p], np.broadcast_to(t[p], X[p].shape))
+        c0 = fm(t0[p]) * kr.pseudo_phase(X[p], np.broadcast_to(t[p], X[p].shape))
+        R = np.block([[G, C], [np.conj(C), np.conj(G)]])
+        pv = np.concatenate([g0, np.conj(c0)])
+        w = np.linalg.solve(R, pv)
+        z = np.concatenate([y[p], np.conj(y[p])])
+        assert abs(np.vdot(w, z) - val[p]) < 1e-9 * max(1.0, abs(val[p]))
+        assert abs(x0 * (1.0 - np.vdot(pv, w).real) - var[p]) < 1e-9 * x0
+
+
+def test_augmented_equals_hermitian_without_xi_minus():
+    # C^BB = C^EE makes xi- vanish: the augmented estimator reduces to the paper's
+    # Hermitian one (same nugget rule, the real form of G + nI has G's spectrum)
+    nside, lmax, K = 32, 64, 16
+    cl = wl.cl_ee(lmax, 50.0)
+    P = sht.synth_map(nside, lmax, wl.draw_alm(cl, 31), spin=2, blm=wl.draw_alm(cl, 32))
+    qu = np.stack([P.real, P.imag], axis=1)
+    pix = wl.sample_pixels(hp.npix(nside), 500, 33)
+    defl = wl.random_deflection(pix.size, 34) * 4
+    tmax = 4 * (2.0 * math.sqrt(K / 3.0) / nside) ** 2 * 1.5
+    tp, tm, x0 = xi.spin2_tables(cl, cl, tmax, 1024)
+    assert np.max(np.abs(tm.f)) < 1e-15
+    herm = kr.lens(nside, K, 2, qu, defl, pix, tp, x0)
+    aug = kr.lens(nside, K, 2, qu, defl, pix, tp, x0, f_minus=tm)
+    scale = np.sqrt(np.mean(np.abs(herm.value) ** 2))
+    assert np.max(np.abs(aug.value - herm.value)) < 1e-12 * scale
+    assert np.max(np.abs(aug.variance - herm.variance)) < 1e-12 * x0
+
+
+def test_augmented_error_statistics_with_pure_e_modes():
+    # B = 0 (xi- = xi+ at l >> 1 scales): the augmented estimator is the exact Gaussian
+    # conditional, its errors match its predicted variance and beat the Hermitian one
+    nside, lmax, K = 64, 128, 16
+    cl = wl.cl_ee(lmax, 100.0)
+    alm = wl.draw_alm(cl, 21)
+    P = sht.synth_map(nside, lmax, alm, spin=2)
+    qu = np.stack([P.real, P.imag], axis=1)
+    pix = wl.sample_pixels(hp.npix(nside), 4000, 22)
+    defl = wl.random_deflection(pix.size, 23)
+    tmax = 4 * (2.0 * math.sqrt(K / 3.0) / nside) ** 2 * 1.5
+    tp, tm, x0 = xi.spin2_tables(cl, None, tmax, 1024)
+    herm = kr.lens(nside, K, 2, qu, defl, pix, tp, x0)
+    aug = kr.lens(nside, K, 2, qu, defl, pix, tp, x0, f_minus=tm)
+    truth = sht.synth_points(lmax, alm, aug.target, spin=2)
+    r = np.abs(aug.value - truth) ** 2 / aug.variance
+    assert 0.85 < np.mean(r) < 1.15
+    e_aug = np.mean(np.abs(aug.value - truth) ** 2)
+    e_herm = np.mean(np.abs(herm.value - truth) ** 2)
+    assert e_aug < 0.9 * e_herm
+    assert np.all(aug.variance <= herm.variance * (1 + 1e-9))
