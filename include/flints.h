@@ -62,6 +62,14 @@ enum { FLINTS_FP64 = 0, FLINTS_MIXED = 1 };
 
 /* plan flags */
 enum {
+    /* spin 2: augmented (widely linear) estimator.  The paper's spin-2 kriging
+     * (Sec. 2.2) conditions on the Hermitian covariance <P_i P_j^*> (xi+) alone;
+     * with this flag (Q, U) at the target are the Gaussian conditional mean given
+     * (Q_i, U_i) of the stencil, which also uses the pseudo-covariance
+     * <P_i P_j> = xi-(beta) exp(2i(a_ij + a_ji)): a 2K x 2K real system.  Equal to
+     * the default when C^BB = C^EE (xi- = 0); strictly more precise otherwise.
+     * Not accepted by the batch entry points. */
+    FLINTS_SPIN2_AUGMENTED = 1u,
     /* spin 2: return P in the frame at the target pixel n instead of the frame at
      * the displaced direction n': P(n') times exp(2i(a_nn' - a_n'n)), a_uv the
      * angle at u (from e_theta towards e_phi) of the geodesic towards v, i.e. the

@@ -20,6 +20,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "flints.h")
 
 FLINTS_FP64 = 0
 FLINTS_MIXED = 1
+FLINTS_SPIN2_AUGMENTED = 1  # spin 2: widely linear estimator with xi+ and xi-
 FLINTS_ROTATE_TO_TARGET = 2  # spin 2: P in the frame at n, not n'
 FLINTS_NO_VARIANCE = 4
 FLINTS_FORCE_FALLBACK = 256  # testing aid: mixed plans re-solve every point in FP64

@@ -21,6 +21,8 @@ cudaError_t launch_lens_spin0(int K, int precision, const LensArgs &a, int R_rin
                               cudaStream_t st);
 cudaError_t launch_lens_spin2(int K, int precision, const LensArgs &a, int R_rings, const LaunchCfg &cfg,
                               cudaStream_t st);
+cudaError_t launch_lens_spin2a(int K, int precision, const LensArgs &a, int R_rings, const LaunchCfg &cfg,
+                               cudaStream_t st);
 
 int device_sm_count() {
     int dev = 0, n = 0;
@@ -39,8 +41,10 @@ size_t device_smem_optin() {
 
 cudaError_t launch_lens(int spin, int K, int precision, const LensArgs &a, int R_rings, const LaunchCfg &cfg,
                         cudaStream_t st) {
-    return spin == 0 ? launch_lens_spin0(K, precision, a, R_rings, cfg, st)
-                     : launch_lens_spin2(K, precision, a, R_rings, cfg, st);
+    if (spin == 0) return launch_lens_spin0(K, precision, a, R_rings, cfg, st);
+    if (spin == 2) return launch_lens_spin2(K, precision, a, R_rings, cfg, st);
+    if (spin == SPIN2_AUG) return launch_lens_spin2a(K, precision, a, R_rings, cfg, st);
+    return cudaErrorInvalidValue;
 }
 }  // namespace flints
 
@@ -54,8 +58,8 @@ struct flints_plan_s {
     double t_max, h, inv_h, xi0, r, r2;
     int n, R_rings;
     double *d_cl, *d_clbb, *d_f, *d_g, *d_fm, *d_gm;
-    Coef64 *d_c64;
-    float4 *d_c32;
+    Coef64 *d_c64, *d_cm64;  // xi+ (spin 0: xi) and, spin 2, xi- interpolation coefficients
+    float4 *d_c32, *d_cm32;
     unsigned long long *d_counters;
     int64_t points;
     LaunchCfg cfg;
@@ -92,6 +96,8 @@ static void free_plan_memory(flints_plan_s *p) {
     cudaFree(p->d_gm);
     cudaFree(p->d_c64);
     cudaFree(p->d_c32);
+    cudaFree(p->d_cm64);
+    cudaFree(p->d_cm32);
     cudaFree(p->d_counters);
 }
 
@@ -111,8 +117,11 @@ int flints_plan(flints_plan_t *out, int64_t nside, int lmax, const double *cl, c
     if (12 * nside * nside < K) return fail(FLINTS_EINVAL, "flints_plan: K exceeds the pixel count");
     if (precision != FLINTS_FP64 && precision != FLINTS_MIXED)
         return fail(FLINTS_EINVAL, "flints_plan: precision must be FLINTS_FP64 or FLINTS_MIXED");
-    if (flags & ~(unsigned)(FLINTS_ROTATE_TO_TARGET | FLINTS_NO_VARIANCE | FLINTS_FORCE_FALLBACK))
+    if (flags & ~(unsigned)(FLINTS_SPIN2_AUGMENTED | FLINTS_ROTATE_TO_TARGET | FLINTS_NO_VARIANCE |
+                            FLINTS_FORCE_FALLBACK))
         return fail(FLINTS_EINVAL, "flints_plan: unknown flag bits 0x%x", flags);
+    if ((flags & FLINTS_SPIN2_AUGMENTED) && spin != 2)
+        return fail(FLINTS_EINVAL, "flints_plan: FLINTS_SPIN2_AUGMENTED applies to spin-2 plans");
     if ((flags & FLINTS_ROTATE_TO_TARGET) && spin != 2)
         return fail(FLINTS_EINVAL, "flints_plan: FLINTS_ROTATE_TO_TARGET applies to spin-2 plans");
     for (int l = 0; l <= lmax; ++l) {
@@ -184,6 +193,10 @@ int flints_plan(flints_plan_t *out, int64_t nside, int lmax, const double *cl, c
     ALLOC(p->d_gm, nn * sizeof(double));
     ALLOC(p->d_c64, (size_t)p->n * sizeof(Coef64));
     ALLOC(p->d_c32, (size_t)p->n * 2 * sizeof(float4));
+    if (spin == 2) {
+        ALLOC(p->d_cm64, (size_t)p->n * sizeof(Coef64));
+        ALLOC(p->d_cm32, (size_t)p->n * 2 * sizeof(float4));
+    }
     ALLOC(p->d_counters, CNT_N * sizeof(unsigned long long));
 #undef ALLOC
     auto bail = [&](cudaError_t err, const char *what) {
@@ -215,7 +228,7 @@ int flints_plan(flints_plan_t *out, int64_t nside, int lmax, const double *cl, c
     p->xi0 = xi0;
     if ((e = finish_table(p->d_f, p->d_g, p->n, p->h, xi0, p->d_c64, p->d_c32, st)) != cudaSuccess)
         return bail(e, "flints_plan: table coefficients");
-    if (spin == 2 && (e = finish_table(p->d_fm, p->d_gm, p->n, p->h, xi0, nullptr, nullptr, st)) != cudaSuccess)
+    if (spin == 2 && (e = finish_table(p->d_fm, p->d_gm, p->n, p->h, xi0, p->d_cm64, p->d_cm32, st)) != cudaSuccess)
         return bail(e, "flints_plan: xi- table");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return bail(e, "flints_plan: table coefficients");
     *out = p;
@@ -275,10 +288,14 @@ static int run(flints_plan_t p, int64_t nside_tgt, int64_t first, int64_t count,
     a.tab.inv_h_hi = (float)p->inv_h;
     a.tab.inv_h_lo = (float)(p->inv_h - (double)a.tab.inv_h_hi);
     a.tab.n = p->n;
+    a.tabm = a.tab;
+    a.tabm.c64 = p->d_cm64;
+    a.tabm.c32 = p->d_cm32;
     a.xi0 = p->xi0;
     a.r2 = p->r2;
     a.counters = p->d_counters;
-    cudaError_t e = launch_lens(p->spin, p->K, p->precision, a, p->R_rings, p->cfg, (cudaStream_t)stream);
+    const int mode = (p->flags & FLINTS_SPIN2_AUGMENTED) ? SPIN2_AUG : p->spin;
+    cudaError_t e = launch_lens(mode, p->K, p->precision, a, p->R_rings, p->cfg, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "lens kernel launch");
     p->points += count;
     return FLINTS_OK;
@@ -395,6 +412,8 @@ int flints_batch_stage(flints_batch_t b, const flints_job *jobs, int n, int tile
         flints_plan_s *p = j.plan;
         if (!p) return fail(FLINTS_EINVAL, "job %d: plan is NULL", i);
         if (p->device != b->device) return fail(FLINTS_EINVAL, "job %d: plan and batch on different devices", i);
+        if (p->flags & FLINTS_SPIN2_AUGMENTED)
+            return fail(FLINTS_EINVAL, "job %d: augmented spin-2 plans run through the single-plan entry points", i);
         const int64_t npix = 12 * p->nside * p->nside;
         if (j.first < 0 || j.count < 0 || j.first > npix || j.count > npix - j.first)
             return fail(FLINTS_EINVAL, "job %d: target range outside the map", i);

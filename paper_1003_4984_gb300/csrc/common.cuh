@@ -291,7 +291,11 @@ struct LensArgs {
     int force_fallback;            // discard double-float solves (testing aid)
     int64_t nside_tgt;             // > 0: targets are the pixel centres of this grid (no deflection)
     int rotate;                    // spin 2: return P in the frame at n instead of n'
+    TableDev tabm;                 // spin 2: xi-/xi+(0) on the same grid (augmented estimator)
 };
+
+// Internal kernel mode of the augmented (widely linear) spin-2 estimator.
+constexpr int SPIN2_AUG = 3;
 
 // Launch shape chosen by the caller or the autotuner (0 = library default).
 // Targets per warp tile (the displacement phase runs one target per lane).

@@ -59,11 +59,13 @@ struct RingRec {
 
 template <int K, int SPIN, class R>
 struct WarpSmem {
-    using Elem = typename std::conditional<SPIN == 0, typename Ops<R>::T, Cx<typename Ops<R>::T>>::type;
+    using Elem = typename std::conditional<SPIN == 2, Cx<typename Ops<R>::T>, typename Ops<R>::T>::type;
     static constexpr int NSLOT = Shape<K>::NSLOT;
     // packed lower triangle of S + n I (row i starts at i(i+1)/2), then the two
-    // bordered right-hand-side rows (c and y), K entries each
-    static constexpr int MAT = K * (K + 1) / 2 + 2 * K;
+    // bordered right-hand-side rows (c and y), K entries each; the augmented
+    // spin-2 system is real, 2K x 2K, with three bordered rows (Q and U
+    // cross-covariances of the target, and the data)
+    static constexpr int MAT = SPIN == SPIN2_AUG ? (2 * K) * (2 * K + 1) / 2 + 3 * (2 * K) : K * (K + 1) / 2 + 2 * K;
     using T = typename Ops<R>::T;
     PointA pts[MAX_TILE_POINTS];
     // neighbour offsets X_i - n', and neighbour z, sin(theta), cos(phi), sin(phi),
@@ -323,6 +325,140 @@ __device__ __forceinline__ Cx<df> transported_phase(Cx<df> a, Cx<df> b, const Ho
     return {df_addf(br, cr), df_addf(bi, ci)};
 }
 
+// Both spin-2 phases of the pair (i -> j), d = X_j - X_i: exp(2i(a_ij - a_ji)) of
+// the Hermitian covariance <P_i P_j^*> (as pair_phase) and exp(2i(a_ij + a_ji)) of
+// the pseudo-covariance <P_i P_j>.  With w_i = A1 + iB1 and w_j = A2 + iB2 the
+// projections of d on the local bases at both ends, they are
+// (w_i conj(w_j))^2 / |w_i w_j|^2 and (w_i w_j)^2 / |w_i w_j|^2.
+template <class R>
+__device__ __forceinline__ void pair_phases_pm(typename Ops<R>::T dx, typename Ops<R>::T dy, typename Ops<R>::T dz,
+                                               typename Ops<R>::T zi, typename Ops<R>::T si, typename Ops<R>::T ci,
+                                               typename Ops<R>::T sni, typename Ops<R>::T zj, typename Ops<R>::T sj,
+                                               typename Ops<R>::T cj, typename Ops<R>::T snj,
+                                               Cx<typename Ops<R>::T> &php, Cx<typename Ops<R>::T> &phm) {
+    using O = Ops<R>;
+    using T = typename O::T;
+    const T A1 = O::sub(O::mul(zi, O::add(O::mul(dx, ci), O::mul(dy, sni))), O::mul(si, dz));
+    const T B1 = O::sub(O::mul(dy, ci), O::mul(dx, sni));
+    const T A2 = O::sub(O::mul(zj, O::add(O::mul(dx, cj), O::mul(dy, snj))), O::mul(sj, dz));
+    const T B2 = O::sub(O::mul(dy, cj), O::mul(dx, snj));
+    const T aa = O::mul(A1, A2), bb = O::mul(B1, B2), ab = O::mul(A1, B2), ba = O::mul(B1, A2);
+    const T qpr = O::add(aa, bb), qpi = O::sub(ba, ab);  // w_i conj(w_j)
+    const T qmr = O::sub(aa, bb), qmi = O::add(ab, ba);  // w_i w_j
+    const T den = O::add(O::mul(qpr, qpr), O::mul(qpi, qpi));
+    if (!O::positive(den)) {  // coincident points
+        php = {O::from(1.0), O::zero()};
+        phm = {O::zero(), O::zero()};
+        return;
+    }
+    const T inv = O::rcp(den);
+    const T pri = O::mul(qpr, qpi), mri = O::mul(qmr, qmi);
+    php = {O::mul(O::sub(O::mul(qpr, qpr), O::mul(qpi, qpi)), inv), O::mul(O::add(pri, pri), inv)};
+    phm = {O::mul(O::sub(O::mul(qmr, qmr), O::mul(qmi, qmi)), inv), O::mul(O::add(mri, mri), inv)};
+}
+
+// Split left-looking Cholesky of an N x N packed lower triangle (row i starts
+// at i(i+1)/2) bordered by NB right-hand-side rows stored after it (row N + b
+// holds the conjugate of the b-th right-hand side); on return the bordered rows
+// hold conj(L^-1 conj(rhs)).  At column j the NROW - j active rows are spread
+// over 32/s lane groups of s lanes, s the largest power of two with
+// (NROW - j) s <= 32, and each group splits the dot product over k < j and
+// reduces it with shuffles.  Elem is real (Ops<R>::T) or complex (Cx<T>).
+// Returns false when a pivot is not positive.
+template <int N, int NB, class R, class Elem>
+__device__ __forceinline__ bool bordered_cholesky(Elem *mat, int lane) {
+    using O = Ops<R>;
+    using T = typename O::T;
+    constexpr bool CPLX = !std::is_same<Elem, T>::value;
+    constexpr int NROW = N + NB;
+    constexpr int NT = (NROW + 31) / 32;  // row slots per lane at s = 1
+    for (int j = 0; j < N; ++j) {
+        const int nrows = NROW - j;
+        int s = 1;
+        while ((s << 1) * nrows <= 32) s <<= 1;
+        const int g = 32 / s;
+        const int part = lane & (s - 1), grp = lane / s;
+        const Elem *Lj = mat + tri<N>(j, 0);
+        Elem srow[NT];
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            const int r = j + grp + t * g;
+            const bool act = r < NROW;
+            const int rr = act ? r : j;
+            const Elem *Lr = mat + tri<N>(rr, 0);
+            if constexpr (!CPLX) {
+                typename O::Acc acc = O::acc((part == 0 && act) ? Lr[j] : O::zero());
+                typename O::Acc acc2 = O::acc(O::zero());
+                if (act) {
+                    int k = part;
+                    for (; k + s < j; k += 2 * s) {  // two independent chains
+                        O::sub_prod(acc, Lr[k], Lj[k]);
+                        O::sub_prod(acc2, Lr[k + s], Lj[k + s]);
+                    }
+                    if (k < j) O::sub_prod(acc, Lr[k], Lj[k]);
+                }
+                T v = O::add_fast(O::val(acc), O::val(acc2));
+                for (int o = 1; o < s; o <<= 1) v = O::add_fast(v, O::shfl_xor(v, o));
+                srow[t] = v;
+            } else {
+                const Elem a0 = Lr[j];
+                typename O::Acc ar = O::acc((part == 0 && act) ? a0.re : O::zero());
+                typename O::Acc ai = O::acc((part == 0 && act) ? a0.im : O::zero());
+                typename O::Acc br = O::acc(O::zero()), bi = O::acc(O::zero());
+                if (act)
+                    for (int k = part; k < j; k += s) {  // real and imaginary parts in two chains each
+                        const Elem a = Lr[k], b = Lj[k];
+                        O::sub_prod(ar, a.re, b.re);
+                        O::sub_prod(br, a.im, b.im);
+                        O::sub_prod(ai, a.im, b.re);
+                        O::add_prod(bi, a.re, b.im);
+                    }
+                T vr = O::add_fast(O::val(ar), O::val(br)), vi = O::add_fast(O::val(ai), O::val(bi));
+                for (int o = 1; o < s; o <<= 1) {
+                    vr = O::add_fast(vr, O::shfl_xor(vr, o));
+                    vi = O::add_fast(vi, O::shfl_xor(vi, o));
+                }
+                srow[t].re = vr;
+                srow[t].im = vi;
+            }
+        }
+        // pivot: row j is held by lane 0 (group 0, part 0, t = 0)
+        T d;
+        if constexpr (!CPLX) {
+            d = O::shfl(srow[0], 0);
+        } else {
+            d = O::shfl(srow[0].re, 0);
+        }
+        if (!O::positive(d)) return false;
+        const T ljj = O::sqrt_(d);
+        const T il = O::rcp(ljj);
+        __syncwarp();
+        if (part == 0) {
+#pragma unroll
+            for (int t = 0; t < NT; ++t) {
+                const int r = j + grp + t * g;
+                if (r < NROW) {
+                    Elem v;
+                    if constexpr (!CPLX) {
+                        v = (r == j) ? ljj : O::mul(srow[t], il);
+                    } else {
+                        if (r == j) {
+                            v.re = ljj;
+                            v.im = O::zero();
+                        } else {
+                            v.re = O::mul(srow[t].re, il);
+                            v.im = O::mul(srow[t].im, il);
+                        }
+                    }
+                    mat[tri<N>(r, j)] = v;
+                }
+            }
+        }
+        __syncwarp();
+    }
+    return true;
+}
+
 // Returns false when a pivot of S + nugget I is not positive.
 
 //
@@ -436,91 +572,7 @@ __device__ bool solve_point(SM &sm, const PointA &P, int lane, double nugget, co
     }
     __syncwarp();
 
-    // ---- split left-looking Cholesky over the bordered rows
-    for (int j = 0; j < K; ++j) {
-        const int nrows = NROW - j;
-        int s = 1;
-        while ((s << 1) * nrows <= 32) s <<= 1;
-        const int g = 32 / s;
-        const int part = lane & (s - 1), grp = lane / s;
-        const Elem *Lj = mat + tri<K>(j, 0);
-        Elem srow[2];
-#pragma unroll
-        for (int t = 0; t < 2; ++t) {
-            const int r = j + grp + t * g;
-            const bool act = r < NROW;
-            const int rr = act ? r : j;
-            const Elem *Lr = mat + tri<K>(rr, 0);
-            if constexpr (SPIN == 0) {
-                typename O::Acc acc = O::acc((part == 0 && act) ? Lr[j] : O::zero());
-                typename O::Acc acc2 = O::acc(O::zero());
-                if (act) {
-                    int k = part;
-                    for (; k + s < j; k += 2 * s) {  // two independent chains
-                        O::sub_prod(acc, Lr[k], Lj[k]);
-                        O::sub_prod(acc2, Lr[k + s], Lj[k + s]);
-                    }
-                    if (k < j) O::sub_prod(acc, Lr[k], Lj[k]);
-                }
-                T v = O::add_fast(O::val(acc), O::val(acc2));
-                for (int o = 1; o < s; o <<= 1) v = O::add_fast(v, O::shfl_xor(v, o));
-                srow[t] = v;
-            } else {
-                const Elem a0 = Lr[j];
-                typename O::Acc ar = O::acc((part == 0 && act) ? a0.re : O::zero());
-                typename O::Acc ai = O::acc((part == 0 && act) ? a0.im : O::zero());
-                typename O::Acc br = O::acc(O::zero()), bi = O::acc(O::zero());
-                if (act)
-                    for (int k = part; k < j; k += s) {  // real and imaginary parts in two chains each
-                        const Elem a = Lr[k], b = Lj[k];
-                        O::sub_prod(ar, a.re, b.re);
-                        O::sub_prod(br, a.im, b.im);
-                        O::sub_prod(ai, a.im, b.re);
-                        O::add_prod(bi, a.re, b.im);
-                    }
-                T vr = O::add_fast(O::val(ar), O::val(br)), vi = O::add_fast(O::val(ai), O::val(bi));
-                for (int o = 1; o < s; o <<= 1) {
-                    vr = O::add_fast(vr, O::shfl_xor(vr, o));
-                    vi = O::add_fast(vi, O::shfl_xor(vi, o));
-                }
-                srow[t].re = vr;
-                srow[t].im = vi;
-            }
-        }
-        // pivot: row j is held by lane 0 (group 0, part 0, t = 0)
-        T d;
-        if constexpr (SPIN == 0) {
-            d = O::shfl(srow[0], 0);
-        } else {
-            d = O::shfl(srow[0].re, 0);
-        }
-        if (!O::positive(d)) return false;
-        const T ljj = O::sqrt_(d);
-        const T il = O::rcp(ljj);
-        __syncwarp();
-        if (part == 0) {
-#pragma unroll
-            for (int t = 0; t < 2; ++t) {
-                const int r = j + grp + t * g;
-                if (r < NROW) {
-                    Elem v;
-                    if constexpr (SPIN == 0) {
-                        v = (r == j) ? ljj : O::mul(srow[t], il);
-                    } else {
-                        if (r == j) {
-                            v.re = ljj;
-                            v.im = O::zero();
-                        } else {
-                            v.re = O::mul(srow[t].re, il);
-                            v.im = O::mul(srow[t].im, il);
-                        }
-                    }
-                    mat[tri<K>(r, j)] = v;
-                }
-            }
-        }
-        __syncwarp();
-    }
+    if (!bordered_cholesky<K, 2, R>(mat, lane)) return false;
     // ---- value = z_c^H z_y = sum_k row_K[k] conj(row_K+1[k]);  variance = 1 - |z_c|^2
     double vr = 0.0, vi = 0.0, nc = 0.0;
 #pragma unroll
@@ -552,6 +604,113 @@ __device__ bool solve_point(SM &sm, const PointA &P, int lane, double nugget, co
     val_im = vi;
     var_rel = 1.0 - nc;
     return true;
+}
+
+// Augmented (widely linear) spin-2 estimate.  With G = <P P^H> / xi+(0) (xi+
+// and the pair phases) and C = <P P^T> / xi+(0) (xi- and the pseudo-phases),
+// the real vector x = (Q_1..Q_K, U_1..U_K) has covariance xi+(0)/2 A with
+//   A = [[Re(G + C), Im(C - G)], [Im(G + C), Re(G - C)]]
+// (diagonal 1; the nugget n is added to it as to G), and the target's (Q, U)
+// the cross-covariances xi+(0)/2 (b_Q, b_U) built the same way from G_i0, C_i0.
+// Then Q = b_Q^T A^-1 x, U = b_U^T A^-1 x, and E|P - P^|^2 = xi+(0)(1 -
+// (|L^-1 b_Q|^2 + |L^-1 b_U|^2)/2).  The factor of A bordered by the rows b_Q,
+// b_U and x gives all three solves.
+template <int K, class R, class SM>
+__device__ bool solve_point_aug(SM &sm, const PointA &P, int lane, double nugget, const TableDev &tab,
+                                const TableDev &tabm, const double (&keyd)[Shape<K>::RPL],
+                                const double (&yre)[Shape<K>::RPL], const double (&yim)[Shape<K>::RPL],
+                                double &val_re, double &val_im, double &var_rel) {
+    using O = Ops<R>;
+    using T = typename O::T;
+    using G = Geom<R, SM>;
+    constexpr int RPL = Shape<K>::RPL, NTRI = Shape<K>::NTRI, N = 2 * K;
+    T *mat = sm.u.mat;
+    // ---- assembly: each pair (i >= j) of neighbours gives four entries of A
+    {
+        int i = 0, j = lane;
+        while (j > i) {
+            j -= i + 1;
+            ++i;
+        }
+        for (int q = lane; q < NTRI; q += 32) {
+            if (i == j) {
+                mat[tri<N>(i, i)] = O::from(1.0 + nugget);
+                mat[tri<N>(K + i, K + i)] = O::from(1.0 + nugget);
+                mat[tri<N>(K + i, i)] = O::zero();
+            } else {
+                const T dx = O::sub(G::x(sm, j), G::x(sm, i));
+                const T dy = O::sub(G::y(sm, j), G::y(sm, i));
+                const T dz = O::sub(G::z(sm, j), G::z(sm, i));
+                const T t = O::add_fast(O::add_fast(O::mul(dx, dx), O::mul(dy, dy)), O::mul(dz, dz));
+                const T fp = table_eval<R>(tab, t), fm = table_eval<R>(tabm, t);
+                Cx<T> php, phm;
+                pair_phases_pm<R>(dx, dy, dz, G::nz(sm, i), G::ns(sm, i), G::nc(sm, i), G::nsn(sm, i), G::nz(sm, j),
+                                  G::ns(sm, j), G::nc(sm, j), G::nsn(sm, j), php, phm);
+                const T gr = O::mul(fp, php.re), gi = O::mul(fp, php.im);
+                const T cr = O::mul(fm, phm.re), ci = O::mul(fm, phm.im);
+                mat[tri<N>(i, j)] = O::add(gr, cr);
+                mat[tri<N>(K + i, K + j)] = O::sub(gr, cr);
+                mat[tri<N>(K + i, j)] = O::add(gi, ci);
+                mat[tri<N>(K + j, i)] = O::sub(ci, gi);
+            }
+            j += 32;
+            while (j > i) {
+                j -= i + 1;
+                ++i;
+            }
+        }
+    }
+    // ---- bordered rows: N = b_Q, N + 1 = b_U, N + 2 = x
+#pragma unroll
+    for (int r = 0; r < RPL; ++r) {
+        const int i = lane + 32 * r;
+        if (i < K) {
+            const T t0 = O::from(keyd[r]);
+            const T fp = table_eval<R>(tab, t0), fm = table_eval<R>(tabm, t0);
+            Cx<T> php, phm;  // of (n' -> X_i); G_i0 takes the conjugate Hermitian phase
+            pair_phases_pm<R>(G::x(sm, i), G::y(sm, i), G::z(sm, i), O::from(P.z), O::from(P.s), O::from(P.cph),
+                              O::from(P.sph), G::nz(sm, i), G::ns(sm, i), G::nc(sm, i), G::nsn(sm, i), php, phm);
+            const T gr = O::mul(fp, php.re), gi = O::neg(O::mul(fp, php.im));
+            const T cr = O::mul(fm, phm.re), ci = O::mul(fm, phm.im);
+            mat[tri<N>(N, i)] = O::add(gr, cr);
+            mat[tri<N>(N, K + i)] = O::add(gi, ci);
+            mat[tri<N>(N + 1, i)] = O::sub(ci, gi);
+            mat[tri<N>(N + 1, K + i)] = O::sub(gr, cr);
+            mat[tri<N>(N + 2, i)] = O::from(yre[r]);
+            mat[tri<N>(N + 2, K + i)] = O::from(yim[r]);
+        }
+    }
+    __syncwarp();
+    if (!bordered_cholesky<N, 3, R>(mat, lane)) return false;
+    double vq = 0.0, vu = 0.0, nn = 0.0;
+    for (int k = lane; k < N; k += 32) {
+        const double zq = O::to(mat[tri<N>(N, k)]), zu = O::to(mat[tri<N>(N + 1, k)]);
+        const double zx = O::to(mat[tri<N>(N + 2, k)]);
+        vq = fma(zq, zx, vq);
+        vu = fma(zu, zx, vu);
+        nn = fma(zq, zq, fma(zu, zu, nn));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        vq += __shfl_xor_sync(FULL, vq, o);
+        vu += __shfl_xor_sync(FULL, vu, o);
+        nn += __shfl_xor_sync(FULL, nn, o);
+    }
+    val_re = vq;
+    val_im = vu;
+    var_rel = 1.0 - 0.5 * nn;
+    return true;
+}
+
+template <int K, int SPIN, class R, class SM>
+__device__ __forceinline__ bool solve_any(SM &sm, const PointA &P, int lane, double nugget, const LensArgs &a,
+                                          const double (&keyd)[Shape<K>::RPL], const double (&yre)[Shape<K>::RPL],
+                                          const double (&yim)[Shape<K>::RPL], double &vre, double &vim,
+                                          double &vrel) {
+    if constexpr (SPIN == SPIN2_AUG)
+        return solve_point_aug<K, R>(sm, P, lane, nugget, a.tab, a.tabm, keyd, yre, yim, vre, vim, vrel);
+    else
+        return solve_point<K, SPIN, R>(sm, P, lane, nugget, a.tab, keyd, yre, yim, vre, vim, vrel);
 }
 
 // ------------------------------------------------------------------ kernel
@@ -636,7 +795,7 @@ __device__ __forceinline__ void process_tile(const LensArgs &a, int R_rings, int
             P.phi = atan2(y, x);
             P.rot_re = 1.0;
             P.rot_im = 0.0;
-            if (SPIN == 2 && a.rotate && dl > 0.0) {
+            if (SPIN != 0 && a.rotate && dl > 0.0) {
                 // P(n) = P(n') exp(2i(a_nn' - a_n'n)) with a_uv the angle at u, from e_theta
                 // towards e_phi, of the geodesic towards v: the polarisation parallel-
                 // transported back along the deflection.  At n the direction is
@@ -951,8 +1110,7 @@ __device__ __forceinline__ void process_tile(const LensArgs &a, int R_rings, int
             bool solved = false;
             if (MIXED) {
                 SMf &smf = *reinterpret_cast<SMf *>(wbase);
-                solved = solve_point<K, SPIN, df>(smf, P, lane, NUGGET_EPS, a.tab, keyd, yre, yim, vre, vim,
-                                                  vrel);
+                solved = solve_any<K, SPIN, df>(smf, P, lane, NUGGET_EPS, a, keyd, yre, yim, vre, vim, vrel);
                 __syncwarp();
                 if (a.force_fallback) solved = false;
                 if (!solved) {
@@ -979,7 +1137,7 @@ __device__ __forceinline__ void process_tile(const LensArgs &a, int R_rings, int
                     nug *= 2.0;
                     flags |= FLINTS_ST_NUGGET;
                 }
-                solved = solve_point<K, SPIN, double>(sm, P, lane, nug, a.tab, keyd, yre, yim, vre, vim, vrel);
+                solved = solve_any<K, SPIN, double>(sm, P, lane, nug, a, keyd, yre, yim, vre, vim, vrel);
                 __syncwarp();
             }
             if (!solved) {

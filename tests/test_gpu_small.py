@@ -170,6 +170,38 @@ def test_spin2_sky_parity(fl, torch, precision, K):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("K,bb_frac", [(16, 0.0), (32, 0.0), (48, 0.0), (32, 0.4)])
+def test_spin2_augmented_parity(fl, torch, precision, K, bb_frac):
+    # FLINTS_SPIN2_AUGMENTED: the widely linear estimator (xi+ and xi-) against the oracle's
+    nside, lmax = 32, 64
+    cl = wl.cl_ee(lmax, 50.0)
+    bb = bb_frac * cl
+    P = sht.synth_map(nside, lmax, wl.draw_alm(cl, 46), spin=2, blm=wl.draw_alm(bb, 47) if bb_frac else None)
+    m = np.ascontiguousarray(np.stack([P.real, P.imag], axis=1))
+    npix = hp.npix(nside)
+    defl = wl.random_deflection(npix, 48) * 8
+    weight = np.abs(cl) + np.abs(bb)
+    t_max, n = xi.grid_rule(weight, K, nside)
+    tp, tm, x0 = xi.spin2_tables(cl, bb, t_max, n)
+    ref = kr.lens(nside, K, 2, m, defl, np.arange(npix), tp, x0, f_minus=tm)
+    plan = fl.Plan(nside, cl, bb, spin=2, K=K, precision=precision, flags=fl.FLINTS_SPIN2_AUGMENTED)
+    out = torch.empty((npix, 2), dtype=torch.float64, device="cuda")
+    var = torch.empty(npix, dtype=torch.float64, device="cuda")
+    plan.lens_full(torch.from_numpy(m).cuda(), torch.from_numpy(defl).cuda(), out, var)
+    torch.cuda.synchronize()
+    v = to_host(out)
+    sigma = float(np.sqrt(np.mean(P.real ** 2 + P.imag ** 2)))
+    assert parity_metric(v[:, 0] + 1j * v[:, 1], ref.value, sigma) <= TOL[precision]
+    assert parity_metric(to_host(var), ref.variance, x0) <= TOL[precision]
+    assert plan.stats()["failed"] == 0
+
+
+def test_augmented_flag_needs_spin2(fl, torch):
+    with pytest.raises(fl.FlintsError):
+        fl.Plan(16, wl.cl_tt(32, 20.0), spin=0, K=16, flags=fl.FLINTS_SPIN2_AUGMENTED)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_spin2_rotation_to_target_frame(fl, torch, precision):
     # FLINTS_ROTATE_TO_TARGET: P returned in the frame at n (parallel transport back
     # along the deflection), against the oracle's rotated output
