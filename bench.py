@@ -43,9 +43,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", choices=["c3", "c4", "c5", "ss"], default="c3",
-                    help="c3: Nside 4096 spin 2 (default); c4: 64-map batched persistent launch; c5: serving; "
-                         "ss: supersampling Nside 2048 -> 4096")
+    ap.add_argument("--workload", choices=["c3", "c3aug", "c4", "c5", "ss"], default="c3",
+                    help="c3: Nside 4096 spin 2 (default); c3aug: the same with the augmented (xi+, xi-) "
+                         "estimator; c4: 64-map batched persistent launch; c5: serving; ss: supersampling "
+                         "Nside 2048 -> 4096")
     ap.add_argument("--duration", type=float, default=45.0, help="c5: seconds of Poisson arrivals")
     ap.add_argument("--profile-case", choices=["mixed", "fp64"], default=None,
                     help="small case for ncu: two launches on 2^18 targets of the resident c3 map")
@@ -87,7 +88,7 @@ def config(n_gpus):
 
 # ------------------------------------------------------------ CPU oracle leg
 def _oracle_worker(args):
-    first, count, seed = args
+    first, count, seed, aug = args
     sys.path.insert(0, ROOT)
     from oracle import kriging as kr
     from oracle import xi
@@ -96,19 +97,19 @@ def _oracle_worker(args):
     t_max, n = xi.grid_rule(np.abs(cl) + np.abs(bb), W.K, W.nside)
     if (t_max, n) not in _TABLE_CACHE:
         _TABLE_CACHE[(t_max, n)] = xi.spin2_tables(cl, bb, t_max, n)
-    tp, _, x0 = _TABLE_CACHE[(t_max, n)]
+    tp, tm, x0 = _TABLE_CACHE[(t_max, n)]
     pix = np.arange(first, first + count)
     defl = wl.random_deflection(count, seed + first)
     qu = wl.HashedMap(W.npix, 6, 2)
     t0 = time.time()
-    kr.lens(W.nside, W.K, 2, qu, defl, pix, tp, x0)
+    kr.lens(W.nside, W.K, 2, qu, defl, pix, tp, x0, f_minus=tm if aug else None)
     return count, time.time() - t0
 
 
 _TABLE_CACHE: dict = {}
 
 
-def cpu_oracle(seconds: float):
+def cpu_oracle(seconds: float, aug: bool = False):
     """Time the oracle (as it stands) on a bounded sample of the workload on all host cores."""
     import multiprocessing as mp
 
@@ -117,16 +118,16 @@ def cpu_oracle(seconds: float):
     per = 256
     # calibrate on one chunk, then size the sample to about `seconds` of wall time
     with ctx.Pool(cores) as pool:
-        n0, t0 = pool.map(_oracle_worker, [(50_000_000, per, 11)])[0]
+        n0, t0 = pool.map(_oracle_worker, [(50_000_000, per, 11, aug)])[0]
         rate1 = n0 / max(t0, 1e-9)
         chunks = max(cores, int(seconds * rate1 * cores / per))
         starts = [(50_000_000 + 7919 * per * k) % (W.npix - per) for k in range(chunks)]
         t = time.time()
-        res = pool.map(_oracle_worker, [(s, per, 11) for s in starts])
+        res = pool.map(_oracle_worker, [(s, per, 11, aug) for s in starts])
         wall = time.time() - t
     pts = sum(r[0] for r in res)
     return {"value": pts / wall, "unit": "pts/s", "cores": cores, "kind": "oracle",
-            "sample": f"{pts} targets of the c3 workload in {chunks} chunks of {per} consecutive RING pixels "
+            "sample": f"{pts} targets of the c3 workload{' (augmented estimator)' if aug else ''} in {chunks} chunks of {per} consecutive RING pixels "
                       f"(hashed-normal Q/U values, per-pixel deflections), {wall:.1f} s wall on {cores} spawned "
                       f"processes"}
 
@@ -192,7 +193,9 @@ def run_ours(args):
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     # the CPU baseline runs first, before any GPU work (spawned pool)
-    cpu = cpu_oracle(args.cpu_seconds) if (rank == 0 and world == 1) else None
+    aug = args.workload == "c3aug"
+    flags = fl.FLINTS_SPIN2_AUGMENTED if aug else 0
+    cpu = cpu_oracle(args.cpu_seconds, aug) if (rank == 0 and world == 1) else None
 
     dev = torch.device("cuda", local)
     fl.load_library()
@@ -205,7 +208,7 @@ def run_ours(args):
     defl = torch.randn((nb * BATCH, 2), dtype=torch.float64, device=dev, generator=g) * (wl.DEFLECTION_RMS / math.sqrt(2))
     out = torch.empty((BATCH, 2), dtype=torch.float64, device=dev)
     var = torch.empty(BATCH, dtype=torch.float64, device=dev)
-    plans = {p: fl.Plan(W.nside, cl, bb, spin=2, K=W.K, precision=p) for p in ("mixed", "fp64")}
+    plans = {p: fl.Plan(W.nside, cl, bb, spin=2, K=W.K, precision=p, flags=flags) for p in ("mixed", "fp64")}
 
     def step(plan, i):
         b = (rank * 5 + i) % nb
@@ -286,12 +289,12 @@ def run_ours(args):
     value = n_gpus * BATCH * args.steps / (total_ms / 1e3)
     fp_value = n_gpus * BATCH * len(fp_per) / (fp_total / 1e3)
     kern_ms = statistics.mean(per)
-    fl32 = flops.mixed_fp32_flops(W.K, 2)
+    fl32 = flops.augmented_flops(W.K, True) if aug else flops.mixed_fp32_flops(W.K, 2)
     achieved = fl32 * BATCH / (kern_ms / 1e3) / 1e12
-    fl64 = flops.fp64_flops(W.K, 2)
+    fl64 = flops.augmented_flops(W.K, False) if aug else flops.fp64_flops(W.K, 2)
     achieved64 = fl64 * BATCH / (statistics.mean(fp_per) / 1e3) / 1e12
     line = {
-        "metric": METRIC, "value": value, "unit": "pts/s", "n_gpus": n_gpus, "steps": args.steps,
+        "metric": METRIC + (" (augmented xi+/xi- estimator)" if aug else ""), "value": value, "unit": "pts/s", "n_gpus": n_gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64 in/out; double-float (2 x f32) factor, f64 geometry",
         "data": "synthetic: white-noise Q/U map (the work does not depend on the values) and per-pixel Gaussian "
@@ -306,12 +309,12 @@ def run_ours(args):
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": flops.FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / flops.FP32_PEAK_TFLOPS, "traffic": None,
-                     "kernel": "lens_kernel<32,2,mixed> (FP32 pipe, double-float)",
+                     "kernel": "lens_kernel<32,%d,mixed> (FP32 pipe, double-float)" % (3 if aug else 2),
                      "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
                      "flops_per_point": fl32},
         "roofline_fp64": {"bound": "alu", "achieved": achieved64, "peak": flops.FP64_PEAK_TFLOPS,
                           "unit": "TFLOP/s", "frac": achieved64 / flops.FP64_PEAK_TFLOPS,
-                          "kernel": "lens_kernel<32,2,fp64>", "flops_per_point": fl64},
+                          "kernel": "lens_kernel<32,%d,fp64>" % (3 if aug else 2), "flops_per_point": fl64},
         "cpu_baseline": cpu,
         "clocks": clocks,
         "gpu_launches": args.steps,
@@ -563,4 +566,4 @@ if __name__ == "__main__":
     elif a.impl == "reference":
         run_reference(a)
     else:
-        run_ours(a)
+        run_ours(a)  # c3, or c3aug

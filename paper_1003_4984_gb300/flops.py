@@ -14,6 +14,11 @@ Counting convention (used for every roofline fraction reported by the bench):
       phase (4 projections of 2 fma + 1 mul, squares and products: 48 flops);
       the K target entries likewise (their chords come from the search);
     - value and variance: 2 dot products of length K;
+* augmented spin 2: a real system of size N = 2K with three right-hand sides:
+  (N^3 - N)/6 multiply-adds and N pivots, three forward solves of N(N-1)/2
+  multiply-adds, per pair of stencil members the chord, two tables (xi+ and
+  xi-), both phases (56 flops) and four entries (8), and three dot products of
+  length N;
 * mixed path: the same steps executed in double-float arithmetic on the FP32
   pipe, each double-float operation costed in FP32 flops: multiply-accumulate
   into an accumulator 15 (one TwoProduct with cross terms, one TwoSum, two
@@ -55,3 +60,22 @@ def mixed_fp32_flops(K: int, spin: int) -> float:
 # 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz; FP64 at the 1.25 TFLOP/s nominal rate.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 FP64_PEAK_TFLOPS = 1.25
+
+
+def augmented_flops(K: int, mixed: bool) -> float:
+    """Augmented spin-2 estimator: FP64 flops, or FP32 flops of its double-float form."""
+    N = 2 * K
+    P = K * (K - 1) / 2
+    macs = (N ** 3 - N) / 6
+    if not mixed:
+        chol = 2 * macs + 2 * 2 * N + N * (N - 1) / 2
+        solve = 3 * (2 * N * (N - 1) / 2 + N)
+        assembly = P * (8 + 2 * 8 + 56 + 8) + K * (2 * 8 + 56 + 8)
+        return chol + solve + assembly + 3 * 2 * N
+    chol = macs * DF_MAC + N * 2 * DF_SPECIAL + N * (N - 1) / 2 * DF_MUL
+    solve = 3 * (N * (N - 1) / 2 * DF_MAC + N * DF_MUL)
+    chord = 3 * DF_ADD + 3 * DF_MUL + 2 * DF_ADD
+    table = DF_MUL + 3 * (DF_MUL + DF_ADD)
+    phases = 24 * DF_MUL + 14 * DF_ADD + DF_SPECIAL
+    entries = 4 * DF_MUL + 4 * DF_ADD
+    return chol + solve + P * (chord + 2 * table + phases + entries) + K * (2 * table + phases + entries)

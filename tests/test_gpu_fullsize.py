@@ -21,6 +21,7 @@ import workloads as wl
 from oracle import healpix as hp
 from oracle import kriging as kr
 from oracle import sht
+from oracle import xi
 from tests.gpu_common import oracle_table, parity_metric, require_gpu, to_host, unexplained_mismatches
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
@@ -94,8 +95,11 @@ def test_fullsize_parity_and_exact_benchmark(fl, W):
     tab, x0, _, _ = oracle_table(cl, bb, W.spin, W.K, W.nside)
     band_map = BandMap(pix, vals)
     results = {}
-    for precision in ("fp64", "mixed"):
-        plan = fl.Plan(W.nside, cl, bb, spin=W.spin, K=W.K, precision=precision)
+    variants = [("fp64", 0), ("mixed", 0)]
+    if W.spin == 2:  # the augmented (xi+, xi-) estimator on the same bands
+        variants += [("fp64-aug", fl.FLINTS_SPIN2_AUGMENTED), ("mixed-aug", fl.FLINTS_SPIN2_AUGMENTED)]
+    for precision, flags in variants:
+        plan = fl.Plan(W.nside, cl, bb, spin=W.spin, K=W.K, precision=precision.split("-")[0], flags=flags)
         got_v, got_s2 = [], []
         for first, count, b0, bn, defl_np, _ in bands:
             defl = torch.from_numpy(defl_np).to(dev)
@@ -121,6 +125,14 @@ def test_fullsize_parity_and_exact_benchmark(fl, W):
         v, s2 = results[precision]
         assert parity_metric(v, ref.value, sigma) <= tol, precision
         assert parity_metric(s2, ref.variance, x0) <= tol, precision
+    if W.spin == 2:
+        _, t_max, n = oracle_table(cl, bb, W.spin, W.K, W.nside)[1:]
+        tp, tm, _ = xi.spin2_tables(cl, bb, t_max, n)
+        ref_aug = kr.lens(W.nside, W.K, 2, band_map, defl, targets, tp, x0, f_minus=tm)
+        for precision, tol in (("fp64-aug", 1e-9), ("mixed-aug", 1e-6)):
+            v, s2 = results[precision]
+            assert parity_metric(v, ref_aug.value, sigma) <= tol, precision
+            assert parity_metric(s2, ref_aug.variance, x0) <= tol, precision
     # exact benchmark on a subsample of the targets
     sub = np.arange(0, targets.size, 6)
     truth = sht.synth_points(W.lmax, alm, ref.target[sub], spin=W.spin)
@@ -130,6 +142,11 @@ def test_fullsize_parity_and_exact_benchmark(fl, W):
     ratio = np.mean(np.abs(err) ** 2 / results["mixed"][1][sub])
     pred = math.sqrt(np.mean(results["mixed"][1][sub]) / np.mean(np.abs(truth) ** 2))
     print(f"{W.name}: rel L2 {rel_l2:.3e}, predicted {pred:.3e}, <|err|^2/sigma^2> {ratio:.3f}")
+    if W.spin == 2:
+        v_aug = results["mixed-aug"][0][sub]
+        rel_aug = math.sqrt(np.mean(np.abs(v_aug - truth) ** 2) / np.mean(np.abs(truth) ** 2))
+        print(f"{W.name}: augmented (xi+, xi-) rel L2 {rel_aug:.3e}")
+        assert rel_aug <= 2e-4 and rel_aug <= 1.02 * rel_l2
     if W.name == "c3":
         # Nside 4096, lmax 4096: the paper's precision (Table 2, abstract).  Here the
         # 1.49e-8 nugget dominates the predicted variance (it models noisy data), so
