@@ -88,6 +88,22 @@ __device__ __forceinline__ df df_rcp(df a) {
     return quick_two_sum(y, corr);
 }
 
+// Pivot of a Cholesky column in double-float: l = sqrt(d) and il = 1/l.  Newton-
+// Raphson on 1/sqrt from the single-precision rsqrtf(d.hi) = r0 (2 ulp): with
+// e = 1 - d r0^2 (|e| < 2^-21, formed from the exact square r0^2 and a double-
+// float product), 1/sqrt(d) = r0 (1 - e)^(-1/2) = r0 (1 + e/2 + 3e^2/8 + O(e^3)),
+// so il carries about 2^-46 relative error; l = d il.  Requires d.hi > 0 normal.
+__device__ __forceinline__ void df_pivot(df d, df &l, df &il) {
+    const float r0 = rsqrtf(d.hi);
+    const float p = __fmul_rn(r0, r0);
+    const float pe = __fmaf_rn(r0, r0, -p);
+    const df m = df_mul(d, df{p, pe});                            // 1 - e
+    const float e = __fsub_rn(__fsub_rn(1.0f, m.hi), m.lo);        // 1 - m.hi is exact
+    const float corr = __fmul_rn(r0, __fmul_rn(e, __fmaf_rn(0.375f, e, 0.5f)));
+    il = quick_two_sum(r0, corr);
+    l = df_mul(d, il);
+}
+
 // Dot-product accumulator: acc -= x*y with the product's rounding error kept;
 // the low word is left unnormalised until the end (its error is relative to
 // the operands, which are O(1) in the kernels).
@@ -137,6 +153,11 @@ struct Ops<double> {
     static __device__ __forceinline__ T neg(T a) { return -a; }
     static __device__ __forceinline__ T sqrt_(T a) { return sqrt(a); }
     static __device__ __forceinline__ T rcp(T a) { return 1.0 / a; }
+    // pivot l = sqrt(d) and 1/l from one reciprocal square root (rsqrt: 1 ulp)
+    static __device__ __forceinline__ void pivot(T d, T &l, T &il) {
+        il = rsqrt(d);
+        l = d * il;
+    }
     static __device__ __forceinline__ bool positive(T a) { return a > 0.0; }
     static __device__ __forceinline__ Acc acc(T x) { return {x}; }
     static __device__ __forceinline__ void sub_prod(Acc &a, T x, T y) { a.v = fma(-x, y, a.v); }
@@ -160,6 +181,7 @@ struct Ops<df> {
     static __device__ __forceinline__ T neg(T a) { return df_neg(a); }
     static __device__ __forceinline__ T sqrt_(T a) { return df_sqrt(a); }
     static __device__ __forceinline__ T rcp(T a) { return df_rcp(a); }
+    static __device__ __forceinline__ void pivot(T d, T &l, T &il) { df_pivot(d, l, il); }
     static __device__ __forceinline__ bool positive(T a) { return a.hi > 0.0f; }
     static __device__ __forceinline__ Acc acc(T x) { return {x.hi, x.lo}; }
     static __device__ __forceinline__ void sub_prod(Acc &a, T x, T y) { dfacc_sub_prod(a, x, y); }

@@ -306,9 +306,11 @@ struct Holo32 {
     float dr, di;
 };
 __device__ __forceinline__ Holo32 holonomy32(float ui, float vi, float uj, float vj, float ti, float tj, float tij) {
-    const float x = (ui * vj - vi * uj) / (4.0f - 0.5f * (ti + tj + tij));
+    // x and w feed a correction of order x that is needed to FP32 accuracy only:
+    // the fast divisions (2 ulp) suffice
+    const float x = __fdividef(ui * vj - vi * uj, 4.0f - 0.5f * (ti + tj + tij));
     const float x2 = x * x;
-    const float w = 1.0f / (1.0f + x2);
+    const float w = __fdividef(1.0f, 1.0f + x2);
     const float q = w * w;
     return {-8.0f * x2 * q, -4.0f * x * (1.0f - x2) * q};
 }
@@ -430,8 +432,8 @@ __device__ __forceinline__ bool bordered_cholesky(Elem *mat, int lane) {
             d = O::shfl(srow[0].re, 0);
         }
         if (!O::positive(d)) return false;
-        const T ljj = O::sqrt_(d);
-        const T il = O::rcp(ljj);
+        T ljj, il;
+        O::pivot(d, ljj, il);
         __syncwarp();
         if (part == 0) {
 #pragma unroll
