@@ -384,6 +384,7 @@ __device__ __forceinline__ bool bordered_cholesky(Elem *mat, int lane) {
         Elem srow[NT];
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
+            if (t > 0 && j + t * g >= NROW) break;  // warp-uniform: no row left for this slot
             const int r = j + grp + t * g;
             const bool act = r < NROW;
             const int rr = act ? r : j;
@@ -439,6 +440,7 @@ __device__ __forceinline__ bool bordered_cholesky(Elem *mat, int lane) {
 #pragma unroll
             for (int t = 0; t < NT; ++t) {
                 const int r = j + grp + t * g;
+                if (t > 0 && j + t * g >= NROW) break;
                 if (r < NROW) {
                     Elem v;
                     if constexpr (!CPLX) {
