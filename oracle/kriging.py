@@ -16,10 +16,10 @@ method in the paper's order:
    a lower bound for every pixel outside the window; points where the proof
    fails are searched again in a larger window.
 3. Covariances (Eqs. fundamental_variance, v_spins): S_ij = xi(t_ij)/xi(0)
-   between stencil pixels, c_i = xi(t(n', n_i))/xi(0) to the target.  Spin 2
-   uses the Hermitian <P_i P_j^*> = xi+(t_ij) exp(2i(a_ij - a_ji)) with a_ij the
-   angle at n_i, measured from e_theta towards e_phi, of the geodesic towards
-   n_j.
+   between stencil pixels, c_i = xi(t(n', n_i))/xi(0) to the target.  Spin s
+   (1: a deflection, 2: Q/U) uses the Hermitian <P_i P_j^*> =
+   xi+(t_ij) exp(is(a_ij - a_ji - pi)) with a_ij the angle at n_i, measured from
+   e_theta towards e_phi, of the geodesic towards n_j.
 4. Cholesky (Sec. 2.4) of S + n I with the nugget n = epsilon = 1.49e-8 when
    that factorisation has only positive pivots, and otherwise the paper's rule
    n = -lambda_min + epsilon (lambda_min the lowest eigenvalue of S).
@@ -218,8 +218,8 @@ class Result:
     target: np.ndarray     # (P, 3) displaced unit vectors
 
 
-def phase2(va: np.ndarray, vb: np.ndarray) -> np.ndarray:
-    """exp(2i a_ab) where a_ab is the angle at va, from e_theta towards e_phi, of the
+def phase_s(va: np.ndarray, vb: np.ndarray, spin: int) -> np.ndarray:
+    """exp(i s a_ab) where a_ab is the angle at va, from e_theta towards e_phi, of the
     tangent direction towards vb (the projection of vb - va on the tangent plane)."""
     e_th, e_ph = local_basis(va)
     d = vb - va
@@ -227,23 +227,31 @@ def phase2(va: np.ndarray, vb: np.ndarray) -> np.ndarray:
     B = np.sum(d * e_ph, axis=-1)
     w = A + 1j * B
     with np.errstate(invalid="ignore", divide="ignore"):  # a point paired with itself has no direction
-        return w * w / (A * A + B * B)
+        return (w / np.abs(w)) ** spin
 
 
-def pair_phase(va: np.ndarray, vb: np.ndarray) -> np.ndarray:
-    """Phase of <P(va) P(vb)^*> relative to xi+: exp(2i (a_ab - a_ba)).
+def phase2(va: np.ndarray, vb: np.ndarray) -> np.ndarray:
+    """exp(2i a_ab) (spin 2)."""
+    return phase_s(va, vb, 2)
+
+
+def pair_phase(va: np.ndarray, vb: np.ndarray, spin: int = 2) -> np.ndarray:
+    """Phase of <P(va) P(vb)^*> relative to xi+: exp(i s (a_ab - a_ba - pi)), both
+    frames referred to the geodesic's direction of travel from va to vb (at vb
+    that direction is a_ba + pi; the pi matters for odd s only).
 
     Coincident points (zero separation) correlate with no rotation: V_ii = 1
     in Eq. v_spins."""
-    ph = phase2(va, vb) * np.conj(phase2(vb, va))
+    ph = (-1.0) ** spin * phase_s(va, vb, spin) * np.conj(phase_s(vb, va, spin))
     return np.where(np.isfinite(ph), ph, 1.0 + 0.0j)
 
 
-def pseudo_phase(va: np.ndarray, vb: np.ndarray) -> np.ndarray:
-    """Phase of the pseudo-covariance <P(va) P(vb)> relative to xi-: exp(2i (a_ab + a_ba)).
+def pseudo_phase(va: np.ndarray, vb: np.ndarray, spin: int = 2) -> np.ndarray:
+    """Phase of the pseudo-covariance <P(va) P(vb)> relative to xi-:
+    exp(i s (a_ab + a_ba + pi)) (the same direction-of-travel convention).
 
     Coincident points have xi-(0) = 0; their phase is set to 0."""
-    ph = phase2(va, vb) * phase2(vb, va)
+    ph = (-1.0) ** spin * phase_s(va, vb, spin) * phase_s(vb, va, spin)
     return np.where(np.isfinite(ph), ph, 0.0 + 0.0j)
 
 
@@ -257,18 +265,21 @@ def real_form(G: np.ndarray, C: np.ndarray) -> np.ndarray:
     return np.concatenate([top, bot], axis=-2)
 
 
-def _estimate_augmented(X, targets, y, S, c, f_minus, T, t0, xi_zero, eps):
+def _estimate_augmented(X, targets, y, S, c, f_minus, T, t0, xi_zero, eps, spin=2):
     """Widely linear (augmented) spin-2 estimate: the Gaussian conditional mean of
     (Q, U) at the target given (Q_i, U_i), using both xi+ (through <P P^*>) and xi-
     (through <P P>), as a 2K x 2K real system."""
     K = X.shape[1]
-    G = S * pair_phase(X[:, :, None, :], X[:, None, :, :])
+    # <P_a P_b> of real E and B fields carries (-1)^s relative to the harmonic sum
+    # sum_m sY(a) (-sY(b))^* = (2l+1)/(4 pi) d^l_{s,-s} pseudo_phase(a, b)
+    sgn = (-1.0) ** spin
+    G = S * pair_phase(X[:, :, None, :], X[:, None, :, :], spin)
     G[:, np.arange(K), np.arange(K)] = 1.0
-    C = f_minus(T.reshape(-1)).reshape(T.shape) * pseudo_phase(X[:, :, None, :], X[:, None, :, :])
+    C = sgn * f_minus(T.reshape(-1)).reshape(T.shape) * pseudo_phase(X[:, :, None, :], X[:, None, :, :], spin)
     C[:, np.arange(K), np.arange(K)] = 0.0
     tb = np.broadcast_to(targets[:, None, :], X.shape)
-    g0 = c * pair_phase(X, tb)            # <P_i P_0^*> / xi+(0)
-    c0 = f_minus(t0) * pseudo_phase(X, tb)  # <P_i P_0> / xi+(0)
+    g0 = c * pair_phase(X, tb, spin)            # <P_i P_0^*> / xi+(0)
+    c0 = sgn * f_minus(t0) * pseudo_phase(X, tb, spin)  # <P_i P_0> / xi+(0)
     A = real_form(G, C)
     B = real_form(g0[:, :, None], c0[:, :, None])  # (batch, 2K, 2): columns for Q_0 and U_0
     L, nug = factor_with_nugget(A, eps)
@@ -284,26 +295,26 @@ def estimate(nside: int, spin: int, maps: np.ndarray, targets: np.ndarray, idx: 
              f_plus, xi_zero: float, eps: float = EPS_NUGGET, f_minus=None):
     """Steps 3-5 on a given stencil ``idx`` (B, K): (values, variances, nuggets).
 
-    ``f_minus`` (spin 2): xi-/xi+(0); when given, the augmented estimator is used."""
+    ``f_minus`` (spin 1, 2): xi-/xi+(0); when given, the augmented estimator is used."""
     K = idx.shape[1]
     X = hp.pix2vec(nside, idx)  # (B, K, 3)
     T = _chord2(X[:, :, None, :], X[:, None, :, :])
     S = f_plus(T.reshape(-1)).reshape(T.shape)
     t0 = _chord2(targets[:, None, :], X)
     c = f_plus(t0)
-    if spin == 2 and f_minus is not None:
+    if spin != 0 and f_minus is not None:
         y = maps[idx, 0] + 1j * maps[idx, 1]
-        return _estimate_augmented(X, targets, y, S, c, f_minus, T, t0, xi_zero, eps)
+        return _estimate_augmented(X, targets, y, S, c, f_minus, T, t0, xi_zero, eps, spin)
     if spin == 0:
         y = maps[idx]
         L, nug = factor_with_nugget(S, eps)
         zc = forward_solve(L, c)
         zy = forward_solve(L, y)
         return np.sum(zc * zy, axis=1), xi_zero * (1.0 - np.sum(zc * zc, axis=1)), nug
-    Ph = pair_phase(X[:, :, None, :], X[:, None, :, :])
+    Ph = pair_phase(X[:, :, None, :], X[:, None, :, :], spin)
     C = S * Ph
     C[:, np.arange(K), np.arange(K)] = 1.0
-    c0 = c * pair_phase(np.broadcast_to(targets[:, None, :], X.shape), X)
+    c0 = c * pair_phase(np.broadcast_to(targets[:, None, :], X.shape), X, spin)
     y = maps[idx, 0] + 1j * maps[idx, 1]
     L, nug = factor_with_nugget(C, eps)
     zc = forward_solve(L, np.conj(c0))
@@ -315,7 +326,8 @@ def interpolate(nside: int, K: int, spin: int, maps: np.ndarray, targets: np.nda
                 f_plus, xi_zero: float, eps: float = EPS_NUGGET, batch: int = 4096, f_minus=None) -> Result:
     """Kriging at unit vectors ``targets`` (P, 3) from a RING map.
 
-    ``maps``: (Npix,) real for spin 0; (Npix, 2) (Q, U) for spin 2.
+    ``maps``: (Npix,) real for spin 0; (Npix, 2) real and imaginary parts for spin 1
+    ((d_theta, d_phi) of a deflection) and spin 2 (Q, U).
     ``f_plus``: callable t -> xi(t)/xi(0) (spin 0) or xi+(t)/xi+(0) (spin 2),
     either an ``xi.HermiteTable`` (tabulated mode) or a direct evaluation.
     ``f_minus`` (spin 2, optional): xi-(t)/xi+(0); selects the augmented estimator.
@@ -348,8 +360,8 @@ def lens(nside: int, K: int, spin: int, maps: np.ndarray, defl: np.ndarray, pix:
     pix = np.asarray(pix, dtype=np.int64)
     tv = displace(nside, pix, np.asarray(defl, dtype=np.float64))
     res = interpolate(nside, K, spin, maps, tv, f_plus, xi_zero, eps, f_minus=f_minus)
-    if rotate and spin == 2:
-        res.value = res.value * pair_phase(hp.pix2vec(nside, pix), tv)
+    if rotate and spin != 0:
+        res.value = res.value * pair_phase(hp.pix2vec(nside, pix), tv, spin)
     return res
 
 

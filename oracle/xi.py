@@ -150,17 +150,18 @@ def wigner_d_fourier(lmax: int, m1: int, m2: int, beta: np.ndarray) -> np.ndarra
     return np.real(phase * (B @ E))
 
 
-def _fourier_coeffs_spin2(cl_p: np.ndarray, cl_m: np.ndarray):
-    """F+_n, F-_n (n = 0..lmax) with xi+-(b) = F_0 + 2 sum_{n>0} F_n cos(n b).
+def _fourier_coeffs_spin(spin: int, cl_p: np.ndarray, cl_m: np.ndarray):
+    """F+_n, F-_n (n = 0..lmax) with xi+-(b) = F_0 + 2 sum_{n>0} F_n cos(n b), spin s = 1, 2.
 
-    From Eq. fft_dfunction with m1 = 2 and m2 = +-2: d^l_{22}(b) = sum_n
-    (Delta^l_{n2})^2 e^{inb} and, using Delta^l_{n,-2} = (-1)^{l+n} Delta^l_{n2},
-    d^l_{2,-2}(b) = sum_n (-1)^{l+n} (Delta^l_{n2})^2 e^{inb}; both are even in n.
+    From Eq. fft_dfunction with m1 = s and m2 = +-s: d^l_{ss}(b) = sum_n
+    (Delta^l_{ns})^2 e^{inb} and, using Delta^l_{n,-s} = (-1)^{l+n} Delta^l_{ns},
+    d^l_{s,-s}(b) = i^{-2s} sum_n (-1)^{l+n} (Delta^l_{ns})^2 e^{inb} (i^{-2s} = -1 for
+    s = 1, +1 for s = 2); both are even in n.
     """
     lmax = len(cl_p) - 1
     ell = np.arange(lmax + 1)
     wp = (2.0 * ell + 1.0) / FOUR_PI * cl_p
-    wm = (2.0 * ell + 1.0) / FOUR_PI * cl_m
+    wm = (2.0 * ell + 1.0) / FOUR_PI * cl_m * (-1.0 if spin % 2 else 1.0)
     Fp = np.zeros(2 * lmax + 1)
     Fm = np.zeros(2 * lmax + 1)
 
@@ -172,20 +173,25 @@ def _fourier_coeffs_spin2(cl_p: np.ndarray, cl_m: np.ndarray):
         Fp[n] += wp[rows] * sq
         Fm[n] += wm[rows] * sgn * sq
 
-    _delta_descent(lmax, 2, visit)
+    _delta_descent(lmax, spin, visit)
     return Fp[lmax:], Fm[lmax:]
 
 
-def xi2_direct(cl_ee: np.ndarray, cl_bb: np.ndarray | None, t: np.ndarray, deriv: bool = False):
-    """(xi+, xi-)(t), and their t-derivatives if ``deriv``, for a spin-2 field.
+def _fourier_coeffs_spin2(cl_p: np.ndarray, cl_m: np.ndarray):
+    return _fourier_coeffs_spin(2, cl_p, cl_m)
+
+
+def xis_direct(spin: int, cl_e: np.ndarray, cl_b: np.ndarray | None, t: np.ndarray, deriv: bool = False):
+    """(xi+, xi-)(t), and their t-derivatives if ``deriv``, for a spin-s field (s = 1, 2):
+    xi+ = sum_l (2l+1)/(4 pi) (C^E + C^B) d^l_{ss}, xi- = sum_l (2l+1)/(4 pi) (C^E - C^B) d^l_{s,-s}.
 
     Uses xi(b) = sum_n F_n cos(n b) with b = 2 asin(sqrt(t)/2); the t-derivative
     is (d xi/d b) / (d t/d b) with d t/d b = 2 sin b, and at t = 0 the limit
     -1/2 sum_n n^2 F_n (d^2 t/d b^2 = 2 at b = 0).
     """
-    cl_ee = np.asarray(cl_ee, dtype=np.float64)
-    cl_bb = np.zeros_like(cl_ee) if cl_bb is None else np.asarray(cl_bb, dtype=np.float64)
-    Fp, Fm = _fourier_coeffs_spin2(cl_ee + cl_bb, cl_ee - cl_bb)
+    cl_e = np.asarray(cl_e, dtype=np.float64)
+    cl_b = np.zeros_like(cl_e) if cl_b is None else np.asarray(cl_b, dtype=np.float64)
+    Fp, Fm = _fourier_coeffs_spin(spin, cl_e + cl_b, cl_e - cl_b)
     t = np.asarray(t, dtype=np.float64)
     beta = 2.0 * np.arcsin(np.sqrt(np.clip(t, 0.0, 4.0)) / 2.0)
     n = np.arange(len(Fp), dtype=np.float64)
@@ -203,6 +209,17 @@ def xi2_direct(cl_ee: np.ndarray, cl_bb: np.ndarray | None, t: np.ndarray, deriv
         dxp = np.where(beta > 0, dxp_db / (2.0 * sb), -0.5 * np.sum(wgt * n * n * Fp))
         dxm = np.where(beta > 0, dxm_db / (2.0 * sb), -0.5 * np.sum(wgt * n * n * Fm))
     return xp, xm, dxp, dxm
+
+
+def xi2_direct(cl_ee: np.ndarray, cl_bb: np.ndarray | None, t: np.ndarray, deriv: bool = False):
+    """(xi+, xi-)(t) (and t-derivatives) for a spin-2 field (Eq. spins_correl)."""
+    return xis_direct(2, cl_ee, cl_bb, t, deriv)
+
+
+def xi1_direct(cl_e: np.ndarray, cl_b: np.ndarray | None, t: np.ndarray, deriv: bool = False):
+    """(xi+, xi-)(t) (and t-derivatives) for a spin-1 field, e.g. a deflection
+    d = grad phi with C^E_l = l(l+1) C^phiphi_l and C^B = 0."""
+    return xis_direct(1, cl_e, cl_b, t, deriv)
 
 
 # --------------------------------------------------------- tabulated mode
@@ -245,6 +262,15 @@ def spin0_table(cl: np.ndarray, t_max: float, n: int):
     f, g = xi0_direct(cl, nodes, deriv=True)
     xi_zero = float(xi0_direct(cl, np.zeros(1))[0])
     return HermiteTable(t_max, n, f / xi_zero, g / xi_zero), xi_zero
+
+
+def spin1_tables(cl_e: np.ndarray, cl_b: np.ndarray | None, t_max: float, n: int):
+    """Tabulated xi+/xi+(0) and xi-/xi+(0) for spin 1; returns (table+, table-, xi+(0))."""
+    nodes = np.arange(n + 1) * (t_max / n)
+    xp, xm, dxp, dxm = xi1_direct(cl_e, cl_b, nodes, deriv=True)
+    x0 = float(xi1_direct(cl_e, cl_b, np.zeros(1))[0][0])
+    return (HermiteTable(t_max, n, xp / x0, dxp / x0),
+            HermiteTable(t_max, n, xm / x0, dxm / x0), x0)
 
 
 def spin2_tables(cl_ee: np.ndarray, cl_bb: np.ndarray | None, t_max: float, n: int):

@@ -428,3 +428,61 @@ def test_augmented_error_statistics_with_pure_e_modes():
     e_herm = np.mean(np.abs(herm.value - truth) ** 2)
     assert e_aug < 0.9 * e_herm
     assert np.all(aug.variance <= herm.variance * (1 + 1e-9))
+
+
+# ------------------------------------------------------------------ spin 1
+@pytest.mark.parametrize("ell", [1, 2, 5, 8])
+def test_spin1_phases_by_addition_theorem(ell):
+    # <P_a P_b^*> and <P_a P_b> of a spin-1 field from the 1Y harmonics of Appendix A;
+    # the odd spin makes the direction-of-travel pi visible
+    a = RNG.normal(size=(40, 3))
+    a /= np.linalg.norm(a, axis=1)[:, None]
+    b = a + RNG.normal(size=(40, 3)) * 0.3
+    b /= np.linalg.norm(b, axis=1)[:, None]
+    beta = 2 * np.arcsin(np.linalg.norm(a - b, axis=1) / 2)
+    w = (2 * ell + 1) / (4 * math.pi)
+    herm = sum(_sY(1, ell, m, a) * np.conj(_sY(1, ell, m, b)) for m in range(-ell, ell + 1))
+    np.testing.assert_allclose(herm, w * wigner_d(ell, 1, 1, beta) * kr.pair_phase(a, b, 1), atol=1e-13)
+    pseudo = sum(_sY(1, ell, m, a) * np.conj(_sY(-1, ell, m, b)) for m in range(-ell, ell + 1))
+    np.testing.assert_allclose(pseudo, w * wigner_d(ell, 1, -1, beta) * kr.pseudo_phase(a, b, 1), atol=1e-13)
+
+
+@pytest.mark.parametrize("spin", [1, 2])
+def test_pseudo_covariance_of_real_fields(spin):
+    # with real E, B fields (a_{l,-m} = (-1)^m a_lm^*) and P = -sum (E + iB)_lm sY_lm,
+    # <P_a P_b> = sum_l (C^E - C^B) sum_m (-1)^m sY_lm(a) sY_l,-m(b); the augmented
+    # estimator models it as (-1)^s xi-(beta) pseudo_phase(a, b)
+    a = RNG.normal(size=(30, 3))
+    a /= np.linalg.norm(a, axis=1)[:, None]
+    b = a + RNG.normal(size=(30, 3)) * 0.3
+    b /= np.linalg.norm(b, axis=1)[:, None]
+    beta = 2 * np.arcsin(np.linalg.norm(a - b, axis=1) / 2)
+    for ell in (2, 3, 6):
+        corr = sum((-1) ** m * _sY(spin, ell, m, a) * _sY(spin, ell, -m, b) for m in range(-ell, ell + 1))
+        model = (-1) ** spin * (2 * ell + 1) / (4 * math.pi) * wigner_d(ell, spin, -spin, beta) \
+            * kr.pseudo_phase(a, b, spin)
+        np.testing.assert_allclose(corr, model, atol=1e-13)
+
+
+def test_spin1_deflection_field_exact_benchmark():
+    # the deflection d = grad phi is a spin-1 field P = d_theta + i d_phi with
+    # C^E = l(l+1) C^phiphi, C^B = 0: kriged from its pixel values at displaced
+    # directions it must match the harmonic gradient there, errors ~ predicted sigma
+    nside, lmax, K = 64, 128, 16
+    phi = wl.draw_alm(wl.cl_phiphi(lmax), 24)
+    ell = np.arange(lmax + 1)
+    cle = wl.cl_phiphi(lmax) * ell * (ell + 1)
+    dmap = sht.synth_map(nside, lmax, phi, gradient=True)
+    pix = wl.sample_pixels(hp.npix(nside), 3000, 25)
+    defl = wl.random_deflection(pix.size, 26) * 2
+    tmax = 4 * (2.0 * math.sqrt(K / 3.0) / nside) ** 2 * 1.5
+    tp, tm, x0 = xi.spin1_tables(cle, None, tmax, 1024)
+    res = kr.lens(nside, K, 1, dmap, defl, pix, tp, x0)
+    gth, gph = sht.synth_gradient_points(lmax, phi, res.target)
+    truth = gth + 1j * gph
+    r = np.abs(res.value - truth) ** 2 / res.variance
+    assert 0.85 < np.mean(r) < 1.15
+    rel = math.sqrt(np.mean(np.abs(res.value - truth) ** 2) / np.mean(np.abs(truth) ** 2))
+    assert rel < 0.05
+    aug = kr.lens(nside, K, 1, dmap, defl, pix, tp, x0, f_minus=tm)
+    assert np.mean(np.abs(aug.value - truth) ** 2) < np.mean(np.abs(res.value - truth) ** 2)

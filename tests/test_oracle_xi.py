@@ -74,7 +74,7 @@ def test_delta_columns_unitary_and_symmetric():
             np.testing.assert_allclose(col[::-1], (-1) ** (ell + m2) * col, atol=1e-14)
 
 
-@pytest.mark.parametrize("m1,m2", [(0, 0), (2, 2), (2, -2)])
+@pytest.mark.parametrize("m1,m2", [(0, 0), (1, 1), (1, -1), (2, 2), (2, -2)])
 def test_appendix_b_route_matches_jacobi(m1, m2):
     L = 40
     beta = np.concatenate([[0.0, 1e-4], RNG.uniform(0, math.pi, 9)])
@@ -99,6 +99,35 @@ def test_xi2_single_multipole(ell):
     np.testing.assert_allclose(dxp[2:], fdp, rtol=1e-5, atol=1e-6 * w * ell * ell)
     # closed-form slope at 0: d^l_22 ~ 1 - (l(l+1) - 4) b^2 / 4 and t ~ b^2
     assert abs(dxp[0] - (-w * (ell * (ell + 1) - 4) / 4)) < 1e-10 * w * ell * ell
+
+
+@pytest.mark.parametrize("ell", [1, 2, 7, 31])
+def test_xi1_single_multipole(ell):
+    # spin 1: xi+ = (2l+1)/4pi d^l_{11}, xi- = (2l+1)/4pi d^l_{1,-1} (Jacobi closed forms)
+    cl = np.zeros(ell + 1)
+    cl[ell] = 1.0
+    t = np.concatenate([[0.0, 1e-8], RNG.uniform(0, 4, 10)])
+    beta = 2 * np.arcsin(np.sqrt(t) / 2)
+    xp, xm, dxp, dxm = xi.xi1_direct(cl, None, t, deriv=True)
+    w = (2 * ell + 1) / (4 * math.pi)
+    np.testing.assert_allclose(xp, w * wigner_d(ell, 1, 1, beta), atol=1e-14)
+    np.testing.assert_allclose(xm, w * wigner_d(ell, 1, -1, beta), atol=1e-14)
+    h = 1e-7
+    tt = t[2:]
+    fdm = (xi.xi1_direct(cl, None, tt + h)[1] - xi.xi1_direct(cl, None, tt - h)[1]) / (2 * h)
+    np.testing.assert_allclose(dxm[2:], fdm, rtol=1e-5, atol=1e-6 * w * ell * ell)
+    # closed-form slope at 0: d^l_11 ~ 1 - (l(l+1) - 1) b^2 / 4 and t ~ b^2
+    assert abs(dxp[0] - (-w * (ell * (ell + 1) - 1) / 4)) < 1e-10 * w * max(ell * ell, 1)
+
+
+def test_xi1_zero_lag():
+    cl = wl.cl_phiphi(200) * np.arange(201) * np.arange(1, 202)  # deflection E spectrum l(l+1) C^phiphi
+    xp, xm = xi.xi1_direct(cl, None, np.zeros(1))
+    ell = np.arange(201)
+    assert abs(xp[0] - np.sum((2 * ell + 1) * cl) / (4 * math.pi)) < 1e-13 * xp[0]
+    assert abs(xm[0]) < 1e-14 * xp[0]  # d^l_{1,-1}(0) = 0
+    # the deflection variance is the 2.5 arcmin rms of the workloads
+    assert abs(math.sqrt(xp[0]) - wl.DEFLECTION_RMS) < 1e-3 * wl.DEFLECTION_RMS
 
 
 def test_xi2_zero_lag():
