@@ -9,9 +9,9 @@
  *   Displacement   Sec. 3.1, lensed-direction equation:
  *                  n' = cos|d| n + sin|d| (d_theta e_theta + d_phi e_phi)/|d|.
  *   Covariances    Eq. fundamental_variance / Eq. correlation_func (spin 0),
- *                  Eq. v_spins / Eq. spins_correl (spin 2).
+ *                  Eq. v_spins / Eq. spins_correl (spin s = 1, 2).
  *   Estimate       Eq. best_temperature_field and Eq. gaussvar (spin 0),
- *                  Eq. major_eq and Eq. gaussvar_pol (spin 2).
+ *                  Eq. major_eq and Eq. gaussvar_pol (spin s).
  *   Regularisation Sec. 2.4: Cholesky of S + n I with n = 1.49e-8.
  *   xi tabulation  Sec. 2.5 step 2 and Appendix B: cubic interpolation.
  *
@@ -19,11 +19,14 @@
  * ---------------------------------------
  * - Map buffers are RING ordered, Npix = 12 Nside^2.  Spin-0 maps are double
  *   [Npix]; spin-2 maps are interleaved (Q, U) double [Npix][2], Q and U given
- *   in the local (e_theta, e_phi) frame of each pixel.
+ *   in the local (e_theta, e_phi) frame of each pixel; spin-1 maps likewise
+ *   hold the two components of a tangent vector field (e.g. a deflection
+ *   (d_theta, d_phi), the real and imaginary parts of P = d_theta + i d_phi).
  * - Deflections are double [count][2] = (d_theta, d_phi) in radians, the
  *   components of d in the local basis at the target pixel.
- * - Outputs: value double [count] (spin 0) or [count][2] (Q, U in the local
- *   frame at n'); variance double [count] (may be NULL); status uint8 [count]
+ * - Outputs: value double [count] (spin 0) or [count][2] (spin 1, 2: the two
+ *   components in the local frame at n'); variance double [count] (may be
+ *   NULL; spin s: of P); status uint8 [count]
  *   (may be NULL; FLINTS_ST_* bits, 0 = clean).
  * - All data pointers are DEVICE pointers owned by the caller, aligned to 16
  *   bytes, and must not overlap.  Calls are asynchronous on the given CUDA
@@ -70,10 +73,10 @@ enum {
      * the default when C^BB = C^EE (xi- = 0); strictly more precise otherwise.
      * Not accepted by the batch entry points. */
     FLINTS_SPIN2_AUGMENTED = 1u,
-    /* spin 2: return P in the frame at the target pixel n instead of the frame at
-     * the displaced direction n': P(n') times exp(2i(a_nn' - a_n'n)), a_uv the
-     * angle at u (from e_theta towards e_phi) of the geodesic towards v, i.e. the
-     * polarisation parallel-transported back along the deflection (Sec. 3.1
+    /* spin s = 1, 2: return P in the frame at the target pixel n instead of the
+     * frame at the displaced direction n': P(n') times exp(is(a_nn' - a_n'n - pi)),
+     * a_uv the angle at u (from e_theta towards e_phi) of the geodesic towards v,
+     * i.e. the field parallel-transported back along the deflection (Sec. 3.1
      * remaps P = Q + iU; the rotation is this library's reading) */
     FLINTS_ROTATE_TO_TARGET = 2u,
     FLINTS_NO_VARIANCE = 4u, /* skip the variance output even if a buffer is given */
@@ -105,7 +108,7 @@ typedef struct {
     int lmax, spin, K, precision;
     double t_max;        /* tabulated squared-chord domain [0, t_max] */
     int n_intervals;     /* cubic Hermite intervals of the xi table */
-    double xi0;          /* xi(0) (spin 0) or xi+(0) (spin 2) */
+    double xi0;          /* xi(0) (spin 0) or xi+(0) (spin 1, 2) */
     double search_radius;/* chord radius of the stencil disc */
 } flints_plan_info;
 
@@ -114,11 +117,16 @@ typedef struct {
  *   out        receives the plan (NULL on failure).
  *   nside      HEALPix resolution, 1 <= nside <= 16384.
  *   lmax       band limit, 0 <= lmax <= 16384.
- *   cl         HOST pointer, [lmax+1]: C_l^TT (spin 0) or C_l^EE (spin 2).
- *   cl_bb      HOST pointer, [lmax+1] C_l^BB (spin 2), or NULL for B = 0.
- *              Ignored for spin 0.
- *   spin       0 or 2.
- *   K          stencil size, 4 <= K <= 48.
+ *   cl         HOST pointer, [lmax+1]: C_l^TT (spin 0), C_l^EE (spin 2), or the
+ *              gradient-mode spectrum of a spin-1 field (a deflection
+ *              d = grad phi: C^E_l = l(l+1) C^phiphi_l).
+ *   cl_bb      HOST pointer, [lmax+1] C_l^BB (spin 1: curl mode), or NULL for
+ *              B = 0.  Ignored for spin 0.
+ *   spin       0, 1 or 2.  Spin-1 xi+- use d^l_{1,+-1}; the spin-s phases are
+ *              exp(is(a_ij - a_ji - pi)), frames referred to the geodesic's
+ *              direction of travel (the pi matters for odd s).  Spin-1 plans
+ *              run through flints_lens_range / flints_supersample.
+ *   K          stencil size: 16, 24, 32 or 48.
  *   precision  FLINTS_FP64 or FLINTS_MIXED.
  *   flags      FLINTS_* plan flags.
  *   stream     CUDA stream for the tabulation (the call returns after it).

@@ -278,6 +278,10 @@ class Plan:
         _dev_f64(out, comp, "out")
         if var is not None:
             _dev_f64(var, (self.npix,), "var")
+        if self.spin == 1:  # spin-1 plans use the range entry point over the whole map
+            _check(_lib.flints_lens_range(self._h, 0, self.npix, _ptr(map_), _ptr(defl), _ptr(out), _ptr(var), None,
+                                          _stream(stream)))
+            return out, var
         fn = _lib.flints_lens_spin0 if self.spin == 0 else _lib.flints_lens_spin2
         _check(fn(self._h, _ptr(map_), _ptr(defl), _ptr(out), _ptr(var), _stream(stream)))
         return out, var

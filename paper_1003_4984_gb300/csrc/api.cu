@@ -23,6 +23,8 @@ cudaError_t launch_lens_spin2(int K, int precision, const LensArgs &a, int R_rin
                               cudaStream_t st);
 cudaError_t launch_lens_spin2a(int K, int precision, const LensArgs &a, int R_rings, const LaunchCfg &cfg,
                                cudaStream_t st);
+cudaError_t launch_lens_spin1(int K, int precision, const LensArgs &a, int R_rings, const LaunchCfg &cfg,
+                              cudaStream_t st);
 
 int device_sm_count() {
     int dev = 0, n = 0;
@@ -42,6 +44,7 @@ size_t device_smem_optin() {
 cudaError_t launch_lens(int spin, int K, int precision, const LensArgs &a, int R_rings, const LaunchCfg &cfg,
                         cudaStream_t st) {
     if (spin == 0) return launch_lens_spin0(K, precision, a, R_rings, cfg, st);
+    if (spin == 1) return launch_lens_spin1(K, precision, a, R_rings, cfg, st);
     if (spin == 2) return launch_lens_spin2(K, precision, a, R_rings, cfg, st);
     if (spin == SPIN2_AUG) return launch_lens_spin2a(K, precision, a, R_rings, cfg, st);
     return cudaErrorInvalidValue;
@@ -112,7 +115,7 @@ int flints_plan(flints_plan_t *out, int64_t nside, int lmax, const double *cl, c
     if (nside < 1 || nside > 16384) return fail(FLINTS_EINVAL, "flints_plan: nside %lld outside [1, 16384]", (long long)nside);
     if (lmax < 0 || lmax > 16384) return fail(FLINTS_EINVAL, "flints_plan: lmax %d outside [0, 16384]", lmax);
     if (!cl) return fail(FLINTS_EINVAL, "flints_plan: cl is NULL");
-    if (spin != 0 && spin != 2) return fail(FLINTS_EINVAL, "flints_plan: spin must be 0 or 2");
+    if (spin != 0 && spin != 1 && spin != 2) return fail(FLINTS_EINVAL, "flints_plan: spin must be 0, 1 or 2");
     if (!supported_K(K)) return fail(FLINTS_EINVAL, "flints_plan: K must be 16, 24, 32 or 48 (got %d)", K);
     if (12 * nside * nside < K) return fail(FLINTS_EINVAL, "flints_plan: K exceeds the pixel count");
     if (precision != FLINTS_FP64 && precision != FLINTS_MIXED)
@@ -122,10 +125,10 @@ int flints_plan(flints_plan_t *out, int64_t nside, int lmax, const double *cl, c
         return fail(FLINTS_EINVAL, "flints_plan: unknown flag bits 0x%x", flags);
     if ((flags & FLINTS_SPIN2_AUGMENTED) && spin != 2)
         return fail(FLINTS_EINVAL, "flints_plan: FLINTS_SPIN2_AUGMENTED applies to spin-2 plans");
-    if ((flags & FLINTS_ROTATE_TO_TARGET) && spin != 2)
-        return fail(FLINTS_EINVAL, "flints_plan: FLINTS_ROTATE_TO_TARGET applies to spin-2 plans");
+    if ((flags & FLINTS_ROTATE_TO_TARGET) && spin == 0)
+        return fail(FLINTS_EINVAL, "flints_plan: FLINTS_ROTATE_TO_TARGET applies to spin-1 and spin-2 plans");
     for (int l = 0; l <= lmax; ++l) {
-        if (!std::isfinite(cl[l]) || (spin == 2 && cl_bb && !std::isfinite(cl_bb[l])))
+        if (!std::isfinite(cl[l]) || (spin != 0 && cl_bb && !std::isfinite(cl_bb[l])))
             return fail(FLINTS_EINVAL, "flints_plan: non-finite spectrum value at l = %d", l);
     }
     cudaStream_t st = (cudaStream_t)stream;
@@ -150,7 +153,7 @@ int flints_plan(flints_plan_t *out, int64_t nside, int lmax, const double *cl, c
         for (int l = 0; l <= lmax; ++l) {
             const double ld = (double)l;
             double c = std::fabs(cl[l]);
-            if (spin == 2 && cl_bb) c = std::fabs(cl[l]) + std::fabs(cl_bb[l]);
+            if (spin != 0 && cl_bb) c = std::fabs(cl[l]) + std::fabs(cl_bb[l]);
             const double a = (2.0 * ld + 1.0) / (4.0 * PI) * c;
             x0 += a;
             if (l >= 4)
@@ -184,7 +187,7 @@ int flints_plan(flints_plan_t *out, int64_t nside, int lmax, const double *cl, c
         return cuda_fail(e, "flints_plan: cudaMalloc");    \
     }
     ALLOC(p->d_cl, ncl * sizeof(double));
-    if (spin == 2 && cl_bb) {
+    if (spin != 0 && cl_bb) {
         ALLOC(p->d_clbb, ncl * sizeof(double));
     }
     ALLOC(p->d_f, nn * sizeof(double));
@@ -193,7 +196,7 @@ int flints_plan(flints_plan_t *out, int64_t nside, int lmax, const double *cl, c
     ALLOC(p->d_gm, nn * sizeof(double));
     ALLOC(p->d_c64, (size_t)p->n * sizeof(Coef64));
     ALLOC(p->d_c32, (size_t)p->n * 2 * sizeof(float4));
-    if (spin == 2) {
+    if (spin != 0) {
         ALLOC(p->d_cm64, (size_t)p->n * sizeof(Coef64));
         ALLOC(p->d_cm32, (size_t)p->n * 2 * sizeof(float4));
     }
@@ -228,7 +231,7 @@ int flints_plan(flints_plan_t *out, int64_t nside, int lmax, const double *cl, c
     p->xi0 = xi0;
     if ((e = finish_table(p->d_f, p->d_g, p->n, p->h, xi0, p->d_c64, p->d_c32, st)) != cudaSuccess)
         return bail(e, "flints_plan: table coefficients");
-    if (spin == 2 && (e = finish_table(p->d_fm, p->d_gm, p->n, p->h, xi0, p->d_cm64, p->d_cm32, st)) != cudaSuccess)
+    if (spin != 0 && (e = finish_table(p->d_fm, p->d_gm, p->n, p->h, xi0, p->d_cm64, p->d_cm32, st)) != cudaSuccess)
         return bail(e, "flints_plan: xi- table");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return bail(e, "flints_plan: table coefficients");
     *out = p;
@@ -310,7 +313,7 @@ int flints_lens_spin0(flints_plan_t p, const double *map, const double *defl, do
 int flints_lens_spin2(flints_plan_t p, const double *qu, const double *defl, double *qu_out, double *var,
                       void *stream) {
     if (!p) return fail(FLINTS_EINVAL, "plan is NULL");
-    if (p->spin != 2) return fail(FLINTS_EINVAL, "flints_lens_spin2 called with a spin-0 plan");
+    if (p->spin != 2) return fail(FLINTS_EINVAL, "flints_lens_spin2 called with a plan of spin %d", p->spin);
     return run(p, 0, 0, 12 * p->nside * p->nside, qu, defl, qu_out, var, nullptr, nullptr, stream);
 }
 
@@ -412,8 +415,9 @@ int flints_batch_stage(flints_batch_t b, const flints_job *jobs, int n, int tile
         flints_plan_s *p = j.plan;
         if (!p) return fail(FLINTS_EINVAL, "job %d: plan is NULL", i);
         if (p->device != b->device) return fail(FLINTS_EINVAL, "job %d: plan and batch on different devices", i);
-        if (p->flags & FLINTS_SPIN2_AUGMENTED)
-            return fail(FLINTS_EINVAL, "job %d: augmented spin-2 plans run through the single-plan entry points", i);
+        if ((p->flags & FLINTS_SPIN2_AUGMENTED) || p->spin == 1)
+            return fail(FLINTS_EINVAL, "job %d: spin-1 and augmented spin-2 plans run through the single-plan entry points",
+                        i);
         const int64_t npix = 12 * p->nside * p->nside;
         if (j.first < 0 || j.count < 0 || j.first > npix || j.count > npix - j.first)
             return fail(FLINTS_EINVAL, "job %d: target range outside the map", i);
@@ -575,7 +579,7 @@ int flints_get_info(flints_plan_t p, flints_plan_info *info) {
 
 int flints_get_table(flints_plan_t p, int which, double *f, double *g, void *stream) {
     if (!p || !f || !g) return fail(FLINTS_EINVAL, "flints_get_table: NULL argument");
-    if (which != 0 && !(which == 1 && p->spin == 2)) return fail(FLINTS_EINVAL, "flints_get_table: bad table index");
+    if (which != 0 && !(which == 1 && p->spin != 0)) return fail(FLINTS_EINVAL, "flints_get_table: bad table index");
     const size_t bytes = ((size_t)p->n + 1) * sizeof(double);
     cudaStream_t st = (cudaStream_t)stream;
     CK(cudaMemcpyAsync(f, which ? p->d_fm : p->d_f, bytes, cudaMemcpyDeviceToHost, st), "read table");

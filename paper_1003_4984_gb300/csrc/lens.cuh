@@ -59,7 +59,7 @@ struct RingRec {
 
 template <int K, int SPIN, class R>
 struct WarpSmem {
-    using Elem = typename std::conditional<SPIN == 2, Cx<typename Ops<R>::T>, typename Ops<R>::T>::type;
+    using Elem = typename std::conditional<SPIN == 1 || SPIN == 2, Cx<typename Ops<R>::T>, typename Ops<R>::T>::type;
     static constexpr int NSLOT = Shape<K>::NSLOT;
     // packed lower triangle of S + n I (row i starts at i(i+1)/2), then the two
     // bordered right-hand-side rows (c and y), K entries each; the augmented
@@ -209,19 +209,20 @@ __device__ __forceinline__ df table_eval<df>(const TableDev &tab, df t) {
     return p;
 }
 
-template <class R>
+template <class R, int S>
 __device__ __forceinline__ Cx<typename Ops<R>::T> pair_phase_uv(
     typename Ops<R>::T dx, typename Ops<R>::T dy, typename Ops<R>::T dz, typename Ops<R>::T zi,
     typename Ops<R>::T si, typename Ops<R>::T ci, typename Ops<R>::T sni, typename Ops<R>::T zj,
     typename Ops<R>::T sj, typename Ops<R>::T cj, typename Ops<R>::T snj, typename Ops<R>::T &u_out,
     typename Ops<R>::T &v_out);
 
-// exp(2i(a_ij - a_ji)) for the pair (i -> j) with d = X_j - X_i, from the
-// projections of d on the local bases at both ends: with e_theta = (z cos phi,
-// z sin phi, -s) and e_phi = (-sin phi, cos phi, 0),
-//   A = d.e_theta = z (dx cos phi + dy sin phi) - s dz,  B = d.e_phi = dy cos phi - dx sin phi,
-// exp(2i a) = (A + iB)^2 / (A^2 + B^2) at each end, the far end conjugated.
-template <class R>
+// exp(is(a_ij - a_ji - pi)) for the pair (i -> j) with d = X_j - X_i, spin s = S,
+// from the projections of d on the local bases at both ends: with e_theta =
+// (z cos phi, z sin phi, -s) and e_phi = (-sin phi, cos phi, 0),
+//   A = d.e_theta = z (dx cos phi + dy sin phi) - s dz,  B = d.e_phi = dy cos phi - dx sin phi.
+// At j, d points along the direction of travel (angle a_ji + pi), so with
+// q = (A1 + i B1)(A2 - i B2) the phase is (q / |q|)^s.
+template <class R, int S>
 __device__ __forceinline__ Cx<typename Ops<R>::T> pair_phase(typename Ops<R>::T dx, typename Ops<R>::T dy,
                                                              typename Ops<R>::T dz, typename Ops<R>::T zi,
                                                              typename Ops<R>::T si, typename Ops<R>::T ci,
@@ -229,11 +230,11 @@ __device__ __forceinline__ Cx<typename Ops<R>::T> pair_phase(typename Ops<R>::T 
                                                              typename Ops<R>::T sj, typename Ops<R>::T cj,
                                                              typename Ops<R>::T snj) {
     typename Ops<R>::T u_dummy, v_dummy;
-    return pair_phase_uv<R>(dx, dy, dz, zi, si, ci, sni, zj, sj, cj, snj, u_dummy, v_dummy);
+    return pair_phase_uv<R, S>(dx, dy, dz, zi, si, ci, sni, zj, sj, cj, snj, u_dummy, v_dummy);
 }
 
 // As pair_phase, also returning the projections (A1, B1) of d on e_theta, e_phi at i.
-template <class R>
+template <class R, int S>
 __device__ __forceinline__ Cx<typename Ops<R>::T> pair_phase_uv(
     typename Ops<R>::T dx, typename Ops<R>::T dy, typename Ops<R>::T dz, typename Ops<R>::T zi,
     typename Ops<R>::T si, typename Ops<R>::T ci, typename Ops<R>::T sni, typename Ops<R>::T zj,
@@ -249,9 +250,16 @@ __device__ __forceinline__ Cx<typename Ops<R>::T> pair_phase_uv(
     const T h2 = O::add(O::mul(dx, cj), O::mul(dy, snj));
     const T A2 = O::sub(O::mul(zj, h2), O::mul(sj, dz));
     const T B2 = O::sub(O::mul(dy, cj), O::mul(dx, snj));
-    // exp(2i a_ij) conj(exp(2i a_ji)) = q^2 / |q|^2 with q = (A1 + i B1)(A2 - i B2)
     const T qr = O::add(O::mul(A1, A2), O::mul(B1, B2));
     const T qi = O::sub(O::mul(B1, A2), O::mul(A1, B2));
+    if constexpr (S == 1) {
+        const T den1 = O::add(O::mul(qr, qr), O::mul(qi, qi));
+        if (!O::positive(den1)) return {O::from(1.0), O::zero()};  // coincident points: no rotation
+        T l, il;
+        O::pivot(den1, l, il);  // il = 1/|q|
+        return {O::mul(qr, il), O::mul(qi, il)};
+    }
+    // s = 2: q^2 / |q|^2
     const T qr2 = O::mul(qr, qr), qi2 = O::mul(qi, qi);
     const T nre = O::sub(qr2, qi2);
     const T qri = O::mul(qr, qi);
@@ -298,19 +306,22 @@ __device__ __forceinline__ Cx<typename Ops<R>::T> cx_conj(Cx<typename Ops<R>::T>
 // (u_i v_j - v_i u_j) / (4 - (t_i + t_j + t_ij)/2) (Van Oosterom-Strackee, with
 // (u, v) the tangent-plane coordinates at n' and t the squared chords), and
 // exp(-2iE) = (1 - ix)^4 / (1 + x^2)^2, i.e. 1 + delta with
-//   delta = (-8x^2 - 4ix(1 - x^2)) / (1 + x^2)^2.
+//   delta = (-8x^2 - 4ix(1 - x^2)) / (1 + x^2)^2
+// (spin 1: exp(-iE) = (1 - ix)^2 / (1 + x^2), delta = (-2x^2 - 2ix) / (1 + x^2)).
 // E is of order |X_i - n'||X_j - n'|, so delta is a small correction computed
 // in FP32 (the double-float path; the FP64 path uses the direct vector form,
 // cheaper in FP64 than the divisions below).
 struct Holo32 {
     float dr, di;
 };
+template <int S>
 __device__ __forceinline__ Holo32 holonomy32(float ui, float vi, float uj, float vj, float ti, float tj, float tij) {
     // x and w feed a correction of order x that is needed to FP32 accuracy only:
     // the fast divisions (2 ulp) suffice
     const float x = __fdividef(ui * vj - vi * uj, 4.0f - 0.5f * (ti + tj + tij));
     const float x2 = x * x;
     const float w = __fdividef(1.0f, 1.0f + x2);
+    if constexpr (S == 1) return {-2.0f * x2 * w, -2.0f * x * w};  // exp(-iE) = (1 - ix)^2 / (1 + x^2)
     const float q = w * w;
     return {-8.0f * x2 * q, -4.0f * x * (1.0f - x2) * q};
 }
@@ -487,13 +498,13 @@ __device__ bool solve_point(SM &sm, const PointA &P, int lane, double nugget, co
     Elem *mat = sm.u.mat;
 
     // ---- spin 2: per-neighbour target phases and tangent coordinates
-    if constexpr (SPIN == 2) {
+    if constexpr (SPIN == 1 || SPIN == 2) {
 #pragma unroll
         for (int r = 0; r < RPL; ++r) {
             const int i = lane + 32 * r;
             if (i < K) {
                 T u, v;
-                const Cx<T> ph = pair_phase_uv<R>(G::x(sm, i), G::y(sm, i), G::z(sm, i), O::from(P.z), O::from(P.s),
+                const Cx<T> ph = pair_phase_uv<R, SPIN>(G::x(sm, i), G::y(sm, i), G::z(sm, i), O::from(P.z), O::from(P.s),
                                                   O::from(P.cph), O::from(P.sph), G::nz(sm, i), G::ns(sm, i),
                                                   G::nc(sm, i), G::nsn(sm, i), u, v);
                 sm.p0r[i] = ph.re;
@@ -533,10 +544,10 @@ __device__ bool solve_point(SM &sm, const PointA &P, int lane, double nugget, co
                     Cx<T> ph;
                     if constexpr (std::is_same<R, double>::value) {
                         // FP64: the direct vector form is cheaper than the transported form's divisions
-                        ph = pair_phase<R>(dx, dy, dz, G::nz(sm, i), G::ns(sm, i), G::nc(sm, i), G::nsn(sm, i),
+                        ph = pair_phase<R, SPIN>(dx, dy, dz, G::nz(sm, i), G::ns(sm, i), G::nc(sm, i), G::nsn(sm, i),
                                            G::nz(sm, j), G::ns(sm, j), G::nc(sm, j), G::nsn(sm, j));
                     } else {
-                        const Holo32 hol = holonomy32(sm.pu[i].hi, sm.pv[i].hi, sm.pu[j].hi, sm.pv[j].hi, sm.ktf[i],
+                        const Holo32 hol = holonomy32<SPIN>(sm.pu[i].hi, sm.pv[i].hi, sm.pu[j].hi, sm.pv[j].hi, sm.ktf[i],
                                                       sm.ktf[j], t.hi);
                         ph = transported_phase(Cx<df>{sm.p0r[i], sm.p0i[i]}, Cx<df>{sm.p0r[j], sm.p0i[j]}, hol);
                     }
@@ -800,20 +811,26 @@ __device__ __forceinline__ void process_tile(const LensArgs &a, int R_rings, int
             P.rot_re = 1.0;
             P.rot_im = 0.0;
             if (SPIN != 0 && a.rotate && dl > 0.0) {
-                // P(n) = P(n') exp(2i(a_nn' - a_n'n)) with a_uv the angle at u, from e_theta
-                // towards e_phi, of the geodesic towards v: the polarisation parallel-
+                // P(n) = P(n') exp(is(a_nn' - a_n'n - pi)) with a_uv the angle at u, from
+                // e_theta towards e_phi, of the geodesic towards v: the field parallel-
                 // transported back along the deflection.  At n the direction is
                 // (d_theta, d_phi) itself; at n' it is (n . e_theta(n'), n . e_phi(n')).
                 const double w1r = dd.x, w1i = dd.y;
                 const double cq = P.cph, sq = P.sph;
                 const double w2r = nx * z * cq + ny * z * sq - nz * s, w2i = ny * cq - nx * sq;
-                const double a1r = w1r * w1r - w1i * w1i, a1i = 2.0 * w1r * w1i;
-                const double a2r = w2r * w2r - w2i * w2i, a2i = 2.0 * w2r * w2i;
                 const double n1 = w1r * w1r + w1i * w1i, n2 = w2r * w2r + w2i * w2i;
                 if (n1 > 0.0 && n2 > 0.0) {
-                    const double inv = 1.0 / (n1 * n2);
-                    P.rot_re = (a1r * a2r + a1i * a2i) * inv;  // a1 conj(a2)
-                    P.rot_im = (a1i * a2r - a1r * a2i) * inv;
+                    if (SPIN == 1) {
+                        const double inv = -rsqrt(n1 * n2);  // exp(-i pi) for odd spin
+                        P.rot_re = (w1r * w2r + w1i * w2i) * inv;  // w1 conj(w2) / |w1 w2|
+                        P.rot_im = (w1i * w2r - w1r * w2i) * inv;
+                    } else {
+                        const double a1r = w1r * w1r - w1i * w1i, a1i = 2.0 * w1r * w1i;
+                        const double a2r = w2r * w2r - w2i * w2i, a2i = 2.0 * w2r * w2i;
+                        const double inv = 1.0 / (n1 * n2);
+                        P.rot_re = (a1r * a2r + a1i * a2i) * inv;  // a1 conj(a2)
+                        P.rot_im = (a1i * a2r - a1r * a2i) * inv;
+                    }
                 }
             }
             P.zf = (float)z;

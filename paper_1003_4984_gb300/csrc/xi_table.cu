@@ -8,13 +8,14 @@
 //     D_{l+1} = (l D_l - (2l+1) u P_l) / (l+1),   P_{l+1} = P_l + D_{l+1},
 // which forms P_l near x = 1 without cancellation.  P'_{l+1} = P'_{l-1} + (2l+1) P_l.
 //
-// Spin 2 (Eq. spins_correl): xi+ = sum_l (2l+1)/(4 pi) (C^EE + C^BB) d^l_{22},
-// xi- = sum_l (2l+1)/(4 pi) (C^EE - C^BB) d^l_{2,-2}, from the Wigner-d
-// recurrence in l at fixed (m, m') = (2, +-2):
+// Spin s = 1, 2 (Eq. spins_correl): xi+ = sum_l (2l+1)/(4 pi) (C^E + C^B) d^l_{ss},
+// xi- = sum_l (2l+1)/(4 pi) (C^E - C^B) d^l_{s,-s}, from the Wigner-d
+// recurrence in l at fixed (m, m') = (s, +-s):
 //     d_{l+1} = a_l (b_l x - m m') d_l - e_l d_{l-1},
-//     a_l = (2l+1) / (l((l+1)^2-4)),  b_l = l(l+1),  e_l = (l+1)(l^2-4) / (l((l+1)^2-4)),
-// started from d^2_{22} = ((1+x)/2)^2 and d^2_{2,-2} = ((1-x)/2)^2.  Because
-// d^l_{22}(1) = 1 for all l, a_l (b_l - 4) - e_l = 1 and the increments obey
+//     a_l = (2l+1) / (l((l+1)^2-s^2)),  b_l = l(l+1),  e_l = (l+1)(l^2-s^2) / (l((l+1)^2-s^2)),
+// started at l = s from d^s_{ss} = ((1+x)/2)^s and d^s_{s,-s} = ((1-x)/2)^s
+// (e_s = 0, so no l = s-1 term is needed).  Because d^l_{ss}(1) = 1 for all l,
+// a_l (b_l - s^2) - e_l = 1 and the increments obey
 //     D_{l+1} = e_l D_l - a_l b_l u d_l,
 // the same cancellation-free form as for spin 0.  x-derivatives follow by
 // differentiating the recurrence; d/dt = -1/2 d/dx.
@@ -55,13 +56,17 @@ __global__ void xi_table_kernel(int spin, int lmax, const double *__restrict__ c
         g[k] = -0.5 * dacc;
         return;
     }
-    // spin 2
+    // spin s = 1 or 2
+    const int sp_ = spin == 1 ? 1 : 2;
+    const double s2 = (double)(sp_ * sp_);
     double sp = 0.0, dsp = 0.0, sm = 0.0, dsm = 0.0;
-    if (lmax >= 2) {
+    if (lmax >= sp_) {
         const double x = 1.0 - u;
-        double d = (1.0 - 0.5 * u) * (1.0 - 0.5 * u), D = 0.0, dd = 1.0 - 0.5 * u, ddm = 0.0;
-        double e2 = 0.25 * u * u, de2 = -0.5 * u, e2m = 0.0, de2m = 0.0;
-        for (int l = 2; l <= lmax; ++l) {
+        // ((1+x)/2)^s, ((1-x)/2)^s = (u/2)^s and their x-derivatives
+        const double hp = 1.0 - 0.5 * u, hm = 0.5 * u;
+        double d = sp_ == 1 ? hp : hp * hp, D = 0.0, dd = sp_ == 1 ? 0.5 : hp, ddm = 0.0;
+        double e2 = sp_ == 1 ? hm : hm * hm, de2 = sp_ == 1 ? -0.5 : -hm, e2m = 0.0, de2m = 0.0;
+        for (int l = sp_; l <= lmax; ++l) {
             const double ld = (double)l;
             const double bb = clbb ? clbb[l] : 0.0;
             const double wp = (2.0 * ld + 1.0) * inv4pi * (cl[l] + bb);
@@ -72,17 +77,17 @@ __global__ void xi_table_kernel(int spin, int lmax, const double *__restrict__ c
             dsm += wm * de2;
             if (l == lmax) break;
             const double lp = ld + 1.0;
-            const double den = ld * (lp * lp - 4.0);
+            const double den = ld * (lp * lp - s2);
             const double al = (2.0 * ld + 1.0) / den;
             const double bl = ld * lp;
-            const double el = lp * (ld * ld - 4.0) / den;
-            // d^l_{22}
+            const double el = lp * (ld * ld - s2) / den;
+            // d^l_{ss}
             const double Dn = el * D - al * bl * u * d;
             const double dn = d + Dn;
-            const double ddn = al * (bl * x - 4.0) * dd + al * bl * d - el * ddm;
-            // d^l_{2,-2}
-            const double e2n = al * (bl * x + 4.0) * e2 - el * e2m;
-            const double de2n = al * (bl * x + 4.0) * de2 + al * bl * e2 - el * de2m;
+            const double ddn = al * (bl * x - s2) * dd + al * bl * d - el * ddm;
+            // d^l_{s,-s}
+            const double e2n = al * (bl * x + s2) * e2 - el * e2m;
+            const double de2n = al * (bl * x + s2) * de2 + al * bl * e2 - el * de2m;
             D = Dn;
             ddm = dd;
             d = dn;

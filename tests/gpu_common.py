@@ -31,6 +31,8 @@ def oracle_table(cl, cl_bb, spin, K, nside):
     t_max, n = xi.grid_rule(weight, K, nside)
     if spin == 0:
         tab, x0 = xi.spin0_table(cl, t_max, n)
+    elif spin == 1:
+        tab, _, x0 = xi.spin1_tables(cl, cl_bb, t_max, n)
     else:
         tab, _, x0 = xi.spin2_tables(cl, cl_bb, t_max, n)
     return tab, x0, t_max, n

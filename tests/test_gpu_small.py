@@ -36,9 +36,13 @@ def torch():
 
 # ---------------------------------------------------------------- xi tables
 @pytest.mark.parametrize("spin,nside,lmax,ld,K", [(0, 64, 128, 100.0, 16), (0, 2048, 4096, 2500.0, 32),
-                                                    (2, 4096, 4096, 2500.0, 32), (2, 256, 512, 312.0, 48)])
+                                                    (2, 4096, 4096, 2500.0, 32), (2, 256, 512, 312.0, 48),
+                                                    (1, 2048, 4096, 2500.0, 32), (1, 64, 128, 100.0, 16)])
 def test_xi_table_matches_oracle(fl, spin, nside, lmax, ld, K):
-    cl = wl.cl_tt(lmax, ld) if spin == 0 else wl.cl_ee(lmax, ld)
+    if spin == 1:  # deflection spectrum l(l+1) C^phiphi
+        cl = wl.cl_phiphi(lmax) * np.arange(lmax + 1) * np.arange(1, lmax + 2)
+    else:
+        cl = wl.cl_tt(lmax, ld) if spin == 0 else wl.cl_ee(lmax, ld)
     bb = None if spin == 0 else 0.1 * cl
     plan = fl.Plan(nside, cl, bb, spin=spin, K=K)
     info = plan.info()
@@ -50,7 +54,7 @@ def test_xi_table_matches_oracle(fl, spin, nside, lmax, ld, K):
     if spin == 0:
         ref, dref = xi.xi0_direct(cl, nodes, deriv=True)
     else:
-        xp, xm, dxp, dxm = xi.xi2_direct(cl, bb, nodes, deriv=True)
+        xp, xm, dxp, dxm = xi.xis_direct(spin, cl, bb, nodes, deriv=True)
         ref, dref = xp, dxp
         fm, gm = plan.table(1)
         np.testing.assert_allclose(fm, xm / xp[0], atol=1e-13)
@@ -224,6 +228,36 @@ def test_spin2_rotation_to_target_frame(fl, torch, precision):
     assert parity_metric(v[:, 0] + 1j * v[:, 1], ref.value, sigma) <= TOL[precision]
     with pytest.raises(fl.FlintsError):
         fl.Plan(nside, wl.cl_tt(lmax, 50.0), spin=0, K=K, flags=fl.FLINTS_ROTATE_TO_TARGET)
+
+
+def _deflection_field(nside, lmax, seed):
+    phi = wl.draw_alm(wl.cl_phiphi(lmax), seed)
+    ell = np.arange(lmax + 1)
+    cle = wl.cl_phiphi(lmax) * ell * (ell + 1)
+    return cle, np.ascontiguousarray(sht.synth_map(nside, lmax, phi, gradient=True))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("K,rotate", [(16, False), (32, False), (48, False), (32, True)])
+def test_spin1_deflection_parity(fl, torch, precision, K, rotate):
+    # spin 1: a deflection field d = grad phi (P = d_theta + i d_phi) lensed by another
+    nside, lmax = 32, 64
+    cle, m = _deflection_field(nside, lmax, 55)
+    npix = hp.npix(nside)
+    defl = wl.random_deflection(npix, 56) * 8
+    tab, x0, _, _ = oracle_table(cle, None, 1, K, nside)
+    ref = kr.lens(nside, K, 1, m, defl, np.arange(npix), tab, x0, rotate=rotate)
+    flags = fl.FLINTS_ROTATE_TO_TARGET if rotate else 0
+    plan = fl.Plan(nside, cle, spin=1, K=K, precision=precision, flags=flags)
+    out = torch.empty((npix, 2), dtype=torch.float64, device="cuda")
+    var = torch.empty(npix, dtype=torch.float64, device="cuda")
+    plan.lens_full(torch.from_numpy(m).cuda(), torch.from_numpy(defl).cuda(), out, var)
+    torch.cuda.synchronize()
+    v = to_host(out)
+    sigma = float(np.sqrt(np.mean(np.sum(m ** 2, axis=1))))
+    assert parity_metric(v[:, 0] + 1j * v[:, 1], ref.value, sigma) <= TOL[precision]
+    assert parity_metric(to_host(var), ref.variance, x0) <= TOL[precision]
+    assert plan.stats()["failed"] == 0
 
 
 @pytest.mark.parametrize("K", [16, 24, 48])

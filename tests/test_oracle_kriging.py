@@ -239,10 +239,11 @@ def test_spin2_error_statistics_match_predicted_variance():
     assert rel < 0.2
 
 
-def test_spin2_pair_phase_factorises_through_the_target():
-    # The pair phase equals conj(phase(n', a)) phase(n', b) exp(-2iE), E the spherical excess
+@pytest.mark.parametrize("spin", [1, 2])
+def test_spin2_pair_phase_factorises_through_the_target(spin):
+    # The pair phase equals conj(phase(n', a)) phase(n', b) exp(-isE), E the spherical excess
     # of the triangle (n', a, b): tan(E/2) = n'.(a x b) / (1 + n'.a + a.b + b.n')
-    # (Van Oosterom-Strackee).  The CUDA path assembles spin-2 covariances this way.
+    # (Van Oosterom-Strackee).  The CUDA path assembles spin-s covariances this way.
     n = RNG.normal(size=(500, 3))
     n /= np.linalg.norm(n, axis=1)[:, None]
     for scale in (1e-3, 3e-2, 0.3):
@@ -253,9 +254,9 @@ def test_spin2_pair_phase_factorises_through_the_target():
         triple = np.einsum("pi,pi->p", n, np.cross(a, b))
         den = 1 + np.sum(n * a, 1) + np.sum(a * b, 1) + np.sum(b * n, 1)
         x = triple / den
-        g = (1 - 1j * x) ** 4 / (1 + x * x) ** 2  # exp(-2iE) with E = 2 atan(x)
-        got = np.conj(kr.pair_phase(n, a)) * kr.pair_phase(n, b) * g
-        np.testing.assert_allclose(got, kr.pair_phase(a, b), atol=1e-12)
+        g = ((1 - 1j * x) ** 2 / (1 + x * x)) ** spin  # exp(-isE) with E = 2 atan(x)
+        got = np.conj(kr.pair_phase(n, a, spin)) * kr.pair_phase(n, b, spin) * g
+        np.testing.assert_allclose(got, kr.pair_phase(a, b, spin), atol=1e-12)
 
 
 # ------------------------------------------------- supersampling (Sec. 2.6)
