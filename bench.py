@@ -31,6 +31,10 @@ import numpy as np  # noqa: E402
 import workloads as wl  # noqa: E402
 
 METRIC = "lensed pts/s at Nside 4096 spin-2 K=32, mixed vs FP64 @2e-4 rel err; p50/p99 ms"
+# DRAM bytes (read + write) per target of lens_kernel<32,2,mixed>, from the ncu capture of
+# `bench.py --profile-case mixed` (13.868 MB for 2^18 targets; profiles/lens_kernel_c3_full_sets.md),
+# scaled to a launch by its target count
+MIXED_DRAM_BYTES_PER_POINT = 13.868288e6 / (1 << 18)
 BATCH = 1 << 24
 W = wl.C3
 
@@ -308,7 +312,10 @@ def run_ours(args):
         "e2e": {"value": n_gpus * BATCH * nb_e2e / (e2e_ms / 1e3), "unit": "pts/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": flops.FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / flops.FP32_PEAK_TFLOPS, "traffic": None,
+                     "frac": achieved / flops.FP32_PEAK_TFLOPS,
+                     "traffic": None if aug else MIXED_DRAM_BYTES_PER_POINT * BATCH,
+                     "traffic_note": "ncu capture of 2^18 targets scaled to the launch; outputs of that case "
+                                     "stayed in L2 (at 2^24 targets 24 B/point more are written back)",
                      "kernel": "lens_kernel<32,%d,mixed> (FP32 pipe, double-float)" % (3 if aug else 2),
                      "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
                      "flops_per_point": fl32},
