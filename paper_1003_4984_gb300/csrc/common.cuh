@@ -163,6 +163,7 @@ struct Ops<double> {
     static __device__ __forceinline__ void sub_prod(Acc &a, T x, T y) { a.v = fma(-x, y, a.v); }
     static __device__ __forceinline__ void add_prod(Acc &a, T x, T y) { a.v = fma(x, y, a.v); }
     static __device__ __forceinline__ T val(Acc a) { return a.v; }
+    static __device__ __forceinline__ T raw(Acc a) { return a.v; }
     static __device__ __forceinline__ T shfl(T v, int src) { return __shfl_sync(FULL, v, src); }
     static __device__ __forceinline__ T shfl_xor(T v, int m) { return __shfl_xor_sync(FULL, v, m); }
 };
@@ -187,6 +188,8 @@ struct Ops<df> {
     static __device__ __forceinline__ void sub_prod(Acc &a, T x, T y) { dfacc_sub_prod(a, x, y); }
     static __device__ __forceinline__ void add_prod(Acc &a, T x, T y) { dfacc_add_prod(a, x, y); }
     static __device__ __forceinline__ T val(Acc a) { return dfacc_val(a); }
+    // the accumulator's two words as stored, unnormalised (acc() reads them back)
+    static __device__ __forceinline__ T raw(Acc a) { return {a.hi, a.lo}; }
     static __device__ __forceinline__ T shfl(T v, int src) {
         return {__shfl_sync(FULL, v.hi, src), __shfl_sync(FULL, v.lo, src)};
     }

@@ -474,6 +474,121 @@ __device__ __forceinline__ bool bordered_cholesky(Elem *mat, int lane) {
     return true;
 }
 
+// Right-looking form of the same factorisation.  Step j takes the pivot of
+// column j, scales the column, and applies the rank-one update
+// A_rc -= L_rj conj(L_cj) to every trailing entry (j < c <= r, bordered rows
+// included), the entries spread round-robin over the 32 lanes.  Trailing
+// entries are kept as unnormalised accumulators between steps (for double-
+// float the running TwoSum word and the collected error word) and normalised
+// when they become part of a column.  Compared with the split left-looking
+// form, every lane stays busy until the last few columns and no shuffle
+// reductions are needed.
+template <int N, int NB, class R, class Elem>
+__device__ __forceinline__ bool bordered_cholesky_rl(Elem *mat, int lane) {
+    using O = Ops<R>;
+    using T = typename O::T;
+    constexpr bool CPLX = !std::is_same<Elem, T>::value;
+    constexpr int NROW = N + NB;
+    for (int j = 0; j < N; ++j) {
+        // pivot
+        T d;
+        if constexpr (CPLX) {
+            d = O::val(O::acc(mat[tri<N>(j, j)].re));
+        } else {
+            d = O::val(O::acc(mat[tri<N>(j, j)]));
+        }
+        if (!O::positive(d)) return false;
+        T ljj, il;
+        O::pivot(d, ljj, il);
+        // column j
+        for (int r = j + 1 + lane; r < NROW; r += 32) {
+            Elem a = mat[tri<N>(r, j)];
+            if constexpr (CPLX) {
+                a.re = O::mul(O::val(O::acc(a.re)), il);
+                a.im = O::mul(O::val(O::acc(a.im)), il);
+            } else {
+                a = O::mul(O::val(O::acc(a)), il);
+            }
+            mat[tri<N>(r, j)] = a;
+        }
+        if (lane == 0) {
+            if constexpr (CPLX) {
+                mat[tri<N>(j, j)] = Elem{ljj, O::zero()};
+            } else {
+                mat[tri<N>(j, j)] = ljj;
+            }
+        }
+        __syncwarp();
+        // rank-one update of the trailing entries: the triangle of rows and
+        // columns j+1..N-1 (m(m+1)/2 entries, walked as q = ri(ri+1)/2 + ci),
+        // then the NB bordered rows (m entries each)
+        const int m = N - 1 - j;
+        const int ntri = m * (m + 1) / 2, ntot = ntri + NB * m;
+        int ri = 0, ci = lane;
+        while (ci > ri) {
+            ci -= ri + 1;
+            ++ri;
+        }
+        int br = -1, bc = 0;
+        for (int q = lane; q < ntot; q += 32) {
+            int r, c;
+            if (q < ntri) {
+                r = j + 1 + ri;
+                c = j + 1 + ci;
+                ci += 32;
+                while (ci > ri) {
+                    ci -= ri + 1;
+                    ++ri;
+                }
+            } else {
+                if (br < 0) {
+                    const int qq = q - ntri;
+                    br = qq / m;
+                    bc = qq - br * m;
+                }
+                r = N + br;
+                c = j + 1 + bc;
+                bc += 32;
+                while (bc >= m) {
+                    bc -= m;
+                    ++br;
+                }
+            }
+            Elem a = mat[tri<N>(r, c)];
+            const Elem x = mat[tri<N>(r, j)], y = mat[tri<N>(c, j)];
+            if constexpr (CPLX) {  // a -= x conj(y)
+                typename O::Acc ar = O::acc(a.re), ai = O::acc(a.im);
+                O::sub_prod(ar, x.re, y.re);
+                O::sub_prod(ai, x.im, y.re);
+                O::sub_prod(ar, x.im, y.im);
+                O::add_prod(ai, x.re, y.im);
+                a.re = O::raw(ar);
+                a.im = O::raw(ai);
+            } else {
+                typename O::Acc ac = O::acc(a);
+                O::sub_prod(ac, x, y);
+                a = O::raw(ac);
+            }
+            mat[tri<N>(r, c)] = a;
+        }
+        __syncwarp();
+    }
+    return true;
+}
+
+// Choice between the two forms, measured on GB300 (c3-like targets): in FP64
+// the pipe executes inactive lanes too, so the right-looking form's fuller
+// lanes win for N <= 32 (spin 2, K = 32: +15 %); in double-float, and for larger
+// N, the left-looking form's register accumulators win (right-looking was 21 %
+// slower for double-float spin 2, K = 32, and 28 % slower in FP64 at N = 48).
+template <int N, int NB, class R, class Elem>
+__device__ __forceinline__ bool factor_bordered(Elem *mat, int lane) {
+    if constexpr (std::is_same<R, double>::value && N <= 32)
+        return bordered_cholesky_rl<N, NB, R>(mat, lane);
+    else
+        return bordered_cholesky<N, NB, R>(mat, lane);
+}
+
 // Returns false when a pivot of S + nugget I is not positive.
 
 //
@@ -587,7 +702,7 @@ __device__ bool solve_point(SM &sm, const PointA &P, int lane, double nugget, co
     }
     __syncwarp();
 
-    if (!bordered_cholesky<K, 2, R>(mat, lane)) return false;
+    if (!factor_bordered<K, 2, R>(mat, lane)) return false;
     // ---- value = z_c^H z_y = sum_k row_K[k] conj(row_K+1[k]);  variance = 1 - |z_c|^2
     double vr = 0.0, vi = 0.0, nc = 0.0;
 #pragma unroll
@@ -696,7 +811,7 @@ __device__ bool solve_point_aug(SM &sm, const PointA &P, int lane, double nugget
         }
     }
     __syncwarp();
-    if (!bordered_cholesky<N, 3, R>(mat, lane)) return false;
+    if (!factor_bordered<N, 3, R>(mat, lane)) return false;
     double vq = 0.0, vu = 0.0, nn = 0.0;
     for (int k = lane; k < N; k += 32) {
         const double zq = O::to(mat[tri<N>(N, k)]), zu = O::to(mat[tri<N>(N + 1, k)]);
