@@ -238,6 +238,29 @@ int flints_get_table(flints_plan_t plan, int which, double *f, double *g, void *
 /* Message describing the last error returned on the calling thread. */
 const char *flints_last_error(void);
 
+/* Harmonic synthesis of a band-limited map on the GPU: the unlensed input of
+ * the remap (Sec. 3.2 synthesises it from C_l; Table 2 counts the transform in
+ * the total).  With sY_lm = (-1)^s N_l e^{i m phi} d^l_{m,-s}(theta) (Appendix A):
+ *   spin 0: T = sum_lm a_lm Y_lm;
+ *   spin s = 1, 2: P = -sum_lm (E + iB)_lm sY_lm, written as (Re P, Im P):
+ *     (Q, U) for s = 2; (d_theta, d_phi) for s = 1 when E_lm = sqrt(l(l+1)) phi_lm.
+ * E, B are real fields (a_{l,-m} = (-1)^m conj(a_lm)); only m >= 0 is given.
+ *   flints_synth_plan: ring geometry, work arrays (about (4 Nside - 1)(2 lmax + 1)
+ *     + Npix complex doubles) and the cuFFT plans for Nside (1..8192), lmax
+ *     (spin..16384) and spin (0, 1, 2).  Allocates; not capturable.
+ *   flints_synthesize: alm (and blm for spin 1, 2; NULL = 0) DEVICE complex
+ *     double [lmax+1][lmax+1] (index [l][m], m <= l read), 16-byte aligned;
+ *     map DEVICE double [Npix] (spin 0) or [Npix][2] (spin 1, 2), RING order.
+ *     Asynchronous on `stream`: an l-recurrence kernel, a folding kernel and
+ *     one inverse FFT per ring size.
+ * Errors: FLINTS_EINVAL (arguments), FLINTS_ENOMEM, FLINTS_ECUDA; the message
+ * is returned by flints_synth_last_error. */
+typedef struct flints_synth_s *flints_synth_t;
+int flints_synth_plan(flints_synth_t *out, int64_t nside, int lmax, int spin, void *stream);
+int flints_synthesize(flints_synth_t plan, const double *alm, const double *blm, double *map, void *stream);
+void flints_synth_free(flints_synth_t plan);
+const char *flints_synth_last_error(void);
+
 /* Lens the target range [first, first+count) without allocating any device
  * memory.  The paper has no counterpart: this entry point exists for callers
  * that cannot call cudaMalloc -- code running during CUDA stream capture,

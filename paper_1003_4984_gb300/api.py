@@ -102,6 +102,13 @@ def load_library(path: str = LIB_PATH):
     lib.flints_lens_noalloc.argtypes = [i64, c_int, dp, dp, c_int, c_int, c_int, i64, i64, vp, vp, vp, vp, vp, vp]
     lib.flints_lens_noalloc.restype = c_int
     lib.flints_noalloc_last_error.restype = ctypes.c_char_p
+    lib.flints_synth_plan.argtypes = [ctypes.POINTER(vp), i64, c_int, c_int, vp]
+    lib.flints_synth_plan.restype = c_int
+    lib.flints_synthesize.argtypes = [vp, vp, vp, vp, vp]
+    lib.flints_synthesize.restype = c_int
+    lib.flints_synth_free.argtypes = [vp]
+    lib.flints_synth_free.restype = None
+    lib.flints_synth_last_error.restype = ctypes.c_char_p
     for name in ("flints_plan", "flints_lens_spin0", "flints_lens_spin2", "flints_lens_range", "flints_stencil",
                  "flints_lens_batch", "flints_get_stats", "flints_reset_stats", "flints_get_info",
                  "flints_get_table"):
@@ -389,3 +396,54 @@ def lens_noalloc(nside: int, cl, map_, defl, out, var=None, status=None, cl_bb=N
     if rc != 0:
         raise FlintsError(f"flints error {rc}: {lib.flints_noalloc_last_error().decode()}")
     return out, var, status
+
+
+class Synth:
+    """GPU harmonic synthesis (flints_synth_plan / flints_synthesize): band-limited
+    RING maps from a_lm.  Spin 0: T; spin 1, 2: (Re P, Im P) of P = -sum (E + iB) sY_lm."""
+
+    def __init__(self, nside: int, lmax: int, spin: int = 0, stream=None):
+        lib = load_library()
+        self.nside, self.lmax, self.spin = int(nside), int(lmax), int(spin)
+        self.npix = 12 * self.nside * self.nside
+        h = ctypes.c_void_p()
+        rc = lib.flints_synth_plan(ctypes.byref(h), self.nside, self.lmax, self.spin, _stream(stream))
+        if rc != 0:
+            raise FlintsError(f"flints error {rc}: {lib.flints_synth_last_error().decode()}")
+        self._h = h
+
+    def _alm(self, a, name):
+        import torch
+
+        if a is None:
+            return None
+        if not (isinstance(a, torch.Tensor) and a.is_cuda and a.dtype == torch.complex128
+                and tuple(a.shape) == (self.lmax + 1, self.lmax + 1) and a.is_contiguous()):
+            raise FlintsError(f"{name} must be a contiguous complex128 CUDA tensor of shape (lmax+1, lmax+1)")
+        return a
+
+    def run(self, alm, blm=None, out=None, stream=None):
+        import torch
+
+        alm = self._alm(alm, "alm")
+        blm = self._alm(blm, "blm")
+        shape = (self.npix,) if self.spin == 0 else (self.npix, 2)
+        if out is None:
+            out = torch.empty(shape, dtype=torch.float64, device=alm.device)
+        _dev_f64(out, shape, "out")
+        lib = load_library()
+        rc = lib.flints_synthesize(self._h, _ptr(alm), _ptr(blm), _ptr(out), _stream(stream))
+        if rc != 0:
+            raise FlintsError(f"flints error {rc}: {lib.flints_synth_last_error().decode()}")
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().flints_synth_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

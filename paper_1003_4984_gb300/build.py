@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 SO = os.path.join(LIBDIR, "libflints.so")
 SOURCES = ["api.cu", "xi_table.cu", "lens_spin0.cu", "lens_spin1.cu", "lens_spin2.cu", "lens_spin2a.cu", "noalloc.cu",
-           "batch_p0.cu", "batch_p1.cu"]
+           "batch_p0.cu", "batch_p1.cu", "synth.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -65,7 +65,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
             if verbose and log:
                 sys.stderr.write(log)
     tmp = SO + f".tmp{os.getpid()}"
-    cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs
+    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(cc))), "lib64")
+    cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcufft", "-Xlinker", "-rpath", "-Xlinker", cuda_lib]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

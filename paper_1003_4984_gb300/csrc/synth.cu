@@ -1,0 +1,486 @@
+// Harmonic synthesis of a band-limited HEALPix map on the GPU: the unlensed
+// input of the remap (Sec. 3.2 draws it from C_l and synthesises it; Table 2
+// counts that transform in the total time).  Spin s = 0, 1, 2:
+//
+//   spin 0:  T(theta, phi) = sum_{l,m} a_lm sY_lm,
+//   spin s:  P = -sum_{l,m} (E + iB)_lm sY_lm  (P = Q + iU for s = 2; for s = 1
+//            with E_lm = sqrt(l(l+1)) phi_lm it is the gradient d_theta + i d_phi),
+//
+// with sY_lm(theta, phi) = (-1)^s N_l e^{i m phi} d^l_{m,-s}(theta),
+// N_l = sqrt((2l+1)/(4 pi)) (Appendix A), and real E, B fields
+// (a_{l,-m} = (-1)^m a_lm^*).  Per ring the sum over l gives coefficients
+//
+//   spin 0:  F_m = sum_l a_lm N_l d^l_{m,0}                       (m >= 0),
+//   spin s:  P_m  = -(-1)^s sum_l (E + iB)_lm N_l d^l_{m,-s},
+//            P_-m = -sum_l (E^* + iB^*)_lm N_l d^l_{m,s}            (m >= 1),
+//
+// and the ring values are the Fourier sums sum_m F_m e^{i m phi_j}, done by
+// folding m modulo the ring length and one inverse FFT per ring (cuFFT).
+//
+// The l-sums use the Wigner-d three-term recurrence in l at fixed (m, m'):
+//   d^{l+1} = (A_l x - B_l) d^l - C_l d^{l-1},  A_l = (2l+1) l (l+1) / D_l,
+//   B_l = (2l+1) m m' / D_l,  C_l = (l+1) sqrt((l^2-m^2)(l^2-m'^2)) / D_l,
+//   D_l = l sqrt(((l+1)^2-m^2)((l+1)^2-m'^2)),  x = cos(theta),
+// started at l0 = max(m, |m'|) from the closed form
+//   d^l_{l,b} = (-1)^{l-b} sqrt((2l)! / ((l+b)!(l-b)!)) c^{l+b} s^{l-b},
+//   d^l_{-l,b} = sqrt((2l)! / ((l+b)!(l-b)!)) c^{l-b} s^{l+b}   (c, s = cos, sin theta/2)
+// with d^l_{m,m'} = d^l_{-m',-m} when |m'| > m.  The start is formed in
+// base-2 logarithms and carried as v 2^E (E an integer, raised in steps of 256
+// while |v| > 2^256), so columns whose start underflows (large m near the
+// poles) still reach their oscillatory range.  One thread runs the columns of
+// one (ring, m) pair for the northern ring and, through
+//   d^l_{m,m'}(pi - theta) = (-1)^{l+m} d^l_{m,-m'}(theta),
+// for its southern mirror as well.
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <vector>
+
+#include "flints.h"
+
+namespace {
+
+constexpr int CHUNK = 256;  // l values staged per pass in shared memory
+constexpr double PI_D = 3.14159265358979323846;
+
+struct SynthRing {
+    double x;          // cos(theta)
+    double lc, ls;     // log2 cos(theta/2), log2 sin(theta/2)
+    double phi0;       // azimuth of the first pixel / pi
+    long long first;   // RING index of the first pixel
+    int n;             // pixels in the ring
+    int pad;
+};
+
+thread_local char g_msg[512] = "no error";
+
+int sfail(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof g_msg, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+// log2 |d^l0_{m,m'}| (as lg) and sign of the starting value of a column
+__device__ __forceinline__ double start_log2(int m, int mp, double lc, double ls, bool &neg) {
+    const double inv_ln2 = 1.4426950408889634;
+    int l, b, pc, ps;
+    if (m >= abs(mp)) {  // first index +l = m, second b = m'
+        l = m;
+        b = mp;
+        pc = l + b;
+        ps = l - b;
+        neg = ((l - b) & 1) != 0;
+    } else if (mp < 0) {  // d_{m,m'} = d_{-m',-m}, first index -m' = +l
+        l = -mp;
+        b = -m;
+        pc = l + b;
+        ps = l - b;
+        neg = ((l - b) & 1) != 0;
+    } else {  // first index -m' = -l
+        l = mp;
+        b = -m;
+        pc = l - b;
+        ps = l + b;
+        neg = false;
+    }
+    const double lf = 0.5 * (lgamma(2.0 * l + 1.0) - lgamma((double)(l + b) + 1.0) - lgamma((double)(l - b) + 1.0));
+    return lf * inv_ln2 + pc * lc + ps * ls;
+}
+
+// One recurrence column carried as v 2^E.
+struct Col {
+    double v, prev, mult;
+    int e;
+    __device__ __forceinline__ void init(double lg, bool neg) {
+        const double fl = floor(lg);
+        e = (int)fl;
+        v = exp2(lg - fl);
+        if (neg) v = -v;
+        prev = 0.0;
+        mult = e < -1074 ? 0.0 : ldexp(1.0, e);
+    }
+    __device__ __forceinline__ void step(double a, double b, double c, double x) {
+        const double nv = fma(fma(a, x, -b), v, -c * prev);
+        prev = v;
+        v = nv;
+        if (fabs(v) > 1.157920892373162e77) {  // 2^256
+            v *= 8.636168555094445e-78;
+            prev *= 8.636168555094445e-78;
+            e += 256;
+            mult = e < -1074 ? 0.0 : ldexp(1.0, e);
+        }
+    }
+    __device__ __forceinline__ double value() const { return v * mult; }
+};
+
+// F layout: spin 0: [ring][m], m = 0..lmax;  spin s: [ring][lmax + m], m = -lmax..lmax.
+// Rings are 1..4N-1, stored at index ring-1.  Threads: x = northern ring (1..2N), y = m.
+template <int S>
+__global__ void __launch_bounds__(128) legendre_kernel(int lmax, int nside, const SynthRing *__restrict__ rings,
+                                                       const double2 *__restrict__ alm, const double2 *__restrict__ blm,
+                                                       double2 *__restrict__ F) {
+    __shared__ double sA[CHUNK], sB[CHUNK], sC[CHUNK];
+    __shared__ double2 sWp[CHUNK], sWm[CHUNK];
+    const int m = blockIdx.y;
+    const int ring = blockIdx.x * blockDim.x + threadIdx.x + 1;  // northern ring incl. the equator
+    const int nnorth = 2 * nside;
+    const bool active = ring <= nnorth;
+    const int NM = S == 0 ? lmax + 1 : 2 * lmax + 1;
+    const int l0 = m > S ? m : S;
+    const double inv4pi = 1.0 / (4.0 * PI_D);
+    SynthRing rg{};
+    if (active) rg = rings[ring - 1];
+    // columns: A = d_{m,-s}, B = d_{m,+s} (spin 0: A only)
+    Col ca{}, cb{};
+    if (active && l0 <= lmax) {
+        bool neg;
+        double lg = start_log2(m, -S, rg.lc, rg.ls, neg);
+        ca.init(lg, neg);
+        if (S > 0) {
+            lg = start_log2(m, S, rg.lc, rg.ls, neg);
+            cb.init(lg, neg);
+        }
+    }
+    // accumulators by parity of l + m (e: even, o: odd); the parity is uniform
+    // across the block (same l and m), so the branches below do not diverge
+    double2 pAe{}, pAo{}, pBe{}, pBo{}, mAe{}, mAo{}, mBe{}, mBo{};
+    for (int c0 = l0; c0 <= lmax; c0 += CHUNK) {
+        const int c1 = min(c0 + CHUNK, lmax + 1);
+        __syncthreads();
+        for (int l = c0 + threadIdx.x; l < c1; l += blockDim.x) {
+            const int k = l - c0;
+            const double ld = (double)l, lp = ld + 1.0;
+            const double md = (double)m, sd = (double)S;
+            const double den = ld * sqrt((lp * lp - md * md) * (lp * lp - sd * sd));
+            if (l == 0 || !(den > 0.0)) {  // l = m = s = 0: d^1 = x d^0
+                sA[k] = 1.0;
+                sB[k] = 0.0;
+                sC[k] = 0.0;
+            } else {
+                sA[k] = (2.0 * ld + 1.0) * ld * lp / den;
+                sB[k] = (2.0 * ld + 1.0) * md * sd / den;  // for m' = +s; m' = -s takes -sB
+                sC[k] = lp * sqrt((ld * ld - md * md) * (ld * ld - sd * sd)) / den;
+            }
+            const double nl = sqrt((2.0 * ld + 1.0) * inv4pi);
+            const double2 a = alm[(size_t)l * (lmax + 1) + m];
+            if (S == 0) {
+                sWp[k] = make_double2(a.x * nl, a.y * nl);
+            } else {
+                const double2 b = blm ? blm[(size_t)l * (lmax + 1) + m] : make_double2(0.0, 0.0);
+                // (E + iB) N and (E^* + iB^*) N
+                sWp[k] = make_double2((a.x - b.y) * nl, (a.y + b.x) * nl);
+                sWm[k] = make_double2((a.x + b.y) * nl, (b.x - a.y) * nl);
+            }
+        }
+        __syncthreads();
+        if (active) {
+            for (int l = c0; l < c1; ++l) {
+                const int k = l - c0;
+                const bool odd = ((l + m) & 1) != 0;
+                const double da = ca.value();
+                const double2 wp = sWp[k];
+                double2 &pa = odd ? pAo : pAe;
+                pa.x = fma(wp.x, da, pa.x);
+                pa.y = fma(wp.y, da, pa.y);
+                if (S > 0) {
+                    const double db = cb.value();
+                    const double2 wm = sWm[k];
+                    double2 &pb = odd ? pBo : pBe;
+                    double2 &ma = odd ? mAo : mAe;
+                    double2 &mb = odd ? mBo : mBe;
+                    pb.x = fma(wp.x, db, pb.x);
+                    pb.y = fma(wp.y, db, pb.y);
+                    ma.x = fma(wm.x, da, ma.x);
+                    ma.y = fma(wm.y, da, ma.y);
+                    mb.x = fma(wm.x, db, mb.x);
+                    mb.y = fma(wm.y, db, mb.y);
+                }
+                if (l < lmax) {
+                    ca.step(sA[k], -sB[k], sC[k], rg.x);
+                    if (S > 0) cb.step(sA[k], sB[k], sC[k], rg.x);
+                }
+            }
+        }
+    }
+    if (!active) return;
+    const int south = 4 * nside - ring;  // mirror ring (== ring at the equator)
+    double2 *Fn = F + (size_t)(ring - 1) * NM;
+    double2 *Fs = F + (size_t)(south - 1) * NM;
+    if (S == 0) {
+        Fn[m] = make_double2(pAe.x + pAo.x, pAe.y + pAo.y);
+        if (south != ring) Fs[m] = make_double2(pAe.x - pAo.x, pAe.y - pAo.y);
+        return;
+    }
+    // P_m = -(-1)^s sum wp d_{m,-s}; south: d_{m,-s}(pi - t) = (-1)^{l+m} d_{m,s}(t)
+    const double sg = (S & 1) ? 1.0 : -1.0;  // -(-1)^s
+    Fn[lmax + m] = make_double2(sg * (pAe.x + pAo.x), sg * (pAe.y + pAo.y));
+    if (south != ring) Fs[lmax + m] = make_double2(sg * (pBe.x - pBo.x), sg * (pBe.y - pBo.y));
+    if (m > 0) {  // P_-m = -sum wm d_{m,s}; south: d_{m,s}(pi - t) = (-1)^{l+m} d_{m,-s}(t)
+        Fn[lmax - m] = make_double2(-(mBe.x + mBo.x), -(mBe.y + mBo.y));
+        if (south != ring) Fs[lmax - m] = make_double2(-(mAe.x - mAo.x), -(mAe.y - mAo.y));
+    }
+}
+
+// Fold the coefficients of one ring modulo its length n, with the phase of the
+// first pixel: H_k = sum_{m = k mod n} F_m e^{i m phi0}.  Spin 0 (real field,
+// F_-m = F_m^*): k = 0..n/2 for a complex-to-real FFT; spin s: k = 0..n-1.
+template <int S>
+__global__ void fold_kernel(int lmax, const SynthRing *__restrict__ rings, const long long *__restrict__ hoff,
+                            const double2 *__restrict__ F, double2 *__restrict__ H) {
+    const int r = blockIdx.x;  // ring index - 1
+    const SynthRing rg = rings[r];
+    const int n = rg.n;
+    const int NM = S == 0 ? lmax + 1 : 2 * lmax + 1;
+    const double2 *Fr = F + (size_t)r * NM;
+    double2 *Hr = H + hoff[r];
+    const int nk = S == 0 ? n / 2 + 1 : n;
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+        double hr = 0.0, hi = 0.0;
+        if (S == 0) {
+            for (int m = k; m <= lmax; m += n) {  // m >= 0, m = k mod n
+                double sp, cp;
+                sincospi((double)m * rg.phi0, &sp, &cp);
+                const double2 f = Fr[m];
+                hr += f.x * cp - f.y * sp;
+                hi += f.x * sp + f.y * cp;
+            }
+            for (int m = (k == 0 ? n : n - k); m <= lmax; m += n) {  // m >= 1, -m = k mod n: conj
+                double sp, cp;
+                sincospi((double)m * rg.phi0, &sp, &cp);
+                const double2 f = Fr[m];
+                hr += f.x * cp - f.y * sp;
+                hi -= f.x * sp + f.y * cp;
+            }
+        } else {
+            // m = k + j n within [-lmax, lmax]
+            int m = k - ((k + lmax) / n) * n;
+            for (; m <= lmax; m += n) {
+                double sp, cp;
+                sincospi((double)m * rg.phi0, &sp, &cp);
+                const double2 f = Fr[lmax + m];
+                hr += f.x * cp - f.y * sp;
+                hi += f.x * sp + f.y * cp;
+            }
+        }
+        Hr[k] = make_double2(hr, hi);
+    }
+}
+
+}  // namespace
+
+struct flints_synth_s {
+    int device;
+    int64_t nside;
+    int lmax, spin;
+    SynthRing *d_rings;
+    long long *d_hoff;
+    double2 *d_F, *d_H;
+    void *d_work;
+    std::vector<SynthRing> rings;
+    std::vector<long long> hoff;
+    // FFT plans: [0] the equatorial belt (2N+1 rings of 4N pixels), then one per
+    // polar ring size 4i (the northern ring i and its southern mirror)
+    std::vector<cufftHandle> plans;
+    std::vector<int> plan_ring;  // first ring (1-based) of each plan
+};
+
+static void synth_release(flints_synth_s *s) {
+    for (cufftHandle h : s->plans) cufftDestroy(h);
+    cudaFree(s->d_rings);
+    cudaFree(s->d_hoff);
+    cudaFree(s->d_F);
+    cudaFree(s->d_H);
+    cudaFree(s->d_work);
+}
+
+extern "C" {
+
+const char *flints_synth_last_error(void) { return g_msg; }
+
+int flints_synth_plan(flints_synth_t *out, int64_t nside, int lmax, int spin, void *stream) {
+    if (!out) return sfail(FLINTS_EINVAL, "flints_synth_plan: out is NULL");
+    *out = nullptr;
+    if (nside < 1 || nside > 8192) return sfail(FLINTS_EINVAL, "flints_synth_plan: nside outside [1, 8192]");
+    if (spin != 0 && spin != 1 && spin != 2) return sfail(FLINTS_EINVAL, "flints_synth_plan: spin must be 0, 1 or 2");
+    if (lmax < spin || lmax > 16384) return sfail(FLINTS_EINVAL, "flints_synth_plan: lmax outside [spin, 16384]");
+    const int64_t N = nside;
+    const int nr = (int)(4 * N - 1);
+    flints_synth_s *s = new flints_synth_s();
+    cudaGetDevice(&s->device);
+    s->nside = nside;
+    s->lmax = lmax;
+    s->spin = spin;
+    s->d_rings = nullptr;
+    s->d_hoff = nullptr;
+    s->d_F = nullptr;
+    s->d_H = nullptr;
+    s->d_work = nullptr;
+    // ring geometry (host, FP64) and the FFT input layout: belt rings first
+    // (contiguous), then each polar pair [north i, south 4N-i] adjacent
+    s->rings.resize(nr);
+    s->hoff.assign(nr, 0);
+    for (int i = 1; i <= nr; ++i) {
+        SynthRing rg{};
+        double z;
+        int nq;
+        long long first;
+        double f;
+        if (i < N) {
+            nq = i;
+            z = 1.0 - (double)i * i / (3.0 * N * N);
+            first = 2LL * i * (i - 1);
+            f = 0.5;
+        } else if (i <= 3 * N) {
+            nq = (int)N;
+            z = (4.0 * N - 2.0 * i) / (3.0 * N);
+            first = 2LL * N * (N - 1) + 4LL * N * (i - N);
+            f = ((i + N) & 1) ? 0.0 : 0.5;
+        } else {
+            const int ip = (int)(4 * N - i);
+            nq = ip;
+            z = -(1.0 - (double)ip * ip / (3.0 * N * N));
+            first = 12LL * N * N - 2LL * ip * (ip + 1);
+            f = 0.5;
+        }
+        const double th = acos(z);
+        rg.x = z;
+        rg.lc = log2(cos(0.5 * th));
+        rg.ls = log2(sin(0.5 * th));
+        rg.phi0 = f / (2.0 * nq);
+        rg.first = first;
+        rg.n = 4 * nq;
+        s->rings[i - 1] = rg;
+    }
+    auto nk = [&](int n) { return (long long)(spin == 0 ? n / 2 + 1 : n); };
+    long long off = 0;
+    for (int i = (int)N; i <= 3 * N; ++i) {
+        s->hoff[i - 1] = off;
+        off += nk(s->rings[i - 1].n);
+    }
+    for (int i = 1; i < N; ++i) {
+        s->hoff[i - 1] = off;
+        off += nk(4 * i);
+        s->hoff[4 * N - i - 1] = off;
+        off += nk(4 * i);
+    }
+    const size_t NM = spin == 0 ? (size_t)lmax + 1 : 2 * (size_t)lmax + 1;
+    cudaError_t e;
+    if ((e = cudaMalloc(&s->d_rings, sizeof(SynthRing) * nr)) != cudaSuccess ||
+        (e = cudaMalloc(&s->d_hoff, sizeof(long long) * nr)) != cudaSuccess ||
+        (e = cudaMalloc(&s->d_F, sizeof(double2) * NM * nr)) != cudaSuccess ||
+        (e = cudaMalloc(&s->d_H, sizeof(double2) * (size_t)off)) != cudaSuccess) {
+        synth_release(s);
+        delete s;
+        return sfail(e == cudaErrorMemoryAllocation ? FLINTS_ENOMEM : FLINTS_ECUDA, "flints_synth_plan: %s",
+                     cudaGetErrorString(e));
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((e = cudaMemcpyAsync(s->d_rings, s->rings.data(), sizeof(SynthRing) * nr, cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(s->d_hoff, s->hoff.data(), sizeof(long long) * nr, cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+        synth_release(s);
+        delete s;
+        return sfail(FLINTS_ECUDA, "flints_synth_plan: %s", cudaGetErrorString(e));
+    }
+    // FFT plans with a shared work area
+    const cufftType type = spin == 0 ? CUFFT_Z2D : CUFFT_Z2Z;
+    size_t work_max = 0;
+    auto make = [&](int n, int batch, long long odist, int first_ring) -> int {
+        cufftHandle h;
+        if (cufftCreate(&h) != CUFFT_SUCCESS) return FLINTS_ECUDA;
+        cufftSetAutoAllocation(h, 0);
+        int nn[1] = {n}, inembed[1] = {(int)nk(n)}, onembed[1] = {n};
+        size_t ws = 0;
+        if (cufftMakePlanMany(h, 1, nn, inembed, 1, (int)nk(n), onembed, 1, (int)odist, type, batch, &ws) !=
+            CUFFT_SUCCESS) {
+            cufftDestroy(h);
+            return FLINTS_ECUDA;
+        }
+        if (ws > work_max) work_max = ws;
+        s->plans.push_back(h);
+        s->plan_ring.push_back(first_ring);
+        return FLINTS_OK;
+    };
+    int rc = make((int)(4 * N), (int)(2 * N + 1), 4 * N, (int)N);
+    for (int i = 1; rc == FLINTS_OK && i < N; ++i)
+        rc = make(4 * i, 2, s->rings[4 * N - i - 1].first - s->rings[i - 1].first, i);
+    if (rc != FLINTS_OK) {
+        synth_release(s);
+        delete s;
+        return sfail(FLINTS_ECUDA, "flints_synth_plan: cuFFT plan creation failed");
+    }
+    if (work_max && (e = cudaMalloc(&s->d_work, work_max)) != cudaSuccess) {
+        synth_release(s);
+        delete s;
+        return sfail(FLINTS_ENOMEM, "flints_synth_plan: FFT work area: %s", cudaGetErrorString(e));
+    }
+    for (cufftHandle h : s->plans) cufftSetWorkArea(h, s->d_work);
+    *out = s;
+    return FLINTS_OK;
+}
+
+int flints_synthesize(flints_synth_t s, const double *alm, const double *blm, double *map, void *stream) {
+    if (!s) return sfail(FLINTS_EINVAL, "flints_synthesize: plan is NULL");
+    if (!alm || !map) return sfail(FLINTS_EINVAL, "flints_synthesize: alm and map must not be NULL");
+    if (((uintptr_t)alm | (uintptr_t)map | (uintptr_t)blm) & 15u)
+        return sfail(FLINTS_EINVAL, "flints_synthesize: alm, blm and map must be 16-byte aligned");
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != s->device) return sfail(FLINTS_EINVAL, "flints_synthesize: plan made on another device");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int N = (int)s->nside, lmax = s->lmax;
+    const dim3 grid((2 * N + 127) / 128, lmax + 1);
+    const double2 *a = reinterpret_cast<const double2 *>(alm);
+    const double2 *b = s->spin == 0 ? nullptr : reinterpret_cast<const double2 *>(blm);
+    const int nr = 4 * N - 1;
+    switch (s->spin) {
+        case 0:
+            legendre_kernel<0><<<grid, 128, 0, st>>>(lmax, N, s->d_rings, a, b, s->d_F);
+            fold_kernel<0><<<nr, 256, 0, st>>>(lmax, s->d_rings, s->d_hoff, s->d_F, s->d_H);
+            break;
+        case 1:
+            legendre_kernel<1><<<grid, 128, 0, st>>>(lmax, N, s->d_rings, a, b, s->d_F);
+            fold_kernel<1><<<nr, 256, 0, st>>>(lmax, s->d_rings, s->d_hoff, s->d_F, s->d_H);
+            break;
+        default:
+            legendre_kernel<2><<<grid, 128, 0, st>>>(lmax, N, s->d_rings, a, b, s->d_F);
+            fold_kernel<2><<<nr, 256, 0, st>>>(lmax, s->d_rings, s->d_hoff, s->d_F, s->d_H);
+            break;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return sfail(FLINTS_ECUDA, "flints_synthesize: kernel launch: %s", cudaGetErrorString(e));
+    for (size_t p = 0; p < s->plans.size(); ++p) {
+        const int r = s->plan_ring[p];
+        cufftHandle h = s->plans[p];
+        if (cufftSetStream(h, st) != CUFFT_SUCCESS) return sfail(FLINTS_ECUDA, "flints_synthesize: cufftSetStream");
+        cufftDoubleComplex *in = reinterpret_cast<cufftDoubleComplex *>(s->d_H + s->hoff[r - 1]);
+        cufftResult fr;
+        if (s->spin == 0) {
+            fr = cufftExecZ2D(h, in, reinterpret_cast<cufftDoubleReal *>(map + s->rings[r - 1].first));
+        } else {
+            fr = cufftExecZ2Z(h, in, reinterpret_cast<cufftDoubleComplex *>(map) + s->rings[r - 1].first,
+                              CUFFT_INVERSE);
+        }
+        if (fr != CUFFT_SUCCESS) return sfail(FLINTS_ECUDA, "flints_synthesize: cuFFT execution failed (%d)", (int)fr);
+    }
+    return FLINTS_OK;
+}
+
+void flints_synth_free(flints_synth_t s) {
+    if (!s) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != s->device) cudaSetDevice(s->device);
+    synth_release(s);
+    if (cur != s->device) cudaSetDevice(cur);
+    delete s;
+}
+
+}  // extern "C"
