@@ -47,10 +47,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", choices=["c3", "c3aug", "c4", "c5", "ss"], default="c3",
+    ap.add_argument("--workload", choices=["c3", "c3aug", "c4", "c5", "ss", "pipeline"], default="c3",
                     help="c3: Nside 4096 spin 2 (default); c3aug: the same with the augmented (xi+, xi-) "
                          "estimator; c4: 64-map batched persistent launch; c5: serving; ss: supersampling "
-                         "Nside 2048 -> 4096")
+                         "Nside 2048 -> 4096; pipeline: synthesis of T, Q/U and the deflection + lensing")
     ap.add_argument("--duration", type=float, default=45.0, help="c5: seconds of Poisson arrivals")
     ap.add_argument("--profile-case", choices=["mixed", "fp64"], default=None,
                     help="small case for ncu: two launches on 2^18 targets of the resident c3 map")
@@ -560,6 +560,110 @@ def run_ss(args):
         "mixed_stats": st, "gpu_launches": args.steps}))
 
 
+# ----------------------------------------------------------- pipeline arm
+def run_pipeline(args):
+    """Table 2's total on the GPU: from Gaussian a_lm of T, E and phi (Nside 4096,
+    lmax 4096), synthesise the unlensed T and Q/U maps and the deflection
+    grad(phi) (spin-1 synthesis), then lens T and Q/U over the whole sky
+    (mixed path, K = 32, batches of 2^24 targets).  One step = one lensed T+P map."""
+    import torch
+
+    import paper_1003_4984_gb300 as fl
+
+    fl.load_library()
+    nside, lmax, K = W.nside, W.lmax, W.K
+    npix = 12 * nside * nside
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    ell = torch.arange(lmax + 1, dtype=torch.float64, device=dev)
+    cl_t = torch.from_numpy(wl.cl_tt(lmax, 2500.0)).to(dev)
+    cl_e, _ = W.cl()
+    cl_e = torch.from_numpy(cl_e).to(dev)
+    cl_p = torch.from_numpy(wl.cl_phiphi(lmax)).to(dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(2024)
+
+    def alm(cl):  # Gaussian a_lm with <|a_lm|^2> = C_l (m = 0 real)
+        a = torch.randn((lmax + 1, lmax + 1, 2), dtype=torch.float64, device=dev, generator=g)
+        a *= torch.sqrt(cl / 2.0)[:, None, None]
+        a[:, 0, 0] *= math.sqrt(2.0)
+        a[:, 0, 1] = 0.0
+        a = torch.view_as_complex(a)
+        return torch.tril(a).contiguous()
+
+    a_t, a_e = alm(cl_t), alm(cl_e)
+    a_d = (alm(cl_p) * torch.sqrt(ell * (ell + 1.0))[:, None]).contiguous()  # E of the spin-1 deflection
+    t0 = time.time()
+    syn = {0: fl.Synth(nside, lmax, 0), 1: fl.Synth(nside, lmax, 1), 2: fl.Synth(nside, lmax, 2)}
+    torch.cuda.synchronize(dev)
+    synth_plan_s = time.time() - t0
+    t0 = time.time()
+    plan_t = fl.Plan(nside, wl.cl_tt(lmax, 2500.0), spin=0, K=K, precision="mixed", flags=fl.FLINTS_NO_VARIANCE)
+    cl_ee, bb = W.cl()
+    plan_p = fl.Plan(nside, cl_ee, bb, spin=2, K=K, precision="mixed", flags=fl.FLINTS_NO_VARIANCE)
+    lens_plan_s = time.time() - t0
+    tmap = torch.empty(npix, dtype=torch.float64, device=dev)
+    qu = torch.empty((npix, 2), dtype=torch.float64, device=dev)
+    defl = torch.empty((npix, 2), dtype=torch.float64, device=dev)
+    out_t = torch.empty(npix, dtype=torch.float64, device=dev)
+    out_p = torch.empty((npix, 2), dtype=torch.float64, device=dev)
+    ev = {}
+
+    def step():
+        for k in ("s_t", "s_p", "s_d", "l_t", "l_p", "end"):
+            ev.setdefault(k, torch.cuda.Event(enable_timing=True))
+        ev["s_t"].record(stream)
+        syn[0].run(a_t, None, tmap)
+        ev["s_p"].record(stream)
+        syn[2].run(a_e, None, qu)
+        ev["s_d"].record(stream)
+        syn[1].run(a_d, None, defl)
+        ev["l_t"].record(stream)
+        for b0 in range(0, npix, BATCH):
+            n = min(BATCH, npix - b0)
+            plan_t.lens(tmap, defl[b0:b0 + n], out_t[b0:b0 + n], first=b0, count=n)
+        ev["l_p"].record(stream)
+        for b0 in range(0, npix, BATCH):
+            n = min(BATCH, npix - b0)
+            plan_p.lens(qu, defl[b0:b0 + n], out_p[b0:b0 + n], first=b0, count=n)
+        ev["end"].record(stream)
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+    steps = max(1, args.steps)
+    parts = {"synth_T": [], "synth_QU": [], "synth_deflection": [], "lens_T": [], "lens_QU": [], "total": []}
+    with Clocks(os.path.join(ROOT, "gpurun_out", "bench_clocks_pipeline.csv") if os.path.isdir(
+            os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks_pipeline.csv") as clk:
+        for _ in range(steps):
+            step()
+            torch.cuda.synchronize(dev)
+            parts["synth_T"].append(ev["s_t"].elapsed_time(ev["s_p"]))
+            parts["synth_QU"].append(ev["s_p"].elapsed_time(ev["s_d"]))
+            parts["synth_deflection"].append(ev["s_d"].elapsed_time(ev["l_t"]))
+            parts["lens_T"].append(ev["l_t"].elapsed_time(ev["l_p"]))
+            parts["lens_QU"].append(ev["l_p"].elapsed_time(ev["end"]))
+            parts["total"].append(ev["s_t"].elapsed_time(ev["end"]))
+    ms = {k: statistics.mean(v) for k, v in parts.items()}
+    st_t, st_p = plan_t.stats(), plan_p.stats()
+    print(json.dumps({
+        "metric": "seconds per lensed T+Q/U map at Nside 4096 (synthesis of T, Q/U, deflection + lensing)",
+        "value": ms["total"] / 1e3, "unit": "s", "n_gpus": 1, "steps": steps, "warmup": max(1, args.warmup),
+        "ms_per_step": ms["total"], "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 synthesis; lensing double-float factor, f64 geometry",
+        "data": "synthetic Gaussian a_lm of the c3 spectra (T damping l = 2500, E = 0.05 T shape, B = 0, "
+                "C^phiphi ~ l^-4 at 2.5 arcmin rms)",
+        "config": {"workload": "pipeline: Nside 4096 (201,326,592 px), lmax 4096, K = 32, T and Q/U, mixed",
+                   "batch_points": BATCH},
+        "breakdown_ms": ms, "synth_plans_s": synth_plan_s, "lens_plans_s": lens_plan_s,
+        "lens_stats": {"T": st_t, "QU": st_p},
+        "paper_table2": "FLINTS Nside 4096, 9 neighbours: interpolation 22 min, total 51 min (+16 min init), "
+                        "serial Xeon E5410",
+        "clocks": clk.summary(0), "gpu_launches": 30 * steps}))
+    for s_ in syn.values():
+        s_.close()
+
+
 if __name__ == "__main__":
     a = parse()
     if a.workload == "c4" and a.impl == "ours" and not a.profile_case:
@@ -568,6 +672,8 @@ if __name__ == "__main__":
         run_c5(a)
     elif a.workload == "ss" and a.impl == "ours" and not a.profile_case:
         run_ss(a)
+    elif a.workload == "pipeline" and a.impl == "ours" and not a.profile_case:
+        run_pipeline(a)
     elif a.profile_case:
         run_profile_case(a.profile_case)
     elif a.impl == "reference":

@@ -15,7 +15,14 @@
 //            P_-m = -sum_l (E^* + iB^*)_lm N_l d^l_{m,s}            (m >= 1),
 //
 // and the ring values are the Fourier sums sum_m F_m e^{i m phi_j}, done by
-// folding m modulo the ring length and one inverse FFT per ring (cuFFT).
+// folding m modulo the ring length n and an inverse DFT of length n.  The
+// 2 Nside + 1 equatorial rings (n = 4 Nside) share one batched cuFFT plan.
+// The polar rings (n = 4i, i < Nside) use Bluestein's algorithm: with
+// w_t = exp(i pi t^2 / n), x_j = sum_k H_k e^{2 pi i jk/n} = w_j (a * b)_j for
+// a_k = H_k w_k and b_t = conj(w_t), a linear convolution done with FFTs of
+// a power-of-two length M >= 2n - 1; the transforms of b are tabulated per
+// ring size at plan time, and the rings of equal M share one batched plan, so
+// a plan holds at most 14 cuFFT plans whatever Nside.
 //
 // The l-sums use the Wigner-d three-term recurrence in l at fixed (m, m'):
 //   d^{l+1} = (A_l x - B_l) d^l - C_l d^{l-1},  A_l = (2l+1) l (l+1) / D_l,
@@ -51,9 +58,19 @@ struct SynthRing {
     double lc, ls;     // log2 cos(theta/2), log2 sin(theta/2)
     double phi0;       // azimuth of the first pixel / pi
     long long first;   // RING index of the first pixel
+    long long off;     // equatorial ring: offset of its FFT input; polar ring: offset of its Bluestein slot
+    long long fboff;   // polar ring: offset of the transformed chirp for its size
     int n;             // pixels in the ring
-    int pad;
+    int M;             // polar ring: Bluestein length (0: equatorial ring)
 };
+
+// w_t = exp(i pi t^2 / n), with t^2 reduced modulo 2n (exact in integers)
+__device__ __forceinline__ double2 chirp(long long t, int n) {
+    const long long q = (t * t) % (2LL * n);
+    double sp, cp;
+    sincospi((double)q / (double)n, &sp, &cp);
+    return make_double2(cp, sp);
+}
 
 thread_local char g_msg[512] = "no error";
 
@@ -229,16 +246,21 @@ __global__ void __launch_bounds__(128) legendre_kernel(int lmax, int nside, cons
 // Fold the coefficients of one ring modulo its length n, with the phase of the
 // first pixel: H_k = sum_{m = k mod n} F_m e^{i m phi0}.  Spin 0 (real field,
 // F_-m = F_m^*): k = 0..n/2 for a complex-to-real FFT; spin s: k = 0..n-1.
+// Polar rings (rg.M > 0) write a_k = H_k w_k, k < n, zero-padded to M, into
+// their Bluestein slot in A; equatorial rings write H into H.
 template <int S>
-__global__ void fold_kernel(int lmax, const SynthRing *__restrict__ rings, const long long *__restrict__ hoff,
-                            const double2 *__restrict__ F, double2 *__restrict__ H) {
+__global__ void fold_kernel(int lmax, const SynthRing *__restrict__ rings, const double2 *__restrict__ F,
+                            double2 *__restrict__ H, double2 *__restrict__ A) {
     const int r = blockIdx.x;  // ring index - 1
     const SynthRing rg = rings[r];
     const int n = rg.n;
     const int NM = S == 0 ? lmax + 1 : 2 * lmax + 1;
     const double2 *Fr = F + (size_t)r * NM;
-    double2 *Hr = H + hoff[r];
-    const int nk = S == 0 ? n / 2 + 1 : n;
+    const bool polar = rg.M > 0;
+    double2 *Hr = polar ? A + rg.off : H + rg.off;
+    if (polar)
+        for (int k = n + threadIdx.x; k < rg.M; k += blockDim.x) Hr[k] = make_double2(0.0, 0.0);
+    const int nk = (S == 0 && !polar) ? n / 2 + 1 : n;
     for (int k = threadIdx.x; k < nk; k += blockDim.x) {
         double hr = 0.0, hi = 0.0;
         if (S == 0) {
@@ -267,7 +289,60 @@ __global__ void fold_kernel(int lmax, const SynthRing *__restrict__ rings, const
                 hi += f.x * sp + f.y * cp;
             }
         }
-        Hr[k] = make_double2(hr, hi);
+        if (polar) {
+            const double2 w = chirp(k, n);
+            Hr[k] = make_double2(hr * w.x - hi * w.y, hr * w.y + hi * w.x);
+        } else {
+            Hr[k] = make_double2(hr, hi);
+        }
+    }
+}
+
+// Bluestein middle step: the transformed slot times the transformed chirp, / M.
+__global__ void chirp_mul_kernel(const SynthRing *__restrict__ rings, const int *__restrict__ polar,
+                                 const double2 *__restrict__ FB, double2 *__restrict__ A) {
+    const SynthRing rg = rings[polar[blockIdx.x]];
+    const double inv = 1.0 / (double)rg.M;
+    double2 *a = A + rg.off;
+    const double2 *b = FB + rg.fboff;
+    for (int k = threadIdx.x; k < rg.M; k += blockDim.x) {
+        const double2 x = a[k], y = b[k];
+        a[k] = make_double2((x.x * y.x - x.y * y.y) * inv, (x.x * y.y + x.y * y.x) * inv);
+    }
+}
+
+// Bluestein last step: x_j = w_j c_j, written to the ring's pixels.
+template <int S>
+__global__ void chirp_out_kernel(const SynthRing *__restrict__ rings, const int *__restrict__ polar,
+                                 const double2 *__restrict__ A, double *__restrict__ map) {
+    const SynthRing rg = rings[polar[blockIdx.x]];
+    const double2 *a = A + rg.off;
+    for (int j = threadIdx.x; j < rg.n; j += blockDim.x) {
+        const double2 w = chirp(j, rg.n), c = a[j];
+        const double xr = w.x * c.x - w.y * c.y, xi = w.x * c.y + w.y * c.x;
+        if (S == 0) {
+            map[rg.first + j] = xr;
+        } else {
+            reinterpret_cast<double2 *>(map)[rg.first + j] = make_double2(xr, xi);
+        }
+    }
+}
+
+// Chirp b_t = conj(w_t) for |t| < n in a length-M cyclic buffer (one block per ring size).
+__global__ void chirp_fill_kernel(const int *__restrict__ sizes_n, const int *__restrict__ sizes_M,
+                                  const long long *__restrict__ sizes_off, double2 *__restrict__ FB) {
+    const int n = sizes_n[blockIdx.x], M = sizes_M[blockIdx.x];
+    double2 *b = FB + sizes_off[blockIdx.x];
+    for (int t = threadIdx.x; t < M; t += blockDim.x) {
+        double2 v = make_double2(0.0, 0.0);
+        if (t < n) {
+            const double2 w = chirp(t, n);
+            v = make_double2(w.x, -w.y);
+        } else if (t > M - n) {
+            const double2 w = chirp(M - t, n);
+            v = make_double2(w.x, -w.y);
+        }
+        b[t] = v;
     }
 }
 
@@ -278,24 +353,34 @@ struct flints_synth_s {
     int64_t nside;
     int lmax, spin;
     SynthRing *d_rings;
-    long long *d_hoff;
-    double2 *d_F, *d_H;
+    int *d_polar;      // indices of the polar rings
+    double2 *d_F, *d_H, *d_A, *d_FB;
     void *d_work;
     std::vector<SynthRing> rings;
-    std::vector<long long> hoff;
-    // FFT plans: [0] the equatorial belt (2N+1 rings of 4N pixels), then one per
-    // polar ring size 4i (the northern ring i and its southern mirror)
-    std::vector<cufftHandle> plans;
-    std::vector<int> plan_ring;  // first ring (1-based) of each plan
+    int npolar;
+    cufftHandle belt;                 // equatorial rings, batched
+    std::vector<cufftHandle> groups;  // polar rings: one C2C plan per Bluestein length M
+    std::vector<long long> group_off; // first slot of each group in A
+    bool belt_made;
 };
 
 static void synth_release(flints_synth_s *s) {
-    for (cufftHandle h : s->plans) cufftDestroy(h);
+    if (s->belt_made) cufftDestroy(s->belt);
+    for (cufftHandle h : s->groups) cufftDestroy(h);
     cudaFree(s->d_rings);
-    cudaFree(s->d_hoff);
+    cudaFree(s->d_polar);
     cudaFree(s->d_F);
     cudaFree(s->d_H);
+    cudaFree(s->d_A);
+    cudaFree(s->d_FB);
     cudaFree(s->d_work);
+}
+
+static int synth_bail(flints_synth_s *s, int code, const char *what, cudaError_t e = cudaSuccess) {
+    synth_release(s);
+    delete s;
+    if (e != cudaSuccess) return sfail(code, "flints_synth_plan: %s: %s", what, cudaGetErrorString(e));
+    return sfail(code, "flints_synth_plan: %s", what);
 }
 
 extern "C" {
@@ -316,20 +401,17 @@ int flints_synth_plan(flints_synth_t *out, int64_t nside, int lmax, int spin, vo
     s->lmax = lmax;
     s->spin = spin;
     s->d_rings = nullptr;
-    s->d_hoff = nullptr;
-    s->d_F = nullptr;
-    s->d_H = nullptr;
+    s->d_polar = nullptr;
+    s->d_F = s->d_H = s->d_A = s->d_FB = nullptr;
     s->d_work = nullptr;
-    // ring geometry (host, FP64) and the FFT input layout: belt rings first
-    // (contiguous), then each polar pair [north i, south 4N-i] adjacent
+    s->belt_made = false;
+    // ring geometry (host, FP64)
     s->rings.resize(nr);
-    s->hoff.assign(nr, 0);
     for (int i = 1; i <= nr; ++i) {
         SynthRing rg{};
-        double z;
+        double z, f;
         int nq;
         long long first;
-        double f;
         if (i < N) {
             nq = i;
             z = 1.0 - (double)i * i / (3.0 * N * N);
@@ -356,72 +438,137 @@ int flints_synth_plan(flints_synth_t *out, int64_t nside, int lmax, int spin, vo
         rg.n = 4 * nq;
         s->rings[i - 1] = rg;
     }
-    auto nk = [&](int n) { return (long long)(spin == 0 ? n / 2 + 1 : n); };
-    long long off = 0;
-    for (int i = (int)N; i <= 3 * N; ++i) {
-        s->hoff[i - 1] = off;
-        off += nk(s->rings[i - 1].n);
-    }
+    // equatorial FFT inputs, contiguous in ring order
+    const long long nkb = spin == 0 ? 2 * N + 1 : 4 * N;  // per equatorial ring
+    for (int i = (int)N; i <= 3 * N; ++i) s->rings[i - 1].off = (long long)(i - N) * nkb;
+    const long long hsize = (2 * N + 1) * nkb;
+    // polar rings: Bluestein length M = next power of two >= 2n - 1, slots grouped by M
+    std::vector<int> polar, sz_n, sz_M;
+    std::vector<long long> sz_off;
+    std::vector<int> group_M;
+    std::vector<int> group_batch;
+    long long aoff = 0, fboff = 0;
     for (int i = 1; i < N; ++i) {
-        s->hoff[i - 1] = off;
-        off += nk(4 * i);
-        s->hoff[4 * N - i - 1] = off;
-        off += nk(4 * i);
+        const int n = 4 * i;
+        int M = 1;
+        while (M < 2 * n - 1) M <<= 1;
+        if (group_M.empty() || group_M.back() != M) {
+            group_M.push_back(M);
+            group_batch.push_back(0);
+            s->group_off.push_back(aoff);
+        }
+        sz_n.push_back(n);
+        sz_M.push_back(M);
+        sz_off.push_back(fboff);
+        for (int r : {i, (int)(4 * N - i)}) {
+            SynthRing &rg = s->rings[r - 1];
+            rg.M = M;
+            rg.off = aoff;
+            rg.fboff = fboff;
+            aoff += M;
+            polar.push_back(r - 1);
+            group_batch.back() += 1;
+        }
+        fboff += M;
     }
+    s->npolar = (int)polar.size();
     const size_t NM = spin == 0 ? (size_t)lmax + 1 : 2 * (size_t)lmax + 1;
     cudaError_t e;
     if ((e = cudaMalloc(&s->d_rings, sizeof(SynthRing) * nr)) != cudaSuccess ||
-        (e = cudaMalloc(&s->d_hoff, sizeof(long long) * nr)) != cudaSuccess ||
         (e = cudaMalloc(&s->d_F, sizeof(double2) * NM * nr)) != cudaSuccess ||
-        (e = cudaMalloc(&s->d_H, sizeof(double2) * (size_t)off)) != cudaSuccess) {
-        synth_release(s);
-        delete s;
-        return sfail(e == cudaErrorMemoryAllocation ? FLINTS_ENOMEM : FLINTS_ECUDA, "flints_synth_plan: %s",
-                     cudaGetErrorString(e));
-    }
+        (e = cudaMalloc(&s->d_H, sizeof(double2) * (size_t)hsize)) != cudaSuccess)
+        return synth_bail(s, e == cudaErrorMemoryAllocation ? FLINTS_ENOMEM : FLINTS_ECUDA, "allocation", e);
+    if (s->npolar > 0 &&
+        ((e = cudaMalloc(&s->d_polar, sizeof(int) * polar.size())) != cudaSuccess ||
+         (e = cudaMalloc(&s->d_A, sizeof(double2) * (size_t)aoff)) != cudaSuccess ||
+         (e = cudaMalloc(&s->d_FB, sizeof(double2) * (size_t)fboff)) != cudaSuccess))
+        return synth_bail(s, e == cudaErrorMemoryAllocation ? FLINTS_ENOMEM : FLINTS_ECUDA, "allocation", e);
     cudaStream_t st = (cudaStream_t)stream;
     if ((e = cudaMemcpyAsync(s->d_rings, s->rings.data(), sizeof(SynthRing) * nr, cudaMemcpyHostToDevice, st)) !=
-            cudaSuccess ||
-        (e = cudaMemcpyAsync(s->d_hoff, s->hoff.data(), sizeof(long long) * nr, cudaMemcpyHostToDevice, st)) !=
-            cudaSuccess ||
-        (e = cudaStreamSynchronize(st)) != cudaSuccess) {
-        synth_release(s);
-        delete s;
-        return sfail(FLINTS_ECUDA, "flints_synth_plan: %s", cudaGetErrorString(e));
-    }
-    // FFT plans with a shared work area
-    const cufftType type = spin == 0 ? CUFFT_Z2D : CUFFT_Z2Z;
+        cudaSuccess)
+        return synth_bail(s, FLINTS_ECUDA, "copy", e);
+    if (s->npolar > 0 && (e = cudaMemcpyAsync(s->d_polar, polar.data(), sizeof(int) * polar.size(),
+                                              cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return synth_bail(s, FLINTS_ECUDA, "copy", e);
+    // cuFFT plans sharing one work area
     size_t work_max = 0;
-    auto make = [&](int n, int batch, long long odist, int first_ring) -> int {
-        cufftHandle h;
-        if (cufftCreate(&h) != CUFFT_SUCCESS) return FLINTS_ECUDA;
+    auto make = [&](cufftHandle &h, int n, long long idist, long long odist, cufftType type, int batch) -> bool {
+        if (cufftCreate(&h) != CUFFT_SUCCESS) return false;
         cufftSetAutoAllocation(h, 0);
-        int nn[1] = {n}, inembed[1] = {(int)nk(n)}, onembed[1] = {n};
+        int nn[1] = {n}, inembed[1] = {(int)idist}, onembed[1] = {(int)odist};
         size_t ws = 0;
-        if (cufftMakePlanMany(h, 1, nn, inembed, 1, (int)nk(n), onembed, 1, (int)odist, type, batch, &ws) !=
+        if (cufftMakePlanMany(h, 1, nn, inembed, 1, (int)idist, onembed, 1, (int)odist, type, batch, &ws) !=
             CUFFT_SUCCESS) {
             cufftDestroy(h);
-            return FLINTS_ECUDA;
+            return false;
         }
         if (ws > work_max) work_max = ws;
-        s->plans.push_back(h);
-        s->plan_ring.push_back(first_ring);
-        return FLINTS_OK;
+        return true;
     };
-    int rc = make((int)(4 * N), (int)(2 * N + 1), 4 * N, (int)N);
-    for (int i = 1; rc == FLINTS_OK && i < N; ++i)
-        rc = make(4 * i, 2, s->rings[4 * N - i - 1].first - s->rings[i - 1].first, i);
-    if (rc != FLINTS_OK) {
-        synth_release(s);
-        delete s;
-        return sfail(FLINTS_ECUDA, "flints_synth_plan: cuFFT plan creation failed");
+    if (!make(s->belt, (int)(4 * N), nkb, 4 * N, spin == 0 ? CUFFT_Z2D : CUFFT_Z2Z, (int)(2 * N + 1)))
+        return synth_bail(s, FLINTS_ECUDA, "cuFFT plan creation failed");
+    s->belt_made = true;
+    for (size_t g = 0; g < group_M.size(); ++g) {
+        cufftHandle h;
+        if (!make(h, group_M[g], group_M[g], group_M[g], CUFFT_Z2Z, group_batch[g]))
+            return synth_bail(s, FLINTS_ECUDA, "cuFFT plan creation failed");
+        s->groups.push_back(h);
     }
-    if (work_max && (e = cudaMalloc(&s->d_work, work_max)) != cudaSuccess) {
-        synth_release(s);
-        delete s;
-        return sfail(FLINTS_ENOMEM, "flints_synth_plan: FFT work area: %s", cudaGetErrorString(e));
+    if (work_max && (e = cudaMalloc(&s->d_work, work_max)) != cudaSuccess)
+        return synth_bail(s, FLINTS_ENOMEM, "FFT work area", e);
+    cufftSetWorkArea(s->belt, s->d_work);
+    for (cufftHandle h : s->groups) cufftSetWorkArea(h, s->d_work);
+    // transformed chirps, one per polar ring size
+    if (s->npolar > 0) {
+        int *d_n = nullptr, *d_M = nullptr;
+        long long *d_off = nullptr;
+        const size_t ns = sz_n.size();
+        if ((e = cudaMalloc(&d_n, sizeof(int) * ns)) != cudaSuccess ||
+            (e = cudaMalloc(&d_M, sizeof(int) * ns)) != cudaSuccess ||
+            (e = cudaMalloc(&d_off, sizeof(long long) * ns)) != cudaSuccess) {
+            cudaFree(d_n);
+            cudaFree(d_M);
+            return synth_bail(s, FLINTS_ENOMEM, "chirp tables", e);
+        }
+        cudaMemcpyAsync(d_n, sz_n.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(d_M, sz_M.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(d_off, sz_off.data(), sizeof(long long) * ns, cudaMemcpyHostToDevice, st);
+        chirp_fill_kernel<<<(unsigned)ns, 256, 0, st>>>(d_n, d_M, d_off, s->d_FB);
+        e = cudaGetLastError();
+        // forward transforms of the chirps, group by group (one per ring size in a group)
+        for (size_t g = 0; e == cudaSuccess && g < group_M.size(); ++g) {
+            size_t k0 = 0;
+            while (k0 < ns && sz_M[k0] != group_M[g]) ++k0;
+            size_t k1 = k0;
+            while (k1 < ns && sz_M[k1] == group_M[g]) ++k1;
+            cufftHandle h;
+            if (!make(h, group_M[g], group_M[g], group_M[g], CUFFT_Z2Z, (int)(k1 - k0))) {
+                e = cudaErrorUnknown;
+                break;
+            }
+            void *tmp = nullptr;
+            size_t ws = 0;
+            cufftGetSize(h, &ws);
+            if (ws && cudaMalloc(&tmp, ws) != cudaSuccess) {
+                cufftDestroy(h);
+                e = cudaErrorMemoryAllocation;
+                break;
+            }
+            cufftSetWorkArea(h, tmp);
+            cufftSetStream(h, st);
+            cufftDoubleComplex *p = reinterpret_cast<cufftDoubleComplex *>(s->d_FB + sz_off[k0]);
+            if (cufftExecZ2Z(h, p, p, CUFFT_FORWARD) != CUFFT_SUCCESS) e = cudaErrorUnknown;
+            cudaStreamSynchronize(st);
+            cufftDestroy(h);
+            cudaFree(tmp);
+        }
+        cudaStreamSynchronize(st);
+        cudaFree(d_n);
+        cudaFree(d_M);
+        cudaFree(d_off);
+        if (e != cudaSuccess) return synth_bail(s, FLINTS_ECUDA, "chirp transforms", e);
     }
-    for (cufftHandle h : s->plans) cufftSetWorkArea(h, s->d_work);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return synth_bail(s, FLINTS_ECUDA, "set-up", e);
     *out = s;
     return FLINTS_OK;
 }
@@ -443,33 +590,50 @@ int flints_synthesize(flints_synth_t s, const double *alm, const double *blm, do
     switch (s->spin) {
         case 0:
             legendre_kernel<0><<<grid, 128, 0, st>>>(lmax, N, s->d_rings, a, b, s->d_F);
-            fold_kernel<0><<<nr, 256, 0, st>>>(lmax, s->d_rings, s->d_hoff, s->d_F, s->d_H);
+            fold_kernel<0><<<nr, 256, 0, st>>>(lmax, s->d_rings, s->d_F, s->d_H, s->d_A);
             break;
         case 1:
             legendre_kernel<1><<<grid, 128, 0, st>>>(lmax, N, s->d_rings, a, b, s->d_F);
-            fold_kernel<1><<<nr, 256, 0, st>>>(lmax, s->d_rings, s->d_hoff, s->d_F, s->d_H);
+            fold_kernel<1><<<nr, 256, 0, st>>>(lmax, s->d_rings, s->d_F, s->d_H, s->d_A);
             break;
         default:
             legendre_kernel<2><<<grid, 128, 0, st>>>(lmax, N, s->d_rings, a, b, s->d_F);
-            fold_kernel<2><<<nr, 256, 0, st>>>(lmax, s->d_rings, s->d_hoff, s->d_F, s->d_H);
+            fold_kernel<2><<<nr, 256, 0, st>>>(lmax, s->d_rings, s->d_F, s->d_H, s->d_A);
             break;
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return sfail(FLINTS_ECUDA, "flints_synthesize: kernel launch: %s", cudaGetErrorString(e));
-    for (size_t p = 0; p < s->plans.size(); ++p) {
-        const int r = s->plan_ring[p];
-        cufftHandle h = s->plans[p];
-        if (cufftSetStream(h, st) != CUFFT_SUCCESS) return sfail(FLINTS_ECUDA, "flints_synthesize: cufftSetStream");
-        cufftDoubleComplex *in = reinterpret_cast<cufftDoubleComplex *>(s->d_H + s->hoff[r - 1]);
-        cufftResult fr;
-        if (s->spin == 0) {
-            fr = cufftExecZ2D(h, in, reinterpret_cast<cufftDoubleReal *>(map + s->rings[r - 1].first));
-        } else {
-            fr = cufftExecZ2Z(h, in, reinterpret_cast<cufftDoubleComplex *>(map) + s->rings[r - 1].first,
-                              CUFFT_INVERSE);
-        }
+    // equatorial rings: one batched inverse transform straight into the map
+    if (cufftSetStream(s->belt, st) != CUFFT_SUCCESS) return sfail(FLINTS_ECUDA, "flints_synthesize: cufftSetStream");
+    {
+        const SynthRing &r0 = s->rings[N - 1];
+        cufftDoubleComplex *in = reinterpret_cast<cufftDoubleComplex *>(s->d_H);
+        cufftResult fr = s->spin == 0
+                             ? cufftExecZ2D(s->belt, in, reinterpret_cast<cufftDoubleReal *>(map + r0.first))
+                             : cufftExecZ2Z(s->belt, in, reinterpret_cast<cufftDoubleComplex *>(map) + r0.first,
+                                            CUFFT_INVERSE);
         if (fr != CUFFT_SUCCESS) return sfail(FLINTS_ECUDA, "flints_synthesize: cuFFT execution failed (%d)", (int)fr);
     }
+    if (s->npolar == 0) return FLINTS_OK;
+    // polar rings: Bluestein convolution
+    for (size_t g = 0; g < s->groups.size(); ++g) {
+        cufftSetStream(s->groups[g], st);
+        cufftDoubleComplex *p = reinterpret_cast<cufftDoubleComplex *>(s->d_A + s->group_off[g]);
+        if (cufftExecZ2Z(s->groups[g], p, p, CUFFT_FORWARD) != CUFFT_SUCCESS)
+            return sfail(FLINTS_ECUDA, "flints_synthesize: cuFFT execution failed");
+    }
+    chirp_mul_kernel<<<s->npolar, 256, 0, st>>>(s->d_rings, s->d_polar, s->d_FB, s->d_A);
+    for (size_t g = 0; g < s->groups.size(); ++g) {
+        cufftDoubleComplex *p = reinterpret_cast<cufftDoubleComplex *>(s->d_A + s->group_off[g]);
+        if (cufftExecZ2Z(s->groups[g], p, p, CUFFT_INVERSE) != CUFFT_SUCCESS)
+            return sfail(FLINTS_ECUDA, "flints_synthesize: cuFFT execution failed");
+    }
+    if (s->spin == 0)
+        chirp_out_kernel<0><<<s->npolar, 256, 0, st>>>(s->d_rings, s->d_polar, s->d_A, map);
+    else
+        chirp_out_kernel<1><<<s->npolar, 256, 0, st>>>(s->d_rings, s->d_polar, s->d_A, map);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return sfail(FLINTS_ECUDA, "flints_synthesize: kernel launch: %s", cudaGetErrorString(e));
     return FLINTS_OK;
 }
 
