@@ -56,6 +56,11 @@ __device__ __forceinline__ df df_add_fast(df a, df b) {
     return quick_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
 }
 __device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+// double-float plus a single float
+__device__ __forceinline__ df df_addf(df a, float c) {
+    const df s = two_sum(a.hi, c);
+    return quick_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
 __device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
 __device__ __forceinline__ df df_mul(df a, df b) {
     float p = __fmul_rn(a.hi, b.hi);
