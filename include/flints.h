@@ -246,8 +246,10 @@ const char *flints_last_error(void);
  *     (Q, U) for s = 2; (d_theta, d_phi) for s = 1 when E_lm = sqrt(l(l+1)) phi_lm.
  * E, B are real fields (a_{l,-m} = (-1)^m conj(a_lm)); only m >= 0 is given.
  *   flints_synth_plan: ring geometry, work arrays (about (4 Nside - 1)(2 lmax + 1)
- *     + Npix complex doubles) and the cuFFT plans for Nside (1..8192), lmax
- *     (spin..16384) and spin (0, 1, 2).  Allocates; not capturable.
+ *     + 2 Npix complex doubles) and the cuFFT plans for Nside (1..8192), lmax
+ *     (spin..16384) and spin (0, 1, 2).  precision FLINTS_FP64: the l-recurrence
+ *     in FP64; FLINTS_MIXED: in double-float on the FP32 pipe (relative error
+ *     about 1e-13 at lmax 4096).  Allocates; not capturable.
  *   flints_synthesize: alm (and blm for spin 1, 2; NULL = 0) DEVICE complex
  *     double [lmax+1][lmax+1] (index [l][m], m <= l read), 16-byte aligned;
  *     map DEVICE double [Npix] (spin 0) or [Npix][2] (spin 1, 2), RING order.
@@ -256,7 +258,7 @@ const char *flints_last_error(void);
  * Errors: FLINTS_EINVAL (arguments), FLINTS_ENOMEM, FLINTS_ECUDA; the message
  * is returned by flints_synth_last_error. */
 typedef struct flints_synth_s *flints_synth_t;
-int flints_synth_plan(flints_synth_t *out, int64_t nside, int lmax, int spin, void *stream);
+int flints_synth_plan(flints_synth_t *out, int64_t nside, int lmax, int spin, int precision, void *stream);
 int flints_synthesize(flints_synth_t plan, const double *alm, const double *blm, double *map, void *stream);
 void flints_synth_free(flints_synth_t plan);
 const char *flints_synth_last_error(void);

@@ -102,7 +102,7 @@ def load_library(path: str = LIB_PATH):
     lib.flints_lens_noalloc.argtypes = [i64, c_int, dp, dp, c_int, c_int, c_int, i64, i64, vp, vp, vp, vp, vp, vp]
     lib.flints_lens_noalloc.restype = c_int
     lib.flints_noalloc_last_error.restype = ctypes.c_char_p
-    lib.flints_synth_plan.argtypes = [ctypes.POINTER(vp), i64, c_int, c_int, vp]
+    lib.flints_synth_plan.argtypes = [ctypes.POINTER(vp), i64, c_int, c_int, c_int, vp]
     lib.flints_synth_plan.restype = c_int
     lib.flints_synthesize.argtypes = [vp, vp, vp, vp, vp]
     lib.flints_synthesize.restype = c_int
@@ -402,12 +402,13 @@ class Synth:
     """GPU harmonic synthesis (flints_synth_plan / flints_synthesize): band-limited
     RING maps from a_lm.  Spin 0: T; spin 1, 2: (Re P, Im P) of P = -sum (E + iB) sY_lm."""
 
-    def __init__(self, nside: int, lmax: int, spin: int = 0, stream=None):
+    def __init__(self, nside: int, lmax: int, spin: int = 0, precision: str = "mixed", stream=None):
         lib = load_library()
         self.nside, self.lmax, self.spin = int(nside), int(lmax), int(spin)
         self.npix = 12 * self.nside * self.nside
+        prec = {"fp64": FLINTS_FP64, "mixed": FLINTS_MIXED}[precision]
         h = ctypes.c_void_p()
-        rc = lib.flints_synth_plan(ctypes.byref(h), self.nside, self.lmax, self.spin, _stream(stream))
+        rc = lib.flints_synth_plan(ctypes.byref(h), self.nside, self.lmax, self.spin, prec, _stream(stream))
         if rc != 0:
             raise FlintsError(f"flints error {rc}: {lib.flints_synth_last_error().decode()}")
         self._h = h

@@ -46,9 +46,12 @@
 #include <cstdio>
 #include <vector>
 
+#include "common.cuh"
 #include "flints.h"
 
 namespace {
+
+using flints::df;
 
 constexpr int CHUNK = 256;  // l values staged per pass in shared memory
 constexpr double PI_D = 3.14159265358979323846;
@@ -246,6 +249,169 @@ __global__ void __launch_bounds__(128) legendre_kernel(int lmax, int nside, cons
 // Fold the coefficients of one ring modulo its length n, with the phase of the
 // first pixel: H_k = sum_{m = k mod n} F_m e^{i m phi0}.  Spin 0 (real field,
 // F_-m = F_m^*): k = 0..n/2 for a complex-to-real FFT; spin s: k = 0..n-1.
+// Double-float form of the same recurrence on the FP32 pipe (the mixed
+// precision of the synthesis): the column carried as v 2^E with v a double-
+// float pair, rescaled by 2^-64 while |v| > 2^64 (FP32 exponent range);
+// coefficients, weights and sums in double-float, the sums (F) written as
+// FP64.  Relative accuracy about 1e-13 after 4096 steps.
+struct ColDF {
+    df v, prev;
+    float mult;
+    int e;
+    __device__ __forceinline__ void init(double lg, bool neg) {
+        const double fl = floor(lg);
+        e = (int)fl;
+        double vd = exp2(lg - fl);
+        if (neg) vd = -vd;
+        v = flints::df_from(vd);
+        prev = df{0.0f, 0.0f};
+        mult = e < -126 ? 0.0f : ldexpf(1.0f, e);
+    }
+    __device__ __forceinline__ void step(df a, df b, df c, df x) {
+        const df t = flints::df_sub(flints::df_mul(a, x), b);
+        const df nv = flints::df_sub(flints::df_mul(t, v), flints::df_mul(c, prev));
+        prev = v;
+        v = nv;
+        if (fabsf(v.hi) > 1.8446744e19f) {  // 2^64
+            const float k = 5.421011e-20f;  // 2^-64
+            v = df{v.hi * k, v.lo * k};
+            prev = df{prev.hi * k, prev.lo * k};
+            e += 64;
+            mult = e < -126 ? 0.0f : ldexpf(1.0f, e);
+        }
+    }
+    __device__ __forceinline__ df value() const { return df{v.hi * mult, v.lo * mult}; }
+};
+
+template <int S>
+__global__ void __launch_bounds__(128) legendre_df_kernel(int lmax, int nside, const SynthRing *__restrict__ rings,
+                                                          const double2 *__restrict__ alm,
+                                                          const double2 *__restrict__ blm, double2 *__restrict__ F) {
+    __shared__ float2 sA[CHUNK], sB[CHUNK], sC[CHUNK];
+    __shared__ float4 sWp[CHUNK], sWm[CHUNK];  // (re.hi, re.lo, im.hi, im.lo)
+    const int m = blockIdx.y;
+    const int ring = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    const int nnorth = 2 * nside;
+    const bool active = ring <= nnorth;
+    const int NM = S == 0 ? lmax + 1 : 2 * lmax + 1;
+    const int l0 = m > S ? m : S;
+    const double inv4pi = 1.0 / (4.0 * PI_D);
+    SynthRing rg{};
+    if (active) rg = rings[ring - 1];
+    const df x = flints::df_from(rg.x);
+    ColDF ca{}, cb{};
+    if (active && l0 <= lmax) {
+        bool neg;
+        double lg = start_log2(m, -S, rg.lc, rg.ls, neg);
+        ca.init(lg, neg);
+        if (S > 0) {
+            lg = start_log2(m, S, rg.lc, rg.ls, neg);
+            cb.init(lg, neg);
+        }
+    }
+    using Acc = flints::dfacc;
+    struct CAcc {  // complex double-float sum
+        Acc re, im;
+    };
+    CAcc pAe{}, pAo{}, pBe{}, pBo{}, mAe{}, mAo{}, mBe{}, mBo{};
+    auto mac = [](CAcc &a, df wr, df wi, df d) {
+        flints::dfacc_add_prod(a.re, wr, d);
+        flints::dfacc_add_prod(a.im, wi, d);
+    };
+    auto f2 = [](double v) {
+        const df d = flints::df_from(v);
+        return make_float2(d.hi, d.lo);
+    };
+    for (int c0 = l0; c0 <= lmax; c0 += CHUNK) {
+        const int c1 = min(c0 + CHUNK, lmax + 1);
+        __syncthreads();
+        for (int l = c0 + threadIdx.x; l < c1; l += blockDim.x) {
+            const int k = l - c0;
+            const double ld = (double)l, lp = ld + 1.0;
+            const double md = (double)m, sd = (double)S;
+            const double den = ld * sqrt((lp * lp - md * md) * (lp * lp - sd * sd));
+            if (l == 0 || !(den > 0.0)) {
+                sA[k] = f2(1.0);
+                sB[k] = f2(0.0);
+                sC[k] = f2(0.0);
+            } else {
+                sA[k] = f2((2.0 * ld + 1.0) * ld * lp / den);
+                sB[k] = f2((2.0 * ld + 1.0) * md * sd / den);
+                sC[k] = f2(lp * sqrt((ld * ld - md * md) * (ld * ld - sd * sd)) / den);
+            }
+            const double nl = sqrt((2.0 * ld + 1.0) * inv4pi);
+            const double2 a = alm[(size_t)l * (lmax + 1) + m];
+            double2 wp, wm = make_double2(0.0, 0.0);
+            if (S == 0) {
+                wp = make_double2(a.x * nl, a.y * nl);
+            } else {
+                const double2 b = blm ? blm[(size_t)l * (lmax + 1) + m] : make_double2(0.0, 0.0);
+                wp = make_double2((a.x - b.y) * nl, (a.y + b.x) * nl);
+                wm = make_double2((a.x + b.y) * nl, (b.x - a.y) * nl);
+            }
+            const float2 pr = f2(wp.x), pi = f2(wp.y), mr = f2(wm.x), mi = f2(wm.y);
+            sWp[k] = make_float4(pr.x, pr.y, pi.x, pi.y);
+            sWm[k] = make_float4(mr.x, mr.y, mi.x, mi.y);
+        }
+        __syncthreads();
+        if (active) {
+            for (int l = c0; l < c1; ++l) {
+                const int k = l - c0;
+                const bool odd = ((l + m) & 1) != 0;
+                const df da = ca.value();
+                const float4 wpf = sWp[k];
+                const df wpr{wpf.x, wpf.y}, wpi{wpf.z, wpf.w};
+                // the parity is uniform across the block: no divergence, no indexed registers
+                if (odd) {
+                    mac(pAo, wpr, wpi, da);
+                } else {
+                    mac(pAe, wpr, wpi, da);
+                }
+                if (S > 0) {
+                    const df db = cb.value();
+                    const float4 wmf = sWm[k];
+                    const df wmr{wmf.x, wmf.y}, wmi{wmf.z, wmf.w};
+                    if (odd) {
+                        mac(pBo, wpr, wpi, db);
+                        mac(mAo, wmr, wmi, da);
+                        mac(mBo, wmr, wmi, db);
+                    } else {
+                        mac(pBe, wpr, wpi, db);
+                        mac(mAe, wmr, wmi, da);
+                        mac(mBe, wmr, wmi, db);
+                    }
+                }
+                if (l < lmax) {
+                    const float2 A = sA[k], B = sB[k], C = sC[k];
+                    const df Ad{A.x, A.y}, Bd{B.x, B.y}, Cd{C.x, C.y};
+                    ca.step(Ad, flints::df_neg(Bd), Cd, x);
+                    if (S > 0) cb.step(Ad, Bd, Cd, x);
+                }
+            }
+        }
+    }
+    if (!active) return;
+    auto val = [](const Acc &acc) { return flints::df_to(flints::dfacc_val(acc)); };
+    auto sum = [&](const CAcc &e_, const CAcc &o_, double sg_o, double sg) {
+        return make_double2(sg * (val(e_.re) + sg_o * val(o_.re)), sg * (val(e_.im) + sg_o * val(o_.im)));
+    };
+    const int south = 4 * nside - ring;
+    double2 *Fn = F + (size_t)(ring - 1) * NM;
+    double2 *Fs = F + (size_t)(south - 1) * NM;
+    if (S == 0) {
+        Fn[m] = sum(pAe, pAo, 1.0, 1.0);
+        if (south != ring) Fs[m] = sum(pAe, pAo, -1.0, 1.0);
+        return;
+    }
+    const double sg = (S & 1) ? 1.0 : -1.0;  // -(-1)^s
+    Fn[lmax + m] = sum(pAe, pAo, 1.0, sg);
+    if (south != ring) Fs[lmax + m] = sum(pBe, pBo, -1.0, sg);
+    if (m > 0) {
+        Fn[lmax - m] = sum(mBe, mBo, 1.0, -1.0);
+        if (south != ring) Fs[lmax - m] = sum(mAe, mAo, -1.0, -1.0);
+    }
+}
+
 // Polar rings (rg.M > 0) write a_k = H_k w_k, k < n, zero-padded to M, into
 // their Bluestein slot in A; equatorial rings write H into H.
 template <int S>
@@ -351,7 +517,7 @@ __global__ void chirp_fill_kernel(const int *__restrict__ sizes_n, const int *__
 struct flints_synth_s {
     int device;
     int64_t nside;
-    int lmax, spin;
+    int lmax, spin, precision;
     SynthRing *d_rings;
     int *d_polar;      // indices of the polar rings
     double2 *d_F, *d_H, *d_A, *d_FB;
@@ -387,12 +553,14 @@ extern "C" {
 
 const char *flints_synth_last_error(void) { return g_msg; }
 
-int flints_synth_plan(flints_synth_t *out, int64_t nside, int lmax, int spin, void *stream) {
+int flints_synth_plan(flints_synth_t *out, int64_t nside, int lmax, int spin, int precision, void *stream) {
     if (!out) return sfail(FLINTS_EINVAL, "flints_synth_plan: out is NULL");
     *out = nullptr;
     if (nside < 1 || nside > 8192) return sfail(FLINTS_EINVAL, "flints_synth_plan: nside outside [1, 8192]");
     if (spin != 0 && spin != 1 && spin != 2) return sfail(FLINTS_EINVAL, "flints_synth_plan: spin must be 0, 1 or 2");
     if (lmax < spin || lmax > 16384) return sfail(FLINTS_EINVAL, "flints_synth_plan: lmax outside [spin, 16384]");
+    if (precision != FLINTS_FP64 && precision != FLINTS_MIXED)
+        return sfail(FLINTS_EINVAL, "flints_synth_plan: precision must be FLINTS_FP64 or FLINTS_MIXED");
     const int64_t N = nside;
     const int nr = (int)(4 * N - 1);
     flints_synth_s *s = new flints_synth_s();
@@ -400,6 +568,7 @@ int flints_synth_plan(flints_synth_t *out, int64_t nside, int lmax, int spin, vo
     s->nside = nside;
     s->lmax = lmax;
     s->spin = spin;
+    s->precision = precision;
     s->d_rings = nullptr;
     s->d_polar = nullptr;
     s->d_F = s->d_H = s->d_A = s->d_FB = nullptr;
@@ -587,17 +756,27 @@ int flints_synthesize(flints_synth_t s, const double *alm, const double *blm, do
     const double2 *a = reinterpret_cast<const double2 *>(alm);
     const double2 *b = s->spin == 0 ? nullptr : reinterpret_cast<const double2 *>(blm);
     const int nr = 4 * N - 1;
+    const bool mixed = s->precision == FLINTS_MIXED;
     switch (s->spin) {
         case 0:
-            legendre_kernel<0><<<grid, 128, 0, st>>>(lmax, N, s->d_rings, a, b, s->d_F);
+            if (mixed)
+                legendre_df_kernel<0><<<grid, 128, 0, st>>>(lmax, N, s->d_rings, a, b, s->d_F);
+            else
+                legendre_kernel<0><<<grid, 128, 0, st>>>(lmax, N, s->d_rings, a, b, s->d_F);
             fold_kernel<0><<<nr, 256, 0, st>>>(lmax, s->d_rings, s->d_F, s->d_H, s->d_A);
             break;
         case 1:
-            legendre_kernel<1><<<grid, 128, 0, st>>>(lmax, N, s->d_rings, a, b, s->d_F);
+            if (mixed)
+                legendre_df_kernel<1><<<grid, 128, 0, st>>>(lmax, N, s->d_rings, a, b, s->d_F);
+            else
+                legendre_kernel<1><<<grid, 128, 0, st>>>(lmax, N, s->d_rings, a, b, s->d_F);
             fold_kernel<1><<<nr, 256, 0, st>>>(lmax, s->d_rings, s->d_F, s->d_H, s->d_A);
             break;
         default:
-            legendre_kernel<2><<<grid, 128, 0, st>>>(lmax, N, s->d_rings, a, b, s->d_F);
+            if (mixed)
+                legendre_df_kernel<2><<<grid, 128, 0, st>>>(lmax, N, s->d_rings, a, b, s->d_F);
+            else
+                legendre_kernel<2><<<grid, 128, 0, st>>>(lmax, N, s->d_rings, a, b, s->d_F);
             fold_kernel<2><<<nr, 256, 0, st>>>(lmax, s->d_rings, s->d_F, s->d_H, s->d_A);
             break;
     }
