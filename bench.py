@@ -47,10 +47,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", choices=["c3", "c3aug", "c4", "c5", "ss", "pipeline"], default="c3",
+    ap.add_argument("--workload", choices=["c3", "c3aug", "c4", "c5", "ss", "pipeline", "spin1"], default="c3",
                     help="c3: Nside 4096 spin 2 (default); c3aug: the same with the augmented (xi+, xi-) "
                          "estimator; c4: 64-map batched persistent launch; c5: serving; ss: supersampling "
-                         "Nside 2048 -> 4096; pipeline: synthesis of T, Q/U and the deflection + lensing")
+                         "Nside 2048 -> 4096; pipeline: synthesis of T, Q/U and the deflection + lensing; "
+                         "spin1: a deflection field (spin 1) lensed at Nside 4096")
     ap.add_argument("--duration", type=float, default=45.0, help="c5: seconds of Poisson arrivals")
     ap.add_argument("--profile-case", choices=["mixed", "fp64"], default=None,
                     help="small case for ncu: two launches on 2^18 targets of the resident c3 map")
@@ -560,6 +561,67 @@ def run_ss(args):
         "mixed_stats": st, "gpu_launches": args.steps}))
 
 
+# -------------------------------------------------------------- spin-1 arm
+def run_spin1(args):
+    """A spin-1 field -- a deflection d = grad phi, C^E_l = l(l+1) C^phiphi_l -- remapped
+    at Nside 4096 (lmax 4096, K = 32), 2^24 targets per step, mixed and FP64."""
+    import torch
+
+    import paper_1003_4984_gb300 as fl
+    from paper_1003_4984_gb300 import flops
+
+    fl.load_library()
+    nside, lmax, K = W.nside, W.lmax, W.K
+    npix = 12 * nside * nside
+    ell = np.arange(lmax + 1)
+    cle = wl.cl_phiphi(lmax) * ell * (ell + 1.0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(77)
+    m = torch.randn((npix, 2), dtype=torch.float64, device=dev, generator=g) * wl.DEFLECTION_RMS
+    nb = npix // BATCH
+    defl = torch.randn((nb * BATCH, 2), dtype=torch.float64, device=dev, generator=g) * (wl.DEFLECTION_RMS / math.sqrt(2))
+    out = torch.empty((BATCH, 2), dtype=torch.float64, device=dev)
+    var = torch.empty(BATCH, dtype=torch.float64, device=dev)
+    res = {}
+    for precision, steps in (("mixed", args.steps), ("fp64", max(1, args.fp64_steps))):
+        plan = fl.Plan(nside, cle, spin=1, K=K, precision=precision)
+
+        def step(i):
+            b = i % nb
+            plan.lens(m, defl[b * BATCH:(b + 1) * BATCH], out, var, first=b * BATCH, count=BATCH)
+
+        for i in range(args.warmup):
+            step(i)
+        torch.cuda.synchronize(dev)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        ev[0].record(stream)
+        for i in range(steps):
+            step(args.warmup + i)
+            ev[i + 1].record(stream)
+        torch.cuda.synchronize(dev)
+        per = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+        res[precision] = (BATCH * steps / (ev[0].elapsed_time(ev[steps]) / 1e3), per, plan.stats())
+        plan.close()
+    value, per, st = res["mixed"]
+    fl32 = flops.mixed_fp32_flops(K, 1)
+    achieved = fl32 * BATCH / (statistics.mean(per) / 1e3) / 1e12
+    print(json.dumps({
+        "metric": "lensed pts/s of a spin-1 deflection field at Nside 4096, K=32", "value": value, "unit": "pts/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(per),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64 in/out; double-float factor", "data": "synthetic white-noise spin-1 map, Gaussian deflections",
+        "config": {"workload": "spin 1: Nside 4096, lmax 4096, C^E = l(l+1) C^phiphi (2.5 arcmin rms), K = 32",
+                   "batch_points": BATCH},
+        "fp64": {"value": res["fp64"][0], "ms_per_step": statistics.mean(res["fp64"][1])},
+        "mixed_over_fp64": value / res["fp64"][0],
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": flops.FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / flops.FP32_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "lens_kernel<32,1,mixed>", "flops_per_point": fl32},
+        "mixed_stats": st, "gpu_launches": args.steps}))
+
+
 # ----------------------------------------------------------- pipeline arm
 def run_pipeline(args):
     """Table 2's total on the GPU: from Gaussian a_lm of T, E and phi (Nside 4096,
@@ -674,6 +736,8 @@ if __name__ == "__main__":
         run_ss(a)
     elif a.workload == "pipeline" and a.impl == "ours" and not a.profile_case:
         run_pipeline(a)
+    elif a.workload == "spin1" and a.impl == "ours" and not a.profile_case:
+        run_spin1(a)
     elif a.profile_case:
         run_profile_case(a.profile_case)
     elif a.impl == "reference":

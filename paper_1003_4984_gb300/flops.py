@@ -11,7 +11,8 @@ Counting convention (used for every roofline fraction reported by the bench):
     - two forward solves (c and y): P multiply-adds each, K scalings each;
     - covariance assembly: per pair the squared chord (3 sub, 3 mul, 2 add)
       and the cubic table (index + 3 fma); spin 2 adds the parallel-transport
-      phase (4 projections of 2 fma + 1 mul, squares and products: 48 flops);
+      phase (4 projections of 2 fma + 1 mul, squares and products: 48 flops;
+      spin 1 is counted the same);
       the K target entries likewise (their chords come from the search);
     - value and variance: 2 dot products of length K;
 * augmented spin 2: a real system of size N = 2K with three right-hand sides:
@@ -33,25 +34,25 @@ DF_MAC, DF_ADD, DF_MUL, DF_SPECIAL = 15, 20, 10, 35
 def fp64_flops(K: int, spin: int) -> float:
     P = K * (K - 1) / 2
     macs = (K ** 3 - K) / 6
-    cm = 4 if spin == 2 else 1  # real multiply-adds per (complex) multiply-add
-    chol = 2 * cm * macs + 2 * 2 * K + (2 if spin == 2 else 1) * P
-    solve = 2 * (2 * cm * P + (2 if spin == 2 else 1) * K)
-    pair = 8 + 8 + (48 + 2 if spin == 2 else 0)
-    assembly = pair * P + (8 + (50 if spin == 2 else 0)) * K
-    dots = 2 * 2 * K * (2 if spin == 2 else 1)
+    cm = 4 if spin != 0 else 1  # real multiply-adds per (complex) multiply-add
+    chol = 2 * cm * macs + 2 * 2 * K + (2 if spin != 0 else 1) * P
+    solve = 2 * (2 * cm * P + (2 if spin != 0 else 1) * K)
+    pair = 8 + 8 + (48 + 2 if spin != 0 else 0)
+    assembly = pair * P + (8 + (50 if spin != 0 else 0)) * K
+    dots = 2 * 2 * K * (2 if spin != 0 else 1)
     return chol + solve + assembly + dots
 
 
 def mixed_fp32_flops(K: int, spin: int) -> float:
     P = K * (K - 1) / 2
     macs = (K ** 3 - K) / 6
-    cm = 4 if spin == 2 else 1
-    chol = cm * macs * DF_MAC + K * 2 * DF_SPECIAL + P * (2 if spin == 2 else 1) * DF_MUL
-    solve = 2 * (cm * P * DF_MAC + K * (2 if spin == 2 else 1) * DF_MUL)
+    cm = 4 if spin != 0 else 1
+    chol = cm * macs * DF_MAC + K * 2 * DF_SPECIAL + P * (2 if spin != 0 else 1) * DF_MUL
+    solve = 2 * (cm * P * DF_MAC + K * (2 if spin != 0 else 1) * DF_MUL)
     chord = 3 * DF_ADD + 3 * DF_MUL + 2 * DF_ADD
     table = DF_MUL + 3 * (DF_MUL + DF_ADD)
-    phase = (27 * DF_MUL + 16 * DF_ADD + DF_SPECIAL) if spin == 2 else 0
-    entry = 2 * DF_MUL if spin == 2 else 0
+    phase = (27 * DF_MUL + 16 * DF_ADD + DF_SPECIAL) if spin != 0 else 0
+    entry = 2 * DF_MUL if spin != 0 else 0
     assembly = P * (chord + table + phase + entry) + K * (table + phase + entry)
     return chol + solve + assembly
 
