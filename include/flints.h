@@ -28,8 +28,10 @@
  *   components in the local frame at n'); variance double [count] (may be
  *   NULL; spin s: of P); status uint8 [count]
  *   (may be NULL; FLINTS_ST_* bits, 0 = clean).
- * - All data pointers are DEVICE pointers owned by the caller, aligned to 16
- *   bytes, and must not overlap.  Calls are asynchronous on the given CUDA
+ * - All data pointers are DEVICE pointers owned by the caller and must not
+ *   overlap.  Deflections and two-component maps and outputs (spin 1, 2) must
+ *   be 16-byte aligned, one-component maps, outputs and variances 8-byte
+ *   aligned.  Calls are asynchronous on the given CUDA
  *   stream (cudaStream_t passed as void*, NULL = legacy default stream); the
  *   caller synchronises the stream before reading results.
  * - Errors found on the host (bad arguments, CUDA launch failures, allocation

@@ -269,8 +269,11 @@ static int run(flints_plan_t p, int64_t nside_tgt, int64_t first, int64_t count,
     if (count == 0) return FLINTS_OK;
     if (!defl && nside_tgt == 0) return fail(FLINTS_EINVAL, "defl is NULL");
     if (!stencil && (!map || !out)) return fail(FLINTS_EINVAL, "map and out must not be NULL");
-    const uintptr_t align = (uintptr_t)map | (uintptr_t)defl | (uintptr_t)out;
-    if (align & 15u) return fail(FLINTS_EINVAL, "map, defl and out must be 16-byte aligned");
+    // defl and two-component maps/outputs are read and written as 16-byte pairs
+    const uintptr_t need = p->spin == 0 ? 7u : 15u;
+    if (((uintptr_t)defl & 15u) || (((uintptr_t)map | (uintptr_t)out) & need) || ((uintptr_t)var & 7u))
+        return fail(FLINTS_EINVAL, "defl (and spin 1/2 map and out) must be 16-byte aligned, spin 0 map, out and var "
+                                   "8-byte aligned");
     LensArgs a{};
     a.nside = p->nside;
     a.first = first;
@@ -423,8 +426,9 @@ int flints_batch_stage(flints_batch_t b, const flints_job *jobs, int n, int tile
             return fail(FLINTS_EINVAL, "job %d: target range outside the map", i);
         if (j.count == 0) continue;
         if (!j.map || !j.defl || !j.out) return fail(FLINTS_EINVAL, "job %d: NULL data pointer", i);
-        if (((uintptr_t)j.map | (uintptr_t)j.defl | (uintptr_t)j.out) & 15u)
-            return fail(FLINTS_EINVAL, "job %d: map, defl and out must be 16-byte aligned", i);
+        if (((uintptr_t)j.defl & 15u) || (((uintptr_t)j.map | (uintptr_t)j.out) & (p->spin == 0 ? 7u : 15u)) ||
+            ((uintptr_t)j.var & 7u))
+            return fail(FLINTS_EINVAL, "job %d: misaligned map, defl, out or var", i);
         BatchJob bj{};
         LensArgs &a = bj.a;
         a.nside = p->nside;

@@ -136,6 +136,8 @@ class LensServer:
                 if left <= 0:
                     continue
                 n = min(left, self.chunk_points, budget)
+                if n < left and n > 1:
+                    n &= ~1  # keep the next chunk's outputs on 16-byte boundaries
                 a = req.next_point
                 jobs.append((self.plan_for(req), req.first + a, n, self.maps[req.map_key], req.defl[a:a + n],
                              req.out[a:a + n], req.var[a:a + n], None))
