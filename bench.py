@@ -400,7 +400,7 @@ def run_c4(args):
         "config": {"workload": "c4: 64 maps, Nside in {256,512,1024,2048}, K in {16,24,32,48}, spin in {0,2}, "
                                "lmax = min(2 Nside, 4096), mixed precision; up to 2^20 targets per map per step",
                    "points_per_step": points, "classes": classes, "launch": list(cfg.key()),
-                   "graph": "one CUDA graph replay per step (job upload, queue reset, 2 persistent kernels)"},
+                   "graph": "one CUDA graph replay per step (job upload, queue reset, one persistent kernel per (precision, spin, K) class; empty classes exit at once)"},
         "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
         "per_job_launches": {"ms": seq_ms, "value": points / (seq_ms / 1e3)},
         "stats": st, "gpu_launches": 2 * args.steps}))

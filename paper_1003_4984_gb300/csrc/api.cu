@@ -10,13 +10,15 @@
 #include "batch_types.cuh"
 
 namespace flints {
-cudaError_t batch_prepare_p0(int wpb, int *max_blocks_per_sm);
-int batch_max_wpb();
-cudaError_t batch_prepare_p1(int wpb, int *max_blocks_per_sm);
-cudaError_t batch_launch_p0(const BatchHeader *hdr, const BatchJob *jobs, unsigned long long *next_tile, int wpb,
-                            int blocks, cudaStream_t st);
-cudaError_t batch_launch_p1(const BatchHeader *hdr, const BatchJob *jobs, unsigned long long *next_tile, int wpb,
-                            int blocks, cudaStream_t st);
+// class index within a precision: 4 * (spin == 2) + index of K in {16, 24, 32, 48}
+cudaError_t batch_prepare_p0(int c, int wpb, int *max_blocks_per_sm);
+cudaError_t batch_prepare_p1(int c, int wpb, int *max_blocks_per_sm);
+cudaError_t batch_launch_p0(int c, const BatchHeader *hdr, const BatchJob *jobs, unsigned long long *next_tile,
+                            int wpb, int blocks, cudaStream_t st);
+cudaError_t batch_launch_p1(int c, const BatchHeader *hdr, const BatchJob *jobs, unsigned long long *next_tile,
+                            int wpb, int blocks, cudaStream_t st);
+int batch_fit_wpb_p0(int c);
+int batch_fit_wpb_p1(int c);
 cudaError_t launch_lens_spin0(int K, int precision, const LensArgs &a, int R_rings, const LaunchCfg &cfg,
                               cudaStream_t st);
 cudaError_t launch_lens_spin2(int K, int precision, const LensArgs &a, int R_rings, const LaunchCfg &cfg,
@@ -345,10 +347,10 @@ int flints_stencil(flints_plan_t p, int64_t first, int64_t count, const double *
 struct flints_batch_s {
     int device, max_jobs, num_sms;
     size_t table_bytes;       // header + job array
-    unsigned char *d_buf;     // device: header, jobs, two work-queue counters
+    unsigned char *d_buf;     // device: header, jobs, one work-queue counter per class
     unsigned char *h_buf;     // pinned host staging of header and jobs
-    int wpb[2], max_bps[2];   // prepared launch shape per precision class
-    int max_wpb;              // warps per block that fit in the opt-in shared memory
+    int wpb[BATCH_CLASSES], max_bps[BATCH_CLASSES];  // prepared launch shape per class
+    int fit_wpb[BATCH_CLASSES];                      // warps per block that fit in shared memory
 };
 
 static BatchHeader *hdr_of(unsigned char *p) { return reinterpret_cast<BatchHeader *>(p); }
@@ -356,7 +358,7 @@ static BatchJob *jobs_of(unsigned char *p) { return reinterpret_cast<BatchJob *>
 
 static int batch_prepare(flints_batch_s *b, int cls, int wpb) {
     int mx = 0;
-    cudaError_t e = cls ? batch_prepare_p1(wpb, &mx) : batch_prepare_p0(wpb, &mx);
+    cudaError_t e = (cls >> 3) ? batch_prepare_p1(cls & 7, wpb, &mx) : batch_prepare_p0(cls & 7, wpb, &mx);
     if (e != cudaSuccess) return cuda_fail(e, "batch kernel set-up");
     if (mx < 1) return fail(FLINTS_EINVAL, "batch kernel: %d warps per block do not fit on an SM", wpb);
     b->wpb[cls] = wpb;
@@ -375,7 +377,7 @@ int flints_batch_create(flints_batch_t *out, int max_jobs) {
     b->max_jobs = max_jobs;
     b->num_sms = device_sm_count();
     b->table_bytes = sizeof(BatchHeader) + sizeof(BatchJob) * (size_t)max_jobs;
-    cudaError_t e = cudaMalloc((void **)&b->d_buf, b->table_bytes + 2 * sizeof(unsigned long long));
+    cudaError_t e = cudaMalloc((void **)&b->d_buf, b->table_bytes + BATCH_CLASSES * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaHostAlloc((void **)&b->h_buf, b->table_bytes, cudaHostAllocDefault);
     if (e != cudaSuccess) {
         cudaFree(b->d_buf);
@@ -383,9 +385,9 @@ int flints_batch_create(flints_batch_t *out, int max_jobs) {
         return cuda_fail(e, "flints_batch_create: allocation");
     }
     std::memset(b->h_buf, 0, b->table_bytes);
-    b->max_wpb = batch_max_wpb();
-    for (int cls = 0; cls < 2; ++cls) {
-        if (int rc = batch_prepare(b, cls, 4)) {
+    for (int cls = 0; cls < BATCH_CLASSES; ++cls) {
+        b->fit_wpb[cls] = (cls >> 3) ? batch_fit_wpb_p1(cls & 7) : batch_fit_wpb_p0(cls & 7);
+        if (int rc = batch_prepare(b, cls, b->fit_wpb[cls] < 4 ? b->fit_wpb[cls] : 4)) {
             cudaFree(b->d_buf);
             cudaFreeHost(b->h_buf);
             delete b;
@@ -460,21 +462,23 @@ int flints_batch_stage(flints_batch_t b, const flints_job *jobs, int n, int tile
         v.push_back(bj);
         p->points += j.count;
     }
-    // precision classes, each in decreasing estimated cost (longest jobs start first)
+    // classes (precision, spin, K), each in decreasing estimated cost
+    // (longest jobs start first)
+    auto cls_of = [](const BatchJob &x) { return 8 * x.precision + (x.spin == 2 ? 4 : 0) + batch_k_index(x.K); };
     auto est = [](const BatchJob &x) {
         return (double)x.a.count * x.K * x.K * x.K * (x.spin == 2 ? 4.0 : 1.0);
     };
     std::stable_sort(v.begin(), v.end(), [&](const BatchJob &x, const BatchJob &y) {
-        if (x.precision != y.precision) return x.precision < y.precision;
+        if (cls_of(x) != cls_of(y)) return cls_of(x) < cls_of(y);
         return est(x) > est(y);
     });
     BatchHeader h{};
     h.tile_pts = tp;
     int k = 0;
-    for (int cls = 0; cls < 2; ++cls) {
+    for (int cls = 0; cls < BATCH_CLASSES; ++cls) {
         h.job_offset[cls] = k;
         int64_t tiles = 0;
-        while (k < (int)v.size() && v[k].precision == cls) {
+        while (k < (int)v.size() && cls_of(v[k]) == cls) {
             v[k].tile_begin = tiles;
             tiles += v[k].ntiles;
             ++k;
@@ -492,23 +496,28 @@ int flints_batch_launch(flints_batch_t b, const flints_launch_cfg *cfg, void *st
     int cur = -1;
     cudaGetDevice(&cur);
     if (cur != b->device) return fail(FLINTS_EINVAL, "batch was created on device %d, current device is %d", b->device, cur);
-    int wpb = (cfg && cfg->warps_per_block > 0) ? cfg->warps_per_block : 4;
-    if (wpb > 8) return fail(FLINTS_EINVAL, "flints_batch_launch: warps_per_block 1..8");
-    if (wpb > b->max_wpb) wpb = b->max_wpb;  // a hint: keep the block within shared memory
+    const int want = (cfg && cfg->warps_per_block > 0) ? cfg->warps_per_block : 4;
+    if (want > 8) return fail(FLINTS_EINVAL, "flints_batch_launch: warps_per_block 1..8");
     cudaStream_t st = (cudaStream_t)stream;
     const BatchHeader *h = hdr_of(b->h_buf);
-    const size_t bytes = sizeof(BatchHeader) + sizeof(BatchJob) * (size_t)(h->njobs[0] + h->njobs[1]);
+    int njobs = 0;
+    for (int cls = 0; cls < BATCH_CLASSES; ++cls) njobs += h->njobs[cls];
+    const size_t bytes = sizeof(BatchHeader) + sizeof(BatchJob) * (size_t)njobs;
     unsigned long long *ctr = reinterpret_cast<unsigned long long *>(b->d_buf + b->table_bytes);
     CK(cudaMemcpyAsync(b->d_buf, b->h_buf, bytes, cudaMemcpyHostToDevice, st), "batch: upload jobs");
-    CK(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned long long), st), "batch: reset work queues");
-    for (int cls = 0; cls < 2; ++cls) {
+    CK(cudaMemsetAsync(ctr, 0, BATCH_CLASSES * sizeof(unsigned long long), st), "batch: reset work queues");
+    // every class kernel is launched (an empty class exits at once), so a captured
+    // graph runs whatever table is staged later
+    for (int cls = 0; cls < BATCH_CLASSES; ++cls) {
+        const int wpb = want < b->fit_wpb[cls] ? want : b->fit_wpb[cls];  // a hint: keep within shared memory
         if (b->wpb[cls] != wpb)
             if (int rc = batch_prepare(b, cls, wpb)) return rc;
         int bps = b->max_bps[cls];
         if (cfg && cfg->blocks_per_sm > 0 && cfg->blocks_per_sm < bps) bps = cfg->blocks_per_sm;
         const int blocks = b->num_sms * bps;
-        cudaError_t e = cls ? batch_launch_p1(hdr_of(b->d_buf), jobs_of(b->d_buf), ctr, wpb, blocks, st)
-                            : batch_launch_p0(hdr_of(b->d_buf), jobs_of(b->d_buf), ctr, wpb, blocks, st);
+        cudaError_t e = (cls >> 3)
+                            ? batch_launch_p1(cls & 7, hdr_of(b->d_buf), jobs_of(b->d_buf), ctr, wpb, blocks, st)
+                            : batch_launch_p0(cls & 7, hdr_of(b->d_buf), jobs_of(b->d_buf), ctr, wpb, blocks, st);
         if (e != cudaSuccess) return cuda_fail(e, "batch kernel launch");
     }
     return FLINTS_OK;
