@@ -403,7 +403,7 @@ def run_c4(args):
                    "graph": "one CUDA graph replay per step (job upload, queue reset, one persistent kernel per (precision, spin, K) class; empty classes exit at once)"},
         "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
         "per_job_launches": {"ms": seq_ms, "value": points / (seq_ms / 1e3)},
-        "stats": st, "gpu_launches": 2 * args.steps}))
+        "stats": st, "gpu_launches": 16 * args.steps}))
 
 
 # ------------------------------------------------------------ c5 serving arm
