@@ -1,0 +1,240 @@
+"""HEALPix base-face geometry for the paper's pixel-centred stencil (Sec. 2.3):
+face coordinates of RING pixels, the continuous face projection, point
+location, vertex-sharing neighbours and the 9 * 4^(y-1) stencil.
+
+Test infrastructure (oracle): only tests/, the smoke check and the CPU-baseline
+leg of the benchmark use it; it shares no code with the CUDA path.
+
+Faces.  The sphere is divided into 12 base faces; face f holds the pixels
+(f, ix, iy), 0 <= ix, iy < N.  Face f has ring coordinate jrll[f] and azimuth
+coordinate jpll[f] (in units of N rings and pi/4):
+    jrll = 2 2 2 2 3 3 3 3 4 4 4 4,   jpll = 1 3 5 7 0 2 4 6 1 3 5 7.
+A point with face coordinates (X, Y) in [0, 1]^2 (pixel centres at
+((ix + 1/2)/N, (iy + 1/2)/N)) lies on ring coordinate rho = jrll - X - Y and
+    rho < 1:      z = 1 - rho^2/3,           phi = (pi/4)(jpll + (X - Y)/rho)
+    1 <= rho <= 3: z = (2 - rho) 2/3,        phi = (pi/4)(jpll + X - Y)
+    rho > 3:      z = -(1 - (4 - rho)^2/3),  phi = (pi/4)(jpll + (X - Y)/(4 - rho)),
+the HEALPix projection, which at pixel centres gives the RING centres
+(ring i = N rho, position j from phi).  Pixel vertices are the images of the
+integer face coordinates.
+
+Stencil (Sec. 2.3, "neighbors()" extended with the NESTED hierarchy): at level
+y the direction's pixel at Nside_c = Nside / 2^(y-1) and the pixels of that
+grid sharing a vertex with it (8, or 7 at the 24 pixels next to the vertices
+where three faces meet), each replaced by its 4^(y-1) sub-pixels at Nside:
+9 * 4^(y-1) (or 8 * 4^(y-1)) RING pixels.  The paper's "pixelization at
+Nside/y" is read as Nside / 2^(y-1), the only grid whose pixels hold
+4^(y-1) pixels each.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import healpix as hp
+from . import kriging as kr
+
+JRLL = np.array([2, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 4])
+JPLL = np.array([1, 3, 5, 7, 0, 2, 4, 6, 1, 3, 5, 7])
+
+
+def _ring_params(N: int, i):
+    """(nr, kshift) of rings i (1-based)."""
+    i = np.asarray(i, dtype=np.int64)
+    nr = np.where(i < N, i, np.where(i > 3 * N, 4 * N - i, N))
+    ks = np.where((i >= N) & (i <= 3 * N), (i - N) & 1, 0)
+    return nr, ks
+
+
+def xyf2ring(N: int, ix, iy, f):
+    """RING index of pixel (f, ix, iy)."""
+    ix, iy, f = (np.asarray(a, dtype=np.int64) for a in (ix, iy, f))
+    jr = JRLL[f] * N - ix - iy - 1
+    nr, ks = _ring_params(N, jr)
+    jp = (JPLL[f] * nr + ix - iy + 1 + ks) // 2
+    jp = np.where(jp > 4 * nr, jp - 4 * nr, jp)
+    jp = np.where(jp < 1, jp + 4 * nr, jp)
+    first = np.where(jr < N, 2 * jr * (jr - 1),
+                     np.where(jr <= 3 * N, 2 * N * (N - 1) + 4 * N * (jr - N), 12 * N * N - 2 * nr * (nr + 1)))
+    return first + jp - 1
+
+
+def ring2xyf(N: int, pix):
+    """(ix, iy, f) of RING pixels, by trying the 12 faces: on face f the ring and
+    position fix ix + iy and (ix - iy mod 8 nr); the face is the one where both
+    coordinates fall in [0, N)."""
+    pix = np.asarray(pix, dtype=np.int64)
+    i = hp.pix2ring(N, pix)[0]
+    first = hp.ring_info(N, i)[0]
+    jp = pix - first + 1
+    nr, ks = _ring_params(N, i)
+    out_ix = np.full(pix.shape, -1, dtype=np.int64)
+    out_iy = np.full(pix.shape, -1, dtype=np.int64)
+    out_f = np.full(pix.shape, -1, dtype=np.int64)
+    for f in range(12):
+        s = JRLL[f] * N - 1 - i
+        d = 2 * jp - 1 - ks - JPLL[f] * nr
+        d = (d + 4 * nr) % (8 * nr) - 4 * nr  # representative in [-4 nr, 4 nr)
+        ok = ((s + d) % 2 == 0)
+        ix = (s + d) // 2
+        iy = (s - d) // 2
+        ok &= (ix >= 0) & (ix < N) & (iy >= 0) & (iy < N)
+        ok &= out_f < 0
+        out_ix = np.where(ok, ix, out_ix)
+        out_iy = np.where(ok, iy, out_iy)
+        out_f = np.where(ok, f, out_f)
+    assert np.all(out_f >= 0), "RING pixel without a face"
+    return out_ix, out_iy, out_f
+
+
+def face2vec(X, Y, f):
+    """Unit vectors of face coordinates (X, Y) on faces f (the projection above)."""
+    X, Y = np.asarray(X, dtype=np.float64), np.asarray(Y, dtype=np.float64)
+    f = np.asarray(f, dtype=np.int64)
+    rho = JRLL[f] - X - Y
+    north, south = rho < 1.0, rho > 3.0
+    rn = np.where(north, rho, np.where(south, 4.0 - rho, 1.0))
+    z = np.where(north, 1.0 - rho * rho / 3.0,
+                 np.where(south, -(1.0 - (4.0 - rho) ** 2 / 3.0), (2.0 - rho) * 2.0 / 3.0))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        t = np.where(north | south, np.where(rn > 0, (X - Y) / np.where(rn > 0, rn, 1.0), 0.0), X - Y)
+    phi = 0.25 * math.pi * (JPLL[f] + t)
+    s = np.sqrt(np.maximum(0.0, (1.0 - z) * (1.0 + z)))
+    return np.stack([s * np.cos(phi), s * np.sin(phi), z], axis=-1)
+
+
+def vertices(N: int, pix):
+    """(n, 4, 3) vertices of RING pixels: images of the integer face coordinates."""
+    ix, iy, f = ring2xyf(N, pix)
+    corners = [(0, 0), (1, 0), (0, 1), (1, 1)]
+    return np.stack([face2vec((ix + a) / N, (iy + b) / N, f) for a, b in corners], axis=-2)
+
+
+def vec2pix(N: int, v):
+    """RING pixel containing each unit vector: the face and (X, Y) that the
+    projection maps onto it (inverse of face2vec), then (ix, iy) = floor(N X, N Y)."""
+    v = np.asarray(v, dtype=np.float64)
+    z = v[..., 2]
+    phi = np.arctan2(v[..., 1], v[..., 0]) % (2.0 * math.pi)
+    a = phi / (0.25 * math.pi)  # azimuth in units of pi/4, [0, 8)
+    best_f = np.full(z.shape, -1, dtype=np.int64)
+    bx = np.zeros(z.shape)
+    by = np.zeros(z.shape)
+    for f in range(12):
+        if JRLL[f] == 2:
+            rho = np.where(z > 2.0 / 3.0, np.sqrt(3.0 * (1.0 - z)), 2.0 - 1.5 * z)
+            scale = np.where(z > 2.0 / 3.0, rho, 1.0)
+        elif JRLL[f] == 4:
+            rho = np.where(z < -2.0 / 3.0, 4.0 - np.sqrt(3.0 * (1.0 + z)), 2.0 - 1.5 * z)
+            scale = np.where(z < -2.0 / 3.0, 4.0 - rho, 1.0)
+        else:
+            rho = 2.0 - 1.5 * z
+            scale = np.ones_like(z)
+        da = (a - JPLL[f] + 4.0) % 8.0 - 4.0  # azimuth offset from the face centre, [-4, 4)
+        d = da * scale
+        s = JRLL[f] - rho
+        X = 0.5 * (s + d)
+        Y = 0.5 * (s - d)
+        ok = (X >= 0) & (X <= 1) & (Y >= 0) & (Y <= 1) & (best_f < 0)
+        best_f = np.where(ok, f, best_f)
+        bx = np.where(ok, X, bx)
+        by = np.where(ok, Y, by)
+    assert np.all(best_f >= 0), "direction outside every face"
+    ix = np.minimum((bx * N).astype(np.int64), N - 1)
+    iy = np.minimum((by * N).astype(np.int64), N - 1)
+    return xyf2ring(N, ix, iy, best_f)
+
+
+def neighbours(N: int, pix, tol: float = 1e-9):
+    """Pixels sharing at least one vertex with each RING pixel, sorted by RING
+    index, padded with -1 to 8 columns."""
+    pix = np.atleast_1d(np.asarray(pix, dtype=np.int64))
+    cand, _ = kr.knn(N, hp.pix2vec(N, pix), min(25, hp.npix(N)))
+    vp = vertices(N, pix)                                   # (n, 4, 3)
+    vc = vertices(N, cand.ravel()).reshape(cand.shape + (4, 3))  # (n, c, 4, 3)
+    dist = np.linalg.norm(vp[:, None, :, None, :] - vc[:, :, None, :, :], axis=-1)
+    share = np.any(dist < tol / N, axis=(2, 3)) & (cand != pix[:, None])
+    out = np.full((pix.size, 8), -1, dtype=np.int64)
+    for r in range(pix.size):
+        nb = np.sort(cand[r][share[r]])
+        assert nb.size <= 8, "more than 8 vertex neighbours"
+        out[r, :nb.size] = nb
+    return out
+
+
+def children(N_c: int, pix_c, level: int):
+    """RING indices (at N_c * 2^level) of the 4^level sub-pixels of RING pixels at
+    N_c, in face-coordinate order (x fastest)."""
+    ix, iy, f = ring2xyf(N_c, pix_c)
+    k = 1 << level
+    a, b = np.meshgrid(np.arange(k), np.arange(k), indexing="xy")
+    a, b = a.ravel(), b.ravel()
+    return xyf2ring(N_c * k, ix[..., None] * k + a, iy[..., None] * k + b, f[..., None])
+
+
+def stencil(N: int, targets, y: int):
+    """The paper's stencil of unit vectors ``targets`` at level y: (n, 9 * 4^(y-1))
+    RING indices at N, -1 where the direction's pixel has 7 neighbours.  Order:
+    the direction's pixel, then its neighbours by RING index, each expanded to
+    its sub-pixels in face-coordinate order."""
+    N_c = N >> (y - 1)
+    assert N_c << (y - 1) == N and N_c >= 1, "Nside must be divisible by 2^(y-1)"
+    c = vec2pix(N_c, targets)
+    nb = neighbours(N_c, c)
+    coarse = np.concatenate([c[:, None], nb], axis=1)  # (n, 9)
+    k = 1 << (2 * (y - 1))
+    out = np.full((coarse.shape[0], 9 * k), -1, dtype=np.int64)
+    valid = coarse >= 0
+    ch = children(N_c, np.where(valid, coarse, 0), y - 1)  # (n, 9, k)
+    ch = np.where(valid[..., None], ch, -1)
+    out[:] = ch.reshape(coarse.shape[0], 9 * k)
+    return out
+
+
+# ------------------------------------------------- estimator with tabulated S^-1
+def inverse_estimate(nside: int, maps: np.ndarray, targets: np.ndarray, idx: np.ndarray, f_plus, xi_zero: float,
+                     eps: float = kr.EPS_NUGGET):
+    """Spin-0 estimate on stencils ``idx`` (-1 = absent member) the way Sec. 2.4
+    forms it: L from the Cholesky of S + n I (nugget rule of Sec. 2.4), L^-1 by
+    direct inversion, S^-1 = L^-T L^-1 (the tabulated matrix), then the weights
+    w = S^-1 c, value = w . y and variance = xi(0) (1 - c . w).  Returns
+    (values, variances, nuggets)."""
+    P = targets.shape[0]
+    val = np.empty(P)
+    var = np.empty(P)
+    nug = np.empty(P)
+    counts = np.sum(idx >= 0, axis=1)
+    for K in np.unique(counts):
+        rows = np.nonzero(counts == K)[0]
+        st = np.stack([r[r >= 0] for r in idx[rows]])  # members in stencil order
+        X = hp.pix2vec(nside, st)
+        T = np.sum((X[:, :, None, :] - X[:, None, :, :]) ** 2, axis=-1)
+        S = f_plus(T.reshape(-1)).reshape(T.shape)
+        L, n = kr.factor_with_nugget(S, eps)
+        eye = np.broadcast_to(np.eye(K), L.shape)
+        Linv = np.stack([kr.forward_solve(L, eye[:, :, k]) for k in range(K)], axis=2)  # L^-1 e_k as columns
+        Sinv = np.einsum("pki,pkj->pij", Linv, Linv)
+        c = f_plus(np.sum((targets[rows][:, None, :] - X) ** 2, axis=-1))
+        w = np.einsum("pij,pj->pi", Sinv, c)
+        val[rows] = np.sum(w * maps[st], axis=1)
+        var[rows] = xi_zero * (1.0 - np.sum(c * w, axis=1))
+        nug[rows] = n
+    return val, var, nug
+
+
+def paper_lens(nside: int, y: int, maps: np.ndarray, defl: np.ndarray, pix: np.ndarray, f_plus, xi_zero: float):
+    """Lensed spin-0 values with the paper's stencil at level y (Secs. 2.3-2.5)."""
+    tv = kr.displace(nside, np.asarray(pix, dtype=np.int64), np.asarray(defl, dtype=np.float64))
+    idx = stencil(nside, tv, y)
+    v, s2, n = inverse_estimate(nside, maps, tv, idx, f_plus, xi_zero)
+    return v, s2, idx, tv
+
+
+def paper_supersample(nside: int, nside_out: int, y: int, maps: np.ndarray, pix_out: np.ndarray, f_plus,
+                      xi_zero: float):
+    """Supersampling (Sec. 2.6) with the paper's stencil at level y."""
+    tv = hp.pix2vec(nside_out, np.asarray(pix_out, dtype=np.int64))
+    idx = stencil(nside, tv, y)
+    v, s2, n = inverse_estimate(nside, maps, tv, idx, f_plus, xi_zero)
+    return v, s2, idx, tv
