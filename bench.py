@@ -47,11 +47,13 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", choices=["c3", "c3aug", "c4", "c5", "ss", "pipeline", "spin1"], default="c3",
+    ap.add_argument("--workload", choices=["c3", "c3aug", "c4", "c5", "ss", "pipeline", "spin1", "paper"],
+                    default="c3",
                     help="c3: Nside 4096 spin 2 (default); c3aug: the same with the augmented (xi+, xi-) "
                          "estimator; c4: 64-map batched persistent launch; c5: serving; ss: supersampling "
                          "Nside 2048 -> 4096; pipeline: synthesis of T, Q/U and the deflection + lensing; "
-                         "spin1: a deflection field (spin 1) lensed at Nside 4096")
+                         "spin1: a deflection field (spin 1) lensed at Nside 4096; paper: the 9/36-pixel stencil "
+                         "with tabulated inverses (lensing at 4096, supersampling 2048 -> 4096)")
     ap.add_argument("--duration", type=float, default=45.0, help="c5: seconds of Poisson arrivals")
     ap.add_argument("--profile-case", choices=["mixed", "fp64"], default=None,
                     help="small case for ncu: two launches on 2^18 targets of the resident c3 map")
@@ -726,6 +728,99 @@ def run_pipeline(args):
         s_.close()
 
 
+# ------------------------------------------------- tabulated-inverse arm
+def run_paper(args):
+    """The paper's own route (Secs. 2.3-2.5): the pixel-centred stencil of 9 (y = 1)
+    and 36 (y = 2) pixels with L^-1 (the factor of S^-1) tabulated per symmetry
+    class of central pixels, two triangular matrix-vector products per target
+    (FP64).  Lensing of an
+    Nside 4096, lmax 4096 temperature map (Table 2's configuration) and
+    supersampling Nside 2048 -> 4096 (Table 1's), 2^24 targets per step.  The
+    plan time (stencils and L^-1 tabulation) is Table 2's "init" column."""
+    import torch
+
+    import paper_1003_4984_gb300 as fl
+    from paper_1003_4984_gb300 import flops
+
+    fl.load_library()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(777)
+    lmax = 4096
+    cl = wl.cl_tt(lmax, 2500.0)
+    steps, warm = max(1, args.steps), max(3, args.warmup)
+    out = torch.empty(BATCH, dtype=torch.float64, device=dev)
+    var = torch.empty(BATCH, dtype=torch.float64, device=dev)
+    res = {}
+    clk_path = os.path.join(ROOT, "gpurun_out", "bench_clocks_paper.csv") if os.path.isdir(
+        os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks_paper.csv"
+    with Clocks(clk_path) as clk:
+        for task, nside, nout in (("lens", 4096, None), ("supersample", 2048, 4096)):
+            npix = 12 * nside * nside
+            m = torch.randn(npix, dtype=torch.float64, device=dev, generator=g)
+            ntgt = 12 * (nout or nside) ** 2
+            nb = ntgt // BATCH
+            defl = None
+            if task == "lens":
+                defl = torch.randn((BATCH, 2), dtype=torch.float64, device=dev, generator=g) * wl.DEFLECTION_RMS
+            for y in (1, 2):
+                torch.cuda.synchronize(dev)
+                t0 = time.perf_counter()
+                plan = fl.PaperPlan(nside, cl, y)
+                torch.cuda.synchronize(dev)
+                plan_s = time.perf_counter() - t0
+                info = plan.info()
+
+                def step(i):
+                    first = (i % nb) * BATCH
+                    if task == "lens":
+                        plan.lens(m, defl, first=first, count=BATCH, out=out, var=var)
+                    else:
+                        plan.supersample(m, nout, first=first, count=BATCH, out=out, var=var)
+
+                for i in range(warm):
+                    step(i)
+                torch.cuda.synchronize(dev)
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+                ev[0].record(stream)
+                for i in range(steps):
+                    step(warm + i)
+                    ev[i + 1].record(stream)
+                torch.cuda.synchronize(dev)
+                per = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+                K = info["K"]
+                res[f"{task}_y{y}"] = {
+                    "value": BATCH * steps / (ev[0].elapsed_time(ev[steps]) / 1e3), "unit": "pts/s",
+                    "ms_per_step": statistics.mean(per), "K": K, "plan_s": plan_s, "slots": info["slots"],
+                    "table_bytes": info["table_bytes"], "window": info["window"],
+                    "nugget_slots": info["nugget_slots"], "failed_slots": info["failed_slots"],
+                    "predicted_precision": math.sqrt(float(var.mean()) / info["xi0"]),
+                    "fp64_tflops": flops.paper_fp64_flops(K) * BATCH / (statistics.mean(per) / 1e3) / 1e12}
+                plan.close()
+            del m, defl
+            torch.cuda.empty_cache()
+    head = res["lens_y1"]
+    achieved = head["fp64_tflops"]
+    print(json.dumps({
+        "metric": "lensed pts/s, Nside 4096 T, lmax 4096, paper stencil (9 px) with tabulated inverses, FP64",
+        "value": head["value"], "unit": "pts/s", "n_gpus": 1, "steps": steps, "warmup": warm,
+        "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic white-noise maps, Gaussian deflections of 2.5 arcmin rms",
+        "config": {"workload": "tabulated inverse: lensing Nside 4096 (y = 1, 2) and supersampling "
+                               "Nside 2048 -> 4096 (y = 1, 2), lmax 4096 (damping l = 2500)",
+                   "batch_points": BATCH, "l2": "inputs larger than L2 (1.6 GB map, 268 MB of deflections)"},
+        "arms": res,
+        "paper_tables": "Table 2 (Nside 4096, 9 neighbours): init 16 min, interpolation 22 min per map; "
+                        "Table 1 (2048 -> 4096): 3.3 min (9) / 19 min (36), precision 3e-3 / 3e-4; serial "
+                        "Xeon E5410",
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": flops.FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / flops.FP64_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "paper::apply_kernel<9>", "peak_kind": "nominal FP64",
+                     "flops_per_point": flops.paper_fp64_flops(9)},
+        "clocks": clk.summary(0), "gpu_launches": steps}))
+
+
 if __name__ == "__main__":
     a = parse()
     if a.workload == "c4" and a.impl == "ours" and not a.profile_case:
@@ -738,6 +833,8 @@ if __name__ == "__main__":
         run_pipeline(a)
     elif a.workload == "spin1" and a.impl == "ours" and not a.profile_case:
         run_spin1(a)
+    elif a.workload == "paper" and a.impl == "ours" and not a.profile_case:
+        run_paper(a)
     elif a.profile_case:
         run_profile_case(a.profile_case)
     elif a.impl == "reference":

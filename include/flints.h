@@ -295,6 +295,84 @@ const char *flints_noalloc_last_error(void);
 /* Release a plan and its device memory (NULL is allowed). */
 void flints_free(flints_plan_t plan);
 
+/* The paper's estimator route with tabulated inverses (Secs. 2.3-2.5): the
+ * pixel-centred stencil at level y and the inverse covariance computed once per
+ * class of central pixels, then two triangular matrix-vector products per
+ * target.  Spin 0, FP64.
+ *
+ * Stencil (Sec. 2.3, neighbours() with the NESTED hierarchy): the target's
+ * pixel at Nside_c = Nside / 2^(y-1) and the pixels of that grid sharing a
+ * vertex with it (8; 7 at the 24 pixels next to the points where three base
+ * faces meet; 6 at Nside_c = 1), each replaced by its 4^(y-1) sub-pixels at
+ * Nside: K = 9 * 4^(y-1) members (8 or 7 * 4^(y-1) where fewer neighbours).
+ * The paper's "pixelization at Nside/y" is read as Nside / 2^(y-1), the grid
+ * whose pixels hold 4^(y-1) pixels each.
+ *
+ * Classes (Sec. 2.4): the grid is invariant under z -> -z, under rotations by
+ * pi/2 and, for central pixels whose stencil lies wholly in the equatorial
+ * belt (folded coarse ring Nside_c + 3 .. 2 Nside_c), under the rotation by
+ * one pixel; with members listed in an order those symmetries keep, one
+ * inverse serves a whole class: about Nside_c^2 / 2 + 4 Nside_c of them.  The
+ * tabulated matrix is L^-1, L the Cholesky factor of S + n I
+ * (S = xi(chord^2)/xi(0), nugget n = 1.49e-8 doubled, at most 8 times, while a
+ * pivot is not positive): value = (L^-1 c) . (L^-1 y) = c^T S^-1 y and
+ * variance xi(0) (1 - |L^-1 c|^2), without the cond(S) loss of an explicit
+ * S^-1 and in half its memory.
+ *
+ * flints_paper_plan: y = 1 or 2; nside in [1, 8192] and divisible by
+ *   2^(y-1); cl HOST [lmax+1] (C_l, l = 0..lmax); precision FLINTS_FP64 (the
+ *   only one).  Builds on `stream` the xi table on [0, min((7 / Nside_c)^2, 4)] (interval
+ *   count by the rule of flints_plan), the stencil table and the L^-1 blocks,
+ *   then synchronises `stream`.  Device memory: 12 Nside_c^2 (K + 1) int32 and
+ *   slots * K (K + 1) / 2 doubles (flints_paper_get_info reports the total).  Errors:
+ *   FLINTS_EINVAL (arguments; a stencil chord beyond the table domain),
+ *   FLINTS_ENOMEM, FLINTS_ECUDA; message in flints_paper_last_error().
+ * flints_paper_lens: lensed values at targets first .. first+count-1 (RING
+ *   pixels of the plan's grid displaced along defl, as flints_lens_range).
+ *   map DEVICE [12 Nside^2] (8-byte aligned), defl DEVICE [count][2] (16-byte
+ *   aligned; entry i belongs to pixel first + i), out and var DEVICE [count]
+ *   (var may be NULL), status DEVICE [count] (may be NULL; FLINTS_ST_NUGGET
+ *   when the class needed a raised nugget, FLINTS_ST_WINDOW when a chord fell
+ *   beyond the table domain, FLINTS_ST_FAILED with NaN outputs when no factor
+ *   was found).  Asynchronous on `stream`.
+ * flints_paper_supersample: values at the centres of pixels first ..
+ *   first+count-1 of the grid nside_out (Sec. 2.6); otherwise as above.
+ * flints_paper_get_info: plan sizes and counters (synchronises `stream`).
+ * flints_paper_tables: copies the stencil table (members DEVICE [12 Nside_c^2]
+ *   [K] int32 RING indices at Nside, -1 past the member count), the class of
+ *   each coarse pixel (slot DEVICE [12 Nside_c^2] int32) and the L^-1 blocks
+ *   (linv DEVICE [slots][K (K + 1) / 2] doubles: column j, rows j .. K-1, from
+ *   offset j K - j (j - 1) / 2; zero past the member count) into caller
+ *   buffers; any may be NULL.
+ * flints_paper_free: releases the plan (NULL is allowed). */
+typedef struct flints_paper_s *flints_paper_t;
+typedef struct flints_paper_info {
+    int64_t nside;          /* map grid */
+    int64_t nside_coarse;   /* Nside / 2^(y-1) */
+    int y, K;               /* level and stencil size 9 * 4^(y-1) */
+    int64_t slots;          /* classes of central pixels (L^-1 blocks) */
+    double t_max;           /* xi table domain [0, t_max] in chord^2 */
+    int n_intervals;
+    double xi0;
+    int64_t table_bytes;    /* stencil table + class map + S^-1 blocks */
+    double max_pair_t;      /* largest chord^2 between members of a stencil */
+    int64_t nugget_slots;   /* classes whose factor needed a raised nugget */
+    int64_t failed_slots;   /* classes without a positive-definite factor */
+    int64_t points;         /* targets processed so far */
+    int64_t window;         /* targets with a chord beyond the table domain */
+} flints_paper_info;
+int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double *cl, int y, int precision,
+                      void *stream);
+int flints_paper_lens(flints_paper_t plan, int64_t first, int64_t count, const double *map, const double *defl,
+                      double *out, double *var, uint8_t *status, void *stream);
+int flints_paper_supersample(flints_paper_t plan, int64_t nside_out, int64_t first, int64_t count,
+                             const double *map, double *out, double *var, uint8_t *status, void *stream);
+int flints_paper_get_info(flints_paper_t plan, flints_paper_info *info, void *stream);
+int flints_paper_tables(flints_paper_t plan, int32_t *members, int32_t *slot, double *linv, void *stream);
+void flints_paper_free(flints_paper_t plan);
+const char *flints_paper_last_error(void);
+
+
 #ifdef __cplusplus
 }
 #endif

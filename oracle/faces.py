@@ -34,6 +34,7 @@ import numpy as np
 
 from . import healpix as hp
 from . import kriging as kr
+from . import xi
 
 JRLL = np.array([2, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 4])
 JPLL = np.array([1, 3, 5, 7, 0, 2, 4, 6, 1, 3, 5, 7])
@@ -192,6 +193,24 @@ def stencil(N: int, targets, y: int):
     return out
 
 
+# ------------------------------------------------- correlation table domain
+PAPER_CHORD_BOUND = 7.0  # chords within a level-y stencil, and to its targets, in units of 1/Nside_c
+
+
+def paper_grid_rule(cl: np.ndarray, nside: int, y: int):
+    """Domain and size of the correlation table for the level-y stencil: every
+    chord between members of a stencil, and from a target in the central coarse
+    pixel to them, is below 7 / Nside_c (Nside_c = Nside / 2^(y-1); the bound
+    found by adding the centre-to-centre chords of the coarse pixels and the
+    radii of the pixels grows from 4.7 at Nside_c = 2 to 6.3 at 64 and
+    converges below 6.5), so t_max = (7 / Nside_c)^2, at most 4 (the antipodal
+    chord^2, reached only for Nside_c <= 3); the interval count
+    follows the error rule of xi.grid_rule.  Returns (t_max, n)."""
+    n_c = nside >> (y - 1)
+    t_max = min((PAPER_CHORD_BOUND / n_c) ** 2, 4.0)  # 4: the chord^2 of antipodal points
+    return t_max, xi.table_size(np.abs(cl), t_max)
+
+
 # ------------------------------------------------- estimator with tabulated S^-1
 def inverse_estimate(nside: int, maps: np.ndarray, targets: np.ndarray, idx: np.ndarray, f_plus, xi_zero: float,
                      eps: float = kr.EPS_NUGGET):
@@ -223,18 +242,144 @@ def inverse_estimate(nside: int, maps: np.ndarray, targets: np.ndarray, idx: np.
     return val, var, nug
 
 
-def paper_lens(nside: int, y: int, maps: np.ndarray, defl: np.ndarray, pix: np.ndarray, f_plus, xi_zero: float):
-    """Lensed spin-0 values with the paper's stencil at level y (Secs. 2.3-2.5)."""
+# ------------------------------------------------- inverse per class of central pixels
+def class_representative(n_c: int, pix_c):
+    """Representative of each central pixel's symmetry class (Sec. 2.4: S^-1 is
+    tabulated once for stencils that the symmetries of the grid map onto each
+    other), with the map of the pixel's stencil onto the representative's:
+    (rep, mirror, dphi), a member v going to R_z(dphi) M v, M the reflection
+    z -> -z when mirror is set.
+
+    The grid is invariant under z -> -z (ring i -> 4 Nc - i, same position j),
+    under rotations by pi/2 about the polar axis (j -> j + nq) and, on the rings
+    of the equatorial belt, under the rotation by one pixel.  A pixel whose
+    stencil lies wholly inside the belt (folded ring Nc + 3 .. 2 Nc: the
+    members' rings stay within Nc + 1 .. 3 Nc - 1) is congruent to the first
+    pixel of its folded ring; any other to the pixel j mod nq of its folded ring."""
+    pix_c = np.asarray(pix_c, dtype=np.int64)
+    ring, j = hp.pix2ring(n_c, pix_c)
+    mirror = ring > 2 * n_c
+    fr = np.where(mirror, 4 * n_c - ring, ring)
+    first, _, _, _, _, nq = hp.ring_info(n_c, fr)
+    jr = np.where(fr >= n_c + 3, 0, j % nq)
+    dphi = (jr - j) * (np.pi / 2.0) / nq
+    return first + jr, mirror, dphi
+
+
+def to_class_frame(v: np.ndarray, mirror, dphi) -> np.ndarray:
+    """Apply the class map (reflection, then rotation about the polar axis) to
+    vectors v (..., K, 3) of stencils whose maps are given per stencil."""
+    mirror = np.asarray(mirror)[..., None]
+    c, s = np.cos(dphi)[..., None], np.sin(dphi)[..., None]
+    x, y, z = v[..., 0], v[..., 1], np.where(mirror, -v[..., 2], v[..., 2])
+    return np.stack([c * x - s * y, s * x + c * y, z], axis=-1)
+
+
+def stencil_ordered(nside: int, y: int, pix_c) -> list:
+    """Members of the level-y stencils of coarse pixels ``pix_c`` in the order
+    that makes congruent stencils list corresponding members at the same place:
+    sorted by (s r, dphi), r the member's ring, s = +1 for a central pixel in the
+    northern half (ring <= 2 Nside_c) and -1 in the southern, dphi the member's
+    azimuth minus the central pixel's, wrapped to (-pi, pi], compared exactly
+    (fractions of a quarter turn).  Rotations about the polar axis keep r and
+    dphi; the reflection z -> -z keeps dphi and maps s r to s r - 4 Nside."""
+    from fractions import Fraction
+
+    n_c = nside >> (y - 1)
+    pix_c = np.atleast_1d(np.asarray(pix_c, dtype=np.int64))
+    idx = stencil(nside, hp.pix2vec(n_c, pix_c), y)
+    ring_c, j_c = hp.pix2ring(n_c, pix_c)
+    _, _, _, _, f_c, nq_c = hp.ring_info(n_c, ring_c)
+    out = []
+    for k in range(pix_c.size):
+        mem = idx[k][idx[k] >= 0]
+        r, j = hp.pix2ring(nside, mem)
+        _, _, _, _, f, nq = hp.ring_info(nside, r)
+        sgn = 1 if ring_c[k] <= 2 * n_c else -1
+        u_c = Fraction(int(2 * j_c[k] + round(2 * f_c[k])), int(2 * nq_c[k]))
+        keys = []
+        for a in range(mem.size):
+            du = Fraction(int(2 * j[a] + round(2 * f[a])), int(2 * nq[a])) - u_c
+            while du > 2:
+                du -= 4
+            while du <= -2:
+                du += 4
+            keys.append((sgn * int(r[a]), du, int(mem[a])))
+        keys.sort()
+        out.append(np.array([m for _, _, m in keys], dtype=np.int64))
+    return out
+
+
+def class_estimate(nside: int, y: int, maps: np.ndarray, targets: np.ndarray, f_plus, xi_zero: float,
+                   eps: float = kr.EPS_NUGGET):
+    """Spin-0 estimate with the inverse tabulated per class (Sec. 2.4): for each
+    class the representative's S + n I is factored (nugget rule of Sec. 2.4) and
+    L^-1 found by direct inversion from the representative's own member
+    positions; a target in coarse pixel c uses that L^-1 with c's members
+    matched to the representative's (the member nearest to R_z(dphi) M v), its
+    own c_i = xi(|n' - x_i|^2)/xi(0) and data: z_c = L^-1 c, z_y = L^-1 y,
+    value c^T S^-1 y = z_c . z_y, variance xi(0) (1 - z_c . z_c).  (The same
+    estimator as w = S^-1 c, w . y with S^-1 = L^-T L^-1 formed explicitly, but
+    without that product's loss of a factor cond(S).)  Returns (values,
+    variances, stencils)."""
+    n_c = nside >> (y - 1)
+    cpix = vec2pix(n_c, targets)
+    idx = stencil(nside, targets, y)
+    rep, mirror, dphi = class_representative(n_c, cpix)
+    P = targets.shape[0]
+    val = np.empty(P)
+    var = np.empty(P)
+    for r in np.unique(rep):
+        rows = np.nonzero(rep == r)[0]
+        ridx = stencil(nside, hp.pix2vec(n_c, np.array([r])), y)[0]
+        ridx = ridx[ridx >= 0]
+        K = ridx.size
+        Xr = hp.pix2vec(nside, ridx)
+        S = f_plus(np.sum((Xr[:, None, :] - Xr[None, :, :]) ** 2, axis=-1).reshape(-1)).reshape(1, K, K)
+        L, _ = kr.factor_with_nugget(S, eps)
+        eye = np.eye(K)[None]
+        Linv = np.stack([kr.forward_solve(L, eye[:, :, k]) for k in range(K)], axis=2)[0]
+        mem = np.stack([row[row >= 0] for row in idx[rows]])  # (n, K): every pixel of a class has K members
+        X = hp.pix2vec(nside, mem)
+        U = to_class_frame(X, mirror[rows], dphi[rows])
+        d = np.linalg.norm(U[:, :, None, :] - Xr[None, None, :, :], axis=-1)
+        perm = np.argmin(d, axis=2)  # member a of c <-> member perm[a] of the representative
+        assert np.max(np.min(d, axis=2)) < 1e-9 / nside, "stencil not congruent to its class representative"
+        assert np.all(np.sort(perm, axis=1) == np.arange(K)), "class map is not a bijection of the members"
+        c = f_plus(np.sum((targets[rows][:, None, :] - X) ** 2, axis=-1))
+        ar = np.arange(rows.size)[:, None]
+        c_r = np.empty_like(c)
+        y_r = np.empty_like(c)
+        c_r[ar, perm] = c  # in the representative's member order
+        y_r[ar, perm] = maps[mem]
+        zc = c_r @ Linv.T
+        zy = y_r @ Linv.T
+        val[rows] = np.sum(zc * zy, axis=1)
+        var[rows] = xi_zero * (1.0 - np.sum(zc * zc, axis=1))
+    return val, var, idx
+
+
+def paper_lens(nside: int, y: int, maps: np.ndarray, defl: np.ndarray, pix: np.ndarray, f_plus, xi_zero: float,
+               classes: bool = False):
+    """Lensed spin-0 values with the paper's stencil at level y (Secs. 2.3-2.5);
+    ``classes``: S^-1 per class of central pixels (class_estimate) instead of
+    per target."""
     tv = kr.displace(nside, np.asarray(pix, dtype=np.int64), np.asarray(defl, dtype=np.float64))
+    if classes:
+        v, s2, idx = class_estimate(nside, y, maps, tv, f_plus, xi_zero)
+        return v, s2, idx, tv
     idx = stencil(nside, tv, y)
     v, s2, n = inverse_estimate(nside, maps, tv, idx, f_plus, xi_zero)
     return v, s2, idx, tv
 
 
 def paper_supersample(nside: int, nside_out: int, y: int, maps: np.ndarray, pix_out: np.ndarray, f_plus,
-                      xi_zero: float):
+                      xi_zero: float, classes: bool = False):
     """Supersampling (Sec. 2.6) with the paper's stencil at level y."""
     tv = hp.pix2vec(nside_out, np.asarray(pix_out, dtype=np.int64))
+    if classes:
+        v, s2, idx = class_estimate(nside, y, maps, tv, f_plus, xi_zero)
+        return v, s2, idx, tv
     idx = stencil(nside, tv, y)
     v, s2, n = inverse_estimate(nside, maps, tv, idx, f_plus, xi_zero)
     return v, s2, idx, tv

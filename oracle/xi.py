@@ -303,6 +303,11 @@ def grid_rule(cl_weight: np.ndarray, K: int, nside: int):
     """
     r = SEARCH_RADIUS_FACTOR * math.sqrt(K / 3.0) / nside
     t_max = 4.0 * r * r
+    return t_max, table_size(cl_weight, t_max)
+
+
+def table_size(cl_weight: np.ndarray, t_max: float) -> int:
+    """Interval count of a table on [0, t_max] under the error rule of grid_rule."""
     cw = np.abs(np.asarray(cl_weight, dtype=np.float64))
     ell = np.arange(cw.size, dtype=np.float64)
     a = (2.0 * ell + 1.0) / FOUR_PI * cw
@@ -313,4 +318,4 @@ def grid_rule(cl_weight: np.ndarray, K: int, nside: int):
     if b4 > 0:
         h = (384.0 * TABLE_TOLERANCE / b4) ** 0.25
         n = max(64, 2 ** int(math.ceil(math.log2(t_max / h))))
-    return t_max, min(n, 65536)
+    return min(n, 65536)

@@ -42,6 +42,14 @@ class _Info(ctypes.Structure):
                 ("xi0", ctypes.c_double), ("search_radius", ctypes.c_double)]
 
 
+class _PaperInfo(ctypes.Structure):
+    _fields_ = [("nside", ctypes.c_int64), ("nside_coarse", ctypes.c_int64), ("y", ctypes.c_int), ("K", ctypes.c_int),
+                ("slots", ctypes.c_int64), ("t_max", ctypes.c_double), ("n_intervals", ctypes.c_int),
+                ("xi0", ctypes.c_double), ("table_bytes", ctypes.c_int64), ("max_pair_t", ctypes.c_double),
+                ("nugget_slots", ctypes.c_int64), ("failed_slots", ctypes.c_int64), ("points", ctypes.c_int64),
+                ("window", ctypes.c_int64)]
+
+
 class LaunchCfg(ctypes.Structure):
     """flints_launch_cfg: warps per block, blocks per SM cap, targets per warp tile (0 = default)."""
     _fields_ = [("warps_per_block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int), ("tile_points", ctypes.c_int)]
@@ -109,6 +117,17 @@ def load_library(path: str = LIB_PATH):
     lib.flints_synth_free.argtypes = [vp]
     lib.flints_synth_free.restype = None
     lib.flints_synth_last_error.restype = ctypes.c_char_p
+    lib.flints_paper_plan.argtypes = [ctypes.POINTER(vp), i64, c_int, dp, c_int, c_int, vp]
+    lib.flints_paper_lens.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp]
+    lib.flints_paper_supersample.argtypes = [vp, i64, i64, i64, vp, vp, vp, vp, vp]
+    lib.flints_paper_get_info.argtypes = [vp, ctypes.POINTER(_PaperInfo), vp]
+    lib.flints_paper_tables.argtypes = [vp, vp, vp, vp, vp]
+    for name in ("flints_paper_plan", "flints_paper_lens", "flints_paper_supersample", "flints_paper_get_info",
+                 "flints_paper_tables"):
+        getattr(lib, name).restype = c_int
+    lib.flints_paper_free.argtypes = [vp]
+    lib.flints_paper_free.restype = None
+    lib.flints_paper_last_error.restype = ctypes.c_char_p
     for name in ("flints_plan", "flints_lens_spin0", "flints_lens_spin2", "flints_lens_range", "flints_stencil",
                  "flints_lens_batch", "flints_get_stats", "flints_reset_stats", "flints_get_info",
                  "flints_get_table"):
@@ -441,6 +460,94 @@ class Synth:
     def close(self):
         if getattr(self, "_h", None):
             load_library().flints_synth_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class PaperPlan:
+    """The paper's stencil with tabulated inverses (flints_paper_*): level-y
+    pixel-centred stencil of 9 * 4^(y-1) pixels, L^-1 (the factor of S^-1)
+    tabulated per symmetry class of central pixels, two triangular
+    matrix-vector products per target (spin 0, FP64)."""
+
+    def __init__(self, nside: int, cl, y: int = 1, stream=None):
+        lib = load_library()
+        cl = np.ascontiguousarray(cl, dtype=np.float64)
+        self.nside, self.y = int(nside), int(y)
+        h = ctypes.c_void_p()
+        rc = lib.flints_paper_plan(ctypes.byref(h), self.nside, cl.size - 1,
+                                   cl.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self.y, FLINTS_FP64,
+                                   _stream(stream))
+        if rc != 0:
+            raise FlintsError(f"flints error {rc}: {lib.flints_paper_last_error().decode()}")
+        self._h = h
+        i = self.info()
+        self.nside_coarse, self.K, self.slots = i["nside_coarse"], i["K"], i["slots"]
+
+    def _raise(self, rc):
+        if rc != 0:
+            raise FlintsError(f"flints error {rc}: {load_library().flints_paper_last_error().decode()}")
+
+    def info(self, stream=None) -> dict:
+        inf = _PaperInfo()
+        self._raise(load_library().flints_paper_get_info(self._h, ctypes.byref(inf), _stream(stream)))
+        return {name: getattr(inf, name) for name, _ in _PaperInfo._fields_}
+
+    def _outputs(self, map_, count, out, var, status):
+        import torch
+
+        _dev_f64(map_, (12 * self.nside * self.nside,), "map")
+        if out is None:
+            out = torch.empty(count, dtype=torch.float64, device=map_.device)
+        if var is None:
+            var = torch.empty(count, dtype=torch.float64, device=map_.device)
+        _dev_f64(out, (count,), "out")
+        _dev_f64(var, (count,), "var")
+        if status is not None and (status.dtype != torch.uint8 or tuple(status.shape) != (count,)):
+            raise FlintsError("status must be a uint8 CUDA tensor of shape (count,)")
+        return out, var
+
+    def lens(self, map_, defl, first: int = 0, count: int | None = None, out=None, var=None, status=None,
+             stream=None):
+        """Lensed values at pixels first .. first+count-1 displaced along defl[(count, 2)]."""
+        if count is None:
+            count = 12 * self.nside * self.nside - first
+        _dev_f64(defl, (count, 2), "defl")
+        out, var = self._outputs(map_, count, out, var, status)
+        self._raise(load_library().flints_paper_lens(self._h, first, count, _ptr(map_), _ptr(defl), _ptr(out),
+                                                     _ptr(var), _ptr(status), _stream(stream)))
+        return out, var
+
+    def supersample(self, map_, nside_out: int, first: int = 0, count: int | None = None, out=None, var=None,
+                    status=None, stream=None):
+        """Values at the centres of pixels first .. first+count-1 of the grid nside_out."""
+        if count is None:
+            count = 12 * nside_out * nside_out - first
+        out, var = self._outputs(map_, count, out, var, status)
+        self._raise(load_library().flints_paper_supersample(self._h, nside_out, first, count, _ptr(map_), _ptr(out),
+                                                            _ptr(var), _ptr(status), _stream(stream)))
+        return out, var
+
+    def tables(self, stream=None):
+        """(members (12 Nc^2, K) int32, slot (12 Nc^2,) int32, linv (slots, K (K + 1) / 2) float64)
+        device copies; linv holds L^-1 packed by columns (column j, rows j .. K-1)."""
+        import torch
+
+        npc = 12 * self.nside_coarse * self.nside_coarse
+        mem = torch.empty((npc, self.K), dtype=torch.int32, device="cuda")
+        slot = torch.empty(npc, dtype=torch.int32, device="cuda")
+        linv = torch.empty((self.slots, self.K * (self.K + 1) // 2), dtype=torch.float64, device="cuda")
+        self._raise(load_library().flints_paper_tables(self._h, _ptr(mem), _ptr(slot), _ptr(linv), _stream(stream)))
+        return mem, slot, linv
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().flints_paper_free(self._h)
             self._h = None
 
     def __del__(self):

@@ -1,0 +1,760 @@
+// The paper's own estimator route (Secs. 2.3-2.5): the pixel-centred stencil of
+// 9 * 4^(y-1) pixels with the inverse covariance tabulated once per symmetry
+// class of central pixels, so that each target costs two triangular
+// matrix-vector products instead of a K x K Cholesky factorisation.
+//
+// The tabulated matrix is L^-1, the factor of S^-1 = L^-T L^-1 (L the Cholesky
+// factor of S + n I): the estimate c^T S^-1 y = (L^-1 c) . (L^-1 y) and its
+// variance xi(0) (1 - |L^-1 c|^2) then carry the rounding of a triangular
+// solve, not that of an explicit inverse (which loses a factor cond(S) ~ 1e8),
+// in half the memory of S^-1.
+//
+// Plan (once per Nside, y and spectrum):
+//   1. xi table on [0, t_max], t_max = min((7 / Nc)^2, 4) (every chord between
+//      stencil members and from a target to them is below 7 / Nc);
+//   2. stencil_kernel: one thread per coarse pixel c (Nc = Nside / 2^(y-1))
+//      writes its members (ordering rule of paper_geom.cuh) and its slot;
+//   3. linv_kernel: one block per slot: S = xi(chord^2)/xi(0) over the slot
+//      representative's members, nugget rule of Sec. 2.4, right-looking
+//      Cholesky in shared memory, L^-1 column by column, stored packed by
+//      columns (column j, rows j .. K-1, contiguous: coalesced lane loads).
+// Per call (apply_kernel): one warp per tile of 32 targets.  Lane l displaces
+// target l and locates its coarse pixel (RING ang2pix at Nc); then per target
+// (three at a time in groups of 10 lanes for K = 9, one at a time for K = 36)
+// the lanes own stencil members l (and l + 32): c_l = xi(|n' - x_l|^2)/xi(0),
+// y_l = map[x_l]; lane i accumulates row i of z_c = L^-1 c and z_y = L^-1 y
+// (c_j, y_j broadcast by shuffles); value = z_c . z_y and variance
+// xi(0) (1 - z_c . z_c), the kriging estimate and its error (Eqs.
+// best_temperature_field, gaussvar).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "flints.h"
+#include "lens.cuh"
+#include "paper_geom.cuh"
+
+namespace flints {
+namespace paper {
+
+constexpr int SINV_THREADS = 64;
+
+// offset of column j of a K x K lower-triangular matrix packed by columns
+__host__ __device__ constexpr int col_start(int K, int j) { return j * K - j * (j - 1) / 2; }
+constexpr int LDS = STENCIL_MAX + 1;  // padded shared-memory row stride
+
+// unit vector of RING pixel p at Nside N
+__device__ __forceinline__ void pix2vec(int64_t N, int64_t p, double &x, double &y, double &z) {
+    int64_t i, j;
+    pix_ring(N, p, i, j);
+    const Ring rg = ring_of(N, i);
+    double sp, cp;
+    sincospi(((double)j + rg.f) / (2.0 * (double)rg.nq), &sp, &cp);
+    x = rg.s * cp;
+    y = rg.s * sp;
+    z = rg.z;
+}
+
+// RING pixel at Nside N containing the unit vector (x, y, z) (the ring scheme's
+// point location of Gorski et al. 2005: belt by the two edge-line families,
+// caps by the distance to the pole, sin(theta) taken from x, y near the poles)
+__device__ __forceinline__ int64_t ang2pix(int64_t N, double x, double y, double z) {
+    const double Nd = (double)N;
+    double phi = atan2(y, x);
+    if (phi < 0.0) phi += 2.0 * PI;
+    double tt = phi * (2.0 / PI);  // [0, 4)
+    if (tt >= 4.0) tt -= 4.0;
+    const double za = fabs(z);
+    if (za <= 2.0 / 3.0) {
+        const double t1 = Nd * (0.5 + tt), t2 = Nd * z * 0.75;
+        const int64_t jp = (int64_t)floor(t1 - t2), jm = (int64_t)floor(t1 + t2);
+        int64_t ir = N + 1 + jp - jm;  // 1 .. 2N+1, from z = 2/3
+        ir = ir < 1 ? 1 : (ir > 2 * N + 1 ? 2 * N + 1 : ir);  // rounding at |z| = 2/3
+        const int64_t kshift = 1 - (ir & 1);
+        int64_t ip = (jp + jm - N + kshift + 1) / 2;
+        ip = pmod(ip, 4 * N);
+        return 2 * N * (N - 1) + (ir - 1) * 4 * N + ip;
+    }
+    const double tp = tt - floor(tt);
+    const double st = sqrt(x * x + y * y);
+    const double tmp = Nd * st * sqrt(3.0 / (1.0 + za));  // N sqrt(3 (1 - |z|))
+    int64_t jp = (int64_t)(tp * tmp), jm = (int64_t)((1.0 - tp) * tmp);
+    jp = jp < 0 ? 0 : (jp > N - 1 ? N - 1 : jp);
+    jm = jm < 0 ? 0 : (jm > N - 1 - jp ? N - 1 - jp : jm);
+    const int64_t ir = jp + jm + 1;  // ring counted from the nearer pole
+    int64_t ip = (int64_t)(tt * (double)ir);
+    ip = pmod(ip, 4 * ir);
+    return z > 0.0 ? 2 * ir * (ir - 1) + ip : 12 * N * N - 2 * ir * (ir + 1) + ip;
+}
+
+// ---------------------------------------------------------------- plan kernels
+__global__ void stencil_kernel(int64_t Nc, int k, int K, int32_t *members, int32_t *slot, int *bad) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= 12 * Nc * Nc) return;
+    int32_t mem[STENCIL_MAX];
+    const int n = stencil_members(Nc, k, c, mem);
+    int32_t *dst = members + c * K;
+    if (n < 0 || n > K) {
+        atomicAdd(bad, 1);
+        for (int m = 0; m < K; ++m) dst[m] = -1;
+    } else {
+        for (int m = 0; m < K; ++m) dst[m] = m < n ? mem[m] : -1;
+    }
+    int64_t i, j;
+    ring_and_pos(Nc, c, i, j);
+    slot[c] = (int32_t)slot_of(Nc, i, j);
+}
+
+struct LinvArgs {
+    int64_t Nc, N, nslot;
+    int K;
+    const int32_t *members;
+    TableDev tab;
+    double *linv;                  // [nslot][K (K + 1) / 2], L^-1 packed by columns
+    int *slot_steps;               // [nslot]: nugget doublings, -1 = no factor found
+    unsigned long long *max_t;     // bits of the largest member-pair chord^2
+    int *counts;                   // [0]: slots with a raised nugget, [1]: failed slots
+};
+
+__global__ void __launch_bounds__(SINV_THREADS) linv_kernel(LinvArgs a) {
+    __shared__ double S[STENCIL_MAX * LDS], Li[STENCIL_MAX * LDS];
+    __shared__ double px[STENCIL_MAX], py[STENCIL_MAX], pz[STENCIL_MAX];
+    __shared__ int n_sh, bad;
+    const int tid = threadIdx.x, nt = blockDim.x, K = a.K;
+    for (int64_t sl = blockIdx.x; sl < a.nslot; sl += gridDim.x) {
+        const int64_t rep = slot_rep(a.Nc, sl);
+        const int32_t *mem = a.members + rep * K;
+        if (tid == 0) {
+            int n = 0;
+            while (n < K && mem[n] >= 0) ++n;
+            n_sh = n;
+        }
+        __syncthreads();
+        const int n = n_sh;
+        for (int m = tid; m < n; m += nt) pix2vec(a.N, mem[m], px[m], py[m], pz[m]);
+        __syncthreads();
+        double tmax = 0.0;
+        double nug = NUGGET_EPS;
+        int steps = 0;
+        bool ok = false;
+        for (; steps <= MAX_NUGGET_STEPS; ++steps) {
+            for (int e = tid; e < n * n; e += nt) {
+                const int i = e / n, j = e - (e / n) * n;
+                if (j > i) continue;
+                if (i == j) {
+                    S[i * LDS + j] = 1.0 + nug;
+                } else {
+                    const double dx = px[i] - px[j], dy = py[i] - py[j], dz = pz[i] - pz[j];
+                    const double t = dx * dx + dy * dy + dz * dz;
+                    tmax = fmax(tmax, t);
+                    S[i * LDS + j] = table_eval<double>(a.tab, t);
+                }
+            }
+            if (tid == 0) bad = 0;
+            __syncthreads();
+            // right-looking Cholesky of the lower triangle, in place
+            for (int kk = 0; kk < n; ++kk) {
+                if (tid == 0) {
+                    const double d = S[kk * LDS + kk];
+                    if (d > 0.0) S[kk * LDS + kk] = sqrt(d); else bad = 1;
+                }
+                __syncthreads();
+                if (bad) break;
+                const double lkk = S[kk * LDS + kk];
+                for (int i = kk + 1 + tid; i < n; i += nt) S[i * LDS + kk] /= lkk;
+                __syncthreads();
+                const int w = n - kk - 1;
+                for (int e = tid; e < w * w; e += nt) {
+                    const int i = kk + 1 + e / w, j = kk + 1 + (e - (e / w) * w);
+                    if (j <= i) S[i * LDS + j] -= S[i * LDS + kk] * S[j * LDS + kk];
+                }
+                __syncthreads();
+            }
+            if (!bad) {
+                ok = true;
+                break;
+            }
+            nug *= 2.0;
+            __syncthreads();
+        }
+        // L^-1, one column per thread: L x = e_col by forward substitution
+        if (ok) {
+            for (int col = tid; col < n; col += nt) {
+                for (int i = 0; i < col; ++i) Li[i * LDS + col] = 0.0;
+                for (int i = col; i < n; ++i) {
+                    double acc = i == col ? 1.0 : 0.0;
+                    for (int m = col; m < i; ++m) acc = fma(-S[i * LDS + m], Li[m * LDS + col], acc);
+                    Li[i * LDS + col] = acc / S[i * LDS + i];
+                }
+            }
+        }
+        __syncthreads();
+        // L^-1 packed by columns: column j (rows j .. K-1) from offset col_start(K, j);
+        // zero outside the n x n block
+        double *dst = a.linv + sl * (int64_t)(K * (K + 1) / 2);
+        for (int j = 0; j < K; ++j) {
+            for (int i = j + tid; i < K; i += nt)
+                dst[col_start(K, j) + i - j] = (ok && i < n && j < n) ? Li[i * LDS + j] : 0.0;
+        }
+        // the largest pair chord (block reduction through atomics on the bit pattern)
+        if (tmax > 0.0) atomicMax(a.max_t, (unsigned long long)__double_as_longlong(tmax));
+        if (tid == 0) {
+            a.slot_steps[sl] = ok ? steps : -1;
+            if (!ok) atomicAdd(a.counts + 1, 1);
+            else if (steps > 0) atomicAdd(a.counts, 1);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- apply kernel
+struct ApplyArgs {
+    int64_t N, Nc, first, count, nside_tgt;
+    const double *map, *defl;
+    double *out, *var;
+    uint8_t *status;
+    const int32_t *members, *slot;
+    const double *linv;
+    const int *slot_steps;
+    TableDev tab;
+    double xi0;
+    unsigned long long *counters;  // points, nugget, -, window, failed
+};
+
+constexpr int APPLY_WARPS = 4;
+constexpr int GROUP = 10;  // lanes per target when K <= 10 (three targets per warp)
+
+// value, variance and status of target p from v = w . y and qc = w . c
+__device__ __forceinline__ void finish_point(const ApplyArgs &a, int64_t p, int32_t sl, double v, double qc,
+                                             bool any_win, unsigned long long &n_win, unsigned long long &n_nug,
+                                             unsigned long long &n_fail) {
+    const int steps = __ldg(a.slot_steps + sl);
+    uint8_t st = 0;
+    if (steps > 0) st |= FLINTS_ST_NUGGET;
+    if (any_win) st |= FLINTS_ST_WINDOW;
+    if (steps < 0) {
+        st |= FLINTS_ST_FAILED;
+        v = __longlong_as_double(0x7ff8000000000000ll);
+        qc = v;
+    }
+    a.out[p] = v;
+    if (a.var) a.var[p] = a.xi0 * (1.0 - qc);
+    if (a.status) a.status[p] = st;
+    n_win += any_win;
+    n_nug += steps > 0;
+    n_fail += steps < 0;
+}
+
+template <int K>
+__global__ void __launch_bounds__(APPLY_WARPS * 32) apply_kernel(ApplyArgs a) {
+    __shared__ double stx[APPLY_WARPS][32], sty[APPLY_WARPS][32], stz[APPLY_WARPS][32];
+    __shared__ int64_t scp[APPLY_WARPS][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t ntiles = (a.count + 31) / 32;
+    unsigned long long n_win = 0, n_nug = 0, n_fail = 0;
+    for (int64_t tile = (int64_t)blockIdx.x * APPLY_WARPS + wid; tile < ntiles;
+         tile += (int64_t)gridDim.x * APPLY_WARPS) {
+        // ---- lane l: target l of the tile and its coarse pixel
+        {
+            const int64_t p = tile * 32 + lane;
+            double x = 0.0, y = 0.0, z = 1.0;
+            if (p < a.count) {
+                const int64_t pix = a.first + p;
+                if (a.nside_tgt > 0) {
+                    pix2vec(a.nside_tgt, pix, x, y, z);
+                } else {
+                    int64_t i, j;
+                    pix_ring(a.N, pix, i, j);
+                    const Ring rg = ring_of(a.N, i);
+                    double sp, cp;
+                    sincospi(((double)j + rg.f) / (2.0 * (double)rg.nq), &sp, &cp);
+                    const double nx = rg.s * cp, ny = rg.s * sp, nz = rg.z;
+                    const double2 dd = __ldg(reinterpret_cast<const double2 *>(a.defl) + p);
+                    const double dl = sqrt(dd.x * dd.x + dd.y * dd.y);
+                    x = nx;
+                    y = ny;
+                    z = nz;
+                    if (dl > 0.0) {
+                        // geodesic step of length |d| along d_theta e_theta + d_phi e_phi
+                        double sd, cd;
+                        sincos(dl, &sd, &cd);
+                        const double kk = sd / dl;
+                        const double tx = dd.x * nz * cp - dd.y * sp;
+                        const double ty = dd.x * nz * sp + dd.y * cp;
+                        const double tz = -dd.x * rg.s;
+                        x = cd * nx + kk * tx;
+                        y = cd * ny + kk * ty;
+                        z = cd * nz + kk * tz;
+                    }
+                }
+                int64_t c = ang2pix(a.Nc, x, y, z);
+                // a non-finite target yields NaN outputs; keep its index inside the grid
+                c = (c < 0 || c >= 12 * a.Nc * a.Nc) ? 0 : c;
+                scp[wid][lane] = c;
+            }
+            stx[wid][lane] = x;
+            sty[wid][lane] = y;
+            stz[wid][lane] = z;
+        }
+        __syncwarp();
+        const int npt = a.count - tile * 32 < 32 ? (int)(a.count - tile * 32) : 32;
+        if constexpr (K <= GROUP) {
+            // three targets at a time, one per group of GROUP lanes (lanes 30, 31 idle)
+            const int g = lane / GROUP, l = lane - g * GROUP, base = g * GROUP;
+            for (int q0 = 0; q0 < npt; q0 += 3) {
+                const int q = q0 + g;
+                const bool has = g < 3 && q < npt;
+                double tx = 0.0, ty = 0.0, tz = 0.0;
+                int64_t c = 0;
+                if (has) {
+                    tx = stx[wid][q];
+                    ty = sty[wid][q];
+                    tz = stz[wid][q];
+                    c = scp[wid][q];
+                }
+                const int32_t sl = has ? __ldg(a.slot + c) : 0;
+                double cv = 0.0, yv = 0.0;
+                bool win = false;
+                if (has && l < K) {
+                    const int32_t m = __ldg(a.members + c * K + l);
+                    if (m >= 0) {
+                        double mx, my, mz;
+                        pix2vec(a.N, m, mx, my, mz);
+                        const double dx = tx - mx, dy = ty - my, dz = tz - mz;
+                        const double t = dx * dx + dy * dy + dz * dz;
+                        win = t > a.tab.t_max;
+                        cv = table_eval<double>(a.tab, t);
+                        yv = __ldg(a.map + m);
+                    }
+                }
+                // z_c = L^-1 c, z_y = L^-1 y: lane l of the group accumulates row l
+                const double *Lr = a.linv + (int64_t)sl * (K * (K + 1) / 2);
+                double zc = 0.0, zy = 0.0;
+#pragma unroll
+                for (int j = 0; j < K; ++j) {
+                    const double cj = __shfl_sync(FULL, cv, base + j);
+                    const double yj = __shfl_sync(FULL, yv, base + j);
+                    if (has && l < K && l >= j) {
+                        const double e = __ldg(Lr + col_start(K, j) + l - j);
+                        zc = fma(e, cj, zc);
+                        zy = fma(e, yj, zy);
+                    }
+                }
+                const double v = zc * zy, qv = zc * zc;
+                double vs = 0.0, qs = 0.0;
+#pragma unroll
+                for (int m = 0; m < K; ++m) {  // group sums, in member order
+                    vs += __shfl_sync(FULL, v, base + m);
+                    qs += __shfl_sync(FULL, qv, base + m);
+                }
+                const unsigned wb = __ballot_sync(FULL, win);
+                if (has && l == 0) {
+                    const bool any_win = ((wb >> base) & ((1u << GROUP) - 1u)) != 0;
+                    finish_point(a, tile * 32 + q, sl, vs, qs, any_win, n_win, n_nug, n_fail);
+                }
+            }
+        } else {
+            // one target at a time; lanes own members l and l + 32.  Consecutive
+            // targets in one coarse pixel reuse the members' positions and data.
+            int64_t prev = -1;
+            double m0x = 0.0, m0y = 0.0, m0z = 0.0, y0 = 0.0, m1x = 0.0, m1y = 0.0, m1z = 0.0, y1 = 0.0;
+            bool v0 = false, v1 = false;
+            for (int q = 0; q < npt; ++q) {
+                const double tx = stx[wid][q], ty = sty[wid][q], tz = stz[wid][q];
+                const int64_t c = scp[wid][q];
+                const int32_t sl = __ldg(a.slot + c);
+                if (c != prev) {
+                    prev = c;
+                    const int32_t *mem = a.members + c * K;
+                    v0 = false;
+                    v1 = false;
+                    y0 = 0.0;
+                    y1 = 0.0;
+                    if (lane < K) {
+                        const int32_t m = __ldg(mem + lane);
+                        if (m >= 0) {
+                            pix2vec(a.N, m, m0x, m0y, m0z);
+                            y0 = __ldg(a.map + m);
+                            v0 = true;
+                        }
+                    }
+                    if (lane + 32 < K) {
+                        const int32_t m = __ldg(mem + lane + 32);
+                        if (m >= 0) {
+                            pix2vec(a.N, m, m1x, m1y, m1z);
+                            y1 = __ldg(a.map + m);
+                            v1 = true;
+                        }
+                    }
+                }
+                double c0 = 0.0, c1 = 0.0;
+                bool win = false;
+                if (v0) {
+                    const double dx = tx - m0x, dy = ty - m0y, dz = tz - m0z;
+                    const double t = dx * dx + dy * dy + dz * dz;
+                    win |= t > a.tab.t_max;
+                    c0 = table_eval<double>(a.tab, t);
+                }
+                if (v1) {
+                    const double dx = tx - m1x, dy = ty - m1y, dz = tz - m1z;
+                    const double t = dx * dx + dy * dy + dz * dz;
+                    win |= t > a.tab.t_max;
+                    c1 = table_eval<double>(a.tab, t);
+                }
+                // z_c = L^-1 c, z_y = L^-1 y: lane l accumulates rows l and l + 32
+                const double *Lr = a.linv + (int64_t)sl * (K * (K + 1) / 2);
+                double zc0 = 0.0, zy0 = 0.0, zc1 = 0.0, zy1 = 0.0;
+#pragma unroll
+                for (int j = 0; j < K; ++j) {
+                    const double cj = j < 32 ? __shfl_sync(FULL, c0, j) : __shfl_sync(FULL, c1, j - 32);
+                    const double yj = j < 32 ? __shfl_sync(FULL, y0, j) : __shfl_sync(FULL, y1, j - 32);
+                    if (lane < K && lane >= j) {
+                        const double e = __ldg(Lr + col_start(K, j) + lane - j);
+                        zc0 = fma(e, cj, zc0);
+                        zy0 = fma(e, yj, zy0);
+                    }
+                    if (lane + 32 < K && lane + 32 >= j) {
+                        const double e = __ldg(Lr + col_start(K, j) + lane + 32 - j);
+                        zc1 = fma(e, cj, zc1);
+                        zy1 = fma(e, yj, zy1);
+                    }
+                }
+                double v = zc0 * zy0 + zc1 * zy1, qc = zc0 * zc0 + zc1 * zc1;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    v += __shfl_xor_sync(FULL, v, o);
+                    qc += __shfl_xor_sync(FULL, qc, o);
+                }
+                const bool any_win = __any_sync(FULL, win);
+                if (lane == 0) finish_point(a, tile * 32 + q, sl, v, qc, any_win, n_win, n_nug, n_fail);
+            }
+        }
+        __syncwarp();
+    }
+    if (lane == 0 && a.counters) {
+        if (n_win) atomicAdd(a.counters + CNT_WINDOW, n_win);
+        if (n_nug) atomicAdd(a.counters + CNT_NUGGET, n_nug);
+        if (n_fail) atomicAdd(a.counters + CNT_FAILED, n_fail);
+    }
+}
+
+}  // namespace paper
+}  // namespace flints
+
+using namespace flints;
+using namespace flints::paper;
+
+struct flints_paper_s {
+    int device;
+    int64_t nside, nside_c, nslot;
+    int y, K, lmax, n;
+    double t_max, h, inv_h, xi0, max_pair_t;
+    int64_t nugget_slots, failed_slots;
+    double *d_cl, *d_f, *d_g, *d_fm, *d_gm;
+    Coef64 *d_c64;
+    float4 *d_c32;
+    int32_t *d_members, *d_slot;
+    int *d_steps, *d_scratch;
+    double *d_linv;
+    unsigned long long *d_counters, *d_maxt;
+    int64_t points;
+};
+
+static thread_local char g_perr[512] = "no error";
+
+static int pfail(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_perr, sizeof g_perr, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+static int pcuda(cudaError_t e, const char *what) {
+    return pfail(e == cudaErrorMemoryAllocation ? FLINTS_ENOMEM : FLINTS_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+static void paper_release(flints_paper_s *p) {
+    cudaFree(p->d_cl);
+    cudaFree(p->d_f);
+    cudaFree(p->d_g);
+    cudaFree(p->d_fm);
+    cudaFree(p->d_gm);
+    cudaFree(p->d_c64);
+    cudaFree(p->d_c32);
+    cudaFree(p->d_members);
+    cudaFree(p->d_slot);
+    cudaFree(p->d_steps);
+    cudaFree(p->d_scratch);
+    cudaFree(p->d_linv);
+    cudaFree(p->d_counters);
+    cudaFree(p->d_maxt);
+}
+
+// interval count of the xi table on [0, t_max]: the cubic Hermite error bound
+// h^4/384 max|f4| below 1e-11 (f4 bounded through the fourth derivatives of
+// P_l at 1), a power of two in [64, 65536]
+static int table_intervals(const double *cl, int lmax, double t_max) {
+    double x0 = 0.0, b4num = 0.0;
+    for (int l = 0; l <= lmax; ++l) {
+        const double ld = (double)l;
+        const double a = (2.0 * ld + 1.0) / (4.0 * PI) * std::fabs(cl[l]);
+        x0 += a;
+        if (l >= 4) b4num += a * ((ld - 3) * (ld - 2) * (ld - 1) * ld * (ld + 1) * (ld + 2) * (ld + 3) * (ld + 4) / 384.0);
+    }
+    const double b4 = x0 > 0 ? b4num / 16.0 / x0 : 0.0;
+    if (!(b4 > 0)) return 64;
+    const double h = std::pow(384.0 * 1e-11 / b4, 0.25);
+    const double want = std::ceil(std::log2(t_max / h));
+    return want > 16 ? 65536 : (want < 6 ? 64 : (1 << (int)want));
+}
+
+extern "C" {
+
+const char *flints_paper_last_error(void) { return g_perr; }
+
+int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double *cl, int y, int precision,
+                      void *stream) {
+    if (!out) return pfail(FLINTS_EINVAL, "flints_paper_plan: out is NULL");
+    *out = nullptr;
+    if (y != 1 && y != 2) return pfail(FLINTS_EINVAL, "flints_paper_plan: level y must be 1 or 2 (got %d)", y);
+    const int k = 1 << (y - 1);
+    if (nside < 1 || nside > 8192 || nside % k != 0)
+        return pfail(FLINTS_EINVAL, "flints_paper_plan: nside %lld must be in [1, 8192] and divisible by %d",
+                     (long long)nside, k);
+    if (lmax < 0 || lmax > 16384) return pfail(FLINTS_EINVAL, "flints_paper_plan: lmax %d outside [0, 16384]", lmax);
+    if (!cl) return pfail(FLINTS_EINVAL, "flints_paper_plan: cl is NULL");
+    if (precision != FLINTS_FP64)
+        return pfail(FLINTS_EINVAL, "flints_paper_plan: the tabulated-inverse path is FP64 (FLINTS_FP64)");
+    for (int l = 0; l <= lmax; ++l)
+        if (!std::isfinite(cl[l])) return pfail(FLINTS_EINVAL, "flints_paper_plan: non-finite cl at l = %d", l);
+    cudaStream_t st = (cudaStream_t)stream;
+    flints_paper_s *p = new flints_paper_s();
+    std::memset(p, 0, sizeof *p);
+    cudaGetDevice(&p->device);
+    p->nside = nside;
+    p->nside_c = nside / k;
+    p->y = y;
+    p->K = 9 * k * k;
+    p->lmax = lmax;
+    p->nslot = slot_count(p->nside_c);
+    const double Dc = 7.0 / (double)p->nside_c;
+    p->t_max = Dc * Dc < 4.0 ? Dc * Dc : 4.0;  // 4: the chord^2 of antipodal points
+    p->n = table_intervals(cl, lmax, p->t_max);
+    p->h = p->t_max / p->n;
+    p->inv_h = p->n / p->t_max;
+    const int64_t npc = 12 * p->nside_c * p->nside_c;
+    const size_t nn = (size_t)p->n + 1;
+    cudaError_t e;
+    auto bail = [&](cudaError_t err, const char *what) {
+        paper_release(p);
+        delete p;
+        return pcuda(err, what);
+    };
+#define PALLOC(ptr, bytes)                                   \
+    if ((e = cudaMalloc((void **)&(ptr), (bytes))) != cudaSuccess) return bail(e, "flints_paper_plan: cudaMalloc");
+    PALLOC(p->d_cl, (size_t)(lmax + 1) * sizeof(double));
+    PALLOC(p->d_f, nn * sizeof(double));
+    PALLOC(p->d_g, nn * sizeof(double));
+    PALLOC(p->d_fm, nn * sizeof(double));
+    PALLOC(p->d_gm, nn * sizeof(double));
+    PALLOC(p->d_c64, (size_t)p->n * sizeof(Coef64));
+    PALLOC(p->d_c32, (size_t)p->n * 2 * sizeof(float4));
+    PALLOC(p->d_members, (size_t)npc * p->K * sizeof(int32_t));
+    PALLOC(p->d_slot, (size_t)npc * sizeof(int32_t));
+    PALLOC(p->d_steps, (size_t)p->nslot * sizeof(int));
+    PALLOC(p->d_scratch, 4 * sizeof(int));
+    PALLOC(p->d_linv, (size_t)p->nslot * (p->K * (p->K + 1) / 2) * sizeof(double));
+    PALLOC(p->d_counters, CNT_N * sizeof(unsigned long long));
+    PALLOC(p->d_maxt, sizeof(unsigned long long));
+#undef PALLOC
+    if ((e = cudaMemcpyAsync(p->d_cl, cl, (size_t)(lmax + 1) * sizeof(double), cudaMemcpyHostToDevice, st)) !=
+        cudaSuccess)
+        return bail(e, "flints_paper_plan: copy cl");
+    if ((e = cudaMemsetAsync(p->d_fm, 0, nn * sizeof(double), st)) != cudaSuccess) return bail(e, "memset");
+    if ((e = cudaMemsetAsync(p->d_gm, 0, nn * sizeof(double), st)) != cudaSuccess) return bail(e, "memset");
+    if ((e = cudaMemsetAsync(p->d_scratch, 0, 4 * sizeof(int), st)) != cudaSuccess) return bail(e, "memset");
+    if ((e = cudaMemsetAsync(p->d_counters, 0, CNT_N * sizeof(unsigned long long), st)) != cudaSuccess)
+        return bail(e, "memset");
+    if ((e = cudaMemsetAsync(p->d_maxt, 0, sizeof(unsigned long long), st)) != cudaSuccess) return bail(e, "memset");
+    if ((e = launch_xi_table(0, lmax, p->d_cl, nullptr, p->t_max, p->n, p->d_f, p->d_g, p->d_fm, p->d_gm, st)) !=
+        cudaSuccess)
+        return bail(e, "flints_paper_plan: xi table kernel");
+    double xi0 = 0.0;
+    if ((e = cudaMemcpyAsync(&xi0, p->d_f, sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return bail(e, "flints_paper_plan: read xi(0)");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return bail(e, "flints_paper_plan: xi table");
+    if (!(xi0 > 0.0) || !std::isfinite(xi0)) {
+        paper_release(p);
+        delete p;
+        return pfail(FLINTS_EINVAL, "flints_paper_plan: xi(0) = %g is not positive", xi0);
+    }
+    p->xi0 = xi0;
+    if ((e = finish_table(p->d_f, p->d_g, p->n, p->h, xi0, p->d_c64, p->d_c32, st)) != cudaSuccess)
+        return bail(e, "flints_paper_plan: table coefficients");
+    stencil_kernel<<<(unsigned)((npc + 127) / 128), 128, 0, st>>>(p->nside_c, k, p->K, p->d_members, p->d_slot,
+                                                                 p->d_scratch + 2);
+    if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "flints_paper_plan: stencil kernel");
+    LinvArgs sa{};
+    sa.Nc = p->nside_c;
+    sa.N = nside;
+    sa.nslot = p->nslot;
+    sa.K = p->K;
+    sa.members = p->d_members;
+    sa.tab.c64 = p->d_c64;
+    sa.tab.c32 = p->d_c32;
+    sa.tab.t_max = p->t_max;
+    sa.tab.inv_h = p->inv_h;
+    sa.tab.inv_h_hi = (float)p->inv_h;
+    sa.tab.inv_h_lo = (float)(p->inv_h - (double)sa.tab.inv_h_hi);
+    sa.tab.n = p->n;
+    sa.linv = p->d_linv;
+    sa.slot_steps = p->d_steps;
+    sa.max_t = p->d_maxt;
+    sa.counts = p->d_scratch;
+    const int64_t grid = p->nslot < 152 * 16 ? p->nslot : 152 * 16;
+    linv_kernel<<<(unsigned)grid, SINV_THREADS, 0, st>>>(sa);
+    if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "flints_paper_plan: L^-1 kernel");
+    int scratch[4] = {0, 0, 0, 0};
+    unsigned long long maxt = 0;
+    if ((e = cudaMemcpyAsync(scratch, p->d_scratch, sizeof scratch, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return bail(e, "flints_paper_plan: read counts");
+    if ((e = cudaMemcpyAsync(&maxt, p->d_maxt, sizeof maxt, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return bail(e, "flints_paper_plan: read chord bound");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return bail(e, "flints_paper_plan: tabulation");
+    double mt;
+    std::memcpy(&mt, &maxt, sizeof mt);
+    p->max_pair_t = mt;
+    p->nugget_slots = scratch[0];
+    p->failed_slots = scratch[1];
+    if (scratch[2] != 0) {
+        paper_release(p);
+        delete p;
+        return pfail(FLINTS_EINVAL, "flints_paper_plan: %d coarse pixels with an inconsistent neighbour set", scratch[2]);
+    }
+    if (mt > p->t_max) {
+        paper_release(p);
+        delete p;
+        return pfail(FLINTS_EINVAL, "flints_paper_plan: stencil chord^2 %g exceeds the table domain %g", mt, p->t_max);
+    }
+    *out = p;
+    return FLINTS_OK;
+}
+
+void flints_paper_free(flints_paper_t p) {
+    if (!p) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != p->device) cudaSetDevice(p->device);
+    paper_release(p);
+    if (cur != p->device) cudaSetDevice(cur);
+    delete p;
+}
+
+static int paper_run(flints_paper_t p, int64_t nside_tgt, int64_t first, int64_t count, const double *map,
+                     const double *defl, double *out, double *var, uint8_t *status, void *stream) {
+    if (!p) return pfail(FLINTS_EINVAL, "plan is NULL");
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != p->device) return pfail(FLINTS_EINVAL, "plan was created on device %d, current device is %d", p->device, cur);
+    if (nside_tgt < 0 || nside_tgt > 16384) return pfail(FLINTS_EINVAL, "nside_out %lld outside [1, 16384]", (long long)nside_tgt);
+    const int64_t nt = nside_tgt > 0 ? nside_tgt : p->nside;
+    const int64_t npix = 12 * nt * nt;
+    if (first < 0 || count < 0 || first > npix || count > npix - first)
+        return pfail(FLINTS_EINVAL, "target range [%lld, %lld) outside [0, %lld)", (long long)first,
+                     (long long)(first + count), (long long)npix);
+    if (count == 0) return FLINTS_OK;
+    if (!map || !out) return pfail(FLINTS_EINVAL, "map and out must not be NULL");
+    if (nside_tgt == 0 && !defl) return pfail(FLINTS_EINVAL, "defl is NULL");
+    if (((uintptr_t)defl & 15u) || (((uintptr_t)map | (uintptr_t)out | (uintptr_t)var) & 7u))
+        return pfail(FLINTS_EINVAL, "defl must be 16-byte aligned, map, out and var 8-byte aligned");
+    ApplyArgs a{};
+    a.N = p->nside;
+    a.Nc = p->nside_c;
+    a.first = first;
+    a.count = count;
+    a.nside_tgt = nside_tgt;
+    a.map = map;
+    a.defl = defl;
+    a.out = out;
+    a.var = var;
+    a.status = status;
+    a.members = p->d_members;
+    a.slot = p->d_slot;
+    a.linv = p->d_linv;
+    a.slot_steps = p->d_steps;
+    a.tab.c64 = p->d_c64;
+    a.tab.c32 = p->d_c32;
+    a.tab.t_max = p->t_max;
+    a.tab.inv_h = p->inv_h;
+    a.tab.n = p->n;
+    a.xi0 = p->xi0;
+    a.counters = p->d_counters;
+    const int64_t tiles = (count + 31) / 32;
+    const int64_t want = (tiles + APPLY_WARPS - 1) / APPLY_WARPS;
+    const int64_t cap = (int64_t)device_sm_count() * 16;
+    const unsigned grid = (unsigned)(want < cap ? want : cap);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (p->K == 9)
+        apply_kernel<9><<<grid, APPLY_WARPS * 32, 0, st>>>(a);
+    else
+        apply_kernel<36><<<grid, APPLY_WARPS * 32, 0, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return pcuda(e, "paper apply kernel launch");
+    p->points += count;
+    return FLINTS_OK;
+}
+
+int flints_paper_lens(flints_paper_t p, int64_t first, int64_t count, const double *map, const double *defl,
+                      double *out, double *var, uint8_t *status, void *stream) {
+    return paper_run(p, 0, first, count, map, defl, out, var, status, stream);
+}
+
+int flints_paper_supersample(flints_paper_t p, int64_t nside_out, int64_t first, int64_t count, const double *map,
+                             double *out, double *var, uint8_t *status, void *stream) {
+    if (nside_out < 1) return pfail(FLINTS_EINVAL, "nside_out must be positive");
+    return paper_run(p, nside_out, first, count, map, nullptr, out, var, status, stream);
+}
+
+int flints_paper_get_info(flints_paper_t p, flints_paper_info *info, void *stream) {
+    if (!p || !info) return pfail(FLINTS_EINVAL, "plan and info must not be NULL");
+    unsigned long long c[CNT_N];
+    cudaError_t e = cudaMemcpyAsync(c, p->d_counters, sizeof c, cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return pcuda(e, "flints_paper_get_info");
+    info->nside = p->nside;
+    info->nside_coarse = p->nside_c;
+    info->y = p->y;
+    info->K = p->K;
+    info->slots = p->nslot;
+    info->t_max = p->t_max;
+    info->n_intervals = p->n;
+    info->xi0 = p->xi0;
+    info->table_bytes = (int64_t)p->nslot * (p->K * (p->K + 1) / 2) * 8 +
+                        12 * p->nside_c * p->nside_c * (int64_t)(p->K + 1) * 4;
+    info->max_pair_t = p->max_pair_t;
+    info->nugget_slots = p->nugget_slots;
+    info->failed_slots = p->failed_slots;
+    info->points = p->points;
+    info->window = (int64_t)c[CNT_WINDOW];
+    return FLINTS_OK;
+}
+
+int flints_paper_tables(flints_paper_t p, int32_t *members, int32_t *slot, double *linv, void *stream) {
+    if (!p) return pfail(FLINTS_EINVAL, "plan is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t npc = 12 * p->nside_c * p->nside_c;
+    cudaError_t e = cudaSuccess;
+    if (members)
+        e = cudaMemcpyAsync(members, p->d_members, (size_t)npc * p->K * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && slot)
+        e = cudaMemcpyAsync(slot, p->d_slot, (size_t)npc * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && linv)
+        e = cudaMemcpyAsync(linv, p->d_linv, (size_t)p->nslot * (p->K * (p->K + 1) / 2) * sizeof(double),
+                            cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return pcuda(e, "flints_paper_tables");
+    return FLINTS_OK;
+}
+
+}  // extern "C"

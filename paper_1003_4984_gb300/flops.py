@@ -80,3 +80,12 @@ def augmented_flops(K: int, mixed: bool) -> float:
     phases = 24 * DF_MUL + 14 * DF_ADD + DF_SPECIAL
     entries = 4 * DF_MUL + 4 * DF_ADD
     return chol + solve + P * (chord + 2 * table + phases + entries) + K * (2 * table + phases + entries)
+
+
+def paper_fp64_flops(K: int) -> float:
+    """FP64 flops per target of the tabulated-inverse route (spin 0): the K
+    covariances to the target (chord^2: 3 subtractions, 3 products, 2 additions;
+    cubic table evaluation: 2 for the abscissa, 3 multiply-adds), z_c = L^-1 c
+    and z_y = L^-1 y (K (K + 1) / 2 multiply-adds each), value z_c . z_y and
+    variance z_c . z_c (2K multiply-adds)."""
+    return K * (8 + 2 + 6) + 2 * K * (K + 1) + 2 * 2 * K

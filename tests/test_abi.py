@@ -45,6 +45,18 @@ def test_binding_loads_and_reports_errors_without_gpu(lib_path):
     assert rc == 1 and b"K must be" in lib.flints_last_error()
 
 
+def test_paper_plan_validates_arguments_without_gpu(lib_path):
+    lib = api.load_library()
+    h = ctypes.c_void_p()
+    cl = (ctypes.c_double * 33)(*([0.0, 0.0] + [1.0] * 31))
+    for args, msg in [((16, 32, cl, 3, 0), b"level y"), ((15, 32, cl, 2, 0), b"divisible"),
+                      ((16, 32, cl, 1, 1), b"FP64"), ((16, 32, None, 1, 0), b"cl is NULL"),
+                      ((16384, 32, cl, 1, 0), b"nside")]:
+        rc = lib.flints_paper_plan(ctypes.byref(h), *args, None)
+        assert rc == 1 and not h.value and msg in lib.flints_paper_last_error(), (args, lib.flints_paper_last_error())
+    assert lib.flints_paper_lens(None, 0, 1, None, None, None, None, None, None) == 1
+
+
 def test_product_path_refuses_without_library(tmp_path):
     with pytest.raises(api.FlintsError):
         api.load_library.__wrapped__(str(tmp_path / "missing.so")) if hasattr(api.load_library, "__wrapped__") else \

@@ -99,3 +99,81 @@ def test_inverse_route_matches_solve_and_exact_benchmark(y, tol):
         assert 0.85 < np.mean(r) < 1.15
     else:  # the 1.49e-8 nugget bounds the predicted variance from below
         assert 0.5 < np.mean(r) < 1.15
+
+
+def _chord_signature(nside, members):
+    """Sorted pairwise chords of a stencil: invariant under rotations and reflections."""
+    X = hp.pix2vec(nside, members)
+    d = np.linalg.norm(X[:, None] - X[None], axis=-1)
+    return np.sort(d[np.triu_indices(members.size, 1)])
+
+
+@pytest.mark.parametrize("n_c,y", [(1, 1), (2, 1), (4, 1), (8, 1), (16, 1), (4, 2), (8, 2)])
+def test_class_representatives_are_congruent(n_c, y):
+    # the symmetry classes of S^-1 tabulation (Sec. 2.4): every coarse pixel's stencil
+    # maps member by member onto its representative's, the representatives lie in
+    # the northern hemisphere's first quarter (or first pixel of a belt ring), and
+    # stencils of one class have the same pairwise chords (a congruence invariant
+    # computed without the class map)
+    nside = n_c << (y - 1)
+    cen = np.arange(hp.npix(n_c))
+    rep, mirror, dphi = fc.class_representative(n_c, cen)
+    ring, j = hp.pix2ring(n_c, rep)
+    assert np.all(ring <= 2 * n_c) and np.all(j < np.maximum(hp.ring_info(n_c, ring)[5], 1))
+    assert np.array_equal(rep[rep], rep)  # a representative represents itself
+    idx = fc.stencil(nside, hp.pix2vec(n_c, cen), y)
+    ridx = fc.stencil(nside, hp.pix2vec(n_c, rep), y)
+    for c in cen:
+        m, r = idx[c][idx[c] >= 0], ridx[c][ridx[c] >= 0]
+        assert m.size == r.size
+        U = fc.to_class_frame(hp.pix2vec(nside, m), mirror[c], dphi[c])
+        d = np.linalg.norm(U[:, None] - hp.pix2vec(nside, r)[None], axis=-1)
+        assert np.max(np.min(d, axis=1)) < 1e-12 and np.unique(np.argmin(d, axis=1)).size == m.size
+        assert np.max(np.abs(_chord_signature(nside, m) - _chord_signature(nside, r))) < 1e-12
+    # class count: rings 1 .. min(Nc + 2, 2 Nc) by quarter-ring positions, one per deeper belt ring
+    n_cls = sum(min(i, n_c) for i in range(1, min(n_c + 2, 2 * n_c) + 1)) + max(0, n_c - 2)
+    assert np.unique(rep).size == n_cls
+
+
+@pytest.mark.parametrize("nside,lmax,y,tol_inv", [(8, 16, 1, 1e-11), (16, 32, 2, 1e-7), (2, 12, 2, 1e-11)])
+def test_class_route_matches_per_target_routes(nside, lmax, y, tol_inv):
+    # L^-1 tabulated from the class representative's geometry gives the Cholesky
+    # solve on each target's own stencil to rounding (1e-10), and the literal
+    # S^-1 = L^-T L^-1 route to that route's own error (an explicit inverse loses
+    # a factor cond(S) ~ 1e8 at y = 2)
+    cl = wl.cl_tt(lmax, 0.7 * lmax)
+    t_max, n = fc.paper_grid_rule(cl, nside, y)
+    tab, x0 = xi.spin0_table(cl, t_max, n)
+    m = sht.synth_map(nside, lmax, wl.draw_alm(cl, 3))
+    pix = np.arange(hp.npix(nside))
+    defl = wl.random_deflection(pix.size, 4, rms=0.5 * math.sqrt(4 * math.pi / hp.npix(nside)))
+    v, s2, idx, tv = fc.paper_lens(nside, y, m, defl, pix, tab, x0)
+    vc, s2c, idxc, _ = fc.paper_lens(nside, y, m, defl, pix, tab, x0, classes=True)
+    assert np.array_equal(idx, idxc)
+    assert np.max(np.abs(vc - v)) <= tol_inv * np.std(m)
+    assert np.max(np.abs(s2c - s2)) <= tol_inv * x0
+    cnt = np.sum(idx >= 0, axis=1)
+    for k in np.unique(cnt):
+        rows = np.nonzero(cnt == k)[0]
+        st = np.stack([r[r >= 0] for r in idx[rows]])
+        ve, se, _ = kr.estimate(nside, 0, m, tv[rows], st, tab, x0)
+        assert np.max(np.abs(vc[rows] - ve)) <= 1e-10 * np.std(m)
+        assert np.max(np.abs(s2c[rows] - se)) <= 1e-10 * x0
+
+
+@pytest.mark.parametrize("n_c,y", [(1, 1), (4, 1), (8, 1), (4, 2)])
+def test_member_order_is_kept_by_the_symmetries(n_c, y):
+    # in the ordering rule, every stencil of a class lists its members so that the
+    # chord matrices coincide (what lets one tabulated factor serve the class)
+    nside = n_c << (y - 1)
+    cen = np.arange(hp.npix(n_c))
+    rep = fc.class_representative(n_c, cen)[0]
+    ordered = fc.stencil_ordered(nside, y, cen)
+    for c in cen:
+        m, r = ordered[c], ordered[rep[c]]
+        assert np.array_equal(np.sort(m), np.sort(fc.stencil(nside, hp.pix2vec(n_c, np.array([c])), y)[0][
+            fc.stencil(nside, hp.pix2vec(n_c, np.array([c])), y)[0] >= 0]))
+        X, Y = hp.pix2vec(nside, m), hp.pix2vec(nside, r)
+        T = np.sum((X[:, None] - X[None]) ** 2, axis=-1)
+        Tr = np.sum((Y[:, None] - Y[None]) ** 2, axis=-1)
+        assert np.max(np.abs(T - Tr)) <= 1e-13 * np.max(Tr)
