@@ -55,9 +55,34 @@ def parse():
                          "spin1: a deflection field (spin 1) lensed at Nside 4096; paper: the 9/36-pixel stencil "
                          "with tabulated inverses (lensing at 4096, supersampling 2048 -> 4096)")
     ap.add_argument("--duration", type=float, default=45.0, help="c5: seconds of Poisson arrivals")
-    ap.add_argument("--profile-case", choices=["mixed", "fp64"], default=None,
-                    help="small case for ncu: two launches on 2^18 targets of the resident c3 map")
+    ap.add_argument("--profile-case", choices=["mixed", "fp64", "paper1", "paper2"], default=None,
+                    help="small case for ncu: two launches on 2^18 targets of the resident c3 map (mixed, "
+                         "fp64), or on 2^20 targets of the tabulated-inverse route at level 1 or 2")
     return ap.parse_args()
+
+
+def run_profile_case_paper(y: int):
+    """Two launches of the tabulated-inverse apply kernel (Nside 4096 lensing, level y)
+    on 2^20 targets of a ring band (the second one is the one to capture)."""
+    import torch
+
+    import paper_1003_4984_gb300 as fl
+
+    fl.load_library()
+    dev = torch.device("cuda", 0)
+    g = torch.Generator(device=dev)
+    g.manual_seed(8)
+    n = 1 << 20
+    nside = 4096
+    m = torch.randn(12 * nside * nside, dtype=torch.float64, device=dev, generator=g)
+    defl = torch.randn((n, 2), dtype=torch.float64, device=dev, generator=g) * wl.DEFLECTION_RMS
+    plan = fl.PaperPlan(nside, wl.cl_tt(4096, 2500.0), y)
+    for _ in range(2):
+        out, var = plan.lens(m, defl, first=100_000_000, count=n)
+    torch.cuda.synchronize()
+    info = plan.info()
+    assert info["window"] == 0 and info["failed_slots"] == 0, info
+    print(json.dumps({"profile_case": f"paper_y{y}", "points": n, "K": info["K"]}))
 
 
 def run_profile_case(precision: str):
@@ -66,6 +91,8 @@ def run_profile_case(precision: str):
 
     import paper_1003_4984_gb300 as fl
 
+    if precision.startswith("paper"):
+        return run_profile_case_paper(int(precision[-1]))
     fl.load_library()
     cl, bb = W.cl()
     dev = torch.device("cuda", 0)

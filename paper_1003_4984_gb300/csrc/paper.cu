@@ -56,6 +56,25 @@ __device__ __forceinline__ void pix2vec(int64_t N, int64_t p, double &x, double 
     z = rg.z;
 }
 
+// unit vectors of all pixels of the map grid, (x, y, z, 0) per pixel: built once
+// per plan so that the per-target kernel gathers member positions instead of
+// recomputing them (FP64 sin/cos/sqrt are scarce on this part)
+__global__ void pixvec_kernel(int64_t N, double2 *pv) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= 12 * N * N) return;
+    double x, y, z;
+    pix2vec(N, p, x, y, z);
+    pv[2 * p] = make_double2(x, y);
+    pv[2 * p + 1] = make_double2(z, 0.0);
+}
+
+__device__ __forceinline__ void member_vec(const double2 *pv, int64_t m, double &x, double &y, double &z) {
+    const double2 a = __ldg(pv + 2 * m), b = __ldg(pv + 2 * m + 1);
+    x = a.x;
+    y = a.y;
+    z = b.x;
+}
+
 // RING pixel at Nside N containing the unit vector (x, y, z) (the ring scheme's
 // point location of Gorski et al. 2005: belt by the two edge-line families,
 // caps by the distance to the pole, sin(theta) taken from x, y near the poles)
@@ -216,6 +235,7 @@ struct ApplyArgs {
     uint8_t *status;
     const int32_t *members, *slot;
     const double *linv;
+    const double2 *pv;             // [12 N^2][2]: (x, y), (z, 0) of every map pixel
     const int *slot_steps;
     TableDev tab;
     double xi0;
@@ -250,6 +270,7 @@ template <int K>
 __global__ void __launch_bounds__(APPLY_WARPS * 32) apply_kernel(ApplyArgs a) {
     __shared__ double stx[APPLY_WARPS][32], sty[APPLY_WARPS][32], stz[APPLY_WARPS][32];
     __shared__ int64_t scp[APPLY_WARPS][32];
+    __shared__ double sc[APPLY_WARPS][K > GROUP ? K : 1], sy[APPLY_WARPS][K > GROUP ? K : 1];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t ntiles = (a.count + 31) / 32;
     unsigned long long n_win = 0, n_nug = 0, n_fail = 0;
@@ -320,7 +341,7 @@ __global__ void __launch_bounds__(APPLY_WARPS * 32) apply_kernel(ApplyArgs a) {
                     const int32_t m = __ldg(a.members + c * K + l);
                     if (m >= 0) {
                         double mx, my, mz;
-                        pix2vec(a.N, m, mx, my, mz);
+                        member_vec(a.pv, m, mx, my, mz);
                         const double dx = tx - mx, dy = ty - my, dz = tz - mz;
                         const double t = dx * dx + dy * dy + dz * dz;
                         win = t > a.tab.t_max;
@@ -341,12 +362,15 @@ __global__ void __launch_bounds__(APPLY_WARPS * 32) apply_kernel(ApplyArgs a) {
                         zy = fma(e, yj, zy);
                     }
                 }
-                const double v = zc * zy, qv = zc * zc;
-                double vs = 0.0, qs = 0.0;
+                // group sums over lanes 0 .. GROUP-1: fold 8-9 onto 0-1, then halve 8 -> 1
+                double vs = zc * zy, qs = zc * zc;
 #pragma unroll
-                for (int m = 0; m < K; ++m) {  // group sums, in member order
-                    vs += __shfl_sync(FULL, v, base + m);
-                    qs += __shfl_sync(FULL, qv, base + m);
+                for (int o = 8; o >= 1; o >>= 1) {
+                    const double tv = __shfl_sync(FULL, vs, lane + o), tq = __shfl_sync(FULL, qs, lane + o);
+                    if (l < o && l + o < GROUP) {
+                        vs += tv;
+                        qs += tq;
+                    }
                 }
                 const unsigned wb = __ballot_sync(FULL, win);
                 if (has && l == 0) {
@@ -374,7 +398,7 @@ __global__ void __launch_bounds__(APPLY_WARPS * 32) apply_kernel(ApplyArgs a) {
                     if (lane < K) {
                         const int32_t m = __ldg(mem + lane);
                         if (m >= 0) {
-                            pix2vec(a.N, m, m0x, m0y, m0z);
+                            member_vec(a.pv, m, m0x, m0y, m0z);
                             y0 = __ldg(a.map + m);
                             v0 = true;
                         }
@@ -382,7 +406,7 @@ __global__ void __launch_bounds__(APPLY_WARPS * 32) apply_kernel(ApplyArgs a) {
                     if (lane + 32 < K) {
                         const int32_t m = __ldg(mem + lane + 32);
                         if (m >= 0) {
-                            pix2vec(a.N, m, m1x, m1y, m1z);
+                            member_vec(a.pv, m, m1x, m1y, m1z);
                             y1 = __ldg(a.map + m);
                             v1 = true;
                         }
@@ -402,25 +426,48 @@ __global__ void __launch_bounds__(APPLY_WARPS * 32) apply_kernel(ApplyArgs a) {
                     win |= t > a.tab.t_max;
                     c1 = table_eval<double>(a.tab, t);
                 }
-                // z_c = L^-1 c, z_y = L^-1 y: lane l accumulates rows l and l + 32
+                // z_c = L^-1 c, z_y = L^-1 y.  c and y go to the warp's shared slots;
+                // rows 0..31: lane l accumulates row l (columns j <= l < 32);
+                // rows 32..35: lane l takes row 32 + (l & 3) on columns (l >> 2) + 8t,
+                // the eight partial sums of a row joined by shuffles.
+                static_assert(K == 36, "the split of rows 32 .. K-1 is laid out for K = 36");
                 const double *Lr = a.linv + (int64_t)sl * (K * (K + 1) / 2);
+                __syncwarp();
+                sc[wid][lane] = c0;
+                sy[wid][lane] = y0;
+                if (lane < K - 32) {
+                    sc[wid][32 + lane] = c1;
+                    sy[wid][32 + lane] = y1;
+                }
+                __syncwarp();
                 double zc0 = 0.0, zy0 = 0.0, zc1 = 0.0, zy1 = 0.0;
 #pragma unroll
-                for (int j = 0; j < K; ++j) {
-                    const double cj = j < 32 ? __shfl_sync(FULL, c0, j) : __shfl_sync(FULL, c1, j - 32);
-                    const double yj = j < 32 ? __shfl_sync(FULL, y0, j) : __shfl_sync(FULL, y1, j - 32);
-                    if (lane < K && lane >= j) {
+                for (int j = 0; j < 32; ++j) {
+                    if (lane >= j) {
                         const double e = __ldg(Lr + col_start(K, j) + lane - j);
-                        zc0 = fma(e, cj, zc0);
-                        zy0 = fma(e, yj, zy0);
-                    }
-                    if (lane + 32 < K && lane + 32 >= j) {
-                        const double e = __ldg(Lr + col_start(K, j) + lane + 32 - j);
-                        zc1 = fma(e, cj, zc1);
-                        zy1 = fma(e, yj, zy1);
+                        zc0 = fma(e, sc[wid][j], zc0);
+                        zy0 = fma(e, sy[wid][j], zy0);
                     }
                 }
-                double v = zc0 * zy0 + zc1 * zy1, qc = zc0 * zc0 + zc1 * zc1;
+                {
+                    const int r = 32 + (lane & 3), g = lane >> 2;
+#pragma unroll
+                    for (int t = 0; t < 5; ++t) {
+                        const int j = g + 8 * t;
+                        if (j <= r) {
+                            const double e = __ldg(Lr + col_start(K, j) + r - j);
+                            zc1 = fma(e, sc[wid][j], zc1);
+                            zy1 = fma(e, sy[wid][j], zy1);
+                        }
+                    }
+#pragma unroll
+                    for (int o = 4; o < 32; o <<= 1) {
+                        zc1 += __shfl_xor_sync(FULL, zc1, o);
+                        zy1 += __shfl_xor_sync(FULL, zy1, o);
+                    }
+                }
+                const bool own1 = lane < K - 32;  // lanes 0..3 count rows 32..35 once
+                double v = zc0 * zy0 + (own1 ? zc1 * zy1 : 0.0), qc = zc0 * zc0 + (own1 ? zc1 * zc1 : 0.0);
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
                     v += __shfl_xor_sync(FULL, v, o);
@@ -457,6 +504,7 @@ struct flints_paper_s {
     int32_t *d_members, *d_slot;
     int *d_steps, *d_scratch;
     double *d_linv;
+    double2 *d_pv;
     unsigned long long *d_counters, *d_maxt;
     int64_t points;
 };
@@ -488,6 +536,7 @@ static void paper_release(flints_paper_s *p) {
     cudaFree(p->d_steps);
     cudaFree(p->d_scratch);
     cudaFree(p->d_linv);
+    cudaFree(p->d_pv);
     cudaFree(p->d_counters);
     cudaFree(p->d_maxt);
 }
@@ -566,6 +615,7 @@ int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double
     PALLOC(p->d_steps, (size_t)p->nslot * sizeof(int));
     PALLOC(p->d_scratch, 4 * sizeof(int));
     PALLOC(p->d_linv, (size_t)p->nslot * (p->K * (p->K + 1) / 2) * sizeof(double));
+    PALLOC(p->d_pv, (size_t)12 * nside * nside * 2 * sizeof(double2));
     PALLOC(p->d_counters, CNT_N * sizeof(unsigned long long));
     PALLOC(p->d_maxt, sizeof(unsigned long long));
 #undef PALLOC
@@ -593,6 +643,8 @@ int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double
     p->xi0 = xi0;
     if ((e = finish_table(p->d_f, p->d_g, p->n, p->h, xi0, p->d_c64, p->d_c32, st)) != cudaSuccess)
         return bail(e, "flints_paper_plan: table coefficients");
+    pixvec_kernel<<<(unsigned)((12 * nside * nside + 255) / 256), 256, 0, st>>>(nside, p->d_pv);
+    if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "flints_paper_plan: pixel vector kernel");
     stencil_kernel<<<(unsigned)((npc + 127) / 128), 128, 0, st>>>(p->nside_c, k, p->K, p->d_members, p->d_slot,
                                                                  p->d_scratch + 2);
     if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "flints_paper_plan: stencil kernel");
@@ -683,6 +735,7 @@ static int paper_run(flints_paper_t p, int64_t nside_tgt, int64_t first, int64_t
     a.members = p->d_members;
     a.slot = p->d_slot;
     a.linv = p->d_linv;
+    a.pv = p->d_pv;
     a.slot_steps = p->d_steps;
     a.tab.c64 = p->d_c64;
     a.tab.c32 = p->d_c32;
@@ -732,7 +785,7 @@ int flints_paper_get_info(flints_paper_t p, flints_paper_info *info, void *strea
     info->n_intervals = p->n;
     info->xi0 = p->xi0;
     info->table_bytes = (int64_t)p->nslot * (p->K * (p->K + 1) / 2) * 8 +
-                        12 * p->nside_c * p->nside_c * (int64_t)(p->K + 1) * 4;
+                        12 * p->nside_c * p->nside_c * (int64_t)(p->K + 1) * 4 + 12 * p->nside * p->nside * 32;
     info->max_pair_t = p->max_pair_t;
     info->nugget_slots = p->nugget_slots;
     info->failed_slots = p->failed_slots;
