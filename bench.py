@@ -217,15 +217,12 @@ def run_ours(args):
     import paper_1003_4984_gb300 as fl
     from paper_1003_4984_gb300 import flops
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
+    from paper_1003_4984_gb300 import ranks
 
+    world, rank, local = ranks.rank_env()
+    if world > 1:
         torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+    dist = ranks.init("nccl")
     # the CPU baseline runs first, before any GPU work (spawned pool)
     aug = args.workload == "c3aug"
     flags = fl.FLINTS_SPIN2_AUGMENTED if aug else 0
@@ -236,7 +233,7 @@ def run_ours(args):
     cl, bb = W.cl()
     stream = torch.cuda.current_stream(dev)
     g = torch.Generator(device=dev)
-    g.manual_seed(1234 + rank)
+    g.manual_seed(ranks.seed(rank, 1234))
     qu = torch.randn((W.npix, 2), dtype=torch.float64, device=dev, generator=g)
     nb = W.npix // BATCH  # 12 batches per sky
     defl = torch.randn((nb * BATCH, 2), dtype=torch.float64, device=dev, generator=g) * (wl.DEFLECTION_RMS / math.sqrt(2))
@@ -245,15 +242,14 @@ def run_ours(args):
     plans = {p: fl.Plan(W.nside, cl, bb, spin=2, K=W.K, precision=p, flags=flags) for p in ("mixed", "fp64")}
 
     def step(plan, i):
-        b = (rank * 5 + i) % nb
+        b = ranks.batch_index(rank, i, nb)
         plan.lens(qu, defl[b * BATCH:(b + 1) * BATCH], out, var, first=b * BATCH, count=BATCH)
 
     def timed(plan, steps, warmup):
         for i in range(warmup):
             step(plan, i)
         torch.cuda.synchronize(dev)
-        if dist:
-            dist.barrier()
+        ranks.barrier(dist)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
         ev[0].record(stream)
         for i in range(steps):
@@ -261,11 +257,7 @@ def run_ours(args):
             ev[i + 1].record(stream)
         torch.cuda.synchronize(dev)
         per = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
-        total = ev[0].elapsed_time(ev[steps])
-        if dist:
-            t = torch.tensor([total], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total = float(t.item())
+        total = ranks.max_over_ranks(ev[0].elapsed_time(ev[steps]), dist, dev)
         return total, per
 
     plans["mixed"].reset_stats()
@@ -287,7 +279,7 @@ def run_ours(args):
     slice_len = (W.npix + nb - 1) // nb
 
     def e2e_step(i):
-        b = (rank * 5 + i) % nb
+        b = ranks.batch_index(rank, i, nb)
         s0 = b * slice_len
         s1 = min(W.npix, s0 + slice_len)
         qu[s0:s1].copy_(h_map[s0:s1], non_blocking=True)  # this step's share of the map upload
@@ -299,19 +291,14 @@ def run_ours(args):
 
     e2e_step(0)
     torch.cuda.synchronize(dev)
-    if dist:
-        dist.barrier()
+    ranks.barrier(dist)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for i in range(nb_e2e):
         e2e_step(1 + i)
     e1.record(stream)
     torch.cuda.synchronize(dev)
-    e2e_ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = ranks.max_over_ranks(e0.elapsed_time(e1), dist, dev)
     h2d = slice_len * 16 + BATCH * 16
     d2h = BATCH * 16 + BATCH * 8
 
@@ -320,8 +307,8 @@ def run_ours(args):
         return
     n_gpus = world
     ms_step = total_ms / args.steps
-    value = n_gpus * BATCH * args.steps / (total_ms / 1e3)
-    fp_value = n_gpus * BATCH * len(fp_per) / (fp_total / 1e3)
+    value = ranks.job_rate(BATCH * args.steps, total_ms / 1e3, n_gpus)
+    fp_value = ranks.job_rate(BATCH * len(fp_per), fp_total / 1e3, n_gpus)
     kern_ms = statistics.mean(per)
     fl32 = flops.augmented_flops(W.K, True) if aug else flops.mixed_fp32_flops(W.K, 2)
     achieved = fl32 * BATCH / (kern_ms / 1e3) / 1e12
@@ -339,7 +326,7 @@ def run_ours(args):
                  "steps": len(fp_per)},
         "mixed_over_fp64": value / fp_value,
         "mixed_stats": st,
-        "e2e": {"value": n_gpus * BATCH * nb_e2e / (e2e_ms / 1e3), "unit": "pts/s",
+        "e2e": {"value": ranks.job_rate(BATCH * nb_e2e, e2e_ms / 1e3, n_gpus), "unit": "pts/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": flops.FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / flops.FP32_PEAK_TFLOPS,
