@@ -55,13 +55,13 @@ def parse():
                          "spin1: a deflection field (spin 1) lensed at Nside 4096; paper: the 9/36-pixel stencil "
                          "with tabulated inverses (lensing at 4096, supersampling 2048 -> 4096)")
     ap.add_argument("--duration", type=float, default=45.0, help="c5: seconds of Poisson arrivals")
-    ap.add_argument("--profile-case", choices=["mixed", "fp64", "paper1", "paper2"], default=None,
+    ap.add_argument("--profile-case", choices=["mixed", "fp64", "paper1", "paper2", "paper1m", "paper2m"], default=None,
                     help="small case for ncu: two launches on 2^18 targets of the resident c3 map (mixed, "
-                         "fp64), or on 2^20 targets of the tabulated-inverse route at level 1 or 2")
+                         "fp64), or on 2^20 targets of the tabulated-inverse route at level 1 or 2 (m: mixed)")
     return ap.parse_args()
 
 
-def run_profile_case_paper(y: int):
+def run_profile_case_paper(y: int, precision: str = "fp64"):
     """Two launches of the tabulated-inverse apply kernel (Nside 4096 lensing, level y)
     on 2^20 targets of a ring band (the second one is the one to capture)."""
     import torch
@@ -76,13 +76,13 @@ def run_profile_case_paper(y: int):
     nside = 4096
     m = torch.randn(12 * nside * nside, dtype=torch.float64, device=dev, generator=g)
     defl = torch.randn((n, 2), dtype=torch.float64, device=dev, generator=g) * wl.DEFLECTION_RMS
-    plan = fl.PaperPlan(nside, wl.cl_tt(4096, 2500.0), y)
+    plan = fl.PaperPlan(nside, wl.cl_tt(4096, 2500.0), y, precision)
     for _ in range(2):
         out, var = plan.lens(m, defl, first=100_000_000, count=n)
     torch.cuda.synchronize()
     info = plan.info()
     assert info["window"] == 0 and info["failed_slots"] == 0, info
-    print(json.dumps({"profile_case": f"paper_y{y}", "points": n, "K": info["K"]}))
+    print(json.dumps({"profile_case": f"paper_y{y}_{precision}", "points": n, "K": info["K"]}))
 
 
 def run_profile_case(precision: str):
@@ -92,7 +92,7 @@ def run_profile_case(precision: str):
     import paper_1003_4984_gb300 as fl
 
     if precision.startswith("paper"):
-        return run_profile_case_paper(int(precision[-1]))
+        return run_profile_case_paper(int(precision[5]), "mixed" if precision.endswith("m") else "fp64")
     fl.load_library()
     cl, bb = W.cl()
     dev = torch.device("cuda", 0)
@@ -746,11 +746,11 @@ def run_pipeline(args):
 def run_paper(args):
     """The paper's own route (Secs. 2.3-2.5): the pixel-centred stencil of 9 (y = 1)
     and 36 (y = 2) pixels with L^-1 (the factor of S^-1) tabulated per symmetry
-    class of central pixels, two triangular matrix-vector products per target
-    (FP64).  Lensing of an
-    Nside 4096, lmax 4096 temperature map (Table 2's configuration) and
-    supersampling Nside 2048 -> 4096 (Table 1's), 2^24 targets per step.  The
-    plan time (stencils and L^-1 tabulation) is Table 2's "init" column."""
+    class of central pixels, two triangular matrix-vector products per target,
+    in FP64 and in double-float (mixed).  Lensing of an Nside 4096, lmax 4096
+    temperature map (Table 2's configuration) and supersampling Nside 2048 ->
+    4096 (Table 1's), 2^24 targets per step.  The plan time (stencils and L^-1
+    tabulation) is Table 2's "init" column."""
     import torch
 
     import paper_1003_4984_gb300 as fl
@@ -779,59 +779,70 @@ def run_paper(args):
             if task == "lens":
                 defl = torch.randn((BATCH, 2), dtype=torch.float64, device=dev, generator=g) * wl.DEFLECTION_RMS
             for y in (1, 2):
-                torch.cuda.synchronize(dev)
-                t0 = time.perf_counter()
-                plan = fl.PaperPlan(nside, cl, y)
-                torch.cuda.synchronize(dev)
-                plan_s = time.perf_counter() - t0
-                info = plan.info()
+                for precision in ("fp64", "mixed"):
+                    torch.cuda.synchronize(dev)
+                    t0 = time.perf_counter()
+                    plan = fl.PaperPlan(nside, cl, y, precision)
+                    torch.cuda.synchronize(dev)
+                    plan_s = time.perf_counter() - t0
+                    info = plan.info()
 
-                def step(i):
-                    first = (i % nb) * BATCH
-                    if task == "lens":
-                        plan.lens(m, defl, first=first, count=BATCH, out=out, var=var)
+                    def step(i):
+                        first = (i % nb) * BATCH
+                        if task == "lens":
+                            plan.lens(m, defl, first=first, count=BATCH, out=out, var=var)
+                        else:
+                            plan.supersample(m, nout, first=first, count=BATCH, out=out, var=var)
+
+                    for i in range(warm):
+                        step(i)
+                    torch.cuda.synchronize(dev)
+                    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+                    ev[0].record(stream)
+                    for i in range(steps):
+                        step(warm + i)
+                        ev[i + 1].record(stream)
+                    torch.cuda.synchronize(dev)
+                    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+                    K = info["K"]
+                    sec = statistics.mean(per) / 1e3
+                    arm = {
+                        "value": BATCH * steps / (ev[0].elapsed_time(ev[steps]) / 1e3), "unit": "pts/s",
+                        "ms_per_step": statistics.mean(per), "K": K, "plan_s": plan_s, "slots": info["slots"],
+                        "table_bytes": info["table_bytes"], "window": info["window"],
+                        "nugget_slots": info["nugget_slots"], "failed_slots": info["failed_slots"],
+                        "predicted_precision": math.sqrt(float(var.mean()) / info["xi0"])}
+                    if precision == "fp64":
+                        arm["fp64_tflops"] = flops.paper_fp64_flops(K) * BATCH / sec / 1e12
                     else:
-                        plan.supersample(m, nout, first=first, count=BATCH, out=out, var=var)
-
-                for i in range(warm):
-                    step(i)
-                torch.cuda.synchronize(dev)
-                ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
-                ev[0].record(stream)
-                for i in range(steps):
-                    step(warm + i)
-                    ev[i + 1].record(stream)
-                torch.cuda.synchronize(dev)
-                per = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
-                K = info["K"]
-                res[f"{task}_y{y}"] = {
-                    "value": BATCH * steps / (ev[0].elapsed_time(ev[steps]) / 1e3), "unit": "pts/s",
-                    "ms_per_step": statistics.mean(per), "K": K, "plan_s": plan_s, "slots": info["slots"],
-                    "table_bytes": info["table_bytes"], "window": info["window"],
-                    "nugget_slots": info["nugget_slots"], "failed_slots": info["failed_slots"],
-                    "predicted_precision": math.sqrt(float(var.mean()) / info["xi0"]),
-                    "fp64_tflops": flops.paper_fp64_flops(K) * BATCH / (statistics.mean(per) / 1e3) / 1e12}
-                plan.close()
+                        arm["fp32_tflops"] = flops.paper_mixed_fp32_flops(K) * BATCH / sec / 1e12
+                    res[f"{task}_y{y}_{precision}"] = arm
+                    plan.close()
+                    torch.cuda.empty_cache()
             del m, defl
             torch.cuda.empty_cache()
-    head = res["lens_y1"]
-    achieved = head["fp64_tflops"]
+    head = res["lens_y1_mixed"]
+    ratios = {f"{t}_y{y}": res[f"{t}_y{y}_mixed"]["value"] / res[f"{t}_y{y}_fp64"]["value"]
+              for t in ("lens", "supersample") for y in (1, 2)}
+    achieved = head["fp32_tflops"]
     print(json.dumps({
-        "metric": "lensed pts/s, Nside 4096 T, lmax 4096, paper stencil (9 px) with tabulated inverses, FP64",
+        "metric": "lensed pts/s, Nside 4096 T, lmax 4096, paper stencil (9 px) with tabulated inverses, mixed vs FP64",
         "value": head["value"], "unit": "pts/s", "n_gpus": 1, "steps": steps, "warmup": warm,
         "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic white-noise maps, Gaussian deflections of 2.5 arcmin rms",
+        "dtype": "f64 in/out; double-float chords, lookups and triangular products",
+        "data": "synthetic white-noise maps, Gaussian deflections of 2.5 arcmin rms",
         "config": {"workload": "tabulated inverse: lensing Nside 4096 (y = 1, 2) and supersampling "
-                               "Nside 2048 -> 4096 (y = 1, 2), lmax 4096 (damping l = 2500)",
+                               "Nside 2048 -> 4096 (y = 1, 2), lmax 4096 (damping l = 2500), FP64 and mixed",
                    "batch_points": BATCH, "l2": "inputs larger than L2 (1.6 GB map, 268 MB of deflections)"},
-        "arms": res,
+        "fp64": {"value": res["lens_y1_fp64"]["value"], "ms_per_step": res["lens_y1_fp64"]["ms_per_step"]},
+        "mixed_over_fp64": ratios, "arms": res,
         "paper_tables": "Table 2 (Nside 4096, 9 neighbours): init 16 min, interpolation 22 min per map; "
                         "Table 1 (2048 -> 4096): 3.3 min (9) / 19 min (36), precision 3e-3 / 3e-4; serial "
                         "Xeon E5410",
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": flops.FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / flops.FP64_PEAK_TFLOPS, "traffic": None,
-                     "kernel": "paper::apply_kernel<9>", "peak_kind": "nominal FP64",
-                     "flops_per_point": flops.paper_fp64_flops(9)},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": flops.FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / flops.FP32_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "paper::apply_kernel_df<9>", "peak_kind": "FP32 from unit counts and 2070 MHz",
+                     "flops_per_point": flops.paper_mixed_fp32_flops(9)},
         "clocks": clk.summary(0), "gpu_launches": steps}))
 
 

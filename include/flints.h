@@ -298,7 +298,7 @@ void flints_free(flints_plan_t plan);
 /* The paper's estimator route with tabulated inverses (Secs. 2.3-2.5): the
  * pixel-centred stencil at level y and the inverse covariance computed once per
  * class of central pixels, then two triangular matrix-vector products per
- * target.  Spin 0, FP64.
+ * target.  Spin 0, FP64 or mixed precision.
  *
  * Stencil (Sec. 2.3, neighbours() with the NESTED hierarchy): the target's
  * pixel at Nside_c = Nside / 2^(y-1) and the pixels of that grid sharing a
@@ -320,8 +320,10 @@ void flints_free(flints_plan_t plan);
  * S^-1 and in half its memory.
  *
  * flints_paper_plan: y = 1 or 2; nside in [1, 8192] and divisible by
- *   2^(y-1); cl HOST [lmax+1] (C_l, l = 0..lmax); precision FLINTS_FP64 (the
- *   only one).  Builds on `stream` the xi table on [0, min((7 / Nside_c)^2, 4)] (interval
+ *   2^(y-1); cl HOST [lmax+1] (C_l, l = 0..lmax); precision FLINTS_FP64, or
+ *   FLINTS_MIXED: the per-target chords, correlation lookups and triangular
+ *   products in double-float on the FP32 pipe (target position and location
+ *   FP64; the L^-1 blocks computed in FP64 and kept as double-float).  Builds on `stream` the xi table on [0, min((7 / Nside_c)^2, 4)] (interval
  *   count by the rule of flints_plan), the stencil table and the L^-1 blocks,
  *   then synchronises `stream`.  Device memory: 12 Nside_c^2 (K + 1) int32 and
  *   slots * K (K + 1) / 2 doubles (flints_paper_get_info reports the total).  Errors:
@@ -343,7 +345,8 @@ void flints_free(flints_plan_t plan);
  *   each coarse pixel (slot DEVICE [12 Nside_c^2] int32) and the L^-1 blocks
  *   (linv DEVICE [slots][K (K + 1) / 2] doubles: column j, rows j .. K-1, from
  *   offset j K - j (j - 1) / 2; zero past the member count) into caller
- *   buffers; any may be NULL.
+ *   buffers; any may be NULL.  Mixed plans keep only double-float blocks:
+ *   linv must be NULL for them (FLINTS_EINVAL otherwise).
  * flints_paper_free: releases the plan (NULL is allowed). */
 typedef struct flints_paper_s *flints_paper_t;
 typedef struct flints_paper_info {
@@ -360,6 +363,7 @@ typedef struct flints_paper_info {
     int64_t failed_slots;   /* classes without a positive-definite factor */
     int64_t points;         /* targets processed so far */
     int64_t window;         /* targets with a chord beyond the table domain */
+    int precision;          /* FLINTS_FP64 or FLINTS_MIXED */
 } flints_paper_info;
 int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double *cl, int y, int precision,
                       void *stream);

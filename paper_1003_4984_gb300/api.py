@@ -47,7 +47,7 @@ class _PaperInfo(ctypes.Structure):
                 ("slots", ctypes.c_int64), ("t_max", ctypes.c_double), ("n_intervals", ctypes.c_int),
                 ("xi0", ctypes.c_double), ("table_bytes", ctypes.c_int64), ("max_pair_t", ctypes.c_double),
                 ("nugget_slots", ctypes.c_int64), ("failed_slots", ctypes.c_int64), ("points", ctypes.c_int64),
-                ("window", ctypes.c_int64)]
+                ("window", ctypes.c_int64), ("precision", ctypes.c_int)]
 
 
 class LaunchCfg(ctypes.Structure):
@@ -473,15 +473,17 @@ class PaperPlan:
     """The paper's stencil with tabulated inverses (flints_paper_*): level-y
     pixel-centred stencil of 9 * 4^(y-1) pixels, L^-1 (the factor of S^-1)
     tabulated per symmetry class of central pixels, two triangular
-    matrix-vector products per target (spin 0, FP64)."""
+    matrix-vector products per target (spin 0; precision "fp64" or "mixed",
+    the per-target arithmetic in double-float on the FP32 pipe)."""
 
-    def __init__(self, nside: int, cl, y: int = 1, stream=None):
+    def __init__(self, nside: int, cl, y: int = 1, precision: str = "fp64", stream=None):
         lib = load_library()
         cl = np.ascontiguousarray(cl, dtype=np.float64)
-        self.nside, self.y = int(nside), int(y)
+        self.nside, self.y, self.precision = int(nside), int(y), precision
+        prec = {"fp64": FLINTS_FP64, "mixed": FLINTS_MIXED}[precision]
         h = ctypes.c_void_p()
         rc = lib.flints_paper_plan(ctypes.byref(h), self.nside, cl.size - 1,
-                                   cl.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self.y, FLINTS_FP64,
+                                   cl.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self.y, prec,
                                    _stream(stream))
         if rc != 0:
             raise FlintsError(f"flints error {rc}: {lib.flints_paper_last_error().decode()}")
@@ -541,7 +543,9 @@ class PaperPlan:
         npc = 12 * self.nside_coarse * self.nside_coarse
         mem = torch.empty((npc, self.K), dtype=torch.int32, device="cuda")
         slot = torch.empty(npc, dtype=torch.int32, device="cuda")
-        linv = torch.empty((self.slots, self.K * (self.K + 1) // 2), dtype=torch.float64, device="cuda")
+        linv = None
+        if self.precision == "fp64":  # mixed plans keep only double-float blocks
+            linv = torch.empty((self.slots, self.K * (self.K + 1) // 2), dtype=torch.float64, device="cuda")
         self._raise(load_library().flints_paper_tables(self._h, _ptr(mem), _ptr(slot), _ptr(linv), _stream(stream)))
         return mem, slot, linv
 

@@ -235,7 +235,9 @@ struct ApplyArgs {
     uint8_t *status;
     const int32_t *members, *slot;
     const double *linv;
-    const double2 *pv;             // [12 N^2][2]: (x, y), (z, 0) of every map pixel
+    const double2 *pv;             // [12 N^2][2]: (x, y), (z, 0) of every map pixel (FP64 plans)
+    const float4 *pvf;             // [12 N^2][2]: double-float (x, y), (z, 0) (mixed plans)
+    const float2 *linvf;           // double-float L^-1 blocks (mixed plans)
     const int *slot_steps;
     TableDev tab;
     double xi0;
@@ -266,11 +268,54 @@ __device__ __forceinline__ void finish_point(const ApplyArgs &a, int64_t p, int3
     n_fail += steps < 0;
 }
 
+// Target p (displaced pixel first + p, or the pixel centre of the nside_tgt
+// grid) and the coarse pixel holding it; p >= count leaves the defaults.
+__device__ __forceinline__ void target_of(const ApplyArgs &a, int64_t p, double &x, double &y, double &z,
+                                          int64_t &c) {
+    if (p >= a.count) return;
+    const int64_t pix = a.first + p;
+    if (a.nside_tgt > 0) {
+        pix2vec(a.nside_tgt, pix, x, y, z);
+    } else {
+        int64_t i, j;
+        pix_ring(a.N, pix, i, j);
+        const Ring rg = ring_of(a.N, i);
+        double sp, cp;
+        sincospi(((double)j + rg.f) / (2.0 * (double)rg.nq), &sp, &cp);
+        const double nx = rg.s * cp, ny = rg.s * sp, nz = rg.z;
+        const double2 dd = __ldg(reinterpret_cast<const double2 *>(a.defl) + p);
+        const double dl = sqrt(dd.x * dd.x + dd.y * dd.y);
+        x = nx;
+        y = ny;
+        z = nz;
+        if (dl > 0.0) {
+            // geodesic step of length |d| along d_theta e_theta + d_phi e_phi
+            double sd, cd;
+            sincos(dl, &sd, &cd);
+            const double kk = sd / dl;
+            const double tx = dd.x * nz * cp - dd.y * sp;
+            const double ty = dd.x * nz * sp + dd.y * cp;
+            const double tz = -dd.x * rg.s;
+            x = cd * nx + kk * tx;
+            y = cd * ny + kk * ty;
+            z = cd * nz + kk * tz;
+        }
+    }
+    c = ang2pix(a.Nc, x, y, z);
+    // a non-finite target yields NaN outputs; keep its index inside the grid
+    c = (c < 0 || c >= 12 * a.Nc * a.Nc) ? 0 : c;
+}
+
 template <int K>
 __global__ void __launch_bounds__(APPLY_WARPS * 32) apply_kernel(ApplyArgs a) {
     __shared__ double stx[APPLY_WARPS][32], sty[APPLY_WARPS][32], stz[APPLY_WARPS][32];
     __shared__ int64_t scp[APPLY_WARPS][32];
     __shared__ double sc[APPLY_WARPS][K > GROUP ? K : 1], sy[APPLY_WARPS][K > GROUP ? K : 1];
+    // per target of the tile: w . y, w . c, class and window flag, finished one
+    // target per lane after the tile
+    __shared__ double rv[APPLY_WARPS][32], rq[APPLY_WARPS][32];
+    __shared__ int32_t rsl[APPLY_WARPS][32];
+    __shared__ unsigned char rwin[APPLY_WARPS][32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t ntiles = (a.count + 31) / 32;
     unsigned long long n_win = 0, n_nug = 0, n_fail = 0;
@@ -278,42 +323,10 @@ __global__ void __launch_bounds__(APPLY_WARPS * 32) apply_kernel(ApplyArgs a) {
          tile += (int64_t)gridDim.x * APPLY_WARPS) {
         // ---- lane l: target l of the tile and its coarse pixel
         {
-            const int64_t p = tile * 32 + lane;
             double x = 0.0, y = 0.0, z = 1.0;
-            if (p < a.count) {
-                const int64_t pix = a.first + p;
-                if (a.nside_tgt > 0) {
-                    pix2vec(a.nside_tgt, pix, x, y, z);
-                } else {
-                    int64_t i, j;
-                    pix_ring(a.N, pix, i, j);
-                    const Ring rg = ring_of(a.N, i);
-                    double sp, cp;
-                    sincospi(((double)j + rg.f) / (2.0 * (double)rg.nq), &sp, &cp);
-                    const double nx = rg.s * cp, ny = rg.s * sp, nz = rg.z;
-                    const double2 dd = __ldg(reinterpret_cast<const double2 *>(a.defl) + p);
-                    const double dl = sqrt(dd.x * dd.x + dd.y * dd.y);
-                    x = nx;
-                    y = ny;
-                    z = nz;
-                    if (dl > 0.0) {
-                        // geodesic step of length |d| along d_theta e_theta + d_phi e_phi
-                        double sd, cd;
-                        sincos(dl, &sd, &cd);
-                        const double kk = sd / dl;
-                        const double tx = dd.x * nz * cp - dd.y * sp;
-                        const double ty = dd.x * nz * sp + dd.y * cp;
-                        const double tz = -dd.x * rg.s;
-                        x = cd * nx + kk * tx;
-                        y = cd * ny + kk * ty;
-                        z = cd * nz + kk * tz;
-                    }
-                }
-                int64_t c = ang2pix(a.Nc, x, y, z);
-                // a non-finite target yields NaN outputs; keep its index inside the grid
-                c = (c < 0 || c >= 12 * a.Nc * a.Nc) ? 0 : c;
-                scp[wid][lane] = c;
-            }
+            int64_t c = 0;
+            target_of(a, tile * 32 + lane, x, y, z, c);
+            scp[wid][lane] = c;
             stx[wid][lane] = x;
             sty[wid][lane] = y;
             stz[wid][lane] = z;
@@ -374,8 +387,10 @@ __global__ void __launch_bounds__(APPLY_WARPS * 32) apply_kernel(ApplyArgs a) {
                 }
                 const unsigned wb = __ballot_sync(FULL, win);
                 if (has && l == 0) {
-                    const bool any_win = ((wb >> base) & ((1u << GROUP) - 1u)) != 0;
-                    finish_point(a, tile * 32 + q, sl, vs, qs, any_win, n_win, n_nug, n_fail);
+                    rv[wid][q] = vs;
+                    rq[wid][q] = qs;
+                    rsl[wid][q] = sl;
+                    rwin[wid][q] = ((wb >> base) & ((1u << GROUP) - 1u)) != 0;
                 }
             }
         } else {
@@ -474,15 +489,305 @@ __global__ void __launch_bounds__(APPLY_WARPS * 32) apply_kernel(ApplyArgs a) {
                     qc += __shfl_xor_sync(FULL, qc, o);
                 }
                 const bool any_win = __any_sync(FULL, win);
-                if (lane == 0) finish_point(a, tile * 32 + q, sl, v, qc, any_win, n_win, n_nug, n_fail);
+                if (lane == 0) {
+                    rv[wid][q] = v;
+                    rq[wid][q] = qc;
+                    rsl[wid][q] = sl;
+                    rwin[wid][q] = any_win;
+                }
             }
         }
         __syncwarp();
+        if (lane < npt)
+            finish_point(a, tile * 32 + lane, rsl[wid][lane], rv[wid][lane], rq[wid][lane], rwin[wid][lane] != 0,
+                         n_win, n_nug, n_fail);
+        __syncwarp();
     }
+    // counts of every lane, summed over the warp
+    const unsigned w_win = __reduce_add_sync(FULL, (unsigned)n_win);
+    const unsigned w_nug = __reduce_add_sync(FULL, (unsigned)n_nug);
+    const unsigned w_fail = __reduce_add_sync(FULL, (unsigned)n_fail);
     if (lane == 0 && a.counters) {
-        if (n_win) atomicAdd(a.counters + CNT_WINDOW, n_win);
-        if (n_nug) atomicAdd(a.counters + CNT_NUGGET, n_nug);
-        if (n_fail) atomicAdd(a.counters + CNT_FAILED, n_fail);
+        if (w_win) atomicAdd(a.counters + CNT_WINDOW, (unsigned long long)w_win);
+        if (w_nug) atomicAdd(a.counters + CNT_NUGGET, (unsigned long long)w_nug);
+        if (w_fail) atomicAdd(a.counters + CNT_FAILED, (unsigned long long)w_fail);
+    }
+}
+
+// ------------------------------------------------------- mixed precision
+// The same route with the per-target arithmetic in double-float (pairs of FP32,
+// about 2^-44 relative per operation) on the FP32 pipe: member positions from a
+// double-float pixel table, chords and the correlation lookup in double-float,
+// z_c = L^-1 c and z_y = L^-1 y accumulated from double-float L^-1 blocks; the
+// target position and its coarse pixel stay FP64.  Chords between nearby unit
+// vectors lose the positions' absolute error (2^-48) relative to the chord:
+// about 1e-10 of chord^2 at Nside 4096.
+__global__ void pixvec_df_kernel(int64_t N, float4 *pvf) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= 12 * N * N) return;
+    double x, y, z;
+    pix2vec(N, p, x, y, z);
+    const df dx = df_from(x), dy = df_from(y), dz = df_from(z);
+    pvf[2 * p] = make_float4(dx.hi, dx.lo, dy.hi, dy.lo);
+    pvf[2 * p + 1] = make_float4(dz.hi, dz.lo, 0.0f, 0.0f);
+}
+
+__global__ void to_df_kernel(const double *src, float2 *dst, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const df v = df_from(src[i]);
+    dst[i] = make_float2(v.hi, v.lo);
+}
+
+__device__ __forceinline__ void member_vec_df(const float4 *pvf, int64_t m, df &x, df &y, df &z) {
+    const float4 u = __ldg(pvf + 2 * m), v = __ldg(pvf + 2 * m + 1);
+    x = {u.x, u.y};
+    y = {u.z, u.w};
+    z = {v.x, v.y};
+}
+
+// |t - m|^2 of double-float unit vectors: the differences' high words cancel
+// exactly or leave a two_sum error, and the squares are positive
+__device__ __forceinline__ df chord2_df(df tx, df ty, df tz, df mx, df my, df mz) {
+    const df dx = df_add_fast(tx, df_neg(mx)), dy = df_add_fast(ty, df_neg(my)), dz = df_add_fast(tz, df_neg(mz));
+    return df_add_fast(df_add_fast(df_mul(dx, dx), df_mul(dy, dy)), df_mul(dz, dz));
+}
+
+__device__ __forceinline__ df shfl_df(df v, int src) {
+    return {__shfl_sync(FULL, v.hi, src), __shfl_sync(FULL, v.lo, src)};
+}
+__device__ __forceinline__ df shfl_xor_df(df v, int o) {
+    return {__shfl_xor_sync(FULL, v.hi, o), __shfl_xor_sync(FULL, v.lo, o)};
+}
+__device__ __forceinline__ df ld_df(const float2 *p) {
+    const float2 v = __ldg(p);
+    return {v.x, v.y};
+}
+
+// A double as a double-float pair without FP64 instructions: hi = x with its
+// mantissa truncated to 24 bits (bit operations), lo = the next 29 bits rounded
+// to 24 (integer to float, exact power-of-two scaling), |x - (hi + lo)| <=
+// 2^-47 |x|.  Values below the float normal range become 0, beyond it +-inf;
+// NaN stays NaN.
+__device__ __forceinline__ df split_double(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    const int e = (int)((b >> 52) & 0x7ff);
+    const unsigned long long mant = b & 0xfffffffffffffull;
+    if (e == 0x7ff) return {__uint_as_float(sign | 0x7f800000u | (mant ? 0x400000u : 0u)), 0.0f};
+    const int fe = e - 1023 + 127;
+    if (fe <= 0) return {__uint_as_float(sign), 0.0f};
+    if (fe >= 255) return {__uint_as_float(sign | 0x7f800000u), 0.0f};
+    const float hi = __uint_as_float(sign | ((unsigned)fe << 23) | (unsigned)(mant >> 29));
+    // the low bits' unit 2^(e - 1075), applied in two exact steps when it lies
+    // below the float normal range (fe > 0 keeps le > -52)
+    const int le = e - 1075 + 127;
+    float lo = __uint2float_rn((unsigned)(mant & 0x1fffffffu)) * __uint_as_float((unsigned)(le > 0 ? le : le + 64) << 23);
+    if (le <= 0) lo *= 5.42101086242752217e-20f;  // 2^-64
+    return {hi, __uint_as_float(__float_as_uint(lo) | sign)};
+}
+
+template <int K>
+__global__ void __launch_bounds__(APPLY_WARPS * 32) apply_kernel_df(ApplyArgs a) {
+    __shared__ df stx[APPLY_WARPS][32], sty[APPLY_WARPS][32], stz[APPLY_WARPS][32];
+    __shared__ int64_t scp[APPLY_WARPS][32];
+    __shared__ df sc[APPLY_WARPS][K > GROUP ? K : 1], sy[APPLY_WARPS][K > GROUP ? K : 1];
+    // per target of the tile: w . y, w . c, class and window flag, finished one
+    // target per lane after the tile (the double conversions then cost one
+    // instruction per 32 targets)
+    __shared__ df rv[APPLY_WARPS][32], rq[APPLY_WARPS][32];
+    __shared__ int32_t rsl[APPLY_WARPS][32];
+    __shared__ unsigned char rwin[APPLY_WARPS][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t ntiles = (a.count + 31) / 32;
+    const float tmaxf = (float)a.tab.t_max;
+    unsigned long long n_win = 0, n_nug = 0, n_fail = 0;
+    for (int64_t tile = (int64_t)blockIdx.x * APPLY_WARPS + wid; tile < ntiles;
+         tile += (int64_t)gridDim.x * APPLY_WARPS) {
+        {
+            double x = 0.0, y = 0.0, z = 1.0;
+            int64_t c = 0;
+            target_of(a, tile * 32 + lane, x, y, z, c);
+            scp[wid][lane] = c;
+            stx[wid][lane] = split_double(x);
+            sty[wid][lane] = split_double(y);
+            stz[wid][lane] = split_double(z);
+        }
+        __syncwarp();
+        const int npt = a.count - tile * 32 < 32 ? (int)(a.count - tile * 32) : 32;
+        if constexpr (K <= GROUP) {
+            const int g = lane / GROUP, l = lane - g * GROUP, base = g * GROUP;
+            for (int q0 = 0; q0 < npt; q0 += 3) {
+                const int q = q0 + g;
+                const bool has = g < 3 && q < npt;
+                int64_t c = 0;
+                df tx{0.0f, 0.0f}, ty{0.0f, 0.0f}, tz{1.0f, 0.0f};
+                if (has) {
+                    tx = stx[wid][q];
+                    ty = sty[wid][q];
+                    tz = stz[wid][q];
+                    c = scp[wid][q];
+                }
+                const int32_t sl = has ? __ldg(a.slot + c) : 0;
+                df cv{0.0f, 0.0f}, yv{0.0f, 0.0f};
+                bool win = false;
+                if (has && l < K) {
+                    const int32_t m = __ldg(a.members + c * K + l);
+                    if (m >= 0) {
+                        df mx, my, mz;
+                        member_vec_df(a.pvf, m, mx, my, mz);
+                        const df t = chord2_df(tx, ty, tz, mx, my, mz);
+                        win = t.hi > tmaxf;
+                        cv = table_eval<df>(a.tab, t);
+                        yv = split_double(__ldg(a.map + m));
+                    }
+                }
+                const float2 *Lr = a.linvf + (int64_t)sl * (K * (K + 1) / 2);
+                dfacc zc{0.0f, 0.0f}, zy{0.0f, 0.0f};
+#pragma unroll
+                for (int j = 0; j < K; ++j) {
+                    const df cj = shfl_df(cv, base + j), yj = shfl_df(yv, base + j);
+                    if (has && l < K && l >= j) {
+                        const df e = ld_df(Lr + col_start(K, j) + l - j);
+                        dfacc_add_prod(zc, e, cj);
+                        dfacc_add_prod(zy, e, yj);
+                    }
+                }
+                const df zcv = dfacc_val(zc), zyv = dfacc_val(zy);
+                df vs = df_mul(zcv, zyv), qs = df_mul(zcv, zcv);
+#pragma unroll
+                for (int o = 8; o >= 1; o >>= 1) {
+                    const df tv = shfl_df(vs, lane + o), tq = shfl_df(qs, lane + o);
+                    if (l < o && l + o < GROUP) {
+                        vs = df_add_fast(vs, tv);
+                        qs = df_add_fast(qs, tq);
+                    }
+                }
+                const unsigned wb = __ballot_sync(FULL, win);
+                if (has && l == 0) {
+                    rv[wid][q] = vs;
+                    rq[wid][q] = qs;
+                    rsl[wid][q] = sl;
+                    rwin[wid][q] = ((wb >> base) & ((1u << GROUP) - 1u)) != 0;
+                }
+            }
+        } else {
+            static_assert(K == 36, "the split of rows 32 .. K-1 is laid out for K = 36");
+            int64_t prev = -1;
+            df m0x{0.0f, 0.0f}, m0y{0.0f, 0.0f}, m0z{0.0f, 0.0f}, y0{0.0f, 0.0f};
+            df m1x{0.0f, 0.0f}, m1y{0.0f, 0.0f}, m1z{0.0f, 0.0f}, y1{0.0f, 0.0f};
+            bool v0 = false, v1 = false;
+            for (int q = 0; q < npt; ++q) {
+                const df tx = stx[wid][q], ty = sty[wid][q], tz = stz[wid][q];
+                const int64_t c = scp[wid][q];
+                const int32_t sl = __ldg(a.slot + c);
+                if (c != prev) {
+                    prev = c;
+                    const int32_t *mem = a.members + c * K;
+                    v0 = false;
+                    v1 = false;
+                    y0 = {0.0f, 0.0f};
+                    y1 = {0.0f, 0.0f};
+                    const int32_t mA = __ldg(mem + lane);
+                    if (mA >= 0) {
+                        member_vec_df(a.pvf, mA, m0x, m0y, m0z);
+                        y0 = split_double(__ldg(a.map + mA));
+                        v0 = true;
+                    }
+                    if (lane + 32 < K) {
+                        const int32_t mB = __ldg(mem + lane + 32);
+                        if (mB >= 0) {
+                            member_vec_df(a.pvf, mB, m1x, m1y, m1z);
+                            y1 = split_double(__ldg(a.map + mB));
+                            v1 = true;
+                        }
+                    }
+                }
+                df c0{0.0f, 0.0f}, c1{0.0f, 0.0f};
+                bool win = false;
+                if (v0) {
+                    const df t = chord2_df(tx, ty, tz, m0x, m0y, m0z);
+                    win |= t.hi > tmaxf;
+                    c0 = table_eval<df>(a.tab, t);
+                }
+                if (v1) {
+                    const df t = chord2_df(tx, ty, tz, m1x, m1y, m1z);
+                    win |= t.hi > tmaxf;
+                    c1 = table_eval<df>(a.tab, t);
+                }
+                const float2 *Lr = a.linvf + (int64_t)sl * (K * (K + 1) / 2);
+                __syncwarp();
+                sc[wid][lane] = c0;
+                sy[wid][lane] = y0;
+                if (lane < K - 32) {
+                    sc[wid][32 + lane] = c1;
+                    sy[wid][32 + lane] = y1;
+                }
+                __syncwarp();
+                dfacc zc0{0.0f, 0.0f}, zy0{0.0f, 0.0f}, zc1{0.0f, 0.0f}, zy1{0.0f, 0.0f};
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    if (lane >= j) {
+                        const df e = ld_df(Lr + col_start(K, j) + lane - j);
+                        dfacc_add_prod(zc0, e, sc[wid][j]);
+                        dfacc_add_prod(zy0, e, sy[wid][j]);
+                    }
+                }
+                df zc1v, zy1v;
+                {
+                    const int r = 32 + (lane & 3), g = lane >> 2;
+#pragma unroll
+                    for (int t = 0; t < 5; ++t) {
+                        const int j = g + 8 * t;
+                        if (j <= r) {
+                            const df e = ld_df(Lr + col_start(K, j) + r - j);
+                            dfacc_add_prod(zc1, e, sc[wid][j]);
+                            dfacc_add_prod(zy1, e, sy[wid][j]);
+                        }
+                    }
+                    zc1v = dfacc_val(zc1);
+                    zy1v = dfacc_val(zy1);
+#pragma unroll
+                    for (int o = 4; o < 32; o <<= 1) {
+                        zc1v = df_add_fast(zc1v, shfl_xor_df(zc1v, o));
+                        zy1v = df_add_fast(zy1v, shfl_xor_df(zy1v, o));
+                    }
+                }
+                const df zc0v = dfacc_val(zc0), zy0v = dfacc_val(zy0);
+                const bool own1 = lane < K - 32;  // lanes 0..3 count rows 32..35 once
+                df v = df_mul(zc0v, zy0v), qc = df_mul(zc0v, zc0v);
+                if (own1) {
+                    v = df_add_fast(v, df_mul(zc1v, zy1v));
+                    qc = df_add_fast(qc, df_mul(zc1v, zc1v));
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    v = df_add_fast(v, shfl_xor_df(v, o));
+                    qc = df_add_fast(qc, shfl_xor_df(qc, o));
+                }
+                const bool any_win = __any_sync(FULL, win);
+                if (lane == 0) {
+                    rv[wid][q] = v;
+                    rq[wid][q] = qc;
+                    rsl[wid][q] = sl;
+                    rwin[wid][q] = any_win;
+                }
+            }
+        }
+        __syncwarp();
+        if (lane < npt)
+            finish_point(a, tile * 32 + lane, rsl[wid][lane], df_to(rv[wid][lane]), df_to(rq[wid][lane]),
+                         rwin[wid][lane] != 0, n_win, n_nug, n_fail);
+        __syncwarp();
+    }
+    // counts of every lane, summed over the warp
+    const unsigned w_win = __reduce_add_sync(FULL, (unsigned)n_win);
+    const unsigned w_nug = __reduce_add_sync(FULL, (unsigned)n_nug);
+    const unsigned w_fail = __reduce_add_sync(FULL, (unsigned)n_fail);
+    if (lane == 0 && a.counters) {
+        if (w_win) atomicAdd(a.counters + CNT_WINDOW, (unsigned long long)w_win);
+        if (w_nug) atomicAdd(a.counters + CNT_NUGGET, (unsigned long long)w_nug);
+        if (w_fail) atomicAdd(a.counters + CNT_FAILED, (unsigned long long)w_fail);
     }
 }
 
@@ -505,6 +810,9 @@ struct flints_paper_s {
     int *d_steps, *d_scratch;
     double *d_linv;
     double2 *d_pv;
+    float4 *d_pvf;
+    float2 *d_linvf;
+    int precision;
     unsigned long long *d_counters, *d_maxt;
     int64_t points;
 };
@@ -537,6 +845,8 @@ static void paper_release(flints_paper_s *p) {
     cudaFree(p->d_scratch);
     cudaFree(p->d_linv);
     cudaFree(p->d_pv);
+    cudaFree(p->d_pvf);
+    cudaFree(p->d_linvf);
     cudaFree(p->d_counters);
     cudaFree(p->d_maxt);
 }
@@ -574,8 +884,8 @@ int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double
                      (long long)nside, k);
     if (lmax < 0 || lmax > 16384) return pfail(FLINTS_EINVAL, "flints_paper_plan: lmax %d outside [0, 16384]", lmax);
     if (!cl) return pfail(FLINTS_EINVAL, "flints_paper_plan: cl is NULL");
-    if (precision != FLINTS_FP64)
-        return pfail(FLINTS_EINVAL, "flints_paper_plan: the tabulated-inverse path is FP64 (FLINTS_FP64)");
+    if (precision != FLINTS_FP64 && precision != FLINTS_MIXED)
+        return pfail(FLINTS_EINVAL, "flints_paper_plan: precision must be FLINTS_FP64 or FLINTS_MIXED");
     for (int l = 0; l <= lmax; ++l)
         if (!std::isfinite(cl[l])) return pfail(FLINTS_EINVAL, "flints_paper_plan: non-finite cl at l = %d", l);
     cudaStream_t st = (cudaStream_t)stream;
@@ -587,6 +897,7 @@ int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double
     p->y = y;
     p->K = 9 * k * k;
     p->lmax = lmax;
+    p->precision = precision;
     p->nslot = slot_count(p->nside_c);
     const double Dc = 7.0 / (double)p->nside_c;
     p->t_max = Dc * Dc < 4.0 ? Dc * Dc : 4.0;  // 4: the chord^2 of antipodal points
@@ -615,7 +926,12 @@ int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double
     PALLOC(p->d_steps, (size_t)p->nslot * sizeof(int));
     PALLOC(p->d_scratch, 4 * sizeof(int));
     PALLOC(p->d_linv, (size_t)p->nslot * (p->K * (p->K + 1) / 2) * sizeof(double));
-    PALLOC(p->d_pv, (size_t)12 * nside * nside * 2 * sizeof(double2));
+    if (precision == FLINTS_MIXED) {
+        PALLOC(p->d_pvf, (size_t)12 * nside * nside * 2 * sizeof(float4));
+        PALLOC(p->d_linvf, (size_t)p->nslot * (p->K * (p->K + 1) / 2) * sizeof(float2));
+    } else {
+        PALLOC(p->d_pv, (size_t)12 * nside * nside * 2 * sizeof(double2));
+    }
     PALLOC(p->d_counters, CNT_N * sizeof(unsigned long long));
     PALLOC(p->d_maxt, sizeof(unsigned long long));
 #undef PALLOC
@@ -643,7 +959,10 @@ int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double
     p->xi0 = xi0;
     if ((e = finish_table(p->d_f, p->d_g, p->n, p->h, xi0, p->d_c64, p->d_c32, st)) != cudaSuccess)
         return bail(e, "flints_paper_plan: table coefficients");
-    pixvec_kernel<<<(unsigned)((12 * nside * nside + 255) / 256), 256, 0, st>>>(nside, p->d_pv);
+    if (precision == FLINTS_MIXED)
+        pixvec_df_kernel<<<(unsigned)((12 * nside * nside + 255) / 256), 256, 0, st>>>(nside, p->d_pvf);
+    else
+        pixvec_kernel<<<(unsigned)((12 * nside * nside + 255) / 256), 256, 0, st>>>(nside, p->d_pv);
     if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "flints_paper_plan: pixel vector kernel");
     stencil_kernel<<<(unsigned)((npc + 127) / 128), 128, 0, st>>>(p->nside_c, k, p->K, p->d_members, p->d_slot,
                                                                  p->d_scratch + 2);
@@ -668,6 +987,11 @@ int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double
     const int64_t grid = p->nslot < 152 * 16 ? p->nslot : 152 * 16;
     linv_kernel<<<(unsigned)grid, SINV_THREADS, 0, st>>>(sa);
     if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "flints_paper_plan: L^-1 kernel");
+    if (precision == FLINTS_MIXED) {
+        const int64_t nl = p->nslot * (int64_t)(p->K * (p->K + 1) / 2);
+        to_df_kernel<<<(unsigned)((nl + 255) / 256), 256, 0, st>>>(p->d_linv, p->d_linvf, nl);
+        if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "flints_paper_plan: double-float L^-1");
+    }
     int scratch[4] = {0, 0, 0, 0};
     unsigned long long maxt = 0;
     if ((e = cudaMemcpyAsync(scratch, p->d_scratch, sizeof scratch, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
@@ -689,6 +1013,10 @@ int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double
         paper_release(p);
         delete p;
         return pfail(FLINTS_EINVAL, "flints_paper_plan: stencil chord^2 %g exceeds the table domain %g", mt, p->t_max);
+    }
+    if (precision == FLINTS_MIXED) {  // only the double-float blocks are kept
+        cudaFree(p->d_linv);
+        p->d_linv = nullptr;
     }
     *out = p;
     return FLINTS_OK;
@@ -736,11 +1064,15 @@ static int paper_run(flints_paper_t p, int64_t nside_tgt, int64_t first, int64_t
     a.slot = p->d_slot;
     a.linv = p->d_linv;
     a.pv = p->d_pv;
+    a.pvf = p->d_pvf;
+    a.linvf = p->d_linvf;
     a.slot_steps = p->d_steps;
     a.tab.c64 = p->d_c64;
     a.tab.c32 = p->d_c32;
     a.tab.t_max = p->t_max;
     a.tab.inv_h = p->inv_h;
+    a.tab.inv_h_hi = (float)p->inv_h;
+    a.tab.inv_h_lo = (float)(p->inv_h - (double)a.tab.inv_h_hi);
     a.tab.n = p->n;
     a.xi0 = p->xi0;
     a.counters = p->d_counters;
@@ -749,10 +1081,18 @@ static int paper_run(flints_paper_t p, int64_t nside_tgt, int64_t first, int64_t
     const int64_t cap = (int64_t)device_sm_count() * 16;
     const unsigned grid = (unsigned)(want < cap ? want : cap);
     cudaStream_t st = (cudaStream_t)stream;
-    if (p->K == 9)
-        apply_kernel<9><<<grid, APPLY_WARPS * 32, 0, st>>>(a);
-    else
-        apply_kernel<36><<<grid, APPLY_WARPS * 32, 0, st>>>(a);
+    const bool mixed = p->precision == FLINTS_MIXED;
+    if (p->K == 9) {
+        if (mixed)
+            apply_kernel_df<9><<<grid, APPLY_WARPS * 32, 0, st>>>(a);
+        else
+            apply_kernel<9><<<grid, APPLY_WARPS * 32, 0, st>>>(a);
+    } else {
+        if (mixed)
+            apply_kernel_df<36><<<grid, APPLY_WARPS * 32, 0, st>>>(a);
+        else
+            apply_kernel<36><<<grid, APPLY_WARPS * 32, 0, st>>>(a);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return pcuda(e, "paper apply kernel launch");
     p->points += count;
@@ -786,6 +1126,7 @@ int flints_paper_get_info(flints_paper_t p, flints_paper_info *info, void *strea
     info->xi0 = p->xi0;
     info->table_bytes = (int64_t)p->nslot * (p->K * (p->K + 1) / 2) * 8 +
                         12 * p->nside_c * p->nside_c * (int64_t)(p->K + 1) * 4 + 12 * p->nside * p->nside * 32;
+    info->precision = p->precision;
     info->max_pair_t = p->max_pair_t;
     info->nugget_slots = p->nugget_slots;
     info->failed_slots = p->failed_slots;
@@ -803,6 +1144,8 @@ int flints_paper_tables(flints_paper_t p, int32_t *members, int32_t *slot, doubl
         e = cudaMemcpyAsync(members, p->d_members, (size_t)npc * p->K * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess && slot)
         e = cudaMemcpyAsync(slot, p->d_slot, (size_t)npc * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
+    if (linv && !p->d_linv)
+        return pfail(FLINTS_EINVAL, "flints_paper_tables: mixed plans keep only double-float L^-1 blocks");
     if (e == cudaSuccess && linv)
         e = cudaMemcpyAsync(linv, p->d_linv, (size_t)p->nslot * (p->K * (p->K + 1) / 2) * sizeof(double),
                             cudaMemcpyDeviceToDevice, st);

@@ -89,3 +89,13 @@ def paper_fp64_flops(K: int) -> float:
     and z_y = L^-1 y (K (K + 1) / 2 multiply-adds each), value z_c . z_y and
     variance z_c . z_c (2K multiply-adds)."""
     return K * (8 + 2 + 6) + 2 * K * (K + 1) + 2 * 2 * K
+
+
+def paper_mixed_fp32_flops(K: int) -> float:
+    """FP32 flops per target of the tabulated-inverse route in double-float: K
+    chords (3 differences, 3 squares, 2 sums) and table lookups (a product and
+    three multiply-adds), K (K + 1) multiply-accumulates for z_c and z_y, and
+    the two dots (2K products and sums)."""
+    chord = 3 * DF_ADD + 3 * DF_MUL + 2 * DF_ADD
+    table = DF_MUL + 3 * (DF_MUL + DF_ADD)
+    return K * (chord + table) + K * (K + 1) * DF_MAC + 2 * K * (DF_MUL + DF_ADD)
