@@ -326,7 +326,7 @@ void flints_free(flints_plan_t plan);
  *   FP64; the L^-1 blocks computed in FP64 and kept as double-float).  Builds on `stream` the xi table on [0, min((7 / Nside_c)^2, 4)] (interval
  *   count by the rule of flints_plan), the stencil table and the L^-1 blocks,
  *   then synchronises `stream`.  Device memory: 12 Nside_c^2 (K + 1) int32 and
- *   slots * K (K + 1) / 2 doubles (flints_paper_get_info reports the total).  Errors:
+ *   slots * len doubles (len below; flints_paper_get_info reports the total).  Errors:
  *   FLINTS_EINVAL (arguments; a stencil chord beyond the table domain),
  *   FLINTS_ENOMEM, FLINTS_ECUDA; message in flints_paper_last_error().
  * flints_paper_lens: lensed values at targets first .. first+count-1 (RING
@@ -343,8 +343,13 @@ void flints_free(flints_plan_t plan);
  * flints_paper_tables: copies the stencil table (members DEVICE [12 Nside_c^2]
  *   [K] int32 RING indices at Nside, -1 past the member count), the class of
  *   each coarse pixel (slot DEVICE [12 Nside_c^2] int32) and the L^-1 blocks
- *   (linv DEVICE [slots][K (K + 1) / 2] doubles: column j, rows j .. K-1, from
- *   offset j K - j (j - 1) / 2; zero past the member count) into caller
+ *   (linv DEVICE [slots][len] doubles, zero past the member count; K = 9:
+ *   len = 45, packed by columns: column j, rows j .. 8, from offset
+ *   9 j - j (j - 1) / 2; K = 36: len = 704, the lane-step layout: entry
+ *   32 u + l (u < 17) holds, for p = l / 2 and t = u (l even) or 17 + u (l
+ *   odd), row p column t when t <= p, else row 31 - p column t - p - 1 (zero
+ *   when that column exceeds the row); entry 544 + 32 t + l (t < 5) holds row
+ *   32 + l % 4, column l / 4 + 8 t (zero above the diagonal)) into caller
  *   buffers; any may be NULL.  Mixed plans keep only double-float blocks:
  *   linv must be NULL for them (FLINTS_EINVAL otherwise).
  * flints_paper_free: releases the plan (NULL is allowed). */

@@ -536,8 +536,9 @@ class PaperPlan:
         return out, var
 
     def tables(self, stream=None):
-        """(members (12 Nc^2, K) int32, slot (12 Nc^2,) int32, linv (slots, K (K + 1) / 2) float64)
-        device copies; linv holds L^-1 packed by columns (column j, rows j .. K-1)."""
+        """(members (12 Nc^2, K) int32, slot (12 Nc^2,) int32, linv (slots, len) float64) device
+        copies; linv holds L^-1 packed by columns (K = 9, len 45) or in the lane-step layout of
+        include/flints.h (K = 36, len 704); None for mixed plans."""
         import torch
 
         npc = 12 * self.nside_coarse * self.nside_coarse
@@ -545,7 +546,8 @@ class PaperPlan:
         slot = torch.empty(npc, dtype=torch.int32, device="cuda")
         linv = None
         if self.precision == "fp64":  # mixed plans keep only double-float blocks
-            linv = torch.empty((self.slots, self.K * (self.K + 1) // 2), dtype=torch.float64, device="cuda")
+            n_l = 704 if self.K == 36 else self.K * (self.K + 1) // 2
+            linv = torch.empty((self.slots, n_l), dtype=torch.float64, device="cuda")
         self._raise(load_library().flints_paper_tables(self._h, _ptr(mem), _ptr(slot), _ptr(linv), _stream(stream)))
         return mem, slot, linv
 

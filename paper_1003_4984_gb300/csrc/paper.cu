@@ -42,6 +42,36 @@ constexpr int SINV_THREADS = 64;
 
 // offset of column j of a K x K lower-triangular matrix packed by columns
 __host__ __device__ constexpr int col_start(int K, int j) { return j * K - j * (j - 1) / 2; }
+
+// L^-1 storage per class.  K = 9: packed by columns.  K = 36: the lane-step
+// layout that the K = 36 kernel reads with one coalesced load per step: rows
+// 0..31 in LS_STEPS steps of 32 lanes, lanes 2p and 2p + 1 sharing rows p and
+// 31 - p (the pair's 33 entries in order: row p, columns 0..p, then row
+// 31 - p, columns 0..31-p; lane 2p takes positions 0..16, lane 2p + 1
+// positions 17..32, position 33 a zero pad), then LS_TAIL steps for rows
+// 32..35 (lane l: row 32 + (l & 3), column (l >> 2) + 8t; zero above the
+// diagonal).
+constexpr int LS_STEPS = 17, LS_TAIL = 5;
+__host__ __device__ constexpr int linv_len(int K) { return K == 36 ? (LS_STEPS + LS_TAIL) * 32 : K * (K + 1) / 2; }
+// (row, column) of entry e of a K = 36 lane-step block; false for a zero pad
+__host__ __device__ inline bool lanestep_entry(int e, int &row, int &col) {
+    if (e < LS_STEPS * 32) {
+        const int u = e >> 5, L = e & 31, p = L >> 1;
+        const int t = (L & 1) ? LS_STEPS + u : u;
+        if (t <= p) {
+            row = p;
+            col = t;
+            return true;
+        }
+        row = 31 - p;
+        col = t - p - 1;
+        return col <= row;
+    }
+    const int f = e - LS_STEPS * 32, t = f >> 5, L = f & 31;
+    row = 32 + (L & 3);
+    col = (L >> 2) + 8 * t;
+    return col <= row;
+}
 constexpr int LDS = STENCIL_MAX + 1;  // padded shared-memory row stride
 
 // unit vector of RING pixel p at Nside N
@@ -209,12 +239,19 @@ __global__ void __launch_bounds__(SINV_THREADS) linv_kernel(LinvArgs a) {
             }
         }
         __syncthreads();
-        // L^-1 packed by columns: column j (rows j .. K-1) from offset col_start(K, j);
-        // zero outside the n x n block
-        double *dst = a.linv + sl * (int64_t)(K * (K + 1) / 2);
-        for (int j = 0; j < K; ++j) {
-            for (int i = j + tid; i < K; i += nt)
-                dst[col_start(K, j) + i - j] = (ok && i < n && j < n) ? Li[i * LDS + j] : 0.0;
+        // L^-1 in the class's storage layout; zero outside the n x n block
+        double *dst = a.linv + sl * (int64_t)linv_len(K);
+        if (K == 36) {
+            for (int e = tid; e < linv_len(36); e += nt) {
+                int i, j;
+                const bool v = lanestep_entry(e, i, j);
+                dst[e] = (ok && v && i < n && j < n) ? Li[i * LDS + j] : 0.0;
+            }
+        } else {
+            for (int j = 0; j < K; ++j) {
+                for (int i = j + tid; i < K; i += nt)
+                    dst[col_start(K, j) + i - j] = (ok && i < n && j < n) ? Li[i * LDS + j] : 0.0;
+            }
         }
         // the largest pair chord (block reduction through atomics on the bit pattern)
         if (tmax > 0.0) atomicMax(a.max_t, (unsigned long long)__double_as_longlong(tmax));
@@ -363,7 +400,7 @@ __global__ void __launch_bounds__(APPLY_WARPS * 32) apply_kernel(ApplyArgs a) {
                     }
                 }
                 // z_c = L^-1 c, z_y = L^-1 y: lane l of the group accumulates row l
-                const double *Lr = a.linv + (int64_t)sl * (K * (K + 1) / 2);
+                const double *Lr = a.linv + (int64_t)sl * linv_len(K);
                 double zc = 0.0, zy = 0.0;
 #pragma unroll
                 for (int j = 0; j < K; ++j) {
@@ -441,12 +478,14 @@ __global__ void __launch_bounds__(APPLY_WARPS * 32) apply_kernel(ApplyArgs a) {
                     win |= t > a.tab.t_max;
                     c1 = table_eval<double>(a.tab, t);
                 }
-                // z_c = L^-1 c, z_y = L^-1 y.  c and y go to the warp's shared slots;
-                // rows 0..31: lane l accumulates row l (columns j <= l < 32);
-                // rows 32..35: lane l takes row 32 + (l & 3) on columns (l >> 2) + 8t,
-                // the eight partial sums of a row joined by shuffles.
-                static_assert(K == 36, "the split of rows 32 .. K-1 is laid out for K = 36");
-                const double *Lr = a.linv + (int64_t)sl * (K * (K + 1) / 2);
+                // z_c = L^-1 c, z_y = L^-1 y from the lane-step block; c and y go to
+                // the warp's shared slots.  Rows 0..31: lanes 2p, 2p + 1 run through
+                // the 33 entries of rows p and 31 - p (lane 2p switches from row p
+                // to row 31 - p after column p; the two halves of row 31 - p are
+                // joined by a shuffle).  Rows 32..35: lane l takes row 32 + (l & 3)
+                // on columns (l >> 2) + 8t, eight partial sums joined by shuffles.
+                static_assert(K == 36, "the lane-step layout is laid out for K = 36");
+                const double *Lr = a.linv + (int64_t)sl * linv_len(K);
                 __syncwarp();
                 sc[wid][lane] = c0;
                 sy[wid][lane] = y0;
@@ -455,25 +494,32 @@ __global__ void __launch_bounds__(APPLY_WARPS * 32) apply_kernel(ApplyArgs a) {
                     sy[wid][32 + lane] = y1;
                 }
                 __syncwarp();
-                double zc0 = 0.0, zy0 = 0.0, zc1 = 0.0, zy1 = 0.0;
+                const int pp = lane >> 1, odd = lane & 1;
+                double zca = 0.0, zya = 0.0, zc0 = 0.0, zy0 = 0.0, zc1 = 0.0, zy1 = 0.0;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    if (lane >= j) {
-                        const double e = __ldg(Lr + col_start(K, j) + lane - j);
-                        zc0 = fma(e, sc[wid][j], zc0);
-                        zy0 = fma(e, sy[wid][j], zy0);
+                for (int u = 0; u < LS_STEPS; ++u) {
+                    const int t = odd ? LS_STEPS + u : u;
+                    if (!odd && u == pp + 1) {
+                        zca = zc0;
+                        zya = zy0;
+                        zc0 = 0.0;
+                        zy0 = 0.0;
                     }
+                    int j = t <= pp ? t : t - pp - 1;
+                    j = j < K ? j : K - 1;  // the zero pad
+                    const double e = __ldg(Lr + u * 32 + lane);
+                    zc0 = fma(e, sc[wid][j], zc0);
+                    zy0 = fma(e, sy[wid][j], zy0);
                 }
+                const double zcb = zc0 + __shfl_xor_sync(FULL, zc0, 1), zyb = zy0 + __shfl_xor_sync(FULL, zy0, 1);
                 {
-                    const int r = 32 + (lane & 3), g = lane >> 2;
+                    const int g = lane >> 2;
 #pragma unroll
-                    for (int t = 0; t < 5; ++t) {
-                        const int j = g + 8 * t;
-                        if (j <= r) {
-                            const double e = __ldg(Lr + col_start(K, j) + r - j);
-                            zc1 = fma(e, sc[wid][j], zc1);
-                            zy1 = fma(e, sy[wid][j], zy1);
-                        }
+                    for (int t = 0; t < LS_TAIL; ++t) {
+                        const int j = g + 8 * t < K ? g + 8 * t : K - 1;  // zero entries past the diagonal
+                        const double e = __ldg(Lr + (LS_STEPS + t) * 32 + lane);
+                        zc1 = fma(e, sc[wid][j], zc1);
+                        zy1 = fma(e, sy[wid][j], zy1);
                     }
 #pragma unroll
                     for (int o = 4; o < 32; o <<= 1) {
@@ -481,8 +527,12 @@ __global__ void __launch_bounds__(APPLY_WARPS * 32) apply_kernel(ApplyArgs a) {
                         zy1 += __shfl_xor_sync(FULL, zy1, o);
                     }
                 }
-                const bool own1 = lane < K - 32;  // lanes 0..3 count rows 32..35 once
-                double v = zc0 * zy0 + (own1 ? zc1 * zy1 : 0.0), qc = zc0 * zc0 + (own1 ? zc1 * zc1 : 0.0);
+                // even lanes count rows p and 31 - p, lanes 0..3 rows 32..35, each once
+                double v = odd ? 0.0 : zca * zya + zcb * zyb, qc = odd ? 0.0 : zca * zca + zcb * zcb;
+                if (lane < K - 32) {
+                    v = fma(zc1, zy1, v);
+                    qc = fma(zc1, zc1, qc);
+                }
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
                     v += __shfl_xor_sync(FULL, v, o);
@@ -642,7 +692,7 @@ __global__ void __launch_bounds__(APPLY_WARPS * 32) apply_kernel_df(ApplyArgs a)
                         yv = split_double(__ldg(a.map + m));
                     }
                 }
-                const float2 *Lr = a.linvf + (int64_t)sl * (K * (K + 1) / 2);
+                const float2 *Lr = a.linvf + (int64_t)sl * linv_len(K);
                 dfacc zc{0.0f, 0.0f}, zy{0.0f, 0.0f};
 #pragma unroll
                 for (int j = 0; j < K; ++j) {
@@ -715,7 +765,7 @@ __global__ void __launch_bounds__(APPLY_WARPS * 32) apply_kernel_df(ApplyArgs a)
                     win |= t.hi > tmaxf;
                     c1 = table_eval<df>(a.tab, t);
                 }
-                const float2 *Lr = a.linvf + (int64_t)sl * (K * (K + 1) / 2);
+                const float2 *Lr = a.linvf + (int64_t)sl * linv_len(K);
                 __syncwarp();
                 sc[wid][lane] = c0;
                 sy[wid][lane] = y0;
@@ -724,26 +774,36 @@ __global__ void __launch_bounds__(APPLY_WARPS * 32) apply_kernel_df(ApplyArgs a)
                     sy[wid][32 + lane] = y1;
                 }
                 __syncwarp();
-                dfacc zc0{0.0f, 0.0f}, zy0{0.0f, 0.0f}, zc1{0.0f, 0.0f}, zy1{0.0f, 0.0f};
+                // the lane-step block, as in the FP64 kernel
+                const int pp = lane >> 1, odd = lane & 1;
+                dfacc zca{0.0f, 0.0f}, zya{0.0f, 0.0f}, zc0{0.0f, 0.0f}, zy0{0.0f, 0.0f};
+                dfacc zc1{0.0f, 0.0f}, zy1{0.0f, 0.0f};
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    if (lane >= j) {
-                        const df e = ld_df(Lr + col_start(K, j) + lane - j);
-                        dfacc_add_prod(zc0, e, sc[wid][j]);
-                        dfacc_add_prod(zy0, e, sy[wid][j]);
+                for (int u = 0; u < LS_STEPS; ++u) {
+                    const int t = odd ? LS_STEPS + u : u;
+                    if (!odd && u == pp + 1) {
+                        zca = zc0;
+                        zya = zy0;
+                        zc0 = {0.0f, 0.0f};
+                        zy0 = {0.0f, 0.0f};
                     }
+                    int j = t <= pp ? t : t - pp - 1;
+                    j = j < K ? j : K - 1;  // the zero pad
+                    const df e = ld_df(Lr + u * 32 + lane);
+                    dfacc_add_prod(zc0, e, sc[wid][j]);
+                    dfacc_add_prod(zy0, e, sy[wid][j]);
                 }
+                const df zc0v = dfacc_val(zc0), zy0v = dfacc_val(zy0);
+                const df zcb = df_add_fast(zc0v, shfl_xor_df(zc0v, 1)), zyb = df_add_fast(zy0v, shfl_xor_df(zy0v, 1));
                 df zc1v, zy1v;
                 {
-                    const int r = 32 + (lane & 3), g = lane >> 2;
+                    const int g = lane >> 2;
 #pragma unroll
-                    for (int t = 0; t < 5; ++t) {
-                        const int j = g + 8 * t;
-                        if (j <= r) {
-                            const df e = ld_df(Lr + col_start(K, j) + r - j);
-                            dfacc_add_prod(zc1, e, sc[wid][j]);
-                            dfacc_add_prod(zy1, e, sy[wid][j]);
-                        }
+                    for (int t = 0; t < LS_TAIL; ++t) {
+                        const int j = g + 8 * t < K ? g + 8 * t : K - 1;  // zero entries past the diagonal
+                        const df e = ld_df(Lr + (LS_STEPS + t) * 32 + lane);
+                        dfacc_add_prod(zc1, e, sc[wid][j]);
+                        dfacc_add_prod(zy1, e, sy[wid][j]);
                     }
                     zc1v = dfacc_val(zc1);
                     zy1v = dfacc_val(zy1);
@@ -753,10 +813,13 @@ __global__ void __launch_bounds__(APPLY_WARPS * 32) apply_kernel_df(ApplyArgs a)
                         zy1v = df_add_fast(zy1v, shfl_xor_df(zy1v, o));
                     }
                 }
-                const df zc0v = dfacc_val(zc0), zy0v = dfacc_val(zy0);
-                const bool own1 = lane < K - 32;  // lanes 0..3 count rows 32..35 once
-                df v = df_mul(zc0v, zy0v), qc = df_mul(zc0v, zc0v);
-                if (own1) {
+                const df zcav = dfacc_val(zca), zyav = dfacc_val(zya);
+                df v{0.0f, 0.0f}, qc{0.0f, 0.0f};
+                if (!odd) {  // even lanes count rows p and 31 - p, lanes 0..3 rows 32..35, each once
+                    v = df_add_fast(df_mul(zcav, zyav), df_mul(zcb, zyb));
+                    qc = df_add_fast(df_mul(zcav, zcav), df_mul(zcb, zcb));
+                }
+                if (lane < K - 32) {
                     v = df_add_fast(v, df_mul(zc1v, zy1v));
                     qc = df_add_fast(qc, df_mul(zc1v, zc1v));
                 }
@@ -925,10 +988,10 @@ int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double
     PALLOC(p->d_slot, (size_t)npc * sizeof(int32_t));
     PALLOC(p->d_steps, (size_t)p->nslot * sizeof(int));
     PALLOC(p->d_scratch, 4 * sizeof(int));
-    PALLOC(p->d_linv, (size_t)p->nslot * (p->K * (p->K + 1) / 2) * sizeof(double));
+    PALLOC(p->d_linv, (size_t)p->nslot * linv_len(p->K) * sizeof(double));
     if (precision == FLINTS_MIXED) {
         PALLOC(p->d_pvf, (size_t)12 * nside * nside * 2 * sizeof(float4));
-        PALLOC(p->d_linvf, (size_t)p->nslot * (p->K * (p->K + 1) / 2) * sizeof(float2));
+        PALLOC(p->d_linvf, (size_t)p->nslot * linv_len(p->K) * sizeof(float2));
     } else {
         PALLOC(p->d_pv, (size_t)12 * nside * nside * 2 * sizeof(double2));
     }
@@ -988,7 +1051,7 @@ int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double
     linv_kernel<<<(unsigned)grid, SINV_THREADS, 0, st>>>(sa);
     if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "flints_paper_plan: L^-1 kernel");
     if (precision == FLINTS_MIXED) {
-        const int64_t nl = p->nslot * (int64_t)(p->K * (p->K + 1) / 2);
+        const int64_t nl = p->nslot * (int64_t)linv_len(p->K);
         to_df_kernel<<<(unsigned)((nl + 255) / 256), 256, 0, st>>>(p->d_linv, p->d_linvf, nl);
         if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "flints_paper_plan: double-float L^-1");
     }
@@ -1124,7 +1187,7 @@ int flints_paper_get_info(flints_paper_t p, flints_paper_info *info, void *strea
     info->t_max = p->t_max;
     info->n_intervals = p->n;
     info->xi0 = p->xi0;
-    info->table_bytes = (int64_t)p->nslot * (p->K * (p->K + 1) / 2) * 8 +
+    info->table_bytes = (int64_t)p->nslot * linv_len(p->K) * 8 +
                         12 * p->nside_c * p->nside_c * (int64_t)(p->K + 1) * 4 + 12 * p->nside * p->nside * 32;
     info->precision = p->precision;
     info->max_pair_t = p->max_pair_t;
@@ -1147,7 +1210,7 @@ int flints_paper_tables(flints_paper_t p, int32_t *members, int32_t *slot, doubl
     if (linv && !p->d_linv)
         return pfail(FLINTS_EINVAL, "flints_paper_tables: mixed plans keep only double-float L^-1 blocks");
     if (e == cudaSuccess && linv)
-        e = cudaMemcpyAsync(linv, p->d_linv, (size_t)p->nslot * (p->K * (p->K + 1) / 2) * sizeof(double),
+        e = cudaMemcpyAsync(linv, p->d_linv, (size_t)p->nslot * linv_len(p->K) * sizeof(double),
                             cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return pcuda(e, "flints_paper_tables");
     return FLINTS_OK;

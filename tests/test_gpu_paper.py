@@ -81,11 +81,31 @@ def test_stencil_table_and_classes(fl, torch, nside, y):
 
 
 def _unpack(packed, K):
+    """Dense L^-1 from a class block: packed by columns (K = 9) or in the
+    lane-step layout of include/flints.h (K = 36)."""
     L = np.zeros((K, K))
-    off = 0
-    for j in range(K):
-        L[j:, j] = packed[off:off + K - j]
-        off += K - j
+    if K != 36:
+        off = 0
+        for j in range(K):
+            L[j:, j] = packed[off:off + K - j]
+            off += K - j
+        return L
+    assert packed.size == 704
+    for u in range(17):
+        for lane in range(32):
+            p, t = lane // 2, (u if lane % 2 == 0 else 17 + u)
+            r, c = (p, t) if t <= p else (31 - p, t - p - 1)
+            if c <= r:
+                L[r, c] = packed[32 * u + lane]
+            else:
+                assert packed[32 * u + lane] == 0
+    for t in range(5):
+        for lane in range(32):
+            r, c = 32 + lane % 4, lane // 4 + 8 * t
+            if c <= r:
+                L[r, c] = packed[544 + 32 * t + lane]
+            else:
+                assert packed[544 + 32 * t + lane] == 0
     return L
 
 
