@@ -197,7 +197,7 @@ def stencil(N: int, targets, y: int):
 PAPER_CHORD_BOUND = 7.0  # chords within a level-y stencil, and to its targets, in units of 1/Nside_c
 
 
-def paper_grid_rule(cl: np.ndarray, nside: int, y: int):
+def paper_grid_rule(cl: np.ndarray, nside: int, y: int, cl_bb: np.ndarray | None = None):
     """Domain and size of the correlation table for the level-y stencil: every
     chord between members of a stencil, and from a target in the central coarse
     pixel to them, is below 7 / Nside_c (Nside_c = Nside / 2^(y-1); the bound
@@ -205,10 +205,12 @@ def paper_grid_rule(cl: np.ndarray, nside: int, y: int):
     radii of the pixels grows from 4.7 at Nside_c = 2 to 6.3 at 64 and
     converges below 6.5), so t_max = (7 / Nside_c)^2, at most 4 (the antipodal
     chord^2, reached only for Nside_c <= 3); the interval count
-    follows the error rule of xi.grid_rule.  Returns (t_max, n)."""
+    follows the error rule of xi.grid_rule (spin 2: weights |C^EE| + |C^BB|).
+    Returns (t_max, n)."""
     n_c = nside >> (y - 1)
     t_max = min((PAPER_CHORD_BOUND / n_c) ** 2, 4.0)  # 4: the chord^2 of antipodal points
-    return t_max, xi.table_size(np.abs(cl), t_max)
+    w = np.abs(cl) if cl_bb is None else np.abs(cl) + np.abs(cl_bb)
+    return t_max, xi.table_size(w, t_max)
 
 
 # ------------------------------------------------- estimator with tabulated S^-1
@@ -310,24 +312,43 @@ def stencil_ordered(nside: int, y: int, pix_c) -> list:
     return out
 
 
+def class_covariance(nside: int, members: np.ndarray, f_plus, spin: int = 0) -> np.ndarray:
+    """Member-member covariance of one stencil (members in order): spin 0
+    xi(t_ij)/xi(0); spin 2 xi+(t_ij)/xi+(0) exp(2i(a_ij - a_ji)) (Eqs. v_spins,
+    spins_correl), unit diagonal."""
+    X = hp.pix2vec(nside, members)
+    K = members.size
+    S = f_plus(np.sum((X[:, None, :] - X[None, :, :]) ** 2, axis=-1).reshape(-1)).reshape(K, K)
+    if spin == 0:
+        return S
+    C = S * kr.pair_phase(X[:, None, :], X[None, :, :], spin)
+    C[np.arange(K), np.arange(K)] = 1.0
+    return C
+
+
 def class_estimate(nside: int, y: int, maps: np.ndarray, targets: np.ndarray, f_plus, xi_zero: float,
-                   eps: float = kr.EPS_NUGGET):
-    """Spin-0 estimate with the inverse tabulated per class (Sec. 2.4): for each
-    class the representative's S + n I is factored (nugget rule of Sec. 2.4) and
+                   eps: float = kr.EPS_NUGGET, spin: int = 0):
+    """Estimate with the inverse tabulated per class (Sec. 2.4): for each class
+    the representative's S + n I is factored (nugget rule of Sec. 2.4) and
     L^-1 found by direct inversion from the representative's own member
     positions; a target in coarse pixel c uses that L^-1 with c's members
     matched to the representative's (the member nearest to R_z(dphi) M v), its
-    own c_i = xi(|n' - x_i|^2)/xi(0) and data: z_c = L^-1 c, z_y = L^-1 y,
-    value c^T S^-1 y = z_c . z_y, variance xi(0) (1 - z_c . z_c).  (The same
-    estimator as w = S^-1 c, w . y with S^-1 = L^-T L^-1 formed explicitly, but
-    without that product's loss of a factor cond(S).)  Returns (values,
-    variances, stencils)."""
+    own covariances c_i and data: z_c = L^-1 conj(c), z_y = L^-1 y, value
+    conj(z_c) . z_y (= c^H S^-1 y), variance xi(0) (1 - |z_c|^2).  (The same
+    estimator as w = S^-1 c with S^-1 = L^-H L^-1 formed explicitly, but
+    without that product's loss of a factor cond(S).)
+
+    Spin 2 (maps (Npix, 2) = Q, U): c_i = xi+(t_i)/xi+(0) exp(2i(a_0i - a_i0));
+    rotations about the polar axis carry the local frames along and leave the
+    member-member phases unchanged, the reflection z -> -z turns every angle a
+    into pi - a and conjugates them, so a mirrored class uses conj(L^-1).
+    Returns (values, variances, stencils)."""
     n_c = nside >> (y - 1)
     cpix = vec2pix(n_c, targets)
     idx = stencil(nside, targets, y)
     rep, mirror, dphi = class_representative(n_c, cpix)
     P = targets.shape[0]
-    val = np.empty(P)
+    val = np.empty(P, dtype=np.float64 if spin == 0 else np.complex128)
     var = np.empty(P)
     for r in np.unique(rep):
         rows = np.nonzero(rep == r)[0]
@@ -335,9 +356,8 @@ def class_estimate(nside: int, y: int, maps: np.ndarray, targets: np.ndarray, f_
         ridx = ridx[ridx >= 0]
         K = ridx.size
         Xr = hp.pix2vec(nside, ridx)
-        S = f_plus(np.sum((Xr[:, None, :] - Xr[None, :, :]) ** 2, axis=-1).reshape(-1)).reshape(1, K, K)
-        L, _ = kr.factor_with_nugget(S, eps)
-        eye = np.eye(K)[None]
+        L, _ = kr.factor_with_nugget(class_covariance(nside, ridx, f_plus, spin)[None], eps)
+        eye = np.eye(K, dtype=L.dtype)[None]
         Linv = np.stack([kr.forward_solve(L, eye[:, :, k]) for k in range(K)], axis=2)[0]
         mem = np.stack([row[row >= 0] for row in idx[rows]])  # (n, K): every pixel of a class has K members
         X = hp.pix2vec(nside, mem)
@@ -346,40 +366,49 @@ def class_estimate(nside: int, y: int, maps: np.ndarray, targets: np.ndarray, f_
         perm = np.argmin(d, axis=2)  # member a of c <-> member perm[a] of the representative
         assert np.max(np.min(d, axis=2)) < 1e-9 / nside, "stencil not congruent to its class representative"
         assert np.all(np.sort(perm, axis=1) == np.arange(K)), "class map is not a bijection of the members"
-        c = f_plus(np.sum((targets[rows][:, None, :] - X) ** 2, axis=-1))
+        tgt = targets[rows][:, None, :]
+        c = f_plus(np.sum((tgt - X) ** 2, axis=-1))
+        if spin == 0:
+            yv = maps[mem]
+        else:
+            c = c * kr.pair_phase(np.broadcast_to(tgt, X.shape), X, spin)
+            yv = maps[mem, 0] + 1j * maps[mem, 1]
         ar = np.arange(rows.size)[:, None]
         c_r = np.empty_like(c)
-        y_r = np.empty_like(c)
+        y_r = np.empty_like(yv)
         c_r[ar, perm] = c  # in the representative's member order
-        y_r[ar, perm] = maps[mem]
-        zc = c_r @ Linv.T
-        zy = y_r @ Linv.T
-        val[rows] = np.sum(zc * zy, axis=1)
-        var[rows] = xi_zero * (1.0 - np.sum(zc * zc, axis=1))
+        y_r[ar, perm] = yv
+        Li = np.where(mirror[rows][:, None, None], np.conj(Linv)[None], Linv[None]) if spin != 0 else Linv[None]
+        zc = np.einsum("pij,pj->pi", Li, np.conj(c_r))
+        zy = np.einsum("pij,pj->pi", Li, y_r)
+        val[rows] = np.sum(np.conj(zc) * zy, axis=1) if spin != 0 else np.sum(zc * zy, axis=1)
+        var[rows] = xi_zero * (1.0 - np.sum(np.abs(zc) ** 2, axis=1))
     return val, var, idx
 
 
 def paper_lens(nside: int, y: int, maps: np.ndarray, defl: np.ndarray, pix: np.ndarray, f_plus, xi_zero: float,
-               classes: bool = False):
-    """Lensed spin-0 values with the paper's stencil at level y (Secs. 2.3-2.5);
-    ``classes``: S^-1 per class of central pixels (class_estimate) instead of
-    per target."""
+               classes: bool = False, spin: int = 0):
+    """Lensed values with the paper's stencil at level y (Secs. 2.3-2.5);
+    ``classes``: the inverse per class of central pixels (class_estimate)
+    instead of S^-1 per target (spin 0 only)."""
     tv = kr.displace(nside, np.asarray(pix, dtype=np.int64), np.asarray(defl, dtype=np.float64))
     if classes:
-        v, s2, idx = class_estimate(nside, y, maps, tv, f_plus, xi_zero)
+        v, s2, idx = class_estimate(nside, y, maps, tv, f_plus, xi_zero, spin=spin)
         return v, s2, idx, tv
+    assert spin == 0, "the per-target S^-1 route is spin 0"
     idx = stencil(nside, tv, y)
     v, s2, n = inverse_estimate(nside, maps, tv, idx, f_plus, xi_zero)
     return v, s2, idx, tv
 
 
 def paper_supersample(nside: int, nside_out: int, y: int, maps: np.ndarray, pix_out: np.ndarray, f_plus,
-                      xi_zero: float, classes: bool = False):
+                      xi_zero: float, classes: bool = False, spin: int = 0):
     """Supersampling (Sec. 2.6) with the paper's stencil at level y."""
     tv = hp.pix2vec(nside_out, np.asarray(pix_out, dtype=np.int64))
     if classes:
-        v, s2, idx = class_estimate(nside, y, maps, tv, f_plus, xi_zero)
+        v, s2, idx = class_estimate(nside, y, maps, tv, f_plus, xi_zero, spin=spin)
         return v, s2, idx, tv
+    assert spin == 0, "the per-target S^-1 route is spin 0"
     idx = stencil(nside, tv, y)
     v, s2, n = inverse_estimate(nside, maps, tv, idx, f_plus, xi_zero)
     return v, s2, idx, tv
