@@ -320,7 +320,11 @@ void flints_free(flints_plan_t plan);
  * S^-1 and in half its memory.
  *
  * flints_paper_plan: y = 1 or 2; nside in [1, 8192] and divisible by
- *   2^(y-1); cl HOST [lmax+1] (C_l, l = 0..lmax); precision FLINTS_FP64, or
+ *   2^(y-1); cl HOST [lmax+1] (spin 0: C_l; spin 2: C_l^EE), cl_bb HOST
+ *   [lmax+1] or NULL (spin 2: C_l^BB; ignored for spin 0); spin 0 or 2
+ *   (spin 2: the member covariances carry the transport phases
+ *   exp(2i(a_ij - a_ji)) with xi+, classes mirrored by z -> -z use conj(L^-1);
+ *   FP64 only); precision FLINTS_FP64, or
  *   FLINTS_MIXED: the per-target chords, correlation lookups and triangular
  *   products in double-float on the FP32 pipe (target position and location
  *   FP64; the L^-1 blocks computed in FP64 and kept as double-float).  Builds on `stream` the xi table on [0, min((7 / Nside_c)^2, 4)] (interval
@@ -331,9 +335,11 @@ void flints_free(flints_plan_t plan);
  *   FLINTS_ENOMEM, FLINTS_ECUDA; message in flints_paper_last_error().
  * flints_paper_lens: lensed values at targets first .. first+count-1 (RING
  *   pixels of the plan's grid displaced along defl, as flints_lens_range).
- *   map DEVICE [12 Nside^2] (8-byte aligned), defl DEVICE [count][2] (16-byte
- *   aligned; entry i belongs to pixel first + i), out and var DEVICE [count]
- *   (var may be NULL), status DEVICE [count] (may be NULL; FLINTS_ST_NUGGET
+ *   map DEVICE [12 Nside^2] (spin 2: [12 Nside^2][2] = Q, U, 16-byte aligned;
+ *   else 8-byte aligned), defl DEVICE [count][2] (16-byte aligned; entry i
+ *   belongs to pixel first + i), out DEVICE [count] (spin 2: [count][2] = Q, U
+ *   in the frame at the displaced direction, 16-byte aligned), var DEVICE
+ *   [count] (may be NULL), status DEVICE [count] (may be NULL; FLINTS_ST_NUGGET
  *   when the class needed a raised nugget, FLINTS_ST_WINDOW when a chord fell
  *   beyond the table domain, FLINTS_ST_FAILED with NaN outputs when no factor
  *   was found).  Asynchronous on `stream`.
@@ -343,7 +349,8 @@ void flints_free(flints_plan_t plan);
  * flints_paper_tables: copies the stencil table (members DEVICE [12 Nside_c^2]
  *   [K] int32 RING indices at Nside, -1 past the member count), the class of
  *   each coarse pixel (slot DEVICE [12 Nside_c^2] int32) and the L^-1 blocks
- *   (linv DEVICE [slots][len] doubles, zero past the member count; K = 9:
+ *   (linv DEVICE [slots][len] doubles, complex (re, im) pairs for spin 2,
+ *   zero past the member count; K = 9:
  *   len = 45, packed by columns: column j, rows j .. 8, from offset
  *   9 j - j (j - 1) / 2; K = 36: len = 704, the lane-step layout: entry
  *   32 u + l (u < 17) holds, for p = l / 2 and t = u (l even) or 17 + u (l
@@ -369,9 +376,10 @@ typedef struct flints_paper_info {
     int64_t points;         /* targets processed so far */
     int64_t window;         /* targets with a chord beyond the table domain */
     int precision;          /* FLINTS_FP64 or FLINTS_MIXED */
+    int spin;               /* 0 or 2 */
 } flints_paper_info;
-int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double *cl, int y, int precision,
-                      void *stream);
+int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double *cl, const double *cl_bb, int y,
+                      int spin, int precision, void *stream);
 int flints_paper_lens(flints_paper_t plan, int64_t first, int64_t count, const double *map, const double *defl,
                       double *out, double *var, uint8_t *status, void *stream);
 int flints_paper_supersample(flints_paper_t plan, int64_t nside_out, int64_t first, int64_t count,

@@ -47,7 +47,7 @@ class _PaperInfo(ctypes.Structure):
                 ("slots", ctypes.c_int64), ("t_max", ctypes.c_double), ("n_intervals", ctypes.c_int),
                 ("xi0", ctypes.c_double), ("table_bytes", ctypes.c_int64), ("max_pair_t", ctypes.c_double),
                 ("nugget_slots", ctypes.c_int64), ("failed_slots", ctypes.c_int64), ("points", ctypes.c_int64),
-                ("window", ctypes.c_int64), ("precision", ctypes.c_int)]
+                ("window", ctypes.c_int64), ("precision", ctypes.c_int), ("spin", ctypes.c_int)]
 
 
 class LaunchCfg(ctypes.Structure):
@@ -117,7 +117,7 @@ def load_library(path: str = LIB_PATH):
     lib.flints_synth_free.argtypes = [vp]
     lib.flints_synth_free.restype = None
     lib.flints_synth_last_error.restype = ctypes.c_char_p
-    lib.flints_paper_plan.argtypes = [ctypes.POINTER(vp), i64, c_int, dp, c_int, c_int, vp]
+    lib.flints_paper_plan.argtypes = [ctypes.POINTER(vp), i64, c_int, dp, dp, c_int, c_int, c_int, vp]
     lib.flints_paper_lens.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp]
     lib.flints_paper_supersample.argtypes = [vp, i64, i64, i64, vp, vp, vp, vp, vp]
     lib.flints_paper_get_info.argtypes = [vp, ctypes.POINTER(_PaperInfo), vp]
@@ -476,14 +476,19 @@ class PaperPlan:
     matrix-vector products per target (spin 0; precision "fp64" or "mixed",
     the per-target arithmetic in double-float on the FP32 pipe)."""
 
-    def __init__(self, nside: int, cl, y: int = 1, precision: str = "fp64", stream=None):
+    def __init__(self, nside: int, cl, y: int = 1, precision: str = "fp64", spin: int = 0, cl_bb=None,
+                 stream=None):
         lib = load_library()
         cl = np.ascontiguousarray(cl, dtype=np.float64)
-        self.nside, self.y, self.precision = int(nside), int(y), precision
+        bb = None if cl_bb is None else np.ascontiguousarray(cl_bb, dtype=np.float64)
+        if bb is not None and bb.size != cl.size:
+            raise FlintsError("cl_bb must have the length of cl")
+        self.nside, self.y, self.precision, self.spin = int(nside), int(y), precision, int(spin)
         prec = {"fp64": FLINTS_FP64, "mixed": FLINTS_MIXED}[precision]
+        dp = ctypes.POINTER(ctypes.c_double)
         h = ctypes.c_void_p()
-        rc = lib.flints_paper_plan(ctypes.byref(h), self.nside, cl.size - 1,
-                                   cl.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self.y, prec,
+        rc = lib.flints_paper_plan(ctypes.byref(h), self.nside, cl.size - 1, cl.ctypes.data_as(dp),
+                                   None if bb is None else bb.ctypes.data_as(dp), self.y, self.spin, prec,
                                    _stream(stream))
         if rc != 0:
             raise FlintsError(f"flints error {rc}: {lib.flints_paper_last_error().decode()}")
@@ -503,12 +508,13 @@ class PaperPlan:
     def _outputs(self, map_, count, out, var, status):
         import torch
 
-        _dev_f64(map_, (12 * self.nside * self.nside,), "map")
+        two = (2,) if self.spin == 2 else ()
+        _dev_f64(map_, (12 * self.nside * self.nside,) + two, "map")
         if out is None:
-            out = torch.empty(count, dtype=torch.float64, device=map_.device)
+            out = torch.empty((count,) + two, dtype=torch.float64, device=map_.device)
         if var is None:
             var = torch.empty(count, dtype=torch.float64, device=map_.device)
-        _dev_f64(out, (count,), "out")
+        _dev_f64(out, (count,) + two, "out")
         _dev_f64(var, (count,), "var")
         if status is not None and (status.dtype != torch.uint8 or tuple(status.shape) != (count,)):
             raise FlintsError("status must be a uint8 CUDA tensor of shape (count,)")
@@ -547,7 +553,8 @@ class PaperPlan:
         linv = None
         if self.precision == "fp64":  # mixed plans keep only double-float blocks
             n_l = 704 if self.K == 36 else self.K * (self.K + 1) // 2
-            linv = torch.empty((self.slots, n_l), dtype=torch.float64, device="cuda")
+            shape = (self.slots, n_l) if self.spin == 0 else (self.slots, n_l, 2)
+            linv = torch.empty(shape, dtype=torch.float64, device="cuda")
         self._raise(load_library().flints_paper_tables(self._h, _ptr(mem), _ptr(slot), _ptr(linv), _stream(stream)))
         return mem, slot, linv
 

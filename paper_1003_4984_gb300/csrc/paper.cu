@@ -264,6 +264,157 @@ __global__ void __launch_bounds__(SINV_THREADS) linv_kernel(LinvArgs a) {
     }
 }
 
+// ------------------------------------------------------ spin 2 (Q, U)
+// Pixel table of spin-2 plans: (cos phi, sin phi), (z, sin theta) per pixel:
+// x = s cos phi, y = s sin phi as in pix2vec, plus the local frame.
+__device__ __forceinline__ void pix_frame(int64_t N, int64_t p, double &c, double &sn, double &z, double &s) {
+    int64_t i, j;
+    pix_ring(N, p, i, j);
+    const Ring rg = ring_of(N, i);
+    sincospi(((double)j + rg.f) / (2.0 * (double)rg.nq), &sn, &c);
+    z = rg.z;
+    s = rg.s;
+}
+
+__global__ void pixframe_kernel(int64_t N, double2 *pv) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= 12 * N * N) return;
+    double c, sn, z, s;
+    pix_frame(N, p, c, sn, z, s);
+    pv[2 * p] = make_double2(c, sn);
+    pv[2 * p + 1] = make_double2(z, s);
+}
+
+// Spin-2 class blocks: C_ij = xi+(t_ij)/xi+(0) exp(2i(a_ij - a_ji)) over the
+// representative's members (unit diagonal, Eqs. v_spins, spins_correl), the
+// nugget rule of Sec. 2.4, a Hermitian right-looking Cholesky C + n I = L L^H
+// in shared memory, L^-1 column by column; written as complex entries in the
+// class's storage layout (as the spin-0 blocks).
+__global__ void __launch_bounds__(SINV_THREADS) linv_kernel_c(LinvArgs a, double2 *linvc) {
+    __shared__ double Sr[STENCIL_MAX * LDS], Si[STENCIL_MAX * LDS], Lr[STENCIL_MAX * LDS], Lim[STENCIL_MAX * LDS];
+    __shared__ double px[STENCIL_MAX], py[STENCIL_MAX], pz[STENCIL_MAX], ps[STENCIL_MAX], pc[STENCIL_MAX],
+        psn[STENCIL_MAX];
+    __shared__ int n_sh, bad;
+    const int tid = threadIdx.x, nt = blockDim.x, K = a.K;
+    for (int64_t sl = blockIdx.x; sl < a.nslot; sl += gridDim.x) {
+        const int64_t rep = slot_rep(a.Nc, sl);
+        const int32_t *mem = a.members + rep * K;
+        if (tid == 0) {
+            int n = 0;
+            while (n < K && mem[n] >= 0) ++n;
+            n_sh = n;
+        }
+        __syncthreads();
+        const int n = n_sh;
+        for (int m = tid; m < n; m += nt) {
+            pix_frame(a.N, mem[m], pc[m], psn[m], pz[m], ps[m]);
+            px[m] = ps[m] * pc[m];
+            py[m] = ps[m] * psn[m];
+        }
+        __syncthreads();
+        double tmax = 0.0;
+        double nug = NUGGET_EPS;
+        int steps = 0;
+        bool ok = false;
+        for (; steps <= MAX_NUGGET_STEPS; ++steps) {
+            for (int e = tid; e < n * n; e += nt) {
+                const int i = e / n, j = e - (e / n) * n;
+                if (j > i) continue;
+                if (i == j) {
+                    Sr[i * LDS + j] = 1.0 + nug;
+                    Si[i * LDS + j] = 0.0;
+                } else {
+                    const double dx = px[j] - px[i], dy = py[j] - py[i], dz = pz[j] - pz[i];
+                    const double t = dx * dx + dy * dy + dz * dz;
+                    tmax = fmax(tmax, t);
+                    const double f = table_eval<double>(a.tab, t);
+                    const Cx<double> ph = pair_phase<double, 2>(dx, dy, dz, pz[i], ps[i], pc[i], psn[i], pz[j], ps[j],
+                                                                pc[j], psn[j]);
+                    Sr[i * LDS + j] = f * ph.re;
+                    Si[i * LDS + j] = f * ph.im;
+                }
+            }
+            if (tid == 0) bad = 0;
+            __syncthreads();
+            for (int kk = 0; kk < n; ++kk) {
+                if (tid == 0) {
+                    const double d = Sr[kk * LDS + kk];
+                    if (d > 0.0) Sr[kk * LDS + kk] = sqrt(d); else bad = 1;
+                }
+                __syncthreads();
+                if (bad) break;
+                const double lkk = Sr[kk * LDS + kk];
+                for (int i = kk + 1 + tid; i < n; i += nt) {
+                    Sr[i * LDS + kk] /= lkk;
+                    Si[i * LDS + kk] /= lkk;
+                }
+                __syncthreads();
+                const int w = n - kk - 1;
+                for (int e = tid; e < w * w; e += nt) {
+                    const int i = kk + 1 + e / w, j = kk + 1 + (e - (e / w) * w);
+                    if (j <= i) {  // A_ij -= L_ik conj(L_jk)
+                        const double ar = Sr[i * LDS + kk], ai = Si[i * LDS + kk];
+                        const double br = Sr[j * LDS + kk], bi = Si[j * LDS + kk];
+                        Sr[i * LDS + j] -= ar * br + ai * bi;
+                        Si[i * LDS + j] -= ai * br - ar * bi;
+                    }
+                }
+                __syncthreads();
+            }
+            if (!bad) {
+                ok = true;
+                break;
+            }
+            nug *= 2.0;
+            __syncthreads();
+        }
+        if (ok) {  // L^-1 by columns: X_cc = 1/L_cc, X_ic = -(sum_{c<=m<i} L_im X_mc)/L_ii
+            for (int col = tid; col < n; col += nt) {
+                for (int i = 0; i < col; ++i) {
+                    Lr[i * LDS + col] = 0.0;
+                    Lim[i * LDS + col] = 0.0;
+                }
+                for (int i = col; i < n; ++i) {
+                    double accr = i == col ? 1.0 : 0.0, acci = 0.0;
+                    for (int m = col; m < i; ++m) {
+                        const double lr = Sr[i * LDS + m], li = Si[i * LDS + m];
+                        const double xr = Lr[m * LDS + col], xi = Lim[m * LDS + col];
+                        accr -= lr * xr - li * xi;
+                        acci -= lr * xi + li * xr;
+                    }
+                    const double d = Sr[i * LDS + i];
+                    Lr[i * LDS + col] = accr / d;
+                    Lim[i * LDS + col] = acci / d;
+                }
+            }
+        }
+        __syncthreads();
+        double2 *dst = linvc + sl * (int64_t)linv_len(K);
+        if (K == 36) {
+            for (int e = tid; e < linv_len(36); e += nt) {
+                int i, j;
+                const bool v = lanestep_entry(e, i, j);
+                const bool in = ok && v && i < n && j < n;
+                dst[e] = make_double2(in ? Lr[i * LDS + j] : 0.0, in ? Lim[i * LDS + j] : 0.0);
+            }
+        } else {
+            for (int j = 0; j < K; ++j) {
+                for (int i = j + tid; i < K; i += nt) {
+                    const bool in = ok && i < n && j < n;
+                    dst[col_start(K, j) + i - j] = make_double2(in ? Lr[i * LDS + j] : 0.0, in ? Lim[i * LDS + j] : 0.0);
+                }
+            }
+        }
+        if (tmax > 0.0) atomicMax(a.max_t, (unsigned long long)__double_as_longlong(tmax));
+        if (tid == 0) {
+            a.slot_steps[sl] = ok ? steps : -1;
+            if (!ok) atomicAdd(a.counts + 1, 1);
+            else if (steps > 0) atomicAdd(a.counts, 1);
+        }
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------- apply kernel
 struct ApplyArgs {
     int64_t N, Nc, first, count, nside_tgt;
@@ -554,6 +705,248 @@ __global__ void __launch_bounds__(APPLY_WARPS * 32) apply_kernel(ApplyArgs a) {
         __syncwarp();
     }
     // counts of every lane, summed over the warp
+    const unsigned w_win = __reduce_add_sync(FULL, (unsigned)n_win);
+    const unsigned w_nug = __reduce_add_sync(FULL, (unsigned)n_nug);
+    const unsigned w_fail = __reduce_add_sync(FULL, (unsigned)n_fail);
+    if (lane == 0 && a.counters) {
+        if (w_win) atomicAdd(a.counters + CNT_WINDOW, (unsigned long long)w_win);
+        if (w_nug) atomicAdd(a.counters + CNT_NUGGET, (unsigned long long)w_nug);
+        if (w_fail) atomicAdd(a.counters + CNT_FAILED, (unsigned long long)w_fail);
+    }
+}
+
+// ------------------------------------------------------- spin-2 apply (FP64)
+// value (Q, U) = conj(z_c) . z_y and variance of target p (spin 2)
+__device__ __forceinline__ void finish_point_s2(const ApplyArgs &a, int64_t p, int32_t sl, double vr, double vi,
+                                                double qc, bool any_win, unsigned long long &n_win,
+                                                unsigned long long &n_nug, unsigned long long &n_fail) {
+    const int steps = __ldg(a.slot_steps + sl);
+    uint8_t st = 0;
+    if (steps > 0) st |= FLINTS_ST_NUGGET;
+    if (any_win) st |= FLINTS_ST_WINDOW;
+    if (steps < 0) {
+        st |= FLINTS_ST_FAILED;
+        vr = vi = qc = __longlong_as_double(0x7ff8000000000000ll);
+    }
+    reinterpret_cast<double2 *>(a.out)[p] = make_double2(vr, vi);
+    if (a.var) a.var[p] = a.xi0 * (1.0 - qc);
+    if (a.status) a.status[p] = st;
+    n_win += any_win;
+    n_nug += steps > 0;
+    n_fail += steps < 0;
+}
+
+// c_m = xi+(t)/xi+(0) exp(2i(a_tm - a_mt)) of member m for the target (t, frame)
+// and its (Q, U); returns false for an absent member
+__device__ __forceinline__ bool member_s2(const ApplyArgs &a, int32_t m, double tx, double ty, double tz, double tzz,
+                                         double ts, double tc, double tsn, double &cr, double &ci, double &yr,
+                                         double &yi, bool &win) {
+    if (m < 0) return false;
+    const double2 f0 = __ldg(a.pv + 2 * m), f1 = __ldg(a.pv + 2 * m + 1);  // (cos, sin phi), (z, s)
+    const double mx = f1.y * f0.x, my = f1.y * f0.y, mz = f1.x;
+    const double dx = mx - tx, dy = my - ty, dz = mz - tz;
+    const double t = dx * dx + dy * dy + dz * dz;
+    win |= t > a.tab.t_max;
+    const double f = table_eval<double>(a.tab, t);
+    const Cx<double> ph = pair_phase<double, 2>(dx, dy, dz, tzz, ts, tc, tsn, f1.x, f1.y, f0.x, f0.y);
+    cr = f * ph.re;
+    ci = f * ph.im;
+    const double2 q = __ldg(reinterpret_cast<const double2 *>(a.map) + m);
+    yr = q.x;
+    yi = q.y;
+    return true;
+}
+
+template <int K>
+__global__ void __launch_bounds__(APPLY_WARPS * 32) apply_kernel_s2(ApplyArgs a) {
+    __shared__ double stx[APPLY_WARPS][32], sty[APPLY_WARPS][32], stz[APPLY_WARPS][32];
+    __shared__ double sts[APPLY_WARPS][32], stc[APPLY_WARPS][32], stn[APPLY_WARPS][32];
+    __shared__ int64_t scp[APPLY_WARPS][32];
+    constexpr int KS = K > GROUP ? K : 1;
+    __shared__ double sxr[APPLY_WARPS][KS], sxi[APPLY_WARPS][KS], syr[APPLY_WARPS][KS], syi[APPLY_WARPS][KS];
+    __shared__ double rvr[APPLY_WARPS][32], rvi[APPLY_WARPS][32], rq[APPLY_WARPS][32];
+    __shared__ int32_t rsl[APPLY_WARPS][32];
+    __shared__ unsigned char rwin[APPLY_WARPS][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t ntiles = (a.count + 31) / 32;
+    const int64_t mirror_from = 6 * a.Nc * a.Nc + 2 * a.Nc;  // first pixel of coarse ring 2 Nc + 1
+    unsigned long long n_win = 0, n_nug = 0, n_fail = 0;
+    for (int64_t tile = (int64_t)blockIdx.x * APPLY_WARPS + wid; tile < ntiles;
+         tile += (int64_t)gridDim.x * APPLY_WARPS) {
+        {
+            double x = 0.0, y = 0.0, z = 1.0;
+            int64_t c = 0;
+            target_of(a, tile * 32 + lane, x, y, z, c);
+            const double sn = sqrt(x * x + y * y);
+            scp[wid][lane] = c;
+            stx[wid][lane] = x;
+            sty[wid][lane] = y;
+            stz[wid][lane] = z;
+            sts[wid][lane] = sn;
+            stc[wid][lane] = sn > 1e-12 ? x / sn : 1.0;
+            stn[wid][lane] = sn > 1e-12 ? y / sn : 0.0;
+        }
+        __syncwarp();
+        const int npt = a.count - tile * 32 < 32 ? (int)(a.count - tile * 32) : 32;
+        if constexpr (K <= GROUP) {
+            const int g = lane / GROUP, l = lane - g * GROUP, base = g * GROUP;
+            for (int q0 = 0; q0 < npt; q0 += 3) {
+                const int q = q0 + g;
+                const bool has = g < 3 && q < npt;
+                const int qq = has ? q : 0;
+                const int64_t c = scp[wid][qq];
+                const int32_t sl = has ? __ldg(a.slot + c) : 0;
+                const double msign = c >= mirror_from ? -1.0 : 1.0;  // conj(L^-1) for mirrored classes
+                double cr = 0.0, ci = 0.0, yr = 0.0, yi = 0.0;
+                bool win = false;
+                if (has && l < K)
+                    member_s2(a, __ldg(a.members + c * K + l), stx[wid][qq], sty[wid][qq], stz[wid][qq],
+                              stz[wid][qq], sts[wid][qq], stc[wid][qq], stn[wid][qq], cr, ci, yr, yi, win);
+                // z_c = L^-1 conj(c), z_y = L^-1 y: lane l of the group accumulates row l
+                const double2 *Lr = reinterpret_cast<const double2 *>(a.linv) + (int64_t)sl * linv_len(K);
+                double zcr = 0.0, zci = 0.0, zyr = 0.0, zyi = 0.0;
+#pragma unroll
+                for (int j = 0; j < K; ++j) {
+                    const double xr = __shfl_sync(FULL, cr, base + j), xi = -__shfl_sync(FULL, ci, base + j);
+                    const double ur = __shfl_sync(FULL, yr, base + j), ui = __shfl_sync(FULL, yi, base + j);
+                    if (has && l < K && l >= j) {
+                        const double2 e = __ldg(Lr + col_start(K, j) + l - j);
+                        const double ei = msign * e.y;
+                        zcr = fma(e.x, xr, fma(-ei, xi, zcr));
+                        zci = fma(e.x, xi, fma(ei, xr, zci));
+                        zyr = fma(e.x, ur, fma(-ei, ui, zyr));
+                        zyi = fma(e.x, ui, fma(ei, ur, zyi));
+                    }
+                }
+                double vr = zcr * zyr + zci * zyi, vi = zcr * zyi - zci * zyr, qs = zcr * zcr + zci * zci;
+#pragma unroll
+                for (int o = 8; o >= 1; o >>= 1) {
+                    const double tr = __shfl_sync(FULL, vr, lane + o), ti = __shfl_sync(FULL, vi, lane + o);
+                    const double tq = __shfl_sync(FULL, qs, lane + o);
+                    if (l < o && l + o < GROUP) {
+                        vr += tr;
+                        vi += ti;
+                        qs += tq;
+                    }
+                }
+                const unsigned wb = __ballot_sync(FULL, win);
+                if (has && l == 0) {
+                    rvr[wid][q] = vr;
+                    rvi[wid][q] = vi;
+                    rq[wid][q] = qs;
+                    rsl[wid][q] = sl;
+                    rwin[wid][q] = ((wb >> base) & ((1u << GROUP) - 1u)) != 0;
+                }
+            }
+        } else {
+            static_assert(K == 36, "the lane-step layout is laid out for K = 36");
+            for (int q = 0; q < npt; ++q) {
+                const int64_t c = scp[wid][q];
+                const int32_t sl = __ldg(a.slot + c);
+                const double msign = c >= mirror_from ? -1.0 : 1.0;
+                const double tx = stx[wid][q], ty = sty[wid][q], tz = stz[wid][q];
+                const double ts = sts[wid][q], tc = stc[wid][q], tn = stn[wid][q];
+                const int32_t *mem = a.members + c * K;
+                double c0r = 0.0, c0i = 0.0, y0r = 0.0, y0i = 0.0, c1r = 0.0, c1i = 0.0, y1r = 0.0, y1i = 0.0;
+                bool win = false;
+                member_s2(a, __ldg(mem + lane), tx, ty, tz, tz, ts, tc, tn, c0r, c0i, y0r, y0i, win);
+                if (lane + 32 < K)
+                    member_s2(a, __ldg(mem + lane + 32), tx, ty, tz, tz, ts, tc, tn, c1r, c1i, y1r, y1i, win);
+                const double2 *Lr = reinterpret_cast<const double2 *>(a.linv) + (int64_t)sl * linv_len(K);
+                __syncwarp();
+                sxr[wid][lane] = c0r;
+                sxi[wid][lane] = -c0i;
+                syr[wid][lane] = y0r;
+                syi[wid][lane] = y0i;
+                if (lane < K - 32) {
+                    sxr[wid][32 + lane] = c1r;
+                    sxi[wid][32 + lane] = -c1i;
+                    syr[wid][32 + lane] = y1r;
+                    syi[wid][32 + lane] = y1i;
+                }
+                __syncwarp();
+                // the lane-step block as in the spin-0 kernel, complex
+                const int pp = lane >> 1, odd = lane & 1;
+                double acr = 0.0, aci = 0.0, ayr = 0.0, ayi = 0.0;  // row p (even lanes)
+                double zcr = 0.0, zci = 0.0, zyr = 0.0, zyi = 0.0;
+#pragma unroll
+                for (int u = 0; u < LS_STEPS; ++u) {
+                    const int t = odd ? LS_STEPS + u : u;
+                    if (!odd && u == pp + 1) {
+                        acr = zcr;
+                        aci = zci;
+                        ayr = zyr;
+                        ayi = zyi;
+                        zcr = zci = zyr = zyi = 0.0;
+                    }
+                    int j = t <= pp ? t : t - pp - 1;
+                    j = j < K ? j : K - 1;  // the zero pad
+                    const double2 e = __ldg(Lr + u * 32 + lane);
+                    const double ei = msign * e.y;
+                    const double xr = sxr[wid][j], xi = sxi[wid][j], ur = syr[wid][j], ui = syi[wid][j];
+                    zcr = fma(e.x, xr, fma(-ei, xi, zcr));
+                    zci = fma(e.x, xi, fma(ei, xr, zci));
+                    zyr = fma(e.x, ur, fma(-ei, ui, zyr));
+                    zyi = fma(e.x, ui, fma(ei, ur, zyi));
+                }
+                const double bcr = zcr + __shfl_xor_sync(FULL, zcr, 1), bci = zci + __shfl_xor_sync(FULL, zci, 1);
+                const double byr = zyr + __shfl_xor_sync(FULL, zyr, 1), byi = zyi + __shfl_xor_sync(FULL, zyi, 1);
+                double tcr = 0.0, tci = 0.0, tyr = 0.0, tyi = 0.0;  // rows 32..35
+                {
+                    const int g = lane >> 2;
+#pragma unroll
+                    for (int t = 0; t < LS_TAIL; ++t) {
+                        const int j = g + 8 * t < K ? g + 8 * t : K - 1;  // zero entries past the diagonal
+                        const double2 e = __ldg(Lr + (LS_STEPS + t) * 32 + lane);
+                        const double ei = msign * e.y;
+                        const double xr = sxr[wid][j], xi = sxi[wid][j], ur = syr[wid][j], ui = syi[wid][j];
+                        tcr = fma(e.x, xr, fma(-ei, xi, tcr));
+                        tci = fma(e.x, xi, fma(ei, xr, tci));
+                        tyr = fma(e.x, ur, fma(-ei, ui, tyr));
+                        tyi = fma(e.x, ui, fma(ei, ur, tyi));
+                    }
+#pragma unroll
+                    for (int o = 4; o < 32; o <<= 1) {
+                        tcr += __shfl_xor_sync(FULL, tcr, o);
+                        tci += __shfl_xor_sync(FULL, tci, o);
+                        tyr += __shfl_xor_sync(FULL, tyr, o);
+                        tyi += __shfl_xor_sync(FULL, tyi, o);
+                    }
+                }
+                // even lanes count rows p and 31 - p, lanes 0..3 rows 32..35, each once
+                double vr = 0.0, vi = 0.0, qc = 0.0;
+                if (!odd) {
+                    vr = acr * ayr + aci * ayi + bcr * byr + bci * byi;
+                    vi = acr * ayi - aci * ayr + bcr * byi - bci * byr;
+                    qc = acr * acr + aci * aci + bcr * bcr + bci * bci;
+                }
+                if (lane < K - 32) {
+                    vr += tcr * tyr + tci * tyi;
+                    vi += tcr * tyi - tci * tyr;
+                    qc += tcr * tcr + tci * tci;
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    vr += __shfl_xor_sync(FULL, vr, o);
+                    vi += __shfl_xor_sync(FULL, vi, o);
+                    qc += __shfl_xor_sync(FULL, qc, o);
+                }
+                const bool any_win = __any_sync(FULL, win);
+                if (lane == 0) {
+                    rvr[wid][q] = vr;
+                    rvi[wid][q] = vi;
+                    rq[wid][q] = qc;
+                    rsl[wid][q] = sl;
+                    rwin[wid][q] = any_win;
+                }
+            }
+        }
+        __syncwarp();
+        if (lane < npt)
+            finish_point_s2(a, tile * 32 + lane, rsl[wid][lane], rvr[wid][lane], rvi[wid][lane], rq[wid][lane],
+                            rwin[wid][lane] != 0, n_win, n_nug, n_fail);
+        __syncwarp();
+    }
     const unsigned w_win = __reduce_add_sync(FULL, (unsigned)n_win);
     const unsigned w_nug = __reduce_add_sync(FULL, (unsigned)n_nug);
     const unsigned w_fail = __reduce_add_sync(FULL, (unsigned)n_fail);
@@ -875,7 +1268,8 @@ struct flints_paper_s {
     double2 *d_pv;
     float4 *d_pvf;
     float2 *d_linvf;
-    int precision;
+    int precision, spin;
+    double *d_clbb;
     unsigned long long *d_counters, *d_maxt;
     int64_t points;
 };
@@ -908,6 +1302,7 @@ static void paper_release(flints_paper_s *p) {
     cudaFree(p->d_scratch);
     cudaFree(p->d_linv);
     cudaFree(p->d_pv);
+    cudaFree(p->d_clbb);
     cudaFree(p->d_pvf);
     cudaFree(p->d_linvf);
     cudaFree(p->d_counters);
@@ -916,12 +1311,12 @@ static void paper_release(flints_paper_s *p) {
 
 // interval count of the xi table on [0, t_max]: the cubic Hermite error bound
 // h^4/384 max|f4| below 1e-11 (f4 bounded through the fourth derivatives of
-// P_l at 1), a power of two in [64, 65536]
-static int table_intervals(const double *cl, int lmax, double t_max) {
+// P_l at 1, weights |C_l| (+ |C_l^BB| for spin 2)), a power of two in [64, 65536]
+static int table_intervals(const double *cl, const double *cl_bb, int lmax, double t_max) {
     double x0 = 0.0, b4num = 0.0;
     for (int l = 0; l <= lmax; ++l) {
         const double ld = (double)l;
-        const double a = (2.0 * ld + 1.0) / (4.0 * PI) * std::fabs(cl[l]);
+        const double a = (2.0 * ld + 1.0) / (4.0 * PI) * (std::fabs(cl[l]) + (cl_bb ? std::fabs(cl_bb[l]) : 0.0));
         x0 += a;
         if (l >= 4) b4num += a * ((ld - 3) * (ld - 2) * (ld - 1) * ld * (ld + 1) * (ld + 2) * (ld + 3) * (ld + 4) / 384.0);
     }
@@ -936,8 +1331,8 @@ extern "C" {
 
 const char *flints_paper_last_error(void) { return g_perr; }
 
-int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double *cl, int y, int precision,
-                      void *stream) {
+int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double *cl, const double *cl_bb, int y,
+                      int spin, int precision, void *stream) {
     if (!out) return pfail(FLINTS_EINVAL, "flints_paper_plan: out is NULL");
     *out = nullptr;
     if (y != 1 && y != 2) return pfail(FLINTS_EINVAL, "flints_paper_plan: level y must be 1 or 2 (got %d)", y);
@@ -949,8 +1344,13 @@ int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double
     if (!cl) return pfail(FLINTS_EINVAL, "flints_paper_plan: cl is NULL");
     if (precision != FLINTS_FP64 && precision != FLINTS_MIXED)
         return pfail(FLINTS_EINVAL, "flints_paper_plan: precision must be FLINTS_FP64 or FLINTS_MIXED");
+    if (spin != 0 && spin != 2) return pfail(FLINTS_EINVAL, "flints_paper_plan: spin must be 0 or 2 (got %d)", spin);
+    if (spin == 2 && precision != FLINTS_FP64)
+        return pfail(FLINTS_EINVAL, "flints_paper_plan: spin-2 plans are FP64 (FLINTS_FP64)");
+    if (spin == 0) cl_bb = nullptr;
     for (int l = 0; l <= lmax; ++l)
-        if (!std::isfinite(cl[l])) return pfail(FLINTS_EINVAL, "flints_paper_plan: non-finite cl at l = %d", l);
+        if (!std::isfinite(cl[l]) || (cl_bb && !std::isfinite(cl_bb[l])))
+            return pfail(FLINTS_EINVAL, "flints_paper_plan: non-finite spectrum value at l = %d", l);
     cudaStream_t st = (cudaStream_t)stream;
     flints_paper_s *p = new flints_paper_s();
     std::memset(p, 0, sizeof *p);
@@ -961,10 +1361,11 @@ int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double
     p->K = 9 * k * k;
     p->lmax = lmax;
     p->precision = precision;
+    p->spin = spin;
     p->nslot = slot_count(p->nside_c);
     const double Dc = 7.0 / (double)p->nside_c;
     p->t_max = Dc * Dc < 4.0 ? Dc * Dc : 4.0;  // 4: the chord^2 of antipodal points
-    p->n = table_intervals(cl, lmax, p->t_max);
+    p->n = table_intervals(cl, cl_bb, lmax, p->t_max);
     p->h = p->t_max / p->n;
     p->inv_h = p->n / p->t_max;
     const int64_t npc = 12 * p->nside_c * p->nside_c;
@@ -988,7 +1389,8 @@ int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double
     PALLOC(p->d_slot, (size_t)npc * sizeof(int32_t));
     PALLOC(p->d_steps, (size_t)p->nslot * sizeof(int));
     PALLOC(p->d_scratch, 4 * sizeof(int));
-    PALLOC(p->d_linv, (size_t)p->nslot * linv_len(p->K) * sizeof(double));
+    PALLOC(p->d_linv, (size_t)p->nslot * linv_len(p->K) * (spin == 2 ? 2 : 1) * sizeof(double));
+    if (cl_bb) PALLOC(p->d_clbb, (size_t)(lmax + 1) * sizeof(double));
     if (precision == FLINTS_MIXED) {
         PALLOC(p->d_pvf, (size_t)12 * nside * nside * 2 * sizeof(float4));
         PALLOC(p->d_linvf, (size_t)p->nslot * linv_len(p->K) * sizeof(float2));
@@ -1001,13 +1403,17 @@ int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double
     if ((e = cudaMemcpyAsync(p->d_cl, cl, (size_t)(lmax + 1) * sizeof(double), cudaMemcpyHostToDevice, st)) !=
         cudaSuccess)
         return bail(e, "flints_paper_plan: copy cl");
+    if (cl_bb &&
+        (e = cudaMemcpyAsync(p->d_clbb, cl_bb, (size_t)(lmax + 1) * sizeof(double), cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess)
+        return bail(e, "flints_paper_plan: copy cl_bb");
     if ((e = cudaMemsetAsync(p->d_fm, 0, nn * sizeof(double), st)) != cudaSuccess) return bail(e, "memset");
     if ((e = cudaMemsetAsync(p->d_gm, 0, nn * sizeof(double), st)) != cudaSuccess) return bail(e, "memset");
     if ((e = cudaMemsetAsync(p->d_scratch, 0, 4 * sizeof(int), st)) != cudaSuccess) return bail(e, "memset");
     if ((e = cudaMemsetAsync(p->d_counters, 0, CNT_N * sizeof(unsigned long long), st)) != cudaSuccess)
         return bail(e, "memset");
     if ((e = cudaMemsetAsync(p->d_maxt, 0, sizeof(unsigned long long), st)) != cudaSuccess) return bail(e, "memset");
-    if ((e = launch_xi_table(0, lmax, p->d_cl, nullptr, p->t_max, p->n, p->d_f, p->d_g, p->d_fm, p->d_gm, st)) !=
+    if ((e = launch_xi_table(spin, lmax, p->d_cl, p->d_clbb, p->t_max, p->n, p->d_f, p->d_g, p->d_fm, p->d_gm, st)) !=
         cudaSuccess)
         return bail(e, "flints_paper_plan: xi table kernel");
     double xi0 = 0.0;
@@ -1024,6 +1430,8 @@ int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double
         return bail(e, "flints_paper_plan: table coefficients");
     if (precision == FLINTS_MIXED)
         pixvec_df_kernel<<<(unsigned)((12 * nside * nside + 255) / 256), 256, 0, st>>>(nside, p->d_pvf);
+    else if (spin == 2)
+        pixframe_kernel<<<(unsigned)((12 * nside * nside + 255) / 256), 256, 0, st>>>(nside, p->d_pv);
     else
         pixvec_kernel<<<(unsigned)((12 * nside * nside + 255) / 256), 256, 0, st>>>(nside, p->d_pv);
     if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "flints_paper_plan: pixel vector kernel");
@@ -1048,7 +1456,10 @@ int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double
     sa.max_t = p->d_maxt;
     sa.counts = p->d_scratch;
     const int64_t grid = p->nslot < 152 * 16 ? p->nslot : 152 * 16;
-    linv_kernel<<<(unsigned)grid, SINV_THREADS, 0, st>>>(sa);
+    if (spin == 2)
+        linv_kernel_c<<<(unsigned)grid, SINV_THREADS, 0, st>>>(sa, reinterpret_cast<double2 *>(p->d_linv));
+    else
+        linv_kernel<<<(unsigned)grid, SINV_THREADS, 0, st>>>(sa);
     if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "flints_paper_plan: L^-1 kernel");
     if (precision == FLINTS_MIXED) {
         const int64_t nl = p->nslot * (int64_t)linv_len(p->K);
@@ -1110,8 +1521,10 @@ static int paper_run(flints_paper_t p, int64_t nside_tgt, int64_t first, int64_t
     if (count == 0) return FLINTS_OK;
     if (!map || !out) return pfail(FLINTS_EINVAL, "map and out must not be NULL");
     if (nside_tgt == 0 && !defl) return pfail(FLINTS_EINVAL, "defl is NULL");
-    if (((uintptr_t)defl & 15u) || (((uintptr_t)map | (uintptr_t)out | (uintptr_t)var) & 7u))
-        return pfail(FLINTS_EINVAL, "defl must be 16-byte aligned, map, out and var 8-byte aligned");
+    const uintptr_t need = p->spin == 2 ? 15u : 7u;
+    if (((uintptr_t)defl & 15u) || (((uintptr_t)map | (uintptr_t)out) & need) || ((uintptr_t)var & 7u))
+        return pfail(FLINTS_EINVAL, "defl (and spin-2 map and out) must be 16-byte aligned, map, out and var 8-byte "
+                                    "aligned");
     ApplyArgs a{};
     a.N = p->nside;
     a.Nc = p->nside_c;
@@ -1145,7 +1558,12 @@ static int paper_run(flints_paper_t p, int64_t nside_tgt, int64_t first, int64_t
     const unsigned grid = (unsigned)(want < cap ? want : cap);
     cudaStream_t st = (cudaStream_t)stream;
     const bool mixed = p->precision == FLINTS_MIXED;
-    if (p->K == 9) {
+    if (p->spin == 2) {
+        if (p->K == 9)
+            apply_kernel_s2<9><<<grid, APPLY_WARPS * 32, 0, st>>>(a);
+        else
+            apply_kernel_s2<36><<<grid, APPLY_WARPS * 32, 0, st>>>(a);
+    } else if (p->K == 9) {
         if (mixed)
             apply_kernel_df<9><<<grid, APPLY_WARPS * 32, 0, st>>>(a);
         else
@@ -1190,6 +1608,8 @@ int flints_paper_get_info(flints_paper_t p, flints_paper_info *info, void *strea
     info->table_bytes = (int64_t)p->nslot * linv_len(p->K) * 8 +
                         12 * p->nside_c * p->nside_c * (int64_t)(p->K + 1) * 4 + 12 * p->nside * p->nside * 32;
     info->precision = p->precision;
+    info->spin = p->spin;
+    if (p->spin == 2) info->table_bytes += (int64_t)p->nslot * linv_len(p->K) * 8;
     info->max_pair_t = p->max_pair_t;
     info->nugget_slots = p->nugget_slots;
     info->failed_slots = p->failed_slots;
@@ -1210,7 +1630,7 @@ int flints_paper_tables(flints_paper_t p, int32_t *members, int32_t *slot, doubl
     if (linv && !p->d_linv)
         return pfail(FLINTS_EINVAL, "flints_paper_tables: mixed plans keep only double-float L^-1 blocks");
     if (e == cudaSuccess && linv)
-        e = cudaMemcpyAsync(linv, p->d_linv, (size_t)p->nslot * linv_len(p->K) * sizeof(double),
+        e = cudaMemcpyAsync(linv, p->d_linv, (size_t)p->nslot * linv_len(p->K) * (p->spin == 2 ? 2 : 1) * sizeof(double),
                             cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return pcuda(e, "flints_paper_tables");
     return FLINTS_OK;

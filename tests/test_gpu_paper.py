@@ -271,3 +271,91 @@ def test_mixed_plan_tables(fl, torch):
     assert plan.info()["precision"] == fl.FLINTS_MIXED
     mem, slot, linv = plan.tables()
     assert linv is None and mem.shape == (12 * 64, 36)
+
+
+# ------------------------------------------------------------------ spin 2
+def _spin2_inputs(nside, lmax, seed, bb_frac=0.3):
+    cl = wl.cl_ee(lmax, 0.7 * lmax)
+    bb = bb_frac * cl
+    P = sht.synth_map(nside, lmax, wl.draw_alm(cl, seed), spin=2, blm=wl.draw_alm(bb, seed + 1))
+    m = np.ascontiguousarray(np.stack([P.real, P.imag], axis=1))
+    return cl, bb, m, float(np.sqrt(np.mean(np.abs(P) ** 2)))
+
+
+def _spin2_table(cl, bb, nside, y):
+    t_max, n = fc.paper_grid_rule(cl, nside, y, bb)
+    tab, _, x0 = xi.spin2_tables(cl, bb, t_max, n)
+    return tab, x0, t_max, n
+
+
+def _spin2_solve_route(nside, m, tv, idx, tab, x0):
+    v = np.empty(tv.shape[0], dtype=np.complex128)
+    s2 = np.empty(tv.shape[0])
+    cnt = np.sum(idx >= 0, axis=1)
+    for k in np.unique(cnt):
+        rows = np.nonzero(cnt == k)[0]
+        st = np.stack([r[r >= 0] for r in idx[rows]])
+        v[rows], s2[rows], _ = kr.estimate(nside, 2, m, tv[rows], st, tab, x0)
+    return v, s2
+
+
+@pytest.mark.parametrize("nside,lmax,y", [(2, 12, 1), (8, 16, 1), (32, 64, 1), (4, 24, 2), (16, 32, 2), (32, 64, 2)])
+def test_spin2_lens_parity_whole_sky(fl, torch, nside, lmax, y):
+    # Q/U lensed with the paper stencil: the class's complex L^-1 (conjugated for the
+    # southern classes) against the oracle's class route and per-target solve
+    cl, bb, m, sigma = _spin2_inputs(nside, lmax, 400 + nside + y)
+    npix = hp.npix(nside)
+    defl = wl.random_deflection(npix, 401 + nside, rms=0.5 * _pixel_size(nside))
+    plan = fl.PaperPlan(nside, cl, y, "fp64", spin=2, cl_bb=bb)
+    t_max, n = fc.paper_grid_rule(cl, nside, y, bb)
+    info = plan.info()
+    assert info["spin"] == 2 and info["t_max"] == t_max and info["n_intervals"] == n
+    st = torch.empty(npix, dtype=torch.uint8, device="cuda")
+    out, var = plan.lens(torch.from_numpy(m).cuda(), torch.from_numpy(np.ascontiguousarray(defl)).cuda(), status=st)
+    torch.cuda.synchronize()
+    o = to_host(out)
+    v = o[:, 0] + 1j * o[:, 1]
+    s2 = to_host(var)
+    tab, x0, _, _ = _spin2_table(cl, bb, nside, y)
+    rv, rs2, idx, tv = fc.paper_lens(nside, y, m, defl, np.arange(npix), tab, x0, classes=True, spin=2)
+    ov, os2 = _spin2_solve_route(nside, m, tv, idx, tab, x0)
+    for a_v, a_s2 in ((rv, rs2), (ov, os2)):
+        assert np.max(np.abs(v - a_v)) <= TOL["fp64"] * sigma
+        assert np.max(np.abs(s2 - a_s2)) <= TOL["fp64"] * x0
+    assert not np.any(to_host(st) & (fl.ST_WINDOW | fl.ST_FAILED))
+
+
+@pytest.mark.parametrize("nside,nout,y", [(16, 32, 1), (16, 32, 2)])
+def test_spin2_supersample_and_ragged(fl, torch, nside, nout, y):
+    cl, bb, m, sigma = _spin2_inputs(nside, 2 * nside, 501)
+    plan = fl.PaperPlan(nside, cl, y, "fp64", spin=2, cl_bb=bb)
+    first, count = 777, 1501
+    out, var = plan.supersample(torch.from_numpy(m).cuda(), nout, first=first, count=count)
+    torch.cuda.synchronize()
+    o = to_host(out)
+    v = o[:, 0] + 1j * o[:, 1]
+    tab, x0, _, _ = _spin2_table(cl, bb, nside, y)
+    rv, rs2, idx, tv = fc.paper_supersample(nside, nout, y, m, np.arange(first, first + count), tab, x0,
+                                            classes=True, spin=2)
+    assert np.max(np.abs(v - rv)) <= TOL["fp64"] * sigma
+    assert np.max(np.abs(to_host(var) - rs2)) <= TOL["fp64"] * x0
+
+
+def test_spin2_linv_blocks(fl, torch):
+    nside, y = 8, 1
+    cl = wl.cl_ee(24, 16.0)
+    bb = 0.3 * cl
+    tab, x0, _, _ = _spin2_table(cl, bb, nside, y)
+    plan = fl.PaperPlan(nside, cl, y, "fp64", spin=2, cl_bb=bb)
+    _, slot, linv = plan.tables()
+    torch.cuda.synchronize()
+    slot, linv = to_host(slot), to_host(linv)
+    reps = np.unique(fc.class_representative(nside, np.arange(hp.npix(nside)))[0])
+    for r, mem in zip(reps, fc.stencil_ordered(nside, y, reps)):
+        k = mem.size
+        C = fc.class_covariance(nside, mem, tab, 2)
+        L, nug = kr.factor_with_nugget(C[None], kr.EPS_NUGGET)
+        ref = np.linalg.inv(L[0])
+        blk = linv[slot[r]]
+        G = _unpack(blk[:, 0], plan.K) + 1j * _unpack(blk[:, 1], plan.K)
+        assert np.max(np.abs(G[:k, :k] - ref)) <= 1e-9 * np.max(np.abs(ref)), f"class of coarse pixel {r}"
