@@ -769,27 +769,33 @@ def run_paper(args):
     res = {}
     clk_path = os.path.join(ROOT, "gpurun_out", "bench_clocks_paper.csv") if os.path.isdir(
         os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks_paper.csv"
+    cl_ee, cl_bb = W.cl()
     with Clocks(clk_path) as clk:
-        for task, nside, nout in (("lens", 4096, None), ("supersample", 2048, 4096)):
+        for task, nside, nout, spin in (("lens", 4096, None, 0), ("supersample", 2048, 4096, 0),
+                                        ("lens_qu", 4096, None, 2)):
             npix = 12 * nside * nside
-            m = torch.randn(npix, dtype=torch.float64, device=dev, generator=g)
+            m = torch.randn((npix, 2) if spin == 2 else (npix,), dtype=torch.float64, device=dev, generator=g)
             ntgt = 12 * (nout or nside) ** 2
             nb = ntgt // BATCH
             defl = None
-            if task == "lens":
+            if task.startswith("lens"):
                 defl = torch.randn((BATCH, 2), dtype=torch.float64, device=dev, generator=g) * wl.DEFLECTION_RMS
+            out = torch.empty((BATCH, 2) if spin == 2 else (BATCH,), dtype=torch.float64, device=dev)
             for y in (1, 2):
                 for precision in ("fp64", "mixed"):
                     torch.cuda.synchronize(dev)
                     t0 = time.perf_counter()
-                    plan = fl.PaperPlan(nside, cl, y, precision)
+                    if spin == 2:
+                        plan = fl.PaperPlan(nside, cl_ee, y, precision, spin=2, cl_bb=cl_bb)
+                    else:
+                        plan = fl.PaperPlan(nside, cl, y, precision)
                     torch.cuda.synchronize(dev)
                     plan_s = time.perf_counter() - t0
                     info = plan.info()
 
                     def step(i):
                         first = (i % nb) * BATCH
-                        if task == "lens":
+                        if task.startswith("lens"):
                             plan.lens(m, defl, first=first, count=BATCH, out=out, var=var)
                         else:
                             plan.supersample(m, nout, first=first, count=BATCH, out=out, var=var)
@@ -813,9 +819,9 @@ def run_paper(args):
                         "nugget_slots": info["nugget_slots"], "failed_slots": info["failed_slots"],
                         "predicted_precision": math.sqrt(float(var.mean()) / info["xi0"])}
                     if precision == "fp64":
-                        arm["fp64_tflops"] = flops.paper_fp64_flops(K) * BATCH / sec / 1e12
+                        arm["fp64_tflops"] = flops.paper_fp64_flops(K, spin) * BATCH / sec / 1e12
                     else:
-                        arm["fp32_tflops"] = flops.paper_mixed_fp32_flops(K) * BATCH / sec / 1e12
+                        arm["fp32_tflops"] = flops.paper_mixed_fp32_flops(K, spin) * BATCH / sec / 1e12
                     res[f"{task}_y{y}_{precision}"] = arm
                     plan.close()
                     torch.cuda.empty_cache()
@@ -823,7 +829,7 @@ def run_paper(args):
             torch.cuda.empty_cache()
     head = res["lens_y1_mixed"]
     ratios = {f"{t}_y{y}": res[f"{t}_y{y}_mixed"]["value"] / res[f"{t}_y{y}_fp64"]["value"]
-              for t in ("lens", "supersample") for y in (1, 2)}
+              for t in ("lens", "supersample", "lens_qu") for y in (1, 2)}
     achieved = head["fp32_tflops"]
     print(json.dumps({
         "metric": "lensed pts/s, Nside 4096 T, lmax 4096, paper stencil (9 px) with tabulated inverses, mixed vs FP64",
@@ -831,8 +837,9 @@ def run_paper(args):
         "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64 in/out; double-float chords, lookups and triangular products",
         "data": "synthetic white-noise maps, Gaussian deflections of 2.5 arcmin rms",
-        "config": {"workload": "tabulated inverse: lensing Nside 4096 (y = 1, 2) and supersampling "
-                               "Nside 2048 -> 4096 (y = 1, 2), lmax 4096 (damping l = 2500), FP64 and mixed",
+        "config": {"workload": "tabulated inverse: lensing Nside 4096 T (y = 1, 2; FP64 and mixed), "
+                               "supersampling Nside 2048 -> 4096 (y = 1, 2; FP64 and mixed), lensing Nside 4096 "
+                               "Q/U (spin 2, c3 spectra, y = 1, 2; FP64 and mixed), lmax 4096",
                    "batch_points": BATCH, "l2": "inputs larger than L2 (1.6 GB map, 268 MB of deflections)"},
         "fp64": {"value": res["lens_y1_fp64"]["value"], "ms_per_step": res["lens_y1_fp64"]["ms_per_step"]},
         "mixed_over_fp64": ratios, "arms": res,

@@ -1247,6 +1247,259 @@ __global__ void __launch_bounds__(APPLY_WARPS * 32) apply_kernel_df(ApplyArgs a)
     }
 }
 
+// ----------------------------------------------- spin 2, double-float
+// Mixed spin-2 plans: a double-float frame table ((cos phi, sin phi), (z, s) as
+// float pairs, 32 B per pixel) and complex double-float L^-1 blocks (float4 per
+// entry: re.hi, re.lo, im.hi, im.lo); chords, correlation lookups, transport
+// phases and the complex triangular products in double-float.
+__global__ void pixframe_df_kernel(int64_t N, float4 *pvf) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= 12 * N * N) return;
+    double c, sn, z, s;
+    pix_frame(N, p, c, sn, z, s);
+    const df a = split_double(c), b = split_double(sn), d = split_double(z), e = split_double(s);
+    pvf[2 * p] = make_float4(a.hi, a.lo, b.hi, b.lo);
+    pvf[2 * p + 1] = make_float4(d.hi, d.lo, e.hi, e.lo);
+}
+
+__global__ void to_df_c_kernel(const double2 *src, float4 *dst, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double2 v = src[i];
+    const df r = split_double(v.x), m = split_double(v.y);
+    dst[i] = make_float4(r.hi, r.lo, m.hi, m.lo);
+}
+
+// c = xi+(t)/xi+(0) exp(2i(a_tm - a_mt)) and (Q, U) of member m in double-float
+__device__ __forceinline__ bool member_s2_df(const ApplyArgs &a, int32_t m, df tx, df ty, df tz, df ts, df tc,
+                                            df tsn, float tmaxf, Cx<df> &cv, Cx<df> &yv, bool &win) {
+    if (m < 0) return false;
+    const float4 f0 = __ldg(a.pvf + 2 * m), f1 = __ldg(a.pvf + 2 * m + 1);
+    const df mc{f0.x, f0.y}, msn{f0.z, f0.w}, mz{f1.x, f1.y}, ms{f1.z, f1.w};
+    const df mx = df_mul(ms, mc), my = df_mul(ms, msn);
+    const df dx = df_add_fast(mx, df_neg(tx)), dy = df_add_fast(my, df_neg(ty)), dz = df_add_fast(mz, df_neg(tz));
+    const df t = df_add_fast(df_add_fast(df_mul(dx, dx), df_mul(dy, dy)), df_mul(dz, dz));
+    win |= t.hi > tmaxf;
+    const df f = table_eval<df>(a.tab, t);
+    const Cx<df> ph = pair_phase<df, 2>(dx, dy, dz, tz, ts, tc, tsn, mz, ms, mc, msn);
+    cv.re = df_mul(f, ph.re);
+    cv.im = df_mul(f, ph.im);
+    const double2 q = __ldg(reinterpret_cast<const double2 *>(a.map) + m);
+    yv.re = split_double(q.x);
+    yv.im = split_double(q.y);
+    return true;
+}
+
+// z += e x for complex double-float e (imaginary part times msign) and x
+__device__ __forceinline__ void cmac_df(dfacc &zr, dfacc &zi, const df er, const df ei, const df xr, const df xi) {
+    dfacc_add_prod(zr, er, xr);
+    dfacc_sub_prod(zr, ei, xi);
+    dfacc_add_prod(zi, er, xi);
+    dfacc_add_prod(zi, ei, xr);
+}
+
+__device__ __forceinline__ df shfl_df2(df v, int src) {
+    return {__shfl_sync(FULL, v.hi, src), __shfl_sync(FULL, v.lo, src)};
+}
+
+template <int K>
+__global__ void __launch_bounds__(APPLY_WARPS * 32) apply_kernel_s2_df(ApplyArgs a) {
+    __shared__ df stx[APPLY_WARPS][32], sty[APPLY_WARPS][32], stz[APPLY_WARPS][32];
+    __shared__ df sts[APPLY_WARPS][32], stc[APPLY_WARPS][32], stn[APPLY_WARPS][32];
+    __shared__ int64_t scp[APPLY_WARPS][32];
+    constexpr int KS = K > GROUP ? K : 1;
+    __shared__ df sxr[APPLY_WARPS][KS], sxi[APPLY_WARPS][KS], syr[APPLY_WARPS][KS], syi[APPLY_WARPS][KS];
+    __shared__ df rvr[APPLY_WARPS][32], rvi[APPLY_WARPS][32], rq[APPLY_WARPS][32];
+    __shared__ int32_t rsl[APPLY_WARPS][32];
+    __shared__ unsigned char rwin[APPLY_WARPS][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t ntiles = (a.count + 31) / 32;
+    const int64_t mirror_from = 6 * a.Nc * a.Nc + 2 * a.Nc;  // first pixel of coarse ring 2 Nc + 1
+    const float tmaxf = (float)a.tab.t_max;
+    const df zero{0.0f, 0.0f};
+    unsigned long long n_win = 0, n_nug = 0, n_fail = 0;
+    for (int64_t tile = (int64_t)blockIdx.x * APPLY_WARPS + wid; tile < ntiles;
+         tile += (int64_t)gridDim.x * APPLY_WARPS) {
+        {
+            double x = 0.0, y = 0.0, z = 1.0;
+            int64_t c = 0;
+            target_of(a, tile * 32 + lane, x, y, z, c);
+            const double sn = sqrt(x * x + y * y);
+            scp[wid][lane] = c;
+            stx[wid][lane] = split_double(x);
+            sty[wid][lane] = split_double(y);
+            stz[wid][lane] = split_double(z);
+            sts[wid][lane] = split_double(sn);
+            stc[wid][lane] = split_double(sn > 1e-12 ? x / sn : 1.0);
+            stn[wid][lane] = split_double(sn > 1e-12 ? y / sn : 0.0);
+        }
+        __syncwarp();
+        const int npt = a.count - tile * 32 < 32 ? (int)(a.count - tile * 32) : 32;
+        if constexpr (K <= GROUP) {
+            const int g = lane / GROUP, l = lane - g * GROUP, base = g * GROUP;
+            for (int q0 = 0; q0 < npt; q0 += 3) {
+                const int q = q0 + g;
+                const bool has = g < 3 && q < npt;
+                const int qq = has ? q : 0;
+                const int64_t c = scp[wid][qq];
+                const int32_t sl = has ? __ldg(a.slot + c) : 0;
+                const bool mir = c >= mirror_from;
+                Cx<df> cv{zero, zero}, yv{zero, zero};
+                bool win = false;
+                if (has && l < K)
+                    member_s2_df(a, __ldg(a.members + c * K + l), stx[wid][qq], sty[wid][qq], stz[wid][qq],
+                                 sts[wid][qq], stc[wid][qq], stn[wid][qq], tmaxf, cv, yv, win);
+                const float4 *Lr = reinterpret_cast<const float4 *>(a.linvf) + (int64_t)sl * linv_len(K);
+                dfacc zcr{0.0f, 0.0f}, zci{0.0f, 0.0f}, zyr{0.0f, 0.0f}, zyi{0.0f, 0.0f};
+#pragma unroll
+                for (int j = 0; j < K; ++j) {
+                    const df xr = shfl_df2(cv.re, base + j), xi = df_neg(shfl_df2(cv.im, base + j));
+                    const df ur = shfl_df2(yv.re, base + j), ui = shfl_df2(yv.im, base + j);
+                    if (has && l < K && l >= j) {
+                        const float4 e4 = __ldg(Lr + col_start(K, j) + l - j);
+                        const df er{e4.x, e4.y}, ei = mir ? df{-e4.z, -e4.w} : df{e4.z, e4.w};
+                        cmac_df(zcr, zci, er, ei, xr, xi);
+                        cmac_df(zyr, zyi, er, ei, ur, ui);
+                    }
+                }
+                const df ar = dfacc_val(zcr), ai = dfacc_val(zci), br = dfacc_val(zyr), bi = dfacc_val(zyi);
+                df vr = df_add_fast(df_mul(ar, br), df_mul(ai, bi));
+                df vi = df_add_fast(df_mul(ar, bi), df_neg(df_mul(ai, br)));
+                df qs = df_add_fast(df_mul(ar, ar), df_mul(ai, ai));
+#pragma unroll
+                for (int o = 8; o >= 1; o >>= 1) {
+                    const df tr = shfl_df2(vr, lane + o), ti = shfl_df2(vi, lane + o), tq = shfl_df2(qs, lane + o);
+                    if (l < o && l + o < GROUP) {
+                        vr = df_add_fast(vr, tr);
+                        vi = df_add_fast(vi, ti);
+                        qs = df_add_fast(qs, tq);
+                    }
+                }
+                const unsigned wb = __ballot_sync(FULL, win);
+                if (has && l == 0) {
+                    rvr[wid][q] = vr;
+                    rvi[wid][q] = vi;
+                    rq[wid][q] = qs;
+                    rsl[wid][q] = sl;
+                    rwin[wid][q] = ((wb >> base) & ((1u << GROUP) - 1u)) != 0;
+                }
+            }
+        } else {
+            static_assert(K == 36, "the lane-step layout is laid out for K = 36");
+            for (int q = 0; q < npt; ++q) {
+                const int64_t c = scp[wid][q];
+                const int32_t sl = __ldg(a.slot + c);
+                const bool mir = c >= mirror_from;
+                const df tx = stx[wid][q], ty = sty[wid][q], tz = stz[wid][q];
+                const df ts = sts[wid][q], tc = stc[wid][q], tn = stn[wid][q];
+                const int32_t *mem = a.members + c * K;
+                Cx<df> c0{zero, zero}, y0{zero, zero}, c1{zero, zero}, y1{zero, zero};
+                bool win = false;
+                member_s2_df(a, __ldg(mem + lane), tx, ty, tz, ts, tc, tn, tmaxf, c0, y0, win);
+                if (lane + 32 < K) member_s2_df(a, __ldg(mem + lane + 32), tx, ty, tz, ts, tc, tn, tmaxf, c1, y1, win);
+                const float4 *Lr = reinterpret_cast<const float4 *>(a.linvf) + (int64_t)sl * linv_len(K);
+                __syncwarp();
+                sxr[wid][lane] = c0.re;
+                sxi[wid][lane] = df_neg(c0.im);
+                syr[wid][lane] = y0.re;
+                syi[wid][lane] = y0.im;
+                if (lane < K - 32) {
+                    sxr[wid][32 + lane] = c1.re;
+                    sxi[wid][32 + lane] = df_neg(c1.im);
+                    syr[wid][32 + lane] = y1.re;
+                    syi[wid][32 + lane] = y1.im;
+                }
+                __syncwarp();
+                const int pp = lane >> 1, odd = lane & 1;
+                dfacc acr{0.0f, 0.0f}, aci{0.0f, 0.0f}, ayr{0.0f, 0.0f}, ayi{0.0f, 0.0f};
+                dfacc zcr{0.0f, 0.0f}, zci{0.0f, 0.0f}, zyr{0.0f, 0.0f}, zyi{0.0f, 0.0f};
+#pragma unroll
+                for (int u = 0; u < LS_STEPS; ++u) {
+                    const int t = odd ? LS_STEPS + u : u;
+                    if (!odd && u == pp + 1) {
+                        acr = zcr;
+                        aci = zci;
+                        ayr = zyr;
+                        ayi = zyi;
+                        zcr = zci = zyr = zyi = dfacc{0.0f, 0.0f};
+                    }
+                    int j = t <= pp ? t : t - pp - 1;
+                    j = j < K ? j : K - 1;  // the zero pad
+                    const float4 e4 = __ldg(Lr + u * 32 + lane);
+                    const df er{e4.x, e4.y}, ei = mir ? df{-e4.z, -e4.w} : df{e4.z, e4.w};
+                    cmac_df(zcr, zci, er, ei, sxr[wid][j], sxi[wid][j]);
+                    cmac_df(zyr, zyi, er, ei, syr[wid][j], syi[wid][j]);
+                }
+                const df b0r = dfacc_val(zcr), b0i = dfacc_val(zci), b1r = dfacc_val(zyr), b1i = dfacc_val(zyi);
+                const df bcr = df_add_fast(b0r, shfl_xor_df(b0r, 1)), bci = df_add_fast(b0i, shfl_xor_df(b0i, 1));
+                const df byr = df_add_fast(b1r, shfl_xor_df(b1r, 1)), byi = df_add_fast(b1i, shfl_xor_df(b1i, 1));
+                dfacc tcr{0.0f, 0.0f}, tci{0.0f, 0.0f}, tyr{0.0f, 0.0f}, tyi{0.0f, 0.0f};
+                {
+                    const int g = lane >> 2;
+#pragma unroll
+                    for (int t = 0; t < LS_TAIL; ++t) {
+                        const int j = g + 8 * t < K ? g + 8 * t : K - 1;  // zero entries past the diagonal
+                        const float4 e4 = __ldg(Lr + (LS_STEPS + t) * 32 + lane);
+                        const df er{e4.x, e4.y}, ei = mir ? df{-e4.z, -e4.w} : df{e4.z, e4.w};
+                        cmac_df(tcr, tci, er, ei, sxr[wid][j], sxi[wid][j]);
+                        cmac_df(tyr, tyi, er, ei, syr[wid][j], syi[wid][j]);
+                    }
+                }
+                df t1r = dfacc_val(tcr), t1i = dfacc_val(tci), t2r = dfacc_val(tyr), t2i = dfacc_val(tyi);
+#pragma unroll
+                for (int o = 4; o < 32; o <<= 1) {
+                    t1r = df_add_fast(t1r, shfl_xor_df(t1r, o));
+                    t1i = df_add_fast(t1i, shfl_xor_df(t1i, o));
+                    t2r = df_add_fast(t2r, shfl_xor_df(t2r, o));
+                    t2i = df_add_fast(t2i, shfl_xor_df(t2i, o));
+                }
+                const df aar = dfacc_val(acr), aai = dfacc_val(aci), abr = dfacc_val(ayr), abi = dfacc_val(ayi);
+                df vr = zero, vi = zero, qc = zero;
+                if (!odd) {  // even lanes count rows p and 31 - p, lanes 0..3 rows 32..35, each once
+                    vr = df_add_fast(df_add_fast(df_mul(aar, abr), df_mul(aai, abi)),
+                                     df_add_fast(df_mul(bcr, byr), df_mul(bci, byi)));
+                    vi = df_add_fast(df_add_fast(df_mul(aar, abi), df_neg(df_mul(aai, abr))),
+                                     df_add_fast(df_mul(bcr, byi), df_neg(df_mul(bci, byr))));
+                    qc = df_add_fast(df_add_fast(df_mul(aar, aar), df_mul(aai, aai)),
+                                     df_add_fast(df_mul(bcr, bcr), df_mul(bci, bci)));
+                }
+                if (lane < K - 32) {
+                    vr = df_add_fast(vr, df_add_fast(df_mul(t1r, t2r), df_mul(t1i, t2i)));
+                    vi = df_add_fast(vi, df_add_fast(df_mul(t1r, t2i), df_neg(df_mul(t1i, t2r))));
+                    qc = df_add_fast(qc, df_add_fast(df_mul(t1r, t1r), df_mul(t1i, t1i)));
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    vr = df_add_fast(vr, shfl_xor_df(vr, o));
+                    vi = df_add_fast(vi, shfl_xor_df(vi, o));
+                    qc = df_add_fast(qc, shfl_xor_df(qc, o));
+                }
+                const bool any_win = __any_sync(FULL, win);
+                if (lane == 0) {
+                    rvr[wid][q] = vr;
+                    rvi[wid][q] = vi;
+                    rq[wid][q] = qc;
+                    rsl[wid][q] = sl;
+                    rwin[wid][q] = any_win;
+                }
+            }
+        }
+        __syncwarp();
+        if (lane < npt)
+            finish_point_s2(a, tile * 32 + lane, rsl[wid][lane], df_to(rvr[wid][lane]), df_to(rvi[wid][lane]),
+                            df_to(rq[wid][lane]), rwin[wid][lane] != 0, n_win, n_nug, n_fail);
+        __syncwarp();
+    }
+    const unsigned w_win = __reduce_add_sync(FULL, (unsigned)n_win);
+    const unsigned w_nug = __reduce_add_sync(FULL, (unsigned)n_nug);
+    const unsigned w_fail = __reduce_add_sync(FULL, (unsigned)n_fail);
+    if (lane == 0 && a.counters) {
+        if (w_win) atomicAdd(a.counters + CNT_WINDOW, (unsigned long long)w_win);
+        if (w_nug) atomicAdd(a.counters + CNT_NUGGET, (unsigned long long)w_nug);
+        if (w_fail) atomicAdd(a.counters + CNT_FAILED, (unsigned long long)w_fail);
+    }
+}
+
 }  // namespace paper
 }  // namespace flints
 
@@ -1345,8 +1598,6 @@ int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double
     if (precision != FLINTS_FP64 && precision != FLINTS_MIXED)
         return pfail(FLINTS_EINVAL, "flints_paper_plan: precision must be FLINTS_FP64 or FLINTS_MIXED");
     if (spin != 0 && spin != 2) return pfail(FLINTS_EINVAL, "flints_paper_plan: spin must be 0 or 2 (got %d)", spin);
-    if (spin == 2 && precision != FLINTS_FP64)
-        return pfail(FLINTS_EINVAL, "flints_paper_plan: spin-2 plans are FP64 (FLINTS_FP64)");
     if (spin == 0) cl_bb = nullptr;
     for (int l = 0; l <= lmax; ++l)
         if (!std::isfinite(cl[l]) || (cl_bb && !std::isfinite(cl_bb[l])))
@@ -1393,7 +1644,7 @@ int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double
     if (cl_bb) PALLOC(p->d_clbb, (size_t)(lmax + 1) * sizeof(double));
     if (precision == FLINTS_MIXED) {
         PALLOC(p->d_pvf, (size_t)12 * nside * nside * 2 * sizeof(float4));
-        PALLOC(p->d_linvf, (size_t)p->nslot * linv_len(p->K) * sizeof(float2));
+        PALLOC(p->d_linvf, (size_t)p->nslot * linv_len(p->K) * (spin == 2 ? 2 : 1) * sizeof(float2));
     } else {
         PALLOC(p->d_pv, (size_t)12 * nside * nside * 2 * sizeof(double2));
     }
@@ -1428,7 +1679,9 @@ int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double
     p->xi0 = xi0;
     if ((e = finish_table(p->d_f, p->d_g, p->n, p->h, xi0, p->d_c64, p->d_c32, st)) != cudaSuccess)
         return bail(e, "flints_paper_plan: table coefficients");
-    if (precision == FLINTS_MIXED)
+    if (precision == FLINTS_MIXED && spin == 2)
+        pixframe_df_kernel<<<(unsigned)((12 * nside * nside + 255) / 256), 256, 0, st>>>(nside, p->d_pvf);
+    else if (precision == FLINTS_MIXED)
         pixvec_df_kernel<<<(unsigned)((12 * nside * nside + 255) / 256), 256, 0, st>>>(nside, p->d_pvf);
     else if (spin == 2)
         pixframe_kernel<<<(unsigned)((12 * nside * nside + 255) / 256), 256, 0, st>>>(nside, p->d_pv);
@@ -1463,7 +1716,11 @@ int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double
     if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "flints_paper_plan: L^-1 kernel");
     if (precision == FLINTS_MIXED) {
         const int64_t nl = p->nslot * (int64_t)linv_len(p->K);
-        to_df_kernel<<<(unsigned)((nl + 255) / 256), 256, 0, st>>>(p->d_linv, p->d_linvf, nl);
+        if (spin == 2)
+            to_df_c_kernel<<<(unsigned)((nl + 255) / 256), 256, 0, st>>>(reinterpret_cast<const double2 *>(p->d_linv),
+                                                                        reinterpret_cast<float4 *>(p->d_linvf), nl);
+        else
+            to_df_kernel<<<(unsigned)((nl + 255) / 256), 256, 0, st>>>(p->d_linv, p->d_linvf, nl);
         if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "flints_paper_plan: double-float L^-1");
     }
     int scratch[4] = {0, 0, 0, 0};
@@ -1559,10 +1816,17 @@ static int paper_run(flints_paper_t p, int64_t nside_tgt, int64_t first, int64_t
     cudaStream_t st = (cudaStream_t)stream;
     const bool mixed = p->precision == FLINTS_MIXED;
     if (p->spin == 2) {
-        if (p->K == 9)
-            apply_kernel_s2<9><<<grid, APPLY_WARPS * 32, 0, st>>>(a);
-        else
-            apply_kernel_s2<36><<<grid, APPLY_WARPS * 32, 0, st>>>(a);
+        if (p->K == 9) {
+            if (mixed)
+                apply_kernel_s2_df<9><<<grid, APPLY_WARPS * 32, 0, st>>>(a);
+            else
+                apply_kernel_s2<9><<<grid, APPLY_WARPS * 32, 0, st>>>(a);
+        } else {
+            if (mixed)
+                apply_kernel_s2_df<36><<<grid, APPLY_WARPS * 32, 0, st>>>(a);
+            else
+                apply_kernel_s2<36><<<grid, APPLY_WARPS * 32, 0, st>>>(a);
+        }
     } else if (p->K == 9) {
         if (mixed)
             apply_kernel_df<9><<<grid, APPLY_WARPS * 32, 0, st>>>(a);

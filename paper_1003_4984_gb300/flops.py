@@ -82,20 +82,26 @@ def augmented_flops(K: int, mixed: bool) -> float:
     return chol + solve + P * (chord + 2 * table + phases + entries) + K * (2 * table + phases + entries)
 
 
-def paper_fp64_flops(K: int) -> float:
-    """FP64 flops per target of the tabulated-inverse route (spin 0): the K
-    covariances to the target (chord^2: 3 subtractions, 3 products, 2 additions;
-    cubic table evaluation: 2 for the abscissa, 3 multiply-adds), z_c = L^-1 c
-    and z_y = L^-1 y (K (K + 1) / 2 multiply-adds each), value z_c . z_y and
-    variance z_c . z_c (2K multiply-adds)."""
-    return K * (8 + 2 + 6) + 2 * K * (K + 1) + 2 * 2 * K
+def paper_fp64_flops(K: int, spin: int = 0) -> float:
+    """FP64 flops per target of the tabulated-inverse route: the K covariances
+    to the target (chord^2: 3 subtractions, 3 products, 2 additions; cubic table
+    evaluation: 2 for the abscissa, 3 multiply-adds; spin 2: the transport
+    phase, 34 flops, and 2 products), z_c = L^-1 conj(c) and z_y = L^-1 y
+    (K (K + 1) / 2 multiply-adds each, complex for spin 2: 4 real ones), value
+    and variance (2K multiply-adds, complex for spin 2)."""
+    cm = 4 if spin else 1
+    return K * (8 + 2 + 6 + (36 if spin else 0)) + cm * 2 * K * (K + 1) + cm * 2 * 2 * K
 
 
-def paper_mixed_fp32_flops(K: int) -> float:
+def paper_mixed_fp32_flops(K: int, spin: int = 0) -> float:
     """FP32 flops per target of the tabulated-inverse route in double-float: K
     chords (3 differences, 3 squares, 2 sums) and table lookups (a product and
-    three multiply-adds), K (K + 1) multiply-accumulates for z_c and z_y, and
-    the two dots (2K products and sums)."""
+    three multiply-adds), spin 2 also the member position (2 products) and the
+    transport phase (27 products, 16 sums, a reciprocal) times the lookup (2
+    products); K (K + 1) multiply-accumulates for z_c and z_y (4 real ones each
+    for spin 2), and the two dots (2K products and sums, complex for spin 2)."""
     chord = 3 * DF_ADD + 3 * DF_MUL + 2 * DF_ADD
     table = DF_MUL + 3 * (DF_MUL + DF_ADD)
-    return K * (chord + table) + K * (K + 1) * DF_MAC + 2 * K * (DF_MUL + DF_ADD)
+    cm = 4 if spin else 1
+    phase = (2 * DF_MUL + 27 * DF_MUL + 16 * DF_ADD + DF_SPECIAL + 2 * DF_MUL) if spin else 0
+    return K * (chord + table + phase) + cm * K * (K + 1) * DF_MAC + cm * 2 * K * (DF_MUL + DF_ADD)

@@ -299,14 +299,15 @@ def _spin2_solve_route(nside, m, tv, idx, tab, x0):
     return v, s2
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("nside,lmax,y", [(2, 12, 1), (8, 16, 1), (32, 64, 1), (4, 24, 2), (16, 32, 2), (32, 64, 2)])
-def test_spin2_lens_parity_whole_sky(fl, torch, nside, lmax, y):
+def test_spin2_lens_parity_whole_sky(fl, torch, nside, lmax, y, precision):
     # Q/U lensed with the paper stencil: the class's complex L^-1 (conjugated for the
     # southern classes) against the oracle's class route and per-target solve
     cl, bb, m, sigma = _spin2_inputs(nside, lmax, 400 + nside + y)
     npix = hp.npix(nside)
     defl = wl.random_deflection(npix, 401 + nside, rms=0.5 * _pixel_size(nside))
-    plan = fl.PaperPlan(nside, cl, y, "fp64", spin=2, cl_bb=bb)
+    plan = fl.PaperPlan(nside, cl, y, precision, spin=2, cl_bb=bb)
     t_max, n = fc.paper_grid_rule(cl, nside, y, bb)
     info = plan.info()
     assert info["spin"] == 2 and info["t_max"] == t_max and info["n_intervals"] == n
@@ -320,15 +321,16 @@ def test_spin2_lens_parity_whole_sky(fl, torch, nside, lmax, y):
     rv, rs2, idx, tv = fc.paper_lens(nside, y, m, defl, np.arange(npix), tab, x0, classes=True, spin=2)
     ov, os2 = _spin2_solve_route(nside, m, tv, idx, tab, x0)
     for a_v, a_s2 in ((rv, rs2), (ov, os2)):
-        assert np.max(np.abs(v - a_v)) <= TOL["fp64"] * sigma
-        assert np.max(np.abs(s2 - a_s2)) <= TOL["fp64"] * x0
+        assert np.max(np.abs(v - a_v)) <= TOL[precision] * sigma
+        assert np.max(np.abs(s2 - a_s2)) <= TOL[precision] * x0
     assert not np.any(to_host(st) & (fl.ST_WINDOW | fl.ST_FAILED))
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("nside,nout,y", [(16, 32, 1), (16, 32, 2)])
-def test_spin2_supersample_and_ragged(fl, torch, nside, nout, y):
+def test_spin2_supersample_and_ragged(fl, torch, nside, nout, y, precision):
     cl, bb, m, sigma = _spin2_inputs(nside, 2 * nside, 501)
-    plan = fl.PaperPlan(nside, cl, y, "fp64", spin=2, cl_bb=bb)
+    plan = fl.PaperPlan(nside, cl, y, precision, spin=2, cl_bb=bb)
     first, count = 777, 1501
     out, var = plan.supersample(torch.from_numpy(m).cuda(), nout, first=first, count=count)
     torch.cuda.synchronize()
@@ -337,8 +339,8 @@ def test_spin2_supersample_and_ragged(fl, torch, nside, nout, y):
     tab, x0, _, _ = _spin2_table(cl, bb, nside, y)
     rv, rs2, idx, tv = fc.paper_supersample(nside, nout, y, m, np.arange(first, first + count), tab, x0,
                                             classes=True, spin=2)
-    assert np.max(np.abs(v - rv)) <= TOL["fp64"] * sigma
-    assert np.max(np.abs(to_host(var) - rs2)) <= TOL["fp64"] * x0
+    assert np.max(np.abs(v - rv)) <= TOL[precision] * sigma
+    assert np.max(np.abs(to_host(var) - rs2)) <= TOL[precision] * x0
 
 
 def test_spin2_linv_blocks(fl, torch):
