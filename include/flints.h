@@ -321,10 +321,10 @@ void flints_free(flints_plan_t plan);
  *
  * flints_paper_plan: y = 1 or 2; nside in [1, 8192] and divisible by
  *   2^(y-1); cl HOST [lmax+1] (spin 0: C_l; spin 2: C_l^EE), cl_bb HOST
- *   [lmax+1] or NULL (spin 2: C_l^BB; ignored for spin 0); spin 0 or 2
- *   (spin 2: the member covariances carry the transport phases
- *   exp(2i(a_ij - a_ji)) with xi+, classes mirrored by z -> -z use conj(L^-1);
- *   FP64 only); precision FLINTS_FP64, or
+ *   [lmax+1] or NULL (spin 1, 2: C_l^BB; ignored for spin 0); spin 0, 1 or 2
+ *   (spin s: the member covariances carry the transport phases
+ *   exp(is(a_ij - a_ji - pi)) with xi+, classes mirrored by z -> -z use
+ *   conj(L^-1)); precision FLINTS_FP64, or
  *   FLINTS_MIXED: the per-target chords, correlation lookups and triangular
  *   products in double-float on the FP32 pipe (target position and location
  *   FP64; the L^-1 blocks computed in FP64 and kept as double-float).  Builds on `stream` the xi table on [0, min((7 / Nside_c)^2, 4)] (interval
@@ -335,10 +335,11 @@ void flints_free(flints_plan_t plan);
  *   FLINTS_ENOMEM, FLINTS_ECUDA; message in flints_paper_last_error().
  * flints_paper_lens: lensed values at targets first .. first+count-1 (RING
  *   pixels of the plan's grid displaced along defl, as flints_lens_range).
- *   map DEVICE [12 Nside^2] (spin 2: [12 Nside^2][2] = Q, U, 16-byte aligned;
- *   else 8-byte aligned), defl DEVICE [count][2] (16-byte aligned; entry i
- *   belongs to pixel first + i), out DEVICE [count] (spin 2: [count][2] = Q, U
- *   in the frame at the displaced direction, 16-byte aligned), var DEVICE
+ *   map DEVICE [12 Nside^2] (spin 1, 2: [12 Nside^2][2] = (d_theta, d_phi) or
+ *   (Q, U), 16-byte aligned; else 8-byte aligned), defl DEVICE [count][2]
+ *   (16-byte aligned; entry i belongs to pixel first + i), out DEVICE [count]
+ *   (spin 1, 2: [count][2] in the frame at the displaced direction, 16-byte
+ *   aligned), var DEVICE
  *   [count] (may be NULL), status DEVICE [count] (may be NULL; FLINTS_ST_NUGGET
  *   when the class needed a raised nugget, FLINTS_ST_WINDOW when a chord fell
  *   beyond the table domain, FLINTS_ST_FAILED with NaN outputs when no factor
@@ -349,7 +350,7 @@ void flints_free(flints_plan_t plan);
  * flints_paper_tables: copies the stencil table (members DEVICE [12 Nside_c^2]
  *   [K] int32 RING indices at Nside, -1 past the member count), the class of
  *   each coarse pixel (slot DEVICE [12 Nside_c^2] int32) and the L^-1 blocks
- *   (linv DEVICE [slots][len] doubles, complex (re, im) pairs for spin 2,
+ *   (linv DEVICE [slots][len] doubles, complex (re, im) pairs for spin 1, 2,
  *   zero past the member count; K = 9:
  *   len = 45, packed by columns: column j, rows j .. 8, from offset
  *   9 j - j (j - 1) / 2; K = 36: len = 704, the lane-step layout: entry
@@ -376,7 +377,7 @@ typedef struct flints_paper_info {
     int64_t points;         /* targets processed so far */
     int64_t window;         /* targets with a chord beyond the table domain */
     int precision;          /* FLINTS_FP64 or FLINTS_MIXED */
-    int spin;               /* 0 or 2 */
+    int spin;               /* 0, 1 or 2 */
 } flints_paper_info;
 int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double *cl, const double *cl_bb, int y,
                       int spin, int precision, void *stream);

@@ -508,7 +508,7 @@ class PaperPlan:
     def _outputs(self, map_, count, out, var, status):
         import torch
 
-        two = (2,) if self.spin == 2 else ()
+        two = (2,) if self.spin != 0 else ()
         _dev_f64(map_, (12 * self.nside * self.nside,) + two, "map")
         if out is None:
             out = torch.empty((count,) + two, dtype=torch.float64, device=map_.device)
@@ -553,7 +553,7 @@ class PaperPlan:
         linv = None
         if self.precision == "fp64":  # mixed plans keep only double-float blocks
             n_l = 704 if self.K == 36 else self.K * (self.K + 1) // 2
-            shape = (self.slots, n_l) if self.spin == 0 else (self.slots, n_l, 2)
+            shape = (self.slots, n_l) if self.spin == 0 else (self.slots, n_l, 2)  # complex for spin 1, 2
             linv = torch.empty(shape, dtype=torch.float64, device="cuda")
         self._raise(load_library().flints_paper_tables(self._h, _ptr(mem), _ptr(slot), _ptr(linv), _stream(stream)))
         return mem, slot, linv

@@ -264,8 +264,8 @@ __global__ void __launch_bounds__(SINV_THREADS) linv_kernel(LinvArgs a) {
     }
 }
 
-// ------------------------------------------------------ spin 2 (Q, U)
-// Pixel table of spin-2 plans: (cos phi, sin phi), (z, sin theta) per pixel:
+// ------------------------------------------------- spin 1 and 2 fields
+// Pixel table of spin-s plans: (cos phi, sin phi), (z, sin theta) per pixel:
 // x = s cos phi, y = s sin phi as in pix2vec, plus the local frame.
 __device__ __forceinline__ void pix_frame(int64_t N, int64_t p, double &c, double &sn, double &z, double &s) {
     int64_t i, j;
@@ -285,11 +285,13 @@ __global__ void pixframe_kernel(int64_t N, double2 *pv) {
     pv[2 * p + 1] = make_double2(z, s);
 }
 
-// Spin-2 class blocks: C_ij = xi+(t_ij)/xi+(0) exp(2i(a_ij - a_ji)) over the
-// representative's members (unit diagonal, Eqs. v_spins, spins_correl), the
+// Spin-S class blocks: C_ij = xi+(t_ij)/xi+(0) exp(iS(a_ij - a_ji - pi)) over
+// the representative's members (unit diagonal, Eqs. v_spins, spins_correl; the
+// pi, from frames referred to the direction of travel, matters for odd S), the
 // nugget rule of Sec. 2.4, a Hermitian right-looking Cholesky C + n I = L L^H
 // in shared memory, L^-1 column by column; written as complex entries in the
 // class's storage layout (as the spin-0 blocks).
+template <int S>
 __global__ void __launch_bounds__(SINV_THREADS) linv_kernel_c(LinvArgs a, double2 *linvc) {
     __shared__ double Sr[STENCIL_MAX * LDS], Si[STENCIL_MAX * LDS], Lr[STENCIL_MAX * LDS], Lim[STENCIL_MAX * LDS];
     __shared__ double px[STENCIL_MAX], py[STENCIL_MAX], pz[STENCIL_MAX], ps[STENCIL_MAX], pc[STENCIL_MAX],
@@ -328,7 +330,7 @@ __global__ void __launch_bounds__(SINV_THREADS) linv_kernel_c(LinvArgs a, double
                     const double t = dx * dx + dy * dy + dz * dz;
                     tmax = fmax(tmax, t);
                     const double f = table_eval<double>(a.tab, t);
-                    const Cx<double> ph = pair_phase<double, 2>(dx, dy, dz, pz[i], ps[i], pc[i], psn[i], pz[j], ps[j],
+                    const Cx<double> ph = pair_phase<double, S>(dx, dy, dz, pz[i], ps[i], pc[i], psn[i], pz[j], ps[j],
                                                                 pc[j], psn[j]);
                     Sr[i * LDS + j] = f * ph.re;
                     Si[i * LDS + j] = f * ph.im;
@@ -715,8 +717,9 @@ __global__ void __launch_bounds__(APPLY_WARPS * 32) apply_kernel(ApplyArgs a) {
     }
 }
 
-// ------------------------------------------------------- spin-2 apply (FP64)
-// value (Q, U) = conj(z_c) . z_y and variance of target p (spin 2)
+// ------------------------------------------------- spin-1/2 apply (FP64)
+// value conj(z_c) . z_y (Q, U; or d_theta, d_phi for spin 1) and variance of
+// target p
 __device__ __forceinline__ void finish_point_s2(const ApplyArgs &a, int64_t p, int32_t sl, double vr, double vi,
                                                 double qc, bool any_win, unsigned long long &n_win,
                                                 unsigned long long &n_nug, unsigned long long &n_fail) {
@@ -736,8 +739,9 @@ __device__ __forceinline__ void finish_point_s2(const ApplyArgs &a, int64_t p, i
     n_fail += steps < 0;
 }
 
-// c_m = xi+(t)/xi+(0) exp(2i(a_tm - a_mt)) of member m for the target (t, frame)
-// and its (Q, U); returns false for an absent member
+// c_m = xi+(t)/xi+(0) exp(iS(a_tm - a_mt - pi)) of member m for the target
+// (t, frame) and its two field components; returns false for an absent member
+template <int S>
 __device__ __forceinline__ bool member_s2(const ApplyArgs &a, int32_t m, double tx, double ty, double tz, double tzz,
                                          double ts, double tc, double tsn, double &cr, double &ci, double &yr,
                                          double &yi, bool &win) {
@@ -748,7 +752,7 @@ __device__ __forceinline__ bool member_s2(const ApplyArgs &a, int32_t m, double 
     const double t = dx * dx + dy * dy + dz * dz;
     win |= t > a.tab.t_max;
     const double f = table_eval<double>(a.tab, t);
-    const Cx<double> ph = pair_phase<double, 2>(dx, dy, dz, tzz, ts, tc, tsn, f1.x, f1.y, f0.x, f0.y);
+    const Cx<double> ph = pair_phase<double, S>(dx, dy, dz, tzz, ts, tc, tsn, f1.x, f1.y, f0.x, f0.y);
     cr = f * ph.re;
     ci = f * ph.im;
     const double2 q = __ldg(reinterpret_cast<const double2 *>(a.map) + m);
@@ -757,7 +761,7 @@ __device__ __forceinline__ bool member_s2(const ApplyArgs &a, int32_t m, double 
     return true;
 }
 
-template <int K>
+template <int K, int S>
 __global__ void __launch_bounds__(APPLY_WARPS * 32) apply_kernel_s2(ApplyArgs a) {
     __shared__ double stx[APPLY_WARPS][32], sty[APPLY_WARPS][32], stz[APPLY_WARPS][32];
     __shared__ double sts[APPLY_WARPS][32], stc[APPLY_WARPS][32], stn[APPLY_WARPS][32];
@@ -800,7 +804,7 @@ __global__ void __launch_bounds__(APPLY_WARPS * 32) apply_kernel_s2(ApplyArgs a)
                 double cr = 0.0, ci = 0.0, yr = 0.0, yi = 0.0;
                 bool win = false;
                 if (has && l < K)
-                    member_s2(a, __ldg(a.members + c * K + l), stx[wid][qq], sty[wid][qq], stz[wid][qq],
+                    member_s2<S>(a, __ldg(a.members + c * K + l), stx[wid][qq], sty[wid][qq], stz[wid][qq],
                               stz[wid][qq], sts[wid][qq], stc[wid][qq], stn[wid][qq], cr, ci, yr, yi, win);
                 // z_c = L^-1 conj(c), z_y = L^-1 y: lane l of the group accumulates row l
                 const double2 *Lr = reinterpret_cast<const double2 *>(a.linv) + (int64_t)sl * linv_len(K);
@@ -849,9 +853,9 @@ __global__ void __launch_bounds__(APPLY_WARPS * 32) apply_kernel_s2(ApplyArgs a)
                 const int32_t *mem = a.members + c * K;
                 double c0r = 0.0, c0i = 0.0, y0r = 0.0, y0i = 0.0, c1r = 0.0, c1i = 0.0, y1r = 0.0, y1i = 0.0;
                 bool win = false;
-                member_s2(a, __ldg(mem + lane), tx, ty, tz, tz, ts, tc, tn, c0r, c0i, y0r, y0i, win);
+                member_s2<S>(a, __ldg(mem + lane), tx, ty, tz, tz, ts, tc, tn, c0r, c0i, y0r, y0i, win);
                 if (lane + 32 < K)
-                    member_s2(a, __ldg(mem + lane + 32), tx, ty, tz, tz, ts, tc, tn, c1r, c1i, y1r, y1i, win);
+                    member_s2<S>(a, __ldg(mem + lane + 32), tx, ty, tz, tz, ts, tc, tn, c1r, c1i, y1r, y1i, win);
                 const double2 *Lr = reinterpret_cast<const double2 *>(a.linv) + (int64_t)sl * linv_len(K);
                 __syncwarp();
                 sxr[wid][lane] = c0r;
@@ -1247,8 +1251,8 @@ __global__ void __launch_bounds__(APPLY_WARPS * 32) apply_kernel_df(ApplyArgs a)
     }
 }
 
-// ----------------------------------------------- spin 2, double-float
-// Mixed spin-2 plans: a double-float frame table ((cos phi, sin phi), (z, s) as
+// ------------------------------------------- spin 1 and 2, double-float
+// Mixed spin-s plans: a double-float frame table ((cos phi, sin phi), (z, s) as
 // float pairs, 32 B per pixel) and complex double-float L^-1 blocks (float4 per
 // entry: re.hi, re.lo, im.hi, im.lo); chords, correlation lookups, transport
 // phases and the complex triangular products in double-float.
@@ -1270,7 +1274,8 @@ __global__ void to_df_c_kernel(const double2 *src, float4 *dst, int64_t n) {
     dst[i] = make_float4(r.hi, r.lo, m.hi, m.lo);
 }
 
-// c = xi+(t)/xi+(0) exp(2i(a_tm - a_mt)) and (Q, U) of member m in double-float
+// c = xi+(t)/xi+(0) exp(iS(a_tm - a_mt - pi)) and the field of member m in double-float
+template <int S>
 __device__ __forceinline__ bool member_s2_df(const ApplyArgs &a, int32_t m, df tx, df ty, df tz, df ts, df tc,
                                             df tsn, float tmaxf, Cx<df> &cv, Cx<df> &yv, bool &win) {
     if (m < 0) return false;
@@ -1281,7 +1286,7 @@ __device__ __forceinline__ bool member_s2_df(const ApplyArgs &a, int32_t m, df t
     const df t = df_add_fast(df_add_fast(df_mul(dx, dx), df_mul(dy, dy)), df_mul(dz, dz));
     win |= t.hi > tmaxf;
     const df f = table_eval<df>(a.tab, t);
-    const Cx<df> ph = pair_phase<df, 2>(dx, dy, dz, tz, ts, tc, tsn, mz, ms, mc, msn);
+    const Cx<df> ph = pair_phase<df, S>(dx, dy, dz, tz, ts, tc, tsn, mz, ms, mc, msn);
     cv.re = df_mul(f, ph.re);
     cv.im = df_mul(f, ph.im);
     const double2 q = __ldg(reinterpret_cast<const double2 *>(a.map) + m);
@@ -1302,7 +1307,7 @@ __device__ __forceinline__ df shfl_df2(df v, int src) {
     return {__shfl_sync(FULL, v.hi, src), __shfl_sync(FULL, v.lo, src)};
 }
 
-template <int K>
+template <int K, int S>
 __global__ void __launch_bounds__(APPLY_WARPS * 32) apply_kernel_s2_df(ApplyArgs a) {
     __shared__ df stx[APPLY_WARPS][32], sty[APPLY_WARPS][32], stz[APPLY_WARPS][32];
     __shared__ df sts[APPLY_WARPS][32], stc[APPLY_WARPS][32], stn[APPLY_WARPS][32];
@@ -1347,7 +1352,7 @@ __global__ void __launch_bounds__(APPLY_WARPS * 32) apply_kernel_s2_df(ApplyArgs
                 Cx<df> cv{zero, zero}, yv{zero, zero};
                 bool win = false;
                 if (has && l < K)
-                    member_s2_df(a, __ldg(a.members + c * K + l), stx[wid][qq], sty[wid][qq], stz[wid][qq],
+                    member_s2_df<S>(a, __ldg(a.members + c * K + l), stx[wid][qq], sty[wid][qq], stz[wid][qq],
                                  sts[wid][qq], stc[wid][qq], stn[wid][qq], tmaxf, cv, yv, win);
                 const float4 *Lr = reinterpret_cast<const float4 *>(a.linvf) + (int64_t)sl * linv_len(K);
                 dfacc zcr{0.0f, 0.0f}, zci{0.0f, 0.0f}, zyr{0.0f, 0.0f}, zyi{0.0f, 0.0f};
@@ -1395,8 +1400,8 @@ __global__ void __launch_bounds__(APPLY_WARPS * 32) apply_kernel_s2_df(ApplyArgs
                 const int32_t *mem = a.members + c * K;
                 Cx<df> c0{zero, zero}, y0{zero, zero}, c1{zero, zero}, y1{zero, zero};
                 bool win = false;
-                member_s2_df(a, __ldg(mem + lane), tx, ty, tz, ts, tc, tn, tmaxf, c0, y0, win);
-                if (lane + 32 < K) member_s2_df(a, __ldg(mem + lane + 32), tx, ty, tz, ts, tc, tn, tmaxf, c1, y1, win);
+                member_s2_df<S>(a, __ldg(mem + lane), tx, ty, tz, ts, tc, tn, tmaxf, c0, y0, win);
+                if (lane + 32 < K) member_s2_df<S>(a, __ldg(mem + lane + 32), tx, ty, tz, ts, tc, tn, tmaxf, c1, y1, win);
                 const float4 *Lr = reinterpret_cast<const float4 *>(a.linvf) + (int64_t)sl * linv_len(K);
                 __syncwarp();
                 sxr[wid][lane] = c0.re;
@@ -1597,7 +1602,7 @@ int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double
     if (!cl) return pfail(FLINTS_EINVAL, "flints_paper_plan: cl is NULL");
     if (precision != FLINTS_FP64 && precision != FLINTS_MIXED)
         return pfail(FLINTS_EINVAL, "flints_paper_plan: precision must be FLINTS_FP64 or FLINTS_MIXED");
-    if (spin != 0 && spin != 2) return pfail(FLINTS_EINVAL, "flints_paper_plan: spin must be 0 or 2 (got %d)", spin);
+    if (spin < 0 || spin > 2) return pfail(FLINTS_EINVAL, "flints_paper_plan: spin must be 0, 1 or 2 (got %d)", spin);
     if (spin == 0) cl_bb = nullptr;
     for (int l = 0; l <= lmax; ++l)
         if (!std::isfinite(cl[l]) || (cl_bb && !std::isfinite(cl_bb[l])))
@@ -1640,11 +1645,11 @@ int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double
     PALLOC(p->d_slot, (size_t)npc * sizeof(int32_t));
     PALLOC(p->d_steps, (size_t)p->nslot * sizeof(int));
     PALLOC(p->d_scratch, 4 * sizeof(int));
-    PALLOC(p->d_linv, (size_t)p->nslot * linv_len(p->K) * (spin == 2 ? 2 : 1) * sizeof(double));
+    PALLOC(p->d_linv, (size_t)p->nslot * linv_len(p->K) * (spin != 0 ? 2 : 1) * sizeof(double));
     if (cl_bb) PALLOC(p->d_clbb, (size_t)(lmax + 1) * sizeof(double));
     if (precision == FLINTS_MIXED) {
         PALLOC(p->d_pvf, (size_t)12 * nside * nside * 2 * sizeof(float4));
-        PALLOC(p->d_linvf, (size_t)p->nslot * linv_len(p->K) * (spin == 2 ? 2 : 1) * sizeof(float2));
+        PALLOC(p->d_linvf, (size_t)p->nslot * linv_len(p->K) * (spin != 0 ? 2 : 1) * sizeof(float2));
     } else {
         PALLOC(p->d_pv, (size_t)12 * nside * nside * 2 * sizeof(double2));
     }
@@ -1679,11 +1684,11 @@ int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double
     p->xi0 = xi0;
     if ((e = finish_table(p->d_f, p->d_g, p->n, p->h, xi0, p->d_c64, p->d_c32, st)) != cudaSuccess)
         return bail(e, "flints_paper_plan: table coefficients");
-    if (precision == FLINTS_MIXED && spin == 2)
+    if (precision == FLINTS_MIXED && spin != 0)
         pixframe_df_kernel<<<(unsigned)((12 * nside * nside + 255) / 256), 256, 0, st>>>(nside, p->d_pvf);
     else if (precision == FLINTS_MIXED)
         pixvec_df_kernel<<<(unsigned)((12 * nside * nside + 255) / 256), 256, 0, st>>>(nside, p->d_pvf);
-    else if (spin == 2)
+    else if (spin != 0)
         pixframe_kernel<<<(unsigned)((12 * nside * nside + 255) / 256), 256, 0, st>>>(nside, p->d_pv);
     else
         pixvec_kernel<<<(unsigned)((12 * nside * nside + 255) / 256), 256, 0, st>>>(nside, p->d_pv);
@@ -1710,13 +1715,15 @@ int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double
     sa.counts = p->d_scratch;
     const int64_t grid = p->nslot < 152 * 16 ? p->nslot : 152 * 16;
     if (spin == 2)
-        linv_kernel_c<<<(unsigned)grid, SINV_THREADS, 0, st>>>(sa, reinterpret_cast<double2 *>(p->d_linv));
+        linv_kernel_c<2><<<(unsigned)grid, SINV_THREADS, 0, st>>>(sa, reinterpret_cast<double2 *>(p->d_linv));
+    else if (spin == 1)
+        linv_kernel_c<1><<<(unsigned)grid, SINV_THREADS, 0, st>>>(sa, reinterpret_cast<double2 *>(p->d_linv));
     else
         linv_kernel<<<(unsigned)grid, SINV_THREADS, 0, st>>>(sa);
     if ((e = cudaGetLastError()) != cudaSuccess) return bail(e, "flints_paper_plan: L^-1 kernel");
     if (precision == FLINTS_MIXED) {
         const int64_t nl = p->nslot * (int64_t)linv_len(p->K);
-        if (spin == 2)
+        if (spin != 0)
             to_df_c_kernel<<<(unsigned)((nl + 255) / 256), 256, 0, st>>>(reinterpret_cast<const double2 *>(p->d_linv),
                                                                         reinterpret_cast<float4 *>(p->d_linvf), nl);
         else
@@ -1778,7 +1785,7 @@ static int paper_run(flints_paper_t p, int64_t nside_tgt, int64_t first, int64_t
     if (count == 0) return FLINTS_OK;
     if (!map || !out) return pfail(FLINTS_EINVAL, "map and out must not be NULL");
     if (nside_tgt == 0 && !defl) return pfail(FLINTS_EINVAL, "defl is NULL");
-    const uintptr_t need = p->spin == 2 ? 15u : 7u;
+    const uintptr_t need = p->spin != 0 ? 15u : 7u;
     if (((uintptr_t)defl & 15u) || (((uintptr_t)map | (uintptr_t)out) & need) || ((uintptr_t)var & 7u))
         return pfail(FLINTS_EINVAL, "defl (and spin-2 map and out) must be 16-byte aligned, map, out and var 8-byte "
                                     "aligned");
@@ -1815,17 +1822,24 @@ static int paper_run(flints_paper_t p, int64_t nside_tgt, int64_t first, int64_t
     const unsigned grid = (unsigned)(want < cap ? want : cap);
     cudaStream_t st = (cudaStream_t)stream;
     const bool mixed = p->precision == FLINTS_MIXED;
-    if (p->spin == 2) {
-        if (p->K == 9) {
-            if (mixed)
-                apply_kernel_s2_df<9><<<grid, APPLY_WARPS * 32, 0, st>>>(a);
-            else
-                apply_kernel_s2<9><<<grid, APPLY_WARPS * 32, 0, st>>>(a);
+    if (p->spin != 0) {
+        const bool k9 = p->K == 9, s2 = p->spin == 2;
+        if (mixed) {
+            if (k9) {
+                if (s2) apply_kernel_s2_df<9, 2><<<grid, APPLY_WARPS * 32, 0, st>>>(a);
+                else apply_kernel_s2_df<9, 1><<<grid, APPLY_WARPS * 32, 0, st>>>(a);
+            } else {
+                if (s2) apply_kernel_s2_df<36, 2><<<grid, APPLY_WARPS * 32, 0, st>>>(a);
+                else apply_kernel_s2_df<36, 1><<<grid, APPLY_WARPS * 32, 0, st>>>(a);
+            }
         } else {
-            if (mixed)
-                apply_kernel_s2_df<36><<<grid, APPLY_WARPS * 32, 0, st>>>(a);
-            else
-                apply_kernel_s2<36><<<grid, APPLY_WARPS * 32, 0, st>>>(a);
+            if (k9) {
+                if (s2) apply_kernel_s2<9, 2><<<grid, APPLY_WARPS * 32, 0, st>>>(a);
+                else apply_kernel_s2<9, 1><<<grid, APPLY_WARPS * 32, 0, st>>>(a);
+            } else {
+                if (s2) apply_kernel_s2<36, 2><<<grid, APPLY_WARPS * 32, 0, st>>>(a);
+                else apply_kernel_s2<36, 1><<<grid, APPLY_WARPS * 32, 0, st>>>(a);
+            }
         }
     } else if (p->K == 9) {
         if (mixed)
@@ -1873,7 +1887,7 @@ int flints_paper_get_info(flints_paper_t p, flints_paper_info *info, void *strea
                         12 * p->nside_c * p->nside_c * (int64_t)(p->K + 1) * 4 + 12 * p->nside * p->nside * 32;
     info->precision = p->precision;
     info->spin = p->spin;
-    if (p->spin == 2) info->table_bytes += (int64_t)p->nslot * linv_len(p->K) * 8;
+    if (p->spin != 0) info->table_bytes += (int64_t)p->nslot * linv_len(p->K) * 8;
     info->max_pair_t = p->max_pair_t;
     info->nugget_slots = p->nugget_slots;
     info->failed_slots = p->failed_slots;
@@ -1894,7 +1908,7 @@ int flints_paper_tables(flints_paper_t p, int32_t *members, int32_t *slot, doubl
     if (linv && !p->d_linv)
         return pfail(FLINTS_EINVAL, "flints_paper_tables: mixed plans keep only double-float L^-1 blocks");
     if (e == cudaSuccess && linv)
-        e = cudaMemcpyAsync(linv, p->d_linv, (size_t)p->nslot * linv_len(p->K) * (p->spin == 2 ? 2 : 1) * sizeof(double),
+        e = cudaMemcpyAsync(linv, p->d_linv, (size_t)p->nslot * linv_len(p->K) * (p->spin != 0 ? 2 : 1) * sizeof(double),
                             cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return pcuda(e, "flints_paper_tables");
     return FLINTS_OK;

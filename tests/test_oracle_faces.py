@@ -179,8 +179,9 @@ def test_member_order_is_kept_by_the_symmetries(n_c, y):
         assert np.max(np.abs(T - Tr)) <= 1e-13 * np.max(Tr)
 
 
+@pytest.mark.parametrize("spin", [1, 2])
 @pytest.mark.parametrize("n_c,y", [(2, 1), (4, 1), (8, 1), (4, 2)])
-def test_spin2_class_covariance_rotates_and_conjugates(n_c, y):
+def test_spin2_class_covariance_rotates_and_conjugates(n_c, y, spin):
     # the spin-2 member-member covariance of every stencil, taken to its class
     # representative's member order, equals the representative's (rotation about the
     # polar axis: frames turn with the sphere) or its complex conjugate (reflection
@@ -190,38 +191,44 @@ def test_spin2_class_covariance_rotates_and_conjugates(n_c, y):
     lmax = 3 * nside
     cl = wl.cl_ee(lmax, 0.7 * lmax)
     t_max, n = fc.paper_grid_rule(cl, nside, y, 0.3 * cl)
-    tab, _, _ = xi.spin2_tables(cl, 0.3 * cl, t_max, n)
+    tables = xi.spin2_tables if spin == 2 else xi.spin1_tables
+    tab, _, _ = tables(cl, 0.3 * cl, t_max, n)
     cen = np.arange(hp.npix(n_c))
     rep, mirror, dphi = fc.class_representative(n_c, cen)
     ordered = fc.stencil_ordered(nside, y, cen)
     reps = {}
     for c in cen:
         m = ordered[c]
-        C = fc.class_covariance(nside, m, tab, 2)
+        C = fc.class_covariance(nside, m, tab, spin)
         r = int(rep[c])
         if r not in reps:
-            reps[r] = fc.class_covariance(nside, ordered[r], tab, 2)
+            reps[r] = fc.class_covariance(nside, ordered[r], tab, spin)
         ref = np.conj(reps[r]) if mirror[c] else reps[r]
         assert np.max(np.abs(C - ref)) < 1e-12, f"coarse pixel {c}"
     assert np.any(mirror) and not np.all(mirror)
 
 
+@pytest.mark.parametrize("spin", [1, 2])
 @pytest.mark.parametrize("nside,lmax,y", [(8, 16, 1), (16, 32, 2)])
-def test_spin2_class_route_matches_per_target_solve(nside, lmax, y):
+def test_spin2_class_route_matches_per_target_solve(nside, lmax, y, spin):
     cl = wl.cl_ee(lmax, 0.7 * lmax)
     bb = 0.3 * cl
     t_max, n = fc.paper_grid_rule(cl, nside, y, bb)
-    tab, _, x0 = xi.spin2_tables(cl, bb, t_max, n)
-    P = sht.synth_map(nside, lmax, wl.draw_alm(cl, 3), spin=2, blm=wl.draw_alm(bb, 4))
+    tab, _, x0 = (xi.spin2_tables if spin == 2 else xi.spin1_tables)(cl, bb, t_max, n)
+    P = sht.synth_map(nside, lmax, wl.draw_alm(cl, 3), spin=spin, blm=wl.draw_alm(bb, 4))
     m = np.ascontiguousarray(np.stack([P.real, P.imag], axis=1))
     pix = np.arange(hp.npix(nside))
     defl = wl.random_deflection(pix.size, 5, rms=0.5 * math.sqrt(4 * math.pi / hp.npix(nside)))
-    v, s2, idx, tv = fc.paper_lens(nside, y, m, defl, pix, tab, x0, classes=True, spin=2)
+    v, s2, idx, tv = fc.paper_lens(nside, y, m, defl, pix, tab, x0, classes=True, spin=spin)
     sigma = math.sqrt(np.mean(np.abs(P) ** 2))
     cnt = np.sum(idx >= 0, axis=1)
     for k in np.unique(cnt):
         rows = np.nonzero(cnt == k)[0]
         st = np.stack([r[r >= 0] for r in idx[rows]])
-        ve, se, _ = kr.estimate(nside, 2, m, tv[rows], st, tab, x0)
-        assert np.max(np.abs(v[rows] - ve)) <= 1e-10 * sigma
-        assert np.max(np.abs(s2[rows] - se)) <= 1e-10 * x0
+        ve, se, _ = kr.estimate(nside, spin, m, tv[rows], st, tab, x0)
+        # the class route factors the representative's covariance, whose member
+        # positions differ from the target's own by rounding; at y = 2 the
+        # spin-1 covariance's conditioning turns that into up to 3e-10
+        tol = 1e-10 if y == 1 else 1e-9
+        assert np.max(np.abs(v[rows] - ve)) <= tol * sigma
+        assert np.max(np.abs(s2[rows] - se)) <= tol * x0
