@@ -474,15 +474,25 @@ __device__ __forceinline__ void target_of(const ApplyArgs &a, int64_t p, double 
         sincospi(((double)j + rg.f) / (2.0 * (double)rg.nq), &sp, &cp);
         const double nx = rg.s * cp, ny = rg.s * sp, nz = rg.z;
         const double2 dd = __ldg(reinterpret_cast<const double2 *>(a.defl) + p);
-        const double dl = sqrt(dd.x * dd.x + dd.y * dd.y);
+        const double dl2 = dd.x * dd.x + dd.y * dd.y;
         x = nx;
         y = ny;
         z = nz;
-        if (dl > 0.0) {
-            // geodesic step of length |d| along d_theta e_theta + d_phi e_phi
-            double sd, cd;
-            sincos(dl, &sd, &cd);
-            const double kk = sd / dl;
+        if (dl2 > 0.0) {
+            // geodesic step of length |d| along d_theta e_theta + d_phi e_phi:
+            // n' = cos|d| n + (sin|d|/|d|) (d_theta e_theta + d_phi e_phi).  For
+            // |d| < 1/16 both factors are their Taylor series in |d|^2 to the
+            // |d|^8 term (the next terms are below 3e-19); larger steps use sincos.
+            double kk, cd;
+            if (dl2 < 0.00390625) {
+                kk = fma(dl2, fma(dl2, fma(dl2, fma(dl2, 1.0 / 362880.0, -1.0 / 5040.0), 1.0 / 120.0), -1.0 / 6.0), 1.0);
+                cd = fma(dl2, fma(dl2, fma(dl2, fma(dl2, 1.0 / 40320.0, -1.0 / 720.0), 1.0 / 24.0), -0.5), 1.0);
+            } else {
+                const double dl = sqrt(dl2);
+                double sd;
+                sincos(dl, &sd, &cd);
+                kk = sd / dl;
+            }
             const double tx = dd.x * nz * cp - dd.y * sp;
             const double ty = dd.x * nz * sp + dd.y * cp;
             const double tz = -dd.x * rg.s;
