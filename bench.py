@@ -143,6 +143,55 @@ def _oracle_worker(args):
 _TABLE_CACHE: dict = {}
 
 
+def _paper_oracle_worker(args):
+    first, count, y = args
+    sys.path.insert(0, ROOT)
+    from oracle import faces as fc
+    from oracle import xi
+
+    nside, lmax = 4096, 4096
+    cl = wl.cl_tt(lmax, 2500.0)
+    t_max, n = fc.paper_grid_rule(cl, nside, y)
+    if ("paper", t_max, n) not in _TABLE_CACHE:
+        _TABLE_CACHE[("paper", t_max, n)] = xi.spin0_table(cl, t_max, n)
+    tab, x0 = _TABLE_CACHE[("paper", t_max, n)]
+    pix = np.arange(first, first + count)
+    defl = wl.random_deflection(count, 77 + first)
+    t0 = time.time()
+    fc.paper_lens(nside, y, wl.HashedMap(12 * nside * nside, 9, 1), defl, pix, tab, x0, classes=True)
+    return count, time.time() - t0
+
+
+def cpu_oracle_paper(seconds: float, y: int = 1):
+    """Time the oracle's class route of the tabulated-inverse lensing (Nside 4096 T,
+    level y) on a bounded sample, on all host cores (spawned processes)."""
+    import multiprocessing as mp
+
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    per = 512
+    npix = 12 * 4096 * 4096
+    # chunk starts spread over the whole sky in a seeded random order, so that the
+    # calibration chunks sample caps and belt alike
+    spread = [int(v) for v in np.random.default_rng(5).integers(0, npix - per, 100_000)]
+    with ctx.Pool(cores) as pool:
+        # calibrate on one chunk per core taken across the sky (caps hold more classes)
+        pool.map(_paper_oracle_worker, [(spread[0], 16, y)] * cores)  # warm each process
+        t = time.time()
+        res = pool.map(_paper_oracle_worker, [(s_, per, y) for s_ in spread[:cores]])
+        rate = cores * per / max(time.time() - t, 1e-9)
+        chunks = max(cores, int(seconds * rate / per))
+        t = time.time()
+        res += pool.map(_paper_oracle_worker, [(s_, per, y) for s_ in spread[cores:cores + chunks]])
+        wall = time.time() - t
+        res = res[cores:]
+    pts = sum(r[0] for r in res)
+    return {"value": pts / wall, "unit": "pts/s", "cores": cores, "kind": "oracle",
+            "sample": f"{pts} targets of Nside 4096 T lensing, level {y}, in {chunks} chunks of {per} consecutive "
+                      f"RING pixels (hashed-normal map values, per-pixel deflections; the oracle's class route), "
+                      f"{wall:.1f} s wall on {cores} spawned processes"}
+
+
 def cpu_oracle(seconds: float, aug: bool = False):
     """Time the oracle (as it stands) on a bounded sample of the workload on all host cores."""
     import multiprocessing as mp
@@ -756,6 +805,8 @@ def run_paper(args):
     import paper_1003_4984_gb300 as fl
     from paper_1003_4984_gb300 import flops
 
+    # the CPU baseline runs first, before any GPU work (spawned pool)
+    cpu = cpu_oracle_paper(args.cpu_seconds, 1)
     fl.load_library()
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
@@ -850,7 +901,7 @@ def run_paper(args):
                      "frac": achieved / flops.FP32_PEAK_TFLOPS, "traffic": None,
                      "kernel": "paper::apply_kernel_df<9>", "peak_kind": "FP32 from unit counts and 2070 MHz",
                      "flops_per_point": flops.paper_mixed_fp32_flops(9)},
-        "clocks": clk.summary(0), "gpu_launches": steps}))
+        "cpu_baseline": cpu, "clocks": clk.summary(0), "gpu_launches": steps}))
 
 
 if __name__ == "__main__":
