@@ -393,3 +393,53 @@ def test_spin1_deflection_field_parity(fl, torch, nside, lmax, y, precision):
     for a_v, a_s2 in ((rv, rs2), (ov, os2)):
         assert np.max(np.abs(v - a_v)) <= TOL[precision] * sigma
         assert np.max(np.abs(to_host(var) - a_s2)) <= TOL[precision] * x0
+
+
+@pytest.fixture(scope="module")
+def qu4096():
+    """The Nside 4096, lmax 4096 Q/U workload (c3 spectra, B = 0): targets sampled on
+    rings of the north cap, the cap/belt boundary, the equator and the south cap,
+    deflected by 2.5 arcmin Gaussian steps, and the map synthesised exactly on the
+    rings their level-1 and level-2 stencils reach."""
+    W = wl.C3
+    cl, bb = W.cl()
+    samples = []
+    for ring in (5, W.nside // 2, W.nside, W.nside + 1, 2 * W.nside, 4 * W.nside - 9):
+        f, n_in = [int(x[0]) for x in hp.ring_info(W.nside, np.array([ring]))[:2]]
+        samples.append(np.arange(f + n_in // 7, f + n_in // 7 + 32))
+    pix = np.concatenate(samples)
+    d = wl.random_deflection(pix.size, 4343)
+    tv = kr.displace(W.nside, pix, d)
+    rings = np.unique(np.concatenate([hp.pix2ring(W.nside, s[s >= 0])[0]
+                                      for s in (fc.stencil(W.nside, tv, 1), fc.stencil(W.nside, tv, 2))]))
+    alm = wl.draw_alm(cl, W.seed_map)
+    bp, bv = sht.synth_rings(W.nside, rings, W.lmax, alm, spin=2)
+    m = np.zeros((W.npix, 2))
+    m[bp, 0] = bv.real
+    m[bp, 1] = bv.imag
+    return W, cl, bb, pix, d, m, float(np.sqrt(np.mean(np.abs(bv) ** 2)))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("y", [1, 2])
+def test_fullsize_4096_qu_sampled(fl, torch, qu4096, y, precision):
+    # the whole-sky Nside 4096 Q/U lensing call with the paper stencil; sampled
+    # outputs against the oracle's class route and per-target solve
+    W, cl, bb, pix, d, m, sigma = qu4096
+    defl = torch.zeros((W.npix, 2), dtype=torch.float64, device="cuda")
+    defl[torch.from_numpy(pix).cuda()] = torch.from_numpy(d).cuda()
+    plan = fl.PaperPlan(W.nside, cl, y, precision, spin=2, cl_bb=bb)
+    out, var = plan.lens(torch.from_numpy(m).cuda(), defl)
+    torch.cuda.synchronize()
+    o = to_host(out)[pix]
+    v = o[:, 0] + 1j * o[:, 1]
+    s2 = to_host(var)[pix]
+    assert plan.info()["window"] == 0
+    plan.close()
+    tab, x0, _, _ = _spin2_table(cl, bb, W.nside, y)
+    rv, rs2, idx, tv = fc.paper_lens(W.nside, y, m, d, pix, tab, x0, classes=True, spin=2)
+    ov, os2 = _spin2_solve_route(W.nside, m, tv, idx, tab, x0)
+    for a_v, a_s2 in ((rv, rs2), (ov, os2)):
+        assert np.max(np.abs(v - a_v)) <= TOL[precision] * sigma
+        assert np.max(np.abs(s2 - a_s2)) <= TOL[precision] * x0
