@@ -37,6 +37,8 @@ METRIC = "lensed pts/s at Nside 4096 spin-2 K=32, mixed vs FP64 @2e-4 rel err; p
 MIXED_DRAM_BYTES_PER_POINT = 13.868288e6 / (1 << 18)
 BATCH = 1 << 24
 W = wl.C3
+# where the nvidia-smi clock samples of the timed regions are written
+OUT_DIR = os.environ.get("FLINTS_BENCH_OUT", "/tmp")
 
 
 def parse():
@@ -310,8 +312,7 @@ def run_ours(args):
         return total, per
 
     plans["mixed"].reset_stats()
-    with Clocks(os.path.join(ROOT, "gpurun_out", f"bench_clocks_r{rank}.csv") if os.path.isdir(
-            os.path.join(ROOT, "gpurun_out")) else f"/tmp/bench_clocks_r{rank}.csv") as clk:
+    with Clocks(os.path.join(OUT_DIR, f"bench_clocks_r{rank}.csv")) as clk:
         total_ms, per = timed(plans["mixed"], args.steps, args.warmup)
     clocks = clk.summary(local)
     st = plans["mixed"].stats()
@@ -760,8 +761,7 @@ def run_pipeline(args):
     torch.cuda.synchronize(dev)
     steps = max(1, args.steps)
     parts = {"synth_T": [], "synth_QU": [], "synth_deflection": [], "lens_T": [], "lens_QU": [], "total": []}
-    with Clocks(os.path.join(ROOT, "gpurun_out", "bench_clocks_pipeline.csv") if os.path.isdir(
-            os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks_pipeline.csv") as clk:
+    with Clocks(os.path.join(OUT_DIR, "bench_clocks_pipeline.csv")) as clk:
         for _ in range(steps):
             step()
             torch.cuda.synchronize(dev)
@@ -818,8 +818,7 @@ def run_paper(args):
     out = torch.empty(BATCH, dtype=torch.float64, device=dev)
     var = torch.empty(BATCH, dtype=torch.float64, device=dev)
     res = {}
-    clk_path = os.path.join(ROOT, "gpurun_out", "bench_clocks_paper.csv") if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks_paper.csv"
+    clk_path = os.path.join(OUT_DIR, "bench_clocks_paper.csv")
     cl_ee, cl_bb = W.cl()
     with Clocks(clk_path) as clk:
         for task, nside, nout, spin in (("lens", 4096, None, 0), ("supersample", 2048, 4096, 0),
