@@ -326,8 +326,22 @@ def class_covariance(nside: int, members: np.ndarray, f_plus, spin: int = 0) -> 
     return C
 
 
+def class_covariance_aug(nside: int, members: np.ndarray, f_plus, f_minus, spin: int = 2) -> np.ndarray:
+    """The augmented (widely linear) member covariance of one stencil: the real
+    2K x 2K form (kriging.real_form) of the Hermitian part G (class_covariance)
+    and the pseudo-covariance C_ij = (-1)^s xi-(t_ij)/xi+(0) exp(is(a_ij + a_ji
+    + pi)) (zero diagonal) of P = Q + iU, in the order (Q_1..Q_K, U_1..U_K)."""
+    X = hp.pix2vec(nside, members)
+    K = members.size
+    G = class_covariance(nside, members, f_plus, spin)
+    T = np.sum((X[:, None, :] - X[None, :, :]) ** 2, axis=-1)
+    C = (-1.0) ** spin * f_minus(T.reshape(-1)).reshape(K, K) * kr.pseudo_phase(X[:, None, :], X[None, :, :], spin)
+    C[np.arange(K), np.arange(K)] = 0.0
+    return kr.real_form(G, C)
+
+
 def class_estimate(nside: int, y: int, maps: np.ndarray, targets: np.ndarray, f_plus, xi_zero: float,
-                   eps: float = kr.EPS_NUGGET, spin: int = 0):
+                   eps: float = kr.EPS_NUGGET, spin: int = 0, f_minus=None):
     """Estimate with the inverse tabulated per class (Sec. 2.4): for each class
     the representative's S + n I is factored (nugget rule of Sec. 2.4) and
     L^-1 found by direct inversion from the representative's own member
@@ -342,6 +356,13 @@ def class_estimate(nside: int, y: int, maps: np.ndarray, targets: np.ndarray, f_
     rotations about the polar axis carry the local frames along and leave the
     member-member phases unchanged, the reflection z -> -z turns every angle a
     into pi - a and conjugates them, so a mirrored class uses conj(L^-1).
+
+    Augmented (``f_minus`` given, spin 1, 2): the class factor is that of the
+    real 2K x 2K form A of (G, C) (class_covariance_aug); conjugating G and C
+    flips the sign of U, A -> D A D with D = diag(I, -I), so a mirrored class
+    uses D L^-1 D; per target the columns B of (<P_i P_0^*>, <P_i P_0>) and the
+    data (Q_i, U_i) give Z_Q, Z_U = L^-1 B and z_x = L^-1 x, the value
+    (Z_Q . z_x, Z_U . z_x) and the variance xi+(0) (1 - (|Z_Q|^2 + |Z_U|^2)/2).
     Returns (values, variances, stencils)."""
     n_c = nside >> (y - 1)
     cpix = vec2pix(n_c, targets)
@@ -356,9 +377,12 @@ def class_estimate(nside: int, y: int, maps: np.ndarray, targets: np.ndarray, f_
         ridx = ridx[ridx >= 0]
         K = ridx.size
         Xr = hp.pix2vec(nside, ridx)
-        L, _ = kr.factor_with_nugget(class_covariance(nside, ridx, f_plus, spin)[None], eps)
-        eye = np.eye(K, dtype=L.dtype)[None]
-        Linv = np.stack([kr.forward_solve(L, eye[:, :, k]) for k in range(K)], axis=2)[0]
+        aug = spin != 0 and f_minus is not None
+        A = class_covariance_aug(nside, ridx, f_plus, f_minus, spin) if aug else class_covariance(nside, ridx, f_plus,
+                                                                                                  spin)
+        L, _ = kr.factor_with_nugget(A[None], eps)
+        eye = np.eye(A.shape[0], dtype=L.dtype)[None]
+        Linv = np.stack([kr.forward_solve(L, eye[:, :, k]) for k in range(A.shape[0])], axis=2)[0]
         mem = np.stack([row[row >= 0] for row in idx[rows]])  # (n, K): every pixel of a class has K members
         X = hp.pix2vec(nside, mem)
         U = to_class_frame(X, mirror[rows], dphi[rows])
@@ -367,7 +391,30 @@ def class_estimate(nside: int, y: int, maps: np.ndarray, targets: np.ndarray, f_
         assert np.max(np.min(d, axis=2)) < 1e-9 / nside, "stencil not congruent to its class representative"
         assert np.all(np.sort(perm, axis=1) == np.arange(K)), "class map is not a bijection of the members"
         tgt = targets[rows][:, None, :]
-        c = f_plus(np.sum((tgt - X) ** 2, axis=-1))
+        t0 = np.sum((tgt - X) ** 2, axis=-1)
+        c = f_plus(t0)
+        if aug:
+            tb = np.broadcast_to(tgt, X.shape)
+            sgn = (-1.0) ** spin
+            g0 = c * kr.pair_phase(X, tb, spin)  # <P_i P_0^*> / xi+(0)
+            c0 = sgn * f_minus(t0) * kr.pseudo_phase(X, tb, spin)  # <P_i P_0> / xi+(0)
+            B = kr.real_form(g0[:, :, None], c0[:, :, None])  # (n, 2K, 2) in c's member order
+            xv = np.concatenate([maps[mem, 0], maps[mem, 1]], axis=1)
+            ar = np.arange(rows.size)[:, None]
+            pos = np.concatenate([perm, K + perm], axis=1)  # c's 2K slots in the representative's order
+            B_r = np.empty_like(B)
+            x_r = np.empty_like(xv)
+            B_r[ar, pos] = B
+            x_r[ar, pos] = xv
+            dsig = np.concatenate([np.ones(K), -np.ones(K)])
+            Lm = Linv * np.outer(dsig, dsig)  # D L^-1 D
+            Li = np.where(mirror[rows][:, None, None], Lm[None], Linv[None])
+            ZQ = np.einsum("pij,pj->pi", Li, B_r[:, :, 0])
+            ZU = np.einsum("pij,pj->pi", Li, B_r[:, :, 1])
+            zx = np.einsum("pij,pj->pi", Li, x_r)
+            val[rows] = np.sum(ZQ * zx, axis=1) + 1j * np.sum(ZU * zx, axis=1)
+            var[rows] = xi_zero * (1.0 - 0.5 * (np.sum(ZQ * ZQ, axis=1) + np.sum(ZU * ZU, axis=1)))
+            continue
         if spin == 0:
             yv = maps[mem]
         else:
@@ -387,13 +434,13 @@ def class_estimate(nside: int, y: int, maps: np.ndarray, targets: np.ndarray, f_
 
 
 def paper_lens(nside: int, y: int, maps: np.ndarray, defl: np.ndarray, pix: np.ndarray, f_plus, xi_zero: float,
-               classes: bool = False, spin: int = 0):
+               classes: bool = False, spin: int = 0, f_minus=None):
     """Lensed values with the paper's stencil at level y (Secs. 2.3-2.5);
     ``classes``: the inverse per class of central pixels (class_estimate)
     instead of S^-1 per target (spin 0 only)."""
     tv = kr.displace(nside, np.asarray(pix, dtype=np.int64), np.asarray(defl, dtype=np.float64))
     if classes:
-        v, s2, idx = class_estimate(nside, y, maps, tv, f_plus, xi_zero, spin=spin)
+        v, s2, idx = class_estimate(nside, y, maps, tv, f_plus, xi_zero, spin=spin, f_minus=f_minus)
         return v, s2, idx, tv
     assert spin == 0, "the per-target S^-1 route is spin 0"
     idx = stencil(nside, tv, y)

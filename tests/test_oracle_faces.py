@@ -232,3 +232,43 @@ def test_spin2_class_route_matches_per_target_solve(nside, lmax, y, spin):
         tol = 1e-10 if y == 1 else 1e-9
         assert np.max(np.abs(v[rows] - ve)) <= tol * sigma
         assert np.max(np.abs(s2[rows] - se)) <= tol * x0
+
+
+@pytest.mark.parametrize("n_c,y", [(4, 1), (8, 1), (4, 2)])
+def test_augmented_class_covariance_and_route(n_c, y):
+    # the augmented (xi+, xi-) member covariance of every stencil equals its class
+    # representative's A (rotation) or D A D, D = diag(I, -I) (reflection: G, C
+    # conjugate, U changes sign); the class route then matches the per-target
+    # augmented solve
+    nside = n_c << (y - 1)
+    lmax = 3 * nside
+    cl = wl.cl_ee(lmax, 0.7 * lmax)
+    bb = 0.3 * cl
+    t_max, n = fc.paper_grid_rule(cl, nside, y, bb)
+    tp, tm, x0 = xi.spin2_tables(cl, bb, t_max, n)
+    cen = np.arange(hp.npix(n_c))
+    rep, mirror, _ = fc.class_representative(n_c, cen)
+    ordered = fc.stencil_ordered(nside, y, cen)
+    reps = {}
+    for c in cen:
+        A = fc.class_covariance_aug(nside, ordered[c], tp, tm, 2)
+        r = int(rep[c])
+        if r not in reps:
+            reps[r] = fc.class_covariance_aug(nside, ordered[r], tp, tm, 2)
+        k = ordered[c].size
+        dsig = np.concatenate([np.ones(k), -np.ones(k)])
+        ref = reps[r] * np.outer(dsig, dsig) if mirror[c] else reps[r]
+        assert np.max(np.abs(A - ref)) < 1e-12, f"coarse pixel {c}"
+    P = sht.synth_map(nside, lmax, wl.draw_alm(cl, 3), spin=2, blm=wl.draw_alm(bb, 4))
+    m = np.ascontiguousarray(np.stack([P.real, P.imag], axis=1))
+    pix = np.arange(hp.npix(nside))
+    defl = wl.random_deflection(pix.size, 5, rms=0.5 * math.sqrt(4 * math.pi / hp.npix(nside)))
+    v, s2, idx, tv = fc.paper_lens(nside, y, m, defl, pix, tp, x0, classes=True, spin=2, f_minus=tm)
+    sigma = math.sqrt(np.mean(np.abs(P) ** 2))
+    cnt = np.sum(idx >= 0, axis=1)
+    for k in np.unique(cnt):
+        rows = np.nonzero(cnt == k)[0]
+        st = np.stack([r[r >= 0] for r in idx[rows]])
+        ve, se, _ = kr.estimate(nside, 2, m, tv[rows], st, tp, x0, f_minus=tm)
+        assert np.max(np.abs(v[rows] - ve)) <= 1e-10 * sigma
+        assert np.max(np.abs(s2[rows] - se)) <= 1e-10 * x0
