@@ -324,7 +324,11 @@ void flints_free(flints_plan_t plan);
  *   [lmax+1] or NULL (spin 1, 2: C_l^BB; ignored for spin 0); spin 0, 1 or 2
  *   (spin s: the member covariances carry the transport phases
  *   exp(is(a_ij - a_ji - pi)) with xi+, classes mirrored by z -> -z use
- *   conj(L^-1)); precision FLINTS_FP64, or
+ *   conj(L^-1)); flags 0 or FLINTS_SPIN2_AUGMENTED (spin 2, FP64: the widely
+ *   linear estimator with xi+ and xi-, the class factor that of the real
+ *   2K x 2K system of (Q_i, U_i), D L^-1 D with D = diag(I, -I) for mirrored
+ *   classes; L^-1 blocks 2K (2K + 1) / 2 doubles packed by columns);
+ *   precision FLINTS_FP64, or
  *   FLINTS_MIXED: the per-target chords, correlation lookups and triangular
  *   products in double-float on the FP32 pipe (target position and location
  *   FP64; the L^-1 blocks computed in FP64 and kept as double-float).  Builds on `stream` the xi table on [0, min((7 / Nside_c)^2, 4)] (interval
@@ -378,9 +382,10 @@ typedef struct flints_paper_info {
     int64_t window;         /* targets with a chord beyond the table domain */
     int precision;          /* FLINTS_FP64 or FLINTS_MIXED */
     int spin;               /* 0, 1 or 2 */
+    unsigned flags;         /* FLINTS_SPIN2_AUGMENTED or 0 */
 } flints_paper_info;
 int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double *cl, const double *cl_bb, int y,
-                      int spin, int precision, void *stream);
+                      int spin, int precision, unsigned flags, void *stream);
 int flints_paper_lens(flints_paper_t plan, int64_t first, int64_t count, const double *map, const double *defl,
                       double *out, double *var, uint8_t *status, void *stream);
 int flints_paper_supersample(flints_paper_t plan, int64_t nside_out, int64_t first, int64_t count,

@@ -47,7 +47,8 @@ class _PaperInfo(ctypes.Structure):
                 ("slots", ctypes.c_int64), ("t_max", ctypes.c_double), ("n_intervals", ctypes.c_int),
                 ("xi0", ctypes.c_double), ("table_bytes", ctypes.c_int64), ("max_pair_t", ctypes.c_double),
                 ("nugget_slots", ctypes.c_int64), ("failed_slots", ctypes.c_int64), ("points", ctypes.c_int64),
-                ("window", ctypes.c_int64), ("precision", ctypes.c_int), ("spin", ctypes.c_int)]
+                ("window", ctypes.c_int64), ("precision", ctypes.c_int), ("spin", ctypes.c_int),
+                ("flags", ctypes.c_uint)]
 
 
 class LaunchCfg(ctypes.Structure):
@@ -117,7 +118,7 @@ def load_library(path: str = LIB_PATH):
     lib.flints_synth_free.argtypes = [vp]
     lib.flints_synth_free.restype = None
     lib.flints_synth_last_error.restype = ctypes.c_char_p
-    lib.flints_paper_plan.argtypes = [ctypes.POINTER(vp), i64, c_int, dp, dp, c_int, c_int, c_int, vp]
+    lib.flints_paper_plan.argtypes = [ctypes.POINTER(vp), i64, c_int, dp, dp, c_int, c_int, c_int, ctypes.c_uint, vp]
     lib.flints_paper_lens.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp]
     lib.flints_paper_supersample.argtypes = [vp, i64, i64, i64, vp, vp, vp, vp, vp]
     lib.flints_paper_get_info.argtypes = [vp, ctypes.POINTER(_PaperInfo), vp]
@@ -477,7 +478,7 @@ class PaperPlan:
     the per-target arithmetic in double-float on the FP32 pipe)."""
 
     def __init__(self, nside: int, cl, y: int = 1, precision: str = "fp64", spin: int = 0, cl_bb=None,
-                 stream=None):
+                 augmented: bool = False, stream=None):
         lib = load_library()
         cl = np.ascontiguousarray(cl, dtype=np.float64)
         bb = None if cl_bb is None else np.ascontiguousarray(cl_bb, dtype=np.float64)
@@ -487,9 +488,10 @@ class PaperPlan:
         prec = {"fp64": FLINTS_FP64, "mixed": FLINTS_MIXED}[precision]
         dp = ctypes.POINTER(ctypes.c_double)
         h = ctypes.c_void_p()
+        self.augmented = bool(augmented)
         rc = lib.flints_paper_plan(ctypes.byref(h), self.nside, cl.size - 1, cl.ctypes.data_as(dp),
                                    None if bb is None else bb.ctypes.data_as(dp), self.y, self.spin, prec,
-                                   _stream(stream))
+                                   FLINTS_SPIN2_AUGMENTED if augmented else 0, _stream(stream))
         if rc != 0:
             raise FlintsError(f"flints error {rc}: {lib.flints_paper_last_error().decode()}")
         self._h = h
@@ -554,6 +556,8 @@ class PaperPlan:
         if self.precision == "fp64":  # mixed plans keep only double-float blocks
             n_l = 704 if self.K == 36 else self.K * (self.K + 1) // 2
             shape = (self.slots, n_l) if self.spin == 0 else (self.slots, n_l, 2)  # complex for spin 1, 2
+            if self.augmented:  # the real 2K x 2K factor packed by columns
+                shape = (self.slots, (2 * self.K) * (2 * self.K + 1) // 2)
             linv = torch.empty(shape, dtype=torch.float64, device="cuda")
         self._raise(load_library().flints_paper_tables(self._h, _ptr(mem), _ptr(slot), _ptr(linv), _stream(stream)))
         return mem, slot, linv

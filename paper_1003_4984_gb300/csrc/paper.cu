@@ -430,6 +430,7 @@ struct ApplyArgs {
     const float2 *linvf;           // double-float L^-1 blocks (mixed plans)
     const int *slot_steps;
     TableDev tab;
+    TableDev tabm;                 // augmented plans: xi-/xi+(0) on the same grid
     double xi0;
     unsigned long long *counters;  // points, nugget, -, window, failed
 };
@@ -727,6 +728,116 @@ __global__ void __launch_bounds__(APPLY_WARPS * 32) apply_kernel(ApplyArgs a) {
     }
 }
 
+// -------------------------------------------- augmented spin 2 (xi+, xi-)
+// Class blocks of the widely linear estimator: the real 2K x 2K form of the
+// Hermitian covariance G_ab = xi+(t)/xi+(0) exp(2i(a_ab - a_ba)) and the
+// pseudo-covariance C_ab = xi-(t)/xi+(0) exp(2i(a_ab + a_ba)) of P = Q + iU,
+// rows and columns (Q_0..Q_{K-1}, U_0..U_{K-1}):
+//   A[Q_a][Q_b] = Re(G + C),  A[U_a][Q_b] = Im(G + C),  A[U_a][U_b] = Re(G - C)
+// (absent members: unit rows), nugget rule of Sec. 2.4, Cholesky and L^-1 in
+// dynamic shared memory, L^-1 packed by columns (2K (2K + 1) / 2 entries).
+__global__ void __launch_bounds__(SINV_THREADS) linv_kernel_aug(LinvArgs a, TableDev tabm, double *linva) {
+    extern __shared__ double dsm[];
+    __shared__ double px[STENCIL_MAX], py[STENCIL_MAX], pz[STENCIL_MAX], ps[STENCIL_MAX], pc[STENCIL_MAX],
+        psn[STENCIL_MAX];
+    __shared__ int n_sh, bad;
+    const int tid = threadIdx.x, nt = blockDim.x, K = a.K, N = 2 * a.K, ld = N + 1;
+    double *S = dsm, *Li = dsm + N * ld;
+    for (int64_t sl = blockIdx.x; sl < a.nslot; sl += gridDim.x) {
+        const int64_t rep = slot_rep(a.Nc, sl);
+        const int32_t *mem = a.members + rep * K;
+        if (tid == 0) {
+            int n = 0;
+            while (n < K && mem[n] >= 0) ++n;
+            n_sh = n;
+        }
+        __syncthreads();
+        const int n = n_sh;
+        for (int m = tid; m < n; m += nt) {
+            pix_frame(a.N, mem[m], pc[m], psn[m], pz[m], ps[m]);
+            px[m] = ps[m] * pc[m];
+            py[m] = ps[m] * psn[m];
+        }
+        __syncthreads();
+        double tmax = 0.0;
+        double nug = NUGGET_EPS;
+        int steps = 0;
+        bool ok = false;
+        for (; steps <= MAX_NUGGET_STEPS; ++steps) {
+            for (int e = tid; e < N * N; e += nt) {
+                const int i = e / N, j = e - (e / N) * N;
+                if (j > i) continue;
+                const int mi = i < K ? i : i - K, mj = j < K ? j : j - K;
+                double v;
+                if (mi >= n || mj >= n) {
+                    v = i == j ? 1.0 : 0.0;
+                } else if (mi == mj) {
+                    v = i == j ? 1.0 + nug : 0.0;  // xi-(0) = 0: no coupling of Q_a and U_a
+                } else {
+                    const double dx = px[mj] - px[mi], dy = py[mj] - py[mi], dz = pz[mj] - pz[mi];
+                    const double t = dx * dx + dy * dy + dz * dz;
+                    tmax = fmax(tmax, t);
+                    const double fp = table_eval<double>(a.tab, t), fm = table_eval<double>(tabm, t);
+                    Cx<double> php, phm;
+                    pair_phases_pm<double>(dx, dy, dz, pz[mi], ps[mi], pc[mi], psn[mi], pz[mj], ps[mj], pc[mj], psn[mj],
+                                           php, phm);
+                    const double gr = fp * php.re, gi = fp * php.im, cr = fm * phm.re, ci = fm * phm.im;
+                    const bool ui = i >= K, uj = j >= K;
+                    v = !ui ? gr + cr : (uj ? gr - cr : gi + ci);
+                }
+                S[i * ld + j] = v;
+            }
+            if (tid == 0) bad = 0;
+            __syncthreads();
+            for (int kk = 0; kk < N; ++kk) {
+                if (tid == 0) {
+                    const double d = S[kk * ld + kk];
+                    if (d > 0.0) S[kk * ld + kk] = sqrt(d); else bad = 1;
+                }
+                __syncthreads();
+                if (bad) break;
+                const double lkk = S[kk * ld + kk];
+                for (int i = kk + 1 + tid; i < N; i += nt) S[i * ld + kk] /= lkk;
+                __syncthreads();
+                const int w = N - kk - 1;
+                for (int e = tid; e < w * w; e += nt) {
+                    const int i = kk + 1 + e / w, j = kk + 1 + (e - (e / w) * w);
+                    if (j <= i) S[i * ld + j] -= S[i * ld + kk] * S[j * ld + kk];
+                }
+                __syncthreads();
+            }
+            if (!bad) {
+                ok = true;
+                break;
+            }
+            nug *= 2.0;
+            __syncthreads();
+        }
+        if (ok) {
+            for (int col = tid; col < N; col += nt) {
+                for (int i = 0; i < col; ++i) Li[i * ld + col] = 0.0;
+                for (int i = col; i < N; ++i) {
+                    double acc = i == col ? 1.0 : 0.0;
+                    for (int m = col; m < i; ++m) acc = fma(-S[i * ld + m], Li[m * ld + col], acc);
+                    Li[i * ld + col] = acc / S[i * ld + i];
+                }
+            }
+        }
+        __syncthreads();
+        double *dst = linva + sl * (int64_t)(N * (N + 1) / 2);
+        for (int j = 0; j < N; ++j) {
+            for (int i = j + tid; i < N; i += nt) dst[col_start(N, j) + i - j] = ok ? Li[i * ld + j] : 0.0;
+        }
+        if (tmax > 0.0) atomicMax(a.max_t, (unsigned long long)__double_as_longlong(tmax));
+        if (tid == 0) {
+            a.slot_steps[sl] = ok ? steps : -1;
+            if (!ok) atomicAdd(a.counts + 1, 1);
+            else if (steps > 0) atomicAdd(a.counts, 1);
+        }
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------- spin-1/2 apply (FP64)
 // value conj(z_c) . z_y (Q, U; or d_theta, d_phi for spin 1) and variance of
 // target p
@@ -953,6 +1064,142 @@ __global__ void __launch_bounds__(APPLY_WARPS * 32) apply_kernel_s2(ApplyArgs a)
                     rsl[wid][q] = sl;
                     rwin[wid][q] = any_win;
                 }
+            }
+        }
+        __syncwarp();
+        if (lane < npt)
+            finish_point_s2(a, tile * 32 + lane, rsl[wid][lane], rvr[wid][lane], rvi[wid][lane], rq[wid][lane],
+                            rwin[wid][lane] != 0, n_win, n_nug, n_fail);
+        __syncwarp();
+    }
+    const unsigned w_win = __reduce_add_sync(FULL, (unsigned)n_win);
+    const unsigned w_nug = __reduce_add_sync(FULL, (unsigned)n_nug);
+    const unsigned w_fail = __reduce_add_sync(FULL, (unsigned)n_fail);
+    if (lane == 0 && a.counters) {
+        if (w_win) atomicAdd(a.counters + CNT_WINDOW, (unsigned long long)w_win);
+        if (w_nug) atomicAdd(a.counters + CNT_NUGGET, (unsigned long long)w_nug);
+        if (w_fail) atomicAdd(a.counters + CNT_FAILED, (unsigned long long)w_fail);
+    }
+}
+
+// Widely linear estimate per target: b_Q, b_U (the columns of (<P_i P_0^*>,
+// <P_i P_0>) in the real form) and x = (Q_i, U_i); Z_Q = L^-1 b_Q, Z_U = L^-1
+// b_U, z_x = L^-1 x; (Q, U) = (Z_Q . z_x, Z_U . z_x), variance xi+(0) (1 -
+// (|Z_Q|^2 + |Z_U|^2)/2).  A class mirrored by z -> -z uses D L^-1 D, D =
+// diag(I, -I): its Q-U entries change sign.  One target per warp; lane l owns
+// rows l + 32t of the 2K.
+template <int K>
+__global__ void __launch_bounds__(APPLY_WARPS * 32) apply_kernel_aug(ApplyArgs a) {
+    constexpr int N = 2 * K, T = (N + 31) / 32;
+    __shared__ double stx[APPLY_WARPS][32], sty[APPLY_WARPS][32], stz[APPLY_WARPS][32];
+    __shared__ double sts[APPLY_WARPS][32], stc[APPLY_WARPS][32], stn[APPLY_WARPS][32];
+    __shared__ int64_t scp[APPLY_WARPS][32];
+    __shared__ double sbq[APPLY_WARPS][N], sbu[APPLY_WARPS][N], sx[APPLY_WARPS][N];
+    __shared__ double rvr[APPLY_WARPS][32], rvi[APPLY_WARPS][32], rq[APPLY_WARPS][32];
+    __shared__ int32_t rsl[APPLY_WARPS][32];
+    __shared__ unsigned char rwin[APPLY_WARPS][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t ntiles = (a.count + 31) / 32;
+    const int64_t mirror_from = 6 * a.Nc * a.Nc + 2 * a.Nc;  // first pixel of coarse ring 2 Nc + 1
+    unsigned long long n_win = 0, n_nug = 0, n_fail = 0;
+    for (int64_t tile = (int64_t)blockIdx.x * APPLY_WARPS + wid; tile < ntiles;
+         tile += (int64_t)gridDim.x * APPLY_WARPS) {
+        {
+            double x = 0.0, y = 0.0, z = 1.0;
+            int64_t c = 0;
+            target_of(a, tile * 32 + lane, x, y, z, c);
+            const double sn = sqrt(x * x + y * y);
+            scp[wid][lane] = c;
+            stx[wid][lane] = x;
+            sty[wid][lane] = y;
+            stz[wid][lane] = z;
+            sts[wid][lane] = sn;
+            stc[wid][lane] = sn > 1e-12 ? x / sn : 1.0;
+            stn[wid][lane] = sn > 1e-12 ? y / sn : 0.0;
+        }
+        __syncwarp();
+        const int npt = a.count - tile * 32 < 32 ? (int)(a.count - tile * 32) : 32;
+        for (int q = 0; q < npt; ++q) {
+            const int64_t c = scp[wid][q];
+            const int32_t sl = __ldg(a.slot + c);
+            const bool mir = c >= mirror_from;
+            const double tx = stx[wid][q], ty = sty[wid][q], tz = stz[wid][q];
+            const double ts = sts[wid][q], tc = stc[wid][q], tn = stn[wid][q];
+            bool win = false;
+            __syncwarp();
+#pragma unroll
+            for (int h = 0; h < (K + 31) / 32; ++h) {
+                const int m = lane + 32 * h;
+                if (m < K) {
+                    const int32_t pm = __ldg(a.members + c * K + m);
+                    double bq0 = 0.0, bq1 = 0.0, bu0 = 0.0, bu1 = 0.0, xq = 0.0, xu = 0.0;
+                    if (pm >= 0) {
+                        const double2 f0 = __ldg(a.pv + 2 * pm), f1 = __ldg(a.pv + 2 * pm + 1);
+                        const double mx = f1.y * f0.x, my = f1.y * f0.y, mz = f1.x;
+                        const double dx = mx - tx, dy = my - ty, dz = mz - tz;
+                        const double t = dx * dx + dy * dy + dz * dz;
+                        win |= t > a.tab.t_max;
+                        const double fp = table_eval<double>(a.tab, t), fm = table_eval<double>(a.tabm, t);
+                        Cx<double> php, phm;  // of (target -> member); G_i0 takes the conjugate Hermitian phase
+                        pair_phases_pm<double>(dx, dy, dz, tz, ts, tc, tn, f1.x, f1.y, f0.x, f0.y, php, phm);
+                        const double gr = fp * php.re, gi = -fp * php.im, cr = fm * phm.re, ci = fm * phm.im;
+                        bq0 = gr + cr;
+                        bq1 = gi + ci;
+                        bu0 = ci - gi;
+                        bu1 = gr - cr;
+                        const double2 qu = __ldg(reinterpret_cast<const double2 *>(a.map) + pm);
+                        xq = qu.x;
+                        xu = qu.y;
+                    }
+                    sbq[wid][m] = bq0;
+                    sbq[wid][K + m] = bq1;
+                    sbu[wid][m] = bu0;
+                    sbu[wid][K + m] = bu1;
+                    sx[wid][m] = xq;
+                    sx[wid][K + m] = xu;
+                }
+            }
+            __syncwarp();
+            const double *Lr = a.linv + (int64_t)sl * (N * (N + 1) / 2);
+            double zq[T], zu[T], zx[T];
+#pragma unroll
+            for (int t = 0; t < T; ++t) zq[t] = zu[t] = zx[t] = 0.0;
+#pragma unroll 2
+            for (int j = 0; j < N; ++j) {
+                const double bqj = sbq[wid][j], buj = sbu[wid][j], xj = sx[wid][j];
+                const int cs = col_start(N, j) - j;
+#pragma unroll
+                for (int t = 0; t < T; ++t) {
+                    const int r = lane + 32 * t;
+                    if (r < N && r >= j) {
+                        double e = __ldg(Lr + cs + r);
+                        if (mir && ((r < K) != (j < K))) e = -e;
+                        zq[t] = fma(e, bqj, zq[t]);
+                        zu[t] = fma(e, buj, zu[t]);
+                        zx[t] = fma(e, xj, zx[t]);
+                    }
+                }
+            }
+            double vq = 0.0, vu = 0.0, nn = 0.0;
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                vq = fma(zq[t], zx[t], vq);
+                vu = fma(zu[t], zx[t], vu);
+                nn = fma(zq[t], zq[t], fma(zu[t], zu[t], nn));
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                vq += __shfl_xor_sync(FULL, vq, o);
+                vu += __shfl_xor_sync(FULL, vu, o);
+                nn += __shfl_xor_sync(FULL, nn, o);
+            }
+            const bool any_win = __any_sync(FULL, win);
+            if (lane == 0) {
+                rvr[wid][q] = vq;
+                rvi[wid][q] = vu;
+                rq[wid][q] = 0.5 * nn;
+                rsl[wid][q] = sl;
+                rwin[wid][q] = any_win;
             }
         }
         __syncwarp();
@@ -1537,7 +1784,10 @@ struct flints_paper_s {
     float4 *d_pvf;
     float2 *d_linvf;
     int precision, spin;
+    unsigned flags;
     double *d_clbb;
+    Coef64 *d_cm64;
+    float4 *d_cm32;
     unsigned long long *d_counters, *d_maxt;
     int64_t points;
 };
@@ -1571,6 +1821,8 @@ static void paper_release(flints_paper_s *p) {
     cudaFree(p->d_linv);
     cudaFree(p->d_pv);
     cudaFree(p->d_clbb);
+    cudaFree(p->d_cm64);
+    cudaFree(p->d_cm32);
     cudaFree(p->d_pvf);
     cudaFree(p->d_linvf);
     cudaFree(p->d_counters);
@@ -1600,7 +1852,7 @@ extern "C" {
 const char *flints_paper_last_error(void) { return g_perr; }
 
 int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double *cl, const double *cl_bb, int y,
-                      int spin, int precision, void *stream) {
+                      int spin, int precision, unsigned flags, void *stream) {
     if (!out) return pfail(FLINTS_EINVAL, "flints_paper_plan: out is NULL");
     *out = nullptr;
     if (y != 1 && y != 2) return pfail(FLINTS_EINVAL, "flints_paper_plan: level y must be 1 or 2 (got %d)", y);
@@ -1613,6 +1865,11 @@ int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double
     if (precision != FLINTS_FP64 && precision != FLINTS_MIXED)
         return pfail(FLINTS_EINVAL, "flints_paper_plan: precision must be FLINTS_FP64 or FLINTS_MIXED");
     if (spin < 0 || spin > 2) return pfail(FLINTS_EINVAL, "flints_paper_plan: spin must be 0, 1 or 2 (got %d)", spin);
+    if (flags & ~(unsigned)FLINTS_SPIN2_AUGMENTED)
+        return pfail(FLINTS_EINVAL, "flints_paper_plan: unknown flag bits 0x%x", flags);
+    const bool aug = (flags & FLINTS_SPIN2_AUGMENTED) != 0;
+    if (aug && (spin != 2 || precision != FLINTS_FP64))
+        return pfail(FLINTS_EINVAL, "flints_paper_plan: FLINTS_SPIN2_AUGMENTED needs a spin-2 FP64 plan");
     if (spin == 0) cl_bb = nullptr;
     for (int l = 0; l <= lmax; ++l)
         if (!std::isfinite(cl[l]) || (cl_bb && !std::isfinite(cl_bb[l])))
@@ -1628,6 +1885,7 @@ int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double
     p->lmax = lmax;
     p->precision = precision;
     p->spin = spin;
+    p->flags = flags;
     p->nslot = slot_count(p->nside_c);
     const double Dc = 7.0 / (double)p->nside_c;
     p->t_max = Dc * Dc < 4.0 ? Dc * Dc : 4.0;  // 4: the chord^2 of antipodal points
@@ -1655,7 +1913,12 @@ int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double
     PALLOC(p->d_slot, (size_t)npc * sizeof(int32_t));
     PALLOC(p->d_steps, (size_t)p->nslot * sizeof(int));
     PALLOC(p->d_scratch, 4 * sizeof(int));
-    PALLOC(p->d_linv, (size_t)p->nslot * linv_len(p->K) * (spin != 0 ? 2 : 1) * sizeof(double));
+    const int64_t lv = aug ? (int64_t)(2 * p->K) * (2 * p->K + 1) / 2 : (int64_t)linv_len(p->K) * (spin != 0 ? 2 : 1);
+    PALLOC(p->d_linv, (size_t)p->nslot * lv * sizeof(double));
+    if (aug) {
+        PALLOC(p->d_cm64, (size_t)p->n * sizeof(Coef64));
+        PALLOC(p->d_cm32, (size_t)p->n * 2 * sizeof(float4));
+    }
     if (cl_bb) PALLOC(p->d_clbb, (size_t)(lmax + 1) * sizeof(double));
     if (precision == FLINTS_MIXED) {
         PALLOC(p->d_pvf, (size_t)12 * nside * nside * 2 * sizeof(float4));
@@ -1694,6 +1957,8 @@ int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double
     p->xi0 = xi0;
     if ((e = finish_table(p->d_f, p->d_g, p->n, p->h, xi0, p->d_c64, p->d_c32, st)) != cudaSuccess)
         return bail(e, "flints_paper_plan: table coefficients");
+    if (aug && (e = finish_table(p->d_fm, p->d_gm, p->n, p->h, xi0, p->d_cm64, p->d_cm32, st)) != cudaSuccess)
+        return bail(e, "flints_paper_plan: xi- table coefficients");
     if (precision == FLINTS_MIXED && spin != 0)
         pixframe_df_kernel<<<(unsigned)((12 * nside * nside + 255) / 256), 256, 0, st>>>(nside, p->d_pvf);
     else if (precision == FLINTS_MIXED)
@@ -1724,7 +1989,16 @@ int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double
     sa.max_t = p->d_maxt;
     sa.counts = p->d_scratch;
     const int64_t grid = p->nslot < 152 * 16 ? p->nslot : 152 * 16;
-    if (spin == 2)
+    if (aug) {
+        TableDev tm = sa.tab;
+        tm.c64 = p->d_cm64;
+        tm.c32 = p->d_cm32;
+        const size_t dsm = (size_t)2 * (2 * p->K) * (2 * p->K + 1) * sizeof(double);
+        if ((e = cudaFuncSetAttribute(linv_kernel_aug, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm)) !=
+            cudaSuccess)
+            return bail(e, "flints_paper_plan: shared memory of the augmented factor");
+        linv_kernel_aug<<<(unsigned)grid, SINV_THREADS, dsm, st>>>(sa, tm, p->d_linv);
+    } else if (spin == 2)
         linv_kernel_c<2><<<(unsigned)grid, SINV_THREADS, 0, st>>>(sa, reinterpret_cast<double2 *>(p->d_linv));
     else if (spin == 1)
         linv_kernel_c<1><<<(unsigned)grid, SINV_THREADS, 0, st>>>(sa, reinterpret_cast<double2 *>(p->d_linv));
@@ -1824,6 +2098,9 @@ static int paper_run(flints_paper_t p, int64_t nside_tgt, int64_t first, int64_t
     a.tab.inv_h_hi = (float)p->inv_h;
     a.tab.inv_h_lo = (float)(p->inv_h - (double)a.tab.inv_h_hi);
     a.tab.n = p->n;
+    a.tabm = a.tab;
+    a.tabm.c64 = p->d_cm64;
+    a.tabm.c32 = p->d_cm32;
     a.xi0 = p->xi0;
     a.counters = p->d_counters;
     const int64_t tiles = (count + 31) / 32;
@@ -1832,7 +2109,12 @@ static int paper_run(flints_paper_t p, int64_t nside_tgt, int64_t first, int64_t
     const unsigned grid = (unsigned)(want < cap ? want : cap);
     cudaStream_t st = (cudaStream_t)stream;
     const bool mixed = p->precision == FLINTS_MIXED;
-    if (p->spin != 0) {
+    if (p->flags & FLINTS_SPIN2_AUGMENTED) {
+        if (p->K == 9)
+            apply_kernel_aug<9><<<grid, APPLY_WARPS * 32, 0, st>>>(a);
+        else
+            apply_kernel_aug<36><<<grid, APPLY_WARPS * 32, 0, st>>>(a);
+    } else if (p->spin != 0) {
         const bool k9 = p->K == 9, s2 = p->spin == 2;
         if (mixed) {
             if (k9) {
@@ -1897,7 +2179,11 @@ int flints_paper_get_info(flints_paper_t p, flints_paper_info *info, void *strea
                         12 * p->nside_c * p->nside_c * (int64_t)(p->K + 1) * 4 + 12 * p->nside * p->nside * 32;
     info->precision = p->precision;
     info->spin = p->spin;
-    if (p->spin != 0) info->table_bytes += (int64_t)p->nslot * linv_len(p->K) * 8;
+    info->flags = p->flags;
+    if (p->flags & FLINTS_SPIN2_AUGMENTED)
+        info->table_bytes += (int64_t)p->nslot * ((2 * p->K) * (2 * p->K + 1) / 2 - linv_len(p->K)) * 8;
+    else if (p->spin != 0)
+        info->table_bytes += (int64_t)p->nslot * linv_len(p->K) * 8;
     info->max_pair_t = p->max_pair_t;
     info->nugget_slots = p->nugget_slots;
     info->failed_slots = p->failed_slots;
@@ -1918,7 +2204,11 @@ int flints_paper_tables(flints_paper_t p, int32_t *members, int32_t *slot, doubl
     if (linv && !p->d_linv)
         return pfail(FLINTS_EINVAL, "flints_paper_tables: mixed plans keep only double-float L^-1 blocks");
     if (e == cudaSuccess && linv)
-        e = cudaMemcpyAsync(linv, p->d_linv, (size_t)p->nslot * linv_len(p->K) * (p->spin != 0 ? 2 : 1) * sizeof(double),
+        e = cudaMemcpyAsync(linv, p->d_linv,
+                            (size_t)p->nslot *
+                                ((p->flags & FLINTS_SPIN2_AUGMENTED) ? (2 * p->K) * (2 * p->K + 1) / 2
+                                                                      : linv_len(p->K) * (p->spin != 0 ? 2 : 1)) *
+                                sizeof(double),
                             cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return pcuda(e, "flints_paper_tables");
     return FLINTS_OK;

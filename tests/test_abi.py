@@ -49,9 +49,11 @@ def test_paper_plan_validates_arguments_without_gpu(lib_path):
     lib = api.load_library()
     h = ctypes.c_void_p()
     cl = (ctypes.c_double * 33)(*([0.0, 0.0] + [1.0] * 31))
-    for args, msg in [((16, 32, cl, None, 3, 0, 0), b"level y"), ((15, 32, cl, None, 2, 0, 0), b"divisible"),
-                      ((16, 32, cl, None, 1, 0, 5), b"precision"), ((16, 32, None, None, 1, 0, 0), b"cl is NULL"),
-                      ((16384, 32, cl, None, 1, 0, 0), b"nside"), ((16, 32, cl, None, 1, 3, 0), b"spin")]:
+    for args, msg in [((16, 32, cl, None, 3, 0, 0, 0), b"level y"), ((15, 32, cl, None, 2, 0, 0, 0), b"divisible"),
+                      ((16, 32, cl, None, 1, 0, 5, 0), b"precision"), ((16, 32, None, None, 1, 0, 0, 0), b"cl is NULL"),
+                      ((16384, 32, cl, None, 1, 0, 0, 0), b"nside"), ((16, 32, cl, None, 1, 3, 0, 0), b"spin"),
+                      ((16, 32, cl, None, 1, 2, 0, 8), b"flag"), ((16, 32, cl, None, 1, 0, 0, 1), b"AUGMENTED"),
+                      ((16, 32, cl, None, 1, 2, 1, 1), b"AUGMENTED")]:
         rc = lib.flints_paper_plan(ctypes.byref(h), *args, None)
         assert rc == 1 and not h.value and msg in lib.flints_paper_last_error(), (args, lib.flints_paper_last_error())
     assert lib.flints_paper_lens(None, 0, 1, None, None, None, None, None, None) == 1

@@ -443,3 +443,56 @@ def test_fullsize_4096_qu_sampled(fl, torch, qu4096, y, precision):
     for a_v, a_s2 in ((rv, rs2), (ov, os2)):
         assert np.max(np.abs(v - a_v)) <= TOL[precision] * sigma
         assert np.max(np.abs(s2 - a_s2)) <= TOL[precision] * x0
+
+
+# ------------------------------------------------------- augmented spin 2
+@pytest.mark.parametrize("nside,lmax,y", [(2, 12, 1), (8, 16, 1), (32, 64, 1), (16, 32, 2), (32, 64, 2)])
+def test_augmented_lens_parity(fl, torch, nside, lmax, y):
+    # the widely linear (xi+, xi-) estimator on the paper stencil: the class's real
+    # 2K x 2K factor (D L^-1 D for the southern classes) against the oracle's
+    # augmented class route and its per-target augmented solve
+    cl, bb, m, sigma = _spin2_inputs(nside, lmax, 700 + nside + y)
+    npix = hp.npix(nside)
+    defl = wl.random_deflection(npix, 701 + nside, rms=0.5 * _pixel_size(nside))
+    plan = fl.PaperPlan(nside, cl, y, "fp64", spin=2, cl_bb=bb, augmented=True)
+    assert plan.info()["flags"] == fl.FLINTS_SPIN2_AUGMENTED
+    st = torch.empty(npix, dtype=torch.uint8, device="cuda")
+    out, var = plan.lens(torch.from_numpy(m).cuda(), torch.from_numpy(np.ascontiguousarray(defl)).cuda(), status=st)
+    torch.cuda.synchronize()
+    o = to_host(out)
+    v = o[:, 0] + 1j * o[:, 1]
+    s2 = to_host(var)
+    t_max, n = fc.paper_grid_rule(cl, nside, y, bb)
+    tp, tm, x0 = xi.spin2_tables(cl, bb, t_max, n)
+    rv, rs2, idx, tv = fc.paper_lens(nside, y, m, defl, np.arange(npix), tp, x0, classes=True, spin=2, f_minus=tm)
+    cnt = np.sum(idx >= 0, axis=1)
+    ov = np.empty(npix, dtype=np.complex128)
+    os2 = np.empty(npix)
+    for k in np.unique(cnt):
+        rows = np.nonzero(cnt == k)[0]
+        stn = np.stack([r[r >= 0] for r in idx[rows]])
+        ov[rows], os2[rows], _ = kr.estimate(nside, 2, m, tv[rows], stn, tp, x0, f_minus=tm)
+    for a_v, a_s2 in ((rv, rs2), (ov, os2)):
+        assert np.max(np.abs(v - a_v)) <= TOL["fp64"] * sigma
+        assert np.max(np.abs(s2 - a_s2)) <= TOL["fp64"] * x0
+    assert not np.any(to_host(st) & (fl.ST_WINDOW | fl.ST_FAILED))
+
+
+def test_augmented_supersample_ragged(fl, torch):
+    nside, nout, y = 16, 32, 2
+    cl, bb, m, sigma = _spin2_inputs(nside, 2 * nside, 801)
+    plan = fl.PaperPlan(nside, cl, y, "fp64", spin=2, cl_bb=bb, augmented=True)
+    first, count = 333, 1701
+    out, var = plan.supersample(torch.from_numpy(m).cuda(), nout, first=first, count=count)
+    torch.cuda.synchronize()
+    o = to_host(out)
+    t_max, n = fc.paper_grid_rule(cl, nside, y, bb)
+    tp, tm, x0 = xi.spin2_tables(cl, bb, t_max, n)
+    rv, rs2, _, _ = fc.paper_supersample(nside, nout, y, m, np.arange(first, first + count), tp, x0, classes=True,
+                                         spin=2)
+    # the Hermitian and augmented estimates differ (B != E): check against the augmented route
+    tv = hp.pix2vec(nout, np.arange(first, first + count))
+    av, as2, _ = fc.class_estimate(nside, y, m, tv, tp, x0, spin=2, f_minus=tm)
+    assert np.max(np.abs(o[:, 0] + 1j * o[:, 1] - av)) <= TOL["fp64"] * sigma
+    assert np.max(np.abs(to_host(var) - as2)) <= TOL["fp64"] * x0
+    assert np.max(np.abs(av - rv)) > 1e-6 * sigma  # the two estimators are distinct here
