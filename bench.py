@@ -822,7 +822,7 @@ def run_paper(args):
     cl_ee, cl_bb = W.cl()
     with Clocks(clk_path) as clk:
         for task, nside, nout, spin in (("lens", 4096, None, 0), ("supersample", 2048, 4096, 0),
-                                        ("lens_qu", 4096, None, 2)):
+                                        ("lens_qu", 4096, None, 2), ("lens_qu_aug", 4096, None, 2)):
             npix = 12 * nside * nside
             m = torch.randn((npix, 2) if spin == 2 else (npix,), dtype=torch.float64, device=dev, generator=g)
             ntgt = 12 * (nout or nside) ** 2
@@ -832,11 +832,12 @@ def run_paper(args):
                 defl = torch.randn((BATCH, 2), dtype=torch.float64, device=dev, generator=g) * wl.DEFLECTION_RMS
             out = torch.empty((BATCH, 2) if spin == 2 else (BATCH,), dtype=torch.float64, device=dev)
             for y in (1, 2):
-                for precision in ("fp64", "mixed"):
+                for precision in (("fp64",) if task.endswith("aug") else ("fp64", "mixed")):
                     torch.cuda.synchronize(dev)
                     t0 = time.perf_counter()
                     if spin == 2:
-                        plan = fl.PaperPlan(nside, cl_ee, y, precision, spin=2, cl_bb=cl_bb)
+                        plan = fl.PaperPlan(nside, cl_ee, y, precision, spin=2, cl_bb=cl_bb,
+                                            augmented=task.endswith("aug"))
                     else:
                         plan = fl.PaperPlan(nside, cl, y, precision)
                     torch.cuda.synchronize(dev)
@@ -868,7 +869,9 @@ def run_paper(args):
                         "table_bytes": info["table_bytes"], "window": info["window"],
                         "nugget_slots": info["nugget_slots"], "failed_slots": info["failed_slots"],
                         "predicted_precision": math.sqrt(float(var.mean()) / info["xi0"])}
-                    if precision == "fp64":
+                    if task.endswith("aug"):
+                        arm["fp64_tflops"] = flops.paper_augmented_fp64_flops(K) * BATCH / sec / 1e12
+                    elif precision == "fp64":
                         arm["fp64_tflops"] = flops.paper_fp64_flops(K, spin) * BATCH / sec / 1e12
                     else:
                         arm["fp32_tflops"] = flops.paper_mixed_fp32_flops(K, spin) * BATCH / sec / 1e12
@@ -889,7 +892,7 @@ def run_paper(args):
         "data": "synthetic white-noise maps, Gaussian deflections of 2.5 arcmin rms",
         "config": {"workload": "tabulated inverse: lensing Nside 4096 T (y = 1, 2; FP64 and mixed), "
                                "supersampling Nside 2048 -> 4096 (y = 1, 2; FP64 and mixed), lensing Nside 4096 "
-                               "Q/U (spin 2, c3 spectra, y = 1, 2; FP64 and mixed), lmax 4096",
+                               "Q/U (spin 2, c3 spectra, y = 1, 2; FP64 and mixed; augmented xi+/xi- FP64), lmax 4096",
                    "batch_points": BATCH, "l2": "inputs larger than L2 (1.6 GB map, 268 MB of deflections)"},
         "fp64": {"value": res["lens_y1_fp64"]["value"], "ms_per_step": res["lens_y1_fp64"]["ms_per_step"]},
         "mixed_over_fp64": ratios, "arms": res,

@@ -105,3 +105,12 @@ def paper_mixed_fp32_flops(K: int, spin: int = 0) -> float:
     cm = 4 if spin else 1
     phase = (2 * DF_MUL + 27 * DF_MUL + 16 * DF_ADD + DF_SPECIAL + 2 * DF_MUL) if spin else 0
     return K * (chord + table + phase) + cm * K * (K + 1) * DF_MAC + cm * 2 * K * (DF_MUL + DF_ADD)
+
+
+def paper_augmented_fp64_flops(K: int) -> float:
+    """FP64 flops per target of the augmented tabulated-inverse route: K member
+    terms (chord 8, two table lookups 2 x 5, the two phases 40, the four
+    real-form entries 8), three triangular products with the real 2K x 2K
+    factor (3 x 2K (2K + 1) / 2 multiply-adds) and the dots (3 x 2K)."""
+    N = 2 * K
+    return K * (8 + 10 + 40 + 8) + 3 * 2 * N * (N + 1) / 2 + 3 * 2 * N
