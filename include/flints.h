@@ -297,8 +297,8 @@ void flints_free(flints_plan_t plan);
 
 /* The paper's estimator route with tabulated inverses (Secs. 2.3-2.5): the
  * pixel-centred stencil at level y and the inverse covariance computed once per
- * class of central pixels, then two triangular matrix-vector products per
- * target.  Spin 0, FP64 or mixed precision.
+ * class of central pixels, then triangular matrix-vector products per target.
+ * Spin 0, 1 and 2 (Hermitian or augmented), FP64 or mixed precision.
  *
  * Stencil (Sec. 2.3, neighbours() with the NESTED hierarchy): the target's
  * pixel at Nside_c = Nside / 2^(y-1) and the pixels of that grid sharing a
@@ -328,23 +328,26 @@ void flints_free(flints_plan_t plan);
  *   linear estimator with xi+ and xi-, the class factor that of the real
  *   2K x 2K system of (Q_i, U_i), D L^-1 D with D = diag(I, -I) for mirrored
  *   classes; L^-1 blocks 2K (2K + 1) / 2 doubles packed by columns);
- *   precision FLINTS_FP64, or
- *   FLINTS_MIXED: the per-target chords, correlation lookups and triangular
- *   products in double-float on the FP32 pipe (target position and location
- *   FP64; the L^-1 blocks computed in FP64 and kept as double-float).  Builds on `stream` the xi table on [0, min((7 / Nside_c)^2, 4)] (interval
- *   count by the rule of flints_plan), the stencil table and the L^-1 blocks,
- *   then synchronises `stream`.  Device memory: 12 Nside_c^2 (K + 1) int32 and
- *   slots * len doubles (len below; flints_paper_get_info reports the total).  Errors:
- *   FLINTS_EINVAL (arguments; a stencil chord beyond the table domain),
- *   FLINTS_ENOMEM, FLINTS_ECUDA; message in flints_paper_last_error().
+ *   precision FLINTS_FP64, or FLINTS_MIXED: the per-target chords,
+ *   correlation lookups and triangular products in double-float on the FP32
+ *   pipe (target position and location FP64; the L^-1 blocks computed in FP64
+ *   and kept as double-float).
+ *   Builds on `stream` the xi table(s) on [0, min((7 / Nside_c)^2, 4)]
+ *   (interval count by the rule of flints_plan), a table of the map pixels'
+ *   positions (and frames, spin 1, 2), the stencil table and the L^-1 blocks,
+ *   then synchronises `stream`.  Device memory: 32 bytes per map pixel,
+ *   12 Nside_c^2 (K + 1) int32, slots * len doubles (len below; complex
+ *   blocks twice that); flints_paper_get_info reports the total.
+ *   Errors: FLINTS_EINVAL (arguments; a stencil chord beyond the table
+ *   domain), FLINTS_ENOMEM, FLINTS_ECUDA; message in flints_paper_last_error().
  * flints_paper_lens: lensed values at targets first .. first+count-1 (RING
  *   pixels of the plan's grid displaced along defl, as flints_lens_range).
  *   map DEVICE [12 Nside^2] (spin 1, 2: [12 Nside^2][2] = (d_theta, d_phi) or
  *   (Q, U), 16-byte aligned; else 8-byte aligned), defl DEVICE [count][2]
  *   (16-byte aligned; entry i belongs to pixel first + i), out DEVICE [count]
  *   (spin 1, 2: [count][2] in the frame at the displaced direction, 16-byte
- *   aligned), var DEVICE
- *   [count] (may be NULL), status DEVICE [count] (may be NULL; FLINTS_ST_NUGGET
+ *   aligned), var DEVICE [count] (may be NULL), status DEVICE [count] (may be
+ *   NULL; FLINTS_ST_NUGGET
  *   when the class needed a raised nugget, FLINTS_ST_WINDOW when a chord fell
  *   beyond the table domain, FLINTS_ST_FAILED with NaN outputs when no factor
  *   was found).  Asynchronous on `stream`.
@@ -355,8 +358,9 @@ void flints_free(flints_plan_t plan);
  *   [K] int32 RING indices at Nside, -1 past the member count), the class of
  *   each coarse pixel (slot DEVICE [12 Nside_c^2] int32) and the L^-1 blocks
  *   (linv DEVICE [slots][len] doubles, complex (re, im) pairs for spin 1, 2,
- *   zero past the member count; K = 9:
- *   len = 45, packed by columns: column j, rows j .. 8, from offset
+ *   zero past the member count; augmented plans: the real 2K x 2K factor packed
+ *   by columns; else K = 9: len = 45, packed by columns: column j, rows j .. 8,
+ *   from offset
  *   9 j - j (j - 1) / 2; K = 36: len = 704, the lane-step layout: entry
  *   32 u + l (u < 17) holds, for p = l / 2 and t = u (l even) or 17 + u (l
  *   odd), row p column t when t <= p, else row 31 - p column t - p - 1 (zero
@@ -374,7 +378,7 @@ typedef struct flints_paper_info {
     double t_max;           /* xi table domain [0, t_max] in chord^2 */
     int n_intervals;
     double xi0;
-    int64_t table_bytes;    /* stencil table + class map + S^-1 blocks */
+    int64_t table_bytes;    /* pixel table + stencil table + class map + L^-1 blocks */
     double max_pair_t;      /* largest chord^2 between members of a stencil */
     int64_t nugget_slots;   /* classes whose factor needed a raised nugget */
     int64_t failed_slots;   /* classes without a positive-definite factor */
