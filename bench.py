@@ -57,15 +57,17 @@ def parse():
                          "spin1: a deflection field (spin 1) lensed at Nside 4096; paper: the 9/36-pixel stencil "
                          "with tabulated inverses (lensing at 4096, supersampling 2048 -> 4096)")
     ap.add_argument("--duration", type=float, default=45.0, help="c5: seconds of Poisson arrivals")
-    ap.add_argument("--profile-case", choices=["mixed", "fp64", "paper1", "paper2", "paper1m", "paper2m"], default=None,
+    ap.add_argument("--profile-case", choices=["mixed", "fp64", "paper1", "paper2", "paper1m", "paper2m", "paper2q", "paper2qm"], default=None,
                     help="small case for ncu: two launches on 2^18 targets of the resident c3 map (mixed, "
-                         "fp64), or on 2^20 targets of the tabulated-inverse route at level 1 or 2 (m: mixed)")
+                         "fp64), or on 2^20 targets of the tabulated-inverse route at level 1 or 2 (m: mixed; q: "
+                         "spin-2 Q/U)")
     return ap.parse_args()
 
 
-def run_profile_case_paper(y: int, precision: str = "fp64"):
-    """Two launches of the tabulated-inverse apply kernel (Nside 4096 lensing, level y)
-    on 2^20 targets of a ring band (the second one is the one to capture)."""
+def run_profile_case_paper(y: int, precision: str = "fp64", spin: int = 0):
+    """Two launches of the tabulated-inverse apply kernel (Nside 4096 lensing, level y;
+    spin 0 T or spin 2 Q/U) on 2^20 targets of a ring band (the second one is the one
+    to capture)."""
     import torch
 
     import paper_1003_4984_gb300 as fl
@@ -76,15 +78,20 @@ def run_profile_case_paper(y: int, precision: str = "fp64"):
     g.manual_seed(8)
     n = 1 << 20
     nside = 4096
-    m = torch.randn(12 * nside * nside, dtype=torch.float64, device=dev, generator=g)
+    m = torch.randn((12 * nside * nside, 2) if spin else (12 * nside * nside,), dtype=torch.float64, device=dev,
+                    generator=g)
     defl = torch.randn((n, 2), dtype=torch.float64, device=dev, generator=g) * wl.DEFLECTION_RMS
-    plan = fl.PaperPlan(nside, wl.cl_tt(4096, 2500.0), y, precision)
+    if spin:
+        cl_ee, cl_bb = W.cl()
+        plan = fl.PaperPlan(nside, cl_ee, y, precision, spin=2, cl_bb=cl_bb)
+    else:
+        plan = fl.PaperPlan(nside, wl.cl_tt(4096, 2500.0), y, precision)
     for _ in range(2):
         out, var = plan.lens(m, defl, first=100_000_000, count=n)
     torch.cuda.synchronize()
     info = plan.info()
     assert info["window"] == 0 and info["failed_slots"] == 0, info
-    print(json.dumps({"profile_case": f"paper_y{y}_{precision}", "points": n, "K": info["K"]}))
+    print(json.dumps({"profile_case": f"paper_y{y}_{precision}_spin{spin}", "points": n, "K": info["K"]}))
 
 
 def run_profile_case(precision: str):
@@ -94,7 +101,8 @@ def run_profile_case(precision: str):
     import paper_1003_4984_gb300 as fl
 
     if precision.startswith("paper"):
-        return run_profile_case_paper(int(precision[5]), "mixed" if precision.endswith("m") else "fp64")
+        return run_profile_case_paper(int(precision[5]), "mixed" if precision.endswith("m") else "fp64",
+                                      2 if "q" in precision else 0)
     fl.load_library()
     cl, bb = W.cl()
     dev = torch.device("cuda", 0)
