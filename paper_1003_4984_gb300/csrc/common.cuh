@@ -135,6 +135,49 @@ __device__ __forceinline__ void dfacc_add_prod(dfacc &a, df x, df y) {
 }
 __device__ __forceinline__ df dfacc_val(dfacc a) { return two_sum(a.hi, a.lo); }
 
+// Anchored double-float accumulator for sums of products whose partial sums are
+// known to stay within |s| <= B.  The high word h holds C + (high part of the
+// sum), C = 6 * 2^e with 2^e >= B, so every value h takes lies in [4, 8] * 2^e:
+// adding a product to h rounds it onto that binade's fixed grid (2^(e-21)), the
+// amount actually added, h_new - h_old, is exact (Sterbenz), and the rounding
+// remainder x*y - (h_new - h_old) is at most half a grid step.  The remainders
+// and the cross terms of the double-float operands collect in the low word l,
+// whose size stays near the grid step.  A multiply-accumulate is 6 FP32
+// instructions (a general double-float one is 12) with an absolute error of
+// about 2^-46 B per step.  The value is (h - C) + l, the first term exact.
+struct anc {
+    float h, l;
+};
+__device__ __forceinline__ anc anc_init(df a, float C) {
+    anc r;
+    r.h = __fadd_rn(C, a.hi);
+    r.l = __fadd_rn(a.lo, __fsub_rn(a.hi, __fsub_rn(r.h, C)));  // a.hi minus what h took: exact
+    return r;
+}
+// a -= x*y
+__device__ __forceinline__ void anc_sub_prod(anc &a, df x, df y) {
+    const float h0 = a.h;
+    a.h = __fmaf_rn(-x.hi, y.hi, h0);
+    float t = __fmaf_rn(-x.hi, y.hi, __fsub_rn(h0, a.h));  // remainder of the high product
+    t = __fmaf_rn(-x.hi, y.lo, t);
+    t = __fmaf_rn(-x.lo, y.hi, t);
+    a.l = __fadd_rn(a.l, t);
+}
+// a += x*y
+__device__ __forceinline__ void anc_add_prod(anc &a, df x, df y) {
+    const float h0 = a.h;
+    a.h = __fmaf_rn(x.hi, y.hi, h0);
+    float t = __fmaf_rn(x.hi, y.hi, __fsub_rn(h0, a.h));
+    t = __fmaf_rn(x.hi, y.lo, t);
+    t = __fmaf_rn(x.lo, y.hi, t);
+    a.l = __fadd_rn(a.l, t);
+}
+// Anchor for partial sums bounded by b >= 0: 6 * 2^e with 2^e > b (b finite).
+__device__ __forceinline__ float anc_anchor(float b) {
+    const unsigned ex = (__float_as_uint(b) >> 23) & 0xffu;  // b < 2^(ex - 126)
+    return __uint_as_float((ex + 1u) << 23) * 6.0f;
+}
+
 // ---------------------------------------------------------------------------
 // Precision policy: the same kernel source is instantiated for FP64 and for
 // double-float.
@@ -336,6 +379,20 @@ struct LaunchCfg {
 };
 
 enum { CNT_POINTS = 0, CNT_NUGGET = 1, CNT_FALLBACK = 2, CNT_WINDOW = 3, CNT_FAILED = 4, CNT_N = 5 };
+
+// Correlation-table grid and stencil search disc of a K-nearest plan (host).
+// The disc has chord radius r = 1.25 sqrt(K/3)/Nside (a cap holding K pixels
+// has radius sqrt(K/3)/Nside), so chords between stencil members are <= 2r and
+// the table covers t = chord^2 in [0, t_max = 4 r^2]; the interval count is the
+// smallest power of two >= 64 (<= 65536) whose cubic Hermite error bound
+// h^4/384 max|f''''| stays below 1e-11 of xi(0), with max|f''''| bounded by
+// sum_l |a_l| P_l''''(1) / (16 xi(0)), a_l = (2l+1)/(4 pi) |C_l| (+ |C_l^BB|
+// when cl_bb is given); R_rings is the number of rings searched on each side.
+struct TableGrid {
+    double r, r2, t_max, h, inv_h;
+    int n, R_rings;
+};
+TableGrid table_grid(int64_t nside, int K, int lmax, const double *cl, const double *cl_bb);
 
 // Host-side launchers (lens_spin0.cu, lens_spin2.cu, xi_table.cu).
 cudaError_t launch_lens(int spin, int K, int precision, const LensArgs &a, int R_rings, const LaunchCfg &cfg,

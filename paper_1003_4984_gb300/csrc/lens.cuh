@@ -1,20 +1,24 @@
 // Fused lensing-remap kernel: one warp per target point (Secs. 2.1-2.5, 3.1).
 //
-// Per tile of 32 consecutive RING targets a warp first displaces all 32
-// directions (one per lane, FP64), then, point by point:
+// Per tile of up to 16 (MAX_TILE_POINTS) consecutive RING targets a warp first
+// displaces all of them (one per lane, FP64), then, point by point:
 //   1. stencil search: the rings whose circle comes within the search radius r
 //      of n' (one ring per lane), the pixel range of each ring that can lie
 //      inside the disc, candidates enumerated in increasing RING index;
-//   2. exact K-nearest selection: squared chords in FP64, a warp bitonic sort
-//      on (chord^2, RING index); the K-th chord must lie inside the disc;
+//   2. exact K-nearest selection: FP32 keys of all candidates pre-select, FP64
+//      squared chords of the selected (or near-tied) ones decide, warp bitonic
+//      sorts on (chord^2, RING index); the K-th chord must lie inside the disc;
 //   3. covariance assembly S_ij = xi(t_ij)/xi(0) (+ nugget on the diagonal)
 //      and c_i = xi(t_i)/xi(0), spin 2 with the parallel-transport phase
 //      exp(2i(a_ij - a_ji)); lower triangle spread over the lanes;
-//   4. left-looking Cholesky, lane l owning rows l and l+32; the nugget is
-//      doubled while a pivot is not positive (Sec. 2.4);
-//   5. forward solves z_c = L^-1 conj(c), z_y = L^-1 y; value = z_c^H z_y,
-//      variance = xi(0) (1 - |z_c|^2) (Eqs. best_temperature_field, gaussvar,
-//      major_eq, gaussvar_pol).
+//   4. Cholesky of the matrix bordered by the right-hand-side rows c and y,
+//      so that the factor's bordered rows are the forward solves z_c, z_y:
+//      right-looking in FP64 for N <= 32 (all lanes share the rank-one
+//      updates), split left-looking otherwise and in double-float (anchored
+//      accumulators); the nugget is doubled while a pivot is not positive
+//      (Sec. 2.4);
+//   5. value = z_c^H z_y, variance = xi(0) (1 - |z_c|^2) (Eqs.
+//      best_temperature_field, gaussvar, major_eq, gaussvar_pol).
 // Precision R = double (FP64 path) or df (double-float on the FP32 pipe, the
 // mixed path: FP64 geometry and selection, double-float assembly, factor and
 // solves, FP64 fallback for points whose double-float factor fails).
@@ -574,15 +578,169 @@ __device__ __forceinline__ bool bordered_cholesky_rl(Elem *mat, int lane) {
     return true;
 }
 
-// Choice between the two forms, measured on GB300 (c3-like targets): in FP64
-// the pipe executes inactive lanes too, so the right-looking form's fuller
-// lanes win for N <= 32 (spin 2, K = 32: +15 %); in double-float, and for larger
-// N, the left-looking form's register accumulators win (right-looking was 21 %
-// slower for double-float spin 2, K = 32, and 28 % slower in FP64 at N = 48).
+// Double-float form of the split left-looking factorisation with anchored
+// accumulators (struct anc).  The partial sums of column j are bounded by the
+// Cauchy-Schwarz inequality: every matrix row r has |L_r| <= sqrt(A_rr) =
+// sqrt(1 + n) and so has the pivot row, the covariance rows (c; b_Q, b_U of the
+// augmented system) have |L^-1 c|^2 <= 1 (resp. <= 2) because the variance they
+// leave is non-negative, and their entries are at most 1: every sum over k < j
+// of L_rk conj(L_jk), plus A_rj, stays below 2.5, anchor C = 6.  The last
+// bordered row holds the data, whose solve L^-1 y has no a-priori bound; its
+// anchor is taken per column from |y_j| + |(L^-1 y)_{<j}| (the running norm of
+// the entries already computed, carried in every lane), so its grid follows the
+// size of its own sums.  Compared with bordered_cholesky<N, NB, df> only the
+// accumulation differs (6 instead of 12 FP32 instructions per real
+// multiply-accumulate); the error per step is about 2^-46 of the bound instead
+// of 2^-48 of the products.
+template <int N, int NB, class Elem>
+__device__ __forceinline__ bool bordered_cholesky_anchored(Elem *mat, int lane) {
+    using O = Ops<df>;
+    constexpr bool CPLX = !std::is_same<Elem, df>::value;
+    constexpr int NROW = N + NB;
+    constexpr int NT = (NROW + 31) / 32;
+    constexpr float C_BOUNDED = 6.0f;
+    float ynorm2 = 0.0f;  // |(L^-1 y)_{<j}|^2 of the data row (row NROW - 1), FP32, identical in every lane
+    for (int j = 0; j < N; ++j) {
+        const int nrows = NROW - j;
+        int s = 1;
+        while ((s << 1) * nrows <= 32) s <<= 1;
+        const int g = 32 / s;
+        const int part = lane & (s - 1), grp = lane / s;
+        const Elem *Lj = mat + tri<N>(j, 0);
+        // anchor of the data row at this column (its initial entry plus the running norm)
+        float cy;
+        {
+            const Elem y0 = mat[tri<N>(NROW - 1, j)];
+            float ay;
+            if constexpr (CPLX) {
+                ay = fmaxf(fabsf(y0.re.hi), fabsf(y0.im.hi));
+            } else {
+                ay = fabsf(y0.hi);
+            }
+            cy = anc_anchor(fmaf(1.001f, ay + sqrtf(ynorm2), 1e-30f));
+        }
+        Elem srow[NT];
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            if (t > 0 && j + t * g >= NROW) break;  // warp-uniform: no row left for this slot
+            const int r = j + grp + t * g;
+            const bool act = r < NROW;
+            const int rr = act ? r : j;
+            const float C = (rr == NROW - 1) ? cy : C_BOUNDED;
+            const Elem *Lr = mat + tri<N>(rr, 0);
+            if constexpr (!CPLX) {
+                anc acc = anc_init((part == 0 && act) ? Lr[j] : O::zero(), C);
+                anc acc2 = anc_init(O::zero(), C);
+                if (act) {
+                    int k = part;
+                    for (; k + s < j; k += 2 * s) {  // two independent chains
+                        anc_sub_prod(acc, Lr[k], Lj[k]);
+                        anc_sub_prod(acc2, Lr[k + s], Lj[k + s]);
+                    }
+                    if (k < j) anc_sub_prod(acc, Lr[k], Lj[k]);
+                }
+                float H = __fadd_rn(__fsub_rn(acc.h, C), __fsub_rn(acc2.h, C));  // exact: grid values in range
+                float Lw = __fadd_rn(acc.l, acc2.l);
+                for (int o = 1; o < s; o <<= 1) {
+                    H = __fadd_rn(H, __shfl_xor_sync(FULL, H, o));
+                    Lw = __fadd_rn(Lw, __shfl_xor_sync(FULL, Lw, o));
+                }
+                srow[t] = two_sum(H, Lw);
+            } else {
+                const Elem a0 = Lr[j];
+                anc ar = anc_init((part == 0 && act) ? a0.re : O::zero(), C);
+                anc ai = anc_init((part == 0 && act) ? a0.im : O::zero(), C);
+                anc br = anc_init(O::zero(), C), bi = anc_init(O::zero(), C);
+                if (act)
+                    for (int k = part; k < j; k += s) {  // real and imaginary parts in two chains each
+                        const Elem a = Lr[k], b = Lj[k];
+                        anc_sub_prod(ar, a.re, b.re);
+                        anc_sub_prod(br, a.im, b.im);
+                        anc_sub_prod(ai, a.im, b.re);
+                        anc_add_prod(bi, a.re, b.im);
+                    }
+                float Hr = __fadd_rn(__fsub_rn(ar.h, C), __fsub_rn(br.h, C));
+                float Hi = __fadd_rn(__fsub_rn(ai.h, C), __fsub_rn(bi.h, C));
+                float Lr_ = __fadd_rn(ar.l, br.l), Li_ = __fadd_rn(ai.l, bi.l);
+                for (int o = 1; o < s; o <<= 1) {
+                    Hr = __fadd_rn(Hr, __shfl_xor_sync(FULL, Hr, o));
+                    Hi = __fadd_rn(Hi, __shfl_xor_sync(FULL, Hi, o));
+                    Lr_ = __fadd_rn(Lr_, __shfl_xor_sync(FULL, Lr_, o));
+                    Li_ = __fadd_rn(Li_, __shfl_xor_sync(FULL, Li_, o));
+                }
+                srow[t].re = two_sum(Hr, Lr_);
+                srow[t].im = two_sum(Hi, Li_);
+            }
+        }
+        // pivot: row j is held by lane 0 (group 0, part 0, t = 0)
+        df d;
+        if constexpr (!CPLX) {
+            d = O::shfl(srow[0], 0);
+        } else {
+            d = O::shfl(srow[0].re, 0);
+        }
+        if (!O::positive(d)) return false;
+        df ljj, il;
+        O::pivot(d, ljj, il);
+        // the data row's new entry (held by the parts of its group) joins the running norm
+        {
+            const int ty = (NROW - 1 - j) / g, gy = (NROW - 1 - j) - ty * g;
+            float vr = 0.0f, vi = 0.0f;
+#pragma unroll
+            for (int t = 0; t < NT; ++t) {
+                if (t == ty) {
+                    if constexpr (!CPLX) {
+                        vr = srow[t].hi;
+                    } else {
+                        vr = srow[t].re.hi;
+                        vi = srow[t].im.hi;
+                    }
+                }
+            }
+            vr = __shfl_sync(FULL, vr, gy * s) * il.hi;
+            if constexpr (CPLX) vi = __shfl_sync(FULL, vi, gy * s) * il.hi;
+            ynorm2 = fmaf(vr, vr, fmaf(vi, vi, ynorm2));
+        }
+        __syncwarp();
+        if (part == 0) {
+#pragma unroll
+            for (int t = 0; t < NT; ++t) {
+                const int r = j + grp + t * g;
+                if (t > 0 && j + t * g >= NROW) break;
+                if (r < NROW) {
+                    Elem v;
+                    if constexpr (!CPLX) {
+                        v = (r == j) ? ljj : O::mul(srow[t], il);
+                    } else {
+                        if (r == j) {
+                            v.re = ljj;
+                            v.im = O::zero();
+                        } else {
+                            v.re = O::mul(srow[t].re, il);
+                            v.im = O::mul(srow[t].im, il);
+                        }
+                    }
+                    mat[tri<N>(r, j)] = v;
+                }
+            }
+        }
+        __syncwarp();
+    }
+    return true;
+}
+
+// Choice between the forms, measured on GB300 (c3-like targets): in FP64 the
+// pipe executes inactive lanes too, so the right-looking form's fuller lanes
+// win for N <= 32 (spin 2, K = 32: +15 %); for larger N the left-looking form's
+// register accumulators win (right-looking was 28 % slower in FP64 at N = 48).
+// Double-float factors use the left-looking form with anchored accumulators
+// (the right-looking form's memory-resident accumulators were 21 % slower).
 template <int N, int NB, class R, class Elem>
 __device__ __forceinline__ bool factor_bordered(Elem *mat, int lane) {
     if constexpr (std::is_same<R, double>::value && N <= 32)
         return bordered_cholesky_rl<N, NB, R>(mat, lane);
+    else if constexpr (std::is_same<R, df>::value)
+        return bordered_cholesky_anchored<N, NB>(mat, lane);
     else
         return bordered_cholesky<N, NB, R>(mat, lane);
 }
