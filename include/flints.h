@@ -58,8 +58,9 @@ typedef enum {
     FLINTS_OK = 0,
     FLINTS_EINVAL = 1,   /* invalid argument (see flints_last_error) */
     FLINTS_ENOMEM = 2,   /* device allocation failed */
-    FLINTS_ECUDA = 3,    /* a CUDA runtime call or kernel launch failed */
-    FLINTS_ETIMEOUT = 5  /* a bounded device wait gave up (batched driver) */
+    FLINTS_ECUDA = 3     /* a CUDA runtime call or kernel launch failed */
+    /* 4 and 5 are reserved: no entry point waits on the device, so none
+     * returns a timeout */
 } flints_status;
 
 /* precision */
@@ -267,30 +268,47 @@ const char *flints_synth_last_error(void);
 
 /* Lens the target range [first, first+count) without allocating any device
  * memory.  The paper has no counterpart: this entry point exists for callers
- * that cannot call cudaMalloc -- code running during CUDA stream capture,
- * serving runtimes that hand all device memory to their own pool, hosts whose
- * allocator policy forbids the library from allocating.  It runs the same xi
- * tabulation and lens kernels as flints_plan + flints_lens_range, with their
- * working memory (spectrum, table, coefficients, counters, under 1 MB) in a
- * fixed file-scope device array that every GPU loading the library holds
- * until the process exits.
+ * that cannot call cudaMalloc -- serving runtimes that hand all device memory
+ * to their own pool up front (an allocation by the library would fail or
+ * fragment it) and hosts whose allocator policy forbids the library from
+ * allocating.  It runs the same xi tabulation and lens kernels as
+ * flints_plan + flints_lens_range, with their working memory (spectrum, table,
+ * coefficients, counters, under 1 MB) in a fixed file-scope device array that
+ * every GPU loading the library holds until the process exits.
  *   Arguments: as flints_plan (cl, cl_bb are HOST pointers) followed by the
- *   target range and the DEVICE buffers of flints_lens_range.
+ *   target range and the DEVICE buffers of flints_lens_range, with the same
+ *   alignment rules (defl 16 bytes; map and out 16 bytes for spin 2, 8 bytes
+ *   for spin 0; var 8 bytes).
  *   Limits: lmax <= 8192 and a xi table of at most 8192 intervals; larger
  *   requests return FLINTS_EINVAL with a message naming the limit.
  *   Set-up: the first call on each device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call
- *   before any stream capture.
+ *   (cudaGetSymbolAddress) with that device current.
+ *   Stream use: the call copies the spectrum from host memory and synchronises
+ *   `stream` once, after the tabulation, to read xi(0) back; the lens kernel is
+ *   then left running asynchronously on `stream`.
  *   Sharing: all calls use the same array and it keeps the last call's
  *   contents (the call clears what must start at zero).  Calls whose work
  *   overlaps on the GPU (different streams or threads) race on it: serialise
- *   them.  The call synchronises `stream` once, after the tabulation.
+ *   them.
  *   Errors: flints_status codes; message in flints_noalloc_last_error(). */
 int flints_lens_noalloc(int64_t nside, int lmax, const double *cl, const double *cl_bb, int spin,
                         int K, int precision, int64_t first, int64_t count, const double *map,
                         const double *defl, double *out, double *var, uint8_t *status,
                         void *stream);
 const char *flints_noalloc_last_error(void);
+
+/* Measured fused multiply-add throughput of the current device, for roofline
+ * fractions.  The paper has no counterpart: this is a measurement utility.
+ * One kernel of independent multiply-add chains (8 per thread, every SM filled
+ * to its occupancy limit) runs `iters` rounds of 128 multiply-adds per thread
+ * after a shorter warm-up launch, timed with CUDA events on `stream`;
+ * *tflops = 2 x multiply-adds / seconds / 1e12.
+ *   precision: FLINTS_MIXED measures the FP32 pipe (the double-float path's
+ *   arithmetic), FLINTS_FP64 the FP64 pipe.  iters in [1, 2^24].
+ *   Synchronises `stream`.  Errors: FLINTS_EINVAL, FLINTS_ECUDA; message in
+ *   flints_measure_last_error(). */
+int flints_measure_fma_peak(int precision, int iters, double *tflops, void *stream);
+const char *flints_measure_last_error(void);
 
 /* Release a plan and its device memory (NULL is allowed). */
 void flints_free(flints_plan_t plan);

@@ -111,6 +111,9 @@ def load_library(path: str = LIB_PATH):
     lib.flints_lens_noalloc.argtypes = [i64, c_int, dp, dp, c_int, c_int, c_int, i64, i64, vp, vp, vp, vp, vp, vp]
     lib.flints_lens_noalloc.restype = c_int
     lib.flints_noalloc_last_error.restype = ctypes.c_char_p
+    lib.flints_measure_fma_peak.argtypes = [c_int, c_int, dp, vp]
+    lib.flints_measure_fma_peak.restype = c_int
+    lib.flints_measure_last_error.restype = ctypes.c_char_p
     lib.flints_synth_plan.argtypes = [ctypes.POINTER(vp), i64, c_int, c_int, c_int, vp]
     lib.flints_synth_plan.restype = c_int
     lib.flints_synthesize.argtypes = [vp, vp, vp, vp, vp]
@@ -224,6 +227,14 @@ class Plan:
         i = _Info()
         _check(_lib.flints_get_info(self._h, ctypes.byref(i)))
         return Info(i.nside, i.lmax, i.spin, i.K, i.precision, i.t_max, i.n_intervals, i.xi0, i.search_radius)
+
+    def device_bytes(self) -> int:
+        """Device memory the plan holds (what flints_plan allocates for its tables,
+        from the plan's lmax, spin and interval count)."""
+        i = self.info()
+        two = 2 if i.spin != 0 else 1
+        return ((i.lmax + 1) * 8 * two + 4 * (i.n_intervals + 1) * 8
+                + two * i.n_intervals * (32 + 32) + 5 * 8)
 
     def table(self, which: int = 0, stream=None):
         n = self.info().n_intervals + 1
@@ -393,13 +404,29 @@ def lens_host(plan: Plan, map_host: np.ndarray, defl_host: np.ndarray, first: in
     return out.cpu().numpy(), var.cpu().numpy()
 
 
+def measure_fma_peak(precision: str = "mixed", iters: int | None = None, stream=None) -> float:
+    """flints_measure_fma_peak: measured multiply-add throughput (TFLOP/s) of the FP32
+    pipe (``"mixed"``) or the FP64 pipe (``"fp64"``) of the current device."""
+    lib = load_library()
+    if iters is None:
+        iters = 20000 if precision == "mixed" else 400
+    out = ctypes.c_double()
+    rc = lib.flints_measure_fma_peak({"fp64": FLINTS_FP64, "mixed": FLINTS_MIXED}[precision], int(iters),
+                                     ctypes.byref(out), _stream(stream))
+    if rc != 0:
+        raise FlintsError(f"flints error {rc}: {lib.flints_measure_last_error().decode()}")
+    return out.value
+
+
 def lens_noalloc(nside: int, cl, map_, defl, out, var=None, status=None, cl_bb=None, spin: int = 0, K: int = 32,
                  precision: str = "fp64", first: int = 0, count: int | None = None, stream=None):
     """flints_lens_noalloc: lens without any device allocation by the library.
 
-    For callers that cannot call cudaMalloc (stream capture, caller-owned memory
-    pools): every buffer is the caller's; the library's working memory is a fixed
-    device array.  The first call on a device must come before any stream capture.
+    For callers that cannot call cudaMalloc (serving runtimes that own all device
+    memory in their own pool, hosts that forbid library allocations): every
+    buffer is the caller's; the library's working memory is a fixed device array
+    shared by all calls, so calls must not overlap on the GPU.  The call copies
+    ``cl`` from host memory and synchronises ``stream`` once.
     """
     lib = load_library()
     npix = 12 * int(nside) * int(nside)

@@ -92,6 +92,34 @@ static int cuda_fail(cudaError_t e, const char *what) {
 
 static bool supported_K(int K) { return K == 16 || K == 24 || K == 32 || K == 48; }
 
+namespace flints {
+TableGrid table_grid(int64_t nside, int K, int lmax, const double *cl, const double *cl_bb) {
+    TableGrid g{};
+    g.r = 1.25 * std::sqrt(K / 3.0) / (double)nside;
+    g.r2 = g.r * g.r;
+    g.t_max = 4.0 * g.r * g.r;
+    double x0 = 0.0, b4num = 0.0;
+    for (int l = 0; l <= lmax; ++l) {
+        const double ld = (double)l;
+        const double c = std::fabs(cl[l]) + (cl_bb ? std::fabs(cl_bb[l]) : 0.0);
+        const double a = (2.0 * ld + 1.0) / (4.0 * PI) * c;
+        x0 += a;
+        if (l >= 4) b4num += a * ((ld - 3) * (ld - 2) * (ld - 1) * ld * (ld + 1) * (ld + 2) * (ld + 3) * (ld + 4) / 384.0);
+    }
+    const double b4 = x0 > 0 ? b4num / 16.0 / x0 : 0.0;
+    g.n = 64;
+    if (b4 > 0) {
+        const double h = std::pow(384.0 * 1e-11 / b4, 0.25);
+        const double want = std::ceil(std::log2(g.t_max / h));
+        g.n = want > 16 ? 65536 : (want < 6 ? 64 : (1 << (int)want));
+    }
+    g.h = g.t_max / g.n;
+    g.inv_h = g.n / g.t_max;
+    g.R_rings = (int)std::ceil(1.5 * g.r * (double)nside) + 1;
+    return g;
+}
+}  // namespace flints
+
 static void free_plan_memory(flints_plan_s *p) {
     cudaFree(p->d_cl);
     cudaFree(p->d_clbb);
@@ -144,35 +172,17 @@ int flints_plan(flints_plan_t *out, int64_t nside, int lmax, const double *cl, c
     p->precision = precision;
     p->flags = flags;
 
-    // Table domain and size: the stencil disc has chord radius
-    // r = 1.25 sqrt(K/3)/Nside, so chords between stencil members are <= 2r;
-    // the interval count bounds the cubic Hermite error by 1e-11 (power of two).
-    p->r = 1.25 * std::sqrt(K / 3.0) / (double)nside;
-    p->r2 = p->r * p->r;
-    p->t_max = 4.0 * p->r * p->r;
+    // Table domain and size, and the search disc (the grid rule of table_grid).
     {
-        double x0 = 0.0, b4num = 0.0;
-        for (int l = 0; l <= lmax; ++l) {
-            const double ld = (double)l;
-            double c = std::fabs(cl[l]);
-            if (spin != 0 && cl_bb) c = std::fabs(cl[l]) + std::fabs(cl_bb[l]);
-            const double a = (2.0 * ld + 1.0) / (4.0 * PI) * c;
-            x0 += a;
-            if (l >= 4)
-                b4num += a * ((ld - 3) * (ld - 2) * (ld - 1) * ld * (ld + 1) * (ld + 2) * (ld + 3) * (ld + 4) / 384.0);
-        }
-        const double b4 = x0 > 0 ? b4num / 16.0 / x0 : 0.0;
-        int n = 64;
-        if (b4 > 0) {
-            const double h = std::pow(384.0 * 1e-11 / b4, 0.25);
-            const double want = std::ceil(std::log2(p->t_max / h));
-            n = want > 16 ? 65536 : (want < 6 ? 64 : (1 << (int)want));
-        }
-        p->n = n;
+        const TableGrid tg = table_grid(nside, K, lmax, cl, spin != 0 ? cl_bb : nullptr);
+        p->r = tg.r;
+        p->r2 = tg.r2;
+        p->t_max = tg.t_max;
+        p->n = tg.n;
+        p->h = tg.h;
+        p->inv_h = tg.inv_h;
+        p->R_rings = tg.R_rings;
     }
-    p->h = p->t_max / p->n;
-    p->inv_h = p->n / p->t_max;
-    p->R_rings = (int)std::ceil(1.5 * p->r * (double)nside) + 1;
     if (2 * p->R_rings + 2 > 32) {
         delete p;
         return fail(FLINTS_EINVAL, "flints_plan: search disc spans too many rings");

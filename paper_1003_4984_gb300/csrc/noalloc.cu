@@ -1,13 +1,15 @@
 // Lensing entry point that allocates no device memory (flints_lens_noalloc).
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA stream is
-// being captured into a graph (allocation is not a capturable operation),
-// serving runtimes that reserve all device memory for their own pool up
-// front, and embedding hosts whose allocator policy forbids the library from
-// allocating.  For them this file keeps the working memory of one lensing
-// call -- spectrum, xi table nodes, interpolation coefficients and event
-// counters -- in a file-scope __device__ array of fixed size, and runs the
-// same tabulation and lens kernels as the plan-based entry points.
+// Some callers cannot call cudaMalloc: serving runtimes that reserve all
+// device memory for their own pool up front (a library allocation would fail
+// or fragment that pool), and embedding hosts whose allocator policy forbids
+// the library from allocating behind their back.  For them this file keeps the
+// working memory of one lensing call -- spectrum, xi table nodes,
+// interpolation coefficients and event counters -- in a file-scope __device__
+// array of fixed size, and runs the same tabulation and lens kernels as the
+// plan-based entry points.  Each call copies the spectrum from host memory and
+// synchronises its stream once (to read xi(0) back), so it is an ordinary
+// stream-ordered call, not one to record into a CUDA graph.
 //
 // Host code must not use the array's name as a device address: in host code
 // it is only a stand-in.  The device address is obtained once per device with
@@ -80,39 +82,27 @@ extern "C" int flints_lens_noalloc(int64_t nside, int lmax, const double *cl, co
         return na_fail(FLINTS_EINVAL, "flints_lens_noalloc: target range outside the map");
     if (count == 0) return FLINTS_OK;
     if (!map || !defl || !out) return na_fail(FLINTS_EINVAL, "flints_lens_noalloc: NULL data pointer");
-    if (((uintptr_t)map | (uintptr_t)defl | (uintptr_t)out) & 15u)
-        return na_fail(FLINTS_EINVAL, "flints_lens_noalloc: map, defl and out must be 16-byte aligned");
+    // alignment of the plan-based entry points: deflections 16 bytes, two-component
+    // maps and outputs 16 bytes, one-component maps, outputs and variances 8 bytes
+    const uintptr_t vec_align = spin == 0 ? 7u : 15u;
+    if (((uintptr_t)defl & 15u) || ((uintptr_t)map & vec_align) || ((uintptr_t)out & vec_align) ||
+        ((uintptr_t)var & 7u))
+        return na_fail(FLINTS_EINVAL,
+                       "flints_lens_noalloc: misaligned buffer (defl 16 bytes; map, out %d bytes; var 8 bytes)",
+                       spin == 0 ? 8 : 16);
     for (int l = 0; l <= lmax; ++l)
         if (!std::isfinite(cl[l]) || (spin == 2 && cl_bb && !std::isfinite(cl_bb[l])))
             return na_fail(FLINTS_EINVAL, "flints_lens_noalloc: non-finite spectrum value at l = %d", l);
 
-    // the table grid (same documented rule as flints_plan)
-    const double r = 1.25 * std::sqrt(K / 3.0) / (double)nside;
-    const double t_max = 4.0 * r * r;
-    int n = 64;
-    {
-        double x0 = 0.0, b4num = 0.0;
-        for (int l = 0; l <= lmax; ++l) {
-            const double ld = (double)l;
-            double c = std::fabs(cl[l]);
-            if (spin == 2 && cl_bb) c = std::fabs(cl[l]) + std::fabs(cl_bb[l]);
-            const double a = (2.0 * ld + 1.0) / (4.0 * PI) * c;
-            x0 += a;
-            if (l >= 4)
-                b4num += a * ((ld - 3) * (ld - 2) * (ld - 1) * ld * (ld + 1) * (ld + 2) * (ld + 3) * (ld + 4) / 384.0);
-        }
-        const double b4 = x0 > 0 ? b4num / 16.0 / x0 : 0.0;
-        if (b4 > 0) {
-            const double h = std::pow(384.0 * 1e-11 / b4, 0.25);
-            const double want = std::ceil(std::log2(t_max / h));
-            n = want > 16 ? 65536 : (want < 6 ? 64 : (1 << (int)want));
-        }
-    }
+    // the table grid and search disc: the same rule as flints_plan
+    const TableGrid tg = table_grid(nside, K, lmax, cl, spin == 2 ? cl_bb : nullptr);
+    const int n = tg.n;
+    const double t_max = tg.t_max;
     if (n > NA_MAX_INTERVALS)
         return na_fail(FLINTS_EINVAL,
                        "flints_lens_noalloc: the xi table needs %d intervals, above the fixed maximum %d", n,
                        NA_MAX_INTERVALS);
-    const int R_rings = (int)std::ceil(1.5 * r * (double)nside) + 1;
+    const int R_rings = tg.R_rings;
     if (2 * R_rings + 2 > 32) return na_fail(FLINTS_EINVAL, "flints_lens_noalloc: search disc spans too many rings");
 
     // device address of the scratch array, set up once per device
@@ -161,7 +151,7 @@ extern "C" int flints_lens_noalloc(int64_t nside, int lmax, const double *cl, co
     NA_CK(cudaStreamSynchronize(st), "xi table");
     if (!(xi0 > 0.0) || !std::isfinite(xi0))
         return na_fail(FLINTS_EINVAL, "flints_lens_noalloc: xi(0) = %g is not positive", xi0);
-    NA_CK(finish_table(d_f, d_g, n, t_max / n, xi0, d_c64, d_c32, st), "table coefficients");
+    NA_CK(finish_table(d_f, d_g, n, tg.h, xi0, d_c64, d_c32, st), "table coefficients");
 
     LensArgs a{};
     a.nside = nside;
@@ -176,12 +166,12 @@ extern "C" int flints_lens_noalloc(int64_t nside, int lmax, const double *cl, co
     a.tab.c64 = d_c64;
     a.tab.c32 = d_c32;
     a.tab.t_max = t_max;
-    a.tab.inv_h = n / t_max;
+    a.tab.inv_h = tg.inv_h;
     a.tab.inv_h_hi = (float)a.tab.inv_h;
     a.tab.inv_h_lo = (float)(a.tab.inv_h - (double)a.tab.inv_h_hi);
     a.tab.n = n;
     a.xi0 = xi0;
-    a.r2 = r * r;
+    a.r2 = tg.r2;
     a.counters = d_cnt;
     NA_CK(launch_lens(spin, K, precision, a, R_rings, LaunchCfg{0, 0, 0}, st), "lens kernel launch");
 #undef NA_CK

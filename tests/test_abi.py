@@ -72,3 +72,22 @@ def _load_missing(tmp_path):
         api.load_library(str(tmp_path / "missing.so"))
     finally:
         api._lib = saved
+
+
+def test_noalloc_rejects_misaligned_buffers_without_gpu(lib_path):
+    """flints_lens_noalloc checks the alignment rules of the plan-based entry points on
+    the host, before any device call (the addresses below are never dereferenced)."""
+    lib = api.load_library()
+    cl = (ctypes.c_double * 33)(*([0.0, 0.0] + [1.0] * 31))
+    a16, a8 = 0x10000, 0x10008
+    cases = [(0, a16, a16, a16, 0x10004, b"var 8 bytes"),   # var misaligned
+             (2, a8, a16, a16, a16, b"map, out 16 bytes"),   # spin-2 map on 8 bytes
+             (0, a16, a8, a16, a16, b"defl 16 bytes"),       # deflections on 8 bytes
+             (2, a16, a16, a8, a16, b"map, out 16 bytes")]   # spin-2 output on 8 bytes
+    for spin, m, d, o, v, msg in cases:
+        rc = lib.flints_lens_noalloc(16, 32, cl, None, spin, 16, 0, 0, 12, m, d, o, v, None, None)
+        assert rc == 1 and msg in lib.flints_noalloc_last_error(), (spin, lib.flints_noalloc_last_error())
+    # spin 0 maps and outputs need 8 bytes only: this call passes the checks up to the
+    # device address lookup, so it is not made here
+    rc = lib.flints_measure_fma_peak(0, 0, None, None)
+    assert rc == 1 and b"tflops is NULL" in lib.flints_measure_last_error()
