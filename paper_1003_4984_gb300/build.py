@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 SO = os.path.join(LIBDIR, "libflints.so")
 SOURCES = ["api.cu", "xi_table.cu", "lens_spin0.cu", "lens_spin1.cu", "lens_spin2.cu", "lens_spin2a.cu", "noalloc.cu",
-           "batch_p0.cu", "batch_p1.cu", "synth.cu", "paper.cu"]
+           "batch_p0.cu", "batch_p1.cu", "synth.cu", "paper.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
