@@ -1,8 +1,13 @@
 """Host-side layout of a multi-GPU run: one process per GPU (torchrun
-environment), independent problems per rank (every target pixel is
-independent, so ranks lens their own maps and batches: weak scaling, no
-collective on the data path); timings are bracketed by barriers and joined by
-a MAX reduction, and the whole-job rate counts the points of all ranks.
+environment), one sky split across the ranks.  Every target pixel is
+independent (the per-pixel locality that makes the method suitable for
+distributed memory, abstract and Sec. 5), so the targets of one map are cut
+into contiguous RING ranges balanced by count, one per rank; each rank holds
+the whole source map (replicated: a stencil may reach pixels of a neighbouring
+range) and lenses its own range with no collective on the data path; outputs
+stay sharded or are gathered to rank 0 afterwards.  Timings are bracketed by
+barriers and joined by a MAX reduction, and the whole-job rate counts the
+points of all ranks.
 
 Backend-agnostic: the CUDA benchmark uses NCCL, the tests gloo on CPU.
 """
@@ -29,14 +34,69 @@ def init(backend: str):
     return dist
 
 
-def batch_index(rank: int, i: int, n_batches: int) -> int:
-    """Target batch of step i on a rank: ranks start 5 batches apart around the sky."""
-    return (rank * 5 + i) % n_batches
+def shard_bounds(n: int, world: int) -> list[tuple[int, int]]:
+    """Contiguous [start, stop) target ranges of a sky of n targets, one per rank,
+    balanced by count (sizes differ by at most one); they tile [0, n) once."""
+    base, extra = divmod(int(n), int(world))
+    out, start = [], 0
+    for r in range(world):
+        stop = start + base + (1 if r < extra else 0)
+        out.append((start, stop))
+        start = stop
+    return out
 
 
-def seed(rank: int, base: int) -> int:
-    """Per-rank seed of the synthetic map and deflections (independent problems)."""
-    return base + rank
+def step_window(bounds: tuple[int, int], step: int, batch: int) -> tuple[int, int]:
+    """(first, count) of benchmark step ``step`` on a rank whose range is ``bounds``:
+    ``batch`` consecutive targets of the range, successive steps walking through it
+    (a range shorter than the batch is lensed whole)."""
+    start, stop = bounds
+    length = stop - start
+    if length <= batch:
+        return start, length
+    span = length - batch + 1
+    return start + (step * batch) % span, batch
+
+
+def lens_shard(lens_range, bounds: tuple[int, int], batch: int):
+    """Lens a rank's whole range in calls of at most ``batch`` consecutive targets.
+
+    ``lens_range(first, count)`` lenses targets [first, first+count) and returns
+    (value, variance) tensors; the results are concatenated in RING order."""
+    import torch
+
+    start, stop = bounds
+    vals, vars_ = [], []
+    for first in range(start, stop, batch):
+        v, s2 = lens_range(first, min(batch, stop - first))
+        vals.append(v)
+        vars_.append(s2)
+    if not vals:
+        return None, None
+    return torch.cat(vals), torch.cat(vars_)
+
+
+def gather_shards(local, bounds: list[tuple[int, int]], dist, rank: int, dst: int = 0):
+    """Whole-sky tensor on rank ``dst`` from every rank's range (None on the others;
+    ``local`` itself when there is no process group).  Shards are padded to the
+    longest one for the collective and trimmed afterwards."""
+    if dist is None:
+        return local
+    import torch
+
+    longest = max(b - a for a, b in bounds)
+    pad = torch.zeros((longest,) + tuple(local.shape[1:]), dtype=local.dtype, device=local.device)
+    pad[:local.shape[0]] = local
+    parts = [torch.empty_like(pad) for _ in bounds] if rank == dst else None
+    dist.gather(pad, parts, dst=dst)
+    if rank != dst:
+        return None
+    return torch.cat([p[:b - a] for p, (a, b) in zip(parts, bounds)])
+
+
+def seed(base: int) -> int:
+    """Seed of the synthetic map and deflections: one sky, the same on every rank."""
+    return base
 
 
 def barrier(dist) -> None:
