@@ -2,14 +2,20 @@
 
 Requests (a contiguous RING target range of a resident map, with its spin,
 stencil size K and deflections) are admitted while their device buffers fit
-in an HBM budget, then advanced chunk by chunk: every scheduling round builds
+in an HBM budget that also counts the resident maps and plans (a request that
+alone exceeds what is left runs when nothing else is admitted), then advanced
+chunk by chunk: every scheduling round builds
 a batch of chunks taken round-robin from all admitted requests (new arrivals
 join the next round while earlier requests are still running) and runs it as
 one persistent batched launch.  Two batch objects on two streams keep one
 batch executing while the next is staged, so work from different requests
 overlaps on the device.  Maps and plans (xi tables) stay resident between
-requests.  Completion is detected on the host with CUDA events; there is no
-device-side waiting.
+requests.  Admission work (deflections produced by a callable, output
+buffers) is queued on the caller's current stream, and each launch stream
+waits for it before reading them.  Completion is detected on the host with
+CUDA events; there is no device-side waiting.  A request can be cancelled
+while pending or running: no further chunks of it are scheduled and its
+memory returns once its chunks in flight have finished.
 
 Results do not depend on how requests are mixed: each target is computed by
 the same per-point code from the same inputs whatever batch carries it.
@@ -41,6 +47,8 @@ class Request:
     admitted_at: float | None = None
     finished_at: float | None = None
     nbytes: int = 0
+    cancelled: bool = False
+    scheduled_points: int = 0
 
     @property
     def latency(self) -> float | None:
@@ -68,10 +76,12 @@ class LensServer:
         self.maps: dict = {}
         self.spectra: dict = {}
         self.plans: dict = {}
-        self.in_use = 0
+        self.in_use = 0          # device bytes of the admitted requests' buffers
+        self.resident = 0        # device bytes of the resident maps and plans
         self.pending: collections.deque = collections.deque()
         self.active: list = []
         self.finished: list = []
+        self.cancelled: list = []
         self.streams = [torch.cuda.Stream(self.dev), torch.cuda.Stream(self.dev)]
         self.batches = [Batch(max_jobs), Batch(max_jobs)]
         self.inflight: list = [None, None]
@@ -80,9 +90,14 @@ class LensServer:
 
     # ------------------------------------------------------------ residency
     def register_map(self, nside: int, spin: int, tensor, cl, cl_bb=None):
-        """Keep an unlensed map and its spectrum resident on the device."""
-        self.maps[(nside, spin)] = tensor
-        self.spectra[(nside, spin)] = (cl, cl_bb)
+        """Keep an unlensed map and its spectrum resident on the device (counted
+        against the HBM budget)."""
+        key = (nside, spin)
+        if key in self.maps:
+            self.resident -= self.maps[key].numel() * self.maps[key].element_size()
+        self.maps[key] = tensor
+        self.spectra[key] = (cl, cl_bb)
+        self.resident += tensor.numel() * tensor.element_size()
 
     def plan_for(self, req: Request) -> Plan:
         key = (*req.map_key, req.K, req.precision)
@@ -90,9 +105,15 @@ class LensServer:
             cl, bb = self.spectra[req.map_key]
             nside, spin = req.map_key
             self.plans[key] = Plan(nside, cl, bb, spin=spin, K=req.K, precision=req.precision)
+            self.resident += self.plans[key].device_bytes()
             if self.cfg is not None:
                 self.plans[key].set_launch(self.cfg)
         return self.plans[key]
+
+    def used_bytes(self) -> int:
+        """Device bytes counted against the budget: resident maps and plans plus the
+        buffers of the admitted requests."""
+        return self.resident + self.in_use
 
     @staticmethod
     def request_bytes(req: Request) -> int:
@@ -103,12 +124,37 @@ class LensServer:
     def submit(self, req: Request):
         self.pending.append(req)
 
+    def cancel(self, rid: int) -> bool:
+        """Cancel request ``rid``: a pending one is dropped, an admitted one gets no
+        further chunks and returns its memory when its chunks in flight finish.
+        Returns False if the request is unknown or already finished."""
+        for req in list(self.pending):
+            if req.rid == rid:
+                self.pending.remove(req)
+                req.cancelled = True
+                self.cancelled.append(req)
+                return True
+        for req in self.active:
+            if req.rid == rid and not req.cancelled:
+                req.cancelled = True
+                req.next_point = req.count  # nothing more is scheduled
+                if req.done_points == req.scheduled_points:
+                    self._release(req)
+                return True
+        return False
+
+    def _release(self, req: Request):
+        self.active.remove(req)
+        self.in_use -= req.nbytes
+        (self.cancelled if req.cancelled else self.finished).append(req)
+
     def _admit(self, now: float):
         torch = self.torch
         while self.pending:
             req = self.pending[0]
             nb = self.request_bytes(req)
-            if self.in_use + nb > self.budget and self.active:
+            self.plan_for(req)  # its tables stay resident and count against the budget
+            if self.used_bytes() + nb > self.budget and self.active:
                 break  # wait for memory to free up (an oversized request runs alone)
             self.pending.popleft()
             spin = req.map_key[1]
@@ -120,7 +166,6 @@ class LensServer:
             req.nbytes = nb
             req.admitted_at = now
             self.in_use += nb
-            self.plan_for(req)
             self.active.append(req)
 
     # ------------------------------------------------------------ scheduling
@@ -139,6 +184,7 @@ class LensServer:
                 if n < left and n > 1:
                     n &= ~1  # keep the next chunk's outputs on 16-byte boundaries
                 a = req.next_point
+                req.scheduled_points = a + n
                 jobs.append((self.plan_for(req), req.first + a, n, self.maps[req.map_key], req.defl[a:a + n],
                              req.out[a:a + n], req.var[a:a + n], None))
                 chunks.append((req, n))
@@ -152,6 +198,13 @@ class LensServer:
         if not jobs:
             return False
         b, s = self.batches[slot], self.streams[slot]
+        # the admission work (deflections from a callable, output buffers) was queued on the
+        # current stream: the launch stream waits for it, and the caching allocator is told
+        # that these buffers are in use on the launch stream
+        s.wait_stream(self.torch.cuda.current_stream(self.dev))
+        for req, _ in chunks:
+            for t in (req.defl, req.out, req.var):
+                t.record_stream(s)
         b.stage(jobs, self.cfg.tile_points if self.cfg else 0)
         b.launch(self.cfg, stream=s)
         ev = self.torch.cuda.Event()
@@ -169,17 +222,20 @@ class LensServer:
             req.done_points += n
             if req.done_points == req.count:
                 req.finished_at = now
-                self.active.remove(req)
-                self.in_use -= req.nbytes
-                self.finished.append(req)
+                self._release(req)
+            elif req.cancelled and req.done_points == req.scheduled_points:
+                req.finished_at = now
+                self._release(req)
         self.inflight[slot] = None
         return True
 
     # ------------------------------------------------------------ main loop
-    def run(self, requests, time_scale: float = 1.0, idle_sleep: float = 2e-4):
+    def run(self, requests, time_scale: float = 1.0, idle_sleep: float = 2e-4, on_tick=None):
         """Serve ``requests`` (sorted by arrival time, seconds) in real time.
 
-        Returns the finished requests; latency = completion - arrival."""
+        ``on_tick(server, now)``, if given, is called once per scheduling round (a
+        caller can cancel requests from it).  Returns the finished requests (the
+        cancelled ones are in ``self.cancelled``); latency = completion - arrival."""
         t0 = time.perf_counter()
 
         def now():
@@ -190,6 +246,8 @@ class LensServer:
             t = now()
             while todo and todo[0].arrival <= t:
                 self.submit(todo.popleft())
+            if on_tick is not None:
+                on_tick(self, t)
             self._admit(t)
             busy = False
             for slot in (0, 1):
