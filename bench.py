@@ -37,6 +37,19 @@ METRIC = "lensed pts/s at Nside 4096 spin-2 K=32, mixed vs FP64 @2e-4 rel err; p
 MIXED_DRAM_BYTES_PER_POINT = 13.868288e6 / (1 << 18)
 BATCH = 1 << 24
 W = wl.C3
+
+
+def _hbm_peak_gbs() -> float:
+    """Measured copy bandwidth of the GB300s (MEASURED_PEAKS.json, hbm_gbs) when the
+    file is present, else the profiling recipe's fallback of 6.8 TB/s."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
+HBM_PEAK_GBS = _hbm_peak_gbs()
 # where the nvidia-smi clock samples of the timed regions are written
 OUT_DIR = os.environ.get("FLINTS_BENCH_OUT", "/tmp")
 
@@ -57,6 +70,8 @@ def parse():
                          "spin1: a deflection field (spin 1) lensed at Nside 4096; paper: the 9/36-pixel stencil "
                          "with tabulated inverses (lensing at 4096, supersampling 2048 -> 4096)")
     ap.add_argument("--duration", type=float, default=45.0, help="c5: seconds of Poisson arrivals")
+    ap.add_argument("--serving-seconds", type=float, default=15.0,
+                    help="c3: seconds of the Poisson serving leg appended to the run (0: none)")
     ap.add_argument("--profile-case", choices=["mixed", "fp64", "paper1", "paper2", "paper1m", "paper2m", "paper2q", "paper2qm"], default=None,
                     help="small case for ncu: two launches on 2^18 targets of the resident c3 map (mixed, "
                          "fp64), or on 2^20 targets of the tabulated-inverse route at level 1 or 2 (m: mixed; q: "
@@ -127,7 +142,9 @@ def config(n_gpus):
                         "(damping l = 2500), B = 0, K = 32",
             "batch_points": BATCH, "npix": W.npix, "nside": W.nside, "lmax": W.lmax, "K": W.K, "spin": 2,
             "l2": "inputs larger than L2 (3.2 GB resident map, 268 MB deflections per step)",
-            "parallelism": f"weak, {n_gpus} rank(s), distinct target batches per rank"}
+            "parallelism": f"{n_gpus} rank(s): one sky split into contiguous RING ranges balanced by count, one "
+                           f"per rank, source map replicated, no data-path collective (weak: 2^24 targets per "
+                           f"rank per step)"}
 
 
 # ------------------------------------------------------------ CPU oracle leg
@@ -210,7 +227,7 @@ def cpu_oracle(seconds: float, aug: bool = False):
     ctx = mp.get_context("spawn")
     per = 256
     # calibrate on one chunk, then size the sample to about `seconds` of wall time
-    with ctx.Pool(cores) as pool:
+    with ctx.Pool(cores, initializer=None if aug else _oracle_init) as pool:
         n0, t0 = pool.map(_oracle_worker, [(50_000_000, per, 11, aug)])[0]
         rate1 = n0 / max(t0, 1e-9)
         chunks = max(cores, int(seconds * rate1 * cores / per))
@@ -270,6 +287,29 @@ class Clocks:
 
 
 # ---------------------------------------------------------------- our arm
+def measured_peaks():
+    """FP32 and FP64 multiply-add throughput measured on this GPU before the timed region
+    (flints_measure_fma_peak), next to the peaks derived from unit counts and clocks."""
+    import paper_1003_4984_gb300 as fl
+    from paper_1003_4984_gb300 import flops
+
+    return {"fp32_tflops": max(fl.measure_fma_peak("mixed") for _ in range(3)),
+            "fp64_tflops": max(fl.measure_fma_peak("fp64") for _ in range(3)),
+            "fp32_derived_tflops": flops.FP32_PEAK_TFLOPS, "fp64_nominal_tflops": flops.FP64_PEAK_TFLOPS,
+            "how": "flints_measure_fma_peak: independent FMA chains on every SM, best of 3, CUDA events"}
+
+
+def roofline_entry(rate, flops_per_point, peak_tflops, kernel, peak_note, **extra):
+    """ALU roofline of a lens kernel: the method's algorithmic flops per point times the
+    measured point rate, against a measured pipe peak."""
+    achieved = rate * flops_per_point / 1e12
+    out = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+           "frac": achieved / peak_tflops, "flops_per_point": flops_per_point, "kernel": kernel,
+           "peak_note": peak_note}
+    out.update(extra)
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -289,20 +329,31 @@ def run_ours(args):
 
     dev = torch.device("cuda", local)
     fl.load_library()
+    peaks = measured_peaks()
     cl, bb = W.cl()
     stream = torch.cuda.current_stream(dev)
+    # one sky, the same on every rank (replicated source map); the targets are split into
+    # contiguous RING ranges, one per rank, and each rank keeps the deflections of its range
+    bounds = ranks.shard_bounds(W.npix, world)[rank]
     g = torch.Generator(device=dev)
-    g.manual_seed(ranks.seed(rank, 1234))
+    g.manual_seed(ranks.seed(1234))
     qu = torch.randn((W.npix, 2), dtype=torch.float64, device=dev, generator=g)
-    nb = W.npix // BATCH  # 12 batches per sky
-    defl = torch.randn((nb * BATCH, 2), dtype=torch.float64, device=dev, generator=g) * (wl.DEFLECTION_RMS / math.sqrt(2))
+    defl_sky = torch.randn((W.npix, 2), dtype=torch.float64, device=dev, generator=g) * (
+        wl.DEFLECTION_RMS / math.sqrt(2))
+    defl = defl_sky[bounds[0]:bounds[1]].clone()
+    del defl_sky
     out = torch.empty((BATCH, 2), dtype=torch.float64, device=dev)
     var = torch.empty(BATCH, dtype=torch.float64, device=dev)
     plans = {p: fl.Plan(W.nside, cl, bb, spin=2, K=W.K, precision=p, flags=flags) for p in ("mixed", "fp64")}
 
+    def window(i):
+        first, count = ranks.step_window(bounds, i, BATCH)
+        return first, count, defl[first - bounds[0]:first - bounds[0] + count]
+
     def step(plan, i):
-        b = ranks.batch_index(rank, i, nb)
-        plan.lens(qu, defl[b * BATCH:(b + 1) * BATCH], out, var, first=b * BATCH, count=BATCH)
+        first, count, d = window(i)
+        plan.lens(qu, d, out[:count], var[:count], first=first, count=count)
+        return count
 
     def timed(plan, steps, warmup):
         for i in range(warmup):
@@ -311,23 +362,26 @@ def run_ours(args):
         ranks.barrier(dist)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
         ev[0].record(stream)
+        pts = 0
         for i in range(steps):
-            step(plan, warmup + i)
+            pts += step(plan, warmup + i)
             ev[i + 1].record(stream)
         torch.cuda.synchronize(dev)
         per = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
         total = ranks.max_over_ranks(ev[0].elapsed_time(ev[steps]), dist, dev)
-        return total, per
+        return total, per, pts
 
     plans["mixed"].reset_stats()
     with Clocks(os.path.join(OUT_DIR, f"bench_clocks_r{rank}.csv")) as clk:
-        total_ms, per = timed(plans["mixed"], args.steps, args.warmup)
+        total_ms, per, pts = timed(plans["mixed"], args.steps, args.warmup)
     clocks = clk.summary(local)
     st = plans["mixed"].stats()
-    fp_total, fp_per = timed(plans["fp64"], max(1, args.fp64_steps), 1)
+    fp_total, fp_per, fp_pts = timed(plans["fp64"], max(1, args.fp64_steps), 1)
 
-    # end to end through the public API with pinned host buffers
-    nb_e2e = min(args.steps, 3)
+    # end to end through the public API with pinned host buffers: every step uploads its
+    # deflections and a twelfth of the map (the whole-sky upload amortised over the 12
+    # steps of a sky) and downloads value and variance
+    nb = 12
     h_map = torch.empty((W.npix, 2), dtype=torch.float64, pin_memory=True)
     h_defl = torch.empty((BATCH, 2), dtype=torch.float64, pin_memory=True)
     h_out = torch.empty((BATCH, 2), dtype=torch.float64, pin_memory=True)
@@ -337,66 +391,84 @@ def run_ours(args):
     slice_len = (W.npix + nb - 1) // nb
 
     def e2e_step(i):
-        b = ranks.batch_index(rank, i, nb)
-        s0 = b * slice_len
+        s0 = (i % nb) * slice_len
         s1 = min(W.npix, s0 + slice_len)
         qu[s0:s1].copy_(h_map[s0:s1], non_blocking=True)  # this step's share of the map upload
-        d = defl[b * BATCH:(b + 1) * BATCH]
-        d.copy_(h_defl, non_blocking=True)
-        plans["mixed"].lens(qu, d, out, var, first=b * BATCH, count=BATCH)
-        h_out.copy_(out, non_blocking=True)
-        h_var.copy_(var, non_blocking=True)
+        first, count, d = window(i)
+        d.copy_(h_defl[:count], non_blocking=True)
+        plans["mixed"].lens(qu, d, out[:count], var[:count], first=first, count=count)
+        h_out[:count].copy_(out[:count], non_blocking=True)
+        h_var[:count].copy_(var[:count], non_blocking=True)
+        return count
 
     e2e_step(0)
     torch.cuda.synchronize(dev)
     ranks.barrier(dist)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for i in range(nb_e2e):
-        e2e_step(1 + i)
+    e2e_pts = 0
+    for i in range(args.steps):
+        e2e_pts += e2e_step(1 + i)
     e1.record(stream)
     torch.cuda.synchronize(dev)
     e2e_ms = ranks.max_over_ranks(e0.elapsed_time(e1), dist, dev)
     h2d = slice_len * 16 + BATCH * 16
     d2h = BATCH * 16 + BATCH * 8
 
+    serving = None
+    if world == 1 and args.serving_seconds > 0 and not aug:
+        serving = serving_leg(dev, args.serving_seconds)
+
     if rank != 0:
         dist.destroy_process_group()
         return
     n_gpus = world
     ms_step = total_ms / args.steps
-    value = ranks.job_rate(BATCH * args.steps, total_ms / 1e3, n_gpus)
-    fp_value = ranks.job_rate(BATCH * len(fp_per), fp_total / 1e3, n_gpus)
-    kern_ms = statistics.mean(per)
-    fl32 = flops.augmented_flops(W.K, True) if aug else flops.mixed_fp32_flops(W.K, 2)
-    achieved = fl32 * BATCH / (kern_ms / 1e3) / 1e12
-    fl64 = flops.augmented_flops(W.K, False) if aug else flops.fp64_flops(W.K, 2)
-    achieved64 = fl64 * BATCH / (statistics.mean(fp_per) / 1e3) / 1e12
+    value = ranks.job_rate(pts, total_ms / 1e3, n_gpus)
+    fp_value = ranks.job_rate(fp_pts, fp_total / 1e3, n_gpus)
+    rate = BATCH / (statistics.mean(per) / 1e3)  # one launch per step: the kernel's own rate
+    rate64 = BATCH / (statistics.mean(fp_per) / 1e3)
+    f_method = flops.augmented_flops(W.K, False) if aug else flops.fp64_flops(W.K, 2)
+    f_issue = flops.augmented_flops(W.K, True) if aug else flops.mixed_fp32_flops(W.K, 2)
+    kname = 3 if aug else 2
+    roof = roofline_entry(
+        rate, f_method, peaks["fp32_tflops"], "lens_kernel<32,%d,mixed> (double-float on the FP32 pipe)" % kname,
+        "measured FP32 multiply-add throughput in this run (flints_measure_fma_peak); derived peak "
+        "152 SMs x 128 lanes x 2 x 2.07 GHz = %.1f TFLOP/s" % flops.FP32_PEAK_TFLOPS,
+        traffic=None if aug else MIXED_DRAM_BYTES_PER_POINT * BATCH,
+        traffic_note="dram bytes read + written per launch, from the ncu capture of 2^18 targets scaled to "
+                     "the launch (outputs of that case stayed in L2; at 2^24 targets 24 B/point more are "
+                     "written back)",
+        flops_convention="the method's own arithmetic per point (FP64 operation count, flops.fp64_flops): "
+                         "the double-float path executes the same steps, each as several FP32 instructions",
+        issue_flops_per_point=f_issue,
+        issue_note="FP32 flops executed per point by the double-float emulation (instruction cost, not "
+                   "algorithmic work)",
+        issue_frac=rate * f_issue / 1e12 / peaks["fp32_tflops"],
+        hbm={"bytes_per_point": 56, "achieved_gbs": rate * 56 / 1e9, "peak_gbs": HBM_PEAK_GBS,
+             "frac": rate * 56 / 1e9 / HBM_PEAK_GBS})
+    roof64 = roofline_entry(rate64, f_method, peaks["fp64_tflops"], "lens_kernel<32,%d,fp64>" % kname,
+                            "measured FP64 multiply-add throughput in this run (flints_measure_fma_peak); "
+                            "nominal 1.25 TFLOP/s")
     line = {
-        "metric": METRIC + (" (augmented xi+/xi- estimator)" if aug else ""), "value": value, "unit": "pts/s", "n_gpus": n_gpus, "steps": args.steps,
+        "metric": METRIC + (" (augmented xi+/xi- estimator)" if aug else ""), "value": value, "unit": "pts/s",
+        "n_gpus": n_gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64 in/out; double-float (2 x f32) factor, f64 geometry",
         "data": "synthetic: white-noise Q/U map (the work does not depend on the values) and per-pixel Gaussian "
                 "deflections of 2.5 arcmin rms",
         "config": config(n_gpus),
-        "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
+        "step_p50_ms": float(np.percentile(per, 50)), "step_p99_ms": float(np.percentile(per, 99)),
+        "serving": serving,
         "fp64": {"value": fp_value, "unit": "pts/s", "ms_per_step": statistics.mean(fp_per),
                  "steps": len(fp_per)},
         "mixed_over_fp64": value / fp_value,
         "mixed_stats": st,
-        "e2e": {"value": ranks.job_rate(BATCH * nb_e2e, e2e_ms / 1e3, n_gpus), "unit": "pts/s",
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": flops.FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / flops.FP32_PEAK_TFLOPS,
-                     "traffic": None if aug else MIXED_DRAM_BYTES_PER_POINT * BATCH,
-                     "traffic_note": "ncu capture of 2^18 targets scaled to the launch; outputs of that case "
-                                     "stayed in L2 (at 2^24 targets 24 B/point more are written back)",
-                     "kernel": "lens_kernel<32,%d,mixed> (FP32 pipe, double-float)" % (3 if aug else 2),
-                     "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
-                     "flops_per_point": fl32},
-        "roofline_fp64": {"bound": "alu", "achieved": achieved64, "peak": flops.FP64_PEAK_TFLOPS,
-                          "unit": "TFLOP/s", "frac": achieved64 / flops.FP64_PEAK_TFLOPS,
-                          "kernel": "lens_kernel<32,%d,fp64>" % (3 if aug else 2), "flops_per_point": fl64},
+        "e2e": {"value": ranks.job_rate(e2e_pts, e2e_ms / 1e3, n_gpus), "unit": "pts/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": args.steps},
+        "roofline": roof,
+        "roofline_fp64": roof64,
+        "peaks_measured": peaks,
         "cpu_baseline": cpu,
         "clocks": clocks,
         "gpu_launches": args.steps,
@@ -481,20 +553,21 @@ def run_c4(args):
 
 
 # ------------------------------------------------------------ c5 serving arm
-def run_c5(args):
+def serving_leg(dev, duration: float, seed: int = 5):
     """Poisson stream of lensing requests (point counts log-uniform in [1e4, 1e8],
     spin 0/2, K 16/32, Nside 512..4096) served with continuous batching under a
-    150 GB HBM budget at about 80 % of the measured capacity."""
+    150 GB HBM budget (resident maps and plans included) at about 80 % of the
+    capacity measured by a calibration burst; latency = completion - arrival."""
     import torch
 
     import paper_1003_4984_gb300 as fl
     from paper_1003_4984_gb300.serving import LensServer, Request, latency_stats
 
     fl.load_library()
-    dev = torch.device("cuda", 0)
     g = torch.Generator(device=dev)
-    g.manual_seed(5)
-    server = LensServer(hbm_budget=150e9, batch_points=1 << 22, chunk_points=1 << 21, max_jobs=64)
+    g.manual_seed(seed)
+    server = LensServer(hbm_budget=150e9, batch_points=1 << 22, chunk_points=1 << 21, max_jobs=64,
+                        device=dev.index or 0)
     for nside in (512, 1024, 2048, 4096):
         for spin in (0, 2):
             lmax = min(2 * nside, 4096)
@@ -504,10 +577,10 @@ def run_c5(args):
             m = torch.randn((npix,) if spin == 0 else (npix, 2), dtype=torch.float64, device=dev, generator=g)
             server.register_map(nside, spin, m, cl)
 
-    def defl_maker(count, seed):
+    def defl_maker(count, sd):
         def make():
             gg = torch.Generator(device=dev)
-            gg.manual_seed(seed)
+            gg.manual_seed(sd)
             return torch.randn((count, 2), dtype=torch.float64, device=dev, generator=gg) * (
                 wl.DEFLECTION_RMS / math.sqrt(2))
         return make
@@ -521,54 +594,103 @@ def run_c5(args):
     torch.cuda.synchronize(dev)
     capacity = sum(r.count for r in creqs) / (time.perf_counter() - t)
     server.finished.clear()
+    launches0 = server.launches
     mean_points = (1e8 - 1e4) / math.log(1e8 / 1e4)
     rate = 0.8 * capacity / mean_points
-    n_jobs = max(10, int(rate * args.duration))
+    n_jobs = max(10, int(rate * duration))
     stream = wl.job_stream(n_jobs, rate, seed=500)
     reqs = [Request(i, (j.nside, j.spin), j.K, j.first, j.count, defl_maker(j.count, i), arrival=j.arrival_s)
             for i, j in enumerate(stream)]
     done = server.run(reqs)
     torch.cuda.synchronize(dev)
     st = latency_stats(done)
-    plans_failed = sum(p.stats()["failed"] for p in server.plans.values())
+    failed = sum(p.stats()["failed"] for p in server.plans.values())
+    server.close()
+    return {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"], "max_ms": st["max_ms"],
+            "pts_per_s": st["points_per_s"], "requests": st["requests"], "points": st["points"],
+            "span_s": st["span_s"], "arrival_rate_hz": rate, "capacity_pts_per_s": capacity,
+            "launches": server.launches - launches0, "failed": failed,
+            "load": "Poisson arrivals at 80 % of the measured capacity, point counts log-uniform in [1e4, 1e8] "
+                    "(capped at Npix), spin 0/2, K 16/32, Nside 512..4096, mixed precision, 150 GB HBM budget "
+                    "including the resident maps and xi tables, deflections generated on the device at "
+                    "admission; latency = completion - arrival"}
+
+
+def run_c5(args):
+    """The serving load alone, for ``--duration`` seconds of arrivals."""
+    import torch
+
+    dev = torch.device("cuda", 0)
+    sv = serving_leg(dev, args.duration)
     print(json.dumps({
         "metric": "serving latency p50/p99 (ms) and lensed pts/s under Poisson load (c5)",
-        "value": st["points_per_s"], "unit": "pts/s", "n_gpus": 1, "higher_is_better": True,
-        "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mean_ms": st["mean_ms"], "max_ms": st["max_ms"],
-        "requests": st["requests"], "points": st["points"], "span_s": st["span_s"],
-        "arrival_rate_hz": rate, "capacity_pts_per_s": capacity, "launches": server.launches,
-        "config": {"workload": "c5: Poisson arrivals at 80 % of measured capacity, counts log-uniform [1e4, 1e8] "
-                               "(capped at Npix), spin 0/2, K 16/32, Nside 512..4096, mixed precision, "
-                               "150 GB HBM budget, resident maps and xi tables",
-                   "batch_points": 1 << 22, "chunk_points": 1 << 21},
+        "value": sv["pts_per_s"], "unit": "pts/s", "n_gpus": 1, "higher_is_better": True,
+        "p50_ms": sv["p50_ms"], "p99_ms": sv["p99_ms"], "serving": sv,
+        "config": {"workload": "c5: " + sv["load"], "batch_points": 1 << 22, "chunk_points": 1 << 21},
         "data": "synthetic white-noise maps; deflections generated on the device at admission",
-        "failed": plans_failed}))
-    server.close()
+        "gpu_launches": 16 * sv["launches"]}))
 
 
 # ----------------------------------------------------------- reference arm
+REF_STEP = 1 << 16  # targets per step of the reference arm (the oracle on the host cores)
+REF_CHUNK = 256
+
+
+def _oracle_init():
+    """Pool initializer: build the oracle's correlation tables once per process."""
+    sys.path.insert(0, ROOT)
+    from oracle import xi
+
+    cl, bb = W.cl()
+    t_max, n = xi.grid_rule(np.abs(cl) + np.abs(bb), W.K, W.nside)
+    if (t_max, n) not in _TABLE_CACHE:
+        _TABLE_CACHE[(t_max, n)] = xi.spin2_tables(cl, bb, t_max, n)
+
+
 def run_reference(args):
+    """The reference arm: the FP64 oracle (as it stands) on all host cores, on the same
+    workload, metric and unit as our arm.  One step is a bounded sample of REF_STEP
+    targets -- REF_STEP / REF_CHUNK chunks of consecutive RING targets spread over the
+    sky, a different set each step -- timed by wall clock around the whole step; the
+    warm-up steps run the same way untimed.  Under torchrun only rank 0 runs."""
+    import multiprocessing as mp
+
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    per_step = []
-    for _ in range(args.warmup):
-        pass
-    steps = max(1, args.steps)
-    budget = max(20.0, min(150.0, 10.0 * steps)) / steps
-    cpu = None
-    for _ in range(steps):
-        cpu = cpu_oracle(budget)
-        per_step.append(cpu["value"])
-    value = statistics.mean(per_step)
-    ms_per_step = BATCH / value * 1e3
+    cores = os.cpu_count() or 1
+    steps, warm = max(1, args.steps), max(0, args.warmup)
+    nchunk = REF_STEP // REF_CHUNK
+    rng = np.random.default_rng(2718)
+
+    def chunks():
+        starts = rng.integers(0, W.npix - REF_CHUNK, nchunk)
+        return [(int(s_), REF_CHUNK, 11, False) for s_ in starts]
+
+    ctx = mp.get_context("spawn")
+    per = []
+    with ctx.Pool(cores, initializer=_oracle_init) as pool:
+        for _ in range(warm):
+            pool.map(_oracle_worker, chunks())
+        for _ in range(steps):
+            work = chunks()
+            t = time.perf_counter()
+            res = pool.map(_oracle_worker, work)
+            per.append(time.perf_counter() - t)
+            assert sum(r[0] for r in res) == REF_STEP
+    total = sum(per)
+    value = steps * REF_STEP / total
+    sample = (f"{steps} steps of {REF_STEP} targets of the c3 workload, each {nchunk} chunks of {REF_CHUNK} "
+              f"consecutive RING pixels at seeded random places on the sky (hashed-normal Q/U values, per-pixel "
+              f"deflections), {total:.1f} s wall on {cores} spawned processes; the GPU arm's step is {BATCH} "
+              f"targets")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pts/s", "n_gpus": world,
-            "steps": steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "steps": steps, "warmup": warm, "ms_per_step": 1e3 * total / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (see cpu_baseline.sample)",
-            "config": config(world),
-            "cpu_baseline": {"value": value, "unit": "pts/s", "cores": cpu["cores"], "kind": "oracle",
-                             "sample": cpu["sample"]},
+            "config": dict(config(world), step_points=REF_STEP),
+            "step_p50_ms": float(np.percentile(per, 50)) * 1e3, "step_p99_ms": float(np.percentile(per, 99)) * 1e3,
+            "cpu_baseline": {"value": value, "unit": "pts/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "pts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
