@@ -172,6 +172,21 @@ __device__ __forceinline__ void anc_add_prod(anc &a, df x, df y) {
     t = __fmaf_rn(x.lo, y.hi, t);
     a.l = __fadd_rn(a.l, t);
 }
+// a += h*h + 2*h*l + l*l, the square of the unnormalised pair (h, l)
+__device__ __forceinline__ void anc_add_sq(anc &a, float h, float l) {
+    const float h0 = a.h;
+    a.h = __fmaf_rn(h, h, h0);
+    float t = __fmaf_rn(h, h, __fsub_rn(h0, a.h));
+    t = __fmaf_rn(l, __fmaf_rn(2.0f, h, l), t);
+    a.l = __fadd_rn(a.l, t);
+}
+// Double-float split of x whose high word lies on the grid of [M, 2M) (M = 1.5 * 2^E,
+// grid 2^(E-23)), for |x| <= 2^(E-1): differences of two such high words are exact
+// in FP32, and the low word keeps x to about 2^(E-48).
+__device__ __forceinline__ df df_on_grid(double x, float M) {
+    const float h = __fsub_rn(__fadd_rn(__double2float_rn(x), M), M);
+    return {h, __double2float_rn(x - (double)h)};
+}
 // Anchor for partial sums bounded by b >= 0: 6 * 2^e with 2^e > b (b finite).
 __device__ __forceinline__ float anc_anchor(float b) {
     const unsigned ex = (__float_as_uint(b) >> 23) & 0xffu;  // b < 2^(ex - 126)

@@ -212,7 +212,9 @@ __device__ __forceinline__ df table_eval<df>(const TableDev &tab, df t) {
     // that term, and the outer step, in double-float.
     const float q = __fmul_rn(s.hi, __fmaf_rn(s.hi, c1.z, c1.x));
     const df r = df_addf(df{c0.z, c0.w}, q);
-    return df_add(df_mul(r, s), df{c0.x, c0.y});
+    // f and s (m0 + ...) are both at most xi(0) = 1 in size: the sum's error is
+    // about 2^-44 absolute
+    return df_add_fast(df_mul(r, s), df{c0.x, c0.y});
 }
 
 template <class R, int S>
@@ -332,12 +334,19 @@ __device__ __forceinline__ Holo32 holonomy32(float ui, float vi, float uj, float
     return {-8.0f * x2 * q, -4.0f * x * (1.0f - x2) * q};
 }
 
-// conj(a) b (1 + delta), delta from holonomy32
+// conj(a) b (1 + delta), delta from holonomy32.  a and b are unit complex
+// numbers, so the two real dot products are anchored sums of products bounded
+// by 1 (anchor 6); the FP32 correction b delta joins their low words.
 __device__ __forceinline__ Cx<df> transported_phase(Cx<df> a, Cx<df> b, const Holo32 &h) {
-    const df br = df_add(df_mul(a.re, b.re), df_mul(a.im, b.im));
-    const df bi = df_sub(df_mul(a.re, b.im), df_mul(a.im, b.re));
-    const float cr = br.hi * h.dr - bi.hi * h.di, ci = br.hi * h.di + bi.hi * h.dr;
-    return {df_addf(br, cr), df_addf(bi, ci)};
+    anc ar{6.0f, 0.0f}, ai{6.0f, 0.0f};
+    anc_add_prod(ar, a.re, b.re);
+    anc_add_prod(ar, a.im, b.im);
+    anc_add_prod(ai, a.re, b.im);
+    anc_sub_prod(ai, a.im, b.re);
+    const float hr = __fsub_rn(ar.h, 6.0f), hi = __fsub_rn(ai.h, 6.0f);  // exact
+    const float br = __fadd_rn(hr, ar.l), bi = __fadd_rn(hi, ai.l);        // FP32 values for the correction
+    const float cr = br * h.dr - bi * h.di, ci = br * h.di + bi * h.dr;
+    return {two_sum(hr, __fadd_rn(ar.l, cr)), two_sum(hi, __fadd_rn(ai.l, ci))};
 }
 
 // Both spin-2 phases of the pair (i -> j), d = X_j - X_i: exp(2i(a_ij - a_ji)) of
@@ -601,13 +610,16 @@ __device__ __forceinline__ bool bordered_cholesky_anchored(Elem *mat, int lane) 
     constexpr float C_BOUNDED = 6.0f;
     float ynorm2 = 0.0f;  // |(L^-1 y)_{<j}|^2 of the data row (row NROW - 1), FP32, identical in every lane
     for (int j = 0; j < N; ++j) {
+        // s = 2^ls lanes per row group: the largest power of two with (NROW - j) s <= 32,
+        // i.e. ls = 5 - ceil(log2(NROW - j)) (at least 0); g = 32 / s groups
         const int nrows = NROW - j;
-        int s = 1;
-        while ((s << 1) * nrows <= 32) s <<= 1;
-        const int g = 32 / s;
-        const int part = lane & (s - 1), grp = lane / s;
+        const int cl2 = nrows > 1 ? 32 - __clz(nrows - 1) : 0;
+        const int ls = cl2 < 5 ? 5 - cl2 : 0;
+        const int s = 1 << ls, g = 32 >> ls;
+        const int part = lane & (s - 1), grp = lane >> ls;
         const Elem *Lj = mat + tri<N>(j, 0);
-        // anchor of the data row at this column (its initial entry plus the running norm)
+        // anchor of the data row at this column (its initial entry plus the running
+        // norm; the square root from rsqrtf, within a few ulps, is covered by 1.01)
         float cy;
         {
             const Elem y0 = mat[tri<N>(NROW - 1, j)];
@@ -617,7 +629,8 @@ __device__ __forceinline__ bool bordered_cholesky_anchored(Elem *mat, int lane) 
             } else {
                 ay = fabsf(y0.hi);
             }
-            cy = anc_anchor(fmaf(1.001f, ay + sqrtf(ynorm2), 1e-30f));
+            const float yn = fmaxf(ynorm2, 1e-30f);
+            cy = anc_anchor(fmaf(1.01f, ay + yn * rsqrtf(yn), 1e-30f));
         }
         Elem srow[NT];
 #pragma unroll
@@ -684,7 +697,7 @@ __device__ __forceinline__ bool bordered_cholesky_anchored(Elem *mat, int lane) 
         O::pivot(d, ljj, il);
         // the data row's new entry (held by the parts of its group) joins the running norm
         {
-            const int ty = (NROW - 1 - j) / g, gy = (NROW - 1 - j) - ty * g;
+            const int ty = (NROW - 1 - j) >> (5 - ls), gy = (NROW - 1 - j) - ty * g;
             float vr = 0.0f, vi = 0.0f;
 #pragma unroll
             for (int t = 0; t < NT; ++t) {
@@ -764,7 +777,6 @@ __device__ bool solve_point(SM &sm, const PointA &P, int lane, double nugget, co
     using T = typename O::T;
     using G = Geom<R, SM>;
     constexpr int RPL = Shape<K>::RPL, NTRI = Shape<K>::NTRI;
-    constexpr int NROW = K + 2;
     using Elem = typename SM::Elem;
     Elem *mat = sm.u.mat;
 
@@ -789,6 +801,9 @@ __device__ bool solve_point(SM &sm, const PointA &P, int lane, double nugget, co
 
     // ---- assembly of the lower triangle
     {
+        // anchor of the squared chords in the double-float path: every chord between
+        // stencil members is at most the table's t_max
+        [[maybe_unused]] const float ct = anc_anchor((float)tab.t_max * 1.0001f);
         int i = 0, j = lane;  // q = lane -> (i, j) with q = i(i+1)/2 + j
         while (j > i) {
             j -= i + 1;
@@ -804,10 +819,23 @@ __device__ bool solve_point(SM &sm, const PointA &P, int lane, double nugget, co
                     e.im = O::zero();
                 }
             } else {
-                const T dx = O::sub(G::x(sm, j), G::x(sm, i));
-                const T dy = O::sub(G::y(sm, j), G::y(sm, i));
-                const T dz = O::sub(G::z(sm, j), G::z(sm, i));
-                const T t = O::add_fast(O::add_fast(O::mul(dx, dx), O::mul(dy, dy)), O::mul(dz, dz));
+                T t;
+                [[maybe_unused]] T dx, dy, dz;
+                if constexpr (std::is_same<R, double>::value) {
+                    dx = O::sub(G::x(sm, j), G::x(sm, i));
+                    dy = O::sub(G::y(sm, j), G::y(sm, i));
+                    dz = O::sub(G::z(sm, j), G::z(sm, i));
+                    t = O::add_fast(O::add_fast(O::mul(dx, dx), O::mul(dy, dy)), O::mul(dz, dz));
+                } else {
+                    // the offsets' high words share one grid (df_on_grid), so their
+                    // differences are exact; the squared chord is an anchored sum
+                    // (every partial sum <= t_max)
+                    anc ta{ct, 0.0f};
+                    anc_add_sq(ta, __fsub_rn(sm.gx[j].hi, sm.gx[i].hi), __fsub_rn(sm.gx[j].lo, sm.gx[i].lo));
+                    anc_add_sq(ta, __fsub_rn(sm.gy[j].hi, sm.gy[i].hi), __fsub_rn(sm.gy[j].lo, sm.gy[i].lo));
+                    anc_add_sq(ta, __fsub_rn(sm.gz[j].hi, sm.gz[i].hi), __fsub_rn(sm.gz[j].lo, sm.gz[i].lo));
+                    t = two_sum(__fsub_rn(ta.h, ct), ta.l);
+                }
                 const T fv = table_eval<R>(tab, t);
                 if constexpr (SPIN == 0) {
                     e = fv;
@@ -1347,9 +1375,12 @@ __device__ __forceinline__ void process_tile(const LensArgs &a, int R_rings, int
                     }
                     if (MIXED) {
                         SMf &smf = *reinterpret_cast<SMf *>(wbase);
-                        smf.gx[i] = df_from(ox);
-                        smf.gy[i] = df_from(oy);
-                        smf.gz[i] = df_from(oz);
+                        // offsets |X_i - n'| <= r (the K-th chord is inside the disc): high
+                        // words on the grid of [M, 2M), M = 1.5 * 2^E with 2^E >= 4 r
+                        const float Mg = 0.25f * anc_anchor(4.0f * sqrtf((float)a.r2));
+                        smf.gx[i] = df_on_grid(ox, Mg);
+                        smf.gy[i] = df_on_grid(oy, Mg);
+                        smf.gz[i] = df_on_grid(oz, Mg);
                         smf.gnz[i] = df_from(cz);
                         smf.gns[i] = df_from(ns);
                         smf.gnc[i] = df_from(nc);
