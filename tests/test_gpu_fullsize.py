@@ -3,9 +3,10 @@ lmax 4096, K = 32, in the launch configuration the benchmark times (batches of
 2^24 consecutive targets of a resident whole-sky map).
 
 The source map is a band-limited realisation synthesised exactly on bands of
-rings around three sampled target stretches (north cap, cap/belt transition,
-equator); the GPU lenses the whole 2^24-target batches containing them, and
-the sampled outputs are compared with
+rings around sampled target stretches (north cap, cap/belt transition,
+equator, south cap), or around 10^4 seeded random pixels on rings drawn over
+the whole sky; the GPU lenses the whole 2^24-target batches containing them,
+and the sampled outputs are compared with
   * the FP64 oracle (same tabulated correlation function): parity metric
     max|gpu - oracle| / sigma_map <= 1e-9 (FP64 path), 1e-6 (mixed path);
   * the exact benchmark of Sec. 3.2, the spherical-harmonic sum at the
@@ -44,11 +45,11 @@ class BandMap:
 
 
 def _bands(W, n_targets):
-    """Three target stretches (north cap, cap/belt transition, equator): for each the
+    """Four target stretches (north cap, cap/belt transition, equator, south cap): for each the
     first pixel, the count, the deflections of its whole 2^24-target batch and the
     rings its stencils reach (from the oracle's own search), plus one ring of margin."""
     out = []
-    for ring in (W.nside // 2, W.nside + 3, 2 * W.nside):
+    for ring in (W.nside // 2, W.nside + 3, 2 * W.nside, 4 * W.nside - W.nside // 3):
         first, n_in = [int(x[0]) for x in hp.ring_info(W.nside, np.array([ring]))[:2]]
         start = first + n_in // 3
         b0 = (start // BATCH) * BATCH
@@ -218,3 +219,95 @@ def test_supersampling_2048_to_4096(fl):
     print(f"supersampling 2048 -> 4096: measured {meas:.3e}, predicted {pred:.3e} (Table 1 precision column)")
     assert 0.6 < ratio < 1.5
     assert meas < 3e-3
+
+
+def _whole_sky_sample(W, n_targets, seed):
+    """n_targets seeded random pixels over the whole sky: 64 rings drawn uniformly in z
+    (so that caps and belt are sampled by area) plus both poles' first rings, both
+    cap/belt transitions and the equator, with random pixels on each ring; the source
+    map is then synthesised exactly on the rings the stencils reach."""
+    rng = np.random.default_rng(seed)
+    N = W.nside
+    z = rng.uniform(-1.0, 1.0, 64)
+    rings = {int(r) for r in np.clip(hp.ring_above(N, z), 1, 4 * N - 1)}
+    rings |= {1, 2, 4 * N - 2, 4 * N - 1, N - 1, N, N + 1, 3 * N - 1, 3 * N, 3 * N + 1, 2 * N}
+    rings = np.array(sorted(rings))
+    first, n_in = hp.ring_info(N, rings)[:2]
+    per = n_targets // rings.size
+    pix = []
+    for f, n in zip(first, n_in):
+        k = min(int(n), per)
+        pix.append(int(f) + rng.choice(int(n), size=k, replace=False))
+    pix = np.unique(np.concatenate(pix))
+    while pix.size < n_targets:  # fill up with random pixels of the sampled rings (the pole rings are short)
+        extra = n_targets - pix.size
+        rr = rng.choice(rings.size, size=extra)
+        cand = first[rr] + (rng.random(extra) * n_in[rr]).astype(np.int64)
+        pix = np.unique(np.concatenate([pix, cand]))
+    return pix[:n_targets]
+
+
+@pytest.mark.parametrize("W", [wl.C3], ids=["c3"])
+def test_exact_benchmark_on_random_pixels_over_the_whole_sky(fl, W):
+    """Sec. 3.2 / Table 2 / abstract: the lensed map against the harmonic sum at the
+    displaced directions, on 10^4 seeded random pixels over the whole sky (both caps,
+    both cap/belt transitions, the equator): relative L2 <= 2e-4 at Nside 4096; the
+    same pixels also give the parity of both GPU paths against the oracle."""
+    import torch
+
+    n_targets = 10_000
+    cl, bb = W.cl()
+    alm = wl.draw_alm(cl, W.seed_map)
+    targets = _whole_sky_sample(W, n_targets, W.seed_sample)
+    batches = np.unique(targets // BATCH)
+    defl_b = {int(b): wl.random_deflection(min(BATCH, W.npix - int(b) * BATCH), 2000 + int(b)) for b in batches}
+    defl = np.concatenate([defl_b[int(t // BATCH)][t - (t // BATCH) * BATCH][None, :] for t in targets])
+    tv = kr.displace(W.nside, targets, defl)
+    idx, _ = kr.knn(W.nside, tv, W.K)
+    stencil_rings = np.unique(hp.pix2ring(W.nside, idx.ravel())[0])
+    rings = np.unique(np.clip(np.concatenate([stencil_rings - 1, stencil_rings, stencil_rings + 1]), 1,
+                              4 * W.nside - 1))
+    p, v = sht.synth_rings(W.nside, rings, W.lmax, alm, spin=W.spin)
+    vals = v if W.spin == 0 else np.stack([v.real, v.imag], axis=1)
+    dev = torch.device("cuda")
+    shape = (W.npix,) if W.spin == 0 else (W.npix, 2)
+    m = torch.zeros(shape, dtype=torch.float64, device=dev)
+    m[torch.from_numpy(p).to(dev)] = torch.from_numpy(vals).to(dev)
+    sigma = float(np.sqrt(np.mean(vals ** 2) * (1 if W.spin == 0 else 2)))
+    tab, x0, _, _ = oracle_table(cl, bb, W.spin, W.K, W.nside)
+    got = {}
+    for precision in ("fp64", "mixed"):
+        plan = fl.Plan(W.nside, cl, bb, spin=W.spin, K=W.K, precision=precision)
+        v_all = np.empty(n_targets, dtype=np.float64 if W.spin == 0 else np.complex128)
+        s_all = np.empty(n_targets)
+        for b in batches:
+            b0 = int(b) * BATCH
+            bn = min(BATCH, W.npix - b0)
+            out, var, st = plan.lens(m, torch.from_numpy(defl_b[int(b)]).to(dev),
+                                     var=torch.empty(bn, dtype=torch.float64, device=dev),
+                                     status=torch.empty(bn, dtype=torch.uint8, device=dev), first=b0, count=bn)
+            torch.cuda.synchronize()
+            sel = np.nonzero(targets // BATCH == b)[0]
+            loc = torch.from_numpy(targets[sel] - b0).to(dev)
+            o = to_host(out[loc])
+            v_all[sel] = o if W.spin == 0 else o[:, 0] + 1j * o[:, 1]
+            s_all[sel] = to_host(var[loc])
+            assert int((st[loc] & fl.ST_FAILED).sum()) == 0
+        s = plan.stats()
+        assert s["failed"] == 0 and s["window"] == 0, s
+        got[precision] = (v_all, s_all)
+        plan.close()
+    ref = kr.lens(W.nside, W.K, W.spin, BandMap(p, vals), defl, targets, tab, x0)
+    for precision, tol in (("fp64", 1e-9), ("mixed", 1e-6)):
+        v, s2 = got[precision]
+        assert parity_metric(v, ref.value, sigma) <= tol, precision
+        assert parity_metric(s2, ref.variance, x0) <= tol, precision
+    truth = sht.synth_points(W.lmax, alm, ref.target, spin=W.spin)
+    south = ref.target[:, 2] < 0
+    for precision in ("fp64", "mixed"):
+        err = got[precision][0] - truth
+        rel_l2 = math.sqrt(np.mean(np.abs(err) ** 2) / np.mean(np.abs(truth) ** 2))
+        rel_s = math.sqrt(np.mean(np.abs(err[south]) ** 2) / np.mean(np.abs(truth[south]) ** 2))
+        print(f"{W.name} whole sky, {n_targets} random pixels ({south.sum()} south), {precision}: "
+              f"rel L2 {rel_l2:.3e} (south {rel_s:.3e})")
+        assert rel_l2 <= 2e-4 and rel_s <= 2e-4, precision
