@@ -736,8 +736,10 @@ def run_ss(args):
         plan.close()
     value, per, xi0, st = res["mixed"]
     precision_pred = math.sqrt(float(var.mean()) / xi0)  # last batch, FP64 plan
-    fl32 = flops.mixed_fp32_flops(Wc.K, 0)
-    achieved = fl32 * BATCH / (statistics.mean(per) / 1e3) / 1e12
+    peaks = measured_peaks()
+    roof = roofline_entry(BATCH / (statistics.mean(per) / 1e3), flops.fp64_flops(Wc.K, 0), peaks["fp32_tflops"],
+                          "lens_kernel<32,0,mixed>", "measured FP32 multiply-add throughput in this run",
+                          traffic=None, issue_flops_per_point=flops.mixed_fp32_flops(Wc.K, 0))
     print(json.dumps({
         "metric": "supersampled pts/s, Nside 2048 -> 4096, lmax 4096, K=32, spin 0", "value": value,
         "unit": "pts/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -751,9 +753,7 @@ def run_ss(args):
         "predicted_precision": precision_pred,
         "paper_table1": "Nside 2048 -> 4096, l 4096: 3e-3 (9 neighbours), 3e-4 (36 neighbours); serial "
                         "Xeon E5410 3.3 / 19 min per map",
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": flops.FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / flops.FP32_PEAK_TFLOPS, "traffic": None,
-                     "kernel": "lens_kernel<32,0,mixed>", "flops_per_point": fl32},
+        "roofline": roof, "peaks_measured": peaks,
         "mixed_stats": st, "gpu_launches": args.steps}))
 
 
@@ -801,8 +801,10 @@ def run_spin1(args):
         res[precision] = (BATCH * steps / (ev[0].elapsed_time(ev[steps]) / 1e3), per, plan.stats())
         plan.close()
     value, per, st = res["mixed"]
-    fl32 = flops.mixed_fp32_flops(K, 1)
-    achieved = fl32 * BATCH / (statistics.mean(per) / 1e3) / 1e12
+    peaks = measured_peaks()
+    roof = roofline_entry(BATCH / (statistics.mean(per) / 1e3), flops.fp64_flops(K, 1), peaks["fp32_tflops"],
+                          "lens_kernel<32,1,mixed>", "measured FP32 multiply-add throughput in this run",
+                          traffic=None, issue_flops_per_point=flops.mixed_fp32_flops(K, 1))
     print(json.dumps({
         "metric": "lensed pts/s of a spin-1 deflection field at Nside 4096, K=32", "value": value, "unit": "pts/s",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(per),
@@ -812,9 +814,7 @@ def run_spin1(args):
                    "batch_points": BATCH},
         "fp64": {"value": res["fp64"][0], "ms_per_step": statistics.mean(res["fp64"][1])},
         "mixed_over_fp64": value / res["fp64"][0],
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": flops.FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / flops.FP32_PEAK_TFLOPS, "traffic": None,
-                     "kernel": "lens_kernel<32,1,mixed>", "flops_per_point": fl32},
+        "roofline": roof, "peaks_measured": peaks,
         "mixed_stats": st, "gpu_launches": args.steps}))
 
 
@@ -999,12 +999,12 @@ def run_paper(args):
                         "table_bytes": info["table_bytes"], "window": info["window"],
                         "nugget_slots": info["nugget_slots"], "failed_slots": info["failed_slots"],
                         "predicted_precision": math.sqrt(float(var.mean()) / info["xi0"])}
-                    if task.endswith("aug"):
-                        arm["fp64_tflops"] = flops.paper_augmented_fp64_flops(K) * BATCH / sec / 1e12
-                    elif precision == "fp64":
-                        arm["fp64_tflops"] = flops.paper_fp64_flops(K, spin) * BATCH / sec / 1e12
-                    else:
-                        arm["fp32_tflops"] = flops.paper_mixed_fp32_flops(K, spin) * BATCH / sec / 1e12
+                    # the method's flops per target (whatever precision executes them), and for
+                    # double-float arms the FP32 instruction cost of the emulation beside them
+                    f_method = flops.paper_augmented_fp64_flops(K) if task.endswith("aug") else flops.paper_fp64_flops(K, spin)
+                    arm["method_tflops"] = f_method * BATCH / sec / 1e12
+                    if precision == "mixed":
+                        arm["issue_fp32_tflops"] = flops.paper_mixed_fp32_flops(K, spin) * BATCH / sec / 1e12
                     res[f"{task}_y{y}_{precision}"] = arm
                     plan.close()
                     torch.cuda.empty_cache()
@@ -1013,7 +1013,12 @@ def run_paper(args):
     head = res["lens_y1_mixed"]
     ratios = {f"{t}_y{y}": res[f"{t}_y{y}_mixed"]["value"] / res[f"{t}_y{y}_fp64"]["value"]
               for t in ("lens", "supersample", "lens_qu") for y in (1, 2)}
-    achieved = head["fp32_tflops"]
+    peaks = measured_peaks()
+    roof = roofline_entry(head["value"], flops.paper_fp64_flops(9), peaks["fp32_tflops"], "paper::apply_kernel_df<9>",
+                          "measured FP32 multiply-add throughput in this run", traffic=None,
+                          issue_flops_per_point=flops.paper_mixed_fp32_flops(9))
+    roof64 = roofline_entry(res["lens_y1_fp64"]["value"], flops.paper_fp64_flops(9), peaks["fp64_tflops"],
+                            "paper::apply_kernel<9>", "measured FP64 multiply-add throughput in this run")
     print(json.dumps({
         "metric": "lensed pts/s, Nside 4096 T, lmax 4096, paper stencil (9 px) with tabulated inverses, mixed vs FP64",
         "value": head["value"], "unit": "pts/s", "n_gpus": 1, "steps": steps, "warmup": warm,
@@ -1029,10 +1034,7 @@ def run_paper(args):
         "paper_tables": "Table 2 (Nside 4096, 9 neighbours): init 16 min, interpolation 22 min per map; "
                         "Table 1 (2048 -> 4096): 3.3 min (9) / 19 min (36), precision 3e-3 / 3e-4; serial "
                         "Xeon E5410",
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": flops.FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / flops.FP32_PEAK_TFLOPS, "traffic": None,
-                     "kernel": "paper::apply_kernel_df<9>", "peak_kind": "FP32 from unit counts and 2070 MHz",
-                     "flops_per_point": flops.paper_mixed_fp32_flops(9)},
+        "roofline": roof, "roofline_fp64": roof64, "peaks_measured": peaks,
         "cpu_baseline": cpu, "clocks": clk.summary(0), "gpu_launches": steps}))
 
 
