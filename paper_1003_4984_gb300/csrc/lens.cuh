@@ -54,8 +54,9 @@ struct PointA {
 
 struct RingRec {
     double z, s, f;
+    double inv2nq;  // 1 / (2 nq): pixel j of the ring sits at phi = pi (j + f) inv2nq
     int64_t first;
-    int n_in, nq, j0, cnt, end, jref;
+    int n_in, j0, cnt, end, jref;
     // FP32 pre-selection key of pixel j of this ring:
     //   a32 + b32 sin^2(pi (j - jref + frac) / n_in)
     float a32, b32, frac, inv_n;
@@ -79,8 +80,7 @@ struct WarpSmem {
     // spin 2: per-neighbour target phase Phi0_i = phase(n' -> X_i), tangent-plane
     // coordinates (u, v) of X_i - n' at n', and squared chords to n'
     typename Ops<R>::T p0r[K], p0i[K], pu[K], pv[K];
-    double kt[K];
-    float ktf[K];
+    float ktf[K];  // squared chords to n' (FP32, for the spherical-excess correction)
     union U {
         struct Cand {
             RingRec rings[32];
@@ -889,30 +889,60 @@ __device__ bool solve_point(SM &sm, const PointA &P, int lane, double nugget, co
     if (!factor_bordered<K, 2, R>(mat, lane)) return false;
     // ---- value = z_c^H z_y = sum_k row_K[k] conj(row_K+1[k]);  variance = 1 - |z_c|^2
     double vr = 0.0, vi = 0.0, nc = 0.0;
+    if constexpr (std::is_same<R, df>::value) {
+        // double-float products and lane reduction on the FP32 pipe, one conversion at the end
+        dfacc ar{0.0f, 0.0f}, ai{0.0f, 0.0f}, an{0.0f, 0.0f};
 #pragma unroll
-    for (int r = 0; r < RPL; ++r) {
-        const int k = lane + 32 * r;
-        if (k < K) {
-            const Elem c = mat[tri<K>(K, k)], y = mat[tri<K>(K + 1, k)];
-            if constexpr (SPIN == 0) {
-                const double cd = O::to(c), yd = O::to(y);
-                vr = fma(cd, yd, vr);
-                nc = fma(cd, cd, nc);
-            } else {
-                const double cr = O::to(c.re), ci = O::to(c.im);
-                const double yr = O::to(y.re), yi = O::to(y.im);
-                // (cr + i ci)(yr - i yi)
-                vr = fma(cr, yr, fma(ci, yi, vr));
-                vi = fma(ci, yr, fma(-cr, yi, vi));
-                nc = fma(cr, cr, fma(ci, ci, nc));
+        for (int r = 0; r < RPL; ++r) {
+            const int k = lane + 32 * r;
+            if (k < K) {
+                const Elem c = mat[tri<K>(K, k)], y = mat[tri<K>(K + 1, k)];
+                if constexpr (SPIN == 0) {
+                    dfacc_add_prod(ar, c, y);
+                    dfacc_add_prod(an, c, c);
+                } else {  // (cr + i ci)(yr - i yi)
+                    dfacc_add_prod(ar, c.re, y.re);
+                    dfacc_add_prod(ar, c.im, y.im);
+                    dfacc_add_prod(ai, c.im, y.re);
+                    dfacc_sub_prod(ai, c.re, y.im);
+                    dfacc_add_prod(an, c.re, c.re);
+                    dfacc_add_prod(an, c.im, c.im);
+                }
             }
         }
-    }
+        df dr = dfacc_val(ar), di = dfacc_val(ai), dn = dfacc_val(an);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        vr += __shfl_xor_sync(FULL, vr, o);
-        vi += __shfl_xor_sync(FULL, vi, o);
-        nc += __shfl_xor_sync(FULL, nc, o);
+        for (int o = 16; o > 0; o >>= 1) {
+            dr = df_add(dr, O::shfl_xor(dr, o));  // the value's terms may cancel: full sum
+            if constexpr (SPIN != 0) di = df_add(di, O::shfl_xor(di, o));
+            dn = df_add_fast(dn, O::shfl_xor(dn, o));  // non-negative terms
+        }
+        vr = df_to(dr);
+        vi = df_to(di);
+        nc = df_to(dn);
+    } else {
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+            const int k = lane + 32 * r;
+            if (k < K) {
+                const Elem c = mat[tri<K>(K, k)], y = mat[tri<K>(K + 1, k)];
+                if constexpr (SPIN == 0) {
+                    vr = fma(c, y, vr);
+                    nc = fma(c, c, nc);
+                } else {
+                    // (cr + i ci)(yr - i yi)
+                    vr = fma(c.re, y.re, fma(c.im, y.im, vr));
+                    vi = fma(c.im, y.re, fma(-c.re, y.im, vi));
+                    nc = fma(c.re, c.re, fma(c.im, c.im, nc));
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            vr += __shfl_xor_sync(FULL, vr, o);
+            vi += __shfl_xor_sync(FULL, vi, o);
+            nc += __shfl_xor_sync(FULL, nc, o);
+        }
     }
     val_re = vr;
     val_im = vi;
@@ -1046,7 +1076,7 @@ template <int K, int SPIN, int MIXED>
 constexpr size_t warp_smem_bytes() {
     using SMd = WarpSmem<K, SPIN, double>;
     using SMf = WarpSmem<K, SPIN, df>;
-    static_assert(offsetof(SMd, gx) == offsetof(SMf, gx) && offsetof(SMd, kt) == offsetof(SMf, kt) &&
+    static_assert(offsetof(SMd, gx) == offsetof(SMf, gx) && offsetof(SMd, ktf) == offsetof(SMf, ktf) &&
                       offsetof(SMd, u) == offsetof(SMf, u),
                   "the FP64 and double-float views of a warp slice must share their layout");
     constexpr size_t WS = sizeof(SMd) > sizeof(SMf) ? sizeof(SMd) : sizeof(SMf);
@@ -1177,7 +1207,10 @@ __device__ __forceinline__ void process_tile(const LensArgs &a, int R_rings, int
                         const int cc = jh - jl + 1;
                         if (cc < rg.n_in) {
                             c = cc;
-                            int m = jl % rg.n_in;
+                            // jl >= -n_in - 2 (phi' from atan2 is in [-pi, pi], half < pi) and
+                            // jl <= n_in / 2: two conditional wraps give jl mod n_in
+                            int m = jl;
+                            if (m < 0) m += rg.n_in;
                             if (m < 0) m += rg.n_in;
                             j0 = m;
                         }
@@ -1187,9 +1220,11 @@ __device__ __forceinline__ void process_tile(const LensArgs &a, int R_rings, int
                     const double u = P.phi * ((double)rg.n_in * (0.5 / PI));
                     const double jr = floor(u - rg.f + 0.5);
                     rec.frac = (float)((jr + rg.f) - u);
-                    int64_t jri = (int64_t)jr % rg.n_in;
+                    // |u| <= n_in / 2, so jr lies in [-n_in / 2 - 1, n_in / 2 + 1]: one wrap each way
+                    int jri = (int)jr;
                     if (jri < 0) jri += rg.n_in;
-                    rec.jref = (int)jri;
+                    if (jri >= rg.n_in) jri -= rg.n_in;
+                    rec.jref = jri;
                     rec.a32 = lbf;
                     rec.b32 = den;
                     rec.inv_n = 1.0f / (float)rg.n_in;
@@ -1198,7 +1233,7 @@ __device__ __forceinline__ void process_tile(const LensArgs &a, int R_rings, int
                     rec.f = rg.f;
                     rec.first = rg.first;
                     rec.n_in = rg.n_in;
-                    rec.nq = rg.nq;
+                    rec.inv2nq = 1.0 / (2.0 * (double)rg.nq);  // beside ring_of's square root, not in the placement chain
                     rec.j0 = j0;
                     rec.cnt = c;
                     cnt = c;
@@ -1266,7 +1301,7 @@ __device__ __forceinline__ void process_tile(const LensArgs &a, int R_rings, int
                 const RingRec &rr = sm.u.cand.rings[pkd >> 24];
                 const int jj = (int)(pkd & 0xffffffu);
                 double sp, cp;
-                sincospi(((double)jj + rr.f) / (2.0 * (double)rr.nq), &sp, &cp);
+                sincospi(((double)jj + rr.f) * rr.inv2nq, &sp, &cp);
                 const double cx = rr.s * cp, cy = rr.s * sp, cz = rr.z;
                 const double ex = P.x - cx, ey = P.y - cy, ez = P.z - cz;
                 sm.u.cand.cx[c] = cx;
@@ -1364,15 +1399,14 @@ __device__ __forceinline__ void process_tile(const LensArgs &a, int R_rings, int
                 if (i < K) {
                     const unsigned c = id[r];
                     keyd[r] = __longlong_as_double((long long)key[r]);
-                    sm.kt[i] = keyd[r];
                     sm.ktf[i] = (float)keyd[r];
                     const double cx = sm.u.cand.cx[c], cy = sm.u.cand.cy[c], cz = sm.u.cand.cz[c];
                     const double ox = cx - P.x, oy = cy - P.y, oz = cz - P.z;
-                    const double ns = sqrt(cx * cx + cy * cy), nc = sm.u.cand.cc[c], nsn = sm.u.cand.cs[c];
-                    {
-                        const uint32_t pkd = sm.u.cand.cpix[c];
-                        pixr[r] = (uint32_t)(sm.u.cand.rings[pkd >> 24].first + (pkd & 0xffffffu));
-                    }
+                    const uint32_t pkd = sm.u.cand.cpix[c];
+                    const RingRec &rr = sm.u.cand.rings[pkd >> 24];
+                    // sin(theta) of the neighbour is its ring's s (cx, cy = s (cos phi, sin phi))
+                    const double ns = rr.s, nc = sm.u.cand.cc[c], nsn = sm.u.cand.cs[c];
+                    pixr[r] = (uint32_t)(rr.first + (pkd & 0xffffffu));
                     if (MIXED) {
                         SMf &smf = *reinterpret_cast<SMf *>(wbase);
                         // offsets |X_i - n'| <= r (the K-th chord is inside the disc): high
