@@ -32,9 +32,13 @@ import workloads as wl  # noqa: E402
 
 METRIC = "lensed pts/s at Nside 4096 spin-2 K=32, mixed vs FP64 @2e-4 rel err; p50/p99 ms"
 # DRAM bytes (read + write) per target of lens_kernel<32,2,mixed>, from the ncu capture of
-# `bench.py --profile-case mixed` (13.868 MB for 2^18 targets; profiles/lens_kernel_c3_full_sets.md),
+# `bench.py --profile-case mixed` (13.864 MB for 2^18 targets; profiles/lens_kernel_c3_full_sets.md),
 # scaled to a launch by its target count
-MIXED_DRAM_BYTES_PER_POINT = 13.868288e6 / (1 << 18)
+MIXED_DRAM_BYTES_PER_POINT = 13.863936e6 / (1 << 18)
+# warp instructions per target of the same kernel in the same capture (6.727 G for 2^18 targets):
+# with the measured point rate, the issue rate against 4 sub-partitions x 152 SMs x 2.07 GHz
+MIXED_WARP_INSTR_PER_POINT = 6.727009143e9 / (1 << 18)
+ISSUE_PEAK_PER_S = 4 * 152 * 2.07e9
 BATCH = 1 << 24
 W = wl.C3
 
@@ -445,6 +449,12 @@ def run_ours(args):
         issue_note="FP32 flops executed per point by the double-float emulation (instruction cost, not "
                    "algorithmic work)",
         issue_frac=rate * f_issue / 1e12 / peaks["fp32_tflops"],
+        issue_rate=None if aug else {
+            "warp_instr_per_point": MIXED_WARP_INSTR_PER_POINT,
+            "achieved_per_s": rate * MIXED_WARP_INSTR_PER_POINT, "peak_per_s": ISSUE_PEAK_PER_S,
+            "frac": rate * MIXED_WARP_INSTR_PER_POINT / ISSUE_PEAK_PER_S,
+            "note": "instructions per target from the ncu capture of 2^18 targets; the issue slot is the "
+                    "binding resource of the double-float emulation"},
         hbm={"bytes_per_point": 56, "achieved_gbs": rate * 56 / 1e9, "peak_gbs": HBM_PEAK_GBS,
              "frac": rate * 56 / 1e9 / HBM_PEAK_GBS})
     roof64 = roofline_entry(rate64, f_method, peaks["fp64_tflops"], "lens_kernel<32,%d,fp64>" % kname,
