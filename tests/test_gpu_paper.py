@@ -14,7 +14,7 @@ Checked against the oracle (oracle/faces.py):
     route (class_estimate) and against the per-target solve route (the
     Cholesky solve on each target's own stencil geometry):
     max |gpu - oracle| <= 1e-9 sigma_map and 1e-9 xi(0) for the FP64 path, 1e-6
-    for the mixed (double-float) path, the north star's two parity bars;
+    for the mixed (double-float) path, the two parity tolerances of this library;
   * at Nside 2048, lmax 4096 (y = 1, 2) on sampled targets of the full-sky call.
 """
 import numpy as np
