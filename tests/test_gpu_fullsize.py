@@ -247,12 +247,14 @@ def _whole_sky_sample(W, n_targets, seed):
     return pix[:n_targets]
 
 
-@pytest.mark.parametrize("W", [wl.C3], ids=["c3"])
+@pytest.mark.parametrize("W", [wl.C2, wl.C3], ids=["c2", "c3"])
 def test_exact_benchmark_on_random_pixels_over_the_whole_sky(fl, W):
     """Sec. 3.2 / Table 2 / abstract: the lensed map against the harmonic sum at the
     displaced directions, on 10^4 seeded random pixels over the whole sky (both caps,
-    both cap/belt transitions, the equator): relative L2 <= 2e-4 at Nside 4096; the
-    same pixels also give the parity of both GPU paths against the oracle."""
+    both cap/belt transitions, the equator): relative L2 <= 2e-4 at Nside 4096 (c3);
+    at Nside 2048 (c2) the error matches the predicted variance (<|err|^2 / sigma^2>
+    ~ 1, Fig. cmb_exp_error); the same pixels also give the parity of both GPU paths
+    against the oracle."""
     import torch
 
     n_targets = 10_000
@@ -305,9 +307,15 @@ def test_exact_benchmark_on_random_pixels_over_the_whole_sky(fl, W):
     truth = sht.synth_points(W.lmax, alm, ref.target, spin=W.spin)
     south = ref.target[:, 2] < 0
     for precision in ("fp64", "mixed"):
-        err = got[precision][0] - truth
+        v, s2 = got[precision]
+        err = v - truth
         rel_l2 = math.sqrt(np.mean(np.abs(err) ** 2) / np.mean(np.abs(truth) ** 2))
         rel_s = math.sqrt(np.mean(np.abs(err[south]) ** 2) / np.mean(np.abs(truth[south]) ** 2))
+        ratio = float(np.mean(np.abs(err) ** 2 / s2))
         print(f"{W.name} whole sky, {n_targets} random pixels ({south.sum()} south), {precision}: "
-              f"rel L2 {rel_l2:.3e} (south {rel_s:.3e})")
-        assert rel_l2 <= 2e-4 and rel_s <= 2e-4, precision
+              f"rel L2 {rel_l2:.3e} (south {rel_s:.3e}), <|err|^2/sigma^2> {ratio:.3f}")
+        if W.name == "c3":
+            assert rel_l2 <= 2e-4 and rel_s <= 2e-4, precision
+            assert ratio < 1.5, precision  # the nugget bounds the error from above at Nside 4096
+        else:
+            assert 0.8 < ratio < 1.25, precision
