@@ -40,7 +40,10 @@
  *   they set status bits and are counted in flints_stats.
  * - A plan owns its device memory (xi tables, counters) and is bound to the
  *   device that was current when it was created.  Plans are not thread-safe:
- *   use one plan per host thread or serialise calls on it.
+ *   use one plan per host thread or serialise calls on it.  Each lens call of
+ *   a plan takes the next of the plan's 64 tile-queue counters (warps take
+ *   their tiles from it), so at most 64 calls of one plan may be in flight on
+ *   the GPU at once, on one stream or several.
  */
 #ifndef FLINTS_H
 #define FLINTS_H
@@ -93,9 +96,12 @@ enum {
 enum {
     FLINTS_ST_NUGGET = 1u,    /* S + 1.49e-8 I had a non-positive pivot; nugget raised (x2 steps) */
     FLINTS_ST_FALLBACK = 2u,  /* mixed path: point re-solved in FP64 */
-    FLINTS_ST_WINDOW = 4u,    /* K-th neighbour outside the search disc: stencil widened */
-    FLINTS_ST_FAILED = 8u,    /* no positive-definite factor found: outputs are NaN */
-    FLINTS_ST_POLE = 16u      /* displaced direction within 1e-12 rad of a pole (spin-2 frame undefined) */
+    FLINTS_ST_WINDOW = 4u,    /* stencil not inside the search disc (K-nearest path) or a member chord
+                                 beyond the table (tabulated route): the point is not solved */
+    FLINTS_ST_FAILED = 8u,    /* no result (no positive-definite factor, stencil outside the disc or
+                                 non-finite deflection): outputs are NaN */
+    FLINTS_ST_POLE = 16u,     /* displaced direction within 1e-12 rad of a pole (spin-2 frame undefined) */
+    FLINTS_ST_INPUT = 32u     /* the target's deflection is not finite (with FLINTS_ST_FAILED) */
 };
 
 typedef struct {

@@ -24,7 +24,7 @@ FLINTS_SPIN2_AUGMENTED = 1  # spin 2: widely linear estimator with xi+ and xi-
 FLINTS_ROTATE_TO_TARGET = 2  # spin 2: P in the frame at n, not n'
 FLINTS_NO_VARIANCE = 4
 FLINTS_FORCE_FALLBACK = 256  # testing aid: mixed plans re-solve every point in FP64
-ST_NUGGET, ST_FALLBACK, ST_WINDOW, ST_FAILED, ST_POLE = 1, 2, 4, 8, 16
+ST_NUGGET, ST_FALLBACK, ST_WINDOW, ST_FAILED, ST_POLE, ST_INPUT = 1, 2, 4, 8, 16, 32
 
 
 class FlintsError(RuntimeError):

@@ -1162,8 +1162,15 @@ __device__ __forceinline__ void process_tile(const LensArgs &a, int R_rings, int
                     }
                 }
             }
-            P.zf = (float)z;
-            P.sf = (float)s;
+            if (!grid && !(isfinite(dd.x) && isfinite(dd.y))) {
+                // a non-finite deflection is not taken as none: the point is not solved
+                const double nan = __longlong_as_double(0x7ff8000000000000ll);
+                P.x = P.y = P.z = P.s = P.phi = nan;
+                P.flags = FLINTS_ST_INPUT;
+                z = nan;
+            }
+            P.zf = (float)P.z;
+            P.sf = (float)P.s;
             P.phif = (float)P.phi;
             P.ic = ring_above(N, z);
         }
@@ -1253,7 +1260,10 @@ __device__ __forceinline__ void process_tile(const LensArgs &a, int R_rings, int
         const int C = cnt;
         __syncwarp();
         bool fail = false;
-        if (C > NSLOT || C < K) {
+        if (flags & FLINTS_ST_INPUT) {
+            fail = true;
+            flags |= FLINTS_ST_FAILED;
+        } else if (C > NSLOT || C < K) {
             fail = true;
             flags |= FLINTS_ST_WINDOW | FLINTS_ST_FAILED;
         }
@@ -1528,8 +1538,20 @@ __global__ void __launch_bounds__(256, 2) lens_kernel(LensArgs a, int R_rings, i
     unsigned char *wbase = smem_raw + (size_t)warp * warp_smem_bytes<K, SPIN, MIXED>();
     const int64_t ntiles = (a.count + tile_pts - 1) / tile_pts;
     Counters ctr;
-    for (int64_t tile = (int64_t)blockIdx.x * wpb + warp; tile < ntiles; tile += (int64_t)gridDim.x * wpb)
-        process_tile<K, SPIN, MIXED>(a, R_rings, tile, tile_pts, wbase, lane, ctr);
+    if (a.queue) {
+        // dynamic tiles: the cost of a tile varies (candidate counts, near ties), and
+        // taking the next free tile keeps every warp busy to the end of the launch
+        for (;;) {
+            unsigned long long t = 0;
+            if (lane == 0) t = atomicAdd(a.queue, 1ull);
+            t = __shfl_sync(FULL, t, 0);
+            if ((int64_t)t >= ntiles) break;
+            process_tile<K, SPIN, MIXED>(a, R_rings, (int64_t)t, tile_pts, wbase, lane, ctr);
+        }
+    } else {
+        for (int64_t tile = (int64_t)blockIdx.x * wpb + warp; tile < ntiles; tile += (int64_t)gridDim.x * wpb)
+            process_tile<K, SPIN, MIXED>(a, R_rings, tile, tile_pts, wbase, lane, ctr);
+    }
     flush_counters(ctr, a.counters, lane);
 }
 

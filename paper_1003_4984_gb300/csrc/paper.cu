@@ -439,14 +439,23 @@ constexpr int APPLY_WARPS = 4;
 constexpr int GROUP = 10;  // lanes per target when K <= 10 (three targets per warp)
 
 // value, variance and status of target p from v = w . y and qc = w . c
+// true when target p is a lensing target whose deflection is not finite (its
+// outputs are NaN: target_of placed it at NaN)
+__device__ __forceinline__ bool bad_deflection(const ApplyArgs &a, int64_t p) {
+    if (a.nside_tgt > 0) return false;
+    const double2 dd = __ldg(reinterpret_cast<const double2 *>(a.defl) + p);
+    return !(isfinite(dd.x) && isfinite(dd.y));
+}
+
 __device__ __forceinline__ void finish_point(const ApplyArgs &a, int64_t p, int32_t sl, double v, double qc,
                                              bool any_win, unsigned long long &n_win, unsigned long long &n_nug,
                                              unsigned long long &n_fail) {
     const int steps = __ldg(a.slot_steps + sl);
-    uint8_t st = 0;
+    const bool bad = bad_deflection(a, p);
+    uint8_t st = bad ? FLINTS_ST_INPUT : 0;
     if (steps > 0) st |= FLINTS_ST_NUGGET;
     if (any_win) st |= FLINTS_ST_WINDOW;
-    if (steps < 0) {
+    if (steps < 0 || bad) {
         st |= FLINTS_ST_FAILED;
         v = __longlong_as_double(0x7ff8000000000000ll);
         qc = v;
@@ -456,7 +465,7 @@ __device__ __forceinline__ void finish_point(const ApplyArgs &a, int64_t p, int3
     if (a.status) a.status[p] = st;
     n_win += any_win;
     n_nug += steps > 0;
-    n_fail += steps < 0;
+    n_fail += steps < 0 || bad;
 }
 
 // Target p (displaced pixel first + p, or the pixel centre of the nside_tgt
@@ -479,6 +488,7 @@ __device__ __forceinline__ void target_of(const ApplyArgs &a, int64_t p, double 
         x = nx;
         y = ny;
         z = nz;
+        if (!(isfinite(dd.x) && isfinite(dd.y))) x = y = z = __longlong_as_double(0x7ff8000000000000ll);
         if (dl2 > 0.0) {
             // geodesic step of length |d| along d_theta e_theta + d_phi e_phi:
             // n' = cos|d| n + (sin|d|/|d|) (d_theta e_theta + d_phi e_phi).  For
@@ -845,10 +855,11 @@ __device__ __forceinline__ void finish_point_s2(const ApplyArgs &a, int64_t p, i
                                                 double qc, bool any_win, unsigned long long &n_win,
                                                 unsigned long long &n_nug, unsigned long long &n_fail) {
     const int steps = __ldg(a.slot_steps + sl);
-    uint8_t st = 0;
+    const bool bad = bad_deflection(a, p);
+    uint8_t st = bad ? FLINTS_ST_INPUT : 0;
     if (steps > 0) st |= FLINTS_ST_NUGGET;
     if (any_win) st |= FLINTS_ST_WINDOW;
-    if (steps < 0) {
+    if (steps < 0 || bad) {
         st |= FLINTS_ST_FAILED;
         vr = vi = qc = __longlong_as_double(0x7ff8000000000000ll);
     }
@@ -857,7 +868,7 @@ __device__ __forceinline__ void finish_point_s2(const ApplyArgs &a, int64_t p, i
     if (a.status) a.status[p] = st;
     n_win += any_win;
     n_nug += steps > 0;
-    n_fail += steps < 0;
+    n_fail += steps < 0 || bad;
 }
 
 // c_m = xi+(t)/xi+(0) exp(iS(a_tm - a_mt - pi)) of member m for the target

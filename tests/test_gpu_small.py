@@ -357,3 +357,75 @@ def test_wrong_spin_entry_point_is_an_error(fl, torch):
     z = torch.zeros((hp.npix(16), 2), dtype=torch.float64, device="cuda")
     with pytest.raises(fl.FlintsError):
         fl.api._check(fl.api._lib.flints_lens_spin2(plan._h, z.data_ptr(), z.data_ptr(), z.data_ptr(), None, None))
+
+
+# ------------------------------------------------------ non-finite inputs
+@pytest.mark.parametrize("spin", [0, 2])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_nonfinite_deflections_are_flagged_not_ignored(fl, torch, spin, precision):
+    """A NaN or infinite deflection is not a zero deflection: the point gets
+    FLINTS_ST_INPUT | FLINTS_ST_FAILED and NaN outputs, the counters count it as
+    failed, and every other point is unchanged (oracle parity)."""
+    nside, lmax, K = 16, 32, 16
+    npix = hp.npix(nside)
+    cl = wl.cl_tt(lmax, 24.0) if spin == 0 else wl.cl_ee(lmax, 24.0)
+    m = sht.synth_map(nside, lmax, wl.draw_alm(cl, 41), spin=spin)
+    if spin == 2:
+        m = np.stack([m.real, m.imag], axis=1)
+    m = np.ascontiguousarray(m)
+    defl = wl.random_deflection(npix, 42) * 4
+    bad = np.array([0, 5, 77, npix // 2, npix - 1])
+    defl_bad = defl.copy()
+    defl_bad[bad[0], 0] = np.nan
+    defl_bad[bad[1], 1] = np.inf
+    defl_bad[bad[2]] = [-np.inf, 0.0]
+    defl_bad[bad[3], 0] = np.nan
+    defl_bad[bad[3], 1] = np.nan
+    defl_bad[bad[4], 1] = -np.nan
+    plan = fl.Plan(nside, cl, spin=spin, K=K, precision=precision)
+    plan.reset_stats()
+    out, var, st = plan.lens(torch.from_numpy(m).cuda(), torch.from_numpy(defl_bad).cuda(),
+                             var=torch.empty(npix, dtype=torch.float64, device="cuda"),
+                             status=torch.empty(npix, dtype=torch.uint8, device="cuda"))
+    torch.cuda.synchronize()
+    o, v, s = to_host(out), to_host(var), to_host(st)
+    if spin == 2:
+        o = o[:, 0] + 1j * o[:, 1]
+    assert np.all(s[bad] == fl.ST_INPUT | fl.ST_FAILED)
+    assert np.all(np.isnan(o[bad])) and np.all(np.isnan(v[bad]))
+    good = np.setdiff1d(np.arange(npix), bad)
+    assert np.all(s[good] & (fl.ST_INPUT | fl.ST_FAILED) == 0)
+    assert plan.stats()["failed"] == bad.size
+    tab, x0, _, _ = oracle_table(cl, None, spin, K, nside)
+    ref = kr.lens(nside, K, spin, m, defl[good], good, tab, x0)
+    sigma = float(np.sqrt(np.mean(np.abs(ref.value) ** 2)))
+    assert parity_metric(o[good], ref.value, sigma) <= TOL[precision]
+    assert parity_metric(v[good], ref.variance, x0) <= TOL[precision]
+    plan.close()
+
+
+def test_nonfinite_deflections_on_the_tabulated_route(fl, torch):
+    """The same rule on the tabulated-inverse route (9-pixel stencil, FP64 and mixed)."""
+    nside, lmax = 16, 32
+    npix = hp.npix(nside)
+    cl = wl.cl_tt(lmax, 24.0)
+    m = torch.from_numpy(sht.synth_map(nside, lmax, wl.draw_alm(cl, 43))).cuda()
+    defl = wl.random_deflection(npix, 44) * 4
+    bad = np.array([3, 100, npix - 2])
+    defl_bad = defl.copy()
+    defl_bad[bad[0], 0] = np.nan
+    defl_bad[bad[1], 1] = np.inf
+    defl_bad[bad[2]] = np.nan
+    for precision in ("fp64", "mixed"):
+        plan = fl.PaperPlan(nside, cl, 1, precision)
+        st = torch.empty(npix, dtype=torch.uint8, device="cuda")
+        out, var = plan.lens(m, torch.from_numpy(defl_bad).cuda(), status=st)
+        ref, _ = plan.lens(m, torch.from_numpy(defl).cuda())
+        torch.cuda.synchronize()
+        o, s, r = to_host(out), to_host(st), to_host(ref)
+        assert np.all(s[bad] & (fl.ST_INPUT | fl.ST_FAILED) == fl.ST_INPUT | fl.ST_FAILED), precision
+        assert np.all(np.isnan(o[bad])) and np.all(np.isnan(to_host(var)[bad])), precision
+        good = np.setdiff1d(np.arange(npix), bad)
+        assert np.all(s[good] & fl.ST_INPUT == 0)
+        np.testing.assert_array_equal(o[good], r[good])
+        plan.close()
