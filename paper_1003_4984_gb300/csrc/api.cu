@@ -66,6 +66,8 @@ struct flints_plan_s {
     Coef64 *d_c64, *d_cm64;  // xi+ (spin 0: xi) and, spin 2, xi- interpolation coefficients
     float4 *d_c32, *d_cm32;
     unsigned long long *d_counters;
+    unsigned long long *d_queue;  // QUEUE_SLOTS tile-queue counters, one per launch in flight
+    unsigned queue_next;
     int64_t points;
     LaunchCfg cfg;
 };
@@ -132,6 +134,7 @@ static void free_plan_memory(flints_plan_s *p) {
     cudaFree(p->d_cm64);
     cudaFree(p->d_cm32);
     cudaFree(p->d_counters);
+    cudaFree(p->d_queue);
 }
 
 extern "C" {
@@ -213,6 +216,7 @@ int flints_plan(flints_plan_t *out, int64_t nside, int lmax, const double *cl, c
         ALLOC(p->d_cm32, (size_t)p->n * 2 * sizeof(float4));
     }
     ALLOC(p->d_counters, CNT_N * sizeof(unsigned long long));
+    ALLOC(p->d_queue, QUEUE_SLOTS * sizeof(unsigned long long));
 #undef ALLOC
     auto bail = [&](cudaError_t err, const char *what) {
         free_plan_memory(p);
@@ -312,8 +316,12 @@ static int run(flints_plan_t p, int64_t nside_tgt, int64_t first, int64_t count,
     a.xi0 = p->xi0;
     a.r2 = p->r2;
     a.counters = p->d_counters;
+    // this launch's tile queue: the next of the plan's counters, zeroed on the stream
+    a.queue = p->d_queue + (p->queue_next++ % QUEUE_SLOTS);
+    cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "tile queue reset");
     const int mode = (p->flags & FLINTS_SPIN2_AUGMENTED) ? SPIN2_AUG : p->spin;
-    cudaError_t e = launch_lens(mode, p->K, p->precision, a, p->R_rings, p->cfg, (cudaStream_t)stream);
+    e = launch_lens(mode, p->K, p->precision, a, p->R_rings, p->cfg, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "lens kernel launch");
     p->points += count;
     return FLINTS_OK;

@@ -380,7 +380,14 @@ struct LensArgs {
     int64_t nside_tgt;             // > 0: targets are the pixel centres of this grid (no deflection)
     int rotate;                    // spin 2: return P in the frame at n instead of n'
     TableDev tabm;                 // spin 2: xi-/xi+(0) on the same grid (augmented estimator)
+    // tile queue of a single-range launch: zero before the launch, warps take tiles by
+    // atomicAdd (NULL: a static grid stride over the tiles)
+    unsigned long long *queue;
 };
+
+// Tile-queue counters a plan keeps: each single-range launch takes the next one, so up
+// to this many launches of one plan may be in flight at once.
+constexpr int QUEUE_SLOTS = 64;
 
 // Internal kernel mode of the augmented (widely linear) spin-2 estimator.
 constexpr int SPIN2_AUG = 3;

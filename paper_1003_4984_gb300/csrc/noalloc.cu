@@ -40,7 +40,8 @@ constexpr size_t OFF_GM = OFF_FM + al(sizeof(double) * (NA_MAX_INTERVALS + 1));
 constexpr size_t OFF_C64 = OFF_GM + al(sizeof(double) * (NA_MAX_INTERVALS + 1));
 constexpr size_t OFF_C32 = OFF_C64 + al(sizeof(Coef64) * NA_MAX_INTERVALS);
 constexpr size_t OFF_CNT = OFF_C32 + al(sizeof(float4) * 2 * NA_MAX_INTERVALS);
-constexpr size_t SCRATCH_BYTES = OFF_CNT + al(sizeof(unsigned long long) * CNT_N);
+constexpr size_t OFF_QUEUE = OFF_CNT + al(sizeof(unsigned long long) * CNT_N);
+constexpr size_t SCRATCH_BYTES = OFF_QUEUE + al(sizeof(unsigned long long));
 
 // The scratch array: every GPU that loads this library holds it until exit.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SCRATCH_BYTES];
@@ -131,6 +132,7 @@ extern "C" int flints_lens_noalloc(int64_t nside, int lmax, const double *cl, co
     Coef64 *d_c64 = reinterpret_cast<Coef64 *>(base + OFF_C64);
     float4 *d_c32 = reinterpret_cast<float4 *>(base + OFF_C32);
     unsigned long long *d_cnt = reinterpret_cast<unsigned long long *>(base + OFF_CNT);
+    unsigned long long *d_queue = reinterpret_cast<unsigned long long *>(base + OFF_QUEUE);
     cudaStream_t st = (cudaStream_t)stream;
     const size_t ncl = (size_t)lmax + 1, nn = (size_t)n + 1;
 
@@ -145,6 +147,7 @@ extern "C" int flints_lens_noalloc(int64_t nside, int lmax, const double *cl, co
     NA_CK(cudaMemsetAsync(d_fm, 0, nn * sizeof(double), st), "clear xi- nodes");
     NA_CK(cudaMemsetAsync(d_gm, 0, nn * sizeof(double), st), "clear xi- slopes");
     NA_CK(cudaMemsetAsync(d_cnt, 0, CNT_N * sizeof(unsigned long long), st), "clear counters");
+    NA_CK(cudaMemsetAsync(d_queue, 0, sizeof(unsigned long long), st), "clear tile queue");
     NA_CK(launch_xi_table(spin, lmax, d_cl, d_clbb, t_max, n, d_f, d_g, d_fm, d_gm, st), "xi table kernel");
     double xi0 = 0.0;
     NA_CK(cudaMemcpyAsync(&xi0, d_f, sizeof(double), cudaMemcpyDeviceToHost, st), "read xi(0)");
@@ -173,6 +176,7 @@ extern "C" int flints_lens_noalloc(int64_t nside, int lmax, const double *cl, co
     a.xi0 = xi0;
     a.r2 = tg.r2;
     a.counters = d_cnt;
+    a.queue = d_queue;
     NA_CK(launch_lens(spin, K, precision, a, R_rings, LaunchCfg{0, 0, 0}, st), "lens kernel launch");
 #undef NA_CK
     return FLINTS_OK;
