@@ -32,12 +32,12 @@ import workloads as wl  # noqa: E402
 
 METRIC = "lensed pts/s at Nside 4096 spin-2 K=32, mixed vs FP64 @2e-4 rel err; p50/p99 ms"
 # DRAM bytes (read + write) per target of lens_kernel<32,2,mixed>, from the ncu capture of
-# `bench.py --profile-case mixed` (13.864 MB for 2^18 targets; profiles/lens_kernel_c3_full_sets.md),
+# `bench.py --profile-case mixed` (13.867 MB for 2^18 targets; profiles/lens_kernel_c3_full_sets.md),
 # scaled to a launch by its target count
-MIXED_DRAM_BYTES_PER_POINT = 13.863936e6 / (1 << 18)
-# warp instructions per target of the same kernel in the same capture (6.727 G for 2^18 targets):
+MIXED_DRAM_BYTES_PER_POINT = (13.866752e6 + 256) / (1 << 18)
+# warp instructions per target of the same kernel in the same capture (6.729 G for 2^18 targets):
 # with the measured point rate, the issue rate against 4 sub-partitions x 152 SMs x 2.07 GHz
-MIXED_WARP_INSTR_PER_POINT = 6.727009143e9 / (1 << 18)
+MIXED_WARP_INSTR_PER_POINT = 6.729288547e9 / (1 << 18)
 ISSUE_PEAK_PER_S = 4 * 152 * 2.07e9
 BATCH = 1 << 24
 W = wl.C3
