@@ -1530,7 +1530,8 @@ __device__ __forceinline__ void process_tile(const LensArgs &a, int R_rings, int
     }
 }
 
-// Single-launch kernel: warps stride over the tiles of one target range.
+// Single-launch kernel: warps take the tiles of one target range from the launch's
+// queue (a static grid stride when no queue is given).
 template <int K, int SPIN, int MIXED>
 __global__ void __launch_bounds__(256, 2) lens_kernel(LensArgs a, int R_rings, int tile_pts) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
