@@ -121,7 +121,18 @@ class LensServer:
         return req.count * (16 + (8 if spin == 0 else 16) + 8)
 
     # ------------------------------------------------------------ admission
+    def check(self, req: Request):
+        """Raise ValueError unless the request's map is registered and its range lies inside it."""
+        if req.map_key not in self.maps:
+            raise ValueError(f"request {req.rid}: no map registered for {req.map_key}")
+        npix = 12 * req.map_key[0] * req.map_key[0]
+        if req.count < 0 or req.first < 0 or req.first + req.count > npix:
+            raise ValueError(f"request {req.rid}: target range [{req.first}, {req.first + req.count}) "
+                             f"outside the map's {npix} pixels")
+
     def submit(self, req: Request):
+        """Queue a request (checked first)."""
+        self.check(req)
         self.pending.append(req)
 
     def cancel(self, rid: int) -> bool:
@@ -167,6 +178,9 @@ class LensServer:
             req.admitted_at = now
             self.in_use += nb
             self.active.append(req)
+            if req.count == 0:  # nothing to lens: done at admission
+                req.finished_at = now
+                self._release(req)
 
     # ------------------------------------------------------------ scheduling
     def _build_jobs(self):
@@ -241,6 +255,8 @@ class LensServer:
         def now():
             return (time.perf_counter() - t0) / time_scale
 
+        for r in requests:  # every request is checked before anything runs
+            self.check(r)
         todo = collections.deque(sorted(requests, key=lambda r: r.arrival))
         while todo or self.pending or self.active or any(self.inflight):
             t = now()

@@ -190,3 +190,29 @@ def test_cancel_pending_and_running_requests():
         ref, rvar, x0 = _alone(fl, server, r)
         assert parity_metric(to_host(r.out), ref, 1.0) <= 1e-12
     server.close()
+
+
+def test_empty_and_invalid_requests():
+    """A request with no targets finishes at admission instead of keeping the loop
+    alive; a request outside its map is refused before anything runs."""
+    fl = require_gpu()
+    import torch
+
+    from paper_1003_4984_gb300.serving import Request
+
+    server = _server_with_maps(2e8)
+    d = torch.from_numpy(wl.random_deflection(3000, 61) * 4).cuda()
+    empty = torch.zeros((0, 2), dtype=torch.float64, device="cuda")
+    reqs = [Request(0, (32, 0), 16, 10, 3000, d, arrival=0.0), Request(1, (64, 2), 32, 5, 0, empty, arrival=0.0)]
+    done = server.run(reqs)
+    torch.cuda.synchronize()
+    assert sorted(r.rid for r in done) == [0, 1] and server.in_use == 0 and not server.active
+    assert next(r for r in done if r.rid == 1).latency is not None
+    ref, _, x0 = _alone(fl, server, next(r for r in done if r.rid == 0))
+    assert parity_metric(to_host(done[[r.rid for r in done].index(0)].out), ref, 1.0) <= 1e-12
+    with pytest.raises(ValueError, match="outside the map"):
+        server.run([Request(2, (32, 0), 16, 12 * 32 * 32 - 5, 10, d[:10])])
+    with pytest.raises(ValueError, match="no map registered"):
+        server.run([Request(3, (128, 0), 16, 0, 10, d[:10])])
+    assert not server.pending and not server.active
+    server.close()
