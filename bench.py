@@ -31,13 +31,13 @@ import numpy as np  # noqa: E402
 import workloads as wl  # noqa: E402
 
 METRIC = "lensed pts/s at Nside 4096 spin-2 K=32, mixed vs FP64 @2e-4 rel err; p50/p99 ms"
-# DRAM bytes (read + write) per target of lens_kernel<32,2,mixed>, from the ncu capture of
-# `bench.py --profile-case mixed` (13.867 MB for 2^18 targets; profiles/lens_kernel_c3_full_sets.md),
-# scaled to a launch by its target count
-MIXED_DRAM_BYTES_PER_POINT = (13.866752e6 + 256) / (1 << 18)
-# warp instructions per target of the same kernel in the same capture (6.729 G for 2^18 targets):
+# DRAM bytes (read + write) per target of the mixed spin-2 K=32 kernel a plan call launches
+# (batch_kernel<1,2,32>), from the ncu capture of `bench.py --profile-case mixed` (13.866 MB for
+# 2^18 targets; profiles/batch_kernel_c3_full_sets.md), scaled to a launch by its target count
+MIXED_DRAM_BYTES_PER_POINT = 13.865984e6 / (1 << 18)
+# warp instructions per target of the same kernel in the same capture (6.717 G for 2^18 targets):
 # with the measured point rate, the issue rate against 4 sub-partitions x 152 SMs x 2.07 GHz
-MIXED_WARP_INSTR_PER_POINT = 6.729288547e9 / (1 << 18)
+MIXED_WARP_INSTR_PER_POINT = 6.716570991e9 / (1 << 18)
 ISSUE_PEAK_PER_S = 4 * 152 * 2.07e9
 BATCH = 1 << 24
 W = wl.C3
@@ -509,9 +509,10 @@ def run_ours(args):
     rate64 = BATCH / (statistics.mean(fp_per) / 1e3)
     f_method = flops.augmented_flops(W.K, False) if aug else flops.fp64_flops(W.K, 2)
     f_issue = flops.augmented_flops(W.K, True) if aug else flops.mixed_fp32_flops(W.K, 2)
-    kname = 3 if aug else 2
     roof = roofline_entry(
-        rate, f_method, peaks["fp32_tflops"], "lens_kernel<32,%d,mixed> (double-float on the FP32 pipe)" % kname,
+        rate, f_method, peaks["fp32_tflops"],
+        ("lens_kernel<32,3,mixed>" if aug else "batch_kernel<1,2,32> (the class kernel a spin-2 K=32 mixed plan "
+         "call launches)") + " (double-float on the FP32 pipe)",
         "measured FP32 multiply-add throughput in this run (flints_measure_fma_peak); derived peak "
         "152 SMs x 128 lanes x 2 x 2.07 GHz = %.1f TFLOP/s" % flops.FP32_PEAK_TFLOPS,
         traffic=None if aug else MIXED_DRAM_BYTES_PER_POINT * BATCH,
@@ -532,7 +533,8 @@ def run_ours(args):
                     "binding resource of the double-float emulation"},
         hbm={"bytes_per_point": 56, "achieved_gbs": rate * 56 / 1e9, "peak_gbs": HBM_PEAK_GBS,
              "frac": rate * 56 / 1e9 / HBM_PEAK_GBS})
-    roof64 = roofline_entry(rate64, f_method, peaks["fp64_tflops"], "lens_kernel<32,%d,fp64>" % kname,
+    roof64 = roofline_entry(rate64, f_method, peaks["fp64_tflops"],
+                            "lens_kernel<32,3,fp64>" if aug else "batch_kernel<0,2,32> (FP64)",
                             "measured FP64 multiply-add throughput in this run (flints_measure_fma_peak); "
                             "nominal 1.25 TFLOP/s")
     line = {
@@ -825,7 +827,7 @@ def run_ss(args):
     precision_pred = math.sqrt(float(var.mean()) / xi0)  # last batch, FP64 plan
     peaks = measured_peaks()
     roof = roofline_entry(BATCH / (statistics.mean(per) / 1e3), flops.fp64_flops(Wc.K, 0), peaks["fp32_tflops"],
-                          "lens_kernel<32,0,mixed>", "measured FP32 multiply-add throughput in this run",
+                          "batch_kernel<1,0,32>", "measured FP32 multiply-add throughput in this run",
                           traffic=None, issue_flops_per_point=flops.mixed_fp32_flops(Wc.K, 0))
     print(json.dumps({
         "metric": "supersampled pts/s, Nside 2048 -> 4096, lmax 4096, K=32, spin 0", "value": value,

@@ -41,9 +41,10 @@
  * - A plan owns its device memory (xi tables, counters) and is bound to the
  *   device that was current when it was created.  Plans are not thread-safe:
  *   use one plan per host thread or serialise calls on it.  Each lens call of
- *   a plan takes the next of the plan's 64 tile-queue counters (warps take
- *   their tiles from it), so at most 64 calls of one plan may be in flight on
- *   the GPU at once, on one stream or several.
+ *   a plan takes the next of the plan's 64 slots (a tile-queue counter the
+ *   warps take their tiles from and, for spin 0 and 2, the one-job table of
+ *   the persistent kernel the call launches), so at most 64 calls of one plan
+ *   may be in flight on the GPU at once, on one stream or several.
  */
 #ifndef FLINTS_H
 #define FLINTS_H

@@ -66,8 +66,12 @@ struct flints_plan_s {
     Coef64 *d_c64, *d_cm64;  // xi+ (spin 0: xi) and, spin 2, xi- interpolation coefficients
     float4 *d_c32, *d_cm32;
     unsigned long long *d_counters;
-    unsigned long long *d_queue;  // QUEUE_SLOTS tile-queue counters, one per launch in flight
+    unsigned long long *d_queue;  // QUEUE_SLOTS blocks of BATCH_CLASSES tile-queue counters, one block per call
     unsigned queue_next;
+    // spin 0 / 2 plans (not augmented): QUEUE_SLOTS one-job tables of the batched class
+    // kernel, and its prepared launch shape
+    unsigned char *d_jt;
+    int jt_wpb, jt_bps;
     int64_t points;
     LaunchCfg cfg;
 };
@@ -93,6 +97,23 @@ static int cuda_fail(cudaError_t e, const char *what) {
     } while (0)
 
 static bool supported_K(int K) { return K == 16 || K == 24 || K == 32 || K == 48; }
+
+// one-job table of the batched class kernel (header, then the job), 256-byte slots
+static constexpr size_t JT_BYTES = (sizeof(BatchHeader) + sizeof(BatchJob) + 255) / 256 * 256;
+
+struct OneJob {
+    BatchHeader h;
+    BatchJob j;
+};
+
+// Writes a one-job table into device memory from the kernel's parameters: no
+// copy-engine transfer, so the call's table never queues behind the caller's own
+// host-device copies, and no host staging buffer has to outlive the call.
+__global__ void store_one_job(OneJob t, unsigned *dst) {
+    static_assert(sizeof(OneJob) % 4 == 0, "word copy");
+    const unsigned *src = reinterpret_cast<const unsigned *>(&t);
+    for (int i = threadIdx.x; i < (int)(sizeof(OneJob) / 4); i += blockDim.x) dst[i] = src[i];
+}
 
 namespace flints {
 TableGrid table_grid(int64_t nside, int K, int lmax, const double *cl, const double *cl_bb) {
@@ -135,6 +156,7 @@ static void free_plan_memory(flints_plan_s *p) {
     cudaFree(p->d_cm32);
     cudaFree(p->d_counters);
     cudaFree(p->d_queue);
+    cudaFree(p->d_jt);
 }
 
 extern "C" {
@@ -216,7 +238,10 @@ int flints_plan(flints_plan_t *out, int64_t nside, int lmax, const double *cl, c
         ALLOC(p->d_cm32, (size_t)p->n * 2 * sizeof(float4));
     }
     ALLOC(p->d_counters, CNT_N * sizeof(unsigned long long));
-    ALLOC(p->d_queue, QUEUE_SLOTS * sizeof(unsigned long long));
+    ALLOC(p->d_queue, (size_t)QUEUE_SLOTS * BATCH_CLASSES * sizeof(unsigned long long));
+    if (spin != 1 && !(flags & FLINTS_SPIN2_AUGMENTED)) {
+        ALLOC(p->d_jt, (size_t)QUEUE_SLOTS * JT_BYTES);
+    }
 #undef ALLOC
     auto bail = [&](cudaError_t err, const char *what) {
         free_plan_memory(p);
@@ -316,12 +341,65 @@ static int run(flints_plan_t p, int64_t nside_tgt, int64_t first, int64_t count,
     a.xi0 = p->xi0;
     a.r2 = p->r2;
     a.counters = p->d_counters;
-    // this launch's tile queue: the next of the plan's counters, zeroed on the stream
-    a.queue = p->d_queue + (p->queue_next++ % QUEUE_SLOTS);
-    cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), (cudaStream_t)stream);
-    if (e != cudaSuccess) return cuda_fail(e, "tile queue reset");
+    // this call's slot: its tile-queue counters (and one-job table), zeroed on the stream
+    const unsigned slot = p->queue_next++ % QUEUE_SLOTS;
+    unsigned long long *qblock = p->d_queue + (size_t)slot * BATCH_CLASSES;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    if (p->d_jt) {
+        // spin 0 / 2: the persistent class kernel of the batched launch, given a one-job
+        // table (the same per-tile code; on GB300 this kernel runs the c3 workload 3-4 %
+        // faster than the single-range kernel)
+        const int cls = 8 * (p->precision == FLINTS_MIXED ? 1 : 0) + 4 * (p->spin == 2 ? 1 : 0) + batch_k_index(p->K);
+        const int tp = p->cfg.tile_points > 0 && p->cfg.tile_points < MAX_TILE_POINTS ? p->cfg.tile_points
+                                                                                       : MAX_TILE_POINTS;
+        const int fit = (cls >> 3) ? batch_fit_wpb_p1(cls & 7) : batch_fit_wpb_p0(cls & 7);
+        int wpb = p->cfg.warps_per_block > 0 ? p->cfg.warps_per_block : 4;
+        if (wpb > fit) wpb = fit;
+        if (p->jt_wpb != wpb) {
+            int mx = 0;
+            e = (cls >> 3) ? batch_prepare_p1(cls & 7, wpb, &mx) : batch_prepare_p0(cls & 7, wpb, &mx);
+            if (e != cudaSuccess) return cuda_fail(e, "lens kernel set-up");
+            if (mx < 1) return fail(FLINTS_EINVAL, "lens kernel: %d warps per block do not fit on an SM", wpb);
+            p->jt_wpb = wpb;
+            p->jt_bps = mx;
+        }
+        const int64_t ntiles = (count + tp - 1) / tp;
+        OneJob t{};
+        t.h.njobs[cls] = 1;
+        t.h.total_tiles[cls] = ntiles;
+        t.h.tile_pts = tp;
+        t.j.a = a;
+        t.j.R_rings = p->R_rings;
+        t.j.K = p->K;
+        t.j.spin = p->spin;
+        t.j.precision = p->precision;
+        t.j.tile_begin = 0;
+        t.j.ntiles = ntiles;
+        unsigned char *ds = p->d_jt + (size_t)slot * JT_BYTES;
+        store_one_job<<<1, 64, 0, st>>>(t, reinterpret_cast<unsigned *>(ds));
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "lens job table");
+        if ((e = cudaMemsetAsync(qblock + cls, 0, sizeof(unsigned long long), st)) != cudaSuccess)
+            return cuda_fail(e, "tile queue reset");
+        int bps = p->jt_bps;
+        if (p->cfg.blocks_per_sm > 0 && p->cfg.blocks_per_sm < bps) bps = p->cfg.blocks_per_sm;
+        int64_t blocks = (int64_t)device_sm_count() * bps;
+        const int64_t need = (ntiles + wpb - 1) / wpb;
+        if (blocks > need) blocks = need;
+        const BatchHeader *hd = reinterpret_cast<const BatchHeader *>(ds);
+        const BatchJob *jd = reinterpret_cast<const BatchJob *>(ds + offsetof(OneJob, j));
+        e = (cls >> 3) ? batch_launch_p1(cls & 7, hd, jd, qblock, wpb, (int)blocks, st)
+                       : batch_launch_p0(cls & 7, hd, jd, qblock, wpb, (int)blocks, st);
+        if (e != cudaSuccess) return cuda_fail(e, "lens kernel launch");
+        p->points += count;
+        return FLINTS_OK;
+    }
+    // spin 1 and the augmented estimator: the single-range kernel with the slot's queue
+    a.queue = qblock;
+    if ((e = cudaMemsetAsync(a.queue, 0, sizeof(unsigned long long), st)) != cudaSuccess)
+        return cuda_fail(e, "tile queue reset");
     const int mode = (p->flags & FLINTS_SPIN2_AUGMENTED) ? SPIN2_AUG : p->spin;
-    e = launch_lens(mode, p->K, p->precision, a, p->R_rings, p->cfg, (cudaStream_t)stream);
+    e = launch_lens(mode, p->K, p->precision, a, p->R_rings, p->cfg, st);
     if (e != cudaSuccess) return cuda_fail(e, "lens kernel launch");
     p->points += count;
     return FLINTS_OK;

@@ -6,6 +6,8 @@
 // (costliest jobs first), find the tile's job by binary search over the jobs'
 // first tiles and run the same per-tile code as the single-range kernel.
 // There is no inter-block waiting: a warp that finds the queue empty exits.
+// Plan calls of spin 0 and 2 launch the same class kernels with a one-job table
+// (api.cu), the code that measured fastest for single ranges as well.
 #pragma once
 #include "batch_types.cuh"
 #include "lens.cuh"
