@@ -429,3 +429,31 @@ def test_nonfinite_deflections_on_the_tabulated_route(fl, torch):
         assert np.all(s[good] & fl.ST_INPUT == 0)
         np.testing.assert_array_equal(o[good], r[good])
         plan.close()
+
+
+def test_many_calls_of_one_plan_in_flight(fl, torch):
+    """A plan's calls take its slots in turn (tile queue and job table): 100 calls
+    issued back to back on two streams, without synchronising, wrap the 64 slots and
+    give the same results as the calls made one at a time."""
+    nside, lmax, K = 16, 32, 16
+    npix = hp.npix(nside)
+    cl = wl.cl_tt(lmax, 24.0)
+    m = torch.from_numpy(sht.synth_map(nside, lmax, wl.draw_alm(cl, 51))).cuda()
+    defl = torch.from_numpy(wl.random_deflection(npix, 52) * 4).cuda()
+    plan = fl.Plan(nside, cl, spin=0, K=K, precision="mixed")
+    n, size = 100, 96
+    firsts = [(37 * i) % (npix - size) for i in range(n)]
+    ref = []
+    for f in firsts:
+        o, _, _ = plan.lens(m, defl[f:f + size], first=f, count=size)
+        torch.cuda.synchronize()
+        ref.append(to_host(o))
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    outs = [torch.full((size,), float("nan"), dtype=torch.float64, device="cuda") for _ in range(n)]
+    torch.cuda.synchronize()
+    for i, f in enumerate(firsts):
+        plan.lens(m, defl[f:f + size], out=outs[i], first=f, count=size, stream=streams[i & 1])
+    torch.cuda.synchronize()
+    for i in range(n):
+        np.testing.assert_array_equal(to_host(outs[i]), ref[i])
+    plan.close()
