@@ -541,7 +541,7 @@ def run_ours(args):
         "metric": METRIC + (" (augmented xi+/xi- estimator)" if aug else ""), "value": value, "unit": "pts/s",
         "n_gpus": n_gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64 in/out; double-float (2 x f32) factor, f64 geometry",
+        "vs_baseline": None, "dtype": "f64 in/out; double-float (2 x f32: an FP64 emulation on the FP32 pipe) assembly, factor and solves; f64 geometry",
         "data": "synthetic: white-noise Q/U map (the work does not depend on the values) and per-pixel Gaussian "
                 "deflections of 2.5 arcmin rms",
         "config": config(n_gpus),
