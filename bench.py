@@ -388,7 +388,7 @@ def run_ours(args):
     batched = None
     if not aug:
         batch = fl.Batch(1)
-        bcfg = fl.LaunchCfg(4, 0, 16)
+        bcfg = fl.LaunchCfg(8, 0, 16)
 
         def stage(i):
             b_first, b_count, b_defl = window(i)

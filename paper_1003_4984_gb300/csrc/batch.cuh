@@ -46,11 +46,21 @@ __global__ void __launch_bounds__(256, 2) batch_kernel(const BatchHeader *__rest
     }
 }
 
+// warps per block that fit in the opt-in shared memory for a class
+template <int MIXED, int SPIN, int K>
+int batch_fit_wpb();
+
+// The kernel's dynamic shared-memory limit is a property of the kernel function,
+// shared by every batch object and plan that launches it: it is always set to the
+// largest block that fits, so a launch with fewer warps per block never finds it
+// lowered by another caller; the occupancy is queried for the requested shape.
 template <int MIXED, int SPIN, int K>
 cudaError_t batch_prepare(int wpb, int *max_blocks_per_sm) {
     const size_t smem = (size_t)wpb * warp_smem_bytes<K, SPIN, MIXED>();
+    const size_t smem_max = (size_t)batch_fit_wpb<MIXED, SPIN, K>() * warp_smem_bytes<K, SPIN, MIXED>();
     auto kern = batch_kernel<MIXED, SPIN, K>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(smem > smem_max ? smem : smem_max));
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(max_blocks_per_sm, kern, wpb * 32, smem);
 }
@@ -63,7 +73,6 @@ cudaError_t batch_launch(const BatchHeader *hdr, const BatchJob *jobs, unsigned 
     return cudaGetLastError();
 }
 
-// warps per block that fit in the opt-in shared memory for a class
 template <int MIXED, int SPIN, int K>
 int batch_fit_wpb() {
     const int fit = (int)(device_smem_optin() / warp_smem_bytes<K, SPIN, MIXED>());
