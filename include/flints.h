@@ -186,7 +186,8 @@ int flints_stencil(flints_plan_t plan, int64_t first, int64_t count,
                    void *stream);
 
 /* Launch shape of a plan's lens launches (the autotuner's knobs).
- *   warps_per_block 1..8 (0: 4; lowered to what fits in shared memory),
+ *   warps_per_block 1..8 (0: 8 for spin-0 and spin-2 plans, 4 for spin-1 and
+ *   augmented ones; lowered to what fits in shared memory),
  *   blocks_per_sm cap (0: as many as fit),
  *   tile_points targets per warp tile 1..16 (0: 16).  cfg NULL restores the
  *   defaults.  Results do not depend on the launch shape. */
