@@ -560,7 +560,8 @@ def run_ours(args):
         "peaks_measured": peaks,
         "cpu_baseline": cpu,
         "clocks": clocks,
-        "gpu_launches": args.steps,
+        # per timed step one plan call: store_one_job (its one-job table) + batch_kernel<1,2,32>
+        "gpu_launches": 2 * args.steps,
     }
     print(json.dumps(line))
 
@@ -843,7 +844,7 @@ def run_ss(args):
         "paper_table1": "Nside 2048 -> 4096, l 4096: 3e-3 (9 neighbours), 3e-4 (36 neighbours); serial "
                         "Xeon E5410 3.3 / 19 min per map",
         "roofline": roof, "peaks_measured": peaks,
-        "mixed_stats": st, "gpu_launches": args.steps}))
+        "mixed_stats": st, "gpu_launches": 2 * args.steps}))
 
 
 # -------------------------------------------------------------- spin-1 arm
