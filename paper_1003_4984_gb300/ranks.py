@@ -62,17 +62,19 @@ def lens_shard(lens_range, bounds: tuple[int, int], batch: int):
     """Lens a rank's whole range in calls of at most ``batch`` consecutive targets.
 
     ``lens_range(first, count)`` lenses targets [first, first+count) and returns
-    (value, variance) tensors; the results are concatenated in RING order."""
+    (value, variance) tensors; the results are concatenated in RING order.  An
+    empty range (a sky with fewer targets than ranks) makes one call with
+    count 0, so the rank still holds typed empty tensors for the gather."""
     import torch
 
     start, stop = bounds
+    if stop <= start:
+        return lens_range(start, 0)
     vals, vars_ = [], []
     for first in range(start, stop, batch):
         v, s2 = lens_range(first, min(batch, stop - first))
         vals.append(v)
         vars_.append(s2)
-    if not vals:
-        return None, None
     return torch.cat(vals), torch.cat(vars_)
 
 

@@ -43,14 +43,14 @@ def _stub_lens(src, defl):
     return lens_range
 
 
-def _worker(rank, world, port, q):
+def _worker(rank, world, port, q, npix=NPIX):
     os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port), "WORLD_SIZE": str(world),
                        "RANK": str(rank), "LOCAL_RANK": str(rank)})
     try:
         w, r, local = ranks.rank_env()
         dist = ranks.init("gloo")
         src, defl = _sky_inputs()
-        bounds = ranks.shard_bounds(NPIX, w)
+        bounds = ranks.shard_bounds(npix, w)
         ranks.barrier(dist)
         val, var = ranks.lens_shard(_stub_lens(src, defl), bounds[r], batch=100)
         full_v = ranks.gather_shards(val, bounds, dist, r)
@@ -101,6 +101,33 @@ def test_gloo_ranks_shard_one_sky(world):
     np.testing.assert_array_equal(full_v, one_v.numpy())
     np.testing.assert_array_equal(full_s, one_s.numpy())
     assert res[0][7] == pytest.approx(world * 1000 / (10.0 + 5.0 * (world - 1)))  # whole-job rate
+
+
+def test_gloo_ranks_with_empty_ranges():
+    """A sky of fewer targets than ranks: the ranks past its end hold empty ranges
+    and still take part in the gather; rank 0 gets exactly the sky."""
+    import torch.multiprocessing as mp
+
+    world, npix = 3, 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, q, npix)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=180) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert all(r[1] != "error" for r in res), res
+    res.sort(key=lambda r: r[0])
+    assert [r[4] for r in res] == [(0, 1), (1, 2), (2, 2)]
+    assert res[2][5] == [(2, 0)] * 6  # the empty range's benchmark windows are empty
+    src, defl = _sky_inputs()
+    one_v, one_s = ranks.lens_shard(_stub_lens(src, defl), (0, npix), batch=npix)
+    full_v, full_s = res[0][6]
+    np.testing.assert_array_equal(full_v, one_v.numpy())
+    np.testing.assert_array_equal(full_s, one_s.numpy())
 
 
 def test_shard_bounds_cover_the_sky_once():
