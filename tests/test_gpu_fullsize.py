@@ -316,6 +316,12 @@ def test_exact_benchmark_on_random_pixels_over_the_whole_sky(fl, W):
               f"rel L2 {rel_l2:.3e} (south {rel_s:.3e}), <|err|^2/sigma^2> {ratio:.3f}")
         if W.name == "c3":
             assert rel_l2 <= 2e-4 and rel_s <= 2e-4, precision
-            assert ratio < 1.5, precision  # the nugget bounds the error from above at Nside 4096
+            # the nugget dominates the predicted variance at Nside 4096 and bounds the error
+            # from above; the oracle on this sample gives <|err|^2/sigma^2> = 0.158
+            assert 0.1 < ratio < 0.25, precision
         else:
+            # the standardised error (v - truth) / sigma ~ N(0, 1) (Sec. 3.2, Fig. cmb_exp_error);
+            # the oracle on this sample gives mean -0.007, std 0.972
+            r = err / np.sqrt(s2)
+            assert abs(np.mean(r)) < 0.05 and 0.9 < np.std(r) < 1.1, (precision, np.mean(r), np.std(r))
             assert 0.8 < ratio < 1.25, precision
