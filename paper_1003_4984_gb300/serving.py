@@ -195,8 +195,10 @@ class LensServer:
                 if left <= 0:
                     continue
                 n = min(left, self.chunk_points, budget)
-                if n < left and n > 1:
+                if n < left:
                     n &= ~1  # keep the next chunk's outputs on 16-byte boundaries
+                    if n == 0:
+                        continue  # one point of room left: the next batch takes an even chunk
                 a = req.next_point
                 req.scheduled_points = a + n
                 jobs.append((self.plan_for(req), req.first + a, n, self.maps[req.map_key], req.defl[a:a + n],
