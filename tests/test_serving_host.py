@@ -4,8 +4,8 @@ touches (streams, events, the batched launch, plans, device buffers).  The
 stand-in launch "lenses" a target by a fixed function of its map value and
 deflection and counts how often each output is written, so the tests see
 which targets each launch received.  An event reports completion on its
-second poll, so every launch stays in flight for at least one scheduling
-round.
+second or fourth poll, so every launch stays in flight for at least one
+scheduling round and the two batch slots do not finish together.
 
 Covered: every target of every request lensed exactly once with the right
 map, deflection and output slices, in launches shared by several requests;
@@ -21,7 +21,7 @@ import pytest
 from paper_1003_4984_gb300 import serving
 from paper_1003_4984_gb300.serving import LensServer, Request, latency_stats
 
-pytestmark = pytest.mark.timeout(120)
+pytestmark = pytest.mark.timeout(30)  # a scheduling loop that never ends fails here
 
 PLAN_BYTES = 4096
 
@@ -54,7 +54,13 @@ class FakeStream:
 
 
 class FakeEvent:
+    """Completes on its second or, for every other event, its fourth poll, so that the
+    two batch slots fall out of step and one relaunches while the other is busy."""
+    made = 0
+
     def __init__(self):
+        FakeEvent.made += 1
+        self.need = 2 if FakeEvent.made % 2 else 4
         self.polls = 0
         self.stream = None
 
@@ -63,7 +69,7 @@ class FakeEvent:
 
     def query(self):
         self.polls += 1
-        return self.polls >= 2
+        return self.polls >= self.need
 
 
 class FakeCuda:
@@ -143,6 +149,7 @@ def server_factory(monkeypatch):
     monkeypatch.setattr(serving, "Plan", FakePlan)
     FakeBatch.launches = []
     FakePlan.made = []
+    FakeEvent.made = 0
 
     def make(budget=1e12, batch_points=5000, chunk_points=1500, max_jobs=8):
         srv = LensServer(hbm_budget=budget, batch_points=batch_points, chunk_points=chunk_points,
@@ -253,16 +260,20 @@ def test_budget_admission_waits_and_oversized_request_runs_alone(server_factory)
 
 def test_cancel_pending_and_running_requests(server_factory):
     srv = server_factory(batch_points=1000, chunk_points=500)
-    reqs = [Request(rid, (32, 0), 32, 300 * rid, 4000, _defl(4000, 200 + rid), arrival=0.0) for rid in range(4)]
+    reqs = [Request(rid, (32, 0), 32, 3000 * rid, 3000, _defl(3000, 200 + rid), arrival=0.0) for rid in range(4)]
     state = {"running": None, "pending": False, "held": None}
 
     def tick(s, now):
         if state["running"] is None:
+            # cancelled as soon as it has chunks in flight: one batch slot then retires and
+            # relaunches while the other still holds a chunk of it
             r1 = next((r for r in s.active if r.rid == 1 and r.scheduled_points > r.done_points), None)
-            if r1 is not None and r1.done_points > 0:
+            if r1 is not None:
                 state["running"] = s.cancel(1)
                 # its chunks in flight still hold its memory
                 state["held"] = r1 in s.active and s.in_use >= r1.nbytes
+                state["scheduled"] = r1.scheduled_points
+                state["launches"] = len(FakeBatch.launches)
         if not state["pending"] and any(r.rid == 9 for r in s.pending):
             state["pending"] = s.cancel(9)
 
@@ -274,6 +285,10 @@ def test_cancel_pending_and_running_requests(server_factory):
     assert sorted(r.rid for r in srv.cancelled) == [1, 9]
     c1 = next(r for r in srv.cancelled if r.rid == 1)
     assert 0 < c1.done_points < c1.count and c1.done_points == c1.scheduled_points
+    # no chunk of it was scheduled after the cancellation
+    assert c1.scheduled_points == state["scheduled"]
+    assert not any(k == (32, 0, 32, "mixed") and c1.first <= f < c1.first + c1.count
+                   for rec in FakeBatch.launches[state["launches"]:] for k, f, _ in rec)
     assert srv.in_use == 0 and not srv.active
     assert late.out is None  # never admitted, no buffers
     assert srv.cancel(1) is False and srv.cancel(12345) is False
