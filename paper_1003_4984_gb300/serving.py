@@ -66,6 +66,8 @@ class LensServer:
                  max_jobs: int = 64, cfg: LaunchCfg | None = None, device: int = 0):
         import torch
 
+        if int(batch_points) < 2 or int(chunk_points) < 2 or int(max_jobs) < 1:
+            raise ValueError("batch_points and chunk_points must be at least 2, max_jobs at least 1")
         self.torch = torch
         self.dev = torch.device("cuda", device)
         self.budget = float(hbm_budget)
@@ -198,7 +200,9 @@ class LensServer:
                 if n < left:
                     n &= ~1  # keep the next chunk's outputs on 16-byte boundaries
                     if n == 0:
-                        continue  # one point of room left: the next batch takes an even chunk
+                        # one point of room left in a batch that already holds work (the
+                        # sizes are at least 2): the next batch takes an even chunk
+                        continue
                 a = req.next_point
                 req.scheduled_points = a + n
                 jobs.append((self.plan_for(req), req.first + a, n, self.maps[req.map_key], req.defl[a:a + n],

@@ -215,6 +215,22 @@ def test_chunks_start_on_even_offsets(server_factory):
     np.testing.assert_array_equal(np.asarray(r.var), np.ones(5000))
 
 
+def test_smallest_chunks_still_progress(server_factory):
+    # two-point chunks and batches: every batch holds one even chunk, the last point alone
+    srv = server_factory(batch_points=2, chunk_points=2, max_jobs=2)
+    reqs = [Request(0, (16, 0), 16, 3, 7, _defl(7, 1), arrival=0.0),
+            Request(1, (16, 2), 16, 0, 5, _defl(5, 2), arrival=0.0)]
+    done = srv.run(reqs)
+    assert sorted(r.rid for r in done) == [0, 1]
+    sizes = [n for rec in FakeBatch.launches for _, _, n in rec]
+    assert sum(sizes) == 12 and all(n in (1, 2) for n in sizes) and sizes.count(1) == 2
+    for r in done:
+        np.testing.assert_array_equal(np.asarray(r.var), np.ones(r.count))
+    for bad in (dict(batch_points=1), dict(chunk_points=1), dict(max_jobs=0)):
+        with pytest.raises(ValueError, match="at least"):
+            server_factory(**bad)
+
+
 def test_resident_maps_and_plans_count_against_the_budget(server_factory):
     srv = server_factory()
     maps = sum(m.numel() * m.element_size() for m in srv.maps.values())
