@@ -8,9 +8,10 @@ mixed-vs-FP64 ratio.  Inputs are larger than L2 (3.2 GB map, 268 MB of
 deflections per step), so no L2 flush is needed.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-Under torchrun (N > 1) every rank lenses its own batches (weak scaling, no
-collective on the data path); timings are bracketed by barriers and the
-maximum over ranks is reported by rank 0.
+Under torchrun (N > 1) the sky is split into contiguous RING ranges, one per
+rank, and every rank lenses batches of its own range of the replicated map
+(weak scaling, no collective on the data path); timings are bracketed by
+barriers and the maximum over ranks is reported by rank 0.
 """
 from __future__ import annotations
 
