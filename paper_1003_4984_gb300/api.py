@@ -169,6 +169,20 @@ def _dev_f64(t, shape, name):
     return t
 
 
+def _dev_buf(t, n: int, name: str, dtype: str = "float64"):
+    """A contiguous CUDA tensor of ``dtype`` with at least ``n`` elements: the check for
+    buffers the library reads or writes through a raw pointer (a host tensor's address
+    handed to a kernel would be an invalid device access)."""
+    import torch
+
+    if (not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != getattr(torch, dtype)
+            or not t.is_contiguous()):
+        raise FlintsError(f"{name} must be a contiguous {dtype} CUDA tensor")
+    if t.numel() < n:
+        raise FlintsError(f"{name} holds {t.numel()} elements, the call needs {n}")
+    return t
+
+
 @dataclass
 class Info:
     nside: int
@@ -279,8 +293,9 @@ class Plan:
         _dev_f64(out, oshape, "out")
         if var is not None:
             _dev_f64(var, (count,), "var")
-        if status is not None and (status.dtype != torch.uint8 or not status.is_cuda or status.numel() != count):
-            raise FlintsError("status must be a uint8 CUDA tensor of length count")
+        if status is not None and (status.dtype != torch.uint8 or not status.is_cuda or status.numel() != count
+                                   or not status.is_contiguous()):
+            raise FlintsError("status must be a contiguous uint8 CUDA tensor of length count")
         _check(_lib.flints_lens_range(self._h, int(first), int(count), _ptr(map_), _ptr(defl), _ptr(out), _ptr(var),
                                       _ptr(status), _stream(stream)))
         return out, var, status
@@ -302,8 +317,9 @@ class Plan:
         _dev_f64(out, oshape, "out")
         if var is not None:
             _dev_f64(var, (count,), "var")
-        if status is not None and (status.dtype != torch.uint8 or not status.is_cuda or status.numel() != count):
-            raise FlintsError("status must be a uint8 CUDA tensor of length count")
+        if status is not None and (status.dtype != torch.uint8 or not status.is_cuda or status.numel() != count
+                                   or not status.is_contiguous()):
+            raise FlintsError("status must be a contiguous uint8 CUDA tensor of length count")
         _check(_lib.flints_supersample(self._h, int(nside_out), int(first), int(count), _ptr(map_), _ptr(out),
                                        _ptr(var), _ptr(status), _stream(stream)))
         return out, var, status
@@ -341,6 +357,15 @@ class Plan:
 def _job_array(jobs):
     arr = (_Job * max(1, len(jobs)))()
     for k, (plan, first, count, m, d, o, v, s) in enumerate(jobs):
+        if int(count) > 0:  # the library reads and writes these through raw device pointers
+            two = 1 if plan.spin == 0 else 2
+            _dev_buf(m, plan.npix * two, f"job {k}: map")
+            _dev_buf(d, 2 * int(count), f"job {k}: defl")
+            _dev_buf(o, int(count) * two, f"job {k}: out")
+            if v is not None:
+                _dev_buf(v, int(count), f"job {k}: var")
+            if s is not None:
+                _dev_buf(s, int(count), f"job {k}: status", "uint8")
         arr[k] = _Job(plan.handle, first, count, _ptr(m), _ptr(d), _ptr(o), _ptr(v), _ptr(s))
     return arr
 
@@ -432,6 +457,15 @@ def lens_noalloc(nside: int, cl, map_, defl, out, var=None, status=None, cl_bb=N
     npix = 12 * int(nside) * int(nside)
     if count is None:
         count = npix - first
+    if int(count) > 0:
+        two = 1 if int(spin) == 0 else 2
+        _dev_buf(map_, npix * two, "map")
+        _dev_buf(defl, 2 * int(count), "defl")
+        _dev_buf(out, int(count) * two, "out")
+        if var is not None:
+            _dev_buf(var, int(count), "var")
+        if status is not None:
+            _dev_buf(status, int(count), "status", "uint8")
     cl = np.ascontiguousarray(cl, dtype=np.float64)
     bb = None if cl_bb is None else np.ascontiguousarray(cl_bb, dtype=np.float64)
     dp = ctypes.POINTER(ctypes.c_double)
@@ -545,8 +579,9 @@ class PaperPlan:
             var = torch.empty(count, dtype=torch.float64, device=map_.device)
         _dev_f64(out, (count,) + two, "out")
         _dev_f64(var, (count,), "var")
-        if status is not None and (status.dtype != torch.uint8 or tuple(status.shape) != (count,)):
-            raise FlintsError("status must be a uint8 CUDA tensor of shape (count,)")
+        if status is not None and (status.dtype != torch.uint8 or tuple(status.shape) != (count,)
+                                   or not status.is_cuda or not status.is_contiguous()):
+            raise FlintsError("status must be a contiguous uint8 CUDA tensor of shape (count,)")
         return out, var
 
     def lens(self, map_, defl, first: int = 0, count: int | None = None, out=None, var=None, status=None,

@@ -91,3 +91,30 @@ def test_noalloc_rejects_misaligned_buffers_without_gpu(lib_path):
     # device address lookup, so it is not made here
     rc = lib.flints_measure_fma_peak(0, 0, None, None)
     assert rc == 1 and b"tflops is NULL" in lib.flints_measure_last_error()
+
+
+def test_binding_refuses_host_or_mistyped_buffers_on_the_host(lib_path):
+    """The binding hands raw pointers to kernels, so a host tensor, a wrong dtype or a
+    strided view is refused before the library is called (a host address given to a
+    kernel would be an invalid device access)."""
+    import numpy as np
+    import torch
+
+    api.load_library()
+    m = torch.zeros(12, dtype=torch.float64)
+    d = torch.zeros((12, 2), dtype=torch.float64)
+    with pytest.raises(api.FlintsError, match="map must be a contiguous float64 CUDA tensor"):
+        api.lens_noalloc(1, np.ones(33), m, d, m.clone(), K=16)
+
+    class _Plan:  # stand-in: only the fields the job table reads
+        spin, npix, handle = 2, 12, 0
+
+    for job, msg in [((_Plan(), 0, 12, m, d, d, None, None), "job 0: map must be"),
+                     ((_Plan(), 0, 0, None, None, None, None, None), None)]:
+        if msg is None:  # an empty job carries no buffers
+            api._job_array([job])
+        else:
+            with pytest.raises(api.FlintsError, match=msg):
+                api._job_array([job])
+    with pytest.raises(api.FlintsError, match="status must be a contiguous uint8 CUDA tensor"):
+        api._dev_buf(torch.zeros(24, dtype=torch.uint8)[::2], 12, "status", "uint8")
