@@ -523,8 +523,9 @@ def run_ours(args):
         flops_convention="the method's own arithmetic per point (FP64 operation count, flops.fp64_flops): "
                          "the double-float path executes the same steps, each as several FP32 instructions",
         issue_flops_per_point=f_issue,
-        issue_note="FP32 flops executed per point by the double-float emulation (instruction cost, not "
-                   "algorithmic work)",
+        issue_note="FP32 flops per point of the plain double-float cost model (instruction cost, not "
+                   "algorithmic work; an upper estimate: the anchored accumulation executes fewer, and "
+                   "issue_rate holds the measured instruction count)",
         issue_frac=rate * f_issue / 1e12 / peaks["fp32_tflops"],
         issue_rate=None if aug else {
             "warp_instr_per_point": MIXED_WARP_INSTR_PER_POINT,

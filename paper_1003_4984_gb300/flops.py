@@ -23,7 +23,12 @@ Counting convention (used for every roofline fraction reported by the bench):
 * mixed path: the same steps executed in double-float arithmetic on the FP32
   pipe, each double-float operation costed in FP32 flops: multiply-accumulate
   into an accumulator 15 (one TwoProduct with cross terms, one TwoSum, two
-  adds), add 20, multiply 10, square root or reciprocal 35.
+  adds), add 20, multiply 10, square root or reciprocal 35.  These are the
+  costs of plain double-float operations: where the kernel accumulates onto
+  an anchor (Cholesky rows, solves, covariance rows; about 6 FP32
+  instructions per real multiply-add) it executes less, so the count is an
+  upper estimate of the emulation's work, and the measured figure is the
+  warp-instruction count of an ncu capture.
 """
 from __future__ import annotations
 
