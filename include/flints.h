@@ -290,7 +290,8 @@ const char *flints_synth_last_error(void);
  *   Limits: lmax <= 8192 and a xi table of at most 8192 intervals; larger
  *   requests return FLINTS_EINVAL with a message naming the limit.
  *   Set-up: the first call on each device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current.
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture begins.
  *   Stream use: the call copies the spectrum from host memory and synchronises
  *   `stream` once, after the tabulation, to read xi(0) back; the lens kernel is
  *   then left running asynchronously on `stream`.

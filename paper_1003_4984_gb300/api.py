@@ -451,7 +451,9 @@ def lens_noalloc(nside: int, cl, map_, defl, out, var=None, status=None, cl_bb=N
     memory in their own pool, hosts that forbid library allocations): every
     buffer is the caller's; the library's working memory is a fixed device array
     shared by all calls, so calls must not overlap on the GPU.  The call copies
-    ``cl`` from host memory and synchronises ``stream`` once.
+    ``cl`` from host memory and synchronises ``stream`` once.  The first call on
+    a device looks up the array's device address; make it before any stream
+    capture begins.
     """
     lib = load_library()
     npix = 12 * int(nside) * int(nside)

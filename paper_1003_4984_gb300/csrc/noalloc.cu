@@ -8,13 +8,12 @@
 // interpolation coefficients and event counters -- in a file-scope __device__
 // array of fixed size, and runs the same tabulation and lens kernels as the
 // plan-based entry points.  Each call copies the spectrum from host memory and
-// synchronises its stream once (to read xi(0) back), so it is an ordinary
-// stream-ordered call, not one to record into a CUDA graph.
+// synchronises its stream once (to read xi(0) back).
 //
 // Host code must not use the array's name as a device address: in host code
 // it is only a stand-in.  The device address is obtained once per device with
 // cudaGetSymbolAddress, with that device current, on the first call made on
-// that device.
+// that device; that first call should come before any stream capture begins.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
