@@ -487,3 +487,61 @@ def test_spin1_deflection_field_exact_benchmark():
     assert rel < 0.05
     aug = kr.lens(nside, K, 1, dmap, defl, pix, tp, x0, f_minus=tm)
     assert np.mean(np.abs(aug.value - truth) ** 2) < np.mean(np.abs(res.value - truth) ** 2)
+
+
+# ------------------------------------------- symmetries of the HEALPix grid
+def _quarter_turn(nside):
+    """RING index of every pixel's image under the rotation by pi/2 about the z axis
+    (ring i holds 4 nq pixels, so pixel j goes to pixel j + nq of the same ring)."""
+    ring, j = hp.pix2ring(nside, np.arange(hp.npix(nside)))
+    first, n_in, _, _, _, nq = hp.ring_info(nside, ring)
+    return first + (j + nq) % n_in
+
+
+def _mirror(nside):
+    """RING index of every pixel's image under z -> -z (ring i -> ring 4 Nside - i, same
+    position in the ring)."""
+    ring, j = hp.pix2ring(nside, np.arange(hp.npix(nside)))
+    return hp.ring_info(nside, 4 * nside - ring)[0] + j
+
+
+@pytest.mark.parametrize("spin", [0, 2])
+def test_lens_commutes_with_the_grid_symmetries(spin):
+    """The whole estimator (displacement, K-nearest stencil, phases, factor) is covariant
+    under the symmetries of the grid.  A quarter turn about z carries every local frame
+    (e_theta, e_phi) along, so maps, deflections and outputs move with their pixels
+    unchanged.  The mirror z -> -z turns e_theta into -e_theta (keeping e_phi): the
+    deflection's theta component changes sign, and a spin-2 P = Q + iU measured from
+    e_theta towards e_phi becomes conj(P) (angle chi -> pi - chi).  Catches mistakes
+    that break these symmetries: a phase or frame sign lost in one hemisphere, a
+    displacement or index slip confined to one cap or one quarter of the rings."""
+    nside, lmax, K = 16, 40, 16
+    npix = hp.npix(nside)
+    cl = wl.cl_tt(lmax, 30.0) if spin == 0 else wl.cl_ee(lmax, 30.0)
+    m = sht.synth_map(nside, lmax, wl.draw_alm(cl, 41), spin=spin)
+    defl = np.random.default_rng(42).normal(scale=0.03, size=(npix, 2))  # about half a pixel
+    t_max, n = xi.grid_rule(np.abs(cl), K, nside)
+    tab, x0 = xi.spin0_table(cl, t_max, n) if spin == 0 else xi.spin2_tables(cl, None, t_max, n)[::2]
+    qu = m if spin == 0 else np.stack([m.real, m.imag], axis=1)
+    pix = np.arange(npix)
+    base = kr.lens(nside, K, spin, qu, defl, pix, tab, x0)
+    sigma = np.sqrt(np.mean(np.abs(m) ** 2))
+
+    rot = _quarter_turn(nside)
+    v = hp.pix2vec(nside, pix)
+    np.testing.assert_allclose(hp.pix2vec(nside, rot), np.stack([-v[:, 1], v[:, 0], v[:, 2]], 1), atol=1e-15)
+    qu_r, defl_r = np.empty_like(qu), np.empty_like(defl)
+    qu_r[rot], defl_r[rot] = qu, defl
+    r = kr.lens(nside, K, spin, qu_r, defl_r, pix, tab, x0)
+    assert np.max(np.abs(r.value[rot] - base.value)) <= 1e-10 * sigma
+    assert np.max(np.abs(r.variance[rot] - base.variance)) <= 1e-10 * x0
+
+    mir = _mirror(nside)
+    np.testing.assert_array_equal(hp.pix2vec(nside, mir), v * np.array([1.0, 1.0, -1.0]))
+    qu_m, defl_m = np.empty_like(qu), np.empty_like(defl)
+    qu_m[mir] = qu if spin == 0 else qu * np.array([1.0, -1.0])
+    defl_m[mir] = defl * np.array([-1.0, 1.0])
+    r = kr.lens(nside, K, spin, qu_m, defl_m, pix, tab, x0)
+    want = base.value if spin == 0 else np.conj(base.value)
+    assert np.max(np.abs(r.value[mir] - want)) <= 1e-10 * sigma
+    assert np.max(np.abs(r.variance[mir] - base.variance)) <= 1e-10 * x0
