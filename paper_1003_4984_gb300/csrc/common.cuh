@@ -97,7 +97,8 @@ __device__ __forceinline__ df df_rcp(df a) {
 // Raphson on 1/sqrt from the single-precision rsqrtf(d.hi) = r0 (2 ulp): with
 // e = 1 - d r0^2 (|e| < 2^-21, formed from the exact square r0^2 and a double-
 // float product), 1/sqrt(d) = r0 (1 - e)^(-1/2) = r0 (1 + e/2 + 3e^2/8 + O(e^3)),
-// so il carries about 2^-46 relative error; l = d il.  Requires d.hi > 0 normal.
+// so il carries a relative error of about 2^-47 typically and 2^-44 at most (the
+// roundings of e and of the correction); l = d il.  Requires d.hi > 0 normal.
 __device__ __forceinline__ void df_pivot(df d, df &l, df &il) {
     const float r0 = rsqrtf(d.hi);
     const float p = __fmul_rn(r0, r0);
@@ -144,7 +145,9 @@ __device__ __forceinline__ df dfacc_val(dfacc a) { return two_sum(a.hi, a.lo); }
 // and the cross terms of the double-float operands collect in the low word l,
 // whose size stays near the grid step.  A multiply-accumulate is 6 FP32
 // instructions (a general double-float one is 12) with an absolute error of
-// about 2^-46 B per step.  The value is (h - C) + l, the first term exact.
+// at most about 2^-46 2^e per step (typically 2^-49 2^e; 2^e <= 2B when the
+// anchor is the smallest one above B).  The value is (h - C) + l, the first
+// term exact.
 struct anc {
     float h, l;
 };
