@@ -4,10 +4,10 @@ precision Cholesky factor corrected by FP64 iterative refinement.
 On the Nside 4096 spin-2 workload (K = 32 nearest pixels, lmax 4096, the
 nugget 1.49e-8 of Sec. 2.4) the normalised covariance S + nI of a stencil has
 eigenvalues down to the nugget (those of S reach 1e-12), so its condition
-number is about 2e9 and kappa * u_32 is about 100: rounded to FP32 the matrix is not positive definite, and a
-factor that exists only after a diagonal shift is too poor a preconditioner
-for refinement to reach the 1e-6 tolerance of the mixed path in a bounded
-number of steps.  These are properties of the covariance the paper builds
+number is about 2e9 and kappa * u_32 is about 100: rounded to FP32 the
+matrix is not positive definite, and a factor that exists only after a
+diagonal shift is too poor a preconditioner for refinement to reach the 1e-6
+tolerance of the mixed path in a bounded number of steps.  These are properties of the covariance the paper builds
 (Eqs. fundamental_variance, spins_correl), checked here with the oracle on
 seeded stencils of that workload.
 """
