@@ -173,7 +173,6 @@ def hashed_normal(idx: np.ndarray, seed: int, ncomp: int = 1) -> np.ndarray:
     """Deterministic N(0,1)-like values per pixel index (SplitMix64 hash, Box-Muller),
     so that any subset of a huge map can be generated without materialising it."""
     idx = np.asarray(idx, dtype=np.uint64)
-    out = []
     with np.errstate(over="ignore"):  # modular 64-bit arithmetic
         return _hashed(idx, seed, ncomp)
 
