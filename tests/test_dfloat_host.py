@@ -4,58 +4,24 @@ pivot and the anchored accumulator) compiled for the host and checked against
 exact rational arithmetic, without a GPU.
 
 The section of common.cuh between ``struct df`` and the precision policy is
-compiled as host C++ with single-precision stand-ins for the CUDA rounding
-intrinsics (each a correctly rounded IEEE operation: __fadd_rn is a + b in
-float, __fmaf_rn is fmaf, and so on; rsqrtf, which the device computes to
-2 ulp, is the correctly rounded value moved by 2 ulp).  The bounds asserted
-are the ones the source states: error-free transforms are exact, general
-double-float operations keep about 2^-44 relative error, the pivot's inverse
-square root 2^-47 typically and 2^-44 at most, and the anchored accumulator about 2^-46 2^e per
-multiply-add, 2^e being the power of two of its anchor (B < 2^e <= 2B when
-the partial sums stay below B; measured worst 2^-46 2^e, median 2^-49 2^e).
+compiled as host C++ (tests/host_compile.py: correctly rounded stand-ins for
+the rounding intrinsics; rsqrtf, which the device computes to 2 ulp, is the
+correctly rounded value moved by 2 ulp).  The bounds asserted are the ones
+the source states: error-free transforms are exact, general double-float
+operations keep about 2^-44 relative error, the pivot's inverse square root
+2^-47 typically and 2^-44 at most, and the anchored accumulator about
+2^-46 2^e per multiply-add, 2^e being the power of two of its anchor
+(B < 2^e <= 2B when the partial sums stay below B; measured worst 2^-46 2^e,
+median 2^-49 2^e).
 Each test draws from its own seeded generator.
 """
-import os
 import random
-import shutil
-import subprocess
 from fractions import Fraction as Fr
 
 import numpy as np
 import pytest
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-COMMON = os.path.join(ROOT, "paper_1003_4984_gb300", "csrc", "common.cuh")
-
-SHIM = r"""
-#include <cmath>
-#include <cstdio>
-#include <cstdlib>
-#include <cstring>
-#include <string>
-// correctly rounded single-precision stand-ins for the CUDA rounding intrinsics
-static inline float __fadd_rn(float a, float b) { volatile float r = a + b; return r; }
-static inline float __fsub_rn(float a, float b) { volatile float r = a - b; return r; }
-static inline float __fmul_rn(float a, float b) { volatile float r = a * b; return r; }
-static inline float __fdiv_rn(float a, float b) { volatile float r = a / b; return r; }
-static inline float __fmaf_rn(float a, float b, float c) { return std::fma(a, b, c); }
-static inline float __fsqrt_rn(float a) { return std::sqrt(a); }
-static inline float __frcp_rn(float a) { volatile float r = 1.0f / a; return r; }
-// rsqrtf: 1/sqrt(a) moved by 2 ulp (down or up with the input's last bit), the device
-// function's documented error bound, so that the pivot's Newton step is tested at it
-static inline float rsqrtf(float a) {
-    float f = (float)(1.0 / std::sqrt((double)a));
-    unsigned u, ua;
-    std::memcpy(&u, &f, 4);
-    std::memcpy(&ua, &a, 4);
-    u = (ua & 1u) ? u + 2u : u - 2u;
-    std::memcpy(&f, &u, 4);
-    return f;
-}
-static inline float __double2float_rn(double x) { volatile float r = (float)x; return r; }
-static inline unsigned __float_as_uint(float f) { unsigned u; std::memcpy(&u, &f, 4); return u; }
-static inline float __uint_as_float(unsigned u) { float f; std::memcpy(&f, &u, 4); return f; }
-"""
+from tests import host_compile as hc
 
 DRIVER = r"""
 static float rd(void) { char b[64]; if (scanf("%63s", b) != 1) exit(2); return strtof(b, nullptr); }
@@ -107,32 +73,16 @@ int main() {
 """
 
 
-def _section() -> str:
-    src = open(COMMON).read()
-    a = src.index("struct df {")
-    b = src.index("// Precision policy")
-    body = src[a:b]
-    body = body[:body.rindex("// ----")]  # drop the banner of the next section
-    return body.replace("__device__ __forceinline__", "static inline")
-
-
 @pytest.fixture(scope="module")
 def run(tmp_path_factory):
-    cxx = shutil.which("g++") or shutil.which("c++")
-    if cxx is None:
+    if hc.compiler() is None:
         pytest.skip("no host C++ compiler")
-    d = tmp_path_factory.mktemp("dfloat")
-    src = d / "dfloat_host.cpp"
-    src.write_text(SHIM + _section() + DRIVER)
-    exe = d / "dfloat_host"
-    r = subprocess.run([cxx, "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", str(src), "-o", str(exe)],
-                       capture_output=True, text=True)
-    assert r.returncode == 0, r.stderr
+    text = hc.cut("common.cuh", "struct df {", "// Precision policy") + DRIVER
+    exe = hc.build(tmp_path_factory.mktemp("dfloat"), "dfloat_host", text)
 
     def call(lines):
-        p = subprocess.run([str(exe)], input="\n".join(lines) + "\n", capture_output=True, text=True)
-        assert p.returncode == 0, p.stderr
-        return [[float.fromhex(t) for t in ln.split()] for ln in p.stdout.splitlines()]
+        out = hc.run(exe, "\n".join(lines) + "\n")
+        return [[float.fromhex(t) for t in ln.split()] for ln in out.splitlines()]
 
     return call
 
