@@ -57,12 +57,15 @@ def test_xi_table_matches_oracle(fl, spin, nside, lmax, ld, K):
         xp, xm, dxp, dxm = xi.xis_direct(spin, cl, bb, nodes, deriv=True)
         ref, dref = xp, dxp
         fm, gm = plan.table(1)
-        np.testing.assert_allclose(fm, xm / xp[0], atol=1e-13)
-        np.testing.assert_allclose(gm * t_max, dxm / xp[0] * t_max, atol=1e-11)
+        np.testing.assert_allclose(fm, xm / xp[0], rtol=0, atol=2e-11)
+        np.testing.assert_allclose(gm * t_max, dxm / xp[0] * t_max, rtol=0, atol=1e-9)
     assert abs(info.xi0 - ref[0]) <= 1e-13 * ref[0]
-    np.testing.assert_allclose(f, ref / ref[0], atol=1e-13)
-    # slopes compared in units of the table domain
-    np.testing.assert_allclose(g * t_max, dref / ref[0] * t_max, atol=1e-11)
+    # absolute bounds in units of xi(0), slopes in units of the table domain: 10x and
+    # more above what the same kernel source gives compiled for the host
+    # (tests/test_xi_table_host.py: values 1e-14, slopes up to 1.2e-10 for spin 1,
+    # xi- values 2e-12); a slope error e moves an interpolated value by e / n at most
+    np.testing.assert_allclose(f, ref / ref[0], rtol=0, atol=1e-13)
+    np.testing.assert_allclose(g * t_max, dref / ref[0] * t_max, rtol=0, atol=1e-9)
 
 
 # ------------------------------------------------------------------ stencil

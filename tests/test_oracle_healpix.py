@@ -12,10 +12,10 @@ def test_nside1_base_pixels():
     # Nside = 1: three rings of four pixels at z = 2/3, 0, -2/3; the middle ring
     # starts at phi = 0, the others are offset by half a pixel (pi/4).
     z, s, phi = hp.pix2ang(1, np.arange(12))
-    np.testing.assert_allclose(z, [2 / 3] * 4 + [0] * 4 + [-2 / 3] * 4, atol=1e-16)
+    np.testing.assert_allclose(z, [2 / 3] * 4 + [0] * 4 + [-2 / 3] * 4, rtol=0, atol=1e-16)
     q = np.pi / 2
     np.testing.assert_allclose(phi, [q / 2 + k * q for k in range(4)] + [k * q for k in range(4)]
-                               + [q / 2 + k * q for k in range(4)], atol=1e-15)
+                               + [q / 2 + k * q for k in range(4)], rtol=0, atol=1e-15)
 
 
 @pytest.mark.parametrize("nside", [1, 2, 4, 16, 64])
@@ -33,7 +33,7 @@ def test_ring_layout(nside):
     assert np.abs(np.sum(v * v, axis=1) - 1).max() <= 1e-15
     # north-south mirror symmetry: pixel p and Npix-1-p have opposite z
     z2 = hp.pix2ang(nside, pix)[0]
-    np.testing.assert_allclose(z2, -z2[::-1], atol=1e-16)
+    np.testing.assert_allclose(z2, -z2[::-1], rtol=0, atol=1e-16)
     # z strictly decreasing from ring to ring; mean z is zero (equal areas)
     zr = hp.ring_info(nside, r)[2]
     assert np.all(np.diff(zr) < 0)

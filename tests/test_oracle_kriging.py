@@ -24,7 +24,7 @@ def test_displacement_geodesic():
     n = hp.pix2vec(nside, pix)
     n2 = kr.displace(nside, pix, defl)
     assert np.array_equal(n2[:5], n[:5])  # zero deflection leaves the centre in place
-    np.testing.assert_allclose(np.linalg.norm(n2, axis=1), 1.0, atol=2e-16)
+    np.testing.assert_allclose(np.linalg.norm(n2, axis=1), 1.0, rtol=0, atol=4.5e-16)  # 2 ulp
     # geodesic length equals |d|
     ang = 2 * np.arcsin(np.linalg.norm(n2 - n, axis=1) / 2)
     np.testing.assert_allclose(ang, np.hypot(defl[:, 0], defl[:, 1]), rtol=1e-12, atol=1e-18)
@@ -33,8 +33,8 @@ def test_displacement_geodesic():
     a = np.sum((n2 - n) * e_th, axis=1)
     b = np.sum((n2 - n) * e_ph, axis=1)
     dl = np.hypot(defl[5:, 0], defl[5:, 1])
-    np.testing.assert_allclose(a[5:] / np.hypot(a[5:], b[5:]), defl[5:, 0] / dl, atol=1e-6)
-    np.testing.assert_allclose(b[5:] / np.hypot(a[5:], b[5:]), defl[5:, 1] / dl, atol=1e-6)
+    np.testing.assert_allclose(a[5:] / np.hypot(a[5:], b[5:]), defl[5:, 0] / dl, rtol=0, atol=1e-6)
+    np.testing.assert_allclose(b[5:] / np.hypot(a[5:], b[5:]), defl[5:, 1] / dl, rtol=0, atol=1e-6)
 
 
 # ---------------------------------------------------------- linear algebra
@@ -44,10 +44,10 @@ def test_cholesky_and_solve_against_numpy():
     A = X @ np.conj(np.swapaxes(X, 1, 2)) + K * np.eye(K)
     L, ok = kr.cholesky_batched(A)
     assert ok.all()
-    np.testing.assert_allclose(L, np.linalg.cholesky(A), atol=1e-12)
+    np.testing.assert_allclose(L, np.linalg.cholesky(A), rtol=0, atol=1e-12)
     b = RNG.normal(size=(P, K)) + 1j * RNG.normal(size=(P, K))
     z = kr.forward_solve(L, b)
-    np.testing.assert_allclose(np.einsum("pij,pj->pi", L, z), b, atol=1e-12)
+    np.testing.assert_allclose(np.einsum("pij,pj->pi", L, z), b, rtol=0, atol=1e-12)
 
 
 def test_nugget_rule_for_indefinite_matrix():
@@ -58,7 +58,7 @@ def test_nugget_rule_for_indefinite_matrix():
     L, nug = kr.factor_with_nugget(S[None])
     # n = -lambda_min + epsilon (Sec. 2.4), up to the extra epsilon steps rounding may need
     assert 3e-6 + kr.EPS_NUGGET - 1e-12 <= nug[0] <= 3e-6 + 3 * kr.EPS_NUGGET
-    np.testing.assert_allclose(L[0] @ L[0].T, S + nug[0] * np.eye(K), atol=1e-14)
+    np.testing.assert_allclose(L[0] @ L[0].T, S + nug[0] * np.eye(K), rtol=0, atol=1e-14)
     # a positive-definite matrix takes n = epsilon
     _, nug = kr.factor_with_nugget(((Q * np.abs(lam)) @ Q.T + 1e-3 * np.eye(K))[None])
     assert nug[0] == kr.EPS_NUGGET
@@ -146,7 +146,7 @@ def test_spin2_pair_phase_by_addition_theorem(ell):
     corr = sum(_sY2(ell, m, a) * np.conj(_sY2(ell, m, b)) for m in range(-ell, ell + 1))
     beta = 2 * np.arcsin(np.linalg.norm(a - b, axis=1) / 2)
     model = (2 * ell + 1) / (4 * math.pi) * wigner_d(ell, 2, 2, beta) * kr.pair_phase(a, b)
-    np.testing.assert_allclose(corr, model, atol=1e-13)
+    np.testing.assert_allclose(corr, model, rtol=0, atol=1e-13)
 
 
 def test_spin2_synthesis_matches_harmonics():
@@ -162,7 +162,7 @@ def test_spin2_synthesis_matches_harmonics():
             ref = a * _sY2(ell, m, v)
             if m > 0:
                 ref = ref + (-(-1) ** m * np.conj(E[ell, m])) * _sY2(ell, -m, v)
-            np.testing.assert_allclose(got, ref, atol=1e-14)
+            np.testing.assert_allclose(got, ref, rtol=0, atol=1e-14)
 
 
 def test_spin2_frame_covariance():
@@ -256,7 +256,7 @@ def test_spin2_pair_phase_factorises_through_the_target(spin):
         x = triple / den
         g = ((1 - 1j * x) ** 2 / (1 + x * x)) ** spin  # exp(-isE) with E = 2 atan(x)
         got = np.conj(kr.pair_phase(n, a, spin)) * kr.pair_phase(n, b, spin) * g
-        np.testing.assert_allclose(got, kr.pair_phase(a, b, spin), atol=1e-12)
+        np.testing.assert_allclose(got, kr.pair_phase(a, b, spin), rtol=0, atol=1e-12)
 
 
 # ------------------------------------------------- supersampling (Sec. 2.6)
@@ -309,7 +309,7 @@ def test_transport_phase_matches_rotation_along_the_geodesic():
         ut = _rodrigues(u, np.cross(npr, n), ang)
         chi = np.arctan2(np.sum(ut * e_ph, axis=1), np.sum(ut * e_th, axis=1))
         got = np.exp(2j * psi) * kr.pair_phase(n, npr)
-        np.testing.assert_allclose(got, np.exp(2j * chi), atol=1e-10)
+        np.testing.assert_allclose(got, np.exp(2j * chi), rtol=0, atol=1e-10)
 
 
 def test_transport_along_a_meridian_keeps_the_frame():
@@ -320,7 +320,7 @@ def test_transport_along_a_meridian_keeps_the_frame():
     defl = np.zeros((pix.size, 2))
     defl[:, 0] = RNG.normal(size=pix.size) * 1e-2
     tv = kr.displace(nside, pix, defl)
-    np.testing.assert_allclose(kr.pair_phase(hp.pix2vec(nside, pix), tv), 1.0, atol=1e-12)
+    np.testing.assert_allclose(kr.pair_phase(hp.pix2vec(nside, pix), tv), 1.0, rtol=0, atol=1e-12)
 
 
 # ----------------------------------------- augmented (widely linear) spin 2
@@ -342,7 +342,7 @@ def test_spin2_pseudo_phase_by_addition_theorem(ell):
     corr = sum(_sY(2, ell, m, a) * np.conj(_sY(-2, ell, m, b)) for m in range(-ell, ell + 1))
     beta = 2 * np.arcsin(np.linalg.norm(a - b, axis=1) / 2)
     model = (2 * ell + 1) / (4 * math.pi) * wigner_d(ell, 2, -2, beta) * kr.pseudo_phase(a, b)
-    np.testing.assert_allclose(corr, model, atol=1e-13)
+    np.testing.assert_allclose(corr, model, rtol=0, atol=1e-13)
 
 
 def _aug_inputs(n_pts, K, spread, seed):
@@ -443,9 +443,9 @@ def test_spin1_phases_by_addition_theorem(ell):
     beta = 2 * np.arcsin(np.linalg.norm(a - b, axis=1) / 2)
     w = (2 * ell + 1) / (4 * math.pi)
     herm = sum(_sY(1, ell, m, a) * np.conj(_sY(1, ell, m, b)) for m in range(-ell, ell + 1))
-    np.testing.assert_allclose(herm, w * wigner_d(ell, 1, 1, beta) * kr.pair_phase(a, b, 1), atol=1e-13)
+    np.testing.assert_allclose(herm, w * wigner_d(ell, 1, 1, beta) * kr.pair_phase(a, b, 1), rtol=0, atol=1e-13)
     pseudo = sum(_sY(1, ell, m, a) * np.conj(_sY(-1, ell, m, b)) for m in range(-ell, ell + 1))
-    np.testing.assert_allclose(pseudo, w * wigner_d(ell, 1, -1, beta) * kr.pseudo_phase(a, b, 1), atol=1e-13)
+    np.testing.assert_allclose(pseudo, w * wigner_d(ell, 1, -1, beta) * kr.pseudo_phase(a, b, 1), rtol=0, atol=1e-13)
 
 
 @pytest.mark.parametrize("spin", [1, 2])
@@ -462,7 +462,7 @@ def test_pseudo_covariance_of_real_fields(spin):
         corr = sum((-1) ** m * _sY(spin, ell, m, a) * _sY(spin, ell, -m, b) for m in range(-ell, ell + 1))
         model = (-1) ** spin * (2 * ell + 1) / (4 * math.pi) * wigner_d(ell, spin, -spin, beta) \
             * kr.pseudo_phase(a, b, spin)
-        np.testing.assert_allclose(corr, model, atol=1e-13)
+        np.testing.assert_allclose(corr, model, rtol=0, atol=1e-13)
 
 
 def test_spin1_deflection_field_exact_benchmark():
@@ -529,7 +529,7 @@ def test_lens_commutes_with_the_grid_symmetries(spin):
 
     rot = _quarter_turn(nside)
     v = hp.pix2vec(nside, pix)
-    np.testing.assert_allclose(hp.pix2vec(nside, rot), np.stack([-v[:, 1], v[:, 0], v[:, 2]], 1), atol=1e-15)
+    np.testing.assert_allclose(hp.pix2vec(nside, rot), np.stack([-v[:, 1], v[:, 0], v[:, 2]], 1), rtol=0, atol=1e-15)
     qu_r, defl_r = np.empty_like(qu), np.empty_like(defl)
     qu_r[rot], defl_r[rot] = qu, defl
     r = kr.lens(nside, K, spin, qu_r, defl_r, pix, tab, x0)

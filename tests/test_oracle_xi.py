@@ -17,12 +17,12 @@ def test_wigner_reference_small_cases():
     b = np.linspace(0.1, 3.0, 7)
     c, s = np.cos(b), np.sin(b)
     # textbook d^1 and d^2 entries
-    np.testing.assert_allclose(wigner_d(1, 1, 0, b), -s / math.sqrt(2), atol=1e-15)
-    np.testing.assert_allclose(wigner_d(1, 0, 1, b), s / math.sqrt(2), atol=1e-15)
-    np.testing.assert_allclose(wigner_d(1, 1, 1, b), (1 + c) / 2, atol=1e-15)
-    np.testing.assert_allclose(wigner_d(2, 2, 2, b), ((1 + c) / 2) ** 2, atol=1e-15)
-    np.testing.assert_allclose(wigner_d(2, 2, -2, b), ((1 - c) / 2) ** 2, atol=1e-15)
-    np.testing.assert_allclose(wigner_d(2, 0, 0, b), (3 * c * c - 1) / 2, atol=1e-15)
+    np.testing.assert_allclose(wigner_d(1, 1, 0, b), -s / math.sqrt(2), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(wigner_d(1, 0, 1, b), s / math.sqrt(2), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(wigner_d(1, 1, 1, b), (1 + c) / 2, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(wigner_d(2, 2, 2, b), ((1 + c) / 2) ** 2, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(wigner_d(2, 2, -2, b), ((1 - c) / 2) ** 2, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(wigner_d(2, 0, 0, b), (3 * c * c - 1) / 2, rtol=0, atol=1e-15)
 
 
 def test_xi0_at_zero_is_spectrum_sum():
@@ -42,7 +42,7 @@ def test_xi0_single_multipole_is_legendre(ell):
     got, dgot = xi.xi0_direct(cl, t, deriv=True)
     x = 1 - t / 2
     ref = (2 * ell + 1) / (4 * math.pi) * eval_legendre(ell, x)
-    np.testing.assert_allclose(got, ref, atol=1e-13 * (2 * ell + 1))
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13 * (2 * ell + 1))
     # derivative against a central difference in t
     h = 1e-6
     fd = (xi.xi0_direct(cl, t[3:] + h) - xi.xi0_direct(cl, t[3:] - h)) / (2 * h)
@@ -71,7 +71,7 @@ def test_delta_columns_unitary_and_symmetric():
             col = D[ell, L - ell: L + ell + 1]
             assert abs(np.sum(col * col) - 1.0) < 1e-13  # rows of a unitary matrix
             # Delta^l_{-u,m2} = (-1)^{l+m2} Delta^l_{u,m2}
-            np.testing.assert_allclose(col[::-1], (-1) ** (ell + m2) * col, atol=1e-14)
+            np.testing.assert_allclose(col[::-1], (-1) ** (ell + m2) * col, rtol=0, atol=1e-14)
 
 
 @pytest.mark.parametrize("m1,m2", [(0, 0), (1, 1), (1, -1), (2, 2), (2, -2)])
@@ -80,7 +80,7 @@ def test_appendix_b_route_matches_jacobi(m1, m2):
     beta = np.concatenate([[0.0, 1e-4], RNG.uniform(0, math.pi, 9)])
     d = xi.wigner_d_fourier(L, m1, m2, beta)
     for ell in range(max(abs(m1), abs(m2)), L + 1):
-        np.testing.assert_allclose(d[ell], wigner_d(ell, m1, m2, beta), atol=2e-14)
+        np.testing.assert_allclose(d[ell], wigner_d(ell, m1, m2, beta), rtol=0, atol=2e-13)  # about 2.5e-15 l: 1e-13 at l = 40 near b = 0, pi
 
 
 @pytest.mark.parametrize("ell", [2, 3, 10, 37])
@@ -91,8 +91,8 @@ def test_xi2_single_multipole(ell):
     beta = 2 * np.arcsin(np.sqrt(t) / 2)
     xp, xm, dxp, dxm = xi.xi2_direct(cl, None, t, deriv=True)
     w = (2 * ell + 1) / (4 * math.pi)
-    np.testing.assert_allclose(xp, w * wigner_d(ell, 2, 2, beta), atol=1e-14)
-    np.testing.assert_allclose(xm, w * wigner_d(ell, 2, -2, beta), atol=1e-14)
+    np.testing.assert_allclose(xp, w * wigner_d(ell, 2, 2, beta), rtol=0, atol=1e-14 * (2 * ell + 1))
+    np.testing.assert_allclose(xm, w * wigner_d(ell, 2, -2, beta), rtol=0, atol=1e-14 * (2 * ell + 1))
     h = 1e-7
     tt = t[2:]
     fdp = (xi.xi2_direct(cl, None, tt + h)[0] - xi.xi2_direct(cl, None, tt - h)[0]) / (2 * h)
@@ -110,8 +110,8 @@ def test_xi1_single_multipole(ell):
     beta = 2 * np.arcsin(np.sqrt(t) / 2)
     xp, xm, dxp, dxm = xi.xi1_direct(cl, None, t, deriv=True)
     w = (2 * ell + 1) / (4 * math.pi)
-    np.testing.assert_allclose(xp, w * wigner_d(ell, 1, 1, beta), atol=1e-14)
-    np.testing.assert_allclose(xm, w * wigner_d(ell, 1, -1, beta), atol=1e-14)
+    np.testing.assert_allclose(xp, w * wigner_d(ell, 1, 1, beta), rtol=0, atol=1e-14 * (2 * ell + 1))
+    np.testing.assert_allclose(xm, w * wigner_d(ell, 1, -1, beta), rtol=0, atol=1e-14 * (2 * ell + 1))
     h = 1e-7
     tt = t[2:]
     fdm = (xi.xi1_direct(cl, None, tt + h)[1] - xi.xi1_direct(cl, None, tt - h)[1]) / (2 * h)
@@ -146,15 +146,16 @@ def test_hermite_table_reproduces_cubics():
     tab = xi.HermiteTable(tmax, n, a + b * nodes + c * nodes ** 2 + d * nodes ** 3,
                           b + 2 * c * nodes + 3 * d * nodes ** 2)
     t = RNG.uniform(0, tmax, 200)
-    np.testing.assert_allclose(tab(t), a + b * t + c * t ** 2 + d * t ** 3, atol=1e-13)
+    np.testing.assert_allclose(tab(t), a + b * t + c * t ** 2 + d * t ** 3, rtol=0, atol=1e-13)
 
 
 def test_table_accuracy_c1_spectrum():
     cl = wl.cl_tt(128, 100.0)
     tmax = 4 * (1.35 * math.sqrt(16 / 3.0) / 64) ** 2
-    tab, x0 = xi.spin0_table(cl, tmax, 256)
+    tab, x0 = xi.spin0_table(cl, tmax, 256)  # a quarter of the grid rule's intervals
     t = RNG.uniform(0, tmax, 500)
-    np.testing.assert_allclose(tab(t), xi.xi0_direct(cl, t) / x0, atol=1e-10)
+    # cubic Hermite error h^4/384 max|f''''| at 256 intervals: measured 5.2e-10
+    np.testing.assert_allclose(tab(t), xi.xi0_direct(cl, t) / x0, rtol=0, atol=1e-9)
     assert tab.f[0] == 1.0
 
 
@@ -171,7 +172,7 @@ def test_grid_rule_meets_tolerance(name, cl, K, nside):
     if name == "c3":
         tp, _, _ = xi.spin2_tables(cl, None, t_max, n)
         ref = xi.xi2_direct(cl, None, t)[0] / xi.xi2_direct(cl, None, np.zeros(1))[0][0]
-        np.testing.assert_allclose(tp(t), ref, atol=1e-10)
+        np.testing.assert_allclose(tp(t), ref, rtol=0, atol=1e-10)
     else:
         tab, x0 = xi.spin0_table(cl, t_max, n)
-        np.testing.assert_allclose(tab(t), xi.xi0_direct(cl, t) / x0, atol=1e-10)
+        np.testing.assert_allclose(tab(t), xi.xi0_direct(cl, t) / x0, rtol=0, atol=1e-10)
