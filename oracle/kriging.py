@@ -36,7 +36,6 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import healpix as hp
-from . import xi as xi_mod
 
 EPS_NUGGET = 1.49e-8  # square root of the double-precision machine epsilon (Sec. 2.4)
 

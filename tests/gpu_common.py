@@ -1,12 +1,9 @@
 """Shared helpers of the GPU parity tests (inputs from ``workloads`` and the oracle)."""
 import itertools
-import math
 
 import numpy as np
-import pytest
 
 import workloads as wl
-from oracle import healpix as hp
 from oracle import kriging as kr
 from oracle import sht
 from oracle import xi

@@ -4,7 +4,6 @@ lensed values/variances of the CUDA path against the FP64 oracle.
 Tolerances (parity metric = max |gpu - oracle| / sigma_map for values and
 max |gpu - oracle| / xi(0) for variances): FP64 path 1e-9, mixed path 1e-6.
 """
-import math
 
 import numpy as np
 import pytest

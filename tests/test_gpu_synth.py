@@ -12,7 +12,6 @@ import numpy as np
 import pytest
 
 import workloads as wl
-from oracle import healpix as hp
 from oracle import sht
 from tests.gpu_common import require_gpu, to_host
 

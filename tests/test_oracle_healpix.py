@@ -1,5 +1,4 @@
 """Pins of the oracle's HEALPix RING geometry and exact K-nearest search."""
-import math
 
 import numpy as np
 import pytest
