@@ -93,7 +93,9 @@ class LensServer:
     # ------------------------------------------------------------ residency
     def register_map(self, nside: int, spin: int, tensor, cl, cl_bb=None):
         """Keep an unlensed map and its spectrum resident on the device (counted
-        against the HBM budget)."""
+        against the HBM budget).  The batched launch serves spin-0 and spin-2 maps."""
+        if spin not in (0, 2):
+            raise ValueError(f"map ({nside}, {spin}): the server lenses spin-0 and spin-2 maps")
         key = (nside, spin)
         if key in self.maps:
             self.resident -= self.maps[key].numel() * self.maps[key].element_size()
@@ -124,13 +126,24 @@ class LensServer:
 
     # ------------------------------------------------------------ admission
     def check(self, req: Request):
-        """Raise ValueError unless the request's map is registered and its range lies inside it."""
+        """Raise ValueError unless the request's map is registered, its range lies inside
+        it, its stencil size and precision are ones the library plans, and its
+        deflections (unless a callable makes them at admission) have one row per target."""
         if req.map_key not in self.maps:
             raise ValueError(f"request {req.rid}: no map registered for {req.map_key}")
         npix = 12 * req.map_key[0] * req.map_key[0]
         if req.count < 0 or req.first < 0 or req.first + req.count > npix:
             raise ValueError(f"request {req.rid}: target range [{req.first}, {req.first + req.count}) "
                              f"outside the map's {npix} pixels")
+        if req.K not in (16, 24, 32, 48):
+            raise ValueError(f"request {req.rid}: K must be 16, 24, 32 or 48 (got {req.K})")
+        if req.precision not in ("fp64", "mixed"):
+            raise ValueError(f"request {req.rid}: precision must be 'fp64' or 'mixed'")
+        if req.defl is None:
+            raise ValueError(f"request {req.rid}: no deflections")
+        if not callable(req.defl) and tuple(req.defl.shape) != (req.count, 2):
+            raise ValueError(f"request {req.rid}: deflections of shape {tuple(req.defl.shape)}, "
+                             f"expected ({req.count}, 2)")
 
     def submit(self, req: Request):
         """Queue a request (checked first)."""

@@ -334,6 +334,16 @@ def test_empty_and_invalid_requests(server_factory):
     with pytest.raises(ValueError, match="outside the map"):
         srv.run([Request(5, (16, 0), 16, 0, 10, _defl(10, 5)),
                  Request(6, (16, 2), 16, 0, 12 * 16 * 16 + 1, _defl(12 * 16 * 16 + 1, 6))])
+    # stencil sizes and precisions the library does not plan, missing or mis-shaped
+    # deflections, a spin-1 map (the batched launch serves spin 0 and 2)
+    for bad, msg in [(Request(7, (16, 0), 20, 0, 10, _defl(10, 7)), "K must be"),
+                     (Request(8, (16, 0), 16, 0, 10, _defl(10, 8), precision="fp32"), "precision"),
+                     (Request(9, (16, 0), 16, 0, 10, None), "no deflections"),
+                     (Request(10, (16, 2), 16, 0, 10, _defl(9, 10)), r"expected \(10, 2\)")]:
+        with pytest.raises(ValueError, match=msg):
+            srv.run([Request(11, (16, 0), 16, 0, 10, _defl(10, 11)), bad])
+    with pytest.raises(ValueError, match="spin-0 and spin-2"):
+        srv.register_map(16, 1, fake(np.zeros((12 * 16 * 16, 2))), cl=np.ones(48))
     assert srv.launches == n_launch and not srv.pending and not srv.active
 
 
