@@ -305,8 +305,14 @@ class LensServer:
 
 
 def latency_stats(finished) -> dict:
+    """p50/p99/mean/max latency (ms) and served points per second of finished requests
+    (latency = completion - arrival; rate over the span from the first arrival to the
+    last completion).  With no finished request the statistics are None."""
     import numpy as np
 
+    if not finished:
+        return {"requests": 0, "p50_ms": None, "p99_ms": None, "mean_ms": None, "max_ms": None, "points": 0,
+                "points_per_s": None, "span_s": None}
     lat = np.array([r.latency for r in finished]) * 1e3
     pts = sum(r.count for r in finished)
     span = max(r.finished_at for r in finished) - min(r.arrival for r in finished)

@@ -377,3 +377,15 @@ def test_deflections_are_produced_at_admission(server_factory):
     for r in done:
         np.testing.assert_array_equal(np.asarray(r.defl), np.asarray(_defl(1500, 300 + r.rid)))
         np.testing.assert_array_equal(np.asarray(r.out), _expected(srv, r))
+
+
+def test_latency_statistics():
+    reqs = [Request(i, (16, 0), 16, 0, 10 * (i + 1), None, arrival=0.1 * i) for i in range(100)]
+    for i, r in enumerate(reqs):
+        r.finished_at = r.arrival + 0.001 * (i + 1)  # latencies 1 .. 100 ms
+    st = latency_stats(reqs)
+    assert st["requests"] == 100 and st["max_ms"] == pytest.approx(100.0) and st["mean_ms"] == pytest.approx(50.5)
+    assert st["p50_ms"] == pytest.approx(50.5) and st["p99_ms"] == pytest.approx(99.01)
+    assert st["points"] == sum(10 * (i + 1) for i in range(100))
+    assert st["span_s"] == pytest.approx(9.9 + 0.1) and st["points_per_s"] == pytest.approx(st["points"] / 10.0)
+    assert latency_stats([])["requests"] == 0 and latency_stats([])["p99_ms"] is None
