@@ -508,6 +508,7 @@ __device__ __forceinline__ bool bordered_cholesky_rl(Elem *mat, int lane) {
         } else {
             d = O::val(O::acc(mat[tri<N>(j, j)]));
         }
+        __syncwarp();  // every lane has read the pivot before lane 0 overwrites it below
         if (!O::positive(d)) return false;
         T ljj, il;
         O::pivot(d, ljj, il);

@@ -7,8 +7,9 @@ stand-ins for the CUDA intrinsics they call: __fadd_rn is a + b in float,
 __fmaf_rn is fmaf, and so on.  Three stand-ins are approximate on the device:
 rsqrtf (2 ulp) is the correctly rounded value moved by 2 ulp so that the code
 that refines it is tested at that bound, rsqrt (1 ulp) and __fdividef (2 ulp)
-are the correctly rounded operations.  Warp shuffles return the calling
-thread's own value: the sections compiled here do not use them."""
+are the correctly rounded operations.  Warp shuffles either return the
+calling thread's own value (sections that only declare them) or run on a
+warp of 32 host threads that meet at every shuffle (warp-synchronous code)."""
 from __future__ import annotations
 
 import os
@@ -48,10 +49,53 @@ static inline double rsqrt(double a) { volatile double r = 1.0 / std::sqrt(a); r
 static inline float __double2float_rn(double x) { volatile float r = (float)x; return r; }
 static inline unsigned __float_as_uint(float f) { unsigned u; std::memcpy(&u, &f, 4); return u; }
 static inline float __uint_as_float(unsigned u) { float f; std::memcpy(&f, &u, 4); return f; }
-template <class T> static inline T __shfl_sync(unsigned, T v, int) { return v; }
-template <class T> static inline T __shfl_xor_sync(unsigned, T v, int) { return v; }
 using std::fma;
 using std::sqrt;
+"""
+
+# Warp shuffles that return the calling thread's own value, for sections that
+# only declare shuffles (in a struct they share with arithmetic under test).
+WARP_IDENTITY = r"""
+template <class T> static inline T __shfl_sync(unsigned, T v, int) { return v; }
+template <class T> static inline T __shfl_xor_sync(unsigned, T v, int) { return v; }
+"""
+
+# A warp of 32 host threads that meet at every shuffle and __syncwarp (warp-
+# synchronous code calls them convergently, in the same order in every lane):
+# run_warp(f) calls f(lane) on 32 threads.  A shuffle publishes each lane's
+# value, waits, reads the source lane's value and waits again before the slot
+# is reused.
+WARP_THREADS = r"""
+#include <barrier>
+#include <thread>
+static std::barrier<> *g_warp_bar = nullptr;
+static thread_local int t_lane = 0;
+static uint64_t g_warp_slot[32];
+template <class T> static inline T __shfl_sync(unsigned, T v, int src) {
+    static_assert(sizeof(T) <= 8, "one word per lane");
+    uint64_t b = 0;
+    std::memcpy(&b, &v, sizeof(T));
+    g_warp_slot[t_lane] = b;
+    g_warp_bar->arrive_and_wait();
+    const uint64_t r = g_warp_slot[src & 31];
+    g_warp_bar->arrive_and_wait();
+    T out;
+    std::memcpy(&out, &r, sizeof(T));
+    return out;
+}
+template <class T> static inline T __shfl_xor_sync(unsigned m, T v, int x) { return __shfl_sync(m, v, t_lane ^ x); }
+template <class T> static inline T __shfl_up_sync(unsigned m, T v, int d) {
+    return __shfl_sync(m, v, t_lane >= d ? t_lane - d : t_lane);
+}
+static inline void __syncwarp(unsigned = 0xffffffffu) { g_warp_bar->arrive_and_wait(); }
+static inline int __clz(unsigned x) { return x ? __builtin_clz(x) : 32; }
+template <class F> static void run_warp(F f) {
+    std::barrier<> bar(32);
+    g_warp_bar = &bar;
+    std::vector<std::thread> th;
+    for (int l = 0; l < 32; ++l) th.emplace_back([&f, l] { t_lane = l; f(l); });
+    for (auto &t : th) t.join();
+}
 """
 
 
@@ -71,14 +115,15 @@ def compiler() -> str | None:
     return shutil.which("g++") or shutil.which("c++")
 
 
-def build(tmpdir, name: str, text: str) -> str:
-    """Compile ``SHIM + text`` into an executable (strict IEEE: no contraction)."""
+def build(tmpdir, name: str, text: str, warp: str = "identity") -> str:
+    """Compile ``SHIM`` + the warp stand-ins (``"identity"`` or ``"threads"``) + ``text``
+    into an executable (strict IEEE: no contraction)."""
     src = os.path.join(str(tmpdir), name + ".cpp")
     with open(src, "w") as f:
-        f.write(SHIM + text)
+        f.write(SHIM + (WARP_THREADS if warp == "threads" else WARP_IDENTITY) + text)
     exe = os.path.join(str(tmpdir), name)
-    r = subprocess.run([compiler(), "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", src, "-o", exe],
-                       capture_output=True, text=True)
+    r = subprocess.run([compiler(), "-std=c++20", "-O2", "-pthread", "-ffp-contract=off", "-fno-fast-math", src, "-o",
+                        exe], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
     return exe
 
