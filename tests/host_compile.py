@@ -66,9 +66,23 @@ template <class T> static inline T __shfl_xor_sync(unsigned, T v, int) { return 
 # value, waits, reads the source lane's value and waits again before the slot
 # is reused.
 WARP_THREADS = r"""
-#include <barrier>
+#include <atomic>
 #include <thread>
-static std::barrier<> *g_warp_bar = nullptr;
+// the lanes' barrier: a generation count; waiting lanes yield their core
+struct WarpBarrier {
+    std::atomic<int> count{0};
+    std::atomic<unsigned> gen{0};
+    void arrive_and_wait() {
+        const unsigned g = gen.load(std::memory_order_acquire);
+        if (count.fetch_add(1, std::memory_order_acq_rel) == 31) {
+            count.store(0, std::memory_order_relaxed);
+            gen.store(g + 1, std::memory_order_release);
+        } else {
+            while (gen.load(std::memory_order_acquire) == g) std::this_thread::yield();
+        }
+    }
+};
+static WarpBarrier *g_warp_bar = nullptr;
 static thread_local int t_lane = 0;
 static uint64_t g_warp_slot[32];
 template <class T> static inline T __shfl_sync(unsigned, T v, int src) {
@@ -90,7 +104,7 @@ template <class T> static inline T __shfl_up_sync(unsigned m, T v, int d) {
 static inline void __syncwarp(unsigned = 0xffffffffu) { g_warp_bar->arrive_and_wait(); }
 static inline int __clz(unsigned x) { return x ? __builtin_clz(x) : 32; }
 template <class F> static void run_warp(F f) {
-    std::barrier<> bar(32);
+    WarpBarrier bar;
     g_warp_bar = &bar;
     std::vector<std::thread> th;
     for (int l = 0; l < 32; ++l) th.emplace_back([&f, l] { t_lane = l; f(l); });
