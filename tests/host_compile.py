@@ -112,6 +112,37 @@ template <class F> static void run_warp(F f) {
 }
 """
 
+# Further stand-ins for compiling a whole kernel header (csrc/lens.cuh) on the host
+# warp: vector types, read-only loads, sincospi and sinpif as sin/cos of pi x (the
+# device functions are within an ulp or two), bit casts, a warp ballot.
+LENS_SHIM = r"""
+#include <cstddef>
+#include <type_traits>
+#include <math.h>
+#define __align__(x) alignas(x)
+#define __device__
+struct double2 { double x, y; };
+static inline double2 make_double2(double x, double y) { return {x, y}; }
+struct float4 { float x, y, z, w; };
+template <class T> static inline T __ldg(const T *p) { return *p; }
+static inline void sincospi(double x, double *s, double *c) { *s = std::sin(M_PI * x); *c = std::cos(M_PI * x); }
+static inline float sinpif(float x) { return (float)std::sin(M_PI * (double)x); }
+static inline double __longlong_as_double(long long v) { double d; std::memcpy(&d, &v, 8); return d; }
+static inline long long __double_as_longlong(double d) { long long v; std::memcpy(&v, &d, 8); return v; }
+static inline int __popc(unsigned x) { return __builtin_popcount(x); }
+static bool g_ballot_slot[32];
+static inline unsigned __ballot_sync(unsigned, int pred) {
+    g_ballot_slot[t_lane] = pred != 0;
+    g_warp_bar->arrive_and_wait();
+    unsigned m = 0;
+    for (int l = 0; l < 32; ++l) m |= (unsigned)g_ballot_slot[l] << l;
+    g_warp_bar->arrive_and_wait();
+    return m;
+}
+template <class T> static inline T atomicAdd(T *p, T v) { T o = *p; *p += v; return o; }
+using std::floor; using std::fabs; using std::fmax; using std::isfinite; using std::atan2;
+"""
+
 
 def cut(path: str, start: str, stop: str, drop_banner: bool = True) -> str:
     """The text of ``path`` from ``start`` up to ``stop`` (the comment banner of the

@@ -23,7 +23,6 @@ from oracle import kriging as kr
 from oracle import sht
 from oracle import xi
 from tests import host_compile as hc
-from tests.test_stencil_host import EXTRA
 
 KERNEL_SHIM = r"""
 #include <sys/mman.h>
@@ -152,7 +151,7 @@ def run(tmp_path_factory):
         if depth == 0:
             break
         k += 1
-    text = (EXTRA + KERNEL_SHIM + '#include "' + hc.ROOT + '/include/flints.h"\nnamespace flints {\n'
+    text = (hc.LENS_SHIM + KERNEL_SHIM + '#include "' + hc.ROOT + '/include/flints.h"\nnamespace flints {\n'
             + hc.cut("common.cuh", "constexpr unsigned FULL", "// Host-side launchers (lens_spin0.cu", False)
             + api[a:k + 1] + "\n"
             + hc.cut("xi_table.cu", "__global__ void xi_table_kernel", "cudaError_t launch_xi_table(", False)

@@ -8,8 +8,7 @@ the belt.  Where the K-th and (K+1)-th neighbours tie to 1e-11, any valid
 K-nearest set is accepted (the same rule as the GPU stencil test).
 
 The lens kernel's device code is compiled for the host as a whole (host
-stand-ins: tests/host_compile.py, plus sincospi and sinpif as sin/cos of pi x
-and a warp ballot on the host warp); the plan's grid rule (table_grid) gives
+stand-ins: tests/host_compile.py); the plan's grid rule (table_grid) gives
 the search disc."""
 import numpy as np
 import pytest
@@ -19,33 +18,7 @@ from oracle import healpix as hp
 from oracle import kriging as kr
 from tests import host_compile as hc
 
-EXTRA = r"""
-#include <cstddef>
-#include <type_traits>
-#include <math.h>
-#define __align__(x) alignas(x)
-#define __device__
-struct double2 { double x, y; };
-static inline double2 make_double2(double x, double y) { return {x, y}; }
-struct float4 { float x, y, z, w; };
-template <class T> static inline T __ldg(const T *p) { return *p; }
-static inline void sincospi(double x, double *s, double *c) { *s = std::sin(M_PI * x); *c = std::cos(M_PI * x); }
-static inline float sinpif(float x) { return (float)std::sin(M_PI * (double)x); }
-static inline double __longlong_as_double(long long v) { double d; std::memcpy(&d, &v, 8); return d; }
-static inline long long __double_as_longlong(double d) { long long v; std::memcpy(&v, &d, 8); return v; }
-static inline int __popc(unsigned x) { return __builtin_popcount(x); }
-static bool g_ballot_slot[32];
-static inline unsigned __ballot_sync(unsigned, int pred) {
-    g_ballot_slot[t_lane] = pred != 0;
-    g_warp_bar->arrive_and_wait();
-    unsigned m = 0;
-    for (int l = 0; l < 32; ++l) m |= (unsigned)g_ballot_slot[l] << l;
-    g_warp_bar->arrive_and_wait();
-    return m;
-}
-template <class T> static inline T atomicAdd(T *p, T v) { T o = *p; *p += v; return o; }
-using std::floor; using std::fabs; using std::fmax; using std::isfinite; using std::atan2;
-"""
+
 
 DRIVER = r"""
 using namespace flints;
@@ -117,7 +90,7 @@ def run(tmp_path_factory):
         if depth == 0:
             break
         k += 1
-    text = (EXTRA + '#include "' + hc.ROOT + '/include/flints.h"\nnamespace flints {\n'
+    text = (hc.LENS_SHIM + '#include "' + hc.ROOT + '/include/flints.h"\nnamespace flints {\n'
             + hc.cut("common.cuh", "constexpr unsigned FULL", "// Host-side launchers (lens_spin0.cu", False)
             + api[a:k + 1] + "\n"
             + hc.cut("lens.cuh", "template <class T>\nstruct Cx {", "// Single-launch kernel", False)
