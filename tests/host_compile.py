@@ -161,11 +161,11 @@ def compiler() -> str | None:
 
 
 def build(tmpdir, name: str, text: str, warp: str = "identity") -> str:
-    """Compile ``SHIM`` + the warp stand-ins (``"identity"`` or ``"threads"``) + ``text``
-    into an executable (strict IEEE: no contraction)."""
+    """Compile ``SHIM`` + the warp stand-ins (``"identity"``, ``"threads"`` or none) +
+    ``text`` into an executable (strict IEEE: no contraction)."""
     src = os.path.join(str(tmpdir), name + ".cpp")
     with open(src, "w") as f:
-        f.write(SHIM + (WARP_THREADS if warp == "threads" else WARP_IDENTITY) + text)
+        f.write(SHIM + {"threads": WARP_THREADS, "identity": WARP_IDENTITY}.get(warp, "") + text)
     exe = os.path.join(str(tmpdir), name)
     r = subprocess.run([compiler(), "-std=c++20", "-O2", "-pthread", "-ffp-contract=off", "-fno-fast-math", src, "-o",
                         exe], capture_output=True, text=True)

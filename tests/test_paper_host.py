@@ -1,0 +1,128 @@
+"""The paper's stencil with tabulated inverses, run through its own C API
+(flints_paper_plan, flints_paper_lens in csrc/paper.cu) on the host: the
+plan's kernels (pixel tables, stencils and classes, the per-class L^-1 in a
+64-thread block with __syncthreads) and the apply kernels (128-thread blocks
+of warp-synchronous code) execute on host threads that run freely between
+barriers (tests/cuda_host.py), so a missing __syncthreads or __syncwarp shows
+as a wrong result.  Results are compared with the oracle's class route (Secs.
+2.3-2.5) on whole skies at Nside 8 to 32, spin 0 and 2, levels y = 1 (9
+pixels) and 2 (36 pixels), FP64 and mixed, and the augmented spin-2
+estimator; tolerances as on the GPU (1e-9 FP64, 1e-6 mixed, of sigma_map and
+xi(0))."""
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import faces as fc
+from oracle import healpix as hp
+from oracle import sht
+from oracle import xi
+from tests import cuda_host as ch
+from tests import host_compile as hc
+
+DRIVER = r"""
+namespace flints {
+int device_sm_count() { return 152; }
+size_t device_smem_optin() { return 232448; }
+}
+static double rd() { char b[64]; if (scanf("%63s", b) != 1) exit(2); return strtod(b, nullptr); }
+int main() {
+    long long nside;
+    int lmax, y, spin, prec, flags, has_bb;
+    while (scanf("%lld %d %d %d %d %d %d", &nside, &lmax, &y, &spin, &prec, &flags, &has_bb) == 7) {
+        std::vector<double> cl(lmax + 1), bb(lmax + 1);
+        for (double &v : cl) v = rd();
+        if (has_bb) for (double &v : bb) v = rd();
+        const long long npix = 12 * nside * nside;
+        const int comp = spin == 0 ? 1 : 2;
+        std::vector<double> map(npix * comp), defl(2 * npix), out(npix * comp), var(npix);
+        std::vector<uint8_t> status(npix);
+        for (double &v : map) v = rd();
+        for (double &v : defl) v = rd();
+        flints_paper_t h = nullptr;
+        int rc = flints_paper_plan(&h, nside, lmax, cl.data(), has_bb ? bb.data() : nullptr, y, spin, prec, flags,
+                                   nullptr);
+        if (rc == 0)
+            rc = flints_paper_lens(h, 0, npix, map.data(), defl.data(), out.data(), var.data(), status.data(), nullptr);
+        printf("%d\n", rc);
+        if (rc != 0) { printf("%s\n", flints_paper_last_error()); continue; }
+        for (long long p = 0; p < npix; ++p) {
+            printf("%d %a %a", (int)status[p], out[p * comp], var[p]);
+            if (comp == 2) printf(" %a", out[p * comp + 1]);
+            printf("\n");
+        }
+        flints_paper_free(h);
+    }
+    return 0;
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def run(tmp_path_factory):
+    if hc.compiler() is None:
+        pytest.skip("no host C++ compiler")
+    exe = ch.build(tmp_path_factory.mktemp("paper"), "paper_host",
+                   ["common.cuh", "lens.cuh", "paper_geom.cuh", "xi_table.cu", "paper.cu"], DRIVER)
+
+    def call(nside, lmax, y, spin, prec, flags, cl, bb, m, defl):
+        head = f"{nside} {lmax} {y} {spin} {prec} {flags} {0 if bb is None else 1} "
+        body = " ".join(x.hex() for x in cl) + ("" if bb is None else " " + " ".join(x.hex() for x in bb))
+        body += " " + " ".join(float(x).hex() for x in np.ravel(m)) + " " + " ".join(float(x).hex() for x in np.ravel(defl))
+        lines = hc.run(exe, head + body + "\n").splitlines()
+        assert lines[0] == "0", lines[:2]
+        rows = [ln.split() for ln in lines[1:]]
+        status = np.array([int(r[0]) for r in rows])
+        out = np.array([float.fromhex(r[1]) for r in rows])
+        if spin:
+            out = out + 1j * np.array([float.fromhex(r[3]) for r in rows])
+        return status, out, np.array([float.fromhex(r[2]) for r in rows])
+
+    return call
+
+
+CASES = [(0, 8, 16, 1), (0, 16, 32, 1), (0, 16, 32, 2), (0, 32, 64, 2), (2, 16, 32, 1), (2, 16, 32, 2)]
+
+
+@pytest.mark.parametrize("spin,nside,lmax,y", CASES, ids=lambda v: str(v))
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_paper_route_matches_the_oracle(spin, nside, lmax, y, prec, run):
+    npix = hp.npix(nside)
+    seed = 100 * nside + 10 * y + spin
+    if spin == 0:
+        cl, bb = wl.cl_tt(lmax, 0.7 * lmax), None
+        m = sht.synth_map(nside, lmax, wl.draw_alm(cl, seed))
+        sigma = float(np.std(m))
+    else:
+        cl = wl.cl_ee(lmax, 0.7 * lmax)
+        bb = 0.3 * cl
+        P = sht.synth_map(nside, lmax, wl.draw_alm(cl, seed), spin=2, blm=wl.draw_alm(bb, seed + 1))
+        m = np.stack([P.real, P.imag], axis=1)
+        sigma = float(np.sqrt(np.mean(np.abs(P) ** 2)))
+    defl = wl.random_deflection(npix, seed + 2, rms=0.5 * np.sqrt(4 * np.pi / npix))
+    t_max, n = fc.paper_grid_rule(cl, nside, y, bb)
+    tab, x0 = xi.spin0_table(cl, t_max, n) if spin == 0 else xi.spin2_tables(cl, bb, t_max, n)[::2]
+    rv, rs2, _, _ = fc.paper_lens(nside, y, m, defl, np.arange(npix), tab, x0, classes=True, spin=spin)
+    status, v, s2 = run(nside, lmax, y, spin, prec, 0, cl, bb, m, defl)
+    tol = 1e-9 if prec == 0 else 1e-6
+    assert np.all(status & (4 | 8) == 0)  # no window or failed points
+    assert np.max(np.abs(v - rv)) <= tol * sigma, np.max(np.abs(v - rv)) / sigma
+    assert np.max(np.abs(s2 - rs2)) <= tol * x0, np.max(np.abs(s2 - rs2)) / x0
+
+
+@pytest.mark.parametrize("nside,lmax,y", [(8, 16, 1), (16, 32, 2)])
+def test_augmented_paper_route_matches_the_oracle(nside, lmax, y, run):
+    npix = hp.npix(nside)
+    cl = wl.cl_ee(lmax, 0.7 * lmax)
+    bb = 0.3 * cl
+    P = sht.synth_map(nside, lmax, wl.draw_alm(cl, 7 + nside), spin=2, blm=wl.draw_alm(bb, 8 + nside))
+    m = np.stack([P.real, P.imag], axis=1)
+    sigma = float(np.sqrt(np.mean(np.abs(P) ** 2)))
+    defl = wl.random_deflection(npix, 9 + nside, rms=0.5 * np.sqrt(4 * np.pi / npix))
+    t_max, n = fc.paper_grid_rule(cl, nside, y, bb)
+    tp, tm, x0 = xi.spin2_tables(cl, bb, t_max, n)
+    rv, rs2, _, _ = fc.paper_lens(nside, y, m, defl, np.arange(npix), tp, x0, classes=True, spin=2, f_minus=tm)
+    status, v, s2 = run(nside, lmax, y, 2, 0, 1, cl, bb, m, defl)  # flags: FLINTS_SPIN2_AUGMENTED
+    assert np.all(status & (4 | 8) == 0)
+    assert np.max(np.abs(v - rv)) <= 1e-9 * sigma and np.max(np.abs(s2 - rs2)) <= 1e-9 * x0
