@@ -46,6 +46,10 @@ static inline cudaError_t cudaMalloc(void **p, size_t n) {
 }
 template <class T> static inline cudaError_t cudaMalloc(T **p, size_t n) { return cudaMalloc((void **)p, n); }
 static inline cudaError_t cudaFree(void *p) { std::free(p); return cudaSuccess; }
+enum { cudaHostAllocDefault = 0 };
+static inline cudaError_t cudaHostAlloc(void **p, size_t n, unsigned) { return cudaMalloc(p, n); }
+static inline cudaError_t cudaFreeHost(void *p) { return cudaFree(p); }
+static inline cudaError_t cudaGetSymbolAddress(void **p, const void *sym) { *p = const_cast<void *>(sym); return cudaSuccess; }
 static inline cudaError_t cudaMemcpyAsync(void *d, const void *s, size_t n, cudaMemcpyKind, cudaStream_t = 0) {
     std::memmove(d, s, n);
     return cudaSuccess;
@@ -97,11 +101,14 @@ struct HostBarrier {
             if (count >= expected) {
                 count = 0;
                 gen.store(g + 1);
+                gen.notify_all();
                 return;
             }
         }
-        if (!leave)
-            while (gen.load() == g) std::this_thread::yield();
+        if (!leave) {
+            for (int spin = 0; spin < 64 && gen.load() == g; ++spin) std::this_thread::yield();
+            while (gen.load() == g) gen.wait(g);  // sleep until the last thread arrives
+        }
     }
 };
 static HostBarrier g_block_bar, g_warp_bar_of[32];
@@ -217,7 +224,7 @@ using std::floor; using std::fabs; using std::fmax; using std::isfinite; using s
 #define __global__
 #define __forceinline__ inline
 #define __shared__ static
-#define __align__(x) alignas(x)
+#define __align__(x) __attribute__((aligned(x)))
 #define __launch_bounds__(...)
 """
 
