@@ -299,41 +299,40 @@ def _oracle(spin, nside, K, cl, bb, m, defl, pix):
 
 
 # (spin, K, precision, warps per block of the plan's launches: 0 = the default, 8)
-@pytest.mark.parametrize("spin,K,prec,wpb", [(0, 16, 0, 0), (0, 48, 1, 0), (2, 32, 0, 0), (2, 24, 1, 2)])
+@pytest.mark.parametrize("spin,K,prec,wpb", [(0, 16, 0, 0), (2, 32, 1, 0), (2, 24, 0, 2)])
 def test_whole_sky_entry_points_match_the_oracle_and_each_other(spin, K, prec, wpb, exe):
     nside, lmax = 8, 16
     npix = hp.npix(nside)
     cl, bb, m, sigma = _sky(spin, nside, lmax, 10 * K + spin)
     defl = wl.random_deflection(npix, 3 + K) * 8
     ref, x0, t_max, n = _oracle(spin, nside, K, cl, bb, m, defl, np.arange(npix))
-    a, b = 100, 100 + 333
+    a, b, c, d = 100, 100 + 333, 500, 500 + 150
     s = Session(exe)
     s.plan(1, nside, cl, bb, spin, K, prec)
     if wpb:
         s.launch(1, wpb, 0, 0)
     s.map(1, nside, np.arange(npix), m)
-    s.full(1, 1, defl)                                   # flints_lens_spin0 / spin2
-    s.lens(1, 0, npix, 1, defl)                          # flints_lens_range, whole sky
-    s.lens(1, a, b - a, 1, defl[a:b])                    # a ragged range
+    s.full(1, 1, defl)                                   # flints_lens_spin0 / spin2, whole sky
+    s.lens(1, a, b - a, 1, defl[a:b])                    # flints_lens_range, a ragged range
     s.stats(1)
     s.noalloc(nside, cl, bb, spin, K, prec, a, b - a, 1, defl[a:b])
-    s.noalloc(nside, cl, bb, spin, K, prec, 0, npix, 1, defl)  # the shared array keeps the last call's contents
-    s.stencil(1, 0, npix, defl)
+    s.noalloc(nside, cl, bb, spin, K, prec, c, d - c, 1, defl[c:d])  # the shared array keeps the last call's contents
+    s.stencil(1, c, d - c, defl[c:d])
     res = s.run()
     plan = res[0]
-    full, rng, part, stats, na1, na2, (sst, idx) = res[-7:]
+    full, part, stats, na1, na2, (sst, idx) = res[-6:]
     assert plan[0] == 0 and plan[1] == t_max and plan[2] == n and abs(plan[3] - x0) <= 1e-13 * x0
     tol = 1e-9 if prec == 0 else 1e-6
-    v_ref = ref.value
-    for st, v, var in (full, rng, na2):
-        assert np.max(np.abs(v - v_ref if spin else v.real - v_ref)) <= tol * sigma
-        assert np.max(np.abs(var - ref.variance)) <= tol * x0
-    assert np.all(rng[0] == 0) and np.all(na2[0] == 0)
+    v_ref = ref.value if spin else ref.value + 0j
+    for (st, v, var), sl in ((full, slice(0, npix)), (part, slice(a, b)), (na2, slice(c, d))):
+        assert np.max(np.abs(v - v_ref[sl])) <= tol * sigma
+        assert np.max(np.abs(var - ref.variance[sl])) <= tol * x0
+    assert np.all(part[0] == 0) and np.all(na1[0] == 0) and np.all(na2[0] == 0)
     # the same per-tile code on the same inputs: identical results
-    assert np.array_equal(full[1], rng[1]) and np.array_equal(rng[1][a:b], part[1])
-    assert np.array_equal(part[1], na1[1]) and np.array_equal(rng[1], na2[1]) and np.array_equal(rng[2], na2[2])
-    assert stats[:2] == [0, npix + npix + (b - a)] and stats[3:] == [0, 0, 0]
-    ref_idx, key = kr.knn(nside, ref.target, K + 1)
+    assert np.array_equal(full[1][a:b], part[1]) and np.array_equal(part[1], na1[1]) and np.array_equal(part[2], na1[2])
+    assert np.array_equal(full[1][c:d], na2[1])
+    assert stats[:2] == [0, npix + (b - a)] and stats[3:] == [0, 0, 0]
+    ref_idx, key = kr.knn(nside, ref.target[c:d], K + 1)
     tie = (key[:, K] - key[:, K - 1]) <= 1e-11 * key[:, K]
     assert np.all(sst == 0) and np.all(np.all(idx == ref_idx[:, :K], axis=1) | tie)
 
@@ -341,7 +340,7 @@ def test_whole_sky_entry_points_match_the_oracle_and_each_other(spin, K, prec, w
 def test_batches_equal_single_calls(exe):
     nside = 16
     npix = hp.npix(nside)
-    specs = [(0, 16, 0, 0, 500), (2, 32, 1, 5, 400), (0, 48, 1, 2000, 300), (2, 24, 0, 100, 0)]
+    specs = [(0, 16, 0, 0, 160), (2, 32, 1, 5, 130), (0, 48, 1, 2000, 96), (2, 24, 0, 100, 0)]
     s = Session(exe)
     maps = {}
     for spin in (0, 2):

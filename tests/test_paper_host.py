@@ -5,7 +5,7 @@ plan's kernels (pixel tables, stencils and classes, the per-class L^-1 in a
 of warp-synchronous code) execute on host threads that run freely between
 barriers (tests/cuda_host.py), so a missing __syncthreads or __syncwarp shows
 as a wrong result.  Results are compared with the oracle's class route (Secs.
-2.3-2.5) on whole skies at Nside 8 to 32, spin 0 and 2, levels y = 1 (9
+2.3-2.5) on whole skies at Nside 8 and 16, spin 0 and 2, levels y = 1 (9
 pixels) and 2 (36 pixels), FP64 and mixed, and the augmented spin-2
 estimator; tolerances as on the GPU (1e-9 FP64, 1e-6 mixed, of sigma_map and
 xi(0))."""
@@ -82,7 +82,7 @@ def run(tmp_path_factory):
     return call
 
 
-CASES = [(0, 8, 16, 1), (0, 16, 32, 1), (0, 16, 32, 2), (0, 32, 64, 2), (2, 16, 32, 1), (2, 16, 32, 2)]
+CASES = [(0, 8, 16, 1), (0, 16, 32, 1), (0, 16, 32, 2), (2, 16, 32, 1), (2, 16, 32, 2)]
 
 
 @pytest.mark.parametrize("spin,nside,lmax,y", CASES, ids=lambda v: str(v))

@@ -130,7 +130,7 @@ def _ranges(N, n):
 @pytest.mark.parametrize("mixed", [0, 1])
 def test_stencils_match_the_oracle(N, K, mixed, run):
     rng = np.random.default_rng(N + K + mixed)
-    n = 160
+    n = 96
     for first in _ranges(N, n):
         # lensing-sized deflections, and some of a pixel or two
         scale = np.where(rng.random(n) < 0.5, wl.DEFLECTION_RMS * 4096 / N, 2.0 / N)
