@@ -14,7 +14,8 @@ the kernels it launches run unchanged on the CPU.
   block's threads; blocks run one at a time); dynamic shared memory is one
   static buffer.
 * Device memory is host memory: cudaMalloc is an aligned allocation, copies
-  and sets are memcpy and memset, streams are synchronous.
+  and sets are memcpy and memset, streams are synchronous; cuFFT's batched
+  one-dimensional transforms are direct sums (small sizes only).
 * Device math not in the C library: sincospi, sinpif (sin/cos of pi x), bit
   casts; the rounding intrinsics and rsqrt(f) come from host_compile.SHIM.
 """
@@ -34,7 +35,8 @@ RUNTIME = r"""
 #include <type_traits>
 #include <math.h>
 typedef int cudaError_t;
-enum { cudaSuccess = 0, cudaErrorInvalidValue = 1, cudaErrorMemoryAllocation = 2, cudaErrorInvalidConfiguration = 9 };
+enum { cudaSuccess = 0, cudaErrorInvalidValue = 1, cudaErrorMemoryAllocation = 2, cudaErrorInvalidConfiguration = 9,
+       cudaErrorUnknown = 999 };
 typedef void *cudaStream_t;
 enum cudaMemcpyKind { cudaMemcpyHostToHost, cudaMemcpyHostToDevice, cudaMemcpyDeviceToHost, cudaMemcpyDeviceToDevice,
                       cudaMemcpyDefault };
@@ -218,7 +220,77 @@ static inline double2 make_double2(double x, double y) { return {x, y}; }
 static inline float2 make_float2(float x, float y) { return {x, y}; }
 static inline float4 make_float4(float x, float y, float z, float w) { return {x, y, z, w}; }
 template <class T> static inline T __ldg(const T *p) { return *p; }
-using std::floor; using std::fabs; using std::fmax; using std::isfinite; using std::atan2;
+using std::floor; using std::fabs; using std::fmax; using std::isfinite; using std::atan2; using std::min; using std::max;
+
+// cuFFT stand-in: one-dimensional batched transforms by direct summation (the
+// sizes of the small skies tested), unnormalised like cuFFT; Z2D takes the
+// n/2 + 1 non-negative frequencies of a Hermitian spectrum
+typedef int cufftHandle;
+typedef int cufftResult;
+enum { CUFFT_SUCCESS = 0, CUFFT_INVALID_PLAN = 1 };
+typedef double2 cufftDoubleComplex;
+typedef double cufftDoubleReal;
+typedef enum { CUFFT_Z2Z = 0x69, CUFFT_Z2D = 0x6c, CUFFT_D2Z = 0x6a } cufftType;
+#define CUFFT_FORWARD -1
+#define CUFFT_INVERSE 1
+struct HostFftPlan {
+    int n = 0, batch = 0;
+    long long idist = 0, odist = 0;
+    cufftType type = CUFFT_Z2Z;
+};
+static std::vector<HostFftPlan> g_fft_plans;
+static inline cufftResult cufftCreate(cufftHandle *h) {
+    g_fft_plans.emplace_back();
+    *h = (int)g_fft_plans.size() - 1;
+    return CUFFT_SUCCESS;
+}
+static inline cufftResult cufftSetAutoAllocation(cufftHandle, int) { return CUFFT_SUCCESS; }
+static inline cufftResult cufftMakePlanMany(cufftHandle h, int rank, int *n, int *, int, int idist, int *, int,
+                                            int odist, cufftType type, int batch, size_t *ws) {
+    if (rank != 1) return CUFFT_INVALID_PLAN;
+    g_fft_plans[h] = HostFftPlan{n[0], batch, idist, odist, type};
+    *ws = 0;
+    return CUFFT_SUCCESS;
+}
+static inline cufftResult cufftGetSize(cufftHandle, size_t *ws) { *ws = 0; return CUFFT_SUCCESS; }
+static inline cufftResult cufftSetWorkArea(cufftHandle, void *) { return CUFFT_SUCCESS; }
+static inline cufftResult cufftSetStream(cufftHandle, cudaStream_t) { return CUFFT_SUCCESS; }
+static inline cufftResult cufftDestroy(cufftHandle) { return CUFFT_SUCCESS; }
+static inline void host_dft(const double2 *in, double2 *out, int n, int sign, bool hermitian_in) {
+    std::vector<double2> x(n), y(n);
+    for (int k = 0; k < n; ++k) {
+        if (!hermitian_in) x[k] = in[k];
+        else if (k <= n / 2) x[k] = in[k];
+        else x[k] = double2{in[n - k].x, -in[n - k].y};
+    }
+    for (int j = 0; j < n; ++j) {
+        long double re = 0, im = 0;
+        for (int k = 0; k < n; ++k) {
+            const long long q = ((long long)j * k) % n;
+            const long double ang = (long double)sign * 2.0L * 3.14159265358979323846264338327950288L * q / n;
+            const long double c = cosl(ang), s = sinl(ang);
+            re += x[k].x * c - x[k].y * s;
+            im += x[k].x * s + x[k].y * c;
+        }
+        y[j] = double2{(double)re, (double)im};
+    }
+    for (int j = 0; j < n; ++j) out[j] = y[j];
+}
+static inline cufftResult cufftExecZ2Z(cufftHandle h, cufftDoubleComplex *in, cufftDoubleComplex *out, int dir) {
+    const HostFftPlan &p = g_fft_plans[h];
+    for (int b = 0; b < p.batch; ++b) host_dft(in + b * p.idist, out + b * p.odist, p.n, dir, false);
+    return CUFFT_SUCCESS;
+}
+static inline cufftResult cufftExecZ2D(cufftHandle h, cufftDoubleComplex *in, cufftDoubleReal *out) {
+    const HostFftPlan &p = g_fft_plans[h];
+    std::vector<double2> y(p.n);
+    for (int b = 0; b < p.batch; ++b) {
+        host_dft(in + b * p.idist, y.data(), p.n, +1, true);
+        for (int j = 0; j < p.n; ++j) out[b * p.odist + j] = y[j].x;
+    }
+    return CUFFT_SUCCESS;
+}
+
 #define __host__
 #define __device__
 #define __global__
@@ -270,9 +342,9 @@ def _launches(src: str) -> str:
 def _split_top(s: str):
     parts, depth, cur = [], 0, ""
     for c in s:
-        if c in "([{<":
+        if c in "([{":
             depth += 1
-        elif c in ")]}>":
+        elif c in ")]}":
             depth -= 1
         if c == "," and depth == 0:
             parts.append(cur)
@@ -287,7 +359,7 @@ def source(name: str) -> str:
     """A CUDA source of the library made host-compilable: local includes and the
     runtime header dropped, launches and dynamic shared memory rewritten."""
     src = open(os.path.join(hc.CSRC, name)).read()
-    src = re.sub(r'^\s*#include\s+["<](cuda_runtime\.h|[a-z_0-9]+\.cuh|flints\.h)[">]\s*$', "", src, flags=re.M)
+    src = re.sub(r'^\s*#include\s+["<](cuda_runtime\.h|cufft\.h|[a-z_0-9]+\.cuh|flints\.h)[">]\s*$', "", src, flags=re.M)
     src = src.replace("#pragma once", "")
     src = re.sub(r"extern __shared__\s+(?:__align__\(\d+\)\s+)?([\w ]+?)\s+(\w+)\[\];",
                  r"\1 *\2 = reinterpret_cast<\1 *>(g_dyn_smem);", src)
