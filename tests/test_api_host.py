@@ -409,3 +409,41 @@ def test_nside_4096_band_and_supersampling(exe):
     tie = (key[:, 32] - key[:, 31]) <= 1e-11 * key[:, 32]
     ok = np.abs(v.real - sref.value) <= 1e-9 * s0
     assert np.all(ok | tie) and np.mean(ok) > 0.5
+
+
+def test_spin1_and_augmented_plans_through_the_single_range_kernel(exe):
+    """Spin-1 plans and augmented spin-2 plans launch the single-range kernel (its tile
+    queue): a deflection field lensed as a spin-1 map and an E/B field with the widely
+    linear estimator, against the oracle."""
+    nside, lmax = 8, 16
+    npix = hp.npix(nside)
+    first, count = 200, 150
+    defl = wl.random_deflection(count, 91) * 8
+    pix = np.arange(first, first + count)
+    # spin 1: the gradient of a potential, spectrum l(l+1) C^phiphi
+    ell = np.arange(lmax + 1.0)
+    cl1 = ell * (ell + 1) * wl.cl_phiphi(lmax)
+    g = sht.synth_map(nside, lmax, wl.draw_alm(wl.cl_phiphi(lmax), 92), gradient=True)
+    t1, n1 = xi.grid_rule(np.abs(cl1), 32, nside)
+    tab1, _, x01 = xi.spin1_tables(cl1, None, t1, n1)
+    ref1 = kr.lens(nside, 32, 1, g, defl, pix, tab1, x01)
+    # augmented spin 2
+    cl2 = wl.cl_ee(lmax, 0.7 * lmax)
+    bb = 0.3 * cl2
+    P = sht.synth_map(nside, lmax, wl.draw_alm(cl2, 93), spin=2, blm=wl.draw_alm(bb, 94))
+    qu = np.stack([P.real, P.imag], 1)
+    t2, n2 = xi.grid_rule(np.abs(cl2) + np.abs(bb), 24, nside)
+    tp, tm, x02 = xi.spin2_tables(cl2, bb, t2, n2)
+    ref2 = kr.lens(nside, 24, 2, qu, defl, pix, tp, x02, f_minus=tm)
+    s = Session(exe)
+    s.plan(1, nside, cl1, None, 1, 32, 0)
+    s.map(1, nside, np.arange(npix), g)
+    s.lens(1, first, count, 1, defl)
+    s.plan(2, nside, cl2, bb, 2, 24, 1, flags=1)  # FLINTS_SPIN2_AUGMENTED, mixed
+    s.map(2, nside, np.arange(npix), qu)
+    s.lens(2, first, count, 2, defl)
+    res = s.run()
+    for (st, v, var), ref, x0, m, tol in ((res[2], ref1, x01, g, 1e-9), (res[5], ref2, x02, qu, 1e-6)):
+        sigma = float(np.sqrt(np.mean(np.sum(m ** 2, 1))))
+        assert np.all(st == 0)
+        assert np.max(np.abs(v - ref.value)) <= tol * sigma and np.max(np.abs(var - ref.variance)) <= tol * x0
