@@ -447,3 +447,65 @@ def test_spin1_and_augmented_plans_through_the_single_range_kernel(exe):
         sigma = float(np.sqrt(np.mean(np.sum(m ** 2, 1))))
         assert np.all(st == 0)
         assert np.max(np.abs(v - ref.value)) <= tol * sigma and np.max(np.abs(var - ref.variance)) <= tol * x0
+
+
+def test_indefinite_covariances_take_the_nugget_steps(exe):
+    """Sec. 2.4's nugget on covariances that are not positive definite (never met on the
+    workloads, whose spectra are positive): a spectrum with a small negative multipole
+    makes S + 1.49e-8 I indefinite on some stencils.  The kernel doubles the nugget
+    until the factor exists (FLINTS_ST_NUGGET), at most 8 times (then FLINTS_ST_FAILED
+    with NaN outputs), and the value is the estimate with that nugget; the mixed kernel
+    re-solves those points on its FP64 path (FLINTS_ST_FALLBACK).  (The oracle's rule,
+    n = -lambda_min + 1.49e-8, is a different reading of the same passage; here the
+    oracle is run with the kernel's nugget.)"""
+    nside, lmax, K = 8, 16, 16
+    npix = hp.npix(nside)
+    cl = wl.cl_tt(lmax, 11.0)
+    cl[lmax] = -0.0043 * cl[2]
+    m = sht.synth_map(nside, lmax, wl.draw_alm(np.abs(cl), 95))
+    sigma = float(np.std(m))
+    defl = wl.random_deflection(npix, 5) * 8
+    pix = np.arange(npix)
+    t_max, n = xi.grid_rule(np.abs(cl), K, nside)
+    tab, x0 = xi.spin0_table(cl, t_max, n)
+    tv = kr.displace(nside, pix, defl)
+    idx, _ = kr.knn(nside, tv, K)
+    X = hp.pix2vec(nside, idx)
+    S = tab(kr._chord2(X[:, :, None, :], X[:, None, :, :]).reshape(-1)).reshape(npix, K, K)
+    S[:, np.arange(K), np.arange(K)] = 1.0
+    eps = kr.EPS_NUGGET
+    # the first nugget eps 2^k (k = 0..8) whose Cholesky exists, as both sides factor in FP64
+    first_ok = np.full(npix, -1)
+    for k in range(8, -1, -1):
+        _, ok = kr.cholesky_batched(S + eps * 2.0 ** k * np.eye(K))
+        first_ok = np.where(ok, k, first_ok)
+    s = Session(exe)
+    s.plan(1, nside, cl, None, 0, K, 0)
+    s.plan(2, nside, cl, None, 0, K, 1)
+    s.map(1, nside, pix, m)
+    s.lens(1, 0, npix, 1, defl)
+    s.lens(2, 0, npix, 1, defl)
+    s.stats(1)
+    res = s.run()
+    (st64, v64, var64), (stmx, vmx, varmx), stats = res[3], res[4], res[5]
+    nug, failed = (st64 & 1) != 0, (st64 & 8) != 0
+    assert np.array_equal(nug, first_ok != 0) and np.array_equal(failed, first_ok < 0)
+    assert 0.05 < np.mean(nug) and np.any(failed)  # the case exercises both outcomes
+    assert np.all(np.isnan(v64[failed])) and np.all(np.isfinite(v64[~failed]))
+    assert stats[2] == np.sum(nug) and stats[5] == np.sum(failed)
+    # values: the oracle's estimate with the nugget the kernel settled on.  Near the edge
+    # of positive definiteness the weights are large (values of 100 sigma and more) and
+    # rounding is amplified alike on both sides: the bound is relative to the value; a
+    # wrong nugget would move it by a large fraction of itself
+    for k in range(0, 9):
+        rows = np.nonzero(first_ok == k)[0]
+        if rows.size == 0:
+            continue
+        v, s2, _ = kr.estimate(nside, 0, m, tv[rows], idx[rows], tab, x0, eps=eps * 2.0 ** k)
+        assert np.all(np.abs(v64[rows].real - v) <= 1e-6 * (sigma + np.abs(v))), k
+        assert np.all(np.abs(var64[rows] - s2) <= 1e-6 * (x0 + np.abs(s2))), k
+    # the mixed kernel: the indefinite points go to its FP64 path and end the same way
+    assert np.all(((stmx & 2) != 0)[first_ok != 0])
+    assert np.array_equal((stmx & (1 | 8)), (st64 & (1 | 8)))
+    ok = ~failed
+    assert np.all(np.abs(vmx[ok] - v64[ok]) <= 1e-6 * (sigma + np.abs(v64[ok])))
