@@ -24,11 +24,14 @@ DRIVER = r"""
 using namespace flints;
 static double rd() { char b[64]; if (scanf("%63s", b) != 1) exit(2); return strtod(b, nullptr); }
 
+static double g_r2_scale = 1.0;  // test knob: shrink the search disc to reach its window check
+
 template <int K, int MIXED> static void stencil(long long N, long long first, int count) {
     std::vector<double> defl(2 * count);
     for (double &v : defl) v = rd();
     const double cl[3] = {0.0, 0.0, 1.0};
-    const TableGrid tg = table_grid(N, K, 2, cl, nullptr);  // the plan's search disc
+    TableGrid tg = table_grid(N, K, 2, cl, nullptr);  // the plan's search disc
+    tg.r2 *= g_r2_scale;
     std::vector<int64_t> st((size_t)count * K, -7);
     std::vector<uint8_t> status(count, 255);
     LensArgs a{};
@@ -64,7 +67,7 @@ template <int K> static void dispatch(int mixed, long long N, long long first, i
 int main() {
     long long N, first;
     int K, mixed, count;
-    while (scanf("%lld %d %d %lld %d", &N, &K, &mixed, &first, &count) == 5) {
+    while (scanf("%lld %d %d %lld %d %lf", &N, &K, &mixed, &first, &count, &g_r2_scale) == 6) {
         switch (K) {
             case 16: dispatch<16>(mixed, N, first, count); break;
             case 24: dispatch<24>(mixed, N, first, count); break;
@@ -97,8 +100,8 @@ def run(tmp_path_factory):
             + "\n}\n" + DRIVER)
     exe = hc.build(tmp_path_factory.mktemp("stencil"), "stencil_host", text, warp="threads")
 
-    def call(N, K, mixed, first, defl):
-        line = f"{N} {K} {mixed} {first} {len(defl)} " + " ".join(float(x).hex() for x in np.ravel(defl))
+    def call(N, K, mixed, first, defl, r2_scale=1.0):
+        line = f"{N} {K} {mixed} {first} {len(defl)} {r2_scale!r} " + " ".join(float(x).hex() for x in np.ravel(defl))
         rows = [ln.split() for ln in hc.run(exe, line + "\n").splitlines()]
         return np.array([int(r[0]) for r in rows]), np.array([[int(t) for t in r[1:]] for r in rows])
 
@@ -144,3 +147,24 @@ def test_targets_at_pixel_centres_keep_their_pixel_first(run):
         status, idx = run(16384, 32, mixed, 1_600_000_000, np.zeros((40, 2)))
         assert np.all(status == 0)
         assert np.array_equal(idx[:, 0], np.arange(1_600_000_000, 1_600_000_040))
+
+
+def test_stencils_outside_a_shrunken_disc_are_flagged(run):
+    """The window check (FLINTS_ST_WINDOW | FLINTS_ST_FAILED when the K-th neighbour lies
+    outside the search disc), never reached with the plan's disc, on a disc shrunk to 0.6
+    of its area: flagged exactly where the oracle's K-th squared chord exceeds it."""
+    N, K = 4096, 32
+    rng = np.random.default_rng(3)
+    first, n = 50_000_000, 192
+    defl = rng.normal(size=(n, 2)) * (2.0 / N)
+    r = 1.25 * np.sqrt(K / 3.0) / N
+    for mixed in (0, 1):
+        status, idx = run(N, K, mixed, first, defl, 0.6)
+        tv = kr.displace(N, np.arange(first, first + n), defl)
+        _, key = kr.knn(N, tv, K)
+        outside = key[:, K - 1] > 0.6 * r * r
+        assert 0 < np.sum(outside) < n  # both outcomes occur
+        near = np.abs(key[:, K - 1] / (0.6 * r * r) - 1) < 1e-6  # too close to call
+        flagged = status == (4 | 8)
+        assert np.array_equal(flagged[~near], outside[~near])
+        assert np.all(status[~flagged] == 0) and np.all(idx[flagged] == -1)
