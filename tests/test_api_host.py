@@ -509,3 +509,32 @@ def test_indefinite_covariances_take_the_nugget_steps(exe):
     assert np.array_equal((stmx & (1 | 8)), (st64 & (1 | 8)))
     ok = ~failed
     assert np.all(np.abs(vmx[ok] - v64[ok]) <= 1e-6 * (sigma + np.abs(v64[ok])))
+
+
+def test_targets_displaced_onto_a_pole(exe):
+    """Targets displaced onto the north pole (to rounding), where the spin-2 frame at
+    the displaced point is undefined: the kernel flags FLINTS_ST_POLE there and takes
+    the frame of phi = 0, the oracle the frame of its displaced vector's rounding-level
+    phi.  Transported back to the frame at the target pixel (FLINTS_ROTATE_TO_TARGET)
+    the lensed value does not depend on that choice, so the two agree; K = 24 is the
+    three northernmost rings at Nside 8, a stencil without ties at the pole.  Every
+    other target lands 1e-3 rad from the pole instead and is not flagged."""
+    nside, lmax, K = 8, 16, 24
+    npix = hp.npix(nside)
+    cl, bb, m, sigma = _sky(2, nside, lmax, 97)
+    pix = np.arange(0, 12)  # the two northernmost rings
+    z, s, _ = hp.pix2ang(nside, pix)
+    defl = np.stack([-np.arctan2(s, z), np.zeros(pix.size)], 1)  # d_theta = -theta: onto the pole
+    defl[1::2, 1] = 1e-3
+    weight = np.abs(cl)
+    t_max, n = xi.grid_rule(weight, K, nside)
+    tab, x0 = xi.spin2_tables(cl, bb, t_max, n)[::2]
+    ref = kr.lens(nside, K, 2, m, defl, pix, tab, x0, rotate=True)
+    s_ = Session(exe)
+    s_.plan(1, nside, cl, bb, 2, K, 0, 2)  # flags: FLINTS_ROTATE_TO_TARGET
+    s_.map(1, nside, np.arange(npix), m)
+    s_.lens(1, 0, pix.size, 1, defl)
+    st, v, var = s_.run()[2]
+    assert np.array_equal(st, np.where(np.arange(pix.size) % 2 == 0, 16, 0))
+    assert np.max(np.abs(v - ref.value)) <= 1e-9 * sigma, np.max(np.abs(v - ref.value)) / sigma
+    assert np.max(np.abs(var - ref.variance)) <= 1e-9 * x0
