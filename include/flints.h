@@ -106,7 +106,9 @@ enum {
 };
 
 typedef struct {
-    int64_t points;      /* points processed since the plan was created or stats reset */
+    int64_t points;      /* points launched since the plan was created or stats reset (host
+                          * count: a batch counts its jobs when they are staged, once; a
+                          * refused call counts none) */
     int64_t nugget;      /* points with FLINTS_ST_NUGGET */
     int64_t fallback;    /* points with FLINTS_ST_FALLBACK */
     int64_t window;      /* points with FLINTS_ST_WINDOW */
@@ -179,8 +181,8 @@ int flints_supersample(flints_plan_t plan, int64_t nside_out, int64_t first, int
 
 /* Stencil of the range [first, first+count): the K nearest RING pixels to
  * each displaced direction, sorted by (squared chord, pixel index), written
- * to idx device int64 [count][K] (the neighbour search of the lens kernels,
- * exposed for verification).  status as for flints_lens_range. */
+ * to idx device int64 [count][K], 8-byte aligned (the neighbour search of the
+ * lens kernels, exposed for verification).  status as for flints_lens_range. */
 int flints_stencil(flints_plan_t plan, int64_t first, int64_t count,
                    const double *defl, int64_t *idx, uint8_t *status,
                    void *stream);

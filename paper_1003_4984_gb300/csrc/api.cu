@@ -312,9 +312,10 @@ static int run(flints_plan_t p, int64_t nside_tgt, int64_t first, int64_t count,
     if (!stencil && (!map || !out)) return fail(FLINTS_EINVAL, "map and out must not be NULL");
     // defl and two-component maps/outputs are read and written as 16-byte pairs
     const uintptr_t need = p->spin == 0 ? 7u : 15u;
-    if (((uintptr_t)defl & 15u) || (((uintptr_t)map | (uintptr_t)out) & need) || ((uintptr_t)var & 7u))
-        return fail(FLINTS_EINVAL, "defl (and spin 1/2 map and out) must be 16-byte aligned, spin 0 map, out and var "
-                                   "8-byte aligned");
+    if (((uintptr_t)defl & 15u) || (((uintptr_t)map | (uintptr_t)out) & need) ||
+        (((uintptr_t)var | (uintptr_t)stencil) & 7u))
+        return fail(FLINTS_EINVAL, "defl (and spin 1/2 map and out) must be 16-byte aligned, spin 0 map, out, var and "
+                                   "idx 8-byte aligned");
     LensArgs a{};
     a.nside = p->nside;
     a.first = first;
@@ -558,8 +559,9 @@ int flints_batch_stage(flints_batch_t b, const flints_job *jobs, int n, int tile
         bj.precision = p->precision;
         bj.ntiles = (j.count + tp - 1) / tp;
         v.push_back(bj);
-        p->points += j.count;
     }
+    // every job is valid: count its points (a refused stage counts none)
+    for (int i = 0; i < n; ++i) jobs[i].plan->points += jobs[i].count;
     // classes (precision, spin, K), each in decreasing estimated cost
     // (longest jobs start first)
     auto cls_of = [](const BatchJob &x) { return 8 * x.precision + (x.spin == 2 ? 4 : 0) + batch_k_index(x.K); };

@@ -177,6 +177,74 @@ int main() {
                                                b.status.data(), nullptr);
             printf("%d\n", rc);
             print_rows(b, count, comp);
+        } else if (o == "reject") {  // plans of spin 0 and 2 (FP64, K = 16) and spin 1: calls refused before any launch
+            flints_plan_t p0 = g_plans[rl()], p2 = g_plans[rl()], p1 = g_plans[rl()];
+            flints_plan_info i;
+            flints_get_info(p0, &i);
+            const long long npix = 12 * i.nside * i.nside;
+            static double buf[4096] __attribute__((aligned(64)));
+            for (double &v : buf) v = std::nan("");
+            static uint8_t st[256];
+            std::memset(st, 255, sizeof st);
+            static int64_t idx[64 * 16];
+            std::fill(idx, idx + 64 * 16, -9);
+            double *m = buf, *d = buf + 2048, *out = buf + 3072, *var = buf + 3584;
+            auto shift = [](const void *q, int by) { return (void *)((const char *)q + by); };
+            auto rep = [](int rc, const char *msg) { printf("%d|%s\n", rc, msg); };
+            const char *(*le)() = flints_last_error;
+            rep(flints_lens_range(nullptr, 0, 4, m, d, out, var, st, nullptr), le());
+            rep(flints_lens_range(p0, -1, 4, m, d, out, var, st, nullptr), le());
+            rep(flints_lens_range(p0, npix - 2, 4, m, d, out, var, st, nullptr), le());
+            rep(flints_lens_range(p0, 0, 4, m, nullptr, out, var, st, nullptr), le());
+            rep(flints_lens_range(p0, 0, 4, nullptr, d, out, var, st, nullptr), le());
+            rep(flints_lens_range(p0, 0, 4, m, (double *)shift(d, 8), out, var, st, nullptr), le());
+            rep(flints_lens_range(p2, 0, 4, (double *)shift(m, 8), d, out, var, st, nullptr), le());
+            rep(flints_lens_range(p2, 0, 4, m, d, (double *)shift(out, 8), var, st, nullptr), le());
+            rep(flints_lens_range(p0, 0, 4, m, d, out, (double *)shift(var, 4), st, nullptr), le());
+            rep(flints_stencil(p0, 0, 4, d, nullptr, st, nullptr), le());
+            rep(flints_stencil(p0, 0, 4, d, (int64_t *)shift(idx, 4), st, nullptr), le());
+            rep(flints_lens_spin0(p2, m, d, out, var, nullptr), le());
+            rep(flints_lens_spin2(p0, m, d, out, var, nullptr), le());
+            rep(flints_supersample(p0, 0, 0, 4, m, out, var, st, nullptr), le());
+            rep(flints_supersample(p0, 2 * i.nside, 48 * i.nside * i.nside - 1, 2, m, out, var, st, nullptr), le());
+            flints_launch_cfg bad[3] = {{9, 0, 0}, {0, 33, 0}, {0, 0, 17}};
+            for (const auto &c : bad) rep(flints_plan_set_launch(p0, &c), le());
+            double f[4], g[4];
+            rep(flints_get_table(p0, 1, f, g, nullptr), le());
+            rep(flints_get_stats(p0, nullptr, nullptr), le());
+            flints_batch_t b = nullptr;
+            rep(flints_batch_create(&b, 0), le());
+            rep(flints_batch_create(&b, 2), le());
+            flints_job ok{p0, 0, 4, m, d, out, var, st};
+            flints_job two[2] = {ok, ok};
+            rep(flints_batch_stage(b, two, 3, 0), le());
+            rep(flints_batch_stage(b, two, 2, 17), le());
+            flints_stats s0{}, s1{};
+            flints_get_stats(p0, &s0, nullptr);
+            two[1].plan = nullptr;
+            rep(flints_batch_stage(b, two, 2, 0), le());
+            two[1] = ok;
+            two[1].plan = p1;
+            rep(flints_batch_stage(b, two, 2, 0), le());
+            two[1] = ok;
+            two[1].first = npix - 1;
+            rep(flints_batch_stage(b, two, 2, 0), le());
+            two[1] = ok;
+            two[1].map = nullptr;
+            rep(flints_batch_stage(b, two, 2, 0), le());
+            two[1] = ok;
+            two[1].var = (double *)shift(var, 4);
+            rep(flints_batch_stage(b, two, 2, 0), le());
+            flints_get_stats(p0, &s1, nullptr);
+            printf("points %lld\n", (long long)(s1.points - s0.points));  // refused stages count no points
+            flints_launch_cfg wide{9, 0, 0};
+            rep(flints_batch_launch(b, &wide, nullptr), le());
+            rep(flints_lens_batch(two, -1, nullptr), le());
+            flints_batch_free(b);
+            bool untouched = std::all_of(buf + 3072, buf + 4096, [](double v) { return std::isnan(v); }) &&
+                             std::all_of(st, st + 256, [](uint8_t v) { return v == 255; }) &&
+                             std::all_of(idx, idx + 64 * 16, [](int64_t v) { return v == -9; });
+            printf("untouched %d\n", untouched ? 1 : 0);
         } else return 3;
         printf("end\n");
         fflush(stdout);
@@ -244,6 +312,10 @@ class Session:
                           + ("" if bb is None else " " + self._h(bb)) + f" {first} {count} {mid} " + self._h(defl))
         self.kinds.append("rows")
 
+    def reject(self, p0, p2, p1):
+        self.lines.append(f"reject {p0} {p2} {p1}")
+        self.kinds.append("reject")
+
     def run(self):
         out = hc.run(self.exe, "\n".join(self.lines) + "\n").split("end\n")
         res = []
@@ -251,6 +323,8 @@ class Session:
             rows = [ln.split() for ln in block.strip().splitlines()]
             if kind in ("plan", "map"):
                 res.append([float.fromhex(t) if "x" in t else int(t) for t in rows[0]])
+            elif kind == "reject":
+                res.append(block.strip().splitlines())
             elif kind == "stats":
                 res.append([int(t) for t in rows[0]])
             elif kind == "stencil":
@@ -538,3 +612,36 @@ def test_targets_displaced_onto_a_pole(exe):
     assert np.array_equal(st, np.where(np.arange(pix.size) % 2 == 0, 16, 0))
     assert np.max(np.abs(v - ref.value)) <= 1e-9 * sigma, np.max(np.abs(v - ref.value)) / sigma
     assert np.max(np.abs(var - ref.variance)) <= 1e-9 * x0
+
+
+def test_invalid_calls_are_refused_before_any_launch(exe):
+    """Every argument check of the K-nearest C API (null and out-of-range arguments,
+    misaligned buffers, a plan of the wrong spin, launch shapes, batch jobs) returns
+    FLINTS_EINVAL with a message naming the fault, writes no output and, for a batch
+    stage refused at a later job, counts no points for the earlier ones."""
+    nside, lmax = 8, 16
+    s_ = Session(exe)
+    s_.plan(1, nside, wl.cl_tt(lmax, 12.0), None, 0, 16, 0)
+    s_.plan(2, nside, wl.cl_ee(lmax, 12.0), np.zeros(lmax + 1), 2, 16, 0)
+    s_.plan(3, nside, wl.cl_phiphi(lmax), None, 1, 16, 0)
+    s_.reject(1, 2, 3)
+    res = s_.run()
+    assert [r[0] for r in res[:3]] == [0, 0, 0]
+    lines = res[3]
+    assert lines[29] == "points 0", lines[29]  # the refused stages counted no points
+    calls, tail = lines[:29] + lines[30:-1], lines[-1:]
+    expect = ["plan is NULL", "target range", "target range", "defl is NULL", "map and out must not be NULL",
+              "16-byte aligned", "16-byte aligned", "16-byte aligned", "8-byte aligned", "idx is NULL",
+              "8-byte aligned", "called with a spin-2 plan", "called with a plan of spin 0", "nside_out",
+              "target range", "warps_per_block 0..8", "warps_per_block 0..8", "warps_per_block 0..8",
+              "bad table index", "NULL argument", "bad arguments", None, "capacity 2", "tile_points 0..16",
+              "job 1: plan is NULL", "job 1: spin-1 and augmented", "job 1: target range outside", "job 1: NULL data",
+              "job 1: misaligned", "warps_per_block 1..8", "bad job list"]
+    assert len(calls) == len(expect), calls
+    for line, msg in zip(calls, expect):
+        rc, text = line.split("|", 1)
+        if msg is None:
+            assert rc == "0", line
+        else:
+            assert rc == "1" and msg in text, (line, msg)
+    assert tail == ["untouched 1"], tail
