@@ -381,7 +381,8 @@ void flints_free(flints_plan_t plan);
  *   beyond the table domain, FLINTS_ST_FAILED with NaN outputs when no factor
  *   was found).  Asynchronous on `stream`.
  * flints_paper_supersample: values at the centres of pixels first ..
- *   first+count-1 of the grid nside_out (Sec. 2.6); otherwise as above.
+ *   first+count-1 of the grid nside_out (1..16384; Sec. 2.6); otherwise as
+ *   above.
  * flints_paper_get_info: plan sizes and counters (synchronises `stream`).
  * flints_paper_tables: copies the stencil table (members DEVICE [12 Nside_c^2]
  *   [K] int32 RING indices at Nside, -1 past the member count), the class of

@@ -2205,6 +2205,8 @@ int flints_paper_get_info(flints_paper_t p, flints_paper_info *info, void *strea
 
 int flints_paper_tables(flints_paper_t p, int32_t *members, int32_t *slot, double *linv, void *stream) {
     if (!p) return pfail(FLINTS_EINVAL, "plan is NULL");
+    if (linv && !p->d_linv)  // refused before any copy is queued
+        return pfail(FLINTS_EINVAL, "flints_paper_tables: mixed plans keep only double-float L^-1 blocks");
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t npc = 12 * p->nside_c * p->nside_c;
     cudaError_t e = cudaSuccess;
@@ -2212,8 +2214,6 @@ int flints_paper_tables(flints_paper_t p, int32_t *members, int32_t *slot, doubl
         e = cudaMemcpyAsync(members, p->d_members, (size_t)npc * p->K * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess && slot)
         e = cudaMemcpyAsync(slot, p->d_slot, (size_t)npc * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
-    if (linv && !p->d_linv)
-        return pfail(FLINTS_EINVAL, "flints_paper_tables: mixed plans keep only double-float L^-1 blocks");
     if (e == cudaSuccess && linv)
         e = cudaMemcpyAsync(linv, p->d_linv,
                             (size_t)p->nslot *

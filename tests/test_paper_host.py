@@ -27,10 +27,64 @@ int device_sm_count() { return 152; }
 size_t device_smem_optin() { return 232448; }
 }
 static double rd() { char b[64]; if (scanf("%63s", b) != 1) exit(2); return strtod(b, nullptr); }
+// Every argument check of the paper API on plans of spin 0 (FP64) and spin 2 (mixed): each
+// call is refused before any launch or copy; prints "rc|message" per call, then whether the
+// output buffers are untouched.
+static void reject(long long nside, int lmax) {
+    std::vector<double> cl(lmax + 1);
+    for (double &v : cl) v = rd();
+    flints_paper_t p0 = nullptr, p2 = nullptr;
+    if (flints_paper_plan(&p0, nside, lmax, cl.data(), nullptr, 1, 0, 0, 0, nullptr) ||
+        flints_paper_plan(&p2, nside, lmax, cl.data(), nullptr, 1, 2, 1, 0, nullptr)) {
+        printf("plan failed: %s\n", flints_paper_last_error());
+        return;
+    }
+    const long long npix = 12 * nside * nside;
+    static double buf[4096] __attribute__((aligned(64)));
+    for (double &v : buf) v = std::nan("");
+    static uint8_t st[256];
+    std::memset(st, 255, sizeof st);
+    static int32_t mem[1 << 16];
+    std::fill(mem, mem + (1 << 16), -7);
+    double *m = buf, *d = buf + 2048, *out = buf + 3072, *var = buf + 3584;
+    auto shift = [](const void *q, int by) { return (double *)((const char *)q + by); };
+    auto rep = [](int rc) { printf("%d|%s\n", rc, flints_paper_last_error()); };
+    flints_paper_info info{};
+    rep(flints_paper_lens(nullptr, 0, 4, m, d, out, var, st, nullptr));
+    rep(flints_paper_lens(p0, -1, 4, m, d, out, var, st, nullptr));
+    rep(flints_paper_lens(p0, npix - 2, 4, m, d, out, var, st, nullptr));
+    rep(flints_paper_lens(p0, 0, 4, nullptr, d, out, var, st, nullptr));
+    rep(flints_paper_lens(p0, 0, 4, m, nullptr, out, var, st, nullptr));
+    rep(flints_paper_lens(p0, 0, 4, m, shift(d, 8), out, var, st, nullptr));
+    rep(flints_paper_lens(p2, 0, 4, shift(m, 8), d, out, var, st, nullptr));
+    rep(flints_paper_lens(p2, 0, 4, m, d, shift(out, 8), var, st, nullptr));
+    rep(flints_paper_lens(p0, 0, 4, m, d, out, shift(var, 4), st, nullptr));
+    rep(flints_paper_supersample(p0, 0, 0, 4, m, out, var, st, nullptr));
+    rep(flints_paper_supersample(p0, 16385, 0, 4, m, out, var, st, nullptr));
+    rep(flints_paper_supersample(p0, 2 * nside, 4 * npix - 1, 2, m, out, var, st, nullptr));
+    rep(flints_paper_get_info(p0, nullptr, nullptr));
+    rep(flints_paper_tables(nullptr, mem, nullptr, nullptr, nullptr));
+    rep(flints_paper_tables(p2, mem, mem + (1 << 15), buf + 3072, nullptr));
+    const bool untouched = std::all_of(buf + 3072, buf + 4096, [](double v) { return std::isnan(v); }) &&
+                           std::all_of(st, st + 256, [](uint8_t v) { return v == 255; }) &&
+                           std::all_of(mem, mem + (1 << 16), [](int32_t v) { return v == -7; });
+    flints_paper_get_info(p0, &info, nullptr);
+    printf("untouched %d points %lld\n", untouched ? 1 : 0, (long long)info.points);
+    flints_paper_free(p0);
+    flints_paper_free(p2);
+}
+
 int main() {
     long long nside;
     int lmax, y, spin, prec, flags, has_bb;
-    while (scanf("%lld %d %d %d %d %d %d", &nside, &lmax, &y, &spin, &prec, &flags, &has_bb) == 7) {
+    char op[16];
+    while (scanf("%15s", op) == 1) {
+        if (std::string(op) == "reject") {
+            if (scanf("%lld %d", &nside, &lmax) != 2) return 2;
+            reject(nside, lmax);
+            continue;
+        }
+        if (scanf("%lld %d %d %d %d %d %d", &nside, &lmax, &y, &spin, &prec, &flags, &has_bb) != 7) return 2;
         std::vector<double> cl(lmax + 1), bb(lmax + 1);
         for (double &v : cl) v = rd();
         if (has_bb) for (double &v : bb) v = rd();
@@ -67,7 +121,7 @@ def run(tmp_path_factory):
                    ["common.cuh", "lens.cuh", "paper_geom.cuh", "xi_table.cu", "paper.cu"], DRIVER)
 
     def call(nside, lmax, y, spin, prec, flags, cl, bb, m, defl):
-        head = f"{nside} {lmax} {y} {spin} {prec} {flags} {0 if bb is None else 1} "
+        head = f"lens {nside} {lmax} {y} {spin} {prec} {flags} {0 if bb is None else 1} "
         body = " ".join(x.hex() for x in cl) + ("" if bb is None else " " + " ".join(x.hex() for x in bb))
         body += " " + " ".join(float(x).hex() for x in np.ravel(m)) + " " + " ".join(float(x).hex() for x in np.ravel(defl))
         lines = hc.run(exe, head + body + "\n").splitlines()
@@ -79,6 +133,7 @@ def run(tmp_path_factory):
             out = out + 1j * np.array([float.fromhex(r[3]) for r in rows])
         return status, out, np.array([float.fromhex(r[2]) for r in rows])
 
+    call.exe = exe
     return call
 
 
@@ -126,3 +181,21 @@ def test_augmented_paper_route_matches_the_oracle(nside, lmax, y, run):
     status, v, s2 = run(nside, lmax, y, 2, 0, 1, cl, bb, m, defl)  # flags: FLINTS_SPIN2_AUGMENTED
     assert np.all(status & (4 | 8) == 0)
     assert np.max(np.abs(v - rv)) <= 1e-9 * sigma and np.max(np.abs(s2 - rs2)) <= 1e-9 * x0
+
+
+def test_invalid_calls_are_refused_before_any_launch(run):
+    """Every argument check of the paper API (null and out-of-range arguments,
+    misaligned buffers, supersampling grids, the L^-1 copy a mixed plan cannot
+    give) returns FLINTS_EINVAL with a message naming the fault, before any
+    launch or copy: the output buffers stay untouched and no point is counted."""
+    cl = wl.cl_tt(16, 12.0)
+    lines = hc.run(run.exe, "reject 8 16 " + " ".join(x.hex() for x in cl) + "\n").splitlines()
+    expect = ["plan is NULL", "target range", "target range", "map and out must not be NULL", "defl is NULL",
+              "16-byte aligned", "16-byte aligned", "16-byte aligned", "8-byte", "nside_out must be positive",
+              "nside_out 16385 outside", "target range", "must not be NULL", "plan is NULL",
+              "mixed plans keep only double-float"]
+    assert len(lines) == len(expect) + 1, lines
+    for line, msg in zip(lines, expect):
+        rc, text = line.split("|", 1)
+        assert rc == "1" and msg in text, (line, msg)
+    assert lines[-1] == "untouched 1 points 0", lines[-1]

@@ -18,10 +18,42 @@ from tests import host_compile as hc
 
 DRIVER = r"""
 static double rd() { char b[64]; if (scanf("%63s", b) != 1) exit(2); return strtod(b, nullptr); }
+// Every argument check of the synthesis API; prints "rc|message" per refused call, then
+// whether the output map is untouched.
+static void reject() {
+    auto rep = [](int rc) { printf("%d|%s\n", rc, flints_synth_last_error()); };
+    flints_synth_t h = nullptr;
+    rep(flints_synth_plan(nullptr, 8, 16, 0, 0, nullptr));
+    rep(flints_synth_plan(&h, 0, 16, 0, 0, nullptr));
+    rep(flints_synth_plan(&h, 8193, 16, 0, 0, nullptr));
+    rep(flints_synth_plan(&h, 8, 16, 3, 0, nullptr));
+    rep(flints_synth_plan(&h, 8, 1, 2, 0, nullptr));
+    rep(flints_synth_plan(&h, 8, 16, 0, 2, nullptr));
+    if (flints_synth_plan(&h, 8, 16, 2, 0, nullptr)) { printf("plan failed\n"); return; }
+    static double buf[4096] __attribute__((aligned(64)));
+    for (double &v : buf) v = std::nan("");
+    static double map[2 * 768] __attribute__((aligned(64)));
+    for (double &v : map) v = std::nan("");
+    rep(flints_synthesize(nullptr, buf, nullptr, map, nullptr));
+    rep(flints_synthesize(h, nullptr, nullptr, map, nullptr));
+    rep(flints_synthesize(h, buf, nullptr, nullptr, nullptr));
+    rep(flints_synthesize(h, buf + 1, nullptr, map, nullptr));
+    rep(flints_synthesize(h, buf, buf + 1, map, nullptr));
+    rep(flints_synthesize(h, buf, nullptr, map + 1, nullptr));
+    printf("untouched %d\n", std::all_of(map, map + 2 * 768, [](double v) { return std::isnan(v); }) ? 1 : 0);
+    flints_synth_free(h);
+}
+
 int main() {
     long long nside;
     int lmax, spin, prec, has_b;
-    while (scanf("%lld %d %d %d %d", &nside, &lmax, &spin, &prec, &has_b) == 5) {
+    char op[16];
+    while (scanf("%15s", op) == 1) {
+        if (std::string(op) == "reject") {
+            reject();
+            continue;
+        }
+        if (scanf("%lld %d %d %d %d", &nside, &lmax, &spin, &prec, &has_b) != 5) return 2;
         const size_t na = (size_t)(lmax + 1) * (lmax + 1);
         std::vector<double> alm(2 * na), blm(2 * na, 0.0);
         for (double &v : alm) v = rd();
@@ -51,13 +83,14 @@ def run(tmp_path_factory):
         def flat(a):
             return " ".join(float(x).hex() for x in np.stack([a.real, a.imag], -1).ravel())
 
-        line = f"{nside} {lmax} {spin} {prec} {0 if blm is None else 1} " + flat(alm) + (
+        line = f"synth {nside} {lmax} {spin} {prec} {0 if blm is None else 1} " + flat(alm) + (
             "" if blm is None else " " + flat(blm))
         lines = hc.run(exe, line + "\n").splitlines()
         assert lines[0] == "0", lines[:2]
         v = np.array([float.fromhex(t) for t in lines[1:]])
         return v if spin == 0 else v[0::2] + 1j * v[1::2]
 
+    call.exe = exe
     return call
 
 
@@ -82,3 +115,18 @@ def test_synthesis_matches_the_oracle(nside, lmax, prec, run):
     g = sht.synth_map(nside, lmax, phi, gradient=True)
     got = run(nside, lmax, 1, prec, phi * np.sqrt(ell * (ell + 1.0))[:, None])
     assert _rel(got, g[:, 0] + 1j * g[:, 1]) <= TOL[prec]
+
+
+def test_invalid_calls_are_refused(run):
+    """Every argument check of the synthesis API (plan sizes, spin, precision, null
+    and misaligned buffers) returns FLINTS_EINVAL with a message naming the fault,
+    and a refused synthesis leaves the output map untouched."""
+    lines = hc.run(run.exe, "reject\n").splitlines()
+    expect = ["out is NULL", "nside outside", "nside outside", "spin must be", "lmax outside", "precision must be",
+              "plan is NULL", "alm and map must not be NULL", "alm and map must not be NULL", "16-byte aligned",
+              "16-byte aligned", "16-byte aligned"]
+    assert len(lines) == len(expect) + 1, lines
+    for line, msg in zip(lines, expect):
+        rc, text = line.split("|", 1)
+        assert rc == "1" and msg in text, (line, msg)
+    assert lines[-1] == "untouched 1"
