@@ -245,6 +245,35 @@ int main() {
                              std::all_of(st, st + 256, [](uint8_t v) { return v == 255; }) &&
                              std::all_of(idx, idx + 64 * 16, [](int64_t v) { return v == -9; });
             printf("untouched %d\n", untouched ? 1 : 0);
+        } else if (o == "nreject") {  // the no-allocation entry point's checks, each refused before any launch
+            static double buf[4096] __attribute__((aligned(64)));
+            for (double &v : buf) v = std::nan("");
+            static uint8_t st[256];
+            std::memset(st, 255, sizeof st);
+            double *m = buf, *d = buf + 2048, *out = buf + 3072, *var = buf + 3584;
+            std::vector<double> cl(4001, 1.0), zero(17, 0.0), bad(17, 1.0);
+            bad[5] = std::nan("");
+            auto rep = [](int rc) { printf("%d|%s\n", rc, flints_noalloc_last_error()); };
+            auto call = [&](long long nside, int lmax, const double *c, int spin, int K, int prec, long long first,
+                            long long count, const double *mm, const double *dd, double *oo, double *vv) {
+                rep(flints_lens_noalloc(nside, lmax, c, nullptr, spin, K, prec, first, count, mm, dd, oo, vv, st,
+                                        nullptr));
+            };
+            call(0, 16, cl.data(), 0, 16, 0, 0, 4, m, d, out, var);
+            call(8, 9000, cl.data(), 0, 16, 0, 0, 4, m, d, out, var);
+            call(8, 16, nullptr, 0, 16, 0, 0, 4, m, d, out, var);
+            call(8, 16, cl.data(), 1, 16, 0, 0, 4, m, d, out, var);
+            call(8, 16, cl.data(), 0, 20, 0, 0, 4, m, d, out, var);
+            call(8, 16, cl.data(), 0, 16, 2, 0, 4, m, d, out, var);
+            call(8, 16, cl.data(), 0, 16, 0, 766, 4, m, d, out, var);
+            call(8, 16, cl.data(), 0, 16, 0, 0, 4, nullptr, d, out, var);
+            call(8, 16, cl.data(), 0, 16, 0, 0, 4, m, d, out, (double *)((char *)var + 4));
+            call(8, 16, cl.data(), 2, 16, 0, 0, 4, m + 1, d, out, var);
+            call(8, 16, bad.data(), 0, 16, 0, 0, 4, m, d, out, var);
+            call(16, 4000, cl.data(), 0, 16, 0, 0, 4, m, d, out, var);
+            call(8, 16, zero.data(), 0, 16, 0, 0, 4, m, d, out, var);
+            printf("untouched %d\n", std::all_of(buf + 3072, buf + 4096, [](double v) { return std::isnan(v); }) &&
+                                             std::all_of(st, st + 256, [](uint8_t v) { return v == 255; }) ? 1 : 0);
         } else return 3;
         printf("end\n");
         fflush(stdout);
@@ -314,6 +343,10 @@ class Session:
 
     def reject(self, p0, p2, p1):
         self.lines.append(f"reject {p0} {p2} {p1}")
+        self.kinds.append("reject")
+
+    def nreject(self):
+        self.lines.append("nreject")
         self.kinds.append("reject")
 
     def run(self):
@@ -645,3 +678,22 @@ def test_invalid_calls_are_refused_before_any_launch(exe):
         else:
             assert rc == "1" and msg in text, (line, msg)
     assert tail == ["untouched 1"], tail
+
+
+def test_invalid_no_allocation_calls_are_refused(exe):
+    """Every check of the no-allocation entry point (sizes, spin, K, precision, range,
+    null and misaligned buffers, a non-finite spectrum, a table above the fixed
+    interval count, a spectrum with xi(0) = 0) returns FLINTS_EINVAL with its message
+    and writes no output."""
+    s_ = Session(exe)
+    s_.nreject()
+    lines = s_.run()[0]
+    expect = ["nside outside", "lmax 9000 exceeds the fixed maximum 8192", "cl is NULL", "spin must be 0 or 2",
+              "K must be", "bad precision", "target range outside", "NULL data pointer", "misaligned buffer",
+              "misaligned buffer", "non-finite spectrum value at l = 5", "65536 intervals, above the fixed maximum",
+              "is not positive"]
+    assert len(lines) == len(expect) + 1, lines
+    for line, msg in zip(lines, expect):
+        rc, text = line.split("|", 1)
+        assert rc == "1" and msg in text, (line, msg)
+    assert lines[-1] == "untouched 1"
