@@ -697,3 +697,38 @@ def test_invalid_no_allocation_calls_are_refused(exe):
         rc, text = line.split("|", 1)
         assert rc == "1" and msg in text, (line, msg)
     assert lines[-1] == "untouched 1"
+
+
+@pytest.mark.parametrize("spin,prec", [(0, 0), (2, 1)], ids=["spin0-fp64", "spin2-mixed"])
+def test_no_variance_and_forced_fallback_flags(spin, prec, exe):
+    """FLINTS_NO_VARIANCE: the values and status are those of the default plan and
+    the variance buffer is left as it was.  FLINTS_FORCE_FALLBACK (mixed plans):
+    every point is re-solved on the FP64 path and carries FLINTS_ST_FALLBACK, its
+    values within 1e-8 of the oracle, and the fallback counter equals the count."""
+    nside, lmax, K = 8, 16, 16
+    npix = hp.npix(nside)
+    cl, bb, m, sigma = _sky(spin, nside, lmax, 55 + spin)
+    pix = np.arange(100, 300)
+    defl = wl.random_deflection(npix, 56 + spin, rms=0.5 * np.sqrt(4 * np.pi / npix))[pix]
+    ref, x0, _, _ = _oracle(spin, nside, K, cl, bb, m, defl, pix)
+    s_ = Session(exe)
+    s_.plan(1, nside, cl, bb, spin, K, prec, 0)
+    s_.plan(2, nside, cl, bb, spin, K, prec, 4)  # FLINTS_NO_VARIANCE
+    s_.map(1, nside, np.arange(npix), m)
+    s_.lens(1, pix[0], pix.size, 1, defl)
+    s_.lens(2, pix[0], pix.size, 1, defl)
+    if prec == 1:
+        s_.plan(3, nside, cl, bb, spin, K, 1, 256)  # FLINTS_FORCE_FALLBACK
+        s_.lens(3, pix[0], pix.size, 1, defl)
+        s_.stats(3)
+    res = s_.run()
+    (st1, v1, var1), (st2, v2, var2) = res[3], res[4]
+    assert np.array_equal(st1, st2) and np.array_equal(v1, v2)
+    assert np.all(np.isnan(var2)) and not np.any(np.isnan(var1))
+    if prec == 1:
+        st3, v3, var3 = res[6]
+        assert np.all(st3 == 2)  # FLINTS_ST_FALLBACK only
+        ref_v = ref.value if spin else ref.value.real
+        assert np.max(np.abs(v3 - ref_v)) <= 1e-8 * sigma
+        assert np.max(np.abs(var3 - ref.variance)) <= 1e-8 * x0
+        assert res[7][3] == pix.size  # fallback counter
