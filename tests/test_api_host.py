@@ -732,3 +732,40 @@ def test_no_variance_and_forced_fallback_flags(spin, prec, exe):
         assert np.max(np.abs(v3 - ref_v)) <= 1e-8 * sigma
         assert np.max(np.abs(var3 - ref.variance)) <= 1e-8 * x0
         assert res[7][3] == pix.size  # fallback counter
+
+
+@pytest.mark.parametrize("spin,prec", [(0, 0), (2, 1)], ids=["spin0-fp64", "spin2-mixed"])
+def test_nonfinite_deflections_in_a_tile(spin, prec, exe):
+    """NaN and infinite deflections among good ones in the same warp tiles: those
+    points get FLINTS_ST_INPUT | FLINTS_ST_FAILED and NaN outputs, the failed counter
+    counts them, and the other points of their tiles keep the oracle's values (the
+    lanes of a bad point leave the warp's collective steps without stalling them)."""
+    nside, lmax, K = 8, 16, 16
+    npix = hp.npix(nside)
+    cl, bb, m, sigma = _sky(spin, nside, lmax, 61 + spin)
+    pix = np.arange(200, 296)
+    defl = wl.random_deflection(npix, 62 + spin, rms=0.5 * np.sqrt(4 * np.pi / npix))[pix]
+    bad = np.array([0, 5, 6, 17, 40, 95])
+    d_bad = defl.copy()
+    d_bad[bad[0], 0] = np.nan
+    d_bad[bad[1], 1] = np.inf
+    d_bad[bad[2]] = [-np.inf, 0.0]
+    d_bad[bad[3]] = [np.nan, np.nan]
+    d_bad[bad[4], 1] = -np.inf
+    d_bad[bad[5], 0] = np.inf
+    good = np.setdiff1d(np.arange(pix.size), bad)
+    ref, x0, _, _ = _oracle(spin, nside, K, cl, bb, m, defl[good], pix[good])
+    s_ = Session(exe)
+    s_.plan(1, nside, cl, bb, spin, K, prec)
+    s_.map(1, nside, np.arange(npix), m)
+    s_.lens(1, pix[0], pix.size, 1, d_bad)
+    s_.stats(1)
+    res = s_.run()
+    st, v, var = res[2]
+    assert np.all(st[bad] == 32 | 8) and np.all(st[good] == 0)  # FLINTS_ST_INPUT | FLINTS_ST_FAILED
+    assert np.all(np.isnan(v[bad].real)) and np.all(np.isnan(var[bad]))
+    assert res[3][5] == bad.size
+    tol = 1e-9 if prec == 0 else 1e-6
+    ref_v = ref.value if spin else ref.value.real
+    assert np.max(np.abs(v[good] - ref_v)) <= tol * sigma
+    assert np.max(np.abs(var[good] - ref.variance)) <= tol * x0

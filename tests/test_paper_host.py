@@ -199,3 +199,31 @@ def test_invalid_calls_are_refused_before_any_launch(run):
         rc, text = line.split("|", 1)
         assert rc == "1" and msg in text, (line, msg)
     assert lines[-1] == "untouched 1 points 0", lines[-1]
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_nonfinite_deflections_on_the_tabulated_route(prec, run):
+    """NaN and infinite deflections on the tabulated route: FLINTS_ST_INPUT |
+    FLINTS_ST_FAILED and NaN outputs there, every other target bit-identical to the
+    run with the finite deflections (the 128-thread apply blocks keep their barriers
+    with bad lanes among them)."""
+    nside, lmax = 8, 16
+    npix = hp.npix(nside)
+    cl = wl.cl_tt(lmax, 0.7 * lmax)
+    m = sht.synth_map(nside, lmax, wl.draw_alm(cl, 71))
+    defl = wl.random_deflection(npix, 72, rms=0.5 * np.sqrt(4 * np.pi / npix))
+    bad = np.array([0, 1, 33, 130, 131, npix - 1])
+    d_bad = defl.copy()
+    d_bad[bad[0], 0] = np.nan
+    d_bad[bad[1], 1] = np.inf
+    d_bad[bad[2]] = [-np.inf, 0.0]
+    d_bad[bad[3]] = [np.nan, np.nan]
+    d_bad[bad[4], 1] = -np.inf
+    d_bad[bad[5], 0] = np.inf
+    st0, v0, s0 = run(nside, lmax, 1, 0, prec, 0, cl, None, m, defl)
+    st, v, s2 = run(nside, lmax, 1, 0, prec, 0, cl, None, m, d_bad)
+    good = np.setdiff1d(np.arange(npix), bad)
+    assert np.all(st[bad] & (32 | 8) == 32 | 8) and np.all(st[good] == st0[good])
+    assert np.all(np.isnan(v[bad])) and np.all(np.isnan(s2[bad]))
+    np.testing.assert_array_equal(v[good], v0[good])
+    np.testing.assert_array_equal(s2[good], s0[good])
