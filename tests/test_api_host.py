@@ -240,6 +240,14 @@ int main() {
             flints_launch_cfg wide{9, 0, 0};
             rep(flints_batch_launch(b, &wide, nullptr), le());
             rep(flints_lens_batch(two, -1, nullptr), le());
+            // empty ranges are accepted with any buffers, and launch nothing
+            rep(flints_lens_range(p0, npix, 0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr), le());
+            rep(flints_lens_range(p2, 0, 0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr), le());
+            rep(flints_stencil(p0, 5, 0, nullptr, idx, nullptr, nullptr), le());
+            rep(flints_supersample(p0, 16, 3, 0, nullptr, nullptr, nullptr, nullptr, nullptr), le());
+            rep(flints_lens_batch(nullptr, 0, nullptr), le());
+            flints_job empty{p2, 7, 0, nullptr, nullptr, nullptr, nullptr, nullptr};
+            rep(flints_lens_batch(&empty, 1, nullptr), le());
             flints_batch_free(b);
             bool untouched = std::all_of(buf + 3072, buf + 4096, [](double v) { return std::isnan(v); }) &&
                              std::all_of(st, st + 256, [](uint8_t v) { return v == 255; }) &&
@@ -272,6 +280,7 @@ int main() {
             call(8, 16, bad.data(), 0, 16, 0, 0, 4, m, d, out, var);
             call(16, 4000, cl.data(), 0, 16, 0, 0, 4, m, d, out, var);
             call(8, 16, zero.data(), 0, 16, 0, 0, 4, m, d, out, var);
+            call(8, 16, cl.data(), 2, 16, 1, 768, 0, nullptr, nullptr, nullptr, nullptr);  // empty: accepted
             printf("untouched %d\n", std::all_of(buf + 3072, buf + 4096, [](double v) { return std::isnan(v); }) &&
                                              std::all_of(st, st + 256, [](uint8_t v) { return v == 255; }) ? 1 : 0);
         } else return 3;
@@ -651,7 +660,9 @@ def test_invalid_calls_are_refused_before_any_launch(exe):
     """Every argument check of the K-nearest C API (null and out-of-range arguments,
     misaligned buffers, a plan of the wrong spin, launch shapes, batch jobs) returns
     FLINTS_EINVAL with a message naming the fault, writes no output and, for a batch
-    stage refused at a later job, counts no points for the earlier ones."""
+    stage refused at a later job, counts no points for the earlier ones.  Empty
+    ranges (count 0, also at first = Npix, and empty batches) succeed with any
+    buffers and write nothing."""
     nside, lmax = 8, 16
     s_ = Session(exe)
     s_.plan(1, nside, wl.cl_tt(lmax, 12.0), None, 0, 16, 0)
@@ -669,7 +680,7 @@ def test_invalid_calls_are_refused_before_any_launch(exe):
               "target range", "warps_per_block 0..8", "warps_per_block 0..8", "warps_per_block 0..8",
               "bad table index", "NULL argument", "bad arguments", None, "capacity 2", "tile_points 0..16",
               "job 1: plan is NULL", "job 1: spin-1 and augmented", "job 1: target range outside", "job 1: NULL data",
-              "job 1: misaligned", "warps_per_block 1..8", "bad job list"]
+              "job 1: misaligned", "warps_per_block 1..8", "bad job list", None, None, None, None, None, None]
     assert len(calls) == len(expect), calls
     for line, msg in zip(calls, expect):
         rc, text = line.split("|", 1)
@@ -691,11 +702,11 @@ def test_invalid_no_allocation_calls_are_refused(exe):
     expect = ["nside outside", "lmax 9000 exceeds the fixed maximum 8192", "cl is NULL", "spin must be 0 or 2",
               "K must be", "bad precision", "target range outside", "NULL data pointer", "misaligned buffer",
               "misaligned buffer", "non-finite spectrum value at l = 5", "65536 intervals, above the fixed maximum",
-              "is not positive"]
+              "is not positive", None]
     assert len(lines) == len(expect) + 1, lines
     for line, msg in zip(lines, expect):
         rc, text = line.split("|", 1)
-        assert rc == "1" and msg in text, (line, msg)
+        assert (rc == "0") if msg is None else (rc == "1" and msg in text), (line, msg)
     assert lines[-1] == "untouched 1"
 
 
