@@ -118,3 +118,84 @@ def test_binding_refuses_host_or_mistyped_buffers_on_the_host(lib_path):
                 api._job_array([job])
     with pytest.raises(api.FlintsError, match="status must be a contiguous uint8 CUDA tensor"):
         api._dev_buf(torch.zeros(24, dtype=torch.uint8)[::2], 12, "status", "uint8")
+
+
+C_LAYOUT = r"""
+#include <stddef.h>
+#include <stdio.h>
+#include "flints.h"
+#define F(T, f) printf(#T " " #f " %zu %zu\n", offsetof(T, f), sizeof(((T *)0)->f))
+#define S(T) printf(#T " sizeof %zu 0\n", sizeof(T))
+int main(void) {
+    flints_plan_t h = 0;
+    S(flints_stats); F(flints_stats, points); F(flints_stats, nugget); F(flints_stats, fallback);
+    F(flints_stats, window); F(flints_stats, failed);
+    S(flints_plan_info); F(flints_plan_info, nside); F(flints_plan_info, lmax); F(flints_plan_info, spin);
+    F(flints_plan_info, K); F(flints_plan_info, precision); F(flints_plan_info, t_max);
+    F(flints_plan_info, n_intervals); F(flints_plan_info, xi0); F(flints_plan_info, search_radius);
+    S(flints_launch_cfg); F(flints_launch_cfg, warps_per_block); F(flints_launch_cfg, blocks_per_sm);
+    F(flints_launch_cfg, tile_points);
+    S(flints_job); F(flints_job, plan); F(flints_job, first); F(flints_job, count); F(flints_job, map);
+    F(flints_job, defl); F(flints_job, out); F(flints_job, var); F(flints_job, status);
+    S(flints_paper_info); F(flints_paper_info, nside); F(flints_paper_info, nside_coarse); F(flints_paper_info, y);
+    F(flints_paper_info, K); F(flints_paper_info, slots); F(flints_paper_info, t_max);
+    F(flints_paper_info, n_intervals); F(flints_paper_info, xi0); F(flints_paper_info, table_bytes);
+    F(flints_paper_info, max_pair_t); F(flints_paper_info, nugget_slots); F(flints_paper_info, failed_slots);
+    F(flints_paper_info, points); F(flints_paper_info, window); F(flints_paper_info, precision);
+    F(flints_paper_info, spin); F(flints_paper_info, flags);
+    printf("const FLINTS_FP64 %d\nconst FLINTS_MIXED %d\n", FLINTS_FP64, FLINTS_MIXED);
+    printf("const FLINTS_SPIN2_AUGMENTED %u\nconst FLINTS_ROTATE_TO_TARGET %u\n", FLINTS_SPIN2_AUGMENTED,
+           FLINTS_ROTATE_TO_TARGET);
+    printf("const FLINTS_NO_VARIANCE %u\nconst FLINTS_FORCE_FALLBACK %u\n", FLINTS_NO_VARIANCE, FLINTS_FORCE_FALLBACK);
+    printf("const ST_NUGGET %u\nconst ST_FALLBACK %u\nconst ST_WINDOW %u\n", FLINTS_ST_NUGGET, FLINTS_ST_FALLBACK,
+           FLINTS_ST_WINDOW);
+    printf("const ST_FAILED %u\nconst ST_POLE %u\nconst ST_INPUT %u\n", FLINTS_ST_FAILED, FLINTS_ST_POLE,
+           FLINTS_ST_INPUT);
+    /* argument checks run on the host: no device is touched */
+    printf("call %d %s\n", flints_plan(&h, 0, 16, 0, 0, 0, 16, FLINTS_FP64, 0u, 0), flints_last_error());
+    return h != 0;
+}
+"""
+
+
+def test_header_is_c_and_its_layouts_match_the_binding(lib_path, tmp_path):
+    """include/flints.h compiles as strict C99; a C program linked against the
+    library sees the struct layouts and constants the ctypes binding uses (a field
+    offset the binding got wrong would hand the library a garbled job or plan info),
+    and gets FLINTS_EINVAL from a plan with Nside 0 without touching a device."""
+    import os
+    import shutil
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "layout.c"
+    src.write_text(C_LAYOUT)
+    exe = tmp_path / "layout"
+    libdir = os.path.dirname(lib_path)
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.dirname(api.HEADER),
+                        str(src), "-o", str(exe), "-L", libdir, "-lflints", f"-Wl,-rpath,{libdir}",
+                        "-Wl,--allow-shlib-undefined"], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines()
+    structs = {"flints_stats": api._Stats, "flints_plan_info": api._Info, "flints_launch_cfg": api.LaunchCfg,
+               "flints_job": api._Job, "flints_paper_info": api._PaperInfo}
+    seen = set()
+    for line in out:
+        kind, *rest = line.split()
+        if kind in structs:
+            field, off, size = rest[0], int(rest[1]), int(rest[2])
+            cls = structs[kind]
+            if field == "sizeof":
+                assert ctypes.sizeof(cls) == off, kind
+            else:
+                desc = getattr(cls, field)
+                assert (desc.offset, desc.size) == (off, size), (kind, field)
+                seen.add((kind, field))
+        elif kind == "const":
+            name, value = rest
+            assert getattr(api, name) == int(value), name
+        else:
+            assert kind == "call" and rest[0] == "1" and "nside" in " ".join(rest[1:]), line
+    # every field the binding declares was checked against the header
+    assert seen == {(k, f) for k, c in structs.items() for f, _ in c._fields_}
