@@ -199,3 +199,60 @@ def test_header_is_c_and_its_layouts_match_the_binding(lib_path, tmp_path):
             assert kind == "call" and rest[0] == "1" and "nside" in " ".join(rest[1:]), line
     # every field the binding declares was checked against the header
     assert seen == {(k, f) for k, c in structs.items() for f, _ in c._fields_}
+
+
+def _prototypes():
+    """{name: (return type, [parameter types])} of the functions in include/flints.h,
+    types as written with the parameter names removed."""
+    import re
+
+    txt = re.sub(r"/\*.*?\*/", "", open(api.HEADER).read(), flags=re.S)
+    protos = {}
+    for ret, name, params in re.findall(r"\b((?:const\s+)?[a-z_0-9]+\s*\*?)\s*(flints_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;",
+                                        txt):
+        types = []
+        for p in params.split(","):
+            p = " ".join(p.split())
+            if p in ("", "void"):
+                continue
+            types.append(re.sub(r"\s*\b[A-Za-z_0-9]+$", "", p).replace(" *", "*"))
+        protos[name] = (" ".join(ret.split()).replace(" *", "*"), types)
+    return protos
+
+
+def _ctype_of(c: str):
+    """The ctypes class that passes a C type with the same calling convention."""
+    if c.endswith("*") or c.endswith("_t") and c.startswith("flints_") or c == "void*":
+        return "ptr"
+    return {"int64_t": ctypes.c_int64, "int": ctypes.c_int, "unsigned": ctypes.c_uint, "double": ctypes.c_double,
+            "void": None}[c]
+
+
+def test_binding_signatures_match_the_header(lib_path):
+    """The argtypes and restype the binding sets for every function of the header
+    match its prototype: same parameter count, integers of the same width and
+    signedness, pointers for pointers (a wrong width would pass garbage in a
+    register)."""
+    lib = api.load_library()
+    protos = _prototypes()
+    assert set(protos) == set(api.header_functions())
+    checked = 0
+    for name, (ret, params) in protos.items():
+        fn = getattr(lib, name)
+        checked += 1
+        argtypes = fn.argtypes if fn.argtypes is not None else []  # none set: a (void) function
+        assert len(argtypes) == len(params), (name, fn.argtypes, params)
+        for a, c in zip(argtypes, params):
+            want = _ctype_of(c)
+            if want == "ptr":
+                assert a is ctypes.c_void_p or a is ctypes.c_char_p or hasattr(a, "_type_") and issubclass(
+                    a, ctypes._Pointer), (name, a, c)
+            else:
+                assert a is want, (name, a, c)
+        r = _ctype_of(ret)
+        if r == "ptr":
+            assert fn.restype in (ctypes.c_char_p, ctypes.c_void_p), (name, fn.restype)
+        else:
+            assert fn.restype is (r if r is not None else None) or (r is ctypes.c_int and fn.restype is ctypes.c_int), \
+                (name, fn.restype, ret)
+    assert checked == len(protos)
