@@ -42,10 +42,20 @@ enum cudaMemcpyKind { cudaMemcpyHostToHost, cudaMemcpyHostToDevice, cudaMemcpyDe
                       cudaMemcpyDefault };
 enum cudaFuncAttribute { cudaFuncAttributeMaxDynamicSharedMemorySize };
 enum cudaDeviceAttr { cudaDevAttrMultiProcessorCount, cudaDevAttrMaxSharedMemoryPerBlockOptin };
+#ifdef FLINTS_HOST_SANITIZE
+// exact sizes (so that the address sanitizer sees an access past the end) and
+// contents that are not zero (device memory is not cleared)
+static inline cudaError_t cudaMalloc(void **p, size_t n) {
+    if (posix_memalign(p, 256, n ? n : 1)) return cudaErrorMemoryAllocation;
+    std::memset(*p, 0xff, n ? n : 1);
+    return cudaSuccess;
+}
+#else
 static inline cudaError_t cudaMalloc(void **p, size_t n) {
     *p = std::aligned_alloc(256, (n + 255) / 256 * 256 + 256);
     return *p ? cudaSuccess : cudaErrorMemoryAllocation;
 }
+#endif
 template <class T> static inline cudaError_t cudaMalloc(T **p, size_t n) { return cudaMalloc((void **)p, n); }
 static inline cudaError_t cudaFree(void *p) { std::free(p); return cudaSuccess; }
 enum { cudaHostAllocDefault = 0 };
@@ -84,7 +94,11 @@ struct dim3 {
 };
 static thread_local dim3 threadIdx, blockIdx;
 static dim3 blockDim, gridDim;
+#ifdef FLINTS_HOST_SANITIZE
+static unsigned char *g_dyn_smem = nullptr;  // per launch: exactly the requested bytes, not cleared
+#else
 static unsigned char g_dyn_smem[256 * 1024] __attribute__((aligned(256)));
+#endif
 
 // a barrier of a changing number of threads: arrive() waits for the others, leave()
 // removes the caller (a thread that returned from the kernel)
@@ -180,7 +194,15 @@ template <class T> static inline T atomicMax(T *p, T v) {
 
 template <class F> static cudaError_t host_launch(dim3 grid, dim3 block, size_t smem, F body) {
     const unsigned nthr = block.x * block.y * block.z;
+#ifdef FLINTS_HOST_SANITIZE
+    if (smem > 256 * 1024) return cudaErrorInvalidValue;
+    void *dyn = nullptr;
+    if (posix_memalign(&dyn, 256, smem ? smem : 1)) return cudaErrorMemoryAllocation;
+    std::memset(dyn, 0xff, smem ? smem : 1);
+    g_dyn_smem = static_cast<unsigned char *>(dyn);
+#else
     if (smem > sizeof g_dyn_smem) return cudaErrorInvalidValue;
+#endif
     blockDim = block;
     gridDim = grid;
     HostBarrier start, end;
@@ -206,6 +228,10 @@ template <class F> static cudaError_t host_launch(dim3 grid, dim3 block, size_t 
             }
         });
     for (auto &th : pool) th.join();
+#ifdef FLINTS_HOST_SANITIZE
+    std::free(dyn);
+    g_dyn_smem = nullptr;
+#endif
     return cudaSuccess;
 }
 static inline void sincospi(double x, double *s, double *c) { *s = std::sin(M_PI * x); *c = std::cos(M_PI * x); }
@@ -366,8 +392,10 @@ def source(name: str) -> str:
     return _launches(src)
 
 
-def build(tmpdir, name: str, files, driver: str) -> str:
-    """Compile the given sources (in order) with the runtime stand-ins and ``driver``."""
-    text = (RUNTIME + '#include "' + hc.ROOT + '/include/flints.h"\n'
-            + "".join(source(f) + "\n" for f in files) + driver)
-    return hc.build(tmpdir, name, text, warp="none")
+def build(tmpdir, name: str, files, driver: str, sanitize: bool = False) -> str:
+    """Compile the given sources (in order) with the runtime stand-ins and ``driver``.
+    ``sanitize``: address and undefined-behaviour sanitizers, device allocations and
+    dynamic shared memory of exactly the requested size and filled with 0xff bytes."""
+    text = (("#define FLINTS_HOST_SANITIZE 1\n" if sanitize else "") + RUNTIME + '#include "' + hc.ROOT
+            + '/include/flints.h"\n' + "".join(source(f) + "\n" for f in files) + driver)
+    return hc.build(tmpdir, name, text, warp="none", sanitize=sanitize)

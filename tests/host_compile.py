@@ -160,15 +160,24 @@ def compiler() -> str | None:
     return shutil.which("g++") or shutil.which("c++")
 
 
-def build(tmpdir, name: str, text: str, warp: str = "identity") -> str:
+# address sanitizer and the undefined-behaviour checks that matter for kernel code
+# (array bounds, shifts, signed overflow); -O0 keeps the build short (the emulated
+# barriers, not the arithmetic, set the run time) and, without contraction or
+# fast-math, rounds exactly as -O2 does
+SANITIZE = ["-fsanitize=address,bounds,shift,signed-integer-overflow", "-fno-sanitize-recover=all",
+            "-fno-omit-frame-pointer", "-O0"]
+
+
+def build(tmpdir, name: str, text: str, warp: str = "identity", sanitize: bool = False) -> str:
     """Compile ``SHIM`` + the warp stand-ins (``"identity"``, ``"threads"`` or none) +
-    ``text`` into an executable (strict IEEE: no contraction)."""
+    ``text`` into an executable (strict IEEE: no contraction; ``sanitize``: with the
+    address and undefined-behaviour sanitizers, any finding ends the run)."""
     src = os.path.join(str(tmpdir), name + ".cpp")
     with open(src, "w") as f:
         f.write(SHIM + {"threads": WARP_THREADS, "identity": WARP_IDENTITY}.get(warp, "") + text)
     exe = os.path.join(str(tmpdir), name)
-    r = subprocess.run([compiler(), "-std=c++20", "-O2", "-pthread", "-ffp-contract=off", "-fno-fast-math", src, "-o",
-                        exe], capture_output=True, text=True)
+    r = subprocess.run([compiler(), "-std=c++20", "-O2", "-pthread", "-ffp-contract=off", "-fno-fast-math"]
+                       + (SANITIZE if sanitize else []) + [src, "-o", exe], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
     return exe
 

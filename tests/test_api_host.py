@@ -287,6 +287,7 @@ int main() {
         printf("end\n");
         fflush(stdout);
     }
+    for (auto &kv : g_plans) flints_free(kv.second);  // every plan's allocations come back (leak check)
     return 0;
 }
 """

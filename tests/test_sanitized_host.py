@@ -1,0 +1,144 @@
+"""The library's CUDA sources under the address sanitizer and the bounds, shift and
+signed-overflow checks (tests/host_compile.SANITIZE), through the host emulation of
+tests/cuda_host.py with device allocations and dynamic shared memory of exactly the
+requested size and filled with 0xff bytes (device memory is not cleared): an
+access past a buffer, a static shared array's row or the requested dynamic shared
+memory, a read of memory nobody wrote that changes a result, or a plan whose
+allocations flints_free does not return, fails these tests (any sanitizer finding
+ends the run with an error).  A GPU would report such an access as a fault, or
+not at all.  One script per C API (K-nearest with batches and the no-allocation
+call, the tabulated route, the synthesis), results against the oracle."""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import faces as fc
+from oracle import healpix as hp
+from oracle import kriging as kr
+from oracle import sht
+from oracle import xi
+from tests import cuda_host as ch
+from tests import host_compile as hc
+from tests import test_api_host as A
+from tests import test_paper_host as P
+from tests import test_synth_host as S
+
+
+@pytest.fixture(scope="module")
+def builds(tmp_path_factory):
+    if hc.compiler() is None:
+        pytest.skip("no host C++ compiler")
+    from concurrent.futures import ThreadPoolExecutor
+
+    d = tmp_path_factory.mktemp("sanitized")
+    jobs = {"api": (A.FILES, A.DRIVER),
+            "paper": (["common.cuh", "lens.cuh", "paper_geom.cuh", "xi_table.cu", "paper.cu"], P.DRIVER),
+            "synth": (["common.cuh", "synth.cu"], S.DRIVER)}
+    with ThreadPoolExecutor(len(jobs)) as pool:  # three compiler processes at once
+        fut = {k: pool.submit(ch.build, d, k + "_san", files, drv, True) for k, (files, drv) in jobs.items()}
+        return {k: f.result() for k, f in fut.items()}
+
+
+def test_k_nearest_api_under_the_sanitizers(builds):
+    nside, lmax = 8, 16
+    npix = hp.npix(nside)
+    pix = np.arange(40, 200)
+    cases = [(0, 16, 0, 0), (2, 32, 1, 0), (2, 24, 0, 1), (0, 48, 1, 4)]  # spin, K, precision, flags
+    s = A.Session(builds["api"])
+    refs = []
+    for k, (spin, K, prec, flags) in enumerate(cases, start=1):
+        cl, bb, m, sigma = A._sky(spin, nside, lmax, 30 + k)
+        if flags & 1:
+            bb = 0.3 * cl
+        defl = wl.random_deflection(npix, 40 + k, rms=0.5 * np.sqrt(4 * np.pi / npix))[pix]
+        weight = np.abs(cl) + (np.abs(bb) if bb is not None else 0.0)
+        t_max, n = xi.grid_rule(weight, K, nside)
+        if spin == 0:
+            tp, x0 = xi.spin0_table(cl, t_max, n)
+            tm = None
+        else:
+            tp, tm, x0 = xi.spin2_tables(cl, bb, t_max, n)
+        ref = kr.lens(nside, K, spin, m, defl, pix, tp, x0, f_minus=tm if flags & 1 else None)
+        refs.append((ref, sigma, x0, prec, flags))
+        s.plan(k, nside, cl, bb, spin, K, prec, flags)
+        s.map(k, nside, np.arange(npix), m)
+        s.lens(k, pix[0], pix.size, k, defl)
+    d1 = wl.random_deflection(npix, 99, rms=0.5 * np.sqrt(4 * np.pi / npix))
+    s.batch([(1, 0, 100, 1, d1[:100]), (2, 700, 68, 2, d1[700:768])], obj=(2, 5))
+    s.stencil(1, 0, 64, d1[:64])
+    s.super(2, 16, 5, 100, 2)
+    cl, _, _, _ = A._sky(2, nside, lmax, 32)
+    s.noalloc(nside, cl, None, 2, 32, 1, 10, 100, 2, d1[10:110])
+    s.reject(1, 2, 3)
+    s.nreject()
+    res = s.run()
+    for k, (ref, sigma, x0, prec, flags) in enumerate(refs):
+        st, v, var = res[3 * k + 2]
+        tol = 1e-9 if prec == 0 else 1e-6
+        ref_v = ref.value if np.iscomplexobj(ref.value) else ref.value + 0j
+        assert np.all(st & 8 == 0)
+        assert np.max(np.abs(v - ref_v)) <= tol * sigma, k
+        if flags & 4:  # FLINTS_NO_VARIANCE: the buffer is left as it was
+            assert np.all(np.isnan(var))
+        else:
+            assert np.max(np.abs(var - ref.variance)) <= tol * x0, k
+    # the later calls ran to completion with their results (their values are checked
+    # against the oracle by the unsanitized tests)
+    assert [len(r[0]) for r in res[12]] == [100, 68] and len(res[13][0]) == 64 and len(res[14][0]) == 100
+    assert len(res[15][0]) == 100
+    assert res[-2][-1] == "untouched 1" and res[-1][-1] == "untouched 1"
+
+
+def test_tabulated_route_under_the_sanitizers(builds):
+    nside, lmax = 8, 16
+    npix = hp.npix(nside)
+    for spin, y, prec, flags in [(0, 1, 0, 0), (0, 2, 1, 0), (2, 1, 1, 0), (2, 2, 0, 1)]:
+        cl = wl.cl_tt(lmax, 0.7 * lmax) if spin == 0 else wl.cl_ee(lmax, 0.7 * lmax)
+        bb = None if spin == 0 else 0.3 * cl
+        if spin == 0:
+            m = sht.synth_map(nside, lmax, wl.draw_alm(cl, 50 + y))
+            sigma = float(np.std(m))
+        else:
+            Pm = sht.synth_map(nside, lmax, wl.draw_alm(cl, 50 + y), spin=2, blm=wl.draw_alm(bb, 60 + y))
+            m = np.stack([Pm.real, Pm.imag], axis=1)
+            sigma = float(np.sqrt(np.mean(np.abs(Pm) ** 2)))
+        defl = wl.random_deflection(npix, 70 + y, rms=0.5 * np.sqrt(4 * np.pi / npix))
+        t_max, n = fc.paper_grid_rule(cl, nside, y, bb)
+        if spin == 0:
+            tp, x0 = xi.spin0_table(cl, t_max, n)
+            tm = None
+        else:
+            tp, tm, x0 = xi.spin2_tables(cl, bb, t_max, n)
+        rv, rs2, _, _ = fc.paper_lens(nside, y, m, defl, np.arange(npix), tp, x0, classes=True, spin=spin,
+                                      f_minus=tm if flags else None)
+        head = f"lens {nside} {lmax} {y} {spin} {prec} {flags} {0 if bb is None else 1} "
+        body = " ".join(x.hex() for x in cl) + ("" if bb is None else " " + " ".join(x.hex() for x in bb))
+        body += " " + " ".join(float(x).hex() for x in np.ravel(m)) + " " + " ".join(
+            float(x).hex() for x in np.ravel(defl))
+        lines = hc.run(builds["paper"], head + body + "\n").splitlines()
+        assert lines[0] == "0", lines[:2]
+        rows = [ln.split() for ln in lines[1:]]
+        v = np.array([float.fromhex(r[1]) for r in rows])
+        if spin:
+            v = v + 1j * np.array([float.fromhex(r[3]) for r in rows])
+        s2 = np.array([float.fromhex(r[2]) for r in rows])
+        tol = 1e-9 if prec == 0 else 1e-6
+        assert np.max(np.abs(v - rv)) <= tol * sigma and np.max(np.abs(s2 - rs2)) <= tol * x0, (spin, y, prec)
+    out = hc.run(builds["paper"], "reject 8 16 " + " ".join(x.hex() for x in wl.cl_tt(16, 12.0)) + "\n")
+    assert out.splitlines()[-1] == "untouched 1 points 0"
+
+
+def test_synthesis_under_the_sanitizers(builds):
+    def flat(a):
+        return " ".join(float(x).hex() for x in np.stack([a.real, a.imag], -1).ravel())
+
+    for nside, lmax, prec in [(8, 16, 0), (4, 300, 1)]:
+        cl = wl.cl_ee(lmax, 0.7 * lmax)
+        e, b = wl.draw_alm(cl, 80 + nside), wl.draw_alm(0.4 * cl, 81 + nside)
+        lines = hc.run(builds["synth"], f"synth {nside} {lmax} 2 {prec} 1 {flat(e)} {flat(b)}\n").splitlines()
+        assert lines[0] == "0"
+        got = np.array([float.fromhex(t) for t in lines[1:]])
+        got = got[0::2] + 1j * got[1::2]
+        ref = sht.synth_map(nside, lmax, e, spin=2, blm=b)
+        assert np.max(np.abs(got - ref)) / np.sqrt(np.mean(np.abs(ref) ** 2)) <= (1e-10, 1e-9)[prec]
+    assert hc.run(builds["synth"], "reject\n").splitlines()[-1] == "untouched 1"
