@@ -142,3 +142,49 @@ def test_synthesis_under_the_sanitizers(builds):
         ref = sht.synth_map(nside, lmax, e, spin=2, blm=b)
         assert np.max(np.abs(got - ref)) / np.sqrt(np.mean(np.abs(ref) ** 2)) <= (1e-10, 1e-9)[prec]
     assert hc.run(builds["synth"], "reject\n").splitlines()[-1] == "untouched 1"
+
+
+def test_rare_kernel_branches_under_the_sanitizers(builds):
+    """The branches the workloads never take, under the sanitizers: spin-1 plans
+    (oracle parity), indefinite stencil covariances (the nugget steps, FP64 failures
+    and the mixed kernel's FP64 fallback) and non-finite deflections inside a tile."""
+    nside, lmax = 8, 16
+    npix = hp.npix(nside)
+    first, count = 200, 120
+    defl = wl.random_deflection(count, 91) * 8
+    pix = np.arange(first, first + count)
+    ell = np.arange(lmax + 1.0)
+    cl1 = ell * (ell + 1) * wl.cl_phiphi(lmax)
+    g = sht.synth_map(nside, lmax, wl.draw_alm(wl.cl_phiphi(lmax), 92), gradient=True)
+    t1, n1 = xi.grid_rule(np.abs(cl1), 16, nside)
+    tab1, _, x01 = xi.spin1_tables(cl1, None, t1, n1)
+    ref1 = kr.lens(nside, 16, 1, g, defl, pix, tab1, x01)
+    cl = wl.cl_tt(lmax, 11.0)
+    cl[lmax] = -0.0043 * cl[2]  # S + 1.49e-8 I indefinite on some stencils
+    m = sht.synth_map(nside, lmax, wl.draw_alm(np.abs(cl), 95))
+    d_all = wl.random_deflection(npix, 5) * 8
+    d_bad = d_all[:96].copy()
+    d_bad[[3, 40, 41], 0] = np.nan
+    s = A.Session(builds["api"])
+    s.plan(1, nside, cl1, None, 1, 16, 1)  # spin 1, mixed
+    s.map(1, nside, np.arange(npix), g)
+    s.lens(1, first, count, 1, defl)
+    s.plan(2, nside, cl, None, 0, 16, 0)
+    s.plan(3, nside, cl, None, 0, 16, 1)
+    s.map(2, nside, np.arange(npix), m)
+    s.lens(2, 0, npix, 2, d_all)
+    s.lens(3, 0, npix, 2, d_all)
+    s.lens(3, 0, 96, 2, d_bad)
+    res = s.run()
+    st, v, var = res[2]
+    sigma = float(np.sqrt(np.mean(np.sum(g ** 2, 1))))
+    assert np.all(st == 0)
+    assert np.max(np.abs(v - ref1.value)) <= 1e-6 * sigma and np.max(np.abs(var - ref1.variance)) <= 1e-6 * x01
+    st64, stmx = res[6][0], res[7][0]
+    assert np.any(st64 & 1) and np.any(st64 & 8)  # nugget steps taken, and failures
+    assert np.array_equal(stmx & (1 | 8), st64 & (1 | 8)) and np.all(stmx[st64 & 1 != 0] & 2)
+    stb, vb, _ = res[8]
+    assert np.all(stb[[3, 40, 41]] == 32 | 8) and np.all(np.isnan(vb[[3, 40, 41]].real))
+    # the other points of those tiles as in the run with finite deflections (NaN where that
+    # run failed too)
+    np.testing.assert_array_equal(np.delete(vb, [3, 40, 41]), np.delete(res[7][1][:96], [3, 40, 41]))
