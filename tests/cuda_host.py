@@ -234,6 +234,10 @@ template <class F> static cudaError_t host_launch(dim3 grid, dim3 block, size_t 
 #endif
     return cudaSuccess;
 }
+// lgamma without glibc's write of the global sign (signgam): the device function has
+// no global state, and the emulated threads call it at once
+static inline double flints_host_lgamma(double x) { int s; return lgamma_r(x, &s); }
+#define lgamma flints_host_lgamma
 static inline void sincospi(double x, double *s, double *c) { *s = std::sin(M_PI * x); *c = std::cos(M_PI * x); }
 static inline float sinpif(float x) { return (float)std::sin(M_PI * (double)x); }
 static inline double __longlong_as_double(long long v) { double d; std::memcpy(&d, &v, 8); return d; }
@@ -392,10 +396,11 @@ def source(name: str) -> str:
     return _launches(src)
 
 
-def build(tmpdir, name: str, files, driver: str, sanitize: bool = False) -> str:
+def build(tmpdir, name: str, files, driver: str, sanitize: str | None = None) -> str:
     """Compile the given sources (in order) with the runtime stand-ins and ``driver``.
-    ``sanitize``: address and undefined-behaviour sanitizers, device allocations and
-    dynamic shared memory of exactly the requested size and filled with 0xff bytes."""
+    ``sanitize`` ("address" or "thread", see host_compile.SANITIZE): with the
+    sanitizer, device allocations and dynamic shared memory of exactly the requested
+    size and filled with 0xff bytes."""
     text = (("#define FLINTS_HOST_SANITIZE 1\n" if sanitize else "") + RUNTIME + '#include "' + hc.ROOT
             + '/include/flints.h"\n' + "".join(source(f) + "\n" for f in files) + driver)
     return hc.build(tmpdir, name, text, warp="none", sanitize=sanitize)

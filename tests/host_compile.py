@@ -164,20 +164,25 @@ def compiler() -> str | None:
 # (array bounds, shifts, signed overflow); -O0 keeps the build short (the emulated
 # barriers, not the arithmetic, set the run time) and, without contraction or
 # fast-math, rounds exactly as -O2 does
-SANITIZE = ["-fsanitize=address,bounds,shift,signed-integer-overflow", "-fno-sanitize-recover=all",
-            "-fno-omit-frame-pointer", "-O0"]
+SANITIZE = {
+    "address": ["-fsanitize=address,bounds,shift,signed-integer-overflow", "-fno-sanitize-recover=all",
+                "-fno-omit-frame-pointer", "-O0"],
+    # data races between the emulated threads: two threads of a block touching the same
+    # word, one of them writing, with no barrier between them
+    "thread": ["-fsanitize=thread", "-O1"],
+}
 
 
-def build(tmpdir, name: str, text: str, warp: str = "identity", sanitize: bool = False) -> str:
+def build(tmpdir, name: str, text: str, warp: str = "identity", sanitize: str | None = None) -> str:
     """Compile ``SHIM`` + the warp stand-ins (``"identity"``, ``"threads"`` or none) +
-    ``text`` into an executable (strict IEEE: no contraction; ``sanitize``: with the
-    address and undefined-behaviour sanitizers, any finding ends the run)."""
+    ``text`` into an executable (strict IEEE: no contraction; ``sanitize``: "address"
+    or "thread", the run then fails on any finding)."""
     src = os.path.join(str(tmpdir), name + ".cpp")
     with open(src, "w") as f:
         f.write(SHIM + {"threads": WARP_THREADS, "identity": WARP_IDENTITY}.get(warp, "") + text)
     exe = os.path.join(str(tmpdir), name)
     r = subprocess.run([compiler(), "-std=c++20", "-O2", "-pthread", "-ffp-contract=off", "-fno-fast-math"]
-                       + (SANITIZE if sanitize else []) + [src, "-o", exe], capture_output=True, text=True)
+                       + (SANITIZE[sanitize] if sanitize else []) + [src, "-o", exe], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
     return exe
 

@@ -1,5 +1,7 @@
-"""The library's CUDA sources under the address sanitizer and the bounds, shift and
-signed-overflow checks (tests/host_compile.SANITIZE), through the host emulation of
+"""The library's CUDA sources under the sanitizers (tests/host_compile.SANITIZE).
+
+First the address sanitizer with the bounds, shift and signed-overflow checks,
+through the host emulation of
 tests/cuda_host.py with device allocations and dynamic shared memory of exactly the
 requested size and filled with 0xff bytes (device memory is not cleared): an
 access past a buffer, a static shared array's row or the requested dynamic shared
@@ -7,7 +9,9 @@ memory, a read of memory nobody wrote that changes a result, or a plan whose
 allocations flints_free does not return, fails these tests (any sanitizer finding
 ends the run with an error).  A GPU would report such an access as a fault, or
 not at all.  One script per C API (K-nearest with batches and the no-allocation
-call, the tabulated route, the synthesis), results against the oracle."""
+call, the tabulated route, the synthesis), results against the oracle.  Then the
+thread sanitizer over the same kernels, as the race check (a report fails the
+run)."""
 import numpy as np
 import pytest
 
@@ -34,9 +38,11 @@ def builds(tmp_path_factory):
     jobs = {"api": (A.FILES, A.DRIVER),
             "paper": (["common.cuh", "lens.cuh", "paper_geom.cuh", "xi_table.cu", "paper.cu"], P.DRIVER),
             "synth": (["common.cuh", "synth.cu"], S.DRIVER)}
-    with ThreadPoolExecutor(len(jobs)) as pool:  # three compiler processes at once
-        fut = {k: pool.submit(ch.build, d, k + "_san", files, drv, True) for k, (files, drv) in jobs.items()}
-        return {k: f.result() for k, f in fut.items()}
+    with ThreadPoolExecutor(2 * len(jobs)) as pool:  # six compiler processes at once
+        fut = {(k, san): pool.submit(ch.build, d, f"{k}_{san}", files, drv, san)
+               for k, (files, drv) in jobs.items() for san in ("address", "thread")}
+        out = {key: f.result() for key, f in fut.items()}
+    return {k: out[(k, "address")] for k in jobs} | {"tsan_" + k: out[(k, "thread")] for k in jobs}
 
 
 def test_k_nearest_api_under_the_sanitizers(builds):
@@ -188,3 +194,50 @@ def test_rare_kernel_branches_under_the_sanitizers(builds):
     # the other points of those tiles as in the run with finite deflections (NaN where that
     # run failed too)
     np.testing.assert_array_equal(np.delete(vb, [3, 40, 41]), np.delete(res[7][1][:96], [3, 40, 41]))
+
+
+# ------------------------------------------------------------ data races
+def _paper_line(nside, lmax, y, spin, prec, flags, seed):
+    npix = hp.npix(nside)
+    cl = wl.cl_tt(lmax, 0.7 * lmax) if spin == 0 else wl.cl_ee(lmax, 0.7 * lmax)
+    bb = None if spin == 0 else 0.3 * cl
+    m = np.random.default_rng(seed).normal(size=npix if spin == 0 else (npix, 2))
+    defl = wl.random_deflection(npix, seed + 1, rms=0.5 * np.sqrt(4 * np.pi / npix))
+    head = f"lens {nside} {lmax} {y} {spin} {prec} {flags} {0 if bb is None else 1} "
+    body = " ".join(x.hex() for x in cl) + ("" if bb is None else " " + " ".join(x.hex() for x in bb))
+    return head + body + " " + " ".join(float(x).hex() for x in np.ravel(m)) + " " + " ".join(
+        float(x).hex() for x in np.ravel(defl)) + "\n"
+
+
+def test_no_data_races_in_the_kernels(builds):
+    """The thread sanitizer over the emulated blocks (compute-sanitizer's race check
+    is not available here): every kernel of the three C APIs -- the lens kernels of
+    spin 0, 1, 2 and the augmented estimator, FP64 and mixed, the persistent class
+    and batch kernels, the stencil and supersampling modes, the no-allocation call,
+    the tabulated route's class-factor and apply kernels, the xi and synthesis
+    kernels -- runs without two threads touching the same word, one writing, with
+    no barrier between them (a report fails the run).  Removing one __syncwarp of
+    the augmented apply kernel is reported."""
+    nside, lmax = 8, 16
+    npix = hp.npix(nside)
+    s = A.Session(builds["tsan_api"])
+    for k, (spin, K, prec, flags) in enumerate([(0, 16, 0, 0), (2, 32, 1, 0), (2, 24, 0, 1), (1, 16, 1, 0)], 1):
+        cl, bb, m, _ = A._sky(0 if spin == 0 else 2, nside, lmax, 20 + k)
+        s.plan(k, nside, cl, 0.3 * cl if flags & 1 else bb, spin, K, prec, flags)
+        s.map(k, nside, np.arange(npix), m)
+        d = wl.random_deflection(npix, 30 + k, rms=0.5 * np.sqrt(4 * np.pi / npix))
+        s.lens(k, 5, 64, k, d[5:69])
+    d = wl.random_deflection(npix, 40, rms=0.5 * np.sqrt(4 * np.pi / npix))
+    s.batch([(1, 0, 64, 1, d[:64]), (2, 300, 64, 2, d[300:364])], obj=(2, 4))
+    s.stencil(2, 0, 32, d[:32])
+    s.super(1, 16, 7, 64, 1)
+    cl, _, _, _ = A._sky(2, nside, lmax, 41)
+    s.noalloc(nside, cl, None, 2, 16, 1, 0, 64, 2, d[:64])
+    res = s.run()
+    assert [len(res[3 * k + 2][0]) for k in range(4)] == [64] * 4
+    for spin, y, prec, flags in [(0, 1, 0, 0), (0, 2, 1, 0), (2, 1, 0, 1)]:
+        assert hc.run(builds["tsan_paper"], _paper_line(nside, lmax, y, spin, prec, flags, 50 + y)).startswith("0\n")
+    cl = wl.cl_ee(300, 210.0)
+    alm = wl.draw_alm(cl, 60)
+    flat = " ".join(float(x).hex() for x in np.stack([alm.real, alm.imag], -1).ravel())
+    assert hc.run(builds["tsan_synth"], f"synth 4 300 2 1 1 {flat} {flat}\n").startswith("0\n")
