@@ -221,7 +221,8 @@ def test_no_data_races_in_the_kernels(builds):
     nside, lmax = 8, 16
     npix = hp.npix(nside)
     s = A.Session(builds["tsan_api"])
-    for k, (spin, K, prec, flags) in enumerate([(0, 16, 0, 0), (2, 32, 1, 0), (2, 24, 0, 1), (1, 16, 1, 0)], 1):
+    plans = [(0, 16, 0, 0), (2, 32, 1, 0), (2, 24, 0, 1), (1, 16, 1, 0), (0, 48, 0, 0)]  # the three factor forms
+    for k, (spin, K, prec, flags) in enumerate(plans, 1):
         cl, bb, m, _ = A._sky(0 if spin == 0 else 2, nside, lmax, 20 + k)
         s.plan(k, nside, cl, 0.3 * cl if flags & 1 else bb, spin, K, prec, flags)
         s.map(k, nside, np.arange(npix), m)
@@ -234,7 +235,7 @@ def test_no_data_races_in_the_kernels(builds):
     cl, _, _, _ = A._sky(2, nside, lmax, 41)
     s.noalloc(nside, cl, None, 2, 16, 1, 0, 64, 2, d[:64])
     res = s.run()
-    assert [len(res[3 * k + 2][0]) for k in range(4)] == [64] * 4
+    assert [len(res[3 * k + 2][0]) for k in range(len(plans))] == [64] * len(plans)
     for spin, y, prec, flags in [(0, 1, 0, 0), (0, 2, 1, 0), (2, 1, 0, 1)]:
         assert hc.run(builds["tsan_paper"], _paper_line(nside, lmax, y, spin, prec, flags, 50 + y)).startswith("0\n")
     cl = wl.cl_ee(300, 210.0)
