@@ -139,10 +139,7 @@ int main() {
 """
 
 
-@pytest.fixture(scope="module")
-def run(tmp_path_factory):
-    if hc.compiler() is None:
-        pytest.skip("no host C++ compiler")
+def _build(d, sanitize=None):
     api = open(hc.CSRC + "/api.cu").read()
     a = api.index("TableGrid table_grid(")
     depth, k = 0, api.index("{", a)
@@ -157,8 +154,7 @@ def run(tmp_path_factory):
             + hc.cut("xi_table.cu", "__global__ void xi_table_kernel", "cudaError_t launch_xi_table(", False)
             + hc.cut("lens.cuh", "template <class T>\nstruct Cx {", "// Single-launch kernel", False)
             + "\n}\n" + DRIVER)
-    d = tmp_path_factory.mktemp("lens")
-    exe = hc.build(d, "lens_host", text, warp="threads")
+    exe = hc.build(d, "lens_host", text, warp="threads", sanitize=sanitize)
 
     def call(spin, K, mixed, N, cl, bb, first, defl, pix, vals):
         path = os.path.join(str(d), "map.bin")
@@ -179,6 +175,13 @@ def run(tmp_path_factory):
         return x0, status, out, var
 
     return call
+
+
+@pytest.fixture(scope="module")
+def run(tmp_path_factory):
+    if hc.compiler() is None:
+        pytest.skip("no host C++ compiler")
+    return _build(tmp_path_factory.mktemp("lens"))
 
 
 def _inputs(spin, N, lmax, ld, first, count, seed):
@@ -226,8 +229,23 @@ CASES = [(0, 64, 16, 128, 100.0, 20_000), (0, 2048, 32, 4096, 2500.0, 25_000_000
 
 @pytest.mark.parametrize("case", CASES, ids=lambda c: f"spin{c[0]}-nside{c[1]}-K{c[2]}")
 def test_lensed_values_and_variances_match_the_oracle(case, run):
+    _check_case(case, run, 32)
+
+
+def test_largest_skies_under_the_sanitizers(tmp_path_factory):
+    """The whole per-tile path at Nside 16384 (pixel indices past 2^31), spin 0 and
+    spin 2, FP64 and mixed, built with the address sanitizer and the signed-overflow
+    and bounds checks: no index computation overflows and no access leaves its array,
+    and the results still match the oracle."""
+    if hc.compiler() is None:
+        pytest.skip("no host C++ compiler")
+    run = _build(tmp_path_factory.mktemp("lens_san"), sanitize="address")
+    for case in CASES[-2:]:
+        _check_case(case, run, 16)
+
+
+def _check_case(case, run, count):
     spin, N, K, lmax, ld, first = case
-    count = 32
     cl, bb, defl, pix, vals = _inputs(spin, N, lmax, ld, first, count, seed=N + K + spin)
     weight = np.abs(cl) + (np.abs(bb) if bb is not None else 0.0)
     t_max, n = xi.grid_rule(weight, K, N)

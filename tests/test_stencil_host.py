@@ -81,10 +81,7 @@ int main() {
 """
 
 
-@pytest.fixture(scope="module")
-def run(tmp_path_factory):
-    if hc.compiler() is None:
-        pytest.skip("no host C++ compiler")
+def _build(tmpdir, sanitize=None):
     api = open(hc.CSRC + "/api.cu").read()
     a = api.index("TableGrid table_grid(")
     depth, k = 0, api.index("{", a)
@@ -98,7 +95,7 @@ def run(tmp_path_factory):
             + api[a:k + 1] + "\n"
             + hc.cut("lens.cuh", "template <class T>\nstruct Cx {", "// Single-launch kernel", False)
             + "\n}\n" + DRIVER)
-    exe = hc.build(tmp_path_factory.mktemp("stencil"), "stencil_host", text, warp="threads")
+    exe = hc.build(tmpdir, "stencil_host", text, warp="threads", sanitize=sanitize)
 
     def call(N, K, mixed, first, defl, r2_scale=1.0):
         line = f"{N} {K} {mixed} {first} {len(defl)} {r2_scale!r} " + " ".join(float(x).hex() for x in np.ravel(defl))
@@ -106,6 +103,13 @@ def run(tmp_path_factory):
         return np.array([int(r[0]) for r in rows]), np.array([[int(t) for t in r[1:]] for r in rows])
 
     return call
+
+
+@pytest.fixture(scope="module")
+def run(tmp_path_factory):
+    if hc.compiler() is None:
+        pytest.skip("no host C++ compiler")
+    return _build(tmp_path_factory.mktemp("stencil"))
 
 
 def _check(N, K, first, defl, status, idx):
@@ -168,3 +172,20 @@ def test_stencils_outside_a_shrunken_disc_are_flagged(run):
         flagged = status == (4 | 8)
         assert np.array_equal(flagged[~near], outside[~near])
         assert np.all(status[~flagged] == 0) and np.all(idx[flagged] == -1)
+
+
+def test_largest_sky_under_the_sanitizers(tmp_path_factory):
+    """The search at Nside 16384 (3.2e9 pixels, past 32-bit signed indices) and K = 48
+    built with the address sanitizer and the signed-overflow and bounds checks: no
+    index computation overflows and no access leaves its array, on both caps, both
+    cap/belt edges and the equator, FP64 and mixed kernels."""
+    if hc.compiler() is None:
+        pytest.skip("no host C++ compiler")
+    run = _build(tmp_path_factory.mktemp("stencil_san"), sanitize="address")
+    N, K, n = 16384, 48, 24
+    rng = np.random.default_rng(7)
+    for mixed in (0, 1):
+        for first in _ranges(N, n):
+            defl = rng.normal(size=(n, 2)) * wl.DEFLECTION_RMS / 4
+            status, idx = run(N, K, mixed, first, defl)
+            _check(N, K, first, defl, status, idx)
