@@ -177,6 +177,16 @@ int main() {
                                                b.status.data(), nullptr);
             printf("%d\n", rc);
             print_rows(b, count, comp);
+        } else if (o == "table") {  // plan which: the plan's xi table copied to the host
+            flints_plan_t p = g_plans[rl()];
+            const int which = (int)rl();
+            flints_plan_info i;
+            flints_get_info(p, &i);
+            std::vector<double> f(i.n_intervals + 1), g(i.n_intervals + 1);
+            printf("%d\n", flints_get_table(p, which, f.data(), g.data(), nullptr));
+            for (int k = 0; k <= i.n_intervals; ++k) printf("%a %a\n", f[k], g[k]);
+        } else if (o == "reset") {
+            printf("%d\n", flints_reset_stats(g_plans[rl()], nullptr));
         } else if (o == "reject") {  // plans of spin 0 and 2 (FP64, K = 16) and spin 1: calls refused before any launch
             flints_plan_t p0 = g_plans[rl()], p2 = g_plans[rl()], p1 = g_plans[rl()];
             flints_plan_info i;
@@ -337,6 +347,14 @@ class Session:
         self.lines.append(f"stencil {pid} {first} {count} " + self._h(defl))
         self.kinds.append("stencil")
 
+    def table(self, pid, which=0):
+        self.lines.append(f"table {pid} {which}")
+        self.kinds.append("table")
+
+    def reset(self, pid):
+        self.lines.append(f"reset {pid}")
+        self.kinds.append("map")
+
     def stats(self, pid):
         self.lines.append(f"stats {pid}")
         self.kinds.append("stats")
@@ -366,6 +384,10 @@ class Session:
             rows = [ln.split() for ln in block.strip().splitlines()]
             if kind in ("plan", "map"):
                 res.append([float.fromhex(t) if "x" in t else int(t) for t in rows[0]])
+            elif kind == "table":
+                assert rows[0] == ["0"], rows[:2]
+                fg = np.array([[float.fromhex(a) for a in r] for r in rows[1:]])
+                res.append((fg[:, 0], fg[:, 1]))
             elif kind == "reject":
                 res.append(block.strip().splitlines())
             elif kind == "stats":
@@ -781,3 +803,47 @@ def test_nonfinite_deflections_in_a_tile(spin, prec, exe):
     ref_v = ref.value if spin else ref.value.real
     assert np.max(np.abs(v[good] - ref_v)) <= tol * sigma
     assert np.max(np.abs(var[good] - ref.variance)) <= tol * x0
+
+
+def test_table_copy_and_stats_reset(exe):
+    """flints_get_table copies the plan's xi table (values and slopes at the nodes,
+    xi+ and xi- for spin 2) within the GPU test's bounds of the oracle's direct sums;
+    flints_reset_stats clears the point count and the counters, which then count
+    only the later calls."""
+    nside, lmax = 8, 16
+    npix = hp.npix(nside)
+    cl0 = wl.cl_tt(lmax, 12.0)
+    cl2 = wl.cl_ee(lmax, 12.0)
+    bb = 0.1 * cl2
+    s = Session(exe)
+    s.plan(1, nside, cl0, None, 0, 16, 0)
+    s.plan(2, nside, cl2, bb, 2, 32, 1)
+    s.table(1, 0)
+    s.table(2, 0)
+    s.table(2, 1)
+    s.map(1, nside, np.arange(npix), sht.synth_map(nside, lmax, wl.draw_alm(cl0, 3)))
+    d = wl.random_deflection(npix, 4, rms=0.5 * np.sqrt(4 * np.pi / npix))
+    s.lens(1, 0, 100, 1, d[:100])
+    s.stats(1)
+    s.reset(1)
+    s.stats(1)
+    s.lens(1, 100, 50, 1, d[100:150])
+    s.stats(1)
+    res = s.run()
+    for k, (spin, cl, b, K) in enumerate([(0, cl0, None, 16), (2, cl2, bb, 32)]):
+        weight = np.abs(cl) + (np.abs(b) if b is not None else 0.0)
+        t_max, n = xi.grid_rule(weight, K, nside)
+        nodes = np.arange(n + 1) * (t_max / n)
+        if spin == 0:
+            ref, dref = xi.xi0_direct(cl, nodes, deriv=True)
+        else:
+            ref, xm, dref, dxm = xi.xis_direct(2, cl, b, nodes, deriv=True)
+            fm, gm = res[4]
+            np.testing.assert_allclose(fm, xm / ref[0], rtol=0, atol=2e-11)
+            np.testing.assert_allclose(gm * t_max, dxm / ref[0] * t_max, rtol=0, atol=1e-9)
+        f, g = res[2 + k]
+        assert f.size == n + 1
+        np.testing.assert_allclose(f, ref / ref[0], rtol=0, atol=1e-13)
+        np.testing.assert_allclose(g * t_max, dref / ref[0] * t_max, rtol=0, atol=1e-9)
+    assert res[7][:2] == [0, 100] and res[8] == [0] and res[9] == [0, 0, 0, 0, 0, 0]
+    assert res[11][:2] == [0, 50]

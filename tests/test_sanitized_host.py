@@ -77,6 +77,8 @@ def test_k_nearest_api_under_the_sanitizers(builds):
     s.noalloc(nside, cl, None, 2, 32, 1, 10, 100, 2, d1[10:110])
     s.reject(1, 2, 3)
     s.nreject()
+    s.table(2, 0)
+    s.table(3, 1)  # xi- of the augmented plan, into host buffers of exactly n + 1 values
     res = s.run()
     for k, (ref, sigma, x0, prec, flags) in enumerate(refs):
         st, v, var = res[3 * k + 2]
@@ -92,7 +94,8 @@ def test_k_nearest_api_under_the_sanitizers(builds):
     # against the oracle by the unsanitized tests)
     assert [len(r[0]) for r in res[12]] == [100, 68] and len(res[13][0]) == 64 and len(res[14][0]) == 100
     assert len(res[15][0]) == 100
-    assert res[-2][-1] == "untouched 1" and res[-1][-1] == "untouched 1"
+    assert res[16][-1] == "untouched 1" and res[17][-1] == "untouched 1"
+    assert res[18][0][0] == 1.0 and res[19][0][0] == 0.0  # xi+(0)/xi+(0), xi-(0)
 
 
 def test_tabulated_route_under_the_sanitizers(builds):
