@@ -122,6 +122,8 @@ typedef struct {
     int n_intervals;     /* cubic Hermite intervals of the xi table */
     double xi0;          /* xi(0) (spin 0) or xi+(0) (spin 1, 2) */
     double search_radius;/* chord radius of the stencil disc */
+    int64_t device_bytes;/* device memory the plan holds: its spectrum and xi tables,
+                          * interpolation coefficients, counters and launch queues */
 } flints_plan_info;
 
 /* Create a plan: copy the spectrum to the device and tabulate xi on the GPU

@@ -39,7 +39,7 @@ class _Stats(ctypes.Structure):
 class _Info(ctypes.Structure):
     _fields_ = [("nside", ctypes.c_int64), ("lmax", ctypes.c_int), ("spin", ctypes.c_int), ("K", ctypes.c_int),
                 ("precision", ctypes.c_int), ("t_max", ctypes.c_double), ("n_intervals", ctypes.c_int),
-                ("xi0", ctypes.c_double), ("search_radius", ctypes.c_double)]
+                ("xi0", ctypes.c_double), ("search_radius", ctypes.c_double), ("device_bytes", ctypes.c_int64)]
 
 
 class _PaperInfo(ctypes.Structure):
@@ -194,6 +194,7 @@ class Info:
     n_intervals: int
     xi0: float
     search_radius: float
+    device_bytes: int
 
 
 class Plan:
@@ -240,15 +241,12 @@ class Plan:
     def info(self) -> Info:
         i = _Info()
         _check(_lib.flints_get_info(self._h, ctypes.byref(i)))
-        return Info(i.nside, i.lmax, i.spin, i.K, i.precision, i.t_max, i.n_intervals, i.xi0, i.search_radius)
+        return Info(i.nside, i.lmax, i.spin, i.K, i.precision, i.t_max, i.n_intervals, i.xi0, i.search_radius,
+                    i.device_bytes)
 
     def device_bytes(self) -> int:
-        """Device memory the plan holds (what flints_plan allocates for its tables,
-        from the plan's lmax, spin and interval count)."""
-        i = self.info()
-        two = 2 if i.spin != 0 else 1
-        return ((i.lmax + 1) * 8 * two + 4 * (i.n_intervals + 1) * 8
-                + two * i.n_intervals * (32 + 32) + 5 * 8)
+        """Device memory the plan holds, as the library counted its allocations."""
+        return self.info().device_bytes
 
     def table(self, which: int = 0, stream=None):
         n = self.info().n_intervals + 1

@@ -73,6 +73,7 @@ struct flints_plan_s {
     unsigned char *d_jt;
     int jt_wpb, jt_bps;
     int64_t points;
+    int64_t device_bytes;  // sum of the plan's device allocations
     LaunchCfg cfg;
 };
 
@@ -222,7 +223,8 @@ int flints_plan(flints_plan_t *out, int64_t nside, int lmax, const double *cl, c
         free_plan_memory(p);                               \
         delete p;                                          \
         return cuda_fail(e, "flints_plan: cudaMalloc");    \
-    }
+    }                                                      \
+    p->device_bytes += (int64_t)(bytes)
     ALLOC(p->d_cl, ncl * sizeof(double));
     if (spin != 0 && cl_bb) {
         ALLOC(p->d_clbb, ncl * sizeof(double));
@@ -687,6 +689,7 @@ int flints_get_info(flints_plan_t p, flints_plan_info *info) {
     info->n_intervals = p->n;
     info->xi0 = p->xi0;
     info->search_radius = p->r;
+    info->device_bytes = p->device_bytes;
     return FLINTS_OK;
 }
 

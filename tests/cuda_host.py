@@ -30,6 +30,7 @@ RUNTIME = r"""
 #include <algorithm>
 #include <atomic>
 #include <cstddef>
+#include <map>
 #include <mutex>
 #include <thread>
 #include <type_traits>
@@ -45,22 +46,46 @@ enum cudaDeviceAttr { cudaDevAttrMultiProcessorCount, cudaDevAttrMaxSharedMemory
 #ifdef FLINTS_HOST_SANITIZE
 // exact sizes (so that the address sanitizer sees an access past the end) and
 // contents that are not zero (device memory is not cleared)
-static inline cudaError_t cudaMalloc(void **p, size_t n) {
+static inline cudaError_t host_alloc_raw(void **p, size_t n) {
     if (posix_memalign(p, 256, n ? n : 1)) return cudaErrorMemoryAllocation;
     std::memset(*p, 0xff, n ? n : 1);
     return cudaSuccess;
 }
 #else
-static inline cudaError_t cudaMalloc(void **p, size_t n) {
+static inline cudaError_t host_alloc_raw(void **p, size_t n) {
     *p = std::aligned_alloc(256, (n + 255) / 256 * 256 + 256);
     return *p ? cudaSuccess : cudaErrorMemoryAllocation;
 }
 #endif
+// ledger of live device allocations (bytes as requested), for the drivers' checks
+static std::mutex g_dev_mutex;
+static std::map<void *, size_t> g_dev_allocs;
+static size_t g_dev_live = 0;
+static inline cudaError_t cudaMalloc(void **p, size_t n) {
+    const cudaError_t e = host_alloc_raw(p, n);
+    if (e == cudaSuccess) {
+        std::lock_guard<std::mutex> lk(g_dev_mutex);
+        g_dev_allocs[*p] = n;
+        g_dev_live += n;
+    }
+    return e;
+}
 template <class T> static inline cudaError_t cudaMalloc(T **p, size_t n) { return cudaMalloc((void **)p, n); }
-static inline cudaError_t cudaFree(void *p) { std::free(p); return cudaSuccess; }
+static inline cudaError_t cudaFree(void *p) {
+    if (p) {
+        std::lock_guard<std::mutex> lk(g_dev_mutex);
+        auto it = g_dev_allocs.find(p);
+        if (it != g_dev_allocs.end()) {
+            g_dev_live -= it->second;
+            g_dev_allocs.erase(it);
+        }
+    }
+    std::free(p);
+    return cudaSuccess;
+}
 enum { cudaHostAllocDefault = 0 };
-static inline cudaError_t cudaHostAlloc(void **p, size_t n, unsigned) { return cudaMalloc(p, n); }
-static inline cudaError_t cudaFreeHost(void *p) { return cudaFree(p); }
+static inline cudaError_t cudaHostAlloc(void **p, size_t n, unsigned) { return host_alloc_raw(p, n); }
+static inline cudaError_t cudaFreeHost(void *p) { std::free(p); return cudaSuccess; }
 static inline cudaError_t cudaGetSymbolAddress(void **p, const void *sym) { *p = const_cast<void *>(sym); return cudaSuccess; }
 static inline cudaError_t cudaMemcpyAsync(void *d, const void *s, size_t n, cudaMemcpyKind, cudaStream_t = 0) {
     std::memmove(d, s, n);

@@ -133,6 +133,7 @@ int main(void) {
     S(flints_plan_info); F(flints_plan_info, nside); F(flints_plan_info, lmax); F(flints_plan_info, spin);
     F(flints_plan_info, K); F(flints_plan_info, precision); F(flints_plan_info, t_max);
     F(flints_plan_info, n_intervals); F(flints_plan_info, xi0); F(flints_plan_info, search_radius);
+    F(flints_plan_info, device_bytes);
     S(flints_launch_cfg); F(flints_launch_cfg, warps_per_block); F(flints_launch_cfg, blocks_per_sm);
     F(flints_launch_cfg, tile_points);
     S(flints_job); F(flints_job, plan); F(flints_job, first); F(flints_job, count); F(flints_job, map);

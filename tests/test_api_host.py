@@ -60,12 +60,15 @@ int main() {
             for (double &v : cl) v = rd();
             if (has_bb) for (double &v : bb) v = rd();
             flints_plan_t p = nullptr;
+            const size_t live = g_dev_live;
             const int rc = flints_plan(&p, nside, lmax, cl.data(), has_bb ? bb.data() : nullptr, spin, K, prec,
                                        (unsigned)flags, nullptr);
             g_plans[id] = p;
             flints_plan_info i{};
             if (rc == 0) flints_get_info(p, &i);
-            printf("%d %a %d %a\n", rc, i.t_max, i.n_intervals, i.xi0);
+            // the plan's reported device bytes, and what it allocated
+            printf("%d %a %d %a %lld %lld\n", rc, i.t_max, i.n_intervals, i.xi0, (long long)i.device_bytes,
+                   (long long)(g_dev_live - live));
         } else if (o == "launch") {  // plan warps_per_block blocks_per_sm tile_points
             flints_plan_t p = g_plans[rl()];
             flints_launch_cfg cfg{(int)rl(), (int)rl(), (int)rl()};
@@ -297,7 +300,14 @@ int main() {
         printf("end\n");
         fflush(stdout);
     }
-    for (auto &kv : g_plans) flints_free(kv.second);  // every plan's allocations come back (leak check)
+    const size_t live = g_dev_live;
+    long long held = 0;
+    for (auto &kv : g_plans) {
+        flints_plan_info i{};
+        if (kv.second && flints_get_info(kv.second, &i) == 0) held += i.device_bytes;
+        flints_free(kv.second);  // every plan's allocations come back (leak check)
+    }
+    if ((long long)(live - g_dev_live) != held) return 4;  // flints_free returned what the plans reported
     return 0;
 }
 """
@@ -847,3 +857,20 @@ def test_table_copy_and_stats_reset(exe):
         np.testing.assert_allclose(g * t_max, dref / ref[0] * t_max, rtol=0, atol=1e-9)
     assert res[7][:2] == [0, 100] and res[8] == [0] and res[9] == [0, 0, 0, 0, 0, 0]
     assert res[11][:2] == [0, 50]
+
+
+def test_plan_reports_the_device_memory_it_holds(exe):
+    """flints_get_info's device_bytes equals what flints_plan allocated on the device
+    (counted by the runtime stand-in) for spin 0, 1, 2 and augmented plans, and
+    flints_free returns exactly that (the driver exits with an error otherwise); the
+    serving loop charges this figure against its memory budget."""
+    nside, lmax = 8, 16
+    s = Session(exe)
+    cases = [(0, 16, 0, 0, False), (2, 32, 1, 0, True), (2, 24, 0, 1, True), (1, 16, 1, 0, False),
+             (2, 48, 0, 0, False)]
+    for k, (spin, K, prec, flags, with_bb) in enumerate(cases, 1):
+        cl = wl.cl_tt(lmax, 12.0) if spin == 0 else wl.cl_ee(lmax, 12.0)
+        s.plan(k, nside, cl, 0.3 * cl if with_bb else None, spin, K, prec, flags)
+    res = s.run()
+    for r, case in zip(res, cases):
+        assert r[0] == 0 and r[4] == r[5] > 0, (case, r)
