@@ -368,7 +368,8 @@ void flints_free(flints_plan_t plan);
  *   positions (and frames, spin 1, 2), the stencil table and the L^-1 blocks,
  *   then synchronises `stream`.  Device memory: 32 bytes per map pixel,
  *   12 Nside_c^2 (K + 1) int32, slots * len doubles (len below; complex
- *   blocks twice that); flints_paper_get_info reports the total.
+ *   blocks twice that), reported by flints_paper_get_info as table_bytes,
+ *   plus the xi tables (device_bytes is the whole).
  *   Errors: FLINTS_EINVAL (arguments; a stencil chord beyond the table
  *   domain), FLINTS_ENOMEM, FLINTS_ECUDA; message in flints_paper_last_error().
  * flints_paper_lens: lensed values at targets first .. first+count-1 (RING
@@ -419,6 +420,8 @@ typedef struct flints_paper_info {
     int precision;          /* FLINTS_FP64 or FLINTS_MIXED */
     int spin;               /* 0, 1 or 2 */
     unsigned flags;         /* FLINTS_SPIN2_AUGMENTED or 0 */
+    int64_t device_bytes;   /* all device memory the plan holds: table_bytes plus the
+                             * spectrum, xi tables, coefficients and counters */
 } flints_paper_info;
 int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double *cl, const double *cl_bb, int y,
                       int spin, int precision, unsigned flags, void *stream);

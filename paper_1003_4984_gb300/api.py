@@ -48,7 +48,7 @@ class _PaperInfo(ctypes.Structure):
                 ("xi0", ctypes.c_double), ("table_bytes", ctypes.c_int64), ("max_pair_t", ctypes.c_double),
                 ("nugget_slots", ctypes.c_int64), ("failed_slots", ctypes.c_int64), ("points", ctypes.c_int64),
                 ("window", ctypes.c_int64), ("precision", ctypes.c_int), ("spin", ctypes.c_int),
-                ("flags", ctypes.c_uint)]
+                ("flags", ctypes.c_uint), ("device_bytes", ctypes.c_int64)]
 
 
 class LaunchCfg(ctypes.Structure):

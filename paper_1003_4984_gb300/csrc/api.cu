@@ -217,14 +217,16 @@ int flints_plan(flints_plan_t *out, int64_t nside, int lmax, const double *cl, c
     const size_t ncl = (size_t)(lmax + 1);
     const size_t nn = (size_t)p->n + 1;
     cudaError_t e;
-#define ALLOC(ptr, bytes)                                  \
-    e = cudaMalloc((void **)&(ptr), (bytes));              \
-    if (e != cudaSuccess) {                                \
-        free_plan_memory(p);                               \
-        delete p;                                          \
-        return cuda_fail(e, "flints_plan: cudaMalloc");    \
-    }                                                      \
-    p->device_bytes += (int64_t)(bytes)
+#define ALLOC(ptr, bytes)                                      \
+    do {                                                       \
+        e = cudaMalloc((void **)&(ptr), (bytes));              \
+        if (e != cudaSuccess) {                                \
+            free_plan_memory(p);                               \
+            delete p;                                          \
+            return cuda_fail(e, "flints_plan: cudaMalloc");    \
+        }                                                      \
+        p->device_bytes += (int64_t)(bytes);                   \
+    } while (0)
     ALLOC(p->d_cl, ncl * sizeof(double));
     if (spin != 0 && cl_bb) {
         ALLOC(p->d_clbb, ncl * sizeof(double));

@@ -1801,6 +1801,7 @@ struct flints_paper_s {
     float4 *d_cm32;
     unsigned long long *d_counters, *d_maxt;
     int64_t points;
+    int64_t device_bytes;  // sum of the plan's device allocations
 };
 
 static thread_local char g_perr[512] = "no error";
@@ -1911,8 +1912,11 @@ int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double
         delete p;
         return pcuda(err, what);
     };
-#define PALLOC(ptr, bytes)                                   \
-    if ((e = cudaMalloc((void **)&(ptr), (bytes))) != cudaSuccess) return bail(e, "flints_paper_plan: cudaMalloc");
+#define PALLOC(ptr, bytes)                                                                                   \
+    do {                                                                                                     \
+        if ((e = cudaMalloc((void **)&(ptr), (bytes))) != cudaSuccess) return bail(e, "flints_paper_plan: cudaMalloc"); \
+        p->device_bytes += (int64_t)(bytes);                                                                 \
+    } while (0)
     PALLOC(p->d_cl, (size_t)(lmax + 1) * sizeof(double));
     PALLOC(p->d_f, nn * sizeof(double));
     PALLOC(p->d_g, nn * sizeof(double));
@@ -2050,6 +2054,7 @@ int flints_paper_plan(flints_paper_t *out, int64_t nside, int lmax, const double
     if (precision == FLINTS_MIXED) {  // only the double-float blocks are kept
         cudaFree(p->d_linv);
         p->d_linv = nullptr;
+        p->device_bytes -= (int64_t)((size_t)p->nslot * lv * sizeof(double));
     }
     *out = p;
     return FLINTS_OK;
@@ -2200,6 +2205,7 @@ int flints_paper_get_info(flints_paper_t p, flints_paper_info *info, void *strea
     info->failed_slots = p->failed_slots;
     info->points = p->points;
     info->window = (int64_t)c[CNT_WINDOW];
+    info->device_bytes = p->device_bytes;
     return FLINTS_OK;
 }
 

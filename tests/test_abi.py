@@ -143,7 +143,7 @@ int main(void) {
     F(flints_paper_info, n_intervals); F(flints_paper_info, xi0); F(flints_paper_info, table_bytes);
     F(flints_paper_info, max_pair_t); F(flints_paper_info, nugget_slots); F(flints_paper_info, failed_slots);
     F(flints_paper_info, points); F(flints_paper_info, window); F(flints_paper_info, precision);
-    F(flints_paper_info, spin); F(flints_paper_info, flags);
+    F(flints_paper_info, spin); F(flints_paper_info, flags); F(flints_paper_info, device_bytes);
     printf("const FLINTS_FP64 %d\nconst FLINTS_MIXED %d\n", FLINTS_FP64, FLINTS_MIXED);
     printf("const FLINTS_SPIN2_AUGMENTED %u\nconst FLINTS_ROTATE_TO_TARGET %u\n", FLINTS_SPIN2_AUGMENTED,
            FLINTS_ROTATE_TO_TARGET);

@@ -77,11 +77,37 @@ static void reject(long long nside, int lmax) {
     flints_paper_free(p2);
 }
 
+// Device memory of plans of every kind: what the plan reports (table_bytes and
+// device_bytes), what it allocated (the runtime stand-in's ledger) and what
+// flints_paper_free returns.
+static void bytes(long long nside, int lmax) {
+    std::vector<double> cl(lmax + 1);
+    for (double &v : cl) v = rd();
+    const int kinds[6][4] = {{1, 0, 0, 0}, {2, 0, 1, 0}, {1, 1, 1, 0}, {2, 2, 0, 0}, {1, 2, 1, 0}, {2, 2, 0, 1}};
+    for (const auto &k : kinds) {  // y, spin, precision, flags
+        flints_paper_t p = nullptr;
+        const size_t live = g_dev_live;
+        const int rc = flints_paper_plan(&p, nside, lmax, cl.data(), nullptr, k[0], k[1], k[2], (unsigned)k[3],
+                                         nullptr);
+        flints_paper_info i{};
+        if (rc == 0) flints_paper_get_info(p, &i, nullptr);
+        const size_t held = g_dev_live;
+        flints_paper_free(p);
+        printf("%d %lld %lld %lld %lld\n", rc, (long long)i.table_bytes, (long long)i.device_bytes,
+               (long long)(held - live), (long long)(held - g_dev_live));
+    }
+}
+
 int main() {
     long long nside;
     int lmax, y, spin, prec, flags, has_bb;
     char op[16];
     while (scanf("%15s", op) == 1) {
+        if (std::string(op) == "bytes") {
+            if (scanf("%lld %d", &nside, &lmax) != 2) return 2;
+            bytes(nside, lmax);
+            continue;
+        }
         if (std::string(op) == "reject") {
             if (scanf("%lld %d", &nside, &lmax) != 2) return 2;
             reject(nside, lmax);
@@ -231,3 +257,17 @@ def test_nonfinite_deflections_on_the_tabulated_route(prec, run):
     assert np.all(np.isnan(v[bad])) and np.all(np.isnan(s2[bad]))
     np.testing.assert_array_equal(v[good], v0[good])
     np.testing.assert_array_equal(s2[good], s0[good])
+
+
+def test_plans_report_the_device_memory_they_hold(run):
+    """flints_paper_get_info's device_bytes equals what flints_paper_plan allocated
+    (counted by the runtime stand-in) and what flints_paper_free returns, for spin 0,
+    1 and 2, y = 1 and 2, FP64, mixed and augmented plans; table_bytes (pixel,
+    stencil and class tables, L^-1 blocks) is part of it."""
+    for nside in (8, 16):
+        cl = wl.cl_tt(32, 22.0)
+        lines = hc.run(run.exe, f"bytes {nside} 32 " + " ".join(x.hex() for x in cl) + "\n").splitlines()
+        assert len(lines) == 6
+        for line in lines:
+            rc, table, dev, alloc, freed = map(int, line.split())
+            assert rc == 0 and 0 < table < dev == alloc == freed, (nside, line)
