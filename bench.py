@@ -1088,7 +1088,8 @@ def run_paper(args):
                     arm = {
                         "value": BATCH * steps / (ev[0].elapsed_time(ev[steps]) / 1e3), "unit": "pts/s",
                         "ms_per_step": statistics.mean(per), "K": K, "plan_s": plan_s, "slots": info["slots"],
-                        "table_bytes": info["table_bytes"], "window": info["window"],
+                        "table_bytes": info["table_bytes"], "device_bytes": info["device_bytes"],
+                        "window": info["window"],
                         "nugget_slots": info["nugget_slots"], "failed_slots": info["failed_slots"],
                         "predicted_precision": math.sqrt(float(var.mean()) / info["xi0"])}
                     # the method's flops per target (whatever precision executes them), and for
