@@ -60,13 +60,14 @@ static inline cudaError_t host_alloc_raw(void **p, size_t n) {
 // ledger of live device allocations (bytes as requested), for the drivers' checks
 static std::mutex g_dev_mutex;
 static std::map<void *, size_t> g_dev_allocs;
-static size_t g_dev_live = 0;
+static size_t g_dev_live = 0, g_dev_alloc_calls = 0;
 static inline cudaError_t cudaMalloc(void **p, size_t n) {
     const cudaError_t e = host_alloc_raw(p, n);
     if (e == cudaSuccess) {
         std::lock_guard<std::mutex> lk(g_dev_mutex);
         g_dev_allocs[*p] = n;
         g_dev_live += n;
+        ++g_dev_alloc_calls;
     }
     return e;
 }

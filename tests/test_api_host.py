@@ -7,7 +7,10 @@ entry point, with the kernels' threads running freely between barriers.
 Results are compared with the FP64 oracle (whole skies at Nside 8 and 16,
 and a band of the Nside 4096 spin-2 workload) within the GPU tolerances, and
 the alternative entry points with each other (identical, as they run the
-same per-tile code)."""
+same per-tile code).  Every run also checks, at exit, that the per-call entry
+points (lensing, supersampling, stencils, staging and launching a batch, the
+no-allocation call) made no device allocation and that flints_free returned
+what the plans reported holding."""
 import numpy as np
 import pytest
 
@@ -25,6 +28,7 @@ DRIVER = r"""
 static double rd() { char b[64]; if (scanf("%63s", b) != 1) exit(2); return strtod(b, nullptr); }
 static long long rl() { long long v; if (scanf("%lld", &v) != 1) exit(2); return v; }
 static std::map<long long, flints_plan_t> g_plans;
+static int g_hot_allocs = 0;  // per-call entry points that allocated device memory (none may)
 static std::map<long long, double *> g_maps;
 struct Buffers {
     std::vector<double> defl, out, var;
@@ -96,6 +100,7 @@ int main() {
             double *m = g_maps[rl()];
             Buffers b = read_job(count, comp);
             int rc;
+            const size_t a0 = g_dev_alloc_calls;
             if (o == "lens")
                 rc = flints_lens_range(p, first, count, m, b.defl.data(), b.out.data(), b.var.data(), b.status.data(),
                                        nullptr);
@@ -104,6 +109,7 @@ int main() {
                                : flints_lens_spin2(p, m, b.defl.data(), b.out.data(), b.var.data(), nullptr);
                 std::fill(b.status.begin(), b.status.end(), 0);
             }
+            g_hot_allocs += g_dev_alloc_calls != a0;
             printf("%d\n", rc);
             print_rows(b, count, comp);
         } else if (o == "super") {
@@ -115,8 +121,10 @@ int main() {
             b.out.assign(comp * count, 0.0);
             b.var.assign(count, 0.0);
             b.status.assign(count, 255);
+            const size_t a0 = g_dev_alloc_calls;
             const int rc = flints_supersample(p, nout, first, count, m, b.out.data(), b.var.data(), b.status.data(),
                                               nullptr);
+            g_hot_allocs += g_dev_alloc_calls != a0;
             printf("%d\n", rc);
             print_rows(b, count, comp);
         } else if (o == "stencil") {
@@ -126,7 +134,9 @@ int main() {
             const long long first = rl(), count = rl();
             Buffers b = read_job(count, 1);
             std::vector<int64_t> idx((size_t)count * i.K, -9);
+            const size_t a0 = g_dev_alloc_calls;
             const int rc = flints_stencil(p, first, count, b.defl.data(), idx.data(), b.status.data(), nullptr);
+            g_hot_allocs += g_dev_alloc_calls != a0;
             printf("%d\n", rc);
             for (long long q = 0; q < count; ++q) {
                 printf("%d", (int)b.status[q]);
@@ -158,9 +168,11 @@ int main() {
             if (o == "batch") rc = flints_lens_batch(jobs.data(), n, nullptr);
             else {
                 flints_batch_t bt = nullptr;
-                rc = flints_batch_create(&bt, n);
+                rc = flints_batch_create(&bt, n);  // allocates; staging and launching must not
+                const size_t a0 = g_dev_alloc_calls;
                 if (rc == 0) rc = flints_batch_stage(bt, jobs.data(), n, cfg.tile_points);
                 if (rc == 0) rc = flints_batch_launch(bt, &cfg, nullptr);
+                g_hot_allocs += g_dev_alloc_calls != a0;
                 flints_batch_free(bt);
             }
             printf("%d\n", rc);
@@ -175,9 +187,11 @@ int main() {
             double *m = g_maps[rl()];
             const int comp = spin == 0 ? 1 : 2;
             Buffers b = read_job(count, comp);
+            const size_t a0 = g_dev_alloc_calls;
             const int rc = flints_lens_noalloc(nside, lmax, cl.data(), has_bb ? bb.data() : nullptr, spin, K, prec,
                                                first, count, m, b.defl.data(), b.out.data(), b.var.data(),
                                                b.status.data(), nullptr);
+            g_hot_allocs += g_dev_alloc_calls != a0;
             printf("%d\n", rc);
             print_rows(b, count, comp);
         } else if (o == "table") {  // plan which: the plan's xi table copied to the host
@@ -308,6 +322,7 @@ int main() {
         flints_free(kv.second);  // every plan's allocations come back (leak check)
     }
     if ((long long)(live - g_dev_live) != held) return 4;  // flints_free returned what the plans reported
+    if (g_hot_allocs) return 5;  // a lens, supersampling, stencil, batch-launch or no-allocation call allocated
     return 0;
 }
 """
