@@ -126,8 +126,11 @@ int main() {
         flints_paper_t h = nullptr;
         int rc = flints_paper_plan(&h, nside, lmax, cl.data(), has_bb ? bb.data() : nullptr, y, spin, prec, flags,
                                    nullptr);
-        if (rc == 0)
+        if (rc == 0) {
+            const size_t a0 = g_dev_alloc_calls;
             rc = flints_paper_lens(h, 0, npix, map.data(), defl.data(), out.data(), var.data(), status.data(), nullptr);
+            if (g_dev_alloc_calls != a0) return 5;  // the per-call path allocates nothing
+        }
         printf("%d\n", rc);
         if (rc != 0) { printf("%s\n", flints_paper_last_error()); continue; }
         for (long long p = 0; p < npix; ++p) {
